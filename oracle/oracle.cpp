@@ -1,0 +1,1396 @@
+// FP64 CPU oracle for the SBR radio-map method of the Sionna RT technical
+// report (arXiv 2504.21719).  TEST INFRASTRUCTURE ONLY: it is loaded by the
+// test-suite, the smoke check and the benchmark's CPU-baseline leg, never by
+// the product path.  It shares no code, header or constant table with the
+// CUDA library; the only common input is the seeded scene data.
+//
+// What it computes (each function names the passage it follows):
+//   * spherical Fibonacci lattice (Sec. 3.1.1);
+//   * transmitter field from antenna pattern and orientation (App. A.1,
+//     Eqs. rotation / theta_phi_prime / F_prime_2_F, antenna pattern Eq. C);
+//   * closest hit by brute force over every triangle (Moller-Trumbore, FP64);
+//   * Fresnel coefficients for incidence from vacuum (Eq. fresnel_vac) and the
+//     single-layer slab (Eqs. fresnel_slab, q_fresnel_slab), complex
+//     permittivity (Eq. eta);
+//   * interaction-type sampling q(R), q(T) (Eq. path-solver-used-dist-event
+//     with S = 0 and q(D) = 0), field update with the TE/TM basis
+//     (Eqs. fresnel_in_vectors, fresnel_out_vectors, reflected_refracted_vectors);
+//   * the radio-map Monte-Carlo estimator (Eq. radio-map-solver-ci-all-2-estimator
+//     with n_S = 0) where the squared tube length cancels against the 1/r
+//     spreading of the path gain (Eq. radio-map-solver-path-gain, Alg. 2);
+//   * a branch-all enumeration (every reflection AND refraction branch, no
+//     sampling) that gives the estimator's exact expectation on tiny scenes;
+//   * forward-mode dual numbers for the gradient with frozen discrete choices;
+//   * a reference LBVH (Morton codes + stable sort + top-down binary radix
+//     tree) that the GPU tree must equal bit for bit.
+//
+// Readings of points the paper leaves open are stated where they are used.
+//
+// Parity status: every function here is pinned by a CPU test to a closed
+// form, an identity, a library routine or brute force (tests/test_oracle_*.py);
+// none is "parity unpinned".
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double C0 = 299792458.0;          // speed of light in vacuum, m/s
+constexpr double EPS0 = 8.8541878128e-12;   // vacuum permittivity, F/m (CODATA 2018)
+
+// ---------------------------------------------------------------------------
+// dual numbers (value + NT tangents) for the frozen-choice gradient
+// ---------------------------------------------------------------------------
+constexpr int NT = 19;  // 8 permittivities + 8 conductivities + 3 TX coordinates
+
+struct D {
+    double v;
+    double g[NT];
+    D() : v(0) { std::memset(g, 0, sizeof g); }
+    D(double x) : v(x) { std::memset(g, 0, sizeof g); }  // NOLINT: implicit by design
+};
+inline D operator+(const D& a, const D& b) { D r(a.v + b.v); for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] + b.g[i]; return r; }
+inline D operator-(const D& a, const D& b) { D r(a.v - b.v); for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] - b.g[i]; return r; }
+inline D operator-(const D& a) { D r(-a.v); for (int i = 0; i < NT; ++i) r.g[i] = -a.g[i]; return r; }
+inline D operator*(const D& a, const D& b) { D r(a.v * b.v); for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] * b.v + a.v * b.g[i]; return r; }
+inline D operator/(const D& a, const D& b) {
+    D r(a.v / b.v);
+    const double ib = 1.0 / b.v;
+    for (int i = 0; i < NT; ++i) r.g[i] = (a.g[i] - r.v * b.g[i]) * ib;
+    return r;
+}
+inline D operator+(const D& a, double b) { D r = a; r.v += b; return r; }
+inline D operator+(double b, const D& a) { return a + b; }
+inline D operator-(const D& a, double b) { D r = a; r.v -= b; return r; }
+inline D operator-(double b, const D& a) { return (-a) + b; }
+inline D operator*(const D& a, double b) { D r(a.v * b); for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] * b; return r; }
+inline D operator*(double b, const D& a) { return a * b; }
+inline D operator/(const D& a, double b) { return a * (1.0 / b); }
+inline D operator/(double a, const D& b) { return D(a) / b; }
+inline D& operator+=(D& a, const D& b) { a = a + b; return a; }
+
+inline double val(double x) { return x; }
+inline double val(const D& x) { return x.v; }
+inline double r_sqrt(double x) { return std::sqrt(x); }
+inline D r_sqrt(const D& a) {
+    D r(std::sqrt(a.v));
+    const double k = (r.v > 0) ? 0.5 / r.v : 0.0;
+    for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] * k;
+    return r;
+}
+inline double r_sin(double x) { return std::sin(x); }
+inline double r_cos(double x) { return std::cos(x); }
+inline double r_exp(double x) { return std::exp(x); }
+inline D r_sin(const D& a) { D r(std::sin(a.v)); const double c = std::cos(a.v); for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] * c; return r; }
+inline D r_cos(const D& a) { D r(std::cos(a.v)); const double s = -std::sin(a.v); for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] * s; return r; }
+inline D r_exp(const D& a) { D r(std::exp(a.v)); for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] * r.v; return r; }
+template <class R> inline R r_abs(const R& a) { return val(a) < 0 ? R(-a) : a; }
+
+// ---------------------------------------------------------------------------
+// complex numbers over a real type R (std::complex is unspecified for D)
+// ---------------------------------------------------------------------------
+template <class R>
+struct Cx {
+    R re, im;
+    Cx() : re(0.0), im(0.0) {}
+    Cx(const R& a) : re(a), im(0.0) {}  // NOLINT
+    Cx(const R& a, const R& b) : re(a), im(b) {}
+};
+template <class R> inline Cx<R> operator+(const Cx<R>& a, const Cx<R>& b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> inline Cx<R> operator-(const Cx<R>& a, const Cx<R>& b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> inline Cx<R> operator*(const Cx<R>& a, const Cx<R>& b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R> inline Cx<R> operator*(const Cx<R>& a, const R& s) { return {a.re * s, a.im * s}; }
+template <class R> inline Cx<R> operator/(const Cx<R>& a, const Cx<R>& b) {
+    R d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+template <class R> inline R abs2(const Cx<R>& a) { return a.re * a.re + a.im * a.im; }
+
+// Principal square root, written from the definition
+//   sqrt(z) = sqrt((|z|+x)/2) + j sgn(y) sqrt((|z|-x)/2),
+// evaluated in the cancellation-free arrangement of Kahan, "Branch cuts for
+// complex elementary functions" (1987): the larger of the two parts comes from
+// a square root, the smaller one from y / (2 * larger).
+template <class R>
+Cx<R> csqrt(const Cx<R>& z) {
+    const double xv = val(z.re), yv = val(z.im);
+    if (xv == 0.0 && yv == 0.0) return Cx<R>(R(0.0), R(0.0));
+    // |z| scaled by a constant so that the squares neither underflow nor overflow
+    const double sc = std::max(std::fabs(xv), std::fabs(yv));
+    R xs = z.re / sc, ys = z.im / sc;
+    R m = r_sqrt(xs * xs + ys * ys) * sc;
+    if (xv >= 0.0) {
+        R a = r_sqrt((m + z.re) * 0.5);
+        return Cx<R>(a, z.im / (a * 2.0));
+    }
+    R b = r_sqrt((m - z.re) * 0.5);
+    R a = r_abs(z.im) / (b * 2.0);
+    return Cx<R>(a, std::signbit(yv) ? R(-b) : b);
+}
+// exp(-j w) for complex w = a + j b:  exp(b) (cos a - j sin a)
+template <class R>
+Cx<R> cexp_mj(const Cx<R>& w) {
+    R e = r_exp(w.im);
+    return Cx<R>(e * r_cos(w.re), -(e * r_sin(w.re)));
+}
+
+// ---------------------------------------------------------------------------
+// small vectors
+// ---------------------------------------------------------------------------
+template <class R>
+struct V3 {
+    R x, y, z;
+};
+template <class R> inline V3<R> operator+(const V3<R>& a, const V3<R>& b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R> inline V3<R> operator-(const V3<R>& a, const V3<R>& b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class R, class S> inline V3<R> scl(const V3<R>& a, const S& s) { return {a.x * s, a.y * s, a.z * s}; }
+inline double dot(const V3<double>& a, const V3<double>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3<double> cross(const V3<double>& a, const V3<double>& b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline double norm(const V3<double>& a) { return std::sqrt(dot(a, a)); }
+inline V3<double> unit(const V3<double>& a) { return scl(a, 1.0 / norm(a)); }
+template <class R> inline V3<R> lift(const V3<double>& a) { return {R(a.x), R(a.y), R(a.z)}; }
+template <class R> inline V3<double> vval(const V3<R>& a) { return {val(a.x), val(a.y), val(a.z)}; }
+// position + t * direction with a real-typed t
+template <class R> inline V3<R> axpy(const V3<R>& o, const R& t, const V3<double>& k) {
+    return {o.x + t * k.x, o.y + t * k.y, o.z + t * k.z};
+}
+
+// complex 3-vector (a field phasor in global Cartesian coordinates)
+template <class R>
+struct CV3 {
+    Cx<R> x, y, z;
+};
+template <class R> inline Cx<R> cdot(const V3<double>& e, const CV3<R>& f) {
+    // e^T f with e real
+    return f.x * R(e.x) + f.y * R(e.y) + f.z * R(e.z);
+}
+template <class R> inline CV3<R> outer(const V3<double>& e, const Cx<R>& a) {
+    return {a * R(e.x), a * R(e.y), a * R(e.z)};
+}
+template <class R> inline CV3<R> operator+(const CV3<R>& a, const CV3<R>& b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R> inline R cnorm2(const CV3<R>& f) { return abs2(f.x) + abs2(f.y) + abs2(f.z); }
+
+// ---------------------------------------------------------------------------
+// counter-based random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014)
+// ---------------------------------------------------------------------------
+inline uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+// Reading: the paper does not fix its random-number generator.  The uniform
+// variate for the interaction at the end of segment l of lattice ray n is the
+// top 24 bits of splitmix64(seed ^ splitmix64(n * 16 + l)), scaled by 2^-24;
+// it is exactly representable in FP32 and FP64.
+inline double rng_u(uint64_t seed, uint64_t n, int l) {
+    uint64_t h = splitmix64(seed ^ splitmix64((n << 4) | (uint64_t)(l & 15)));
+    return (double)(h >> 40) * (1.0 / 16777216.0);
+}
+
+// ---------------------------------------------------------------------------
+// Spherical Fibonacci lattice (Sec. 3.1.1)
+// ---------------------------------------------------------------------------
+// cos(theta_n) = 1 - 2n/(N-1); phi_n = 2 pi frac(n / phi_g).  Since
+// 1/phi_g = phi_g - 1, frac(n / phi_g) = frac(n (phi_g - 1)), evaluated as the
+// 64-bit fixed-point product n * round(2^64 (phi_g - 1)) mod 2^64 so that the
+// fractional part carries no cancellation for large n.  N = 1 gives
+// theta = pi/2, phi = pi.
+constexpr uint64_t WEYL_GOLDEN = 0x9E3779B97F4A7C16ULL;  // nearest integer to 2^64 * (phi_g - 1)
+
+V3<double> fibonacci_dir(int64_t n, int64_t N) {
+    double ct, st, phi;
+    if (N == 1) {
+        ct = 0.0; st = 1.0; phi = PI;
+    } else {
+        ct = 1.0 - 2.0 * (double)n / (double)(N - 1);
+        st = std::sqrt((1.0 - ct) * (1.0 + ct));
+        uint64_t f = (uint64_t)n * WEYL_GOLDEN;
+        phi = 2.0 * PI * ((double)f * 0x1.0p-64);
+    }
+    return {st * std::cos(phi), st * std::sin(phi), ct};
+}
+
+// ---------------------------------------------------------------------------
+// Transmitter field (App. A.1 and the antenna pattern, Eq. C)
+// ---------------------------------------------------------------------------
+struct Rot { double m[3][3]; };
+// R(alpha, beta, gamma) = Rz(alpha) Ry(beta) Rx(gamma)   (Eq. rotation)
+Rot rotation(double a, double b, double g) {
+    double Rz[3][3] = {{std::cos(a), -std::sin(a), 0}, {std::sin(a), std::cos(a), 0}, {0, 0, 1}};
+    double Ry[3][3] = {{std::cos(b), 0, std::sin(b)}, {0, 1, 0}, {-std::sin(b), 0, std::cos(b)}};
+    double Rx[3][3] = {{1, 0, 0}, {0, std::cos(g), -std::sin(g)}, {0, std::sin(g), std::cos(g)}};
+    double T[3][3] = {};
+    Rot R = {};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) T[i][j] += Ry[i][k] * Rx[k][j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) R.m[i][j] += Rz[i][k] * T[k][j];
+    return R;
+}
+inline V3<double> mul(const Rot& R, const V3<double>& v) {
+    return {R.m[0][0] * v.x + R.m[0][1] * v.y + R.m[0][2] * v.z,
+            R.m[1][0] * v.x + R.m[1][1] * v.y + R.m[1][2] * v.z,
+            R.m[2][0] * v.x + R.m[2][1] * v.y + R.m[2][2] * v.z};
+}
+inline V3<double> mulT(const Rot& R, const V3<double>& v) {
+    return {R.m[0][0] * v.x + R.m[1][0] * v.y + R.m[2][0] * v.z,
+            R.m[0][1] * v.x + R.m[1][1] * v.y + R.m[2][1] * v.z,
+            R.m[0][2] * v.x + R.m[1][2] * v.y + R.m[2][2] * v.z};
+}
+// spherical unit vectors theta_hat, phi_hat at (theta, phi)  (Eq. spherical_vecs)
+inline V3<double> theta_hat(double th, double ph) {
+    return {std::cos(th) * std::cos(ph), std::cos(th) * std::sin(ph), -std::sin(th)};
+}
+inline V3<double> phi_hat(double ph) { return {-std::sin(ph), std::cos(ph), 0.0}; }
+
+// Antenna pattern C = (C_theta, C_phi) in the antenna's local frame.
+//   pattern 0: isotropic, |C|^2 = 1 for the chosen polarisation;
+//   pattern 1: short dipole along the local z axis, C_theta = sqrt(3/2) sin(theta').
+// Both satisfy the normalisation integral of G = |C|^2 over the sphere = 4 pi.
+// Polarisation 0 puts the pattern on theta' (vertical), 1 on phi' (horizontal).
+// Returns the global-frame field vector R (C_theta theta_hat' + C_phi phi_hat')
+// for the departure direction k (global frame), i.e. the first column of the
+// transfer cascade applied to the pattern.
+V3<double> tx_field(const V3<double>& k, const Rot& R, int pattern, int pol) {
+    V3<double> kl = mulT(R, k);  // direction in the antenna frame (Eq. theta_phi_prime)
+    double zc = std::max(-1.0, std::min(1.0, kl.z));
+    double th = std::acos(zc);
+    // Reading at the poles: atan2(0, 0) = 0.
+    double ph = std::atan2(kl.y, kl.x);
+    double g = 1.0;
+    if (pattern == 1) g = std::sqrt(1.5) * std::sin(th);
+    V3<double> e_local = (pol == 0) ? theta_hat(th, ph) : phi_hat(ph);
+    return scl(mul(R, e_local), g);
+}
+
+// ---------------------------------------------------------------------------
+// Fresnel / slab coefficients (App. A.7 and A.7.1)
+// ---------------------------------------------------------------------------
+template <class R>
+struct Coefs {
+    Cx<R> r_perp, r_par, t_perp, t_par;
+};
+// Complex relative permittivity, Eq. eta:  eta = eps_r - j sigma / (eps0 omega)
+template <class R>
+inline Cx<R> permittivity(const R& eps_r, const R& sigma, double omega) {
+    return Cx<R>(eps_r, -(sigma / (EPS0 * omega)));
+}
+// Incidence from vacuum on a half-space (Eq. fresnel_vac), or on a slab of
+// electrical thickness k0d = 2 pi d / lambda0 (Eqs. fresnel_slab,
+// q_fresnel_slab) when k0d > 0.  Reading: thickness <= 0 means a half-space,
+// whose transmitted wave never leaves the material: t = 0.
+template <class R>
+Coefs<R> fresnel(const Cx<R>& eta, double cos1, const R& k0d, bool slab) {
+    const double sin2 = (1.0 - cos1) * (1.0 + cos1);
+    Cx<R> s = csqrt(eta - Cx<R>(R(sin2)));
+    Cx<R> c{R(cos1)};
+    Cx<R> ec = eta * R(cos1);
+    Coefs<R> o;
+    Cx<R> rp = (c - s) / (c + s);
+    Cx<R> rl = (ec - s) / (ec + s);
+    if (!slab) {
+        o.r_perp = rp;
+        o.r_par = rl;
+        o.t_perp = Cx<R>(R(0.0));
+        o.t_par = Cx<R>(R(0.0));
+        return o;
+    }
+    Cx<R> q = s * k0d;
+    Cx<R> e1 = cexp_mj(q);                      // exp(-j q)
+    Cx<R> e2 = e1 * e1;                         // exp(-j 2q)
+    Cx<R> one(R(1.0));
+    Cx<R> rp2 = rp * rp, rl2 = rl * rl;
+    o.r_perp = rp * (one - e2) / (one - rp2 * e2);
+    o.r_par = rl * (one - e2) / (one - rl2 * e2);
+    o.t_perp = (one - rp2) * e1 / (one - rp2 * e2);
+    o.t_par = (one - rl2) * e1 / (one - rl2 * e2);
+    return o;
+}
+// The vacuum-incidence transmission coefficients of Eq. fresnel_vac (used by
+// the pins only; the slab model above replaces them on the path).
+template <class R>
+void fresnel_vac_t(const Cx<R>& eta, double cos1, Cx<R>* t_perp, Cx<R>* t_par) {
+    const double sin2 = (1.0 - cos1) * (1.0 + cos1);
+    Cx<R> s = csqrt(eta - Cx<R>(R(sin2)));
+    Cx<R> c{R(cos1)};
+    Cx<R> ec = eta * R(cos1);
+    *t_perp = (c * R(2.0)) / (c + s);
+    *t_par = (csqrt(eta) * R(2.0 * cos1)) / (ec + s);
+}
+
+// ---------------------------------------------------------------------------
+// scene
+// ---------------------------------------------------------------------------
+struct Tri {
+    V3<double> a, b, c, e1, e2, n;  // n = unit((b - a) x (c - a))
+    double area2;                    // |(b - a) x (c - a)|
+    double len[3];                   // |c-b|, |a-c|, |b-a| (edge opposite a, b, c)
+    int mat;
+};
+
+struct Scene {
+    std::vector<Tri> tris;
+    std::vector<double> eps, sigma, thick;
+};
+
+Scene make_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                 const int32_t* tri_mat, const float* mats, int nm) {
+    (void)nv;
+    Scene s;
+    s.tris.resize(nt);
+    for (int64_t i = 0; i < nt; ++i) {
+        Tri& t = s.tris[i];
+        auto V = [&](int j) {
+            const float* p = verts + 3 * (int64_t)tris[3 * i + j];
+            return V3<double>{p[0], p[1], p[2]};
+        };
+        t.a = V(0); t.b = V(1); t.c = V(2);
+        t.e1 = t.b - t.a;
+        t.e2 = t.c - t.a;
+        V3<double> cr = cross(t.e1, t.e2);
+        t.area2 = norm(cr);
+        t.n = t.area2 > 0 ? scl(cr, 1.0 / t.area2) : V3<double>{0, 0, 1};
+        t.len[0] = norm(t.c - t.b);
+        t.len[1] = norm(t.a - t.c);
+        t.len[2] = norm(t.b - t.a);
+        t.mat = tri_mat[i];
+    }
+    for (int m = 0; m < nm; ++m) {
+        s.eps.push_back(mats[3 * m]);
+        s.sigma.push_back(mats[3 * m + 1]);
+        s.thick.push_back(mats[3 * m + 2]);
+    }
+    return s;
+}
+
+// Moller-Trumbore in FP64, edges inclusive (a hit on a shared edge counts for
+// both triangles).  Returns t > 0 or +inf.
+inline double hit_mt(const Tri& T, const V3<double>& o, const V3<double>& k) {
+    V3<double> p = cross(k, T.e2);
+    double det = dot(T.e1, p);
+    if (det == 0.0) return INFINITY;
+    double inv = 1.0 / det;
+    V3<double> tv = o - T.a;
+    double u = dot(tv, p) * inv;
+    if (u < 0.0 || u > 1.0) return INFINITY;
+    V3<double> q = cross(tv, T.e1);
+    double v = dot(k, q) * inv;
+    if (v < 0.0 || u + v > 1.0) return INFINITY;
+    double t = dot(T.e2, q) * inv;
+    return t > 0.0 ? t : INFINITY;
+}
+
+// Reading (paper silent): the closest hit excludes the primitive the ray just
+// left; equal distances go to the smaller triangle index.
+inline void closest_hit(const Scene& S, const V3<double>& o, const V3<double>& k, int exclude,
+                        int* prim, double* t) {
+    int best = -1;
+    double tb = INFINITY;
+    const int nt = (int)S.tris.size();
+    for (int i = 0; i < nt; ++i) {
+        if (i == exclude) continue;
+        double ti = hit_mt(S.tris[i], o, k);
+        if (ti < tb) { tb = ti; best = i; }
+    }
+    *prim = best;
+    *t = tb;
+}
+
+// Intersection with the plane of a given triangle, plus the signed distance
+// (m) of the hit point to the triangle (positive inside, negative outside):
+// min over edges of barycentric * (2 area / edge length).
+inline bool plane_hit(const Tri& T, const V3<double>& o, const V3<double>& k, double* t, double* margin) {
+    double den = dot(T.n, k);
+    if (den == 0.0 || T.area2 == 0.0) return false;
+    *t = dot(T.n, T.a - o) / den;
+    V3<double> p = o + scl(k, *t);
+    // barycentrics via sub-triangle areas (signed along n)
+    double wa = dot(cross(T.b - p, T.c - p), T.n) / T.area2;
+    double wb = dot(cross(T.c - p, T.a - p), T.n) / T.area2;
+    double wc = 1.0 - wa - wb;
+    double da = wa * T.area2 / T.len[0];
+    double db = wb * T.area2 / T.len[1];
+    double dc = wc * T.area2 / T.len[2];
+    *margin = std::min(da, std::min(db, dc));
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// public structs (mirrored by the ctypes wrapper)
+// ---------------------------------------------------------------------------
+struct or_tx {
+    double pos[3];
+    double yaw, pitch, roll;
+    int32_t pol, pattern;
+    int64_t num_rays, ray_begin, ray_count, ray_stride;
+    uint64_t seed;
+};
+struct or_params {
+    double freq_hz;
+    int32_t max_depth, flags;
+    double map_origin[3];
+    double cell_size;
+    int32_t nx, ny, deposit, pad;
+};
+enum { F_REFLECT = 1, F_REFRACT = 2, F_LOS = 4 };
+struct or_report {
+    int64_t segments, deposits, adopted_hit, adopted_cell, adopted_decision, failures;
+    int64_t fail_ray;
+    int32_t fail_depth, fail_kind;  // 1 hit, 2 deposit cell, 3 decision, 4 segment
+    double fail_info[4];
+};
+constexpr int32_t NO_CELL = -32768;
+enum { MODE_PLAIN = 0, MODE_REPLAY = 1, MODE_FROZEN = 2 };
+
+// per-segment record, shared layout with the GPU's debug record:
+// {prim (-2 no segment, -1 miss), ix, iy (NO_CELL = no deposit), decision (0 R, 1 T, -1 none)}
+struct Rec {
+    int32_t prim, ix, iy, dec;
+};
+
+struct MapGeom {
+    double x0, y0, z, cell, K;  // K = 4 pi / (N Delta^2) * (lambda0 / 4 pi)^2
+    int nx, ny, bilinear;
+};
+
+// ---------------------------------------------------------------------------
+// deposit (Eq. radio-map-solver-ci-all-2-estimator, n_S = 0)
+// ---------------------------------------------------------------------------
+// For a segment with origin o and direction k that ends at t_h (inf = escaped):
+// t_c = (z_M - o_z) / k_z; if 1e-9 < t_c < t_h the crossing (x, y) adds
+//   K * |E|^2 / (|k_z| * Pr)
+// to its cell (box), or splits it over the four nearest cell centres with
+// tent weights (bilinear).  Rays parallel to the plane (k_z = 0) never
+// deposit.  The plane does not stop the ray.
+template <class R>
+struct Crossing {
+    bool valid;
+    double tc_v;      // value of t_c
+    R x, y;           // crossing point
+    int ix, iy;       // box: cell; bilinear: lower-left cell of the 2x2 stencil
+    double ux, uy;    // (x - x0)/Delta (box) or (x - x0)/Delta - 0.5 (bilinear)
+};
+template <class R>
+Crossing<R> crossing(const MapGeom& g, const V3<R>& o, const V3<double>& k, double t_h) {
+    Crossing<R> c;
+    c.valid = false;
+    if (k.z == 0.0) return c;
+    R tc = (R(g.z) - o.z) / k.z;
+    c.tc_v = val(tc);
+    if (!(c.tc_v > 1e-9 && c.tc_v < t_h)) return c;
+    c.x = o.x + tc * k.x;
+    c.y = o.y + tc * k.y;
+    double sh = g.bilinear ? 0.5 : 0.0;
+    c.ux = (val(c.x) - g.x0) / g.cell - sh;
+    c.uy = (val(c.y) - g.y0) / g.cell - sh;
+    c.ix = (int)std::floor(c.ux);
+    c.iy = (int)std::floor(c.uy);
+    if (g.bilinear) {
+        if (c.ix < -1 || c.ix > g.nx - 1 || c.iy < -1 || c.iy > g.ny - 1) return c;
+    } else {
+        if (c.ix < 0 || c.ix >= g.nx || c.iy < 0 || c.iy >= g.ny) return c;
+    }
+    c.valid = true;
+    return c;
+}
+
+// A deposit sink accumulates either a map (double) or a gradient functional.
+struct DepList {
+    std::vector<int32_t> cell;
+    std::vector<double> val;
+};
+
+template <class R>
+struct Sink;
+template <>
+struct Sink<double> {
+    DepList* list;
+    void add(int cell, const double& v) { list->cell.push_back(cell); list->val.push_back(v); }
+};
+template <>
+struct Sink<D> {
+    const double* gmap;  // dL/dC per cell
+    double acc[NT];
+    void add(int cell, const D& v) {
+        const double w = gmap[cell];
+        for (int i = 0; i < NT; ++i) acc[i] += w * v.g[i];
+    }
+};
+
+template <class R, class SinkT>
+void deposit(const MapGeom& g, const Crossing<R>& c, int ix, int iy, const R& value, SinkT& sink) {
+    if (!g.bilinear) {
+        if (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny) sink.add(iy * g.nx + ix, value);
+        return;
+    }
+    // tent weights relative to the (possibly adopted) lower-left index
+    double sh = 0.5;
+    R fx = (c.x - g.x0) / g.cell - (sh + ix);
+    R fy = (c.y - g.y0) / g.cell - (sh + iy);
+    R wx[2] = {R(1.0) - fx, fx};
+    R wy[2] = {R(1.0) - fy, fy};
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+            int cx = ix + a, cy = iy + b;
+            if (cx < 0 || cx >= g.nx || cy < 0 || cy >= g.ny) continue;
+            sink.add(cy * g.nx + cx, value * (wx[a] * wy[b]));
+        }
+}
+
+// ---------------------------------------------------------------------------
+// the SBR loop for one lattice ray
+// ---------------------------------------------------------------------------
+struct TxC {
+    Rot R;
+    int pattern, pol;
+    int64_t N;
+    uint64_t seed;
+};
+
+struct Ctx {
+    const Scene* S;
+    MapGeom g;
+    double omega, k0;  // angular frequency, vacuum wavenumber
+    int L, flags;
+    int mode;
+    // sampling materials (detached q): eps, sigma
+    const double* s_eps;
+    const double* s_sig;
+};
+
+// Tolerance (m) for certifying a discrete near-tie in replay-check mode.
+// FP32 carries a unit roundoff of 6e-8; positions accumulate O(10) roundings
+// per bounce relative to the coordinate magnitude and the distance travelled,
+// so 1e-5 * (1 m + |p|_inf + path length) is a >10x margin.
+inline double tie_tol(const V3<double>& p, double path) {
+    double pm = std::max(std::fabs(p.x), std::max(std::fabs(p.y), std::fabs(p.z)));
+    return 1e-5 * (1.0 + pm + path);
+}
+
+struct ReplayState {
+    or_report rep;
+    void fail(int64_t ray, int depth, int kind, double a, double b, double c, double d) {
+        if (rep.failures == 0) {
+            rep.fail_ray = ray;
+            rep.fail_depth = depth;
+            rep.fail_kind = kind;
+            rep.fail_info[0] = a; rep.fail_info[1] = b; rep.fail_info[2] = c; rep.fail_info[3] = d;
+        }
+        rep.failures++;
+    }
+};
+
+// Is the GPU's choice of closest primitive (pg; -1 = miss) consistent with
+// FP64 up to a perturbation of size tol?  pg must be a near-hit no farther
+// than every robust hit (margin >= +tol) by more than tol.
+bool certify_hit(const Scene& S, const V3<double>& o, const V3<double>& k, int exclude, int pg,
+                 double path, double* tg) {
+    double tgv = INFINITY;
+    if (pg >= 0) {
+        if (pg == exclude || pg >= (int)S.tris.size()) return false;
+        double t, m;
+        if (!plane_hit(S.tris[pg], o, k, &t, &m)) return false;
+        V3<double> p = o + scl(k, t);
+        double tol = tie_tol(p, path + std::max(t, 0.0));
+        if (!(t > -tol) || m < -tol) return false;
+        tgv = t;
+    }
+    for (int i = 0; i < (int)S.tris.size(); ++i) {
+        if (i == exclude || i == pg) continue;
+        double t, m;
+        if (!plane_hit(S.tris[i], o, k, &t, &m)) continue;
+        if (!(t > 0.0)) continue;
+        V3<double> p = o + scl(k, t);
+        double tol = tie_tol(p, path + t);
+        if (m >= tol && t < tgv - tol) return false;  // a robust hit clearly in front
+    }
+    *tg = tgv;
+    return true;
+}
+
+template <class R, class SinkT>
+void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta, const R* k0d,
+               int64_t n, int64_t i_sub, Rec* rec_io, SinkT& sink, ReplayState* rs,
+               double* pw, double* pw2, double* esc) {
+    const Scene& S = *C.S;
+    const int L = C.L;
+    const int npol = (tx.pol == 2) ? 2 : 1;
+    V3<double> k = fibonacci_dir(n, tx.N);
+    CV3<R> E[2];
+    for (int p = 0; p < npol; ++p) {
+        int pol = (tx.pol == 2) ? p : tx.pol;
+        V3<double> f = tx_field(k, tx.R, tx.pattern, pol);
+        E[p] = {Cx<R>(R(f.x)), Cx<R>(R(f.y)), Cx<R>(R(f.z))};
+    }
+    V3<R> o = txpos;
+    double inv_pr = 1.0;  // 1 / Pr(chi): detached from the parameters
+    double path = 0.0;    // unfolded length (only used for tie tolerances)
+    int prev = -1;
+    int l = 0;
+    for (; l <= L; ++l) {
+        V3<double> ov = vval(o);
+        Rec* rec = rec_io ? rec_io + (size_t)i_sub * (L + 1) + l : nullptr;
+        // ---- closest hit -------------------------------------------------
+        int prim;
+        double th;
+        if (C.mode == MODE_FROZEN) {
+            prim = rec->prim;
+            th = INFINITY;
+            if (prim >= 0) {
+                double m;
+                plane_hit(S.tris[prim], ov, k, &th, &m);
+            }
+        } else {
+            closest_hit(S, ov, k, prev, &prim, &th);
+            if (C.mode == MODE_REPLAY) {
+                rs->rep.segments++;
+                if (rec->prim == -2) { rs->fail(i_sub, l, 4, prim, 0, 0, 0); return; }
+                if (rec->prim != prim) {
+                    double tg;
+                    if (certify_hit(S, ov, k, prev, rec->prim, path, &tg)) {
+                        rs->rep.adopted_hit++;
+                        prim = rec->prim;
+                        th = tg;
+                    } else {
+                        rs->fail(i_sub, l, 1, prim, rec->prim, th, path);
+                        return;
+                    }
+                }
+            }
+        }
+        // exact (typed) hit distance along the frozen primitive's plane
+        R t_h(INFINITY);
+        if (prim >= 0) {
+            const Tri& T = S.tris[prim];
+            R num = R(dot(T.n, T.a)) - (o.x * T.n.x + o.y * T.n.y + o.z * T.n.z);
+            t_h = num / dot(T.n, k);
+        }
+        double w2 = 0.0;
+        for (int p = 0; p < npol; ++p) w2 += val(cnorm2(E[p]));
+        const double pwr = w2 * inv_pr;
+        if (pw) { pw[l] += pwr; pw2[l] += pwr * pwr; if (prim < 0) esc[l] += pwr; }
+        // ---- deposit -------------------------------------------------------
+        bool los_ok = (l > 0) || (C.flags & F_LOS);
+        Crossing<R> cr = crossing(C.g, o, k, prim >= 0 ? val(t_h) : INFINITY);
+        int dix = NO_CELL, diy = NO_CELL;
+        if (cr.valid && los_ok) { dix = cr.ix; diy = cr.iy; }
+        if (C.mode == MODE_FROZEN) {
+            dix = rec->ix; diy = rec->iy;
+            if (dix != NO_CELL && !cr.valid) {
+                // recompute the crossing point without the validity window
+                R tc = (R(C.g.z) - o.z) / k.z;
+                cr.x = o.x + tc * k.x;
+                cr.y = o.y + tc * k.y;
+            }
+        } else if (C.mode == MODE_REPLAY) {
+            if (rec->ix != dix || rec->iy != diy) {
+                // certify: the crossing sits within tol of a cell boundary, the
+                // map edge, the segment end or the minimum distance
+                double tc = (k.z != 0.0) ? (C.g.z - ov.z) / k.z : INFINITY;
+                V3<double> pc = ov + scl(k, std::isfinite(tc) ? tc : 0.0);
+                double tol = tie_tol(pc, path + std::max(0.0, std::isfinite(tc) ? tc : 0.0));
+                double sh = C.g.bilinear ? 0.5 : 0.0;
+                double ux = (pc.x - C.g.x0) / C.g.cell - sh, uy = (pc.y - C.g.y0) / C.g.cell - sh;
+                double bx = tol / C.g.cell;
+                auto near_int = [&](double u) { return std::fabs(u - std::nearbyint(u)) <= bx; };
+                bool ok = false;
+                bool gpu_dep = rec->ix != NO_CELL, or_dep = dix != NO_CELL;
+                double th_v = prim >= 0 ? val(t_h) : INFINITY;
+                if (gpu_dep && or_dep) {
+                    ok = std::abs(rec->ix - dix) <= 1 && std::abs(rec->iy - diy) <= 1 &&
+                         (rec->ix == dix || near_int(ux)) && (rec->iy == diy || near_int(uy));
+                } else if (los_ok && std::isfinite(tc)) {
+                    // existence differs: the window ends or the map edge decide
+                    bool near_end = std::fabs(tc - th_v) <= tol || std::fabs(tc) <= tol;
+                    bool near_edge = near_int(ux) || near_int(uy);
+                    ok = near_end || near_edge;
+                    if (gpu_dep) {
+                        int ex = (int)std::floor(ux), ey = (int)std::floor(uy);
+                        ok = ok && std::abs(rec->ix - ex) <= 1 && std::abs(rec->iy - ey) <= 1;
+                    }
+                }
+                if (!ok) { rs->fail(i_sub, l, 2, dix, diy, rec->ix, rec->iy); return; }
+                rs->rep.adopted_cell++;
+                dix = rec->ix; diy = rec->iy;
+                if (gpu_dep && !cr.valid) {
+                    R tcr = (R(C.g.z) - o.z) / k.z;
+                    cr.x = o.x + tcr * k.x;
+                    cr.y = o.y + tcr * k.y;
+                }
+            }
+        }
+        if (rec && C.mode == MODE_PLAIN) { rec->prim = prim; rec->ix = dix; rec->iy = diy; rec->dec = -1; }
+        if (dix != NO_CELL) {
+            R e2(0.0);
+            for (int p = 0; p < npol; ++p) e2 = e2 + cnorm2(E[p]);
+            R value = e2 * (C.g.K * inv_pr / std::fabs(k.z));
+            deposit(C.g, cr, dix, diy, value, sink);
+            if (rs) rs->rep.deposits++;
+        }
+        // ---- termination ---------------------------------------------------
+        if (prim < 0 || l == L) break;
+        // ---- shading (Sec. 3.1.2 sampling, App. A.7 field update) ---------
+        const Tri& T = S.tris[prim];
+        const int m = T.mat;
+        // normal oriented towards the incident side (n . k < 0)
+        V3<double> nn = dot(T.n, k) < 0.0 ? T.n : scl(T.n, -1.0);
+        double cos1 = -dot(k, nn);
+        cos1 = std::min(1.0, std::max(0.0, cos1));
+        bool slab = S.thick[m] > 0.0;
+        Coefs<R> cf = fresnel(eta[m], cos1, k0d[m], slab);
+        // sampling probabilities from the (detached) sampling materials
+        double qR, qT;
+        {
+            Cx<double> es = permittivity(C.s_eps[m], C.s_sig[m], C.omega);
+            double kd = C.k0 * S.thick[m];
+            Coefs<double> cs = fresnel(es, cos1, kd, slab);
+            double wR = (C.flags & F_REFLECT) ? abs2(cs.r_perp) + abs2(cs.r_par) : 0.0;
+            double wT = (C.flags & F_REFRACT) ? abs2(cs.t_perp) + abs2(cs.t_par) : 0.0;
+            if (!(wR + wT > 0.0)) {
+                if (rec && C.mode == MODE_PLAIN) rec->dec = -1;
+                if (C.mode == MODE_REPLAY && rec->dec != -1) rs->fail(i_sub, l, 3, -1, rec->dec, 0, 0);
+                break;
+            }
+            qR = wR / (wR + wT);
+            qT = wT / (wR + wT);
+        }
+        double u = rng_u(tx.seed, (uint64_t)n, l);
+        int dec = (u < qR) ? 0 : 1;
+        if (C.mode == MODE_FROZEN) {
+            dec = rec->dec;
+        } else if (C.mode == MODE_REPLAY) {
+            if (rec->dec != dec) {
+                if (std::fabs(u - qR) <= 1e-5 && (rec->dec == 0 || rec->dec == 1)) {
+                    rs->rep.adopted_decision++;
+                    dec = rec->dec;
+                } else {
+                    rs->fail(i_sub, l, 3, dec, rec->dec, u, qR);
+                    return;
+                }
+            }
+        } else if (rec) {
+            rec->dec = dec;
+        }
+        // TE/TM basis: e_perp = k x n / |k x n|, e_par,i = e_perp x k.
+        // At normal incidence any transverse basis is valid (the field update
+        // is then independent of the choice); take e_perp from the axis least
+        // aligned with k.
+        V3<double> kxn = cross(k, nn);
+        double kxn_n = norm(kxn);
+        V3<double> ep;
+        if (kxn_n > 1e-12) {
+            ep = scl(kxn, 1.0 / kxn_n);
+        } else {
+            V3<double> ax = std::fabs(k.x) < 0.5 ? V3<double>{1, 0, 0} : V3<double>{0, 1, 0};
+            ep = unit(cross(k, ax));
+        }
+        V3<double> epi = cross(ep, k);
+        V3<double> k_out;
+        V3<double> epo;
+        Cx<R> cperp, cpar;
+        if (dec == 0) {
+            k_out = k - scl(nn, 2.0 * dot(k, nn));
+            epo = unit(cross(ep, k_out));
+            cperp = cf.r_perp;
+            cpar = cf.r_par;
+            inv_pr /= qR;
+        } else {
+            k_out = k;  // thin slab: no deflection (Sec. 2.3)
+            epo = epi;
+            cperp = cf.t_perp;
+            cpar = cf.t_par;
+            inv_pr /= qT;
+        }
+        for (int p = 0; p < npol; ++p) {
+            Cx<R> a = cdot(ep, E[p]);
+            Cx<R> b = cdot(epi, E[p]);
+            E[p] = outer(ep, cperp * a) + outer(epo, cpar * b);
+        }
+        // new origin: hit point pushed off the surface along the outgoing side.
+        // Reading (paper silent): offset 2^-16 * max(1, |p|_inf) metres.
+        V3<R> ph = axpy(o, t_h, k);
+        V3<double> phv = vval(ph);
+        const R* big = &ph.x;
+        if (std::fabs(phv.y) > std::fabs(val(*big))) big = &ph.y;
+        if (std::fabs(phv.z) > std::fabs(val(*big))) big = &ph.z;
+        R delta = std::fabs(val(*big)) > 1.0 ? r_abs(*big) * 0x1.0p-16 : R(0x1.0p-16);
+        V3<double> nout = (dec == 0) ? nn : scl(nn, -1.0);
+        o = {ph.x + delta * nout.x, ph.y + delta * nout.y, ph.z + delta * nout.z};
+        path += val(t_h);
+        k = k_out;
+        prev = prim;
+    }
+    // remaining record slots: no segment
+    if (rec_io && C.mode == MODE_PLAIN)
+        for (int j = l + 1; j <= L; ++j) rec_io[(size_t)i_sub * (L + 1) + j] = Rec{-2, NO_CELL, NO_CELL, -1};
+    if (C.mode == MODE_REPLAY)
+        for (int j = l + 1; j <= L; ++j)
+            if (rec_io[(size_t)i_sub * (L + 1) + j].prim != -2) { rs->fail(i_sub, j, 4, -2, rec_io[(size_t)i_sub * (L + 1) + j].prim, 0, 0); return; }
+}
+
+MapGeom make_geom(const or_params& P, int64_t N) {
+    MapGeom g;
+    g.cell = P.cell_size;
+    g.nx = P.nx;
+    g.ny = P.ny;
+    g.x0 = P.map_origin[0] - 0.5 * P.nx * P.cell_size;
+    g.y0 = P.map_origin[1] - 0.5 * P.ny * P.cell_size;
+    g.z = P.map_origin[2];
+    g.bilinear = P.deposit == 1;
+    double lam = C0 / P.freq_hz;
+    double a = lam / (4.0 * PI);
+    g.K = 4.0 * PI / ((double)N * P.cell_size * P.cell_size) * a * a;
+    return g;
+}
+
+inline int64_t subset_count(const or_tx& t) {
+    if (t.ray_count >= 0) return t.ray_count;
+    return (t.num_rays - t.ray_begin + t.ray_stride - 1) / t.ray_stride;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C entry points (loaded with ctypes by the tests)
+// ===========================================================================
+extern "C" {
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+double or_rng_u(uint64_t seed, uint64_t n, int l) { return rng_u(seed, n, l); }
+uint64_t or_splitmix64(uint64_t x) { return splitmix64(x); }
+
+void or_fibonacci(int64_t N, int64_t begin, int64_t count, int64_t stride, double* out) {
+    for (int64_t i = 0; i < count; ++i) {
+        V3<double> k = fibonacci_dir(begin + i * stride, N);
+        out[3 * i] = k.x; out[3 * i + 1] = k.y; out[3 * i + 2] = k.z;
+    }
+}
+
+void or_tx_field(const double* dirs, int64_t n, double yaw, double pitch, double roll,
+                 int pattern, int pol, double* out) {
+    Rot R = rotation(yaw, pitch, roll);
+    for (int64_t i = 0; i < n; ++i) {
+        V3<double> f = tx_field({dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2]}, R, pattern, pol);
+        out[3 * i] = f.x; out[3 * i + 1] = f.y; out[3 * i + 2] = f.z;
+    }
+}
+
+void or_rotation(double yaw, double pitch, double roll, double* out9) {
+    Rot R = rotation(yaw, pitch, roll);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) out9[3 * i + j] = R.m[i][j];
+}
+
+void or_csqrt(double re, double im, double* out) {
+    Cx<double> z = csqrt(Cx<double>(re, im));
+    out[0] = z.re; out[1] = z.im;
+}
+
+// out[8] = r_perp, r_par, t_perp, t_par (re, im).  k0d <= 0: half-space.
+void or_fresnel(double eps_r, double sigma, double omega, double cos1, double k0d, double* out) {
+    Cx<double> eta = permittivity(eps_r, sigma, omega);
+    Coefs<double> c = fresnel(eta, cos1, k0d, k0d > 0.0);
+    Cx<double> v[4] = {c.r_perp, c.r_par, c.t_perp, c.t_par};
+    for (int i = 0; i < 4; ++i) { out[2 * i] = v[i].re; out[2 * i + 1] = v[i].im; }
+}
+
+void or_fresnel_vac_t(double eps_r, double sigma, double omega, double cos1, double* out) {
+    Cx<double> eta = permittivity(eps_r, sigma, omega);
+    Cx<double> a, b;
+    fresnel_vac_t(eta, cos1, &a, &b);
+    out[0] = a.re; out[1] = a.im; out[2] = b.re; out[3] = b.im;
+}
+
+// Field update at one interface, for the pins: incident direction k, surface
+// normal n (any sign), incident field E (complex, 6 doubles), decision (0 R,
+// 1 T).  Writes the outgoing direction (3) and field (6).
+void or_interact(const double* k3, const double* n3, const double* E6, double eps_r, double sigma,
+                 double omega, double k0d, int dec, double* kout, double* Eout) {
+    V3<double> k{k3[0], k3[1], k3[2]}, n{n3[0], n3[1], n3[2]};
+    n = unit(n);
+    V3<double> nn = dot(n, k) < 0.0 ? n : scl(n, -1.0);
+    double cos1 = std::min(1.0, std::max(0.0, -dot(k, nn)));
+    Coefs<double> cf = fresnel(permittivity(eps_r, sigma, omega), cos1, k0d, k0d > 0.0);
+    V3<double> kxn = cross(k, nn);
+    double kn = norm(kxn);
+    V3<double> ep;
+    if (kn > 1e-12) ep = scl(kxn, 1.0 / kn);
+    else {
+        V3<double> ax = std::fabs(k.x) < 0.5 ? V3<double>{1, 0, 0} : V3<double>{0, 1, 0};
+        ep = unit(cross(k, ax));
+    }
+    V3<double> epi = cross(ep, k);
+    V3<double> ko = dec == 0 ? k - scl(nn, 2.0 * dot(k, nn)) : k;
+    V3<double> epo = dec == 0 ? unit(cross(ep, ko)) : epi;
+    CV3<double> E{Cx<double>(E6[0], E6[1]), Cx<double>(E6[2], E6[3]), Cx<double>(E6[4], E6[5])};
+    Cx<double> a = cdot(ep, E), b = cdot(epi, E);
+    CV3<double> Eo = dec == 0 ? outer(ep, cf.r_perp * a) + outer(epo, cf.r_par * b)
+                              : outer(ep, cf.t_perp * a) + outer(epo, cf.t_par * b);
+    kout[0] = ko.x; kout[1] = ko.y; kout[2] = ko.z;
+    Eout[0] = Eo.x.re; Eout[1] = Eo.x.im; Eout[2] = Eo.y.re; Eout[3] = Eo.y.im;
+    Eout[4] = Eo.z.re; Eout[5] = Eo.z.im;
+}
+
+// Closest hit of a batch of rays (brute force), for the pins.
+void or_closest_hit(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                    const double* o, const double* k, int64_t nrays, const int32_t* exclude,
+                    int32_t* prim_out, double* t_out) {
+    std::vector<int32_t> mat(nt, 0);
+    float dummy[3] = {1, 0, 0};
+    Scene S = make_scene(verts, nv, tris, nt, mat.data(), dummy, 1);
+    for (int64_t i = 0; i < nrays; ++i) {
+        int p;
+        double t;
+        closest_hit(S, {o[3 * i], o[3 * i + 1], o[3 * i + 2]}, {k[3 * i], k[3 * i + 1], k[3 * i + 2]},
+                    exclude ? exclude[i] : -1, &p, &t);
+        prim_out[i] = p;
+        t_out[i] = t;
+    }
+}
+
+// Radio map of one transmitter.
+//   mode 0 plain:  RNG decisions; writes rec (if non-null) and the map;
+//   mode 1 replay: follows the given record, certifying every differing
+//                  discrete choice as an FP64 near-tie (report.failures = 0
+//                  when all differences are certified);
+//   mode 2 frozen: takes hits, cells and decisions from rec.
+// sampling_mats (nm x 2: eps, sigma) or null = the scene's own materials;
+// eval_mats likewise overrides the materials the fields are evaluated with.
+// map_out [ny][nx] is overwritten.  stats (or null): per depth 0..L
+// [power, power^2, escaped power] sums of w |E|^2 (without the 4 pi / N factor).
+int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                 const int32_t* tri_mat, const float* mats, int nm, const or_tx* tx,
+                 const or_params* P, int mode, int32_t* rec, const double* sampling_mats,
+                 const double* eval_mats, double* map_out, double* stats, or_report* report) {
+    if (P->max_depth < 0 || P->max_depth > 15) return 1;
+    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
+    if (eval_mats)
+        for (int m = 0; m < nm; ++m) { S.eps[m] = eval_mats[2 * m]; S.sigma[m] = eval_mats[2 * m + 1]; }
+    std::vector<double> seps(S.eps), ssig(S.sigma);
+    if (sampling_mats)
+        for (int m = 0; m < nm; ++m) { seps[m] = sampling_mats[2 * m]; ssig[m] = sampling_mats[2 * m + 1]; }
+    Ctx C;
+    C.S = &S;
+    C.g = make_geom(*P, tx->num_rays);
+    C.omega = 2.0 * PI * P->freq_hz;
+    C.k0 = C.omega / C0;
+    C.L = P->max_depth;
+    C.flags = P->flags;
+    C.mode = mode;
+    C.s_eps = seps.data();
+    C.s_sig = ssig.data();
+    TxC T;
+    T.R = rotation(tx->yaw, tx->pitch, tx->roll);
+    T.pattern = tx->pattern;
+    T.pol = tx->pol;
+    T.N = tx->num_rays;
+    T.seed = tx->seed;
+    std::vector<Cx<double>> eta(nm);
+    std::vector<double> k0d(nm);
+    for (int m = 0; m < nm; ++m) {
+        eta[m] = permittivity(S.eps[m], S.sigma[m], C.omega);
+        k0d[m] = C.k0 * S.thick[m];
+    }
+    V3<double> pos{tx->pos[0], tx->pos[1], tx->pos[2]};
+    const int64_t cnt = subset_count(*tx);
+    const int L = P->max_depth;
+    const int64_t CH = 2048;  // fixed chunking: the summation order is independent of threads
+    const int64_t nch = (cnt + CH - 1) / CH;
+    std::vector<DepList> lists(nch);
+    const int nthr = or_num_threads();
+    std::vector<double> st((size_t)nthr * 3 * (L + 1), 0.0);
+    std::vector<ReplayState> rss(nch);
+    for (auto& r : rss) std::memset(&r.rep, 0, sizeof r.rep);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < nch; ++c) {
+#ifdef _OPENMP
+        int tid = omp_get_thread_num();
+#else
+        int tid = 0;
+#endif
+        double* sp = stats ? st.data() + (size_t)tid * 3 * (L + 1) : nullptr;
+        Sink<double> sink{&lists[c]};
+        int64_t e = std::min(cnt, (c + 1) * CH);
+        for (int64_t i = c * CH; i < e; ++i) {
+            int64_t n = tx->ray_begin + i * tx->ray_stride;
+            trace_ray<double>(C, T, pos, eta.data(), k0d.data(), n, i, (Rec*)rec, sink,
+                              mode == MODE_REPLAY ? &rss[c] : nullptr, sp, sp ? sp + (L + 1) : nullptr,
+                              sp ? sp + 2 * (L + 1) : nullptr);
+        }
+    }
+    std::memset(map_out, 0, sizeof(double) * (size_t)P->nx * P->ny);
+    for (int64_t c = 0; c < nch; ++c)
+        for (size_t j = 0; j < lists[c].cell.size(); ++j) map_out[lists[c].cell[j]] += lists[c].val[j];
+    if (stats) {
+        std::memset(stats, 0, sizeof(double) * 3 * (L + 1));
+        for (int t = 0; t < nthr; ++t)
+            for (int j = 0; j < 3 * (L + 1); ++j) stats[j] += st[(size_t)t * 3 * (L + 1) + j];
+    }
+    if (report) {
+        std::memset(report, 0, sizeof *report);
+        bool have_fail = false;
+        for (int64_t c = 0; c < nch; ++c) {
+            const or_report& r = rss[c].rep;
+            report->segments += r.segments;
+            report->deposits += r.deposits;
+            report->adopted_hit += r.adopted_hit;
+            report->adopted_cell += r.adopted_cell;
+            report->adopted_decision += r.adopted_decision;
+            report->failures += r.failures;
+            if (r.failures && !have_fail) {
+                have_fail = true;
+                report->fail_ray = r.fail_ray;
+                report->fail_depth = r.fail_depth;
+                report->fail_kind = r.fail_kind;
+                std::memcpy(report->fail_info, r.fail_info, sizeof r.fail_info);
+            }
+        }
+    }
+    return 0;
+}
+
+// Gradient of  sum_i dLdC[i] * C_i  with respect to (eps_r[m], sigma[m] for
+// m < nm, tx position), with hits, cells and decisions frozen to rec (from a
+// plain run) and the sampling probabilities detached.  Forward-mode dual
+// numbers; nm <= 8.  grad_out: [nm] d/deps, [nm] d/dsigma, [3] d/dtx.
+int or_grad(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
+            const float* mats, int nm, const or_tx* tx, const or_params* P, const int32_t* rec,
+            const double* dLdC, double* grad_out) {
+    if (nm > 8) return 1;
+    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
+    Ctx C;
+    C.S = &S;
+    C.g = make_geom(*P, tx->num_rays);
+    C.omega = 2.0 * PI * P->freq_hz;
+    C.k0 = C.omega / C0;
+    C.L = P->max_depth;
+    C.flags = P->flags;
+    C.mode = MODE_FROZEN;
+    C.s_eps = S.eps.data();
+    C.s_sig = S.sigma.data();
+    TxC T;
+    T.R = rotation(tx->yaw, tx->pitch, tx->roll);
+    T.pattern = tx->pattern;
+    T.pol = tx->pol;
+    T.N = tx->num_rays;
+    T.seed = tx->seed;
+    std::vector<Cx<D>> eta(nm);
+    std::vector<D> k0d(nm);
+    for (int m = 0; m < nm; ++m) {
+        D e(S.eps[m]);
+        e.g[m] = 1.0;
+        D s(S.sigma[m]);
+        s.g[8 + m] = 1.0;
+        eta[m] = permittivity(e, s, C.omega);
+        k0d[m] = D(C.k0 * S.thick[m]);
+    }
+    V3<D> pos{D(tx->pos[0]), D(tx->pos[1]), D(tx->pos[2])};
+    pos.x.g[16] = 1.0;
+    pos.y.g[17] = 1.0;
+    pos.z.g[18] = 1.0;
+    const int64_t cnt = subset_count(*tx);
+    const int nthr = or_num_threads();
+    std::vector<double> acc((size_t)nthr * NT, 0.0);
+#pragma omp parallel
+    {
+#ifdef _OPENMP
+        int tid = omp_get_thread_num();
+#else
+        int tid = 0;
+#endif
+        Sink<D> sink;
+        sink.gmap = dLdC;
+        std::memset(sink.acc, 0, sizeof sink.acc);
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < cnt; ++i) {
+            int64_t n = tx->ray_begin + i * tx->ray_stride;
+            trace_ray<D>(C, T, pos, eta.data(), k0d.data(), n, i, (Rec*)rec, sink, nullptr, nullptr,
+                         nullptr, nullptr);
+        }
+        for (int j = 0; j < NT; ++j) acc[(size_t)tid * NT + j] = sink.acc[j];
+    }
+    double g[NT] = {};
+    for (int t = 0; t < nthr; ++t)
+        for (int j = 0; j < NT; ++j) g[j] += acc[(size_t)t * NT + j];
+    for (int m = 0; m < nm; ++m) { grad_out[m] = g[m]; grad_out[nm + m] = g[8 + m]; }
+    for (int j = 0; j < 3; ++j) grad_out[2 * nm + j] = g[16 + j];
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Branch-all enumeration: both R and T are followed at every interaction with
+// their full fields (no sampling, no 1/Pr), which is the exact expectation of
+// the Monte-Carlo estimator over the interaction-type choices (Sec. 3.1.2 and
+// the importance-sampling primer, App. E: E[|a|^2 / q] = sum over branches).
+// power_out[l]: sum over all branches alive at segment l of |E|^2; escaped_out[l]:
+// the part of it whose segment hits nothing.  (Multiply by 4 pi / N for
+// power x solid angle.)
+// ---------------------------------------------------------------------------
+namespace {
+struct BranchCtx {
+    const Ctx* C;
+    const Scene* S;
+    const Cx<double>* eta;
+    const double* k0d;
+    int npol;
+    DepList* list;
+    double* pw;
+    double* esc;
+};
+void branch(const BranchCtx& B, V3<double> o, V3<double> k, CV3<double>* E, int prev, int l) {
+    const Ctx& C = *B.C;
+    const Scene& S = *B.S;
+    int prim;
+    double th;
+    closest_hit(S, o, k, prev, &prim, &th);
+    double w2 = 0.0;
+    for (int p = 0; p < B.npol; ++p) w2 += cnorm2(E[p]);
+    B.pw[l] += w2;
+    if (prim < 0) B.esc[l] += w2;
+    bool los_ok = (l > 0) || (C.flags & F_LOS);
+    Crossing<double> cr = crossing(C.g, o, k, prim >= 0 ? th : INFINITY);
+    if (cr.valid && los_ok) {
+        Sink<double> sink{B.list};
+        deposit(C.g, cr, cr.ix, cr.iy, w2 * (C.g.K / std::fabs(k.z)), sink);
+    }
+    if (prim < 0 || l == C.L) return;
+    const Tri& T = S.tris[prim];
+    const int m = T.mat;
+    V3<double> nn = dot(T.n, k) < 0.0 ? T.n : scl(T.n, -1.0);
+    double cos1 = std::min(1.0, std::max(0.0, -dot(k, nn)));
+    bool slab = S.thick[m] > 0.0;
+    Coefs<double> cf = fresnel(B.eta[m], cos1, B.k0d[m], slab);
+    V3<double> kxn = cross(k, nn);
+    double kn = norm(kxn);
+    V3<double> ep;
+    if (kn > 1e-12) ep = scl(kxn, 1.0 / kn);
+    else {
+        V3<double> ax = std::fabs(k.x) < 0.5 ? V3<double>{1, 0, 0} : V3<double>{0, 1, 0};
+        ep = unit(cross(k, ax));
+    }
+    V3<double> epi = cross(ep, k);
+    V3<double> ph = o + scl(k, th);
+    double pm = std::max(std::fabs(ph.x), std::max(std::fabs(ph.y), std::fabs(ph.z)));
+    double delta = std::ldexp(std::max(1.0, pm), -16);
+    double wR = (C.flags & F_REFLECT) ? abs2(cf.r_perp) + abs2(cf.r_par) : 0.0;
+    double wT = (C.flags & F_REFRACT) ? abs2(cf.t_perp) + abs2(cf.t_par) : 0.0;
+    for (int dec = 0; dec < 2; ++dec) {
+        if ((dec == 0 ? wR : wT) <= 0.0) continue;
+        V3<double> ko = dec == 0 ? k - scl(nn, 2.0 * dot(k, nn)) : k;
+        V3<double> epo = dec == 0 ? unit(cross(ep, ko)) : epi;
+        Cx<double> cp = dec == 0 ? cf.r_perp : cf.t_perp;
+        Cx<double> cl = dec == 0 ? cf.r_par : cf.t_par;
+        CV3<double> En[2];
+        for (int p = 0; p < B.npol; ++p) {
+            Cx<double> a = cdot(ep, E[p]), b = cdot(epi, E[p]);
+            En[p] = outer(ep, cp * a) + outer(epo, cl * b);
+        }
+        V3<double> nout = dec == 0 ? nn : scl(nn, -1.0);
+        branch(B, ph + scl(nout, delta), ko, En, prim, l + 1);
+    }
+}
+}  // namespace
+
+int or_branch_all(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                  const int32_t* tri_mat, const float* mats, int nm, const or_tx* tx,
+                  const or_params* P, double* map_out, double* power_out, double* escaped_out) {
+    if (P->max_depth < 0 || P->max_depth > 12) return 1;
+    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
+    Ctx C;
+    C.S = &S;
+    C.g = make_geom(*P, tx->num_rays);
+    C.omega = 2.0 * PI * P->freq_hz;
+    C.k0 = C.omega / C0;
+    C.L = P->max_depth;
+    C.flags = P->flags;
+    C.mode = MODE_PLAIN;
+    std::vector<Cx<double>> eta(nm);
+    std::vector<double> k0d(nm);
+    for (int m = 0; m < nm; ++m) {
+        eta[m] = permittivity(S.eps[m], S.sigma[m], C.omega);
+        k0d[m] = C.k0 * S.thick[m];
+    }
+    Rot R = rotation(tx->yaw, tx->pitch, tx->roll);
+    const int npol = tx->pol == 2 ? 2 : 1;
+    const int64_t cnt = subset_count(*tx);
+    const int L = P->max_depth;
+    const int64_t CH = 256;
+    const int64_t nch = (cnt + CH - 1) / CH;
+    std::vector<DepList> lists(nch);
+    std::vector<double> pw((size_t)nch * (L + 1), 0.0), es((size_t)nch * (L + 1), 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < nch; ++c) {
+        BranchCtx B{&C, &S, eta.data(), k0d.data(), npol, &lists[c], pw.data() + c * (L + 1),
+                    es.data() + c * (L + 1)};
+        int64_t e = std::min(cnt, (c + 1) * CH);
+        for (int64_t i = c * CH; i < e; ++i) {
+            int64_t n = tx->ray_begin + i * tx->ray_stride;
+            V3<double> k = fibonacci_dir(n, tx->num_rays);
+            CV3<double> E[2];
+            for (int p = 0; p < npol; ++p) {
+                V3<double> f = tx_field(k, R, tx->pattern, tx->pol == 2 ? p : tx->pol);
+                E[p] = {Cx<double>(f.x), Cx<double>(f.y), Cx<double>(f.z)};
+            }
+            branch(B, {tx->pos[0], tx->pos[1], tx->pos[2]}, k, E, -1, 0);
+        }
+    }
+    std::memset(map_out, 0, sizeof(double) * (size_t)P->nx * P->ny);
+    for (int64_t c = 0; c < nch; ++c)
+        for (size_t j = 0; j < lists[c].cell.size(); ++j) map_out[lists[c].cell[j]] += lists[c].val[j];
+    for (int j = 0; j <= L; ++j) {
+        power_out[j] = 0;
+        escaped_out[j] = 0;
+        for (int64_t c = 0; c < nch; ++c) { power_out[j] += pw[c * (L + 1) + j]; escaped_out[j] += es[c * (L + 1) + j]; }
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Reference LBVH.  Not in the paper (it relies on Mitsuba's acceleration
+// structure); the tree here is the binary radix tree of Karras (HPG 2012) over
+// the sorted Morton codes, built TOP-DOWN by splitting each range at its
+// highest differing key bit -- a different algorithm from the GPU's
+// per-node parallel construction that must give the identical tree.
+//
+// Morton codes, in FP32 with round-to-nearest and no fused operations (this
+// file is compiled with -ffp-contract=off):
+//   lo, hi   = per-triangle AABB (exact min / max of the FP32 vertices);
+//   c2       = lo + hi                    (doubled centroid);
+//   cmin/cmax= min / max of c2 over all triangles;
+//   scale_a  = 2097151 / (cmax_a - cmin_a)     (0 if the extent is 0);
+//   q_a      = min(trunc((c2_a - cmin_a) * scale_a), 2097151);
+//   key      = interleave(qx, qy, qz): bit i of qx -> bit 3i+2, qy -> 3i+1, qz -> 3i.
+// Keys are sorted stably (ties keep triangle order); equal keys are told
+// apart by their sorted position: delta(i, j) = clz64(k_i ^ k_j) if the keys
+// differ, else 64 + clz32(i ^ j).  Internal node of range [a, b] with split g:
+// left = leaf g if a == g else internal g; right = leaf g+1 if b == g+1 else
+// internal g+1; the root is internal node 0.  Leaves are encoded as ~pos.
+// ---------------------------------------------------------------------------
+namespace {
+inline uint64_t spread3(uint32_t v) {
+    uint64_t r = 0;
+    for (int i = 0; i < 21; ++i) r |= (uint64_t)((v >> i) & 1u) << (3 * i);
+    return r;
+}
+inline int clz64(uint64_t x) { return x ? __builtin_clzll(x) : 64; }
+inline int clz32(uint32_t x) { return x ? __builtin_clz(x) : 32; }
+}  // namespace
+
+void or_morton(const float* verts, const int32_t* tris, int64_t nt, uint64_t* keys_out,
+               float* aabb_out /* [nt][6] lo, hi */) {
+    std::vector<float> c2(3 * nt);
+    float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nt; ++i) {
+        float lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            float v0 = verts[3 * tris[3 * i] + a], v1 = verts[3 * tris[3 * i + 1] + a],
+                  v2 = verts[3 * tris[3 * i + 2] + a];
+            lo[a] = std::min(v0, std::min(v1, v2));
+            hi[a] = std::max(v0, std::max(v1, v2));
+            volatile float s = lo[a] + hi[a];
+            c2[3 * i + a] = s;
+            cmin[a] = std::min(cmin[a], (float)s);
+            cmax[a] = std::max(cmax[a], (float)s);
+            if (aabb_out) { aabb_out[6 * i + a] = lo[a]; aabb_out[6 * i + 3 + a] = hi[a]; }
+        }
+    }
+    float scale[3];
+    for (int a = 0; a < 3; ++a) {
+        volatile float e = cmax[a] - cmin[a];
+        scale[a] = (e > 0.0f) ? (float)(2097151.0f / (float)e) : 0.0f;
+    }
+    for (int64_t i = 0; i < nt; ++i) {
+        uint32_t q[3];
+        for (int a = 0; a < 3; ++a) {
+            volatile float d = c2[3 * i + a] - cmin[a];
+            volatile float f = (float)d * scale[a];
+            uint32_t u = (uint32_t)(float)f;
+            q[a] = u > 2097151u ? 2097151u : u;
+        }
+        keys_out[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+    }
+}
+
+// Outputs: sorted keys [nt], sorted triangle ids [nt], for each internal node
+// i < nt-1: child[2] (>= 0 internal, < 0 = ~leaf position) and the two child
+// AABBs [2][6] (lo xyz, hi xyz).
+int or_lbvh(const float* verts, const int32_t* tris, int64_t nt, uint64_t* keys_sorted,
+            int32_t* order, int32_t* child, float* child_aabb) {
+    if (nt <= 0) return 0;
+    std::vector<uint64_t> keys(nt);
+    std::vector<float> box(6 * nt);
+    or_morton(verts, tris, nt, keys.data(), box.data());
+    std::vector<int32_t> idx(nt);
+    for (int64_t i = 0; i < nt; ++i) idx[i] = (int32_t)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return keys[a] < keys[b]; });
+    for (int64_t i = 0; i < nt; ++i) { order[i] = idx[i]; keys_sorted[i] = keys[idx[i]]; }
+    if (nt == 1) return 0;
+    auto delta = [&](int64_t i, int64_t j) -> int {
+        if (keys_sorted[i] != keys_sorted[j]) return clz64(keys_sorted[i] ^ keys_sorted[j]);
+        return 64 + clz32((uint32_t)i ^ (uint32_t)j);
+    };
+    std::vector<float> nodebox(6 * (nt - 1));
+    // explicit stack of ranges (top-down); AABBs are filled bottom-up afterwards
+    struct Rg { int64_t a, b, id; };
+    std::vector<Rg> st{{0, nt - 1, 0}};
+    std::vector<Rg> all;
+    while (!st.empty()) {
+        Rg r = st.back();
+        st.pop_back();
+        all.push_back(r);
+        int cp = delta(r.a, r.b);
+        int64_t g = r.a;
+        while (g + 1 <= r.b - 1 && delta(r.a, g + 1) > cp) ++g;
+        int32_t L = (r.a == g) ? ~(int32_t)g : (int32_t)g;
+        int32_t R = (r.b == g + 1) ? ~(int32_t)(g + 1) : (int32_t)(g + 1);
+        child[2 * r.id] = L;
+        child[2 * r.id + 1] = R;
+        if (L >= 0) st.push_back({r.a, g, L});
+        if (R >= 0) st.push_back({g + 1, r.b, R});
+    }
+    // AABBs: a node's box is the exact union of its leaves' boxes; process
+    // ranges from the smallest up so children are done before parents.
+    std::sort(all.begin(), all.end(), [](const Rg& x, const Rg& y) { return (x.b - x.a) < (y.b - y.a); });
+    auto cbox = [&](int32_t c, float* out) {
+        const float* src = c < 0 ? &box[6 * (size_t)idx[~c]] : &nodebox[6 * (size_t)c];
+        std::memcpy(out, src, 6 * sizeof(float));
+    };
+    for (const Rg& r : all) {
+        float lb[6], rb[6];
+        cbox(child[2 * r.id], lb);
+        cbox(child[2 * r.id + 1], rb);
+        std::memcpy(&child_aabb[12 * (size_t)r.id], lb, sizeof lb);
+        std::memcpy(&child_aabb[12 * (size_t)r.id + 6], rb, sizeof rb);
+        float* nb = &nodebox[6 * (size_t)r.id];
+        for (int a = 0; a < 3; ++a) {
+            nb[a] = std::min(lb[a], rb[a]);
+            nb[3 + a] = std::max(lb[3 + a], rb[3 + a]);
+        }
+    }
+    return 0;
+}
+
+}  // extern "C"
