@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Radio-map ray-bounces/s of the SBR tracer on B300.
+
+One step = one full radio map of the Manhattan workload: 10 x 10 box
+buildings (1202 triangles, seed 2), one transmitter at (0, 0, 30) m, 28 GHz,
+1e7 Fibonacci rays, up to 5 reflections / refractions, 512 x 512 cells of
+1 m.  The metric counts segments (closest-hit queries with their deposit and
+shading) on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank traces its own copy of the workload (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SEGMENT_BYTES = 184      # compulsory wavefront bytes per segment (ray state r/w, hit, queue)
+METRIC = "radio-map ray-bounces/s"
+UNIT = "ray-bounces/s"
+WORKLOAD = ("manhattan seed 2: 10x10 box buildings, 1202 triangles, 4 materials (ground half-space + 3 slab); "
+            "1 TX at (0,0,30) m isotropic V-pol; 28 GHz; 1e7 Fibonacci rays; max depth 5 (R+T); "
+            "512x512 map of 1 m cells at z=1.5 m")
+PROFILE = os.path.join(ROOT, "profiles", "k_trace_manhattan_1e7.md")
+TRACE_SOURCES = [os.path.join(ROOT, "paper_2504_21719_b300", "csrc", f) for f in ("trace.cu", "common.cuh")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the tracer from the committed ncu summary, if
+    the kernel source is unchanged since it was taken; else None."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for p in TRACE_SOURCES:
+        h.update(open(p, "rb").read())
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip().strip("-* `")] = v.strip().strip("` ")
+    if vals.get("source_sha256") != h.hexdigest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def tuned(gpu_name: str, key: str):
+    try:
+        t = json.load(open(os.path.join(ROOT, "paper_2504_21719_b300", "tuning.json")))
+        e = t.get(gpu_name, {}).get(key) or t.get("default", {}).get(key)
+        if e:
+            return int(e["block_size"]), int(e["blocks_per_sm"])
+    except Exception:
+        pass
+    return 0, 0
+
+
+def oracle_sample(target_s: float = 15.0, max_rays: int = 2_000_000):
+    """The FP64 oracle, as it stands, on a bounded lattice subset of the workload."""
+    import oracle
+    from synth import scenes as S
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+
+    def run(stride, begin=0):
+        tx.ray_stride, tx.ray_begin = stride, begin
+        t0 = time.perf_counter()
+        r = oracle.radio_map(sc, tx, p, want_record=True)
+        dt = time.perf_counter() - t0
+        segs = int((r["record"][:, :, 0] != -2).sum())
+        return segs, dt, tx.count()
+
+    segs, dt, n = run(1000)                       # calibration: 1e4 rays
+    rate = n / max(dt, 1e-3)
+    rays = int(min(max_rays, max(2e4, rate * target_s)))
+    stride = max(1, tx.num_rays // rays)
+    segs, dt, n = run(stride, 1)
+    return {"value": segs / dt, "unit": "segments/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"workload lattice subset: every {stride}th of 1e7 rays ({n} rays, {segs} segments, "
+                      f"{dt:.1f} s), FP64 brute force over 1202 triangles"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2504_21719_b300 import api
+    from synth import scenes as S
+
+    gpu_name = torch.cuda.get_device_name(local)
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    blk, bps = tuned(gpu_name, "manhattan")
+    params = api.params_from(p, block_size=blk, blocks_per_sm=bps)
+    gs = api.Scene.from_obj(sc)
+    maps = torch.empty((1, p.ny, p.nx), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        api.trace(gs, [tx], params, out=maps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    step_ms, kern_ms, segs = [], [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()                         # L2 (126 MB) flushed between timed steps
+        torch.cuda.synchronize()
+        ev0.record()
+        r = api.trace(gs, [tx], params, out=maps)
+        ev1.record()
+        torch.cuda.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        kern_ms.append(r["stats"]["kernel_ms"])
+        segs.append(r["stats"]["segments"])
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    total_segs = sum(segs)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        s = torch.tensor([total_segs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        total_ms, total_segs = float(t), float(s)
+    value = total_segs / (total_ms / 1e3)
+
+    # roofline of the tracer kernel (its launches timed with CUDA events on its stream)
+    pk = peaks()
+    peak = pk.get("hbm_gbs")
+    kavg = statistics.mean(kern_ms) / 1e3
+    seg_step = statistics.mean(segs)
+    achieved = SEGMENT_BYTES * seg_step / kavg / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak if peak else 6400.0,
+                "unit": "GB/s", "frac": round(achieved / (peak if peak else 6400.0), 4),
+                "traffic": traffic, "peak_source": "measured" if peak else "fallback",
+                "algorithmic_bytes_per_segment": SEGMENT_BYTES,
+                "kernel": "k_trace (persistent forward tracer)", "kernel_ms": round(1e3 * kavg, 4)}
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if rank == 0 or world > 1:
+        vh = torch.from_numpy(sc.verts).pin_memory()
+        th = torch.from_numpy(sc.tris).pin_memory()
+        mh = torch.from_numpy(sc.tri_mat).pin_memory()
+        out_h = torch.empty((1, p.ny, p.nx), dtype=torch.float32).pin_memory()
+        e_ms, e_segs = [], []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2 = api.Scene(vh, th, mh, sc.mats)
+            r = api.trace(g2, [tx], params, out=maps)
+            out_h.copy_(maps, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            g2.free()
+            if i >= args.warmup:
+                e_ms.append(dt * 1e3)
+                e_segs.append(r["stats"]["segments"])
+        h2d = sc.verts.nbytes + sc.tris.nbytes + sc.tri_mat.nbytes + sc.mats.nbytes + 72 + 56
+        e2e = {"value": sum(e_segs) / (sum(e_ms) / 1e3) * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(out_h.numel() * 4 + 576),
+               "includes": "scene upload + LBVH build + trace + map readback, per step"}
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra = run_extra(api, S, torch, gpu_name)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays": tx.num_rays, "max_depth": p.max_depth, "map": [p.ny, p.nx],
+                   "triangles": sc.nt, "segments_per_step": int(seg_step), "block_size": blk or 128,
+                   "blocks_per_sm": bps or "max occupancy", "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+        "clocks": clk, "extra": extra,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return line
+
+
+def run_extra(api, S, torch, gpu_name):
+    """Batched 64-TX form and forward+adjoint of the differentiable workload."""
+    out = {}
+    sc, txs, p = S.workload(3)
+    blk, bps = tuned(gpu_name, "batched")
+    gs = api.Scene.from_obj(sc)
+    prm = api.params_from(p, block_size=blk, blocks_per_sm=bps)
+    maps = torch.empty((len(txs), p.ny, p.nx), dtype=torch.float32, device="cuda")
+    plan = api.TracePlan(gs, txs, prm, maps)
+    for _ in range(3):
+        plan.launch()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, segs = [], 0
+    for _ in range(5):
+        ev0.record()
+        plan.launch()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        segs = plan.stats()["segments"]
+    out["batched_64tx"] = {"value": round(segs / (statistics.mean(ms) / 1e3), 1), "unit": UNIT,
+                           "ms_per_launch": round(statistics.mean(ms), 3), "segments": segs,
+                           "rays": sum(t.num_rays for t in txs), "form": "CUDA graph, one persistent launch"}
+    plan.free()
+    gs.free()
+
+    sc, txs, p = S.workload(4)
+    gs = api.Scene.from_obj(sc)
+    tgt_sc = S.Scene(sc.name, sc.verts, sc.tris, sc.tri_mat, S.perturb_materials(sc.mats, 40))
+    gt = api.Scene.from_obj(tgt_sc)
+    tgt = api.trace(gt, txs, p)["maps"][0]
+    gt.free()
+    f_ms, b_ms, segs = [], [], 0
+    for i in range(8):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = api.trace(gs, txs, p)
+        loss, dL, _ = api.db_mse_loss(f["maps"][0], tgt)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        api.grad(gs, txs, p, dL.view(1, p.ny, p.nx))
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if i >= 3:
+            f_ms.append(f["stats"]["kernel_ms"])
+            segs = f["stats"]["segments"]
+            b_ms.append((t2 - t1) * 1e3)
+    fk = statistics.mean(f_ms)
+    out["differentiable"] = {"fwd_kernel_ms": round(fk, 3), "adj_call_ms": round(statistics.mean(b_ms), 3),
+                             "fwd_plus_adj_over_fwd": round((fk + statistics.mean(b_ms)) / fk, 3),
+                             "fwd_value": round(segs / (fk / 1e3), 1), "unit": UNIT}
+    gs.free()
+    return out
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    import oracle
+    from synth import scenes as S
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    stride = 50                                    # 2e5 rays per step
+    times, segs = [], []
+    for i in range(args.warmup + args.steps):
+        tx.ray_stride, tx.ray_begin = stride, i % stride
+        t0 = time.perf_counter()
+        r = oracle.radio_map(sc, tx, p, want_record=True)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            segs.append(int((r["record"][:, :, 0] != -2).sum()))
+    value = sum(segs) / sum(times)
+    sample = (f"per step: every {stride}th ray of the 1e7-ray lattice ({tx.count()} rays), FP64 brute force over "
+              f"{sc.nt} triangles, OpenMP")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sampled": True},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return line
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

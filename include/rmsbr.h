@@ -1,0 +1,240 @@
+/*
+ * rmsbr.h -- C ABI of the B300 (sm_103a) shooting-and-bouncing-of-rays (SBR)
+ * radio-map library.
+ *
+ * The library computes the radio map of the Sionna RT technical report
+ * (arXiv 2504.21719, Sec. 4): rays leave a transmitter in the directions of a
+ * spherical Fibonacci lattice (Sec. 3.1.1), are traced through a triangle
+ * mesh (Sec. 2.1) with an LBVH, are specularly reflected or refracted through
+ * thin slabs with the radio-material model (App. A.7, Eqs. fresnel_vac,
+ * fresnel_slab), choosing one interaction per hit with the Fresnel-power
+ * heuristic (Eq. path-solver-used-dist-event), and deposit path gain into the
+ * cells of a horizontal measurement plane wherever they cross it
+ * (Eq. radio-map-solver-ci-all-2-estimator, n_S = 0, with the squared ray-tube
+ * length cancelled by the 1/r spreading of Eq. radio-map-solver-path-gain).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named *_dev are CUDA device memory owned by the CALLER; pointers
+ *    named *_host are host memory owned by the caller and only read during the
+ *    call.  Handles (rm_scene, rm_trace_plan) are owned by the library and
+ *    released with the matching *_free call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it.
+ *  - Every call returns an rm_status; no C++ exception crosses the ABI.  On a
+ *    non-OK status, rm_last_error() returns a thread-local message.  Arguments
+ *    are validated on the host before anything is enqueued; RM_EINVAL means
+ *    nothing was launched.
+ *  - Floating-point work is FP32 on the device; counts are 64-bit.
+ *  - Maps are row-major [ny][nx] (cell (ix, iy) at index iy * nx + ix) of
+ *    linear path gain (dimensionless, not dB).  Cell (0, 0) has its lower-left
+ *    corner at (map_origin.x - nx*cell/2, map_origin.y - ny*cell/2).
+ */
+#ifndef RMSBR_H
+#define RMSBR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RM_OK = 0,
+    RM_EINVAL = 1,     /* bad argument; nothing was launched */
+    RM_ENOMEM = 2,     /* a device allocation failed */
+    RM_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
+    RM_EOVERFLOW = 4,  /* a device-side bound was hit (BVH stack); affected rays were dropped */
+    RM_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    RM_ESTATE = 6      /* call order: e.g. tracing before rm_bvh_build, or during stream capture */
+} rm_status;
+
+#define RM_MAX_DEPTH 15      /* maximum number of interactions L */
+#define RM_MAX_MATERIALS 32  /* radio materials per scene */
+#define RM_MAX_TX 64         /* transmitters per trace call */
+
+/* Radio material: the complex relative permittivity is
+ *   eta = eps_r - j sigma / (eps0 omega)                     (Eq. eta)
+ * evaluated at the trace frequency.  thickness > 0: a single-layer slab of
+ * that thickness in metres (Eqs. fresnel_slab, q_fresnel_slab) that reflects
+ * and transmits without deflection (Sec. 2.3); thickness <= 0: a half-space
+ * that only reflects (Eq. fresnel_vac, transmission coefficient 0). */
+typedef struct {
+    float eps_r;
+    float sigma;      /* S/m */
+    float thickness;  /* m */
+} rm_material;
+
+/* One transmitter.  Rays are the lattice directions n = ray_begin + i *
+ * ray_stride, i < ray_count, of a spherical Fibonacci lattice with num_rays
+ * points (Sec. 3.1.1); each carries the solid angle 4 pi / num_rays, so
+ * disjoint subsets of one lattice give maps that add up to the full map.
+ * The antenna (pattern, pol) is oriented by yaw/pitch/roll (rad) as
+ * R = Rz(yaw) Ry(pitch) Rx(roll) (Eq. rotation); its field in the departure
+ * direction is R (C_theta theta' + C_phi phi') with the local angles of
+ * Eq. theta_phi_prime and the pattern C of Eq. C. */
+typedef struct {
+    float pos[3];        /* m */
+    float yaw, pitch, roll;
+    int32_t pol;         /* 0 vertical (theta'), 1 horizontal (phi'), 2 dual: both, maps add (Sec. 4.5) */
+    int32_t pattern;     /* 0 isotropic (G = 1), 1 short dipole (G = 1.5 sin^2 theta') */
+    uint64_t num_rays;   /* N_S >= 1 */
+    uint64_t ray_begin;
+    uint64_t ray_count;  /* UINT64_MAX: all of ceil((num_rays - ray_begin) / ray_stride) */
+    uint64_t ray_stride; /* >= 1 */
+    uint64_t seed;       /* seed of the counter-based interaction sampler */
+} rm_tx;
+
+/* trace flags */
+#define RM_REFLECT 1u   /* allow specular reflection */
+#define RM_REFRACT 2u   /* allow refraction through slabs */
+#define RM_LOS 4u       /* deposit the line-of-sight segment (depth 0) */
+#define RM_STATS 8u     /* collect per-depth power statistics (slower) */
+
+typedef struct {
+    double freq_hz;          /* carrier frequency f; lambda0 = c0 / f */
+    int32_t max_depth;       /* L in [0, RM_MAX_DEPTH]; segments l = 0..L are deposited */
+    uint32_t flags;          /* RM_REFLECT | RM_REFRACT | RM_LOS [| RM_STATS] */
+    float map_origin[3];     /* centre of the map; the plane is z = map_origin[2], normal +z */
+    float cell_size;         /* m, > 0 */
+    int32_t nx, ny;          /* cells, >= 1, nx * ny <= 2^31 - 1, nx, ny <= 32767 */
+    int32_t deposit;         /* 0: box cells (the paper's estimator); 1: bilinear (tent) splat */
+    int32_t block_size;      /* threads per block of the tracer; 0 = tuned default */
+    int32_t blocks_per_sm;   /* resident blocks per SM of the persistent grid; 0 = tuned default */
+    int32_t reserved;
+} rm_trace_params;
+
+/* Counters of one trace call, summed over all transmitters. */
+typedef struct {
+    uint64_t rays;           /* lattice rays launched */
+    uint64_t segments;       /* closest-hit queries = ray-bounces traced */
+    uint64_t nodes_visited;  /* BVH internal nodes fetched */
+    uint64_t tris_tested;    /* ray-triangle tests */
+    uint64_t deposits;       /* plane crossings deposited into a map */
+    uint64_t escapes;        /* segments that hit nothing */
+    uint64_t segments_per_depth[RM_MAX_DEPTH + 1];
+    /* RM_STATS only: sums over segments at depth l of w |E|^2 with w = 1 / Pr(chi),
+     * (times 4 pi / N_S this is the power times solid angle carried), their
+     * squares, and the part of the first sum whose segment escaped. */
+    double power_per_depth[RM_MAX_DEPTH + 1];
+    double power2_per_depth[RM_MAX_DEPTH + 1];
+    double escaped_power_per_depth[RM_MAX_DEPTH + 1];
+    int32_t status;          /* rm_status of the device-side checks */
+    int32_t reserved;
+    double kernel_ms;        /* device time of the tracer kernel (CUDA events on `stream`) */
+} rm_stats;
+
+/* Debug record of one segment (layout [tx][i][l], i the subset index,
+ * l = 0..L).  prim: original triangle index hit, -1 escaped, -2 the ray had
+ * already terminated.  ix, iy: deposited cell (bilinear: lower-left cell of
+ * the 2x2 stencil), -32768 for no deposit.  decision: 0 reflection,
+ * 1 refraction, -1 none. */
+typedef struct {
+    int32_t prim, ix, iy, decision;
+} rm_segment_record;
+
+typedef struct rm_scene rm_scene;
+typedef struct rm_trace_plan rm_trace_plan;
+
+/* Copies a triangle mesh (Sec. 2.1) to library-owned device memory and
+ * computes per-triangle bounding boxes.
+ *   verts_dev  float [nv][3] (m); tris_dev int32 [nt][3] vertex indices;
+ *   tri_mat_dev int32 [nt] material index per triangle; mats_host [nm].
+ * nt may be 0 (free space).  Index ranges are checked on the device and
+ * reported as RM_EINVAL (this call synchronises `stream`).  Caller buffers
+ * may be freed after return.  *out is set on RM_OK only. */
+rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tris_dev, int64_t nt,
+                          const int32_t* tri_mat_dev, const rm_material* mats_host, int32_t nm,
+                          void* stream, rm_scene** out);
+
+/* Replaces the material table (no BVH rebuild).  sampling_host_or_null
+ * (nm entries) sets the materials from which the interaction probabilities
+ * q(R), q(T) are computed (detached from the fields); NULL = mats_host. */
+rm_status rm_scene_set_materials(rm_scene* scene, const rm_material* mats_host, int32_t nm,
+                                 const rm_material* sampling_host_or_null);
+
+/* Builds the LBVH on `stream`: 63-bit Morton codes of the doubled triangle
+ * centroids, a stable 8-bit-digit radix sort, the Karras (HPG 2012) binary
+ * radix tree with duplicate keys ordered by position, an exact AABB refit,
+ * and the 64-byte two-child node layout.  Not part of the paper (its
+ * implementation uses Mitsuba's acceleration structure).  Must precede
+ * tracing; may be called again after rm_scene_upload only. */
+rm_status rm_bvh_build(rm_scene* scene, void* stream);
+
+/* Exports the built tree for inspection (synchronous).  Host outputs:
+ * keys [nt] sorted Morton codes, order [nt] sorted triangle ids,
+ * child [nt-1][2] (>= 0 internal node, < 0 leaf ~position),
+ * child_aabb [nt-1][2][6] (lo xyz, hi xyz of each child). */
+rm_status rm_bvh_export(const rm_scene* scene, uint64_t* keys_host, int32_t* order_host,
+                        int32_t* child_host, float* child_aabb_host);
+
+/* Traces the radio maps of ntx transmitters (1 <= ntx <= RM_MAX_TX) in one
+ * persistent launch whose work queue hands out (transmitter, ray) items, and
+ * writes maps_dev [ntx][ny][nx] (overwritten; FP32 atomics, so the order of
+ * additions, and the last bits, vary between runs).  Each map is the
+ * estimator of Eq. radio-map-solver-ci-all-2-estimator for its transmitter.
+ * stats_host_or_null receives the counters.  record_dev_or_null receives one
+ * rm_segment_record per (tx, ray, depth).  Synchronises `stream` before
+ * returning (to read the device status); returns RM_ESTATE if `stream` is
+ * capturing (use rm_trace_plan_* for graph launches). */
+rm_status rm_radio_map_trace(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
+                             const rm_trace_params* params, float* maps_dev,
+                             rm_stats* stats_host_or_null, rm_segment_record* record_dev_or_null,
+                             void* stream);
+
+/* Vector-Jacobian product of the maps: given dL_dmaps_dev [ntx][ny][nx],
+ * re-traces the same rays (same lattice, same sampler, hence the same hits,
+ * decisions and cells) and accumulates
+ *   d_eps_dev[m]   += sum_i dL/dC_i dC_i/d eps_r[m]
+ *   d_sigma_dev[m] += sum_i dL/dC_i dC_i/d sigma[m]           (m < nm)
+ *   d_txpos_dev[t][3] += sum_i dL/dC_i dC_i/d pos[t]
+ * with the discrete choices held fixed and the sampling probabilities
+ * detached (the derivative of f / q is taken as f' / q).  The outputs are
+ * ACCUMULATED into (zero them first).  Under box deposit the maps do not
+ * depend on the transmitter positions at fixed cells, so d_txpos stays 0;
+ * bilinear deposit gives the derivative through the crossing points.
+ * sampling_host_or_null overrides the scene's sampling materials for this
+ * call.  Any of the three outputs may be NULL.  stats_host_or_null and
+ * record_dev_or_null report the re-trace exactly as rm_radio_map_trace does
+ * (the record must equal the forward call's).  Synchronises `stream`. */
+rm_status rm_radio_map_grad(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
+                            const rm_trace_params* params, const float* dL_dmaps_dev,
+                            float* d_eps_dev, float* d_sigma_dev, float* d_txpos_dev,
+                            const rm_material* sampling_host_or_null, rm_stats* stats_host_or_null,
+                            rm_segment_record* record_dev_or_null, void* stream);
+
+/* Loss of the differentiable workload: mean over the cells V where both maps
+ * exceed floor_linear of (10 log10 C_i - 10 log10 T_i)^2.  Writes loss_dev[0]
+ * (float), dL_dmaps_dev [ncells] (0 outside V) and valid_dev[0] = |V|
+ * (int64).  Asynchronous on `stream`. */
+rm_status rm_db_mse_loss(const float* maps_dev, const float* target_dev, int64_t ncells,
+                         float floor_linear, float* loss_dev, float* dL_dmaps_dev,
+                         int64_t* valid_dev, void* stream);
+
+/* A trace captured once into a CUDA graph (map clear + persistent tracer),
+ * for repeated launches with the same arguments.  The plan owns its scratch
+ * memory; maps_dev must outlive it. */
+rm_status rm_trace_plan_create(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
+                               const rm_trace_params* params, float* maps_dev, void* stream,
+                               rm_trace_plan** out);
+rm_status rm_trace_plan_launch(rm_trace_plan* plan, void* stream);
+/* Counters of the last launch (synchronises `stream`). */
+rm_status rm_trace_plan_stats(rm_trace_plan* plan, void* stream, rm_stats* stats_host);
+void rm_trace_plan_free(rm_trace_plan* plan);
+
+/* Number of triangles / BVH nodes of a scene (host call, no device work). */
+rm_status rm_scene_info(const rm_scene* scene, int64_t* nt, int64_t* nnodes, int32_t* nm,
+                        int32_t* built);
+
+void rm_scene_free(rm_scene* scene);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* rm_last_error(void);
+
+/* Library version string. */
+const char* rm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMSBR_H */

@@ -1,0 +1,547 @@
+// C ABI of the SBR radio-map library (declared in include/rmsbr.h): argument
+// validation, scene and plan lifetime, per-call constant tables and launches.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace rmsbr;
+
+struct rm_scene {
+    int device = 0;
+    int64_t nv = 0, nt = 0;
+    int32_t nm = 0;
+    float* verts = nullptr;
+    int32_t* tris = nullptr;
+    int32_t* tri_mat = nullptr;
+    std::vector<rm_material> mats, smats;
+    bool has_smats = false;
+    bool built = false;
+    uint64_t* keys = nullptr;
+    int32_t* order = nullptr;
+    float4* nodes = nullptr;
+    float4* trirec = nullptr;
+};
+
+struct rm_trace_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    char* dev = nullptr;
+    Scratch* scratch = nullptr;
+    int ntx = 0, L = 0;
+};
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double C0 = 299792458.0;          // m/s
+constexpr double EPS0 = 8.8541878128e-12;   // F/m (CODATA 2018)
+constexpr int DEFAULT_BLOCK = 128;
+
+thread_local std::string g_err;
+
+rm_status fail(rm_status s, const std::string& m) {
+    g_err = m;
+    return s;
+}
+rm_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? RM_ENOMEM : RM_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define RM_CUDA(expr)                                      \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+rm_status check_device(const rm_scene* sc) {
+    int dev = -1;
+    RM_CUDA(cudaGetDevice(&dev));
+    if (dev != sc->device) return fail(RM_ESTATE, "current device differs from the scene's device");
+    return RM_OK;
+}
+
+rm_status check_materials(const rm_material* m, int32_t nm) {
+    if (nm < 1 || nm > RM_MAX_MATERIALS) return fail(RM_EINVAL, "nm must be in [1, 32]");
+    if (!m) return fail(RM_EINVAL, "materials pointer is NULL");
+    for (int i = 0; i < nm; ++i)
+        if (!std::isfinite(m[i].eps_r) || !std::isfinite(m[i].sigma) || !std::isfinite(m[i].thickness) ||
+            m[i].eps_r <= 0.0f || m[i].sigma < 0.0f)
+            return fail(RM_EINVAL, "material " + std::to_string(i) + " has eps_r <= 0, sigma < 0 or a non-finite value");
+    return RM_OK;
+}
+
+uint64_t tx_count(const rm_tx& t) {
+    if (t.ray_count != UINT64_MAX) return t.ray_count;
+    if (t.ray_begin >= t.num_rays) return 0;
+    return (t.num_rays - t.ray_begin + t.ray_stride - 1) / t.ray_stride;
+}
+
+rm_status validate(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p) {
+    if (!sc) return fail(RM_EINVAL, "scene is NULL");
+    if (!sc->built) return fail(RM_ESTATE, "rm_bvh_build has not been called on this scene");
+    if (!tx || !p) return fail(RM_EINVAL, "tx or params is NULL");
+    if (ntx < 1 || ntx > RM_MAX_TX) return fail(RM_EINVAL, "ntx must be in [1, 64]");
+    if (!(p->freq_hz > 0.0) || !std::isfinite(p->freq_hz)) return fail(RM_EINVAL, "freq_hz must be > 0");
+    if (p->max_depth < 0 || p->max_depth > RM_MAX_DEPTH) return fail(RM_EINVAL, "max_depth must be in [0, 15]");
+    if (!(p->cell_size > 0.0f) || !std::isfinite(p->cell_size)) return fail(RM_EINVAL, "cell_size must be > 0");
+    if (p->nx < 1 || p->ny < 1 || p->nx > 32767 || p->ny > 32767 || (int64_t)p->nx * p->ny > INT32_MAX)
+        return fail(RM_EINVAL, "nx, ny must be in [1, 32767] with nx*ny < 2^31");
+    if (p->deposit != 0 && p->deposit != 1) return fail(RM_EINVAL, "deposit must be 0 (box) or 1 (bilinear)");
+    if (p->block_size != 0 && (p->block_size < 32 || p->block_size > MAX_BLOCK || (p->block_size & 31)))
+        return fail(RM_EINVAL, "block_size must be 0 or a multiple of 32 in [32, 256]");
+    if (p->blocks_per_sm < 0) return fail(RM_EINVAL, "blocks_per_sm must be >= 0");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(p->map_origin[i])) return fail(RM_EINVAL, "map_origin must be finite");
+    for (int t = 0; t < ntx; ++t) {
+        const rm_tx& x = tx[t];
+        const std::string w = "tx " + std::to_string(t) + ": ";
+        if (x.num_rays < 1 || x.num_rays >= (1ULL << 59)) return fail(RM_EINVAL, w + "num_rays must be in [1, 2^59)");
+        if (x.ray_stride < 1) return fail(RM_EINVAL, w + "ray_stride must be >= 1");
+        if (x.pol < 0 || x.pol > 2) return fail(RM_EINVAL, w + "pol must be 0, 1 or 2");
+        if (x.pattern < 0 || x.pattern > 1) return fail(RM_EINVAL, w + "pattern must be 0 or 1");
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(x.pos[i])) return fail(RM_EINVAL, w + "position must be finite");
+        if (!std::isfinite(x.yaw) || !std::isfinite(x.pitch) || !std::isfinite(x.roll))
+            return fail(RM_EINVAL, w + "orientation must be finite");
+        const uint64_t c = tx_count(x);
+        if (c > 0) {
+            if (x.ray_begin >= x.num_rays) return fail(RM_EINVAL, w + "ray_begin >= num_rays");
+            if ((c - 1) > (x.num_rays - 1 - x.ray_begin) / x.ray_stride)
+                return fail(RM_EINVAL, w + "ray subset exceeds the lattice");
+        }
+    }
+    if (ntx > 1) {
+        const int np = tx[0].pol == 2 ? 2 : 1;
+        for (int t = 1; t < ntx; ++t)
+            if ((tx[t].pol == 2 ? 2 : 1) != np)
+                return fail(RM_EINVAL, "all transmitters of one call must be dual-polarised or none");
+    }
+    return RM_OK;
+}
+
+struct Prepared {
+    TraceArgs a;
+    std::vector<MatDev> mats;
+    std::vector<TxDev> tx;
+    int npol = 1;
+    bool bilinear = false;
+    int block = DEFAULT_BLOCK;
+    int bps = 0;
+    double kernel_ms = 0.0;
+};
+
+void rotation(double a, double b, double g, float* R) {
+    // R = Rz(a) Ry(b) Rx(g)  (Eq. rotation)
+    const double ca = std::cos(a), sa = std::sin(a), cb = std::cos(b), sb = std::sin(b), cg = std::cos(g),
+                 sg = std::sin(g);
+    const double M[9] = {ca * cb, ca * sb * sg - sa * cg, ca * sb * cg + sa * sg,
+                         sa * cb, sa * sb * sg + ca * cg, sa * sb * cg - ca * sg,
+                         -sb,     cb * sg,                cb * cg};
+    for (int i = 0; i < 9; ++i) R[i] = (float)M[i];
+}
+
+void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
+             const rm_material* sampling_override, Prepared* P) {
+    const double f = p->freq_hz, omega = 2.0 * PI * f, k0 = omega / C0, lam = C0 / f;
+    const std::vector<rm_material>& sm = sc->has_smats ? sc->smats : sc->mats;
+    P->mats.resize(sc->nm);
+    bool same = !sampling_override && !sc->has_smats;
+    for (int m = 0; m < sc->nm; ++m) {
+        const rm_material& e = sc->mats[m];
+        const rm_material& s = sampling_override ? sampling_override[m] : sm[m];
+        MatDev& d = P->mats[m];
+        d.eta_re = e.eps_r;
+        d.eta_im = (float)(-(double)e.sigma / (EPS0 * omega));
+        d.seta_re = s.eps_r;
+        d.seta_im = (float)(-(double)s.sigma / (EPS0 * omega));
+        const double k0d = e.thickness > 0.0f ? k0 * (double)e.thickness : 0.0;
+        d.k0d_hi = (float)k0d;
+        d.k0d_lo = (float)(k0d - (double)d.k0d_hi);
+        d.slab = e.thickness > 0.0f ? 1 : 0;
+        d.pad = 0;
+        if (s.eps_r != e.eps_r || s.sigma != e.sigma) same = false;
+    }
+    P->tx.resize(ntx);
+    unsigned long long work = 0, rec = 0;
+    const double a = lam / (4.0 * PI);
+    for (int t = 0; t < ntx; ++t) {
+        TxDev& d = P->tx[t];
+        std::memset(&d, 0, sizeof d);
+        for (int i = 0; i < 3; ++i) d.pos[i] = tx[t].pos[i];
+        rotation(tx[t].yaw, tx[t].pitch, tx[t].roll, d.R);
+        d.pattern = tx[t].pattern;
+        d.pol = tx[t].pol;
+        d.dep_scale = (float)(4.0 * PI / ((double)tx[t].num_rays * (double)p->cell_size * (double)p->cell_size) * a * a);
+        d.N = tx[t].num_rays;
+        d.begin = tx[t].ray_begin;
+        d.stride = tx[t].ray_stride;
+        d.count = tx_count(tx[t]);
+        d.work_begin = work;
+        d.seed = tx[t].seed;
+        d.rec_begin = rec;
+        work += d.count;
+        rec += d.count * (unsigned long long)(p->max_depth + 1);
+    }
+    TraceArgs& A = P->a;
+    std::memset(&A, 0, sizeof A);
+    A.nodes = sc->nodes;
+    A.tris = sc->trirec;
+    A.nt = (int32_t)sc->nt;
+    A.ntx = ntx;
+    A.nm = sc->nm;
+    A.L = p->max_depth;
+    A.flags = p->flags;
+    A.x0 = (float)((double)p->map_origin[0] - 0.5 * p->nx * (double)p->cell_size);
+    A.y0 = (float)((double)p->map_origin[1] - 0.5 * p->ny * (double)p->cell_size);
+    A.zm = p->map_origin[2];
+    A.cell = p->cell_size;
+    A.inv_cell = (float)(1.0 / (double)p->cell_size);
+    A.nx = p->nx;
+    A.ny = p->ny;
+    A.inv_eps0_omega = (float)(1.0 / (EPS0 * omega));
+    A.same_sampling = same ? 1 : 0;
+    A.total = work;
+    A.ncell = (unsigned long long)p->nx * p->ny;
+    P->npol = tx[0].pol == 2 ? 2 : 1;
+    P->bilinear = p->deposit == 1;
+    P->block = p->block_size ? p->block_size : DEFAULT_BLOCK;
+    P->bps = p->blocks_per_sm;
+}
+
+// device block: [Scratch | MatDev[nm] | TxDev[ntx]]
+size_t table_bytes(const Prepared& P, size_t* o_mat, size_t* o_tx) {
+    size_t off = (sizeof(Scratch) + 255) & ~size_t(255);
+    *o_mat = off;
+    off += (P.mats.size() * sizeof(MatDev) + 255) & ~size_t(255);
+    *o_tx = off;
+    off += P.tx.size() * sizeof(TxDev);
+    return off;
+}
+
+void fill_stats(const Scratch& h, const Prepared& P, rm_stats* st) {
+    std::memset(st, 0, sizeof *st);
+    st->rays = h.cnt[0];
+    st->segments = h.cnt[1];
+    st->nodes_visited = h.cnt[2];
+    st->tris_tested = h.cnt[3];
+    st->deposits = h.cnt[4];
+    st->escapes = h.cnt[5];
+    for (int l = 0; l <= RM_MAX_DEPTH; ++l) {
+        st->segments_per_depth[l] = h.seg_depth[l];
+        st->power_per_depth[l] = h.pw[l];
+        st->power2_per_depth[l] = h.pw2[l];
+        st->escaped_power_per_depth[l] = h.esc[l];
+    }
+    st->status = (h.status & 1) ? RM_EOVERFLOW : RM_OK;
+    st->kernel_ms = P.kernel_ms;
+}
+
+rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p, float* maps,
+                    const float* dLdC, float* d_eps, float* d_sig, float* d_tx, const rm_material* smats,
+                    rm_stats* stats, rm_segment_record* record, void* stream, bool adjoint) {
+    rm_status st = validate(sc, tx, ntx, p);
+    if (st != RM_OK) return st;
+    if ((st = check_device(sc)) != RM_OK) return st;
+    if (!adjoint && !maps) return fail(RM_EINVAL, "maps_dev is NULL");
+    if (adjoint && !dLdC) return fail(RM_EINVAL, "dL_dmaps_dev is NULL");
+    if (smats && (st = check_materials(smats, sc->nm)) != RM_OK) return st;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RM_CUDA(cudaStreamIsCapturing(S(stream), &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(RM_ESTATE, "stream is capturing; use rm_trace_plan_create for graph launches");
+
+    Prepared P;
+    prepare(sc, tx, ntx, p, smats, &P);
+    const bool debug = record != nullptr || (p->flags & RM_STATS);
+    size_t o_mat, o_tx;
+    const size_t bytes = table_bytes(P, &o_mat, &o_tx);
+    cudaEvent_t ev[2];
+    RM_CUDA(cudaEventCreate(&ev[0]));
+    RM_CUDA(cudaEventCreate(&ev[1]));
+    bool timed = false;
+    char* dev = nullptr;
+    RM_CUDA(cudaMallocAsync((void**)&dev, bytes, S(stream)));
+    Scratch host;
+    cudaError_t e = cudaSuccess;
+    int grid = 0;
+    do {
+        if ((e = cudaMemsetAsync(dev, 0, sizeof(Scratch), S(stream))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(dev + o_mat, P.mats.data(), P.mats.size() * sizeof(MatDev),
+                                 cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice,
+                                 S(stream))) != cudaSuccess) break;
+        if (!adjoint && (e = cudaMemsetAsync(maps, 0, sizeof(float) * P.a.ncell * ntx, S(stream))) != cudaSuccess) break;
+        unsigned long long nrec = 0;
+        for (const TxDev& t : P.tx) nrec += t.count * (unsigned long long)(p->max_depth + 1);
+        if (record && (e = launch_fill_record(record, nrec, S(stream))) != cudaSuccess) break;
+        P.a.mats = reinterpret_cast<const MatDev*>(dev + o_mat);
+        P.a.tx = reinterpret_cast<const TxDev*>(dev + o_tx);
+        P.a.scratch = reinterpret_cast<Scratch*>(dev);
+        P.a.maps = maps;
+        P.a.dLdC = dLdC;
+        P.a.record = record;
+        if (P.a.total > 0) {
+            if ((e = cudaEventRecord(ev[0], S(stream))) != cudaSuccess) break;
+            if ((e = launch_trace(P.a, P.npol, debug, P.bilinear, adjoint, P.block, P.bps, S(stream), &grid)) !=
+                cudaSuccess)
+                break;
+            if ((e = cudaEventRecord(ev[1], S(stream))) != cudaSuccess) break;
+            timed = true;
+        }
+        if (adjoint && (e = launch_grad_out(reinterpret_cast<const Scratch*>(dev)->grad, sc->nm, ntx, d_eps, d_sig,
+                                            d_tx, S(stream))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(&host, dev, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
+    } while (false);
+    cudaError_t e2 = cudaFreeAsync(dev, S(stream));
+    cudaError_t e3 = cudaStreamSynchronize(S(stream));
+    float ms = 0.0f;
+    if (timed && e == cudaSuccess && e3 == cudaSuccess && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess)
+        P.kernel_ms = ms;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) return cuda_fail(e, adjoint ? "rm_radio_map_grad" : "rm_radio_map_trace");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
+    if (stats) fill_stats(host, P, stats);
+    if (host.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow; affected rays were dropped");
+    return RM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rm_last_error(void) { return g_err.c_str(); }
+
+const char* rm_version(void) { return "rmsbr 0.1 (sm_103a)"; }
+
+rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tris_dev, int64_t nt,
+                          const int32_t* tri_mat_dev, const rm_material* mats_host, int32_t nm, void* stream,
+                          rm_scene** out) {
+    if (!out) return fail(RM_EINVAL, "out is NULL");
+    if (nv < 0 || nt < 0) return fail(RM_EINVAL, "nv and nt must be >= 0");
+    if (nt > (int64_t)INT32_MAX / 4) return fail(RM_EINVAL, "nt too large");
+    if (nt > 0 && (!verts_dev || !tris_dev || !tri_mat_dev || nv < 1))
+        return fail(RM_EINVAL, "mesh pointers are NULL for a non-empty mesh");
+    rm_status st = check_materials(mats_host, nm);
+    if (st != RM_OK) return st;
+    rm_scene* sc = new rm_scene();
+    RM_CUDA(cudaGetDevice(&sc->device));
+    sc->nv = nv;
+    sc->nt = nt;
+    sc->nm = nm;
+    sc->mats.assign(mats_host, mats_host + nm);
+    auto cleanup = [&](rm_status s) { rm_scene_free(sc); return s; };
+    cudaError_t e;
+    if (nt > 0) {
+        if ((e = cudaMalloc((void**)&sc->verts, sizeof(float) * 3 * nv)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
+        if ((e = cudaMalloc((void**)&sc->tris, sizeof(int32_t) * 3 * nt)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
+        if ((e = cudaMalloc((void**)&sc->tri_mat, sizeof(int32_t) * nt)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
+        int32_t* flag = nullptr;
+        if ((e = cudaMallocAsync((void**)&flag, sizeof(int32_t), S(stream))) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocAsync"));
+        int32_t hflag = 0;
+        do {
+            if ((e = cudaMemcpyAsync(sc->verts, verts_dev, sizeof(float) * 3 * nv, cudaMemcpyDeviceToDevice, S(stream))) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(sc->tris, tris_dev, sizeof(int32_t) * 3 * nt, cudaMemcpyDeviceToDevice, S(stream))) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(sc->tri_mat, tri_mat_dev, sizeof(int32_t) * nt, cudaMemcpyDeviceToDevice, S(stream))) != cudaSuccess) break;
+            if ((e = cudaMemsetAsync(flag, 0, sizeof(int32_t), S(stream))) != cudaSuccess) break;
+            if ((e = check_indices(sc->tris, sc->tri_mat, nt, nv, nm, flag, S(stream))) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
+        } while (false);
+        cudaFreeAsync(flag, S(stream));
+        cudaError_t es = cudaStreamSynchronize(S(stream));
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "rm_scene_upload"));
+        if (es != cudaSuccess) return cleanup(cuda_fail(es, "cudaStreamSynchronize"));
+        if (hflag) return cleanup(fail(RM_EINVAL, "a vertex or material index is out of range"));
+    }
+    *out = sc;
+    return RM_OK;
+}
+
+rm_status rm_scene_set_materials(rm_scene* sc, const rm_material* mats_host, int32_t nm,
+                                 const rm_material* sampling_host_or_null) {
+    if (!sc) return fail(RM_EINVAL, "scene is NULL");
+    if (nm != sc->nm) return fail(RM_EINVAL, "nm must equal the scene's material count");
+    rm_status st = check_materials(mats_host, nm);
+    if (st != RM_OK) return st;
+    if (sampling_host_or_null && (st = check_materials(sampling_host_or_null, nm)) != RM_OK) return st;
+    sc->mats.assign(mats_host, mats_host + nm);
+    sc->has_smats = sampling_host_or_null != nullptr;
+    if (sc->has_smats) sc->smats.assign(sampling_host_or_null, sampling_host_or_null + nm);
+    else sc->smats.clear();
+    return RM_OK;
+}
+
+rm_status rm_bvh_build(rm_scene* sc, void* stream) {
+    if (!sc) return fail(RM_EINVAL, "scene is NULL");
+    rm_status st = check_device(sc);
+    if (st != RM_OK) return st;
+    if (sc->built) return fail(RM_ESTATE, "the BVH of this scene is already built");
+    const int64_t n = sc->nt;
+    if (n > 0) {
+        RM_CUDA(cudaMalloc((void**)&sc->keys, sizeof(uint64_t) * n));
+        RM_CUDA(cudaMalloc((void**)&sc->order, sizeof(int32_t) * n));
+        RM_CUDA(cudaMalloc((void**)&sc->nodes, sizeof(float4) * 4 * (n > 1 ? n - 1 : 1)));
+        RM_CUDA(cudaMalloc((void**)&sc->trirec, sizeof(float4) * 3 * n));
+        BvhBuffers B{sc->verts, sc->tris, sc->tri_mat, n, sc->keys, sc->order, sc->nodes, sc->trirec};
+        RM_CUDA(build_bvh(B, S(stream)));
+        RM_CUDA(cudaStreamSynchronize(S(stream)));
+    }
+    sc->built = true;
+    return RM_OK;
+}
+
+rm_status rm_bvh_export(const rm_scene* sc, uint64_t* keys_host, int32_t* order_host, int32_t* child_host,
+                        float* child_aabb_host) {
+    if (!sc) return fail(RM_EINVAL, "scene is NULL");
+    if (!sc->built) return fail(RM_ESTATE, "rm_bvh_build has not been called on this scene");
+    rm_status st = check_device(sc);
+    if (st != RM_OK) return st;
+    const int64_t n = sc->nt;
+    if (n <= 0) return RM_OK;
+    if (keys_host) RM_CUDA(cudaMemcpy(keys_host, sc->keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+    if (order_host) RM_CUDA(cudaMemcpy(order_host, sc->order, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (n > 1 && (child_host || child_aabb_host)) {
+        std::vector<float4> nodes((size_t)4 * (n - 1));
+        RM_CUDA(cudaMemcpy(nodes.data(), sc->nodes, sizeof(float4) * 4 * (n - 1), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n - 1; ++i) {
+            const float* f = reinterpret_cast<const float*>(&nodes[4 * i]);
+            if (child_host) {
+                std::memcpy(&child_host[2 * i], &f[12], sizeof(int32_t));
+                std::memcpy(&child_host[2 * i + 1], &f[13], sizeof(int32_t));
+            }
+            if (child_aabb_host) std::memcpy(&child_aabb_host[12 * i], f, 12 * sizeof(float));
+        }
+    }
+    return RM_OK;
+}
+
+rm_status rm_radio_map_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
+                             float* maps_dev, rm_stats* stats, rm_segment_record* record, void* stream) {
+    return run_trace(sc, tx, ntx, p, maps_dev, nullptr, nullptr, nullptr, nullptr, nullptr, stats, record, stream,
+                     false);
+}
+
+rm_status rm_radio_map_grad(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
+                            const float* dL_dmaps_dev, float* d_eps_dev, float* d_sigma_dev, float* d_txpos_dev,
+                            const rm_material* sampling_host_or_null, rm_stats* stats, rm_segment_record* record,
+                            void* stream) {
+    return run_trace(sc, tx, ntx, p, nullptr, dL_dmaps_dev, d_eps_dev, d_sigma_dev, d_txpos_dev,
+                     sampling_host_or_null, stats, record, stream, true);
+}
+
+rm_status rm_db_mse_loss(const float* maps_dev, const float* target_dev, int64_t ncells, float floor_linear,
+                         float* loss_dev, float* dL_dmaps_dev, int64_t* valid_dev, void* stream) {
+    if (!maps_dev || !target_dev || !dL_dmaps_dev) return fail(RM_EINVAL, "NULL buffer");
+    if (ncells < 1) return fail(RM_EINVAL, "ncells must be >= 1");
+    if (!(floor_linear >= 0.0f)) return fail(RM_EINVAL, "floor_linear must be >= 0");
+    double* acc = nullptr;
+    RM_CUDA(cudaMallocAsync((void**)&acc, 2 * sizeof(double), S(stream)));
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), S(stream));
+    if (e == cudaSuccess)
+        e = launch_db_mse(maps_dev, target_dev, ncells, floor_linear, acc, loss_dev, dL_dmaps_dev, valid_dev, S(stream));
+    cudaError_t e2 = cudaFreeAsync(acc, S(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rm_db_mse_loss");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return RM_OK;
+}
+
+rm_status rm_trace_plan_create(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
+                               float* maps_dev, void* stream, rm_trace_plan** out) {
+    if (!out) return fail(RM_EINVAL, "out is NULL");
+    rm_status st = validate(sc, tx, ntx, p);
+    if (st != RM_OK) return st;
+    if ((st = check_device(sc)) != RM_OK) return st;
+    if (!maps_dev) return fail(RM_EINVAL, "maps_dev is NULL");
+    if (p->flags & RM_STATS) return fail(RM_EINVAL, "RM_STATS is not available in a plan");
+    Prepared P;
+    prepare(sc, tx, ntx, p, nullptr, &P);
+    size_t o_mat, o_tx;
+    const size_t bytes = table_bytes(P, &o_mat, &o_tx);
+    rm_trace_plan* pl = new rm_trace_plan();
+    pl->ntx = ntx;
+    pl->L = p->max_depth;
+    auto cleanup = [&](rm_status s) { rm_trace_plan_free(pl); return s; };
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(S(stream))) != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamSynchronize"));
+    if ((e = cudaMalloc((void**)&pl->dev, bytes)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
+    if ((e = cudaMemcpy(pl->dev + o_mat, P.mats.data(), P.mats.size() * sizeof(MatDev), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMemcpy"));
+    if ((e = cudaMemcpy(pl->dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMemcpy"));
+    pl->scratch = reinterpret_cast<Scratch*>(pl->dev);
+    P.a.mats = reinterpret_cast<const MatDev*>(pl->dev + o_mat);
+    P.a.tx = reinterpret_cast<const TxDev*>(pl->dev + o_tx);
+    P.a.scratch = pl->scratch;
+    P.a.maps = maps_dev;
+    cudaStream_t cap;
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    cudaError_t ec = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (ec == cudaSuccess) {
+        cudaError_t ek = cudaMemsetAsync(pl->dev, 0, sizeof(Scratch), cap);
+        if (ek == cudaSuccess) ek = cudaMemsetAsync(maps_dev, 0, sizeof(float) * P.a.ncell * ntx, cap);
+        int grid = 0;
+        if (ek == cudaSuccess && P.a.total > 0)
+            ek = launch_trace(P.a, P.npol, false, P.bilinear, false, P.block, P.bps, cap, &grid);
+        ec = cudaStreamEndCapture(cap, &pl->graph);
+        if (ek != cudaSuccess) ec = ek;
+    }
+    if (ec == cudaSuccess) ec = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+    cudaStreamDestroy(cap);
+    if (ec != cudaSuccess) return cleanup(cuda_fail(ec, "graph capture"));
+    *out = pl;
+    return RM_OK;
+}
+
+rm_status rm_trace_plan_launch(rm_trace_plan* pl, void* stream) {
+    if (!pl || !pl->exec) return fail(RM_EINVAL, "plan is NULL");
+    RM_CUDA(cudaGraphLaunch(pl->exec, S(stream)));
+    return RM_OK;
+}
+
+rm_status rm_trace_plan_stats(rm_trace_plan* pl, void* stream, rm_stats* out) {
+    if (!pl || !out) return fail(RM_EINVAL, "NULL argument");
+    Scratch h;
+    RM_CUDA(cudaMemcpyAsync(&h, pl->scratch, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream)));
+    RM_CUDA(cudaStreamSynchronize(S(stream)));
+    Prepared P;
+    fill_stats(h, P, out);
+    if (h.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow; affected rays were dropped");
+    return RM_OK;
+}
+
+void rm_trace_plan_free(rm_trace_plan* pl) {
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->dev) cudaFree(pl->dev);
+    delete pl;
+}
+
+rm_status rm_scene_info(const rm_scene* sc, int64_t* nt, int64_t* nnodes, int32_t* nm, int32_t* built) {
+    if (!sc) return fail(RM_EINVAL, "scene is NULL");
+    if (nt) *nt = sc->nt;
+    if (nnodes) *nnodes = sc->nt > 1 ? sc->nt - 1 : 0;
+    if (nm) *nm = sc->nm;
+    if (built) *built = sc->built ? 1 : 0;
+    return RM_OK;
+}
+
+void rm_scene_free(rm_scene* sc) {
+    if (!sc) return;
+    cudaFree(sc->verts);
+    cudaFree(sc->tris);
+    cudaFree(sc->tri_mat);
+    cudaFree(sc->keys);
+    cudaFree(sc->order);
+    cudaFree(sc->nodes);
+    cudaFree(sc->trirec);
+    delete sc;
+}
+
+}  // extern "C"

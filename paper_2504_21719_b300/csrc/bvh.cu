@@ -1,0 +1,370 @@
+// LBVH construction on the GPU.  Not part of the paper (Sionna RT relies on
+// Mitsuba's acceleration structure); the tree is the binary radix tree of
+// Karras, "Maximizing parallelism in the construction of BVHs, octrees and
+// k-d trees" (HPG 2012), over 63-bit Morton codes of the doubled triangle
+// centroids, with duplicate keys ordered by their sorted position.
+//
+// Every floating-point step that decides an integer (the Morton quantisation)
+// uses explicitly rounded FP32 intrinsics, and every min / max is the
+// comparison-select (b < a ? b : a), so the tree is identical bit for bit on
+// any run and to any other IEEE implementation of the same definition.
+//
+// Node layout (64 bytes = 4 x float4) of internal node i:
+//   [0] lo0.x lo0.y lo0.z hi0.x   [1] hi0.y hi0.z lo1.x lo1.y
+//   [2] lo1.z hi1.x hi1.y hi1.z   [3] child0 child1 (int bits) 0 0
+// child >= 0: internal node; child < 0: leaf ~p, the triangle at sorted
+// position p, whose 48-byte record is trirec[3p .. 3p+2]:
+//   [0] a.x a.y a.z b.x   [1] b.y b.z c.x c.y   [2] c.z mat(int) orig(int) 0
+#include "common.cuh"
+
+namespace rmsbr {
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+
+__device__ __forceinline__ float fmin_sel(float a, float b) { return (b < a) ? b : a; }
+__device__ __forceinline__ float fmax_sel(float a, float b) { return (a < b) ? b : a; }
+
+__global__ void k_check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t nt, int64_t nv,
+                                int32_t nm, int32_t* flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    bool bad = false;
+    for (int j = 0; j < 3; ++j) {
+        int32_t v = tris[3 * i + j];
+        bad |= (v < 0) || ((int64_t)v >= nv);
+    }
+    int32_t m = tri_mat[i];
+    bad |= (m < 0) || (m >= nm);
+    if (bad) atomicOr(flag, 1);
+}
+
+// Per-triangle AABB and doubled centroid c2 = lo + hi; per-block min / max of c2.
+__global__ void k_tri_aabb(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
+                           float* __restrict__ aabb, float* __restrict__ c2, float* __restrict__ blk) {
+    __shared__ float smin[3][256], smax[3][256];
+    const int tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (i < nt) {
+        const int32_t i0 = tris[3 * i], i1 = tris[3 * i + 1], i2 = tris[3 * i + 2];
+        for (int a = 0; a < 3; ++a) {
+            const float v0 = verts[3 * (int64_t)i0 + a], v1 = verts[3 * (int64_t)i1 + a],
+                        v2 = verts[3 * (int64_t)i2 + a];
+            const float lo = fmin_sel(v0, fmin_sel(v1, v2));
+            const float hi = fmax_sel(v0, fmax_sel(v1, v2));
+            const float c = __fadd_rn(lo, hi);
+            aabb[6 * i + a] = lo;
+            aabb[6 * i + 3 + a] = hi;
+            c2[3 * i + a] = c;
+            mn[a] = c;
+            mx[a] = c;
+        }
+    }
+    for (int a = 0; a < 3; ++a) { smin[a][tid] = mn[a]; smax[a][tid] = mx[a]; }
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][tid] = fmin_sel(smin[a][tid], smin[a][tid + s]);
+                smax[a][tid] = fmax_sel(smax[a][tid], smax[a][tid + s]);
+            }
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int a = 0; a < 3; ++a) { blk[6 * blockIdx.x + a] = smin[a][0]; blk[6 * blockIdx.x + 3 + a] = smax[a][0]; }
+}
+
+__global__ void k_minmax_final(const float* __restrict__ blk, int nblk, float* __restrict__ out) {
+    __shared__ float smin[3][256], smax[3][256];
+    const int tid = threadIdx.x;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = tid; b < nblk; b += 256)
+        for (int a = 0; a < 3; ++a) { mn[a] = fmin_sel(mn[a], blk[6 * b + a]); mx[a] = fmax_sel(mx[a], blk[6 * b + 3 + a]); }
+    for (int a = 0; a < 3; ++a) { smin[a][tid] = mn[a]; smax[a][tid] = mx[a]; }
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][tid] = fmin_sel(smin[a][tid], smin[a][tid + s]);
+                smax[a][tid] = fmax_sel(smax[a][tid], smax[a][tid + s]);
+            }
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int a = 0; a < 3; ++a) { out[a] = smin[a][0]; out[3 + a] = smax[a][0]; }
+}
+
+// spread the low 21 bits of v to every third bit of a 64-bit word
+__device__ __forceinline__ uint64_t spread21(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+
+// q_a = min(trunc((c2_a - cmin_a) * (2097151 / (cmax_a - cmin_a))), 2097151)
+// key = interleave(qx, qy, qz) with x on bit 3i+2, y on 3i+1, z on 3i.
+__global__ void k_morton(const float* __restrict__ c2, const float* __restrict__ bounds, int64_t nt,
+                         uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        const float e = __fsub_rn(bounds[3 + a], bounds[a]);
+        const float scale = (e > 0.0f) ? __fdiv_rn(2097151.0f, e) : 0.0f;
+        const float f = __fmul_rn(__fsub_rn(c2[3 * i + a], bounds[a]), scale);
+        const uint32_t u = __float2uint_rz(f);
+        q[a] = u > 2097151u ? 2097151u : u;
+    }
+    keys[i] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+    vals[i] = (int32_t)i;
+}
+
+// ---------------- stable LSD radix sort of (key, value), 8-bit digits ----------------
+__global__ void k_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
+                       int nblk) {
+    __shared__ uint32_t s_h[256];
+    const int tid = threadIdx.x;
+    s_h[tid] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        const int64_t idx = base + (int64_t)j * SORT_THREADS + tid;
+        if (idx < n) atomicAdd(&s_h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)tid * nblk + blockIdx.x] = s_h[tid];
+}
+
+// exclusive scan of hist[0 .. total) in place (one block of 1024 threads)
+__global__ void k_scan(uint32_t* __restrict__ hist, int64_t total) {
+    __shared__ uint32_t s[1024];
+    const int tid = threadIdx.x;
+    const int64_t len = (total + 1023) / 1024;
+    const int64_t b = (int64_t)tid * len, e = min(total, b + len);
+    uint32_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += hist[i];
+    s[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t v = (tid >= off) ? s[tid - off] : 0u;
+        __syncthreads();
+        s[tid] += v;
+        __syncthreads();
+    }
+    uint32_t run = s[tid] - sum;  // exclusive prefix of this chunk
+    for (int64_t i = b; i < e; ++i) {
+        uint32_t v = hist[i];
+        hist[i] = run;
+        run += v;
+    }
+}
+
+__global__ void k_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n,
+                          int shift, const uint32_t* __restrict__ offs, int nblk, uint64_t* __restrict__ kout,
+                          int32_t* __restrict__ vout) {
+    __shared__ uint32_t s_wc[SORT_WARPS][256];
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_base[256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_run[tid] = 0;
+    s_base[tid] = offs[(int64_t)tid * nblk + blockIdx.x];
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        for (int j = tid; j < SORT_WARPS * 256; j += SORT_THREADS) (&s_wc[0][0])[j] = 0;
+        __syncthreads();
+        const int64_t idx = base + (int64_t)r * SORT_THREADS + tid;
+        const bool valid = idx < n;
+        uint64_t key = 0;
+        int32_t val = 0;
+        uint32_t d = 256;
+        if (valid) {
+            key = kin[idx];
+            val = vin[idx];
+            d = (uint32_t)((key >> shift) & 255u);
+        }
+        const unsigned peers = __match_any_sync(FULL_MASK, d);
+        const int rank = __popc(peers & lt);
+        if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t off = s_run[d];
+            for (int w = 0; w < warp; ++w) off += s_wc[w][d];
+            const uint32_t dst = s_base[d] + off + rank;
+            kout[dst] = key;
+            vout[dst] = val;
+        }
+        __syncthreads();
+        uint32_t tot = 0;
+        for (int w = 0; w < SORT_WARPS; ++w) tot += s_wc[w][tid];
+        s_run[tid] += tot;
+        __syncthreads();
+    }
+}
+
+// ---------------- Karras hierarchy ----------------
+__device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    const uint64_t a = k[i], b = k[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+__global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, float4* __restrict__ nodes,
+                         int32_t* __restrict__ parent_leaf, int32_t* __restrict__ parent_node) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) > 0 ? 1 : -1;
+    const int dmin = delta(k, n, i, i - d);
+    int64_t lmax = 2;
+    while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = delta(k, n, i, j);
+    int64_t s = 0;
+    int64_t div = 2;
+    int64_t t = (l + div - 1) / div;
+    while (true) {
+        if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+        div <<= 1;
+        t = (l + div - 1) / div;
+    }
+    const int64_t g = i + s * d + (d < 0 ? -1 : 0);
+    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    const int32_t c0 = (lo == g) ? ~(int32_t)g : (int32_t)g;
+    const int32_t c1 = (hi == g + 1) ? ~(int32_t)(g + 1) : (int32_t)(g + 1);
+    nodes[4 * i + 3] = make_float4(__int_as_float(c0), __int_as_float(c1), 0.0f, 0.0f);
+    if (c0 < 0) parent_leaf[g] = (int32_t)i; else parent_node[g] = (int32_t)i;
+    if (c1 < 0) parent_leaf[g + 1] = (int32_t)i; else parent_node[g + 1] = (int32_t)i;
+}
+
+// Bottom-up refit: each leaf writes its triangle box into its parent's
+// child slot; the second child to arrive at a node (atomic visit counter)
+// forms the node's box and carries on upward.  No thread ever waits.
+__global__ void k_refit(const float* __restrict__ tri_aabb, const int32_t* __restrict__ order, int64_t n,
+                        const int32_t* __restrict__ parent_leaf, const int32_t* __restrict__ parent_node,
+                        float4* nodes, int32_t* visit) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float box[6];
+    const int32_t tri = order[p];
+    for (int a = 0; a < 6; ++a) box[a] = tri_aabb[6 * (int64_t)tri + a];
+    int32_t me = ~(int32_t)p;
+    int32_t node = parent_leaf[p];
+    float* nf = reinterpret_cast<float*>(nodes);
+    // the path to the root of a valid tree is shorter than n nodes
+    for (int64_t step = 0; step < n; ++step) {
+        const float4 c = __ldcg(&nodes[4 * (int64_t)node + 3]);
+        const int slot = (__float_as_int(c.x) == me) ? 0 : 1;
+        float* dst = nf + 16 * (int64_t)node + 6 * slot;
+        for (int a = 0; a < 6; ++a) __stcg(dst + a, box[a]);
+        __threadfence();
+        if (atomicAdd(&visit[node], 1) == 0) return;
+        __threadfence();
+        const float* src = nf + 16 * (int64_t)node;
+        float lb[6], rb[6];
+        for (int a = 0; a < 6; ++a) { lb[a] = __ldcg(src + a); rb[a] = __ldcg(src + 6 + a); }
+        for (int a = 0; a < 3; ++a) {
+            box[a] = fmin_sel(lb[a], rb[a]);
+            box[3 + a] = fmax_sel(lb[3 + a], rb[3 + a]);
+        }
+        if (node == 0) return;
+        me = node;
+        node = parent_node[node];
+    }
+}
+
+__global__ void k_trirec(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                         const int32_t* __restrict__ tri_mat, const int32_t* __restrict__ order, int64_t n,
+                         float4* __restrict__ rec) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t t = order[p];
+    const float* a = verts + 3 * (int64_t)tris[3 * (int64_t)t];
+    const float* b = verts + 3 * (int64_t)tris[3 * (int64_t)t + 1];
+    const float* c = verts + 3 * (int64_t)tris[3 * (int64_t)t + 2];
+    rec[3 * p + 0] = make_float4(a[0], a[1], a[2], b[0]);
+    rec[3 * p + 1] = make_float4(b[1], b[2], c[0], c[1]);
+    rec[3 * p + 2] = make_float4(c[2], __int_as_float(tri_mat[t]), __int_as_float(t), 0.0f);
+}
+
+inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t nt, int64_t nv, int32_t nm,
+                          int32_t* flag_dev, cudaStream_t s) {
+    if (nt <= 0) return cudaSuccess;
+    k_check_indices<<<nb(nt, 256), 256, 0, s>>>(tris, tri_mat, nt, nv, nm, flag_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s) {
+    const int64_t n = B.nt;
+    if (n <= 0) return cudaSuccess;
+    cudaError_t err;
+    const int nblk_a = (int)nb(n, 256);
+    const int nblk_s = (int)nb(n, SORT_TILE);
+    // scratch: aabb [6n] f32, c2 [3n] f32, blk [6 nblk_a] f32, bounds [6] f32,
+    // keys2 [n] u64, vals [2n] i32, hist [256 nblk_s] u32, parents [2n] i32, visit [n] i32
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_aabb = take(sizeof(float) * 6 * n), o_c2 = take(sizeof(float) * 3 * n),
+                 o_blk = take(sizeof(float) * 6 * nblk_a), o_bnd = take(sizeof(float) * 6),
+                 o_k2 = take(sizeof(uint64_t) * n), o_v1 = take(sizeof(int32_t) * n),
+                 o_v2 = take(sizeof(int32_t) * n), o_h = take(sizeof(uint32_t) * 256 * (size_t)nblk_s),
+                 o_pl = take(sizeof(int32_t) * n), o_pn = take(sizeof(int32_t) * n),
+                 o_vis = take(sizeof(int32_t) * n);
+    char* base = nullptr;
+    if ((err = cudaMallocAsync((void**)&base, off, s)) != cudaSuccess) return err;
+    float* aabb = (float*)(base + o_aabb);
+    float* c2 = (float*)(base + o_c2);
+    float* blk = (float*)(base + o_blk);
+    float* bnd = (float*)(base + o_bnd);
+    uint64_t* k1 = B.keys_sorted;
+    uint64_t* k2 = (uint64_t*)(base + o_k2);
+    int32_t* v1 = (int32_t*)(base + o_v1);
+    int32_t* v2 = (int32_t*)(base + o_v2);
+    uint32_t* hist = (uint32_t*)(base + o_h);
+    int32_t* pl = (int32_t*)(base + o_pl);
+    int32_t* pn = (int32_t*)(base + o_pn);
+    int32_t* vis = (int32_t*)(base + o_vis);
+
+    k_tri_aabb<<<nblk_a, 256, 0, s>>>(B.verts, B.tris, n, aabb, c2, blk);
+    k_minmax_final<<<1, 256, 0, s>>>(blk, nblk_a, bnd);
+    k_morton<<<nblk_a, 256, 0, s>>>(c2, bnd, n, k1, v1);
+    // 8 passes; after an even number of passes the result is back in (k1, v1)
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        uint64_t* kin = (pass & 1) ? k2 : k1;
+        uint64_t* kout = (pass & 1) ? k1 : k2;
+        int32_t* vin = (pass & 1) ? v2 : v1;
+        int32_t* vout = (pass & 1) ? v1 : v2;
+        k_hist<<<nblk_s, SORT_THREADS, 0, s>>>(kin, n, shift, hist, nblk_s);
+        k_scan<<<1, 1024, 0, s>>>(hist, (int64_t)256 * nblk_s);
+        k_scatter<<<nblk_s, SORT_THREADS, 0, s>>>(kin, vin, n, shift, hist, nblk_s, kout, vout);
+    }
+    if ((err = cudaMemcpyAsync(B.order, v1, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return err;
+    if (n >= 2) {
+        k_karras<<<nb(n - 1, 256), 256, 0, s>>>(k1, n, B.nodes, pl, pn);
+        if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * n, s)) != cudaSuccess) return err;
+        k_refit<<<nb(n, 256), 256, 0, s>>>(aabb, B.order, n, pl, pn, B.nodes, vis);
+    }
+    k_trirec<<<nb(n, 256), 256, 0, s>>>(B.verts, B.tris, B.tri_mat, B.order, n, B.trirec);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    return cudaFreeAsync(base, s);
+}
+
+}  // namespace rmsbr

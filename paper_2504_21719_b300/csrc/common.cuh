@@ -1,0 +1,101 @@
+// Device-side data layouts shared by the kernels of the SBR radio-map library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rmsbr.h"
+
+namespace rmsbr {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr int MAX_BLOCK = 256;        // threads per block of the tracer (at most)
+constexpr int STACK_SIZE = 64;        // BVH traversal stack entries per ray
+constexpr int32_t NO_CELL = -32768;
+
+// Per-material constants at the trace frequency.  eta = eps_r - j sigma /
+// (eps0 omega) for the fields and for the (detached) sampling probabilities;
+// k0d = 2 pi d / lambda0 split into two floats (hi + lo) so the slab phase
+// keeps FP64 accuracy in its constant.
+struct MatDev {
+    float eta_re, eta_im;
+    float seta_re, seta_im;
+    float k0d_hi, k0d_lo;
+    int32_t slab;
+    int32_t pad;
+};
+
+// Per-transmitter constants.
+struct TxDev {
+    float pos[3];
+    float R[9];                  // antenna orientation, row-major
+    int32_t pattern, pol;
+    float dep_scale;             // (4 pi / (N Delta^2)) (lambda0 / 4 pi)^2
+    float pad;
+    unsigned long long N;        // lattice size
+    unsigned long long begin, stride, count;
+    unsigned long long work_begin;  // first work item of this transmitter
+    unsigned long long seed;
+    unsigned long long rec_begin;   // first debug record of this transmitter
+};
+
+// Scratch of one trace launch (zeroed before the launch).
+struct Scratch {
+    unsigned long long next;     // work-queue head
+    unsigned long long cnt[6];   // rays, segments, nodes, tris, deposits, escapes
+    unsigned long long seg_depth[RM_MAX_DEPTH + 1];
+    double pw[RM_MAX_DEPTH + 1], pw2[RM_MAX_DEPTH + 1], esc[RM_MAX_DEPTH + 1];
+    double grad[2 * RM_MAX_MATERIALS + 3 * RM_MAX_TX];
+    int32_t status;              // bit 0: stack overflow
+    int32_t pad;
+};
+
+struct TraceArgs {
+    const float4* nodes;         // [nt-1][4]
+    const float4* tris;          // [nt][3], leaf order
+    int32_t nt;
+    int32_t ntx, nm;
+    int32_t L;
+    uint32_t flags;
+    float x0, y0, zm, cell, inv_cell;
+    int32_t nx, ny;
+    float inv_eps0_omega;        // 1 / (eps0 omega): d eta / d sigma = -j / (eps0 omega)
+    int32_t same_sampling;
+    unsigned long long total;    // work items (sum of ray counts)
+    unsigned long long ncell;    // nx * ny
+    const MatDev* mats;          // [nm]
+    const TxDev* tx;             // [ntx]
+    Scratch* scratch;
+    float* maps;                 // [ntx][ny][nx] (forward)
+    const float* dLdC;           // [ntx][ny][nx] (adjoint)
+    rm_segment_record* record;   // optional
+};
+
+// Host-side launchers (trace.cu)
+cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint,
+                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out);
+int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, int block);
+
+// BVH build (bvh.cu)
+struct BvhBuffers {
+    const float* verts;
+    const int32_t* tris;
+    const int32_t* tri_mat;
+    int64_t nt;
+    uint64_t* keys_sorted;   // [nt]
+    int32_t* order;          // [nt]
+    float4* nodes;           // [nt-1][4]
+    float4* trirec;          // [nt][3]
+};
+cudaError_t build_bvh(const BvhBuffers& b, cudaStream_t s);
+cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t nt, int64_t nv, int32_t nm,
+                          int32_t* flag_dev, cudaStream_t s);
+
+// loss (loss.cu)
+cudaError_t launch_db_mse(const float* maps, const float* target, int64_t n, float floor_lin,
+                          double* acc_dev, float* loss, float* dLdC, int64_t* valid, cudaStream_t s);
+cudaError_t launch_fill_record(rm_segment_record* rec, unsigned long long n, cudaStream_t s);
+cudaError_t launch_grad_out(const double* grad, int nm, int ntx, float* d_eps, float* d_sigma, float* d_tx,
+                            cudaStream_t s);
+
+}  // namespace rmsbr

@@ -1,0 +1,756 @@
+// Persistent SBR tracer (forward radio map and its adjoint) for sm_103a.
+//
+// One launch handles every transmitter of a call.  A global work counter
+// hands out work items w in [0, total); item w is ray i of transmitter t
+// (w = work_begin[t] + i), lattice direction n = begin + i * stride.  Each
+// thread owns one ray slot kept entirely in registers; whenever lanes of a
+// warp are free the warp refills them with ONE atomic on the counter
+// (warp-level compaction between bounces: a warp never idles while work is
+// left).  Per loop iteration every active lane traces one segment:
+//   1. closest hit through the LBVH (stack traversal, nearer child first,
+//      robust slab test, watertight ray-triangle test of Woop, Benthin &
+//      Wald, JCGT 2013);
+//   2. deposit at the plane crossing (Eq. radio-map-solver-ci-all-2-estimator),
+//      warp-aggregated by destination cell before the FP32 atomic;
+//   3. if l < L and the ray hit: Fresnel / slab coefficients (App. A.7),
+//      sampling of reflection vs refraction with q(R), q(T)
+//      (Eq. path-solver-used-dist-event with S = 0, q(D) = 0), field update
+//      with the TE/TM basis, new direction and origin.
+// The adjoint instantiation re-traces the identical rays and, instead of
+// writing the map, accumulates d(sum_i g_i C_i)/d(theta) by forward-mode
+// tangents of the field with respect to each material met on the path.
+//
+// This file is compiled with -fmad=false: every operation that steers a
+// discrete choice is rounded the same way in the forward and the adjoint
+// instantiations, so both take the same hits, decisions and cells.
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace rmsbr {
+namespace {
+
+// ------------------------------------------------------------------ complex
+struct cf {
+    float r, i;
+};
+__device__ __forceinline__ cf C(float r, float i = 0.0f) { return {r, i}; }
+__device__ __forceinline__ cf operator+(cf a, cf b) { return {a.r + b.r, a.i + b.i}; }
+__device__ __forceinline__ cf operator-(cf a, cf b) { return {a.r - b.r, a.i - b.i}; }
+__device__ __forceinline__ cf operator*(cf a, cf b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ cf operator*(cf a, float s) { return {a.r * s, a.i * s}; }
+__device__ __forceinline__ cf cdiv(cf a, cf b) {
+    const float inv = 1.0f / (b.r * b.r + b.i * b.i);
+    return {(a.r * b.r + a.i * b.i) * inv, (a.i * b.r - a.r * b.i) * inv};
+}
+__device__ __forceinline__ float cabs2(cf a) { return a.r * a.r + a.i * a.i; }
+// conj(a) * b
+__device__ __forceinline__ cf cjmul(cf a, cf b) { return {a.r * b.r + a.i * b.i, a.r * b.i - a.i * b.r}; }
+// principal square root: sqrt((|z|+x)/2) + j sgn(y) sqrt((|z|-x)/2), with the
+// smaller part formed as y / (2 * larger) (Kahan 1987) to avoid cancellation
+__device__ __forceinline__ cf csqrt_p(cf z) {
+    if (z.r == 0.0f && z.i == 0.0f) return {0.0f, 0.0f};
+    const float m = hypotf(z.r, z.i);
+    if (z.r >= 0.0f) {
+        const float a = sqrtf(0.5f * (m + z.r));
+        return {a, z.i / (2.0f * a)};
+    }
+    const float b = sqrtf(0.5f * (m - z.r));
+    return {fabsf(z.i) / (2.0f * b), copysignf(b, z.i)};
+}
+// exp(-j w) = exp(Im w) (cos Re w - j sin Re w)
+__device__ __forceinline__ cf cexp_mj(cf w) {
+    float s, c;
+    sincosf(w.r, &s, &c);
+    const float e = expf(w.i);
+    return {e * c, -e * s};
+}
+
+struct f3 {
+    float x, y, z;
+};
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 operator*(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ f3 normalize(f3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ float sel(f3 v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
+// e^T E for a real unit vector e and a complex 3-vector E
+__device__ __forceinline__ cf edot(f3 e, const cf* E) { return E[0] * e.x + E[1] * e.y + E[2] * e.z; }
+
+// ------------------------------------------------------------------ RNG
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+// uniform in [0, 1) on a 2^-24 grid: exact in FP32
+__device__ __forceinline__ float rng_u(unsigned long long seed, unsigned long long n, int l) {
+    const unsigned long long h = splitmix64(seed ^ splitmix64((n << 4) | (unsigned long long)(l & 15)));
+    return (float)(unsigned)(h >> 40) * 0x1p-24f;
+}
+
+// ------------------------------------------------------------------ Fresnel
+struct Coef {
+    cf rp, rl, tp, tl;  // r_perp, r_par, t_perp, t_par
+};
+// Incidence from vacuum (Eq. fresnel_vac); for a slab, the single-layer
+// coefficients of Eqs. fresnel_slab / q_fresnel_slab with r' the
+// half-space r of the same polarisation.  A half-space has t = 0.
+__device__ __forceinline__ Coef fresnel(cf eta, float cos1, float k0d_hi, float k0d_lo, bool slab, cf* s_out) {
+    const float sin2 = (1.0f - cos1) * (1.0f + cos1);
+    const cf s = csqrt_p(C(eta.r - sin2, eta.i));
+    const cf c = C(cos1);
+    const cf ec = eta * cos1;
+    Coef o;
+    o.rp = cdiv(c - s, c + s);
+    o.rl = cdiv(ec - s, ec + s);
+    if (s_out) *s_out = s;
+    if (!slab) {
+        o.tp = C(0.0f);
+        o.tl = C(0.0f);
+        return o;
+    }
+    const cf q = C(k0d_hi * s.r + k0d_lo * s.r, k0d_hi * s.i + k0d_lo * s.i);
+    const cf e1 = cexp_mj(q);
+    const cf e2 = e1 * e1;
+    const cf one = C(1.0f);
+    const cf rp2 = o.rp * o.rp, rl2 = o.rl * o.rl;
+    const cf dp = one - rp2 * e2, dl = one - rl2 * e2;
+    const cf rp = cdiv(o.rp * (one - e2), dp);
+    const cf rl = cdiv(o.rl * (one - e2), dl);
+    o.tp = cdiv((one - rp2) * e1, dp);
+    o.tl = cdiv((one - rl2) * e1, dl);
+    o.rp = rp;
+    o.rl = rl;
+    return o;
+}
+
+// d/d eta of the chosen pair of coefficients (hand-derived; the oracle checks
+// them through its dual numbers).  Half-space: r_perp = (c - s)/(c + s),
+// r_par = (eta c - s)/(eta c + s), s = sqrt(eta - sin^2), ds/deta = 1/(2s).
+// Slab: r = r'(1 - x)/(1 - r'^2 x), t = (1 - r'^2) y / (1 - r'^2 x),
+// y = exp(-j k0d s), x = y^2.
+__device__ __forceinline__ void fresnel_deta(cf eta, float cos1, float k0d, bool slab, int dec, cf* dperp,
+                                             cf* dpar) {
+    const float sin2 = (1.0f - cos1) * (1.0f + cos1);
+    const cf s = csqrt_p(C(eta.r - sin2, eta.i));
+    const cf c = C(cos1);
+    const cf ec = eta * cos1;
+    const cf one = C(1.0f);
+    const cf cps = c + s, ecs = ec + s;
+    const cf rp = cdiv(c - s, cps), rl = cdiv(ec - s, ecs);
+    // d r_perp / d eta = -c / (s (c + s)^2);  d r_par / d eta = c (2 s^2 - eta) / (s (eta c + s)^2)
+    const cf drp = cdiv(C(-cos1), s * cps * cps);
+    const cf drl = cdiv((s * s * 2.0f - eta) * cos1, s * ecs * ecs);
+    if (!slab) {
+        *dperp = drp;
+        *dpar = drl;
+        return;
+    }
+    const cf y = cexp_mj(s * k0d);
+    const cf x = y * y;
+    const cf dq = cdiv(C(k0d * 0.5f), s);          // dq/deta = k0d / (2 s)
+    const cf dy = y * C(0.0f, -1.0f) * dq;          // dy/deta = -j y dq
+    const cf dx = y * dy * 2.0f;
+    cf out[2];
+    for (int p = 0; p < 2; ++p) {
+        const cf r1 = p == 0 ? rp : rl;
+        const cf dr1 = p == 0 ? drp : drl;
+        const cf r2 = r1 * r1;
+        const cf D = one - r2 * x;
+        const cf D2 = D * D;
+        if (dec == 0) {
+            // dr/dr' = (1 - x)(1 + r'^2 x) / D^2 ; dr/dx = r'(r'^2 - 1) / D^2
+            const cf a = cdiv((one - x) * (one + r2 * x), D2);
+            const cf b = cdiv(r1 * (r2 - one), D2);
+            out[p] = a * dr1 + b * dx;
+        } else {
+            // dt/dr' = -2 r' y (1 - x) / D^2 ; dt/dy = (1 - r'^2)(1 + r'^2 x) / D^2
+            const cf a = cdiv(r1 * y * (one - x) * (-2.0f), D2);
+            const cf b = cdiv((one - r2) * (one + r2 * x), D2);
+            out[p] = a * dr1 + b * dy;
+        }
+    }
+    *dperp = out[0];
+    *dpar = out[1];
+}
+
+// ------------------------------------------------------------------ traversal
+struct Ray {
+    float ox, oy, oz, kx, ky, kz;
+};
+
+__device__ __forceinline__ bool box_hit(float lx, float ly, float lz, float hx, float hy, float hz, const Ray& r,
+                                        float ix, float iy, float iz, float tmax, float& tnear) {
+    const float t0x = (lx - r.ox) * ix, t1x = (hx - r.ox) * ix;
+    const float t0y = (ly - r.oy) * iy, t1y = (hy - r.oy) * iy;
+    const float t0z = (lz - r.oz) * iz, t1z = (hz - r.oz) * iz;
+    const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+    // robust slab test: widen the far distance by 1 + 2 gamma_3 (Ize, JCGT 2013)
+    tf = tf * 1.0000004f;
+    tnear = tn;
+    return tn <= tf;
+}
+
+struct Hit {
+    int slot;   // leaf position, -1 = none
+    int prim;   // original triangle index
+    float t;
+};
+
+// Closest hit along the ray, excluding leaf `exclude`.  Equal distances go to
+// the smaller original triangle index.
+__device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, int nt,
+                                           const Ray& r, int exclude, unsigned& c_nodes, unsigned& c_tris,
+                                           bool& overflow) {
+    Hit h{-1, 0x7fffffff, INFINITY};
+    if (nt <= 0) return h;
+    const float ooeps = 0x1p-80f;
+    const float ix = 1.0f / (fabsf(r.kx) > ooeps ? r.kx : copysignf(ooeps, r.kx));
+    const float iy = 1.0f / (fabsf(r.ky) > ooeps ? r.ky : copysignf(ooeps, r.ky));
+    const float iz = 1.0f / (fabsf(r.kz) > ooeps ? r.kz : copysignf(ooeps, r.kz));
+    // watertight test set-up: kz = dominant axis, (kx, ky) keep the winding
+    const float ax = fabsf(r.kx), ay = fabsf(r.ky), az = fabsf(r.kz);
+    int kzi = (ay > ax) ? 1 : 0;
+    if (az > fmaxf(ax, ay)) kzi = 2;
+    int kxi = kzi == 2 ? 0 : kzi + 1;
+    int kyi = kxi == 2 ? 0 : kxi + 1;
+    const f3 k{r.kx, r.ky, r.kz};
+    const float dz = sel(k, kzi);
+    if (dz < 0.0f) {
+        const int t = kxi;
+        kxi = kyi;
+        kyi = t;
+    }
+    const float Sx = sel(k, kxi) / dz, Sy = sel(k, kyi) / dz, Sz = 1.0f / dz;
+    const f3 o{r.ox, r.oy, r.oz};
+    const float opx = sel(o, kxi), opy = sel(o, kyi), opz = sel(o, kzi);
+
+    int stack[STACK_SIZE];
+    int sp = 0;
+    int cur = (nt == 1) ? ~0 : 0;
+    // a valid tree is visited at most once per node and leaf: 2 nt - 1 steps
+    long long budget = 2LL * nt + 8;
+    while (true) {
+        if (--budget < 0) {
+            overflow = true;
+            break;
+        }
+        if (cur >= 0) {
+            ++c_nodes;
+            const float4* nd = nodes + 4 * (size_t)cur;
+            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            float tn0, tn1;
+            const bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, ix, iy, iz, h.t, tn0);
+            const bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, ix, iy, iz, h.t, tn1);
+            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            if (h0 && h1) {
+                const bool first0 = tn0 <= tn1;
+                if (sp < STACK_SIZE) stack[sp++] = first0 ? c1 : c0;
+                else overflow = true;
+                cur = first0 ? c0 : c1;
+            } else if (h0) {
+                cur = c0;
+            } else if (h1) {
+                cur = c1;
+            } else {
+                if (sp == 0) break;
+                cur = stack[--sp];
+            }
+        } else {
+            const int slot = ~cur;
+            if (slot != exclude) {
+                ++c_tris;
+                const float4* tp = tris + 3 * (size_t)slot;
+                const float4 r0 = __ldg(tp), r1 = __ldg(tp + 1), r2 = __ldg(tp + 2);
+                const f3 va{r0.x, r0.y, r0.z}, vb{r0.w, r1.x, r1.y}, vc{r1.z, r1.w, r2.x};
+                const float Akx = sel(va, kxi) - opx, Aky = sel(va, kyi) - opy, Akz = sel(va, kzi) - opz;
+                const float Bkx = sel(vb, kxi) - opx, Bky = sel(vb, kyi) - opy, Bkz = sel(vb, kzi) - opz;
+                const float Ckx = sel(vc, kxi) - opx, Cky = sel(vc, kyi) - opy, Ckz = sel(vc, kzi) - opz;
+                const float Ax = Akx - Sx * Akz, Ay = Aky - Sy * Akz;
+                const float Bx = Bkx - Sx * Bkz, By = Bky - Sy * Bkz;
+                const float Cx = Ckx - Sx * Ckz, Cy = Cky - Sy * Ckz;
+                float U = Cx * By - Cy * Bx;
+                float V = Ax * Cy - Ay * Cx;
+                float W = Bx * Ay - By * Ax;
+                if (U == 0.0f || V == 0.0f || W == 0.0f) {
+                    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+                    V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+                    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+                }
+                const bool neg = (U < 0.0f || V < 0.0f || W < 0.0f);
+                const bool pos = (U > 0.0f || V > 0.0f || W > 0.0f);
+                float det = U + V + W;
+                if (!(neg && pos) && det != 0.0f) {
+                    float T = U * (Sz * Akz) + V * (Sz * Bkz) + W * (Sz * Ckz);
+                    if (det < 0.0f) {
+                        T = -T;
+                        det = -det;
+                    }
+                    if (T > 0.0f && !(T > h.t * det)) {
+                        const float t = T / det;
+                        const int prim = __float_as_int(r2.z);
+                        if (t < h.t || (t == h.t && prim < h.prim)) {
+                            h.t = t;
+                            h.slot = slot;
+                            h.prim = prim;
+                        }
+                    }
+                }
+            }
+            if (sp == 0) break;
+            cur = stack[--sp];
+        }
+    }
+    return h;
+}
+
+// ------------------------------------------------------------------ kernel
+constexpr int NGRAD = 2 * RM_MAX_MATERIALS + 3 * RM_MAX_TX;
+constexpr int MAXSLOT = RM_MAX_DEPTH;
+
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN>
+__global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
+    __shared__ MatDev s_mat[RM_MAX_MATERIALS];
+    __shared__ TxDev s_tx[RM_MAX_TX];
+    __shared__ float s_agg[MAX_BLOCK];
+    __shared__ float s_grad[ADJ ? NGRAD : 1];
+    __shared__ unsigned long long s_cnt[6];
+    __shared__ unsigned long long s_segd[DEBUG ? RM_MAX_DEPTH + 1 : 1];
+    __shared__ double s_pw[DEBUG ? 3 * (RM_MAX_DEPTH + 1) : 1];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        const int nmw = A.nm * (int)(sizeof(MatDev) / 4), ntw = A.ntx * (int)(sizeof(TxDev) / 4);
+        for (int i = tid; i < nmw; i += blockDim.x) reinterpret_cast<int*>(s_mat)[i] = reinterpret_cast<const int*>(A.mats)[i];
+        for (int i = tid; i < ntw; i += blockDim.x) reinterpret_cast<int*>(s_tx)[i] = reinterpret_cast<const int*>(A.tx)[i];
+        if (ADJ)
+            for (int i = tid; i < NGRAD; i += blockDim.x) s_grad[i] = 0.0f;
+        if (tid < 6) s_cnt[tid] = 0;
+        if (DEBUG) {
+            for (int i = tid; i < RM_MAX_DEPTH + 1; i += blockDim.x) s_segd[i] = 0;
+            for (int i = tid; i < 3 * (RM_MAX_DEPTH + 1); i += blockDim.x) s_pw[i] = 0.0;
+        }
+    }
+    __syncthreads();
+
+    const unsigned lt = (1u << lane) - 1u;
+    const bool stats = DEBUG && (A.flags & RM_STATS);
+    // ray state
+    bool active = false, exhausted = false;
+    Ray r{0, 0, 0, 0, 0, 1};
+    cf E[NPOL][3];
+    float inv_pr = 1.0f;
+    int depth = 0, prev = -1, txi = 0;
+    unsigned long long n = 0, isub = 0;
+    // adjoint state: tangents dE/d eta per material met on the path
+    cf Tg[ADJ ? MAXSLOT : 1][NPOL][3];
+    int Tm[ADJ ? MAXSLOT : 1];
+    int nslot = 0;
+    float J[(ADJ && BILIN) ? 9 : 1];  // d origin / d tx position, column-major
+    unsigned c_rays = 0, c_seg = 0, c_nodes = 0, c_tris = 0, c_dep = 0, c_esc = 0;
+    bool overflow = false;
+
+    while (true) {
+        // ---------------- refill free lanes (one atomic per warp) ----------------
+        if (!exhausted) {
+            const unsigned need = __ballot_sync(FULL_MASK, !active);
+            if (need) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(&A.scratch->next, (unsigned long long)__popc(need));
+                b = __shfl_sync(FULL_MASK, b, 0);
+                if (b + __popc(need) >= A.total) exhausted = true;
+                if (!active) {
+                    const unsigned long long w = b + __popc(need & lt);
+                    if (w < A.total) {
+                        // transmitter of item w (work_begin ascending)
+                        int lo = 0, hi = A.ntx - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_tx[mid].work_begin <= w) lo = mid; else hi = mid - 1;
+                        }
+                        txi = lo;
+                        const TxDev& T = s_tx[txi];
+                        isub = w - T.work_begin;
+                        n = T.begin + isub * T.stride;
+                        // Fibonacci lattice (Sec. 3.1.1): cos theta = 1 - 2n/(N-1),
+                        // sin theta = 2 sqrt(n (N-1-n)) / (N-1), phi = 2 pi frac(n (phi_g - 1))
+                        float ct, st, sp, cp;
+                        if (T.N <= 1ULL) {
+                            ct = 0.0f; st = 1.0f; sp = 0.0f; cp = -1.0f;
+                        } else {
+                            const unsigned long long Nm1 = T.N - 1ULL;
+                            const float inv = 1.0f / (float)Nm1;
+                            ct = (float)((long long)Nm1 - 2LL * (long long)n) * inv;
+                            st = 2.0f * sqrtf((float)n * (float)(Nm1 - n)) * inv;
+                            const unsigned long long f = n * 0x9E3779B97F4A7C16ULL;  // nearest integer to 2^64 (phi_g - 1)
+                            const float x = (float)(int)(unsigned)(f >> 32) * 0x1p-31f;  // phi / pi in [-1, 1)
+                            sincospif(x, &sp, &cp);
+                        }
+                        r.kx = st * cp; r.ky = st * sp; r.kz = ct;
+                        r.ox = T.pos[0]; r.oy = T.pos[1]; r.oz = T.pos[2];
+                        // antenna field R (C_theta theta' + C_phi phi') in the local angles (App. A.1)
+                        const float lx = T.R[0] * r.kx + T.R[3] * r.ky + T.R[6] * r.kz;
+                        const float ly = T.R[1] * r.kx + T.R[4] * r.ky + T.R[7] * r.kz;
+                        const float lz = T.R[2] * r.kx + T.R[5] * r.ky + T.R[8] * r.kz;
+                        const float sxy = sqrtf(lx * lx + ly * ly);
+                        float cph = 1.0f, sph = 0.0f;
+                        if (sxy > 0.0f) { cph = lx / sxy; sph = ly / sxy; }
+                        const float g = (T.pattern == 1) ? 1.2247448713915890f * sxy : 1.0f;
+                        const f3 th_l{lz * cph, lz * sph, -sxy}, ph_l{-sph, cph, 0.0f};
+                        for (int p = 0; p < NPOL; ++p) {
+                            const int pol = (NPOL == 2) ? p : T.pol;
+                            const f3 e = pol == 0 ? th_l : ph_l;
+                            E[p][0] = C(g * (T.R[0] * e.x + T.R[1] * e.y + T.R[2] * e.z));
+                            E[p][1] = C(g * (T.R[3] * e.x + T.R[4] * e.y + T.R[5] * e.z));
+                            E[p][2] = C(g * (T.R[6] * e.x + T.R[7] * e.y + T.R[8] * e.z));
+                        }
+                        inv_pr = 1.0f;
+                        depth = 0;
+                        prev = -1;
+                        active = true;
+                        ++c_rays;
+                        if (ADJ) {
+                            nslot = 0;
+                            if (BILIN) {
+                                for (int j = 0; j < 9; ++j) J[j] = (j % 4 == 0) ? 1.0f : 0.0f;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (__ballot_sync(FULL_MASK, active) == 0) break;
+
+        // ---------------- closest hit ----------------
+        Hit h{-1, 0x7fffffff, INFINITY};
+        if (active) {
+            h = closest_hit(A.nodes, A.tris, A.nt, r, prev, c_nodes, c_tris, overflow);
+            ++c_seg;
+            if (h.slot < 0) ++c_esc;
+        }
+        float e2 = 0.0f;
+        if (active)
+            for (int p = 0; p < NPOL; ++p) e2 += cabs2(E[p][0]) + cabs2(E[p][1]) + cabs2(E[p][2]);
+        if (DEBUG && active) atomicAdd(&s_segd[depth], 1ULL);
+        if (stats && active) {
+            const float pw = e2 * inv_pr;
+            atomicAdd(&s_pw[depth], (double)pw);
+            atomicAdd(&s_pw[RM_MAX_DEPTH + 1 + depth], (double)pw * (double)pw);
+            if (h.slot < 0) atomicAdd(&s_pw[2 * (RM_MAX_DEPTH + 1) + depth], (double)pw);
+        }
+
+        // ---------------- plane crossing ----------------
+        bool dep = false;
+        int ix = NO_CELL, iy = NO_CELL;
+        float fx = 0.0f, fy = 0.0f;
+        if (active && r.kz != 0.0f && (depth > 0 || (A.flags & RM_LOS))) {
+            const float tc = (A.zm - r.oz) / r.kz;
+            if (tc > 1e-9f && tc < h.t) {
+                const float cx = r.ox + tc * r.kx, cy = r.oy + tc * r.ky;
+                float ux = (cx - A.x0) * A.inv_cell, uy = (cy - A.y0) * A.inv_cell;
+                if (BILIN) {
+                    ux -= 0.5f;
+                    uy -= 0.5f;
+                    if (ux >= -1.0f && ux < (float)A.nx && uy >= -1.0f && uy < (float)A.ny) {
+                        const float flx = floorf(ux), fly = floorf(uy);
+                        ix = (int)flx; iy = (int)fly;
+                        fx = ux - flx; fy = uy - fly;
+                        dep = true;
+                    }
+                } else if (ux >= 0.0f && ux < (float)A.nx && uy >= 0.0f && uy < (float)A.ny) {
+                    ix = (int)ux; iy = (int)uy;
+                    dep = true;
+                }
+            }
+        }
+        rm_segment_record* rec = nullptr;
+        if (DEBUG && active && A.record) {
+            rec = A.record + s_tx[txi].rec_begin + isub * (unsigned long long)(A.L + 1) + depth;
+            rec->prim = h.slot >= 0 ? h.prim : -1;
+            rec->ix = ix;
+            rec->iy = iy;
+            rec->decision = -1;
+        }
+        const float value = dep ? s_tx[txi].dep_scale * e2 * inv_pr / fabsf(r.kz) : 0.0f;
+        if (dep) ++c_dep;
+        const unsigned long long mbase = (unsigned long long)txi * A.ncell;
+
+        if (!ADJ) {
+            // warp-aggregated FP32 atomics: lanes that hit the same cell add
+            // their values first, then one lane issues the atomic
+            const int ncorner = BILIN ? 4 : 1;
+            for (int cn = 0; cn < ncorner; ++cn) {
+                float v = value;
+                unsigned long long key = ~0ULL;
+                if (dep) {
+                    int cxi = ix, cyi = iy;
+                    if (BILIN) {
+                        const int a = cn & 1, b = cn >> 1;
+                        cxi += a; cyi += b;
+                        v *= (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy);
+                        if (cxi >= 0 && cxi < A.nx && cyi >= 0 && cyi < A.ny)
+                            key = mbase + (unsigned long long)cyi * A.nx + cxi;
+                    } else {
+                        key = mbase + (unsigned long long)cyi * A.nx + cxi;
+                    }
+                }
+                const unsigned peers = __match_any_sync(FULL_MASK, key);
+                if (key != ~0ULL) {
+                    if (__popc(peers) == 1) {
+                        atomicAdd(A.maps + key, v);
+                    } else {
+                        s_agg[tid] = v;
+                        __syncwarp(peers);
+                        if (lane == __ffs(peers) - 1) {
+                            float sum = 0.0f;
+                            for (unsigned m = peers; m; m &= m - 1) sum += s_agg[(warp << 5) + __ffs(m) - 1];
+                            atomicAdd(A.maps + key, sum);
+                        }
+                        __syncwarp(peers);
+                    }
+                }
+            }
+        } else if (dep) {
+            // adjoint: gather g = dL/dC at the deposit (and its spatial derivative)
+            float G = 0.0f, Gx = 0.0f, Gy = 0.0f;
+            if (BILIN) {
+                for (int cn = 0; cn < 4; ++cn) {
+                    const int a = cn & 1, b = cn >> 1;
+                    const int cxi = ix + a, cyi = iy + b;
+                    if (cxi < 0 || cxi >= A.nx || cyi < 0 || cyi >= A.ny) continue;
+                    const float g = __ldg(A.dLdC + mbase + (unsigned long long)cyi * A.nx + cxi);
+                    const float wx = a ? fx : 1.0f - fx, wy = b ? fy : 1.0f - fy;
+                    G += g * wx * wy;
+                    Gx += g * (a ? 1.0f : -1.0f) * wy;
+                    Gy += g * wx * (b ? 1.0f : -1.0f);
+                }
+                Gx *= A.inv_cell;
+                Gy *= A.inv_cell;
+            } else {
+                G = __ldg(A.dLdC + mbase + (unsigned long long)iy * A.nx + ix);
+            }
+            const float sc = s_tx[txi].dep_scale * inv_pr / fabsf(r.kz);
+            if (G != 0.0f) {
+                for (int s = 0; s < nslot; ++s) {
+                    cf z = C(0.0f);
+                    for (int p = 0; p < NPOL; ++p)
+                        for (int a = 0; a < 3; ++a) z = z + cjmul(E[p][a], Tg[s][p][a]);
+                    // d|E|^2/d eps_r = 2 Re(E^H T); d|E|^2/d sigma = 2 Re(E^H T (-j/(eps0 w))) = 2 Im(E^H T)/(eps0 w)
+                    atomicAdd(&s_grad[Tm[s]], 2.0f * sc * G * z.r);
+                    atomicAdd(&s_grad[RM_MAX_MATERIALS + Tm[s]], 2.0f * sc * G * z.i * A.inv_eps0_omega);
+                }
+            }
+            if (BILIN && (Gx != 0.0f || Gy != 0.0f)) {
+                // crossing x_c = o + t_c k with t_c = (z_M - o_z)/k_z: dx_c/do = I - k e_z^T / k_z
+                const float ax = r.kx / r.kz, ay = r.ky / r.kz;
+                const float v = sc * e2;
+                for (int c = 0; c < 3; ++c) {
+                    const float dx = J[3 * c + 0] - ax * J[3 * c + 2];
+                    const float dy = J[3 * c + 1] - ay * J[3 * c + 2];
+                    atomicAdd(&s_grad[2 * RM_MAX_MATERIALS + 3 * txi + c], v * (Gx * dx + Gy * dy));
+                }
+            }
+        }
+
+        // ---------------- termination / interaction ----------------
+        if (active) {
+            if (h.slot < 0 || depth >= A.L) {
+                active = false;
+            } else {
+                const float4* tp = A.tris + 3 * (size_t)h.slot;
+                const float4 q0 = __ldg(tp), q1 = __ldg(tp + 1), q2 = __ldg(tp + 2);
+                const f3 va{q0.x, q0.y, q0.z}, vb{q0.w, q1.x, q1.y}, vc{q1.z, q1.w, q2.x};
+                const int mat = __float_as_int(q2.y);
+                f3 nrm = normalize(cross(vb - va, vc - va));
+                const f3 k{r.kx, r.ky, r.kz};
+                if (dot(k, nrm) > 0.0f) nrm = nrm * -1.0f;  // oriented towards the incident side
+                const float cos1 = fminf(1.0f, fmaxf(0.0f, -dot(k, nrm)));
+                const MatDev M = s_mat[mat];
+                const cf eta = C(M.eta_re, M.eta_im);
+                const Coef co = fresnel(eta, cos1, M.k0d_hi, M.k0d_lo, M.slab != 0, nullptr);
+                float wR, wT;
+                if (A.same_sampling) {
+                    wR = cabs2(co.rp) + cabs2(co.rl);
+                    wT = cabs2(co.tp) + cabs2(co.tl);
+                } else {
+                    const Coef cs = fresnel(C(M.seta_re, M.seta_im), cos1, M.k0d_hi, M.k0d_lo, M.slab != 0, nullptr);
+                    wR = cabs2(cs.rp) + cabs2(cs.rl);
+                    wT = cabs2(cs.tp) + cabs2(cs.tl);
+                }
+                if (!(A.flags & RM_REFLECT)) wR = 0.0f;
+                if (!(A.flags & RM_REFRACT)) wT = 0.0f;
+                const float wsum = wR + wT;
+                if (!(wsum > 0.0f)) {
+                    active = false;
+                } else {
+                    const float qR = wR / wsum;
+                    const float u = rng_u(s_tx[txi].seed, n, depth);
+                    const int dec = (u < qR) ? 0 : 1;
+                    if (rec) rec->decision = dec;
+                    inv_pr = inv_pr * (wsum / (dec == 0 ? wR : wT));
+                    // TE/TM basis (Eqs. fresnel_in_vectors, fresnel_out_vectors)
+                    f3 ep = cross(k, nrm);
+                    const float len = sqrtf(dot(ep, ep));
+                    if (len > 1e-6f) {
+                        ep = ep * (1.0f / len);
+                    } else {
+                        const f3 axv = fabsf(k.x) < 0.5f ? f3{1.0f, 0.0f, 0.0f} : f3{0.0f, 1.0f, 0.0f};
+                        ep = normalize(cross(k, axv));
+                    }
+                    const f3 epi = cross(ep, k);
+                    f3 ko, epo;
+                    cf cpe, cpa;
+                    if (dec == 0) {
+                        ko = normalize(k - nrm * (2.0f * dot(k, nrm)));
+                        epo = normalize(cross(ep, ko));
+                        cpe = co.rp; cpa = co.rl;
+                    } else {
+                        ko = k;  // thin slab: no deflection (Sec. 2.3)
+                        epo = epi;
+                        cpe = co.tp; cpa = co.tl;
+                    }
+                    if (ADJ) {
+                        // existing tangents see the same interaction matrix
+                        for (int s = 0; s < nslot; ++s)
+                            for (int p = 0; p < NPOL; ++p) {
+                                const cf a = edot(ep, Tg[s][p]), b = edot(epi, Tg[s][p]);
+                                const cf ca = cpe * a, cb = cpa * b;
+                                Tg[s][p][0] = ca * ep.x + cb * epo.x;
+                                Tg[s][p][1] = ca * ep.y + cb * epo.y;
+                                Tg[s][p][2] = ca * ep.z + cb * epo.z;
+                            }
+                        // new tangent of this interaction, merged per material
+                        cf dpe, dpa;
+                        fresnel_deta(eta, cos1, M.k0d_hi + M.k0d_lo, M.slab != 0, dec, &dpe, &dpa);
+                        int s = 0;
+                        while (s < nslot && Tm[s] != mat) ++s;
+                        if (s == nslot) {
+                            if (nslot < MAXSLOT) {
+                                Tm[s] = mat;
+                                for (int p = 0; p < NPOL; ++p)
+                                    for (int a = 0; a < 3; ++a) Tg[s][p][a] = C(0.0f);
+                                ++nslot;
+                            } else {
+                                s = -1;
+                                overflow = true;
+                            }
+                        }
+                        if (s >= 0)
+                            for (int p = 0; p < NPOL; ++p) {
+                                const cf a = edot(ep, E[p]), b = edot(epi, E[p]);
+                                const cf ca = dpe * a, cb = dpa * b;
+                                Tg[s][p][0] = Tg[s][p][0] + (ca * ep.x + cb * epo.x);
+                                Tg[s][p][1] = Tg[s][p][1] + (ca * ep.y + cb * epo.y);
+                                Tg[s][p][2] = Tg[s][p][2] + (ca * ep.z + cb * epo.z);
+                            }
+                        if (BILIN) {
+                            // hit point on the plane of the triangle: dp/do = I - k n^T / (n . k)
+                            const float inv_nk = 1.0f / dot(nrm, k);
+                            for (int c = 0; c < 3; ++c) {
+                                const float nj = (nrm.x * J[3 * c] + nrm.y * J[3 * c + 1] + nrm.z * J[3 * c + 2]) * inv_nk;
+                                J[3 * c + 0] -= k.x * nj;
+                                J[3 * c + 1] -= k.y * nj;
+                                J[3 * c + 2] -= k.z * nj;
+                            }
+                        }
+                    }
+                    for (int p = 0; p < NPOL; ++p) {
+                        const cf a = edot(ep, E[p]), b = edot(epi, E[p]);
+                        const cf ca = cpe * a, cb = cpa * b;
+                        E[p][0] = ca * ep.x + cb * epo.x;
+                        E[p][1] = ca * ep.y + cb * epo.y;
+                        E[p][2] = ca * ep.z + cb * epo.z;
+                    }
+                    // new origin: hit point pushed 2^-16 max(1, |p|_inf) off the surface
+                    const float px = r.ox + h.t * r.kx, py = r.oy + h.t * r.ky, pz = r.oz + h.t * r.kz;
+                    const float pm = fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz)));
+                    const float delta = fmaxf(1.0f, pm) * 0x1p-16f;
+                    const float sgn = dec == 0 ? delta : -delta;
+                    r.ox = px + sgn * nrm.x;
+                    r.oy = py + sgn * nrm.y;
+                    r.oz = pz + sgn * nrm.z;
+                    r.kx = ko.x; r.ky = ko.y; r.kz = ko.z;
+                    prev = h.slot;
+                    ++depth;
+                }
+            }
+        }
+    }
+
+    // ---------------- flush counters ----------------
+    if (overflow) atomicOr(&A.scratch->status, 1);
+    unsigned v[6] = {c_rays, c_seg, c_nodes, c_tris, c_dep, c_esc};
+    for (int j = 0; j < 6; ++j) {
+        unsigned s = __reduce_add_sync(FULL_MASK, v[j]);
+        if (lane == 0 && s) atomicAdd(&s_cnt[j], (unsigned long long)s);
+    }
+    __syncthreads();
+    if (tid < 6 && s_cnt[tid]) atomicAdd(&A.scratch->cnt[tid], s_cnt[tid]);
+    if (DEBUG)
+        for (int i = tid; i < RM_MAX_DEPTH + 1; i += blockDim.x)
+            if (s_segd[i]) atomicAdd(&A.scratch->seg_depth[i], s_segd[i]);
+    if (DEBUG && stats) {
+        for (int i = tid; i < RM_MAX_DEPTH + 1; i += blockDim.x) {
+            atomicAdd(&A.scratch->pw[i], s_pw[i]);
+            atomicAdd(&A.scratch->pw2[i], s_pw[RM_MAX_DEPTH + 1 + i]);
+            atomicAdd(&A.scratch->esc[i], s_pw[2 * (RM_MAX_DEPTH + 1) + i]);
+        }
+    }
+    if (ADJ)
+        for (int i = tid; i < NGRAD; i += blockDim.x)
+            if (s_grad[i] != 0.0f) atomicAdd(&A.scratch->grad[i], (double)s_grad[i]);
+}
+
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN>
+const void* kernel_ptr() {
+    return reinterpret_cast<const void*>(&k_trace<ADJ, NPOL, DEBUG, BILIN>);
+}
+
+const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint) {
+#define RM_SEL(A, P, D, B) \
+    if (adjoint == A && npol == P && debug == D && bilinear == B) return kernel_ptr<A, P, D, B>();
+    RM_SEL(false, 1, false, false) RM_SEL(false, 1, false, true) RM_SEL(false, 1, true, false)
+    RM_SEL(false, 1, true, true) RM_SEL(false, 2, false, false) RM_SEL(false, 2, false, true)
+    RM_SEL(false, 2, true, false) RM_SEL(false, 2, true, true) RM_SEL(true, 1, false, false)
+    RM_SEL(true, 1, false, true) RM_SEL(true, 1, true, false) RM_SEL(true, 1, true, true)
+    RM_SEL(true, 2, false, false) RM_SEL(true, 2, false, true) RM_SEL(true, 2, true, false)
+    RM_SEL(true, 2, true, true)
+#undef RM_SEL
+    return nullptr;
+}
+
+}  // namespace
+
+int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, int block) {
+    const void* k = select_kernel(npol, debug, bilinear, adjoint);
+    int nb = 0;
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, int block,
+                         int blocks_per_sm, cudaStream_t s, int* grid_out) {
+    const void* k = select_kernel(npol, debug, bilinear, adjoint);
+    if (!k) return cudaErrorInvalidValue;
+    if (block <= 0 || block > MAX_BLOCK || (block & 31)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t err;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, 0)) != cudaSuccess) return err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int bps = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
+    const int grid = bps * sms;
+    if (grid_out) *grid_out = grid;
+    void* args[] = {const_cast<TraceArgs*>(&a)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, 0, s);
+}
+
+}  // namespace rmsbr

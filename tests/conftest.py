@@ -18,3 +18,15 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def api():
+    """The CUDA path (librmsbr.so through its ctypes binding); GPU tests only."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_21719_b300 import build
+    build.build()
+    from paper_2504_21719_b300 import api as A
+    return A

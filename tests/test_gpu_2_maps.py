@@ -1,0 +1,205 @@
+"""GPU radio maps vs the FP64 oracle, cell by cell, after the oracle has
+replayed (and certified) the GPU's discrete choices.  Tolerance: 1e-3
+relative per cell above -150 dB."""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+from gpu_helpers import compare_maps, FLOOR
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(api, sc, tx, p, gs=None, **kw):
+    own = gs is None
+    if own:
+        gs = api.Scene.from_obj(sc)
+    r = api.trace(gs, [tx], p, record=True, **kw)
+    torch.cuda.synchronize()
+    out = (r["maps"][0].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
+    if own:
+        gs.free()
+    return out
+
+
+def test_free_space_map(orc, api):
+    sc = S.empty_scene()
+    tx = S.Tx(pos=(0.3, -0.2, 10.0), num_rays=300_000, seed=1)
+    p = S.TraceParams(3.5e9, 0, cell_size=2.0, nx=40, ny=40)
+    m, rec, st = _run(api, sc, tx, p)
+    assert st["segments"] == tx.num_rays and st["escapes"] == tx.num_rays
+    compare_maps(orc, sc, tx, p, m, rec)
+
+
+def test_two_ray_workload(orc, api):
+    sc, txs, p = S.workload(1)
+    m, rec, st = _run(api, sc, txs[0], p)
+    assert st["rays"] == 100_000
+    compare_maps(orc, sc, txs[0], p, m, rec)
+
+
+@pytest.mark.parametrize("stride,begin", [(97, 0), (1009, 5)])
+def test_manhattan_depth5_subset(orc, api, stride, begin):
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    tx.ray_stride, tx.ray_begin = stride, begin
+    m, rec, st = _run(api, sc, tx, p)
+    assert st["rays"] == tx.count()
+    assert st["segments"] == int((rec[:, 0] != -2).sum())
+    info = compare_maps(orc, sc, tx, p, m, rec)
+    assert info["cells"] > 5000
+
+
+def test_manhattan_full_size_sampled(orc, api):
+    """Full workload (1e7 rays, depth 5, 512 x 512) in the benchmark's launch
+    configuration: a sampled 1-in-997 set of its records is replayed by the
+    oracle, the full map equals the sum of disjoint subset maps, and the
+    records of the full run equal those of the subset run."""
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    gs = api.Scene.from_obj(sc)
+    full = api.trace(gs, [tx], p, record=True)
+    fm = full["maps"][0].double().cpu().numpy()
+    L = p.max_depth
+    frec = full["record"].view(tx.num_rays, L + 1, 4)
+    st = 997
+    sub = copy.copy(tx)
+    sub.ray_stride, sub.ray_begin = st, 3
+    srec_full = frec[3::st].cpu().numpy()
+    r = api.trace(gs, [sub], p, record=True)
+    srec = r["record"].view(sub.count(), L + 1, 4).cpu().numpy()
+    assert np.array_equal(srec, srec_full)
+    compare_maps(orc, sc, sub, p, r["maps"][0].cpu().numpy(), srec)
+    # disjoint subsets add up to the full map (FP32 atomics: order-only noise)
+    parts = torch.zeros_like(full["maps"][0], dtype=torch.float64)
+    for b in range(4):
+        t = copy.copy(tx)
+        t.ray_begin, t.ray_stride = b, 4
+        parts += api.trace(gs, [t], p)["maps"][0].double()
+    pm = parts.cpu().numpy()
+    mask = fm > FLOOR
+    assert np.all(np.abs(pm - fm)[mask] <= 2e-5 * fm[mask])
+    assert full["stats"]["rays"] == tx.num_rays
+    # the benchmark's (record-free) kernel gives the same map
+    plain = api.trace(gs, [tx], p)
+    pm2 = plain["maps"][0].double().cpu().numpy()
+    assert np.all(np.abs(pm2 - fm)[mask] <= 2e-5 * fm[mask])
+    assert plain["stats"]["segments"] == full["stats"]["segments"]
+    gs.free()
+
+
+def test_batched_64_tx_matches_oracle_and_single(orc, api):
+    sc, txs, p = S.workload(3)
+    for t in txs:
+        t.ray_stride = 64
+    gs = api.Scene.from_obj(sc)
+    r = api.trace(gs, txs, p, record=True)
+    maps = r["maps"].cpu().numpy()
+    rec = r["record"].cpu().numpy()
+    L = p.max_depth
+    offs = np.cumsum([0] + [t.count() * (L + 1) for t in txs])
+    for i in (0, 17, 40, 63):
+        compare_maps(orc, sc, txs[i], p, maps[i], rec[offs[i]:offs[i + 1]])
+        single = api.trace(gs, [txs[i]], p, record=True)
+        assert np.array_equal(single["record"].cpu().numpy(), rec[offs[i]:offs[i + 1]])
+        sm = single["maps"][0].double().cpu().numpy()
+        mask = sm > FLOOR
+        assert np.all(np.abs(maps[i] - sm)[mask] <= 2e-5 * sm[mask])
+    assert r["stats"]["rays"] == sum(t.count() for t in txs)
+    gs.free()
+
+
+def test_bilinear_deposit(orc, api):
+    sc, txs, p = S.workload(4)
+    tx = txs[0]
+    tx.ray_stride = 13
+    m, rec, _ = _run(api, sc, tx, p)
+    compare_maps(orc, sc, tx, p, m, rec)
+
+
+@pytest.mark.parametrize("pol,pattern,ori", [(2, 0, (0.0, 0.0, 0.0)), (1, 1, (0.4, -0.9, 0.3)), (0, 1, (1.2, 0.5, -2.0))])
+def test_polarisation_pattern_orientation(orc, api, pol, pattern, ori):
+    sc = S.ground_and_wall(wall_mat=(4.0, 0.02, 0.2))
+    tx = S.Tx(pos=(0.0, 0.0, 10.0), num_rays=200_000, yaw=ori[0], pitch=ori[1], roll=ori[2], pol=pol,
+              pattern=pattern, seed=9)
+    p = S.TraceParams(28e9, 3, cell_size=2.0, nx=64, ny=64)
+    m, rec, _ = _run(api, sc, tx, p)
+    compare_maps(orc, sc, tx, p, m, rec)
+
+
+def test_edge_cases(orc, api):
+    # single triangle, depth 0, 1 x 1 map, reflection off
+    g = S.ground_plane(50.0)
+    one = S.Scene("one", g.verts, g.tris[:1], g.tri_mat[:1], g.mats)
+    tx = S.Tx(pos=(1.0, -2.0, 5.0), num_rays=50_000, seed=3)
+    for L, nx, refl in ((0, 1, True), (2, 7, True), (3, 16, False)):
+        p = S.TraceParams(2.4e9, L, cell_size=3.0, nx=nx, ny=nx, reflect=refl)
+        m, rec, _ = _run(api, one, tx, p)
+        compare_maps(orc, one, tx, p, m, rec)
+    # empty subset: no rays, zero map
+    gs = api.Scene.from_obj(g)
+    t0 = S.Tx(pos=(0, 0, 5.0), num_rays=1000, ray_count=0)
+    r = api.trace(gs, [t0], S.TraceParams(1e9, 2, nx=4, ny=4))
+    assert r["stats"]["rays"] == 0 and float(r["maps"].abs().sum()) == 0.0
+    gs.free()
+
+
+def test_deep_closed_box(orc, api):
+    sc = S.closed_box(10.0, mat=(3.0, 0.05, 0.2))
+    tx = S.Tx(pos=(1.0, 2.0, 3.0), num_rays=20_000, seed=5)
+    p = S.TraceParams(28e9, 15, cell_size=1.0, nx=20, ny=20, map_origin=(0, 0, -2.0))
+    m, rec, st = _run(api, sc, tx, p)
+    assert st["segments_per_depth"][15] > 0
+    compare_maps(orc, sc, tx, p, m, rec)
+
+
+def test_energy_per_depth_matches_branch_all(orc, api):
+    """Lossless closed box: E[sum w|E|^2] per depth from the GPU statistics
+    equals the branch-all expectation within 4 sigma of the per-ray spread."""
+    sc = S.closed_box(10.0, mat=(3.0, 0.0, 0.2))
+    N, L = 4000, 6
+    tx = S.Tx(pos=(1.0, 2.0, 3.0), num_rays=N, seed=21)
+    p = S.TraceParams(28e9, L, cell_size=1.0, nx=20, ny=20, map_origin=(0, 0, -2.0))
+    _, pw, esc = orc.branch_all(sc, tx, p)
+    gs = api.Scene.from_obj(sc)
+    st = api.trace(gs, [tx], api.params_from(p, stats=True))["stats"]
+    gs.free()
+    for l in range(L + 1):
+        s1, s2 = st["power_per_depth"][l], st["power2_per_depth"][l]
+        n = N
+        var = max(s2 - s1 * s1 / n, 0.0)
+        sigma = np.sqrt(var) + 1e-6 * pw[l]
+        assert abs(s1 - pw[l]) <= 4 * sigma, (l, s1, pw[l], sigma)
+
+
+def test_graph_plan_matches_trace(api):
+    sc, txs, p = S.workload(3)
+    txs = txs[:8]
+    for t in txs:
+        t.ray_stride = 16
+    gs = api.Scene.from_obj(sc)
+    ref = api.trace(gs, txs, p)["maps"].double()
+    out = torch.empty((len(txs), p.ny, p.nx), dtype=torch.float32, device="cuda")
+    plan = api.TracePlan(gs, txs, p, out)
+    for _ in range(3):
+        plan.launch()
+    torch.cuda.synchronize()
+    st = plan.stats()
+    assert st["rays"] == sum(t.count() for t in txs)
+    mask = ref > FLOOR
+    assert torch.all((out.double() - ref).abs()[mask] <= 2e-5 * ref[mask])
+    plan.free()
+    gs.free()
+
+
+def test_upload_rejects_bad_indices(api):
+    sc = S.ground_plane()
+    bad = S.Scene("bad", sc.verts, sc.tris + 10, sc.tri_mat, sc.mats)
+    with pytest.raises(api.RmError):
+        api.Scene.from_obj(bad)
+    bad2 = S.Scene("bad2", sc.verts, sc.tris, sc.tri_mat + 1, sc.mats)
+    with pytest.raises(api.RmError):
+        api.Scene.from_obj(bad2)

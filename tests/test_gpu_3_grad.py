@@ -1,0 +1,130 @@
+"""Adjoint kernel vs the oracle's dual-number gradient (same frozen choices,
+taken from the GPU's own record) and vs GPU finite differences; dB loss."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+from gpu_helpers import compare_maps
+
+pytestmark = pytest.mark.gpu
+GRAD_RTOL = 1e-2
+
+
+def _setup(stride=13, deposit=1):
+    sc, txs, p = S.workload(4)
+    tx = txs[0]
+    tx.ray_stride = stride
+    p.deposit = deposit
+    return sc, tx, p
+
+
+def _target(api, sc, tx, p):
+    tgt = S.perturb_materials(sc.mats, 40)
+    gs = api.Scene.from_obj(S.Scene(sc.name, sc.verts, sc.tris, sc.tri_mat, tgt))
+    m = api.trace(gs, [tx], p)["maps"][0]
+    gs.free()
+    return m
+
+
+def test_db_loss_kernel(api):
+    rng = np.random.default_rng(0)
+    a = 10 ** rng.uniform(-20, -5, size=5000)
+    b = 10 ** rng.uniform(-20, -5, size=5000)
+    a[:100] = 0
+    ta, tb = torch.tensor(a, dtype=torch.float32, device="cuda"), torch.tensor(b, dtype=torch.float32, device="cuda")
+    loss, g, valid = api.db_mse_loss(ta, tb, 1e-15)
+    a32, b32 = a.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+    V = (a32 > 1e-15) & (b32 > 1e-15)
+    d = 10 * (np.log10(a32[V]) - np.log10(b32[V]))
+    assert int(valid) == V.sum()
+    assert abs(float(loss) - np.mean(d * d)) <= 1e-5 * np.mean(d * d)
+    gref = np.zeros_like(a32)
+    gref[V] = 2 / V.sum() * d * 10 / (math.log(10) * a32[V])
+    gg = g.double().cpu().numpy()
+    assert np.allclose(gg, gref, rtol=2e-4, atol=0)
+
+
+def test_adjoint_retrace_takes_forward_choices(api):
+    sc, tx, p = _setup()
+    gs = api.Scene.from_obj(sc)
+    f = api.trace(gs, [tx], p, record=True)
+    g = torch.rand_like(f["maps"])
+    a = api.grad(gs, [tx], p, g, record=True)
+    assert torch.equal(f["record"], a["record"])
+    assert a["stats"]["segments"] == f["stats"]["segments"]
+    gs.free()
+
+
+@pytest.mark.parametrize("deposit", [1, 0])
+def test_adjoint_matches_oracle_gradient(orc, api, deposit):
+    sc, tx, p = _setup(deposit=deposit)
+    gs = api.Scene.from_obj(sc)
+    tgt = _target(api, sc, tx, p)
+    f = api.trace(gs, [tx], p, record=True)
+    loss, dLdC, valid = api.db_mse_loss(f["maps"][0], tgt)
+    assert int(valid) > 1000
+    a = api.grad(gs, [tx], p, dLdC.view(1, p.ny, p.nx))
+    ad = np.concatenate([a["d_eps"].cpu().numpy(), a["d_sigma"].cpu().numpy(), a["d_tx"][0].cpu().numpy()])
+    rec = f["record"].view(tx.count(), p.max_depth + 1, 4).cpu().numpy()
+    # the oracle certifies the GPU's choices, then differentiates along them
+    compare_maps(orc, sc, tx, p, f["maps"][0].cpu().numpy(), rec)
+    de, ds, dt = orc.grad(sc, tx, p, rec, dLdC.double().cpu().numpy())
+    ref = np.concatenate([de, ds, dt])
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    err = np.abs(ad - ref) / scale
+    assert np.all(err <= GRAD_RTOL), err
+    if deposit == 0:
+        assert np.all(ad[-3:] == 0.0)
+    gs.free()
+
+
+def test_adjoint_vs_gpu_finite_differences(api):
+    """Materials only (frozen sampling): central differences of the FP32
+    traced loss with h = 1e-3 relative.  The 0.2 m slab phase turns ~50 rad
+    per unit permittivity at 28 GHz, so a 1e-3 step carries ~1% truncation."""
+    sc, tx, p = _setup(stride=3)
+    gs = api.Scene.from_obj(sc)
+    tgt = _target(api, sc, tx, p)
+    mats0 = sc.mats.astype(np.float64)
+    f = api.trace(gs, [tx], p)
+    _, dLdC, _ = api.db_mse_loss(f["maps"][0], tgt)
+    g = dLdC.view(1, p.ny, p.nx)
+    a = api.grad(gs, [tx], p, g)
+
+    def J(m):
+        gs.set_materials(m, sampling=mats0)
+        mp = api.trace(gs, [tx], p)["maps"][0].double()
+        return float((mp * g[0].double()).sum())
+
+    fd = []
+    for j in range(2 * sc.nm):
+        m, c = j % sc.nm, j // sc.nm
+        h = 1e-3 * abs(mats0[m, c])
+        mp, mm = mats0.copy(), mats0.copy()
+        mp[m, c] += h
+        mm[m, c] -= h
+        fd.append((J(mp) - J(mm)) / (2 * h))
+    fd = np.array(fd)
+    ad = np.concatenate([a["d_eps"].cpu().numpy(), a["d_sigma"].cpu().numpy()])
+    scale = np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max())
+    assert np.all(np.abs(ad - fd) <= 5e-2 * scale), np.abs(ad - fd) / scale
+    gs.free()
+
+
+def test_autograd_function(api):
+    sc, tx, p = _setup(stride=29)
+    gs = api.Scene.from_obj(sc)
+    tgt = _target(api, sc, tx, p)
+    eps = torch.tensor(sc.mats[:, 0], dtype=torch.float64, requires_grad=True)
+    sig = torch.tensor(sc.mats[:, 1], dtype=torch.float64, requires_grad=True)
+    pos = torch.tensor([tx.pos], dtype=torch.float64, requires_grad=True)
+    maps = api.RadioMap.apply(eps, sig, pos, gs, [tx], p, sc.mats[:, 2])
+    loss, dLdC, _ = api.db_mse_loss(maps[0].detach(), tgt)
+    maps.backward(dLdC.view_as(maps))
+    ref = api.grad(gs, [tx], p, dLdC.view_as(maps))
+    assert torch.allclose(eps.grad.float().cuda(), ref["d_eps"], rtol=1e-5, atol=0)
+    assert torch.allclose(pos.grad.float().cuda(), ref["d_tx"], rtol=1e-5, atol=0)
+    gs.free()
