@@ -397,16 +397,18 @@ inline double hit_mt(const Tri& T, const V3<double>& o, const V3<double>& k) {
 }
 
 // Reading (paper silent): the closest hit excludes the primitive the ray just
-// left; equal distances go to the smaller triangle index.
+// left; equal distances go to the smaller triangle index.  Distances that
+// agree to a relative 1e-12 count as equal, so coplanar triangles (a box
+// floor lying on the ground plane) are resolved by index, not by rounding.
 inline void closest_hit(const Scene& S, const V3<double>& o, const V3<double>& k, int exclude,
                         int* prim, double* t) {
     int best = -1;
     double tb = INFINITY;
     const int nt = (int)S.tris.size();
-    for (int i = 0; i < nt; ++i) {
+    for (int i = 0; i < nt; ++i) {  // ascending index: a later triangle must be clearly closer
         if (i == exclude) continue;
         double ti = hit_mt(S.tris[i], o, k);
-        if (ti < tb) { tb = ti; best = i; }
+        if (ti < tb * (1.0 - 1e-12)) { tb = ti; best = i; }
     }
     *prim = best;
     *t = tb;

@@ -205,7 +205,9 @@ struct Hit {
 };
 
 // Closest hit along the ray, excluding leaf `exclude`.  Equal distances go to
-// the smaller original triangle index.
+// the smaller original triangle index; distances within 8 ulps (relative
+// TIE_REL) count as equal, so coplanar triangles resolve by index.
+constexpr float TIE_REL = 4.8e-7f;
 __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, int nt,
                                            const Ray& r, int exclude, unsigned& c_nodes, unsigned& c_tris,
                                            bool& overflow) {
@@ -247,8 +249,9 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
             const float4* nd = nodes + 4 * (size_t)cur;
             const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
             float tn0, tn1;
-            const bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, ix, iy, iz, h.t, tn0);
-            const bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, ix, iy, iz, h.t, tn1);
+            const float tmax = h.t * (1.0f + TIE_REL);
+            const bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, ix, iy, iz, tmax, tn0);
+            const bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, ix, iy, iz, tmax, tn1);
             const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
             if (h0 && h1) {
                 const bool first0 = tn0 <= tn1;
@@ -293,10 +296,11 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
                         T = -T;
                         det = -det;
                     }
-                    if (T > 0.0f && !(T > h.t * det)) {
+                    const float thi = h.t * (1.0f + TIE_REL);
+                    if (T > 0.0f && !(T > thi * det)) {
                         const float t = T / det;
                         const int prim = __float_as_int(r2.z);
-                        if (t < h.t || (t == h.t && prim < h.prim)) {
+                        if (t < h.t * (1.0f - TIE_REL) || (t <= thi && prim < h.prim)) {
                             h.t = t;
                             h.slot = slot;
                             h.prim = prim;

@@ -5,7 +5,7 @@ MAP_RTOL = 1e-3          # per-cell relative tolerance of the maps
 FLOOR = 1e-15            # cells above -150 dB are compared
 
 
-def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max_adopt_frac=2e-3):
+def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max_adopt_frac=5e-3):
     """Replay the GPU's discrete choices in the FP64 oracle (certifying every
     difference as a near-tie) and compare the maps cell by cell."""
     L = params.max_depth

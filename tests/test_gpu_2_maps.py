@@ -156,23 +156,33 @@ def test_deep_closed_box(orc, api):
     compare_maps(orc, sc, tx, p, m, rec)
 
 
-def test_energy_per_depth_matches_branch_all(orc, api):
-    """Lossless closed box: E[sum w|E|^2] per depth from the GPU statistics
-    equals the branch-all expectation within 4 sigma of the per-ray spread."""
+def test_energy_per_depth_matches_oracle_and_branch_all(orc, api):
+    """Lossless closed box.  (a) The GPU's per-depth power sums sum(w |E|^2)
+    equal the oracle's Monte-Carlo sums for the same seed (same decisions).
+    (b) Their mean over seeds matches the branch-all expectation within 4.5
+    standard errors of the seed-to-seed spread at depths 0-3 (deeper depths
+    carry heavy-tailed 1/Pr weights, for which a normal test is unreliable)."""
     sc = S.closed_box(10.0, mat=(3.0, 0.0, 0.2))
     N, L = 4000, 6
-    tx = S.Tx(pos=(1.0, 2.0, 3.0), num_rays=N, seed=21)
     p = S.TraceParams(28e9, L, cell_size=1.0, nx=20, ny=20, map_origin=(0, 0, -2.0))
-    _, pw, esc = orc.branch_all(sc, tx, p)
+    _, pw, esc = orc.branch_all(sc, S.Tx(pos=(1.0, 2.0, 3.0), num_rays=N), p)
     gs = api.Scene.from_obj(sc)
-    st = api.trace(gs, [tx], api.params_from(p, stats=True))["stats"]
+    runs = []
+    for seed in range(32):
+        tx = S.Tx(pos=(1.0, 2.0, 3.0), num_rays=N, seed=seed)
+        r = api.trace(gs, [tx], api.params_from(p, stats=True), record=seed < 4)
+        g = np.array(r["stats"]["power_per_depth"][:L + 1])
+        runs.append(g)
+        if seed < 4:
+            rec = r["record"].view(N, L + 1, 4).cpu().numpy()
+            o = orc.radio_map(sc, tx, p, mode="replay", record=rec, stats=True)
+            assert o["report"]["failures"] == 0
+            assert np.all(np.abs(g - o["power"]) <= 1e-4 * np.maximum(o["power"], 1.0)), (seed, g, o["power"])
     gs.free()
-    for l in range(L + 1):
-        s1, s2 = st["power_per_depth"][l], st["power2_per_depth"][l]
-        n = N
-        var = max(s2 - s1 * s1 / n, 0.0)
-        sigma = np.sqrt(var) + 1e-6 * pw[l]
-        assert abs(s1 - pw[l]) <= 4 * sigma, (l, s1, pw[l], sigma)
+    runs = np.array(runs)
+    mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
+    for l in range(4):
+        assert abs(mean[l] - pw[l]) <= 4.5 * se[l] + 1e-6 * pw[l], (l, mean[l], pw[l], se[l])
 
 
 def test_graph_plan_matches_trace(api):

@@ -44,7 +44,8 @@ def test_db_loss_kernel(api):
     gref = np.zeros_like(a32)
     gref[V] = 2 / V.sum() * d * 10 / (math.log(10) * a32[V])
     gg = g.double().cpu().numpy()
-    assert np.allclose(gg, gref, rtol=2e-4, atol=0)
+    # FP32 log10 difference: absolute error ~1e-6 dB, i.e. relative error grows as d -> 0
+    assert np.allclose(gg, gref, rtol=2e-4, atol=1e-5 * np.abs(gref).max())
 
 
 def test_adjoint_retrace_takes_forward_choices(api):
@@ -83,8 +84,9 @@ def test_adjoint_matches_oracle_gradient(orc, api, deposit):
 
 def test_adjoint_vs_gpu_finite_differences(api):
     """Materials only (frozen sampling): central differences of the FP32
-    traced loss with h = 1e-3 relative.  The 0.2 m slab phase turns ~50 rad
-    per unit permittivity at 28 GHz, so a 1e-3 step carries ~1% truncation."""
+    traced loss with h = 1e-3 relative, Richardson-extrapolated with 2h.  The
+    0.2 m slab phase turns ~50 rad per unit permittivity at 28 GHz, so a plain
+    1e-3 central step alone carries percent-level truncation."""
     sc, tx, p = _setup(stride=3)
     gs = api.Scene.from_obj(sc)
     tgt = _target(api, sc, tx, p)
@@ -99,18 +101,22 @@ def test_adjoint_vs_gpu_finite_differences(api):
         mp = api.trace(gs, [tx], p)["maps"][0].double()
         return float((mp * g[0].double()).sum())
 
+    def central(m, c, h):
+        mp, mm = mats0.copy(), mats0.copy()
+        mp[m, c] += h
+        mm[m, c] -= h
+        return (J(mp) - J(mm)) / (2 * h)
+
     fd = []
     for j in range(2 * sc.nm):
         m, c = j % sc.nm, j // sc.nm
         h = 1e-3 * abs(mats0[m, c])
-        mp, mm = mats0.copy(), mats0.copy()
-        mp[m, c] += h
-        mm[m, c] -= h
-        fd.append((J(mp) - J(mm)) / (2 * h))
+        # Richardson extrapolation of the steps 2h and h (truncation O(h^4))
+        fd.append((4 * central(m, c, h) - central(m, c, 2 * h)) / 3)
     fd = np.array(fd)
     ad = np.concatenate([a["d_eps"].cpu().numpy(), a["d_sigma"].cpu().numpy()])
     scale = np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max())
-    assert np.all(np.abs(ad - fd) <= 5e-2 * scale), np.abs(ad - fd) / scale
+    assert np.all(np.abs(ad - fd) <= 2e-2 * scale), np.abs(ad - fd) / scale
     gs.free()
 
 
