@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rays", type=int, default=0, help="override the ray count (profiling a smaller case)")
     return ap.parse_args()
 
 
@@ -187,6 +189,8 @@ def run_ours(args, world, rank, local):
     gpu_name = torch.cuda.get_device_name(local)
     sc, txs, p = S.workload(2)
     tx = txs[0]
+    if args.rays:
+        tx.num_rays = args.rays
     blk, bps = tuned(gpu_name, "manhattan")
     params = api.params_from(p, block_size=blk, blocks_per_sm=bps)
     gs = api.Scene.from_obj(sc)
@@ -237,7 +241,7 @@ def run_ours(args, world, rank, local):
 
     # end to end through the public API from pinned host memory
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         vh = torch.from_numpy(sc.verts).pin_memory()
         th = torch.from_numpy(sc.tris).pin_memory()
         mh = torch.from_numpy(sc.tri_mat).pin_memory()
@@ -270,7 +274,7 @@ def run_ours(args, world, rank, local):
             dist.destroy_process_group()
         return None
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.rays:
         cpu = oracle_sample()
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
