@@ -46,7 +46,8 @@ class OrParams(C.Structure):
 class OrReport(C.Structure):
     _fields_ = [("segments", C.c_int64), ("deposits", C.c_int64), ("adopted_hit", C.c_int64),
                 ("adopted_cell", C.c_int64), ("adopted_decision", C.c_int64),
-                ("failures", C.c_int64), ("fail_ray", C.c_int64), ("fail_depth", C.c_int32),
+                ("failures", C.c_int64), ("adopted_hit_tie", C.c_int64), ("fail_ray", C.c_int64),
+                ("fail_depth", C.c_int32),
                 ("fail_kind", C.c_int32), ("fail_info", C.c_double * 4)]
 
     def as_dict(self):
@@ -79,7 +80,7 @@ def lib():
         _lib.or_closest_hit.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int64, P, P, P]
         _lib.or_radio_map.restype = C.c_int
         _lib.or_radio_map.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, C.c_int, P,
-                                      P, P, P, P, P]
+                                      P, P, P, P, P, P]
         _lib.or_grad.restype = C.c_int
         _lib.or_grad.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, P, P, P]
         _lib.or_branch_all.restype = C.c_int
@@ -220,7 +221,7 @@ MODES = {"plain": 0, "replay": 1, "frozen": 2}
 
 
 def radio_map(scene, tx, params, mode: str = "plain", record=None, want_record: bool = False,
-              sampling_mats=None, eval_mats=None, stats: bool = False):
+              sampling_mats=None, eval_mats=None, stats: bool = False, mass: bool = False):
     """Radio map [ny, nx] (float64) of one transmitter.
 
     mode 'plain'  : decisions from the counter-based RNG; ``want_record``
@@ -244,10 +245,11 @@ def radio_map(scene, tx, params, mode: str = "plain", record=None, want_record: 
     em = None if eval_mats is None else np.ascontiguousarray(np.asarray(eval_mats, np.float64)[:, :2])
     mp = np.empty((params.ny, params.nx), np.float64)
     st = np.empty(3 * (L + 1), np.float64) if stats else None
+    ms = np.empty((params.ny, params.nx), np.float64) if mass else None
     rep = OrReport()
     rc = lib().or_radio_map(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), C.byref(otx),
                             C.byref(op), MODES[mode], _p(rec), _p(sm), _p(em), _p(mp), _p(st),
-                            C.byref(rep))
+                            C.byref(rep), _p(ms))
     if rc != 0:
         raise ValueError(f"or_radio_map failed ({rc})")
     out = {"map": mp}
@@ -258,6 +260,8 @@ def radio_map(scene, tx, params, mode: str = "plain", record=None, want_record: 
         out["power"], out["power2"], out["escaped"] = s[0], s[1], s[2]
     if mode == "replay":
         out["report"] = rep.as_dict()
+    if mass:
+        out["mass"] = ms
     return out
 
 

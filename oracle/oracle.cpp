@@ -453,6 +453,7 @@ struct or_params {
 enum { F_REFLECT = 1, F_REFRACT = 2, F_LOS = 4 };
 struct or_report {
     int64_t segments, deposits, adopted_hit, adopted_cell, adopted_decision, failures;
+    int64_t adopted_hit_tie;  // adopted hits whose distance equals the FP64 closest hit within tol
     int64_t fail_ray;
     int32_t fail_depth, fail_kind;  // 1 hit, 2 deposit cell, 3 decision, 4 segment
     double fail_info[4];
@@ -523,7 +524,11 @@ struct Sink;
 template <>
 struct Sink<double> {
     DepList* list;
+    DepList* mass = nullptr;  // unweighted deposit value per stencil cell (bilinear error bound)
     void add(int cell, const double& v) { list->cell.push_back(cell); list->val.push_back(v); }
+    void add_mass(int cell, const double& v) {
+        if (mass) { mass->cell.push_back(cell); mass->val.push_back(v); }
+    }
 };
 template <>
 struct Sink<D> {
@@ -533,12 +538,16 @@ struct Sink<D> {
         const double w = gmap[cell];
         for (int i = 0; i < NT; ++i) acc[i] += w * v.g[i];
     }
+    void add_mass(int, const D&) {}
 };
 
 template <class R, class SinkT>
 void deposit(const MapGeom& g, const Crossing<R>& c, int ix, int iy, const R& value, SinkT& sink) {
     if (!g.bilinear) {
-        if (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny) sink.add(iy * g.nx + ix, value);
+        if (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny) {
+            sink.add(iy * g.nx + ix, value);
+            sink.add_mass(iy * g.nx + ix, value);
+        }
         return;
     }
     // tent weights relative to the (possibly adopted) lower-left index
@@ -552,6 +561,7 @@ void deposit(const MapGeom& g, const Crossing<R>& c, int ix, int iy, const R& va
             int cx = ix + a, cy = iy + b;
             if (cx < 0 || cx >= g.nx || cy < 0 || cy >= g.ny) continue;
             sink.add(cy * g.nx + cx, value * (wx[a] * wy[b]));
+            sink.add_mass(cy * g.nx + cx, value);
         }
 }
 
@@ -667,6 +677,9 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
                     double tg;
                     if (certify_hit(S, ov, k, prev, rec->prim, path, &tg)) {
                         rs->rep.adopted_hit++;
+                        if (prim >= 0 && std::isfinite(tg) &&
+                            std::fabs(tg - th) <= tie_tol(ov + scl(k, th), path + th))
+                            rs->rep.adopted_hit_tie++;
                         prim = rec->prim;
                         th = tg;
                     } else {
@@ -986,7 +999,8 @@ void or_closest_hit(const float* verts, int64_t nv, const int32_t* tris, int64_t
 int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                  const int32_t* tri_mat, const float* mats, int nm, const or_tx* tx,
                  const or_params* P, int mode, int32_t* rec, const double* sampling_mats,
-                 const double* eval_mats, double* map_out, double* stats, or_report* report) {
+                 const double* eval_mats, double* map_out, double* stats, or_report* report,
+                 double* mass_out) {
     if (P->max_depth < 0 || P->max_depth > 15) return 1;
     Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
     if (eval_mats)
@@ -1021,7 +1035,7 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
     const int L = P->max_depth;
     const int64_t CH = 2048;  // fixed chunking: the summation order is independent of threads
     const int64_t nch = (cnt + CH - 1) / CH;
-    std::vector<DepList> lists(nch);
+    std::vector<DepList> lists(nch), masses(mass_out ? nch : 0);
     const int nthr = or_num_threads();
     std::vector<double> st((size_t)nthr * 3 * (L + 1), 0.0);
     std::vector<ReplayState> rss(nch);
@@ -1034,7 +1048,7 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
         int tid = 0;
 #endif
         double* sp = stats ? st.data() + (size_t)tid * 3 * (L + 1) : nullptr;
-        Sink<double> sink{&lists[c]};
+        Sink<double> sink{&lists[c], mass_out ? &masses[c] : nullptr};
         int64_t e = std::min(cnt, (c + 1) * CH);
         for (int64_t i = c * CH; i < e; ++i) {
             int64_t n = tx->ray_begin + i * tx->ray_stride;
@@ -1046,6 +1060,11 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
     std::memset(map_out, 0, sizeof(double) * (size_t)P->nx * P->ny);
     for (int64_t c = 0; c < nch; ++c)
         for (size_t j = 0; j < lists[c].cell.size(); ++j) map_out[lists[c].cell[j]] += lists[c].val[j];
+    if (mass_out) {
+        std::memset(mass_out, 0, sizeof(double) * (size_t)P->nx * P->ny);
+        for (int64_t c = 0; c < nch; ++c)
+            for (size_t j = 0; j < masses[c].cell.size(); ++j) mass_out[masses[c].cell[j]] += masses[c].val[j];
+    }
     if (stats) {
         std::memset(stats, 0, sizeof(double) * 3 * (L + 1));
         for (int t = 0; t < nthr; ++t)
@@ -1061,6 +1080,7 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
             report->adopted_hit += r.adopted_hit;
             report->adopted_cell += r.adopted_cell;
             report->adopted_decision += r.adopted_decision;
+            report->adopted_hit_tie += r.adopted_hit_tie;
             report->failures += r.failures;
             if (r.failures && !have_fail) {
                 have_fail = true;

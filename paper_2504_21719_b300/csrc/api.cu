@@ -135,6 +135,40 @@ struct Prepared {
     double kernel_ms = 0.0;
 };
 
+uint64_t gcd64(uint64_t a, uint64_t b) {
+    while (b) {
+        const uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Visit order of a transmitter's rays.  In a Fibonacci lattice of N points the
+// directions n and n + F_k (F_k a Fibonacci number near 1.24 sqrt(N)) are
+// nearest neighbours, so visiting i = j F_k mod count gives every warp a tight
+// bundle of directions (coherent traversal) without changing which rays are
+// traced.  Identity for strided subsets, small counts, or no coprime F_k.
+uint64_t visit_step(const rm_tx& t, uint64_t count) {
+    if (t.ray_stride != 1 || count < 4096) return 1;
+    const double target = 1.24 * std::sqrt((double)t.num_rays);
+    std::vector<uint64_t> fib{1, 2};
+    while (fib.back() < (1ULL << 40)) fib.push_back(fib[fib.size() - 1] + fib[fib.size() - 2]);
+    size_t k = 0;
+    for (size_t i = 0; i < fib.size(); ++i)
+        if (std::fabs((double)fib[i] - target) < std::fabs((double)fib[k] - target)) k = i;
+    const int order[5] = {0, -1, 1, -2, 2};
+    for (int d : order) {
+        const long long j = (long long)k + d;
+        if (j < 1 || j >= (long long)fib.size()) continue;
+        const uint64_t F = fib[j];
+        if (F >= count || gcd64(F, count) != 1) continue;
+        if ((double)F * (double)count >= 9.0e18) continue;  // (j * F) must fit in 64 bits
+        return F;
+    }
+    return 1;
+}
+
 void rotation(double a, double b, double g, float* R) {
     // R = Rz(a) Ry(b) Rx(g)  (Eq. rotation)
     const double ca = std::cos(a), sa = std::sin(a), cb = std::cos(b), sb = std::sin(b), cg = std::cos(g),
@@ -184,6 +218,7 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
         d.work_begin = work;
         d.seed = tx[t].seed;
         d.rec_begin = rec;
+        d.perm = visit_step(tx[t], d.count);
         work += d.count;
         rec += d.count * (unsigned long long)(p->max_depth + 1);
     }

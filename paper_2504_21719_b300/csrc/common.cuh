@@ -37,6 +37,7 @@ struct TxDev {
     unsigned long long work_begin;  // first work item of this transmitter
     unsigned long long seed;
     unsigned long long rec_begin;   // first debug record of this transmitter
+    unsigned long long perm;        // visit order: subset index i = (j * perm) mod count (1 = identity)
 };
 
 // Scratch of one trace launch (zeroed before the launch).

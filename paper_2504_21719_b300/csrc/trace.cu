@@ -234,80 +234,89 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
     const f3 o{r.ox, r.oy, r.oz};
     const float opx = sel(o, kxi), opy = sel(o, kyi), opz = sel(o, kzi);
 
+    // ray-triangle test of leaf `slot` (watertight; Woop, Benthin & Wald 2013)
+    auto test_leaf = [&](int slot) {
+        if (slot == exclude) return;
+        ++c_tris;
+        const float4* tp = tris + 3 * (size_t)slot;
+        const float4 r0 = __ldg(tp), r1 = __ldg(tp + 1), r2 = __ldg(tp + 2);
+        const f3 va{r0.x, r0.y, r0.z}, vb{r0.w, r1.x, r1.y}, vc{r1.z, r1.w, r2.x};
+        const float Akx = sel(va, kxi) - opx, Aky = sel(va, kyi) - opy, Akz = sel(va, kzi) - opz;
+        const float Bkx = sel(vb, kxi) - opx, Bky = sel(vb, kyi) - opy, Bkz = sel(vb, kzi) - opz;
+        const float Ckx = sel(vc, kxi) - opx, Cky = sel(vc, kyi) - opy, Ckz = sel(vc, kzi) - opz;
+        const float Ax = Akx - Sx * Akz, Ay = Aky - Sy * Akz;
+        const float Bx = Bkx - Sx * Bkz, By = Bky - Sy * Bkz;
+        const float Cx = Ckx - Sx * Ckz, Cy = Cky - Sy * Ckz;
+        float U = Cx * By - Cy * Bx;
+        float V = Ax * Cy - Ay * Cx;
+        float W = Bx * Ay - By * Ax;
+        if (U == 0.0f || V == 0.0f || W == 0.0f) {
+            U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+            V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+            W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+        }
+        const bool neg = (U < 0.0f || V < 0.0f || W < 0.0f);
+        const bool pos = (U > 0.0f || V > 0.0f || W > 0.0f);
+        float det = U + V + W;
+        if ((neg && pos) || det == 0.0f) return;
+        float T = U * (Sz * Akz) + V * (Sz * Bkz) + W * (Sz * Ckz);
+        if (det < 0.0f) {
+            T = -T;
+            det = -det;
+        }
+        const float thi = h.t * (1.0f + TIE_REL);
+        if (!(T > 0.0f) || T > thi * det) return;
+        const float t = T / det;
+        const int prim = __float_as_int(r2.z);
+        if (t < h.t * (1.0f - TIE_REL) || (t <= thi && prim < h.prim)) {
+            h.t = t;
+            h.slot = slot;
+            h.prim = prim;
+        }
+    };
+    if (nt == 1) {
+        test_leaf(0);
+        return h;
+    }
+
+    // Stack traversal over internal nodes; a hit leaf child is tested inside
+    // its parent's step, so leaves never take a loop iteration of their own.
     int stack[STACK_SIZE];
     int sp = 0;
-    int cur = (nt == 1) ? ~0 : 0;
-    // a valid tree is visited at most once per node and leaf: 2 nt - 1 steps
+    int cur = 0;
+    // a valid tree has nt - 1 internal nodes, each visited at most once
     long long budget = 2LL * nt + 8;
     while (true) {
         if (--budget < 0) {
             overflow = true;
             break;
         }
-        if (cur >= 0) {
-            ++c_nodes;
-            const float4* nd = nodes + 4 * (size_t)cur;
-            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-            float tn0, tn1;
-            const float tmax = h.t * (1.0f + TIE_REL);
-            const bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, ix, iy, iz, tmax, tn0);
-            const bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, ix, iy, iz, tmax, tn1);
-            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-            if (h0 && h1) {
-                const bool first0 = tn0 <= tn1;
-                if (sp < STACK_SIZE) stack[sp++] = first0 ? c1 : c0;
-                else overflow = true;
-                cur = first0 ? c0 : c1;
-            } else if (h0) {
-                cur = c0;
-            } else if (h1) {
-                cur = c1;
-            } else {
-                if (sp == 0) break;
-                cur = stack[--sp];
-            }
+        ++c_nodes;
+        const float4* nd = nodes + 4 * (size_t)cur;
+        const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+        float tn0, tn1;
+        const float tmax = h.t * (1.0f + TIE_REL);
+        bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, ix, iy, iz, tmax, tn0);
+        bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, ix, iy, iz, tmax, tn1);
+        const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+        if (h0 && c0 < 0) {
+            test_leaf(~c0);
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            test_leaf(~c1);
+            h1 = false;
+        }
+        if (h0 && h1) {
+            const bool first0 = tn0 <= tn1;
+            if (sp < STACK_SIZE) stack[sp++] = first0 ? c1 : c0;
+            else overflow = true;
+            cur = first0 ? c0 : c1;
+        } else if (h0) {
+            cur = c0;
+        } else if (h1) {
+            cur = c1;
         } else {
-            const int slot = ~cur;
-            if (slot != exclude) {
-                ++c_tris;
-                const float4* tp = tris + 3 * (size_t)slot;
-                const float4 r0 = __ldg(tp), r1 = __ldg(tp + 1), r2 = __ldg(tp + 2);
-                const f3 va{r0.x, r0.y, r0.z}, vb{r0.w, r1.x, r1.y}, vc{r1.z, r1.w, r2.x};
-                const float Akx = sel(va, kxi) - opx, Aky = sel(va, kyi) - opy, Akz = sel(va, kzi) - opz;
-                const float Bkx = sel(vb, kxi) - opx, Bky = sel(vb, kyi) - opy, Bkz = sel(vb, kzi) - opz;
-                const float Ckx = sel(vc, kxi) - opx, Cky = sel(vc, kyi) - opy, Ckz = sel(vc, kzi) - opz;
-                const float Ax = Akx - Sx * Akz, Ay = Aky - Sy * Akz;
-                const float Bx = Bkx - Sx * Bkz, By = Bky - Sy * Bkz;
-                const float Cx = Ckx - Sx * Ckz, Cy = Cky - Sy * Ckz;
-                float U = Cx * By - Cy * Bx;
-                float V = Ax * Cy - Ay * Cx;
-                float W = Bx * Ay - By * Ax;
-                if (U == 0.0f || V == 0.0f || W == 0.0f) {
-                    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
-                    V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
-                    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
-                }
-                const bool neg = (U < 0.0f || V < 0.0f || W < 0.0f);
-                const bool pos = (U > 0.0f || V > 0.0f || W > 0.0f);
-                float det = U + V + W;
-                if (!(neg && pos) && det != 0.0f) {
-                    float T = U * (Sz * Akz) + V * (Sz * Bkz) + W * (Sz * Ckz);
-                    if (det < 0.0f) {
-                        T = -T;
-                        det = -det;
-                    }
-                    const float thi = h.t * (1.0f + TIE_REL);
-                    if (T > 0.0f && !(T > thi * det)) {
-                        const float t = T / det;
-                        const int prim = __float_as_int(r2.z);
-                        if (t < h.t * (1.0f - TIE_REL) || (t <= thi && prim < h.prim)) {
-                            h.t = t;
-                            h.slot = slot;
-                            h.prim = prim;
-                        }
-                    }
-                }
-            }
             if (sp == 0) break;
             cur = stack[--sp];
         }
@@ -381,7 +390,10 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                         }
                         txi = lo;
                         const TxDev& T = s_tx[txi];
+                        // neighbouring work items visit neighbouring lattice directions:
+                        // i = j * F mod count with F a Fibonacci number (lattice neighbour step)
                         isub = w - T.work_begin;
+                        if (T.perm > 1ULL) isub = (isub * T.perm) % T.count;
                         n = T.begin + isub * T.stride;
                         // Fibonacci lattice (Sec. 3.1.1): cos theta = 1 - 2n/(N-1),
                         // sin theta = 2 sqrt(n (N-1-n)) / (N-1), phi = 2 pi frac(n (phi_g - 1))

@@ -3,14 +3,23 @@ import numpy as np
 
 MAP_RTOL = 1e-3          # per-cell relative tolerance of the maps
 FLOOR = 1e-15            # cells above -150 dB are compared
+# Bilinear (tent) deposits: a weight is (1 - f) or f with f the FP32 fractional
+# cell coordinate of a crossing point.  FP32 ray origins near |x| ~ 300 m after a
+# few bounces carry ~5 roundings of 2^-24 * 300 m = 1.8e-5 m each, i.e. up to
+# ~1e-4 m, so f is off by up to 5e-5 cells for 2 m cells and a product weight
+# by twice that.  A cell may therefore differ by WEIGHT_ATOL times the
+# unweighted value of the deposits whose stencil covers it (2x margin).
+WEIGHT_ATOL = 2e-4
+MAX_ADOPT_FRAC = 1e-2
 
 
-def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max_adopt_frac=5e-3):
+def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max_adopt_frac=MAX_ADOPT_FRAC):
     """Replay the GPU's discrete choices in the FP64 oracle (certifying every
     difference as a near-tie) and compare the maps cell by cell."""
     L = params.max_depth
     rec = np.asarray(gpu_record).reshape(tx.count(), L + 1, 4)
-    r = orc.radio_map(scene, tx, params, mode="replay", record=rec)
+    bil = params.deposit == 1
+    r = orc.radio_map(scene, tx, params, mode="replay", record=rec, mass=bil)
     rep = r["report"]
     assert rep["failures"] == 0, rep
     adopted = rep["adopted_hit"] + rep["adopted_cell"] + rep["adopted_decision"]
@@ -18,8 +27,13 @@ def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max
     ref = r["map"]
     g = np.asarray(gpu_map, np.float64).reshape(ref.shape)
     mask = (ref > FLOOR) | (g > FLOOR)
-    rel = np.abs(g - ref)[mask] / np.maximum(ref[mask], 1e-300)
-    worst = float(rel.max()) if rel.size else 0.0
-    assert worst <= rtol, (worst, int(mask.sum()), rep)
+    err = np.abs(g - ref)[mask]
+    bound = rtol * ref[mask]
+    if bil:
+        bound = bound + WEIGHT_ATOL * r["mass"][mask]
+    rel = err / np.maximum(ref[mask], 1e-300)
+    worst = float((err / np.maximum(bound, 1e-300)).max()) if err.size else 0.0
+    assert np.all(err <= bound), (worst, float(rel.max()), int(mask.sum()), rep)
     assert np.all(g[~mask] <= FLOOR)
-    return {"worst_rel": worst, "cells": int(mask.sum()), "report": rep}
+    return {"worst_rel": float(rel.max()) if rel.size else 0.0, "worst_vs_bound": worst,
+            "cells": int(mask.sum()), "report": rep}
