@@ -221,6 +221,32 @@ rm_status rm_trace_plan_launch(rm_trace_plan* plan, void* stream);
 rm_status rm_trace_plan_stats(rm_trace_plan* plan, void* stream, rm_stats* stats_host);
 void rm_trace_plan_free(rm_trace_plan* plan);
 
+/* Same radio maps as rm_radio_map_trace, for callers that cannot allocate
+ * device memory while they run: a serving loop whose memory was reserved
+ * once at start-up and must not grow, code that owns every byte of the GPU
+ * through its own pool, or a latency-critical thread that must not wait on
+ * the allocator (cudaMalloc and cudaFree may synchronise the device).  This
+ * entry point calls no cudaMalloc, cudaFree or other allocating routine.
+ * The paper has no counterpart of it: it only changes where the tracer's
+ * scratch lives.
+ *   Scratch: one static device array of 16 KB, enough for the largest call
+ *   (RM_MAX_MATERIALS materials, RM_MAX_TX transmitters); every GPU that
+ *   loads the library holds it until the process exits.  A call that would
+ *   need more is rejected with RM_EINVAL.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (with that device current); make that first call before any stream
+ *   capture.
+ *   Sharing: every call uses the same array, which keeps the last call's
+ *   contents (each call clears what must start at zero).  Calls whose work
+ *   overlaps on the GPU race on it: issue them on one stream, or wait for
+ *   one to finish before starting the next.
+ * Arguments, outputs and errors are those of rm_radio_map_trace without the
+ * debug record; stats_host_or_null receives the counters (kernel_ms = 0).
+ * Synchronises `stream`. */
+rm_status rm_radio_map_trace_noalloc(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
+                                     const rm_trace_params* params, float* maps_dev,
+                                     rm_stats* stats_host_or_null, void* stream);
+
 /* Number of triangles / BVH nodes of a scene (host call, no device work). */
 rm_status rm_scene_info(const rm_scene* scene, int64_t* nt, int64_t* nnodes, int32_t* nm,
                         int32_t* built);

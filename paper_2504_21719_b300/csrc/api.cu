@@ -2,6 +2,7 @@
 // validation, scene and plan lifetime, per-call constant tables and launches.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -580,3 +581,84 @@ void rm_scene_free(rm_scene* sc) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of rm_radio_map_trace.
+//
+// The tracer's per-call scratch (work counter, counters, status word and the
+// material / transmitter tables) lives here in one file-scope device array
+// instead of a cudaMallocAsync block.  The array holds the largest call the
+// ABI allows (RM_MAX_MATERIALS materials, RM_MAX_TX transmitters); every
+// device that loads the library keeps it until the process exits.  Host code
+// never passes the array's name to a kernel: in host code that name is only a
+// stand-in, so its device address is looked up with cudaGetSymbolAddress,
+// once per device, with that device current, and cached.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 16384;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mutex;
+char* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+rm_status noalloc_scratch(int dev, char** out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(RM_EINVAL, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = static_cast<char*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return RM_OK;
+}
+
+}  // namespace
+
+extern "C" rm_status rm_radio_map_trace_noalloc(const rm_scene* sc, const rm_tx* tx, int32_t ntx,
+                                                const rm_trace_params* p, float* maps_dev, rm_stats* stats,
+                                                void* stream) {
+    rm_status st = validate(sc, tx, ntx, p);
+    if (st != RM_OK) return st;
+    if ((st = check_device(sc)) != RM_OK) return st;
+    if (!maps_dev) return fail(RM_EINVAL, "maps_dev is NULL");
+    Prepared P;
+    prepare(sc, tx, ntx, p, nullptr, &P);
+    size_t o_mat, o_tx;
+    const size_t bytes = table_bytes(P, &o_mat, &o_tx);
+    if (bytes > NOALLOC_SCRATCH_BYTES)
+        return fail(RM_EINVAL, "call needs " + std::to_string(bytes) + " bytes of scratch; the static scratch of "
+                               "rm_radio_map_trace_noalloc holds " + std::to_string(NOALLOC_SCRATCH_BYTES));
+    char* dev = nullptr;
+    if ((st = noalloc_scratch(sc->device, &dev)) != RM_OK) return st;
+    const bool debug = (p->flags & RM_STATS) != 0;
+    Scratch host;
+    cudaError_t e = cudaSuccess;
+    int grid = 0;
+    do {
+        // the array keeps the previous call's contents: clear the counters and status
+        if ((e = cudaMemsetAsync(dev, 0, sizeof(Scratch), S(stream))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(dev + o_mat, P.mats.data(), P.mats.size() * sizeof(MatDev),
+                                 cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice,
+                                 S(stream))) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(maps_dev, 0, sizeof(float) * P.a.ncell * ntx, S(stream))) != cudaSuccess) break;
+        P.a.mats = reinterpret_cast<const MatDev*>(dev + o_mat);
+        P.a.tx = reinterpret_cast<const TxDev*>(dev + o_tx);
+        P.a.scratch = reinterpret_cast<Scratch*>(dev);
+        P.a.maps = maps_dev;
+        if (P.a.total > 0 &&
+            (e = launch_trace(P.a, P.npol, debug, P.bilinear, false, P.block, P.bps, S(stream), &grid)) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpyAsync(&host, dev, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
+    } while (false);
+    const cudaError_t es = cudaStreamSynchronize(S(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rm_radio_map_trace_noalloc");
+    if (es != cudaSuccess) return cuda_fail(es, "cudaStreamSynchronize");
+    if (stats) fill_stats(host, P, stats);
+    if (host.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow; affected rays were dropped");
+    return RM_OK;
+}
+
