@@ -138,14 +138,8 @@ def profiled_traffic():
 
 
 def tuned(gpu_name: str, key: str):
-    try:
-        t = json.load(open(os.path.join(ROOT, "paper_2504_21719_b300", "tuning.json")))
-        e = t.get(gpu_name, {}).get(key) or t.get("default", {}).get(key)
-        if e:
-            return int(e["block_size"]), int(e["blocks_per_sm"])
-    except Exception:
-        pass
-    return 0, 0
+    from paper_2504_21719_b300.autotune import lookup
+    return lookup(gpu_name, key)
 
 
 def oracle_sample(target_s: float = 15.0, max_rays: int = 10_000_000):
@@ -191,8 +185,8 @@ def run_ours(args, world, rank, local):
     tx = txs[0]
     if args.rays:
         tx.num_rays = args.rays
-    blk, bps = tuned(gpu_name, "manhattan")
-    params = api.params_from(p, block_size=blk, blocks_per_sm=bps)
+    blk, bps, qch = tuned(gpu_name, "manhattan")
+    params = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch)
     gs = api.Scene.from_obj(sc)
     maps = torch.empty((1, p.ny, p.nx), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -291,7 +285,8 @@ def run_ours(args, world, rank, local):
                    "triangles": sc.nt, "segments_per_step": int(seg_step),
                    "nodes_per_segment": round(sum(nodes) / sum(segs), 2),
                    "tris_per_segment": round(sum(tris) / sum(segs), 2), "block_size": blk or 128,
-                   "blocks_per_sm": bps or "max occupancy", "l2": "flushed between timed steps (256 MB write)",
+                   "blocks_per_sm": bps or "max occupancy", "queue_chunk": qch or 1, "tuned": bool(blk),
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
         "clocks": clk, "extra": extra,
@@ -306,9 +301,9 @@ def run_extra(api, S, torch, gpu_name):
     """Batched 64-TX form and forward+adjoint of the differentiable workload."""
     out = {}
     sc, txs, p = S.workload(3)
-    blk, bps = tuned(gpu_name, "batched")
+    blk, bps, qch = tuned(gpu_name, "batched")
     gs = api.Scene.from_obj(sc)
-    prm = api.params_from(p, block_size=blk, blocks_per_sm=bps)
+    prm = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch)
     maps = torch.empty((len(txs), p.ny, p.nx), dtype=torch.float32, device="cuda")
     plan = api.TracePlan(gs, txs, prm, maps)
     for _ in range(3):
@@ -354,6 +349,27 @@ def run_extra(api, S, torch, gpu_name):
     out["differentiable"] = {"fwd_kernel_ms": round(fk, 3), "adj_call_ms": round(statistics.mean(b_ms), 3),
                              "fwd_plus_adj_over_fwd": round((fk + statistics.mean(b_ms)) / fk, 3),
                              "fwd_value": round(segs / (fk / 1e3), 1), "unit": UNIT}
+    gs.free()
+
+    # large city: 0.97M triangles, 16 TX x 1e8 rays, depth 8, one launch each way
+    sc, txs, p = S.workload(5)
+    gs = api.Scene.from_obj(sc)
+    blk, bps, qch = tuned(gpu_name, "city")
+    p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch)
+    small = [S.Tx(pos=txs[0].pos, num_rays=1_000_000, seed=txs[0].seed)]
+    api.trace(gs, small, p)
+    f = api.trace(gs, txs, p)
+    g = torch.full_like(f["maps"], 1.0 / f["maps"].numel())
+    a = api.grad(gs, txs, p, g)
+    fk, ak = f["stats"]["kernel_ms"], a["stats"]["kernel_ms"]
+    segs = f["stats"]["segments"]
+    out["large_city"] = {"triangles": sc.nt, "rays": f["stats"]["rays"], "segments": segs,
+                         "fwd_kernel_ms": round(fk, 1), "fwd_value": round(segs / (fk / 1e3), 1),
+                         "adj_kernel_ms": round(ak, 1), "adj_value": round(segs / (ak / 1e3), 1),
+                         "fwd_plus_adj_over_fwd": round((fk + ak) / fk, 3), "unit": UNIT,
+                         "nodes_per_segment": round(f["stats"]["nodes_visited"] / segs, 2),
+                         "tris_per_segment": round(f["stats"]["tris_tested"] / segs, 2)}
+    del f, a, g
     gs.free()
     return out
 

@@ -100,7 +100,8 @@ typedef struct {
     int32_t deposit;         /* 0: box cells (the paper's estimator); 1: bilinear (tent) splat */
     int32_t block_size;      /* threads per block of the tracer; 0 = tuned default */
     int32_t blocks_per_sm;   /* resident blocks per SM of the persistent grid; 0 = tuned default */
-    int32_t reserved;
+    int32_t queue_chunk;     /* work items a warp takes per work-queue access, in units of 32 (1..64);
+                                0 = default (1) */
 } rm_trace_params;
 
 /* Counters of one trace call, summed over all transmitters. */

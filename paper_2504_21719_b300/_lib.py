@@ -35,7 +35,7 @@ class rm_trace_params(C.Structure):
     _fields_ = [("freq_hz", C.c_double), ("max_depth", C.c_int32), ("flags", C.c_uint32),
                 ("map_origin", C.c_float * 3), ("cell_size", C.c_float), ("nx", C.c_int32),
                 ("ny", C.c_int32), ("deposit", C.c_int32), ("block_size", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("reserved", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("queue_chunk", C.c_int32)]
 
 
 _D = RM_MAX_DEPTH + 1

@@ -64,7 +64,7 @@ def tx_from(obj) -> L.rm_tx:
 
 def params_struct(freq_hz, max_depth, map_origin=(0.0, 0.0, 1.5), cell_size=1.0, nx=100, ny=100,
                   reflect=True, refract=True, los=True, stats=False, deposit=0, block_size=0,
-                  blocks_per_sm=0) -> L.rm_trace_params:
+                  blocks_per_sm=0, queue_chunk=0) -> L.rm_trace_params:
     p = L.rm_trace_params()
     p.freq_hz = float(freq_hz)
     p.max_depth = int(max_depth)
@@ -74,13 +74,13 @@ def params_struct(freq_hz, max_depth, map_origin=(0.0, 0.0, 1.5), cell_size=1.0,
         p.map_origin[i] = float(map_origin[i])
     p.cell_size = float(cell_size)
     p.nx, p.ny, p.deposit = int(nx), int(ny), int(deposit)
-    p.block_size, p.blocks_per_sm = int(block_size), int(blocks_per_sm)
+    p.block_size, p.blocks_per_sm, p.queue_chunk = int(block_size), int(blocks_per_sm), int(queue_chunk)
     return p
 
 
-def params_from(obj, stats=False, block_size=0, blocks_per_sm=0) -> L.rm_trace_params:
+def params_from(obj, stats=False, block_size=0, blocks_per_sm=0, queue_chunk=0) -> L.rm_trace_params:
     return params_struct(obj.freq_hz, obj.max_depth, obj.map_origin, obj.cell_size, obj.nx, obj.ny, obj.reflect,
-                         obj.refract, obj.los, stats, obj.deposit, block_size, blocks_per_sm)
+                         obj.refract, obj.los, stats, obj.deposit, block_size, blocks_per_sm, queue_chunk)
 
 
 def _tx_array(txs):

@@ -96,6 +96,7 @@ rm_status validate(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_tr
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > MAX_BLOCK || (p->block_size & 31)))
         return fail(RM_EINVAL, "block_size must be 0 or a multiple of 32 in [32, 256]");
     if (p->blocks_per_sm < 0) return fail(RM_EINVAL, "blocks_per_sm must be >= 0");
+    if (p->queue_chunk < 0 || p->queue_chunk > 64) return fail(RM_EINVAL, "queue_chunk must be in [0, 64]");
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(p->map_origin[i])) return fail(RM_EINVAL, "map_origin must be finite");
     for (int t = 0; t < ntx; ++t) {
@@ -242,6 +243,7 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
     A.inv_eps0_omega = (float)(1.0 / (EPS0 * omega));
     A.same_sampling = same ? 1 : 0;
     A.total = work;
+    A.qchunk = 32ULL * (unsigned long long)(p->queue_chunk > 0 ? p->queue_chunk : 1);
     A.ncell = (unsigned long long)p->nx * p->ny;
     P->npol = tx[0].pol == 2 ? 2 : 1;
     P->bilinear = p->deposit == 1;

@@ -63,6 +63,7 @@ struct TraceArgs {
     float inv_eps0_omega;        // 1 / (eps0 omega): d eta / d sigma = -j / (eps0 omega)
     int32_t same_sampling;
     unsigned long long total;    // work items (sum of ray counts)
+    unsigned long long qchunk;   // work items a warp takes per queue access (multiple of 32)
     unsigned long long ncell;    // nx * ny
     const MatDev* mats;          // [nm]
     const TxDev* tx;             // [ntx]

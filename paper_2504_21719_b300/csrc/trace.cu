@@ -357,6 +357,8 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
     const bool stats = DEBUG && (A.flags & RM_STATS);
     // ray state
     bool active = false, exhausted = false;
+    // warp-local work queue [qb, qe) (warp-uniform), refilled A.qchunk items at a time
+    unsigned long long qb = 0, qe = 0;
     Ray r{0, 0, 0, 0, 0, 1};
     cf E[NPOL][3];
     float inv_pr = 1.0f;
@@ -372,15 +374,26 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
 
     while (true) {
         // ---------------- refill free lanes (one atomic per warp) ----------------
-        if (!exhausted) {
-            const unsigned need = __ballot_sync(FULL_MASK, !active);
-            if (need) {
-                unsigned long long b = 0;
-                if (lane == 0) b = atomicAdd(&A.scratch->next, (unsigned long long)__popc(need));
+        const unsigned need = __ballot_sync(FULL_MASK, !active);
+        if (need && !(exhausted && qb >= qe)) {
+            const unsigned long long nneed = (unsigned long long)__popc(need);
+            const unsigned long long rem = qe - qb;
+            unsigned long long b = 0;
+            const bool fetch = rem < nneed && !exhausted;
+            if (fetch) {
+                if (lane == 0) b = atomicAdd(&A.scratch->next, A.qchunk);
                 b = __shfl_sync(FULL_MASK, b, 0);
-                if (b + __popc(need) >= A.total) exhausted = true;
+                if (b + A.qchunk >= A.total) exhausted = true;
+            }
+            // lane rank r takes the r-th item of (rest of the local queue, then the new chunk)
+            const unsigned long long rk = (unsigned long long)__popc(need & lt);
+            const bool got_chunk = fetch && b < A.total;
+            const unsigned long long ce = got_chunk ? min(b + A.qchunk, A.total) : b;
+            {
                 if (!active) {
-                    const unsigned long long w = b + __popc(need & lt);
+                    unsigned long long w = ~0ULL;
+                    if (rk < rem) w = qb + rk;
+                    else if (got_chunk && b + (rk - rem) < ce) w = b + (rk - rem);
                     if (w < A.total) {
                         // transmitter of item w (work_begin ascending)
                         int lo = 0, hi = A.ntx - 1;
@@ -440,6 +453,16 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                         }
                     }
                 }
+            }
+            // advance the warp-local queue (identical on every lane)
+            if (rem >= nneed) {
+                qb += nneed;
+            } else if (got_chunk) {
+                const unsigned long long used = nneed - rem;
+                qb = min(b + used, ce);
+                qe = ce;
+            } else {
+                qb = qe;
             }
         }
         if (__ballot_sync(FULL_MASK, active) == 0) break;

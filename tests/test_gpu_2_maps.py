@@ -213,3 +213,29 @@ def test_upload_rejects_bad_indices(api):
     bad2 = S.Scene("bad2", sc.verts, sc.tris, sc.tri_mat + 1, sc.mats)
     with pytest.raises(api.RmError):
         api.Scene.from_obj(bad2)
+
+
+def test_large_city_sampled_and_partition(orc, api):
+    """Procedural city (0.97M triangles), depth 8, 2048 x 2048 maps: a sampled
+    lattice subset of one transmitter is replayed by the oracle (brute force
+    over every triangle); at full size (16 TX x 1e8 rays in one launch) the
+    maps equal the sum of two disjoint halves."""
+    sc, txs, p = S.workload(5)
+    gs = api.Scene.from_obj(sc)
+    sub = copy.copy(txs[0])
+    sub.ray_stride, sub.ray_begin = 333_331, 7
+    r = api.trace(gs, [sub], p, record=True)
+    info = compare_maps(orc, sc, sub, p, r["maps"][0].cpu().numpy(), r["record"].cpu().numpy())
+    assert info["cells"] > 100
+    full = api.trace(gs, txs, p)
+    assert full["stats"]["rays"] == 16 * 100_000_000
+    parts = torch.zeros_like(full["maps"], dtype=torch.float64)
+    for b in range(2):
+        half = [copy.copy(t) for t in txs]
+        for t in half:
+            t.ray_begin, t.ray_stride = b, 2
+        parts += api.trace(gs, half, p)["maps"].double()
+    fm = full["maps"].double()
+    mask = fm > FLOOR
+    assert torch.all((parts - fm).abs()[mask] <= 2e-5 * fm[mask])
+    gs.free()
