@@ -170,8 +170,9 @@ rm_status rm_bvh_export(const rm_scene* scene, uint64_t* keys_host, int32_t* ord
 
 /* Traces the radio maps of ntx transmitters (1 <= ntx <= RM_MAX_TX) in one
  * persistent launch whose work queue hands out (transmitter, ray) items, and
- * writes maps_dev [ntx][ny][nx] (overwritten; FP32 atomics, so the order of
- * additions, and the last bits, vary between runs).  Each map is the
+ * writes maps_dev [ntx][ny][nx] (overwritten).  Deposits are accumulated in an
+ * internal FP64 map (a cell under a transmitter can receive ~1e5 of them) and
+ * rounded once to FP32; the order of the atomic additions varies between runs.  Each map is the
  * estimator of Eq. radio-map-solver-ci-all-2-estimator for its transmitter.
  * stats_host_or_null receives the counters.  record_dev_or_null receives one
  * rm_segment_record per (tx, ray, depth).  Synchronises `stream` before
@@ -243,6 +244,8 @@ void rm_trace_plan_free(rm_trace_plan* plan);
  *   one to finish before starting the next.
  * Arguments, outputs and errors are those of rm_radio_map_trace without the
  * debug record; stats_host_or_null receives the counters (kernel_ms = 0).
+ * Deposits are accumulated with FP32 atomics directly in maps_dev (no FP64
+ * buffer), so cells that receive very many deposits carry FP32 summation error.
  * Synchronises `stream`. */
 rm_status rm_radio_map_trace_noalloc(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
                                      const rm_trace_params* params, float* maps_dev,

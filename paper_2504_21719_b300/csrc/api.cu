@@ -261,6 +261,13 @@ size_t table_bytes(const Prepared& P, size_t* o_mat, size_t* o_tx) {
     return off;
 }
 
+// the same block followed by the FP64 accumulation maps [ntx][ny][nx]
+size_t block_bytes_with_maps64(const Prepared& P, size_t* o_mat, size_t* o_tx, size_t* o_m64) {
+    const size_t t = table_bytes(P, o_mat, o_tx);
+    *o_m64 = (t + 255) & ~size_t(255);
+    return *o_m64 + sizeof(double) * P.a.ncell * P.tx.size();
+}
+
 void fill_stats(const Scratch& h, const Prepared& P, rm_stats* st) {
     std::memset(st, 0, sizeof *st);
     st->rays = h.cnt[0];
@@ -296,8 +303,8 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
     Prepared P;
     prepare(sc, tx, ntx, p, smats, &P);
     const bool debug = record != nullptr || (p->flags & RM_STATS);
-    size_t o_mat, o_tx;
-    const size_t bytes = table_bytes(P, &o_mat, &o_tx);
+    size_t o_mat, o_tx, o_m64 = 0;
+    const size_t bytes = adjoint ? table_bytes(P, &o_mat, &o_tx) : block_bytes_with_maps64(P, &o_mat, &o_tx, &o_m64);
     cudaEvent_t ev[2];
     RM_CUDA(cudaEventCreate(&ev[0]));
     RM_CUDA(cudaEventCreate(&ev[1]));
@@ -313,7 +320,8 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
                                  cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice,
                                  S(stream))) != cudaSuccess) break;
-        if (!adjoint && (e = cudaMemsetAsync(maps, 0, sizeof(float) * P.a.ncell * ntx, S(stream))) != cudaSuccess) break;
+        if (!adjoint && (e = cudaMemsetAsync(dev + o_m64, 0, sizeof(double) * P.a.ncell * ntx, S(stream))) != cudaSuccess)
+            break;
         unsigned long long nrec = 0;
         for (const TxDev& t : P.tx) nrec += t.count * (unsigned long long)(p->max_depth + 1);
         if (record && (e = launch_fill_record(record, nrec, S(stream))) != cudaSuccess) break;
@@ -321,6 +329,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         P.a.tx = reinterpret_cast<const TxDev*>(dev + o_tx);
         P.a.scratch = reinterpret_cast<Scratch*>(dev);
         P.a.maps = maps;
+        P.a.maps64 = adjoint ? nullptr : reinterpret_cast<double*>(dev + o_m64);
         P.a.dLdC = dLdC;
         P.a.record = record;
         if (P.a.total > 0) {
@@ -333,6 +342,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         }
         if (adjoint && (e = launch_grad_out(reinterpret_cast<const Scratch*>(dev)->grad, sc->nm, ntx, d_eps, d_sig,
                                             d_tx, S(stream))) != cudaSuccess) break;
+        if (!adjoint && (e = launch_map_to_f32(P.a.maps64, maps, P.a.ncell * ntx, S(stream))) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(&host, dev, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
     } while (false);
     cudaError_t e2 = cudaFreeAsync(dev, S(stream));
@@ -499,8 +509,8 @@ rm_status rm_trace_plan_create(const rm_scene* sc, const rm_tx* tx, int32_t ntx,
     if (p->flags & RM_STATS) return fail(RM_EINVAL, "RM_STATS is not available in a plan");
     Prepared P;
     prepare(sc, tx, ntx, p, nullptr, &P);
-    size_t o_mat, o_tx;
-    const size_t bytes = table_bytes(P, &o_mat, &o_tx);
+    size_t o_mat, o_tx, o_m64;
+    const size_t bytes = block_bytes_with_maps64(P, &o_mat, &o_tx, &o_m64);
     rm_trace_plan* pl = new rm_trace_plan();
     pl->ntx = ntx;
     pl->L = p->max_depth;
@@ -517,15 +527,17 @@ rm_status rm_trace_plan_create(const rm_scene* sc, const rm_tx* tx, int32_t ntx,
     P.a.tx = reinterpret_cast<const TxDev*>(pl->dev + o_tx);
     P.a.scratch = pl->scratch;
     P.a.maps = maps_dev;
+    P.a.maps64 = reinterpret_cast<double*>(pl->dev + o_m64);
     cudaStream_t cap;
     if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
     cudaError_t ec = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (ec == cudaSuccess) {
         cudaError_t ek = cudaMemsetAsync(pl->dev, 0, sizeof(Scratch), cap);
-        if (ek == cudaSuccess) ek = cudaMemsetAsync(maps_dev, 0, sizeof(float) * P.a.ncell * ntx, cap);
+        if (ek == cudaSuccess) ek = cudaMemsetAsync(P.a.maps64, 0, sizeof(double) * P.a.ncell * ntx, cap);
         int grid = 0;
         if (ek == cudaSuccess && P.a.total > 0)
             ek = launch_trace(P.a, P.npol, false, P.bilinear, false, P.block, P.bps, cap, &grid);
+        if (ek == cudaSuccess) ek = launch_map_to_f32(P.a.maps64, maps_dev, P.a.ncell * ntx, cap);
         ec = cudaStreamEndCapture(cap, &pl->graph);
         if (ek != cudaSuccess) ec = ek;
     }

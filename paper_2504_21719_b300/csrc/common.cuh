@@ -68,7 +68,8 @@ struct TraceArgs {
     const MatDev* mats;          // [nm]
     const TxDev* tx;             // [ntx]
     Scratch* scratch;
-    float* maps;                 // [ntx][ny][nx] (forward)
+    float* maps;                 // [ntx][ny][nx] (forward, FP32 accumulation when maps64 is null)
+    double* maps64;              // [ntx][ny][nx] FP64 accumulation buffer (forward), or null
     const float* dLdC;           // [ntx][ny][nx] (adjoint)
     rm_segment_record* record;   // optional
 };
@@ -97,6 +98,7 @@ cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t n
 cudaError_t launch_db_mse(const float* maps, const float* target, int64_t n, float floor_lin,
                           double* acc_dev, float* loss, float* dLdC, int64_t* valid, cudaStream_t s);
 cudaError_t launch_fill_record(rm_segment_record* rec, unsigned long long n, cudaStream_t s);
+cudaError_t launch_map_to_f32(const double* m64, float* m, unsigned long long n, cudaStream_t s);
 cudaError_t launch_grad_out(const double* grad, int nm, int ntx, float* d_eps, float* d_sigma, float* d_tx,
                             cudaStream_t s);
 

@@ -76,7 +76,20 @@ __global__ void k_fill_record(rm_segment_record* r, unsigned long long n) {
         r[i] = rm_segment_record{-2, NO_CELL, NO_CELL, -1};
 }
 
+__global__ void k_map_to_f32(const double* __restrict__ m64, float* __restrict__ m, unsigned long long n) {
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        m[i] = (float)m64[i];
+}
+
 }  // namespace
+
+cudaError_t launch_map_to_f32(const double* m64, float* m, unsigned long long n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned long long b = (n + 255) / 256;
+    k_map_to_f32<<<(unsigned)(b < 8192 ? b : 8192), 256, 0, s>>>(m64, m, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_db_mse(const float* maps, const float* target, int64_t n, float floor_lin, double* acc,
                           float* loss, float* dLdC, int64_t* valid, cudaStream_t s) {

@@ -380,15 +380,17 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
             const unsigned long long rem = qe - qb;
             unsigned long long b = 0;
             const bool fetch = rem < nneed && !exhausted;
+            // queue chunk of one warp (the default): take exactly the items the free lanes need
+            const unsigned long long take = A.qchunk > 32ULL ? A.qchunk : nneed;
             if (fetch) {
-                if (lane == 0) b = atomicAdd(&A.scratch->next, A.qchunk);
+                if (lane == 0) b = atomicAdd(&A.scratch->next, take);
                 b = __shfl_sync(FULL_MASK, b, 0);
-                if (b + A.qchunk >= A.total) exhausted = true;
+                if (b + take >= A.total) exhausted = true;
             }
             // lane rank r takes the r-th item of (rest of the local queue, then the new chunk)
             const unsigned long long rk = (unsigned long long)__popc(need & lt);
             const bool got_chunk = fetch && b < A.total;
-            const unsigned long long ce = got_chunk ? min(b + A.qchunk, A.total) : b;
+            const unsigned long long ce = got_chunk ? min(b + take, A.total) : b;
             {
                 if (!active) {
                     unsigned long long w = ~0ULL;
@@ -542,17 +544,23 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                 }
                 const unsigned peers = __match_any_sync(FULL_MASK, key);
                 if (key != ~0ULL) {
-                    if (__popc(peers) == 1) {
-                        atomicAdd(A.maps + key, v);
-                    } else {
+                    float sum = v;
+                    bool leader = true;
+                    if (__popc(peers) > 1) {
                         s_agg[tid] = v;
                         __syncwarp(peers);
-                        if (lane == __ffs(peers) - 1) {
-                            float sum = 0.0f;
+                        leader = lane == __ffs(peers) - 1;
+                        if (leader) {
+                            sum = 0.0f;
                             for (unsigned m = peers; m; m &= m - 1) sum += s_agg[(warp << 5) + __ffs(m) - 1];
-                            atomicAdd(A.maps + key, sum);
                         }
                         __syncwarp(peers);
+                    }
+                    // FP64 reduction (no return value): a cell may receive ~1e5 deposits,
+                    // which FP32 accumulation would round to ~1e-2
+                    if (leader) {
+                        if (A.maps64) atomicAdd(A.maps64 + key, (double)sum);
+                        else atomicAdd(A.maps + key, sum);
                     }
                 }
             }
