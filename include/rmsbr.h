@@ -156,15 +156,19 @@ rm_status rm_scene_set_materials(rm_scene* scene, const rm_material* mats_host, 
 /* Builds the LBVH on `stream`: 63-bit Morton codes of the doubled triangle
  * centroids, a stable 8-bit-digit radix sort, the Karras (HPG 2012) binary
  * radix tree with duplicate keys ordered by position, an exact AABB refit,
- * and the 64-byte two-child node layout.  Not part of the paper (its
+ * and the 64-byte two-child node layout.  Up to 16 triangles as large as a
+ * quarter of the scene are kept out of the tree (see rm_bvh_export).  Not part of the paper (its
  * implementation uses Mitsuba's acceleration structure).  Must precede
  * tracing; may be called again after rm_scene_upload only. */
 rm_status rm_bvh_build(rm_scene* scene, void* stream);
 
 /* Exports the built tree for inspection (synchronous).  Host outputs:
  * keys [nt] sorted Morton codes, order [nt] sorted triangle ids,
- * child [nt-1][2] (>= 0 internal node, < 0 leaf ~position),
- * child_aabb [nt-1][2][6] (lo xyz, hi xyz of each child). */
+ * child [nn][2] (>= 0 internal node, < 0 leaf ~position),
+ * child_aabb [nn][2][6] (lo xyz, hi xyz of each child), nn = nodes from
+ * rm_scene_info.  Triangles whose largest AABB extent is at least a quarter
+ * of the scene's (at most 16 of them) are not in the tree: their key is
+ * 2^64 - 1, they end `order`, and the tracer tests them from a list. */
 rm_status rm_bvh_export(const rm_scene* scene, uint64_t* keys_host, int32_t* order_host,
                         int32_t* child_host, float* child_aabb_host);
 
@@ -251,7 +255,7 @@ rm_status rm_radio_map_trace_noalloc(const rm_scene* scene, const rm_tx* tx_host
                                      const rm_trace_params* params, float* maps_dev,
                                      rm_stats* stats_host_or_null, void* stream);
 
-/* Number of triangles / BVH nodes of a scene (host call, no device work). */
+/* Number of triangles / internal BVH nodes of a scene (host call, no device work). */
 rm_status rm_scene_info(const rm_scene* scene, int64_t* nt, int64_t* nnodes, int32_t* nm,
                         int32_t* built);
 

@@ -85,9 +85,9 @@ def lib():
         _lib.or_grad.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, P, P, P]
         _lib.or_branch_all.restype = C.c_int
         _lib.or_branch_all.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, P, P, P]
-        _lib.or_morton.argtypes = [P, P, C.c_int64, P, P]
+        _lib.or_morton.argtypes = [P, P, C.c_int64, P, P, P]
         _lib.or_lbvh.restype = C.c_int
-        _lib.or_lbvh.argtypes = [P, P, C.c_int64, P, P, P, P]
+        _lib.or_lbvh.argtypes = [P, P, C.c_int64, P, P, P, P, P]
         _lib.or_num_threads.restype = C.c_int
     return _lib
 
@@ -296,21 +296,26 @@ def branch_all(scene, tx, params):
 
 
 def morton(scene):
+    """(keys [nt] with 2^64-1 for large triangles, AABBs [nt, 6], number of large triangles)."""
     v, t, _, _ = _scene_arrays(scene)
     keys = np.empty(len(t), np.uint64)
     box = np.empty((len(t), 6), np.float32)
-    lib().or_morton(_p(v), _p(t), len(t), _p(keys), _p(box))
-    return keys, box
+    nl = C.c_int64(0)
+    lib().or_morton(_p(v), _p(t), len(t), _p(keys), _p(box), C.byref(nl))
+    return keys, box, int(nl.value)
 
 
 def lbvh(scene):
-    """Reference LBVH: sorted keys, order, child [nt-1, 2], child AABBs [nt-1, 2, 6]."""
+    """Reference LBVH: sorted keys, order, nlarge, child [ns-1, 2], child AABBs [ns-1, 2, 6]
+    with ns = nt - nlarge (the large triangles are the last nlarge entries of order)."""
     v, t, _, _ = _scene_arrays(scene)
     nt = len(t)
     keys = np.zeros(max(nt, 1), np.uint64)
     order = np.zeros(max(nt, 1), np.int32)
     child = np.zeros((max(nt - 1, 1), 2), np.int32)
     box = np.zeros((max(nt - 1, 1), 2, 6), np.float32)
-    lib().or_lbvh(_p(v), _p(t), nt, _p(keys), _p(order), _p(child), _p(box))
-    return {"keys": keys[:nt], "order": order[:nt], "child": child[:max(nt - 1, 0)],
-            "child_aabb": box[:max(nt - 1, 0)]}
+    nl = C.c_int64(0)
+    lib().or_lbvh(_p(v), _p(t), nt, _p(keys), _p(order), _p(child), _p(box), C.byref(nl))
+    ns = nt - int(nl.value)
+    return {"keys": keys[:nt], "order": order[:nt], "nlarge": int(nl.value), "child": child[:max(ns - 1, 0)],
+            "child_aabb": box[:max(ns - 1, 0)]}

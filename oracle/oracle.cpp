@@ -1321,30 +1321,68 @@ inline int clz64(uint64_t x) { return x ? __builtin_clzll(x) : 64; }
 inline int clz32(uint32_t x) { return x ? __builtin_clz(x) : 32; }
 }  // namespace
 
+// Large triangles (the ground of a city) would inflate every box on their
+// path to the root; they are kept out of the tree and tested from a short
+// list instead.  A triangle is large when its largest AABB extent is at
+// least a quarter of the scene AABB's largest extent (FP32: extents are
+// hi - lo, the threshold 0.25f * scene extent), unless more than 16 are, in
+// which case none is.  Large triangles get the key 2^64 - 1 (after every
+// Morton code) and take no part in the Morton bounds.
+constexpr int MAX_LARGE = 16;
+
 void or_morton(const float* verts, const int32_t* tris, int64_t nt, uint64_t* keys_out,
-               float* aabb_out /* [nt][6] lo, hi */) {
-    std::vector<float> c2(3 * nt);
-    float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+               float* aabb_out /* [nt][6] lo, hi */, int64_t* nlarge_out) {
+    std::vector<float> c2(3 * nt), box(6 * nt);
+    float slo[3] = {INFINITY, INFINITY, INFINITY}, shi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t i = 0; i < nt; ++i) {
-        float lo[3], hi[3];
         for (int a = 0; a < 3; ++a) {
             float v0 = verts[3 * tris[3 * i] + a], v1 = verts[3 * tris[3 * i + 1] + a],
                   v2 = verts[3 * tris[3 * i + 2] + a];
-            lo[a] = std::min(v0, std::min(v1, v2));
-            hi[a] = std::max(v0, std::max(v1, v2));
-            volatile float s = lo[a] + hi[a];
+            float lo = std::min(v0, std::min(v1, v2));
+            float hi = std::max(v0, std::max(v1, v2));
+            box[6 * i + a] = lo;
+            box[6 * i + 3 + a] = hi;
+            volatile float s = lo + hi;
             c2[3 * i + a] = s;
-            cmin[a] = std::min(cmin[a], (float)s);
-            cmax[a] = std::max(cmax[a], (float)s);
-            if (aabb_out) { aabb_out[6 * i + a] = lo[a]; aabb_out[6 * i + 3 + a] = hi[a]; }
+            slo[a] = std::min(slo[a], lo);
+            shi[a] = std::max(shi[a], hi);
         }
     }
+    if (aabb_out) std::memcpy(aabb_out, box.data(), sizeof(float) * 6 * nt);
+    auto extent = [](const float* lo, const float* hi) {
+        volatile float ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+        return std::max(std::max((float)ex, (float)ey), (float)ez);
+    };
+    const float es = nt > 0 ? extent(slo, shi) : 0.0f;
+    volatile float thr = 0.25f * es;
+    std::vector<char> large(nt, 0);
+    int64_t nl = 0;
+    for (int64_t i = 0; i < nt; ++i) {
+        large[i] = extent(&box[6 * i], &box[6 * i + 3]) >= (float)thr;
+        nl += large[i];
+    }
+    if (nl > MAX_LARGE) {
+        std::fill(large.begin(), large.end(), 0);
+        nl = 0;
+    }
+    if (nlarge_out) *nlarge_out = nl;
+    float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nt; ++i)
+        if (!large[i])
+            for (int a = 0; a < 3; ++a) {
+                cmin[a] = std::min(cmin[a], c2[3 * i + a]);
+                cmax[a] = std::max(cmax[a], c2[3 * i + a]);
+            }
     float scale[3];
     for (int a = 0; a < 3; ++a) {
         volatile float e = cmax[a] - cmin[a];
         scale[a] = (e > 0.0f) ? (float)(2097151.0f / (float)e) : 0.0f;
     }
     for (int64_t i = 0; i < nt; ++i) {
+        if (large[i]) {
+            keys_out[i] = ~0ULL;
+            continue;
+        }
         uint32_t q[3];
         for (int a = 0; a < 3; ++a) {
             volatile float d = c2[3 * i + a] - cmin[a];
@@ -1356,20 +1394,26 @@ void or_morton(const float* verts, const int32_t* tris, int64_t nt, uint64_t* ke
     }
 }
 
-// Outputs: sorted keys [nt], sorted triangle ids [nt], for each internal node
-// i < nt-1: child[2] (>= 0 internal, < 0 = ~leaf position) and the two child
-// AABBs [2][6] (lo xyz, hi xyz).
-int or_lbvh(const float* verts, const int32_t* tris, int64_t nt, uint64_t* keys_sorted,
-            int32_t* order, int32_t* child, float* child_aabb) {
-    if (nt <= 0) return 0;
-    std::vector<uint64_t> keys(nt);
-    std::vector<float> box(6 * nt);
-    or_morton(verts, tris, nt, keys.data(), box.data());
-    std::vector<int32_t> idx(nt);
-    for (int64_t i = 0; i < nt; ++i) idx[i] = (int32_t)i;
+// Outputs: sorted keys [nt] (the large triangles last, key 2^64 - 1), sorted
+// triangle ids [nt], the number of large triangles, and for each internal
+// node i < ns-1 of the tree over the ns = nt - nlarge others: child[2]
+// (>= 0 internal, < 0 = ~leaf position) and the two child AABBs [2][6]
+// (lo xyz, hi xyz).
+int or_lbvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t* keys_sorted,
+            int32_t* order, int32_t* child, float* child_aabb, int64_t* nlarge_out) {
+    if (nlarge_out) *nlarge_out = 0;
+    if (nt_all <= 0) return 0;
+    std::vector<uint64_t> keys(nt_all);
+    std::vector<float> box(6 * nt_all);
+    int64_t nl = 0;
+    or_morton(verts, tris, nt_all, keys.data(), box.data(), &nl);
+    if (nlarge_out) *nlarge_out = nl;
+    std::vector<int32_t> idx(nt_all);
+    for (int64_t i = 0; i < nt_all; ++i) idx[i] = (int32_t)i;
     std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return keys[a] < keys[b]; });
-    for (int64_t i = 0; i < nt; ++i) { order[i] = idx[i]; keys_sorted[i] = keys[idx[i]]; }
-    if (nt == 1) return 0;
+    for (int64_t i = 0; i < nt_all; ++i) { order[i] = idx[i]; keys_sorted[i] = keys[idx[i]]; }
+    const int64_t nt = nt_all - nl;  // the tree covers sorted positions [0, nt)
+    if (nt <= 1) return 0;
     auto delta = [&](int64_t i, int64_t j) -> int {
         if (keys_sorted[i] != keys_sorted[j]) return clz64(keys_sorted[i] ^ keys_sorted[j]);
         return 64 + clz32((uint32_t)i ^ (uint32_t)j);

@@ -135,17 +135,25 @@ class Scene:
         self._smats = sm
         _check(L.load().rm_scene_set_materials(self.handle, self._mats, self.nm, sm), "rm_scene_set_materials")
 
+    def info(self):
+        nt, nn, nm, built = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
+        _check(L.load().rm_scene_info(self.handle, C.byref(nt), C.byref(nn), C.byref(nm), C.byref(built)),
+               "rm_scene_info")
+        return {"nt": nt.value, "nodes": nn.value, "nm": nm.value, "built": bool(built.value)}
+
     def export_bvh(self):
         n = self.nt
+        nn = self.info()["nodes"]
         keys = np.zeros(max(n, 1), np.uint64)
         order = np.zeros(max(n, 1), np.int32)
-        child = np.zeros((max(n - 1, 1), 2), np.int32)
-        box = np.zeros((max(n - 1, 1), 2, 6), np.float32)
+        child = np.zeros((max(nn, 1), 2), np.int32)
+        box = np.zeros((max(nn, 1), 2, 6), np.float32)
         _check(L.load().rm_bvh_export(self.handle, keys.ctypes.data_as(C.c_void_p), order.ctypes.data_as(C.c_void_p),
                                       child.ctypes.data_as(C.c_void_p), box.ctypes.data_as(C.c_void_p)),
                "rm_bvh_export")
-        return {"keys": keys[:n], "order": order[:n], "child": child[:max(n - 1, 0)],
-                "child_aabb": box[:max(n - 1, 0)]}
+        nlarge = int((keys[:n] == np.uint64(2 ** 64 - 1)).sum())
+        return {"keys": keys[:n], "order": order[:n], "nlarge": nlarge, "child": child[:nn],
+                "child_aabb": box[:nn]}
 
     def free(self):
         if getattr(self, "handle", None):

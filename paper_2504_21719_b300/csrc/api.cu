@@ -20,6 +20,7 @@ struct rm_scene {
     std::vector<rm_material> mats, smats;
     bool has_smats = false;
     bool built = false;
+    int64_t nlarge = 0;          // triangles kept out of the tree (tested from a list)
     uint64_t* keys = nullptr;
     int32_t* order = nullptr;
     float4* nodes = nullptr;
@@ -228,7 +229,8 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
     std::memset(&A, 0, sizeof A);
     A.nodes = sc->nodes;
     A.tris = sc->trirec;
-    A.nt = (int32_t)sc->nt;
+    A.nt = (int32_t)(sc->nt - sc->nlarge);
+    A.nlarge = (int32_t)sc->nlarge;
     A.ntx = ntx;
     A.nm = sc->nm;
     A.L = p->max_depth;
@@ -437,7 +439,7 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
         RM_CUDA(cudaMalloc((void**)&sc->nodes, sizeof(float4) * 4 * (n > 1 ? n - 1 : 1)));
         RM_CUDA(cudaMalloc((void**)&sc->trirec, sizeof(float4) * 3 * n));
         BvhBuffers B{sc->verts, sc->tris, sc->tri_mat, n, sc->keys, sc->order, sc->nodes, sc->trirec};
-        RM_CUDA(build_bvh(B, S(stream)));
+        RM_CUDA(build_bvh(B, S(stream), &sc->nlarge));
         RM_CUDA(cudaStreamSynchronize(S(stream)));
     }
     sc->built = true;
@@ -454,10 +456,11 @@ rm_status rm_bvh_export(const rm_scene* sc, uint64_t* keys_host, int32_t* order_
     if (n <= 0) return RM_OK;
     if (keys_host) RM_CUDA(cudaMemcpy(keys_host, sc->keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
     if (order_host) RM_CUDA(cudaMemcpy(order_host, sc->order, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
-    if (n > 1 && (child_host || child_aabb_host)) {
-        std::vector<float4> nodes((size_t)4 * (n - 1));
-        RM_CUDA(cudaMemcpy(nodes.data(), sc->nodes, sizeof(float4) * 4 * (n - 1), cudaMemcpyDeviceToHost));
-        for (int64_t i = 0; i < n - 1; ++i) {
+    const int64_t ns = n - sc->nlarge;
+    if (ns > 1 && (child_host || child_aabb_host)) {
+        std::vector<float4> nodes((size_t)4 * (ns - 1));
+        RM_CUDA(cudaMemcpy(nodes.data(), sc->nodes, sizeof(float4) * 4 * (ns - 1), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < ns - 1; ++i) {
             const float* f = reinterpret_cast<const float*>(&nodes[4 * i]);
             if (child_host) {
                 std::memcpy(&child_host[2 * i], &f[12], sizeof(int32_t));
@@ -576,7 +579,8 @@ void rm_trace_plan_free(rm_trace_plan* pl) {
 rm_status rm_scene_info(const rm_scene* sc, int64_t* nt, int64_t* nnodes, int32_t* nm, int32_t* built) {
     if (!sc) return fail(RM_EINVAL, "scene is NULL");
     if (nt) *nt = sc->nt;
-    if (nnodes) *nnodes = sc->nt > 1 ? sc->nt - 1 : 0;
+    const int64_t ns = sc->nt - sc->nlarge;
+    if (nnodes) *nnodes = ns > 1 ? ns - 1 : 0;
     if (nm) *nm = sc->nm;
     if (built) *built = sc->built ? 1 : 0;
     return RM_OK;

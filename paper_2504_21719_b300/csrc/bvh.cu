@@ -12,6 +12,10 @@
 // Node layout (64 bytes = 4 x float4) of internal node i:
 //   [0] lo0.x lo0.y lo0.z hi0.x   [1] hi0.y hi0.z lo1.x lo1.y
 //   [2] lo1.z hi1.x hi1.y hi1.z   [3] child0 child1 (int bits) 0 0
+// Triangles whose largest AABB extent is at least a quarter of the scene's
+// (the ground of a city; at most 16 of them) stay out of the tree: they sort
+// last (key 2^64 - 1) and the tracer tests them from a short list, so their
+// huge boxes do not inflate every node on their path to the root.
 // child >= 0: internal node; child < 0: leaf ~p, the triangle at sorted
 // position p, whose 48-byte record is trirec[3p .. 3p+2]:
 //   [0] a.x a.y a.z b.x   [1] b.y b.z c.x c.y   [2] c.z mat(int) orig(int) 0
@@ -20,6 +24,7 @@
 namespace rmsbr {
 namespace {
 
+constexpr int MAX_LARGE = 16;   // at most this many large triangles are kept out of the tree
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
@@ -42,7 +47,8 @@ __global__ void k_check_indices(const int32_t* tris, const int32_t* tri_mat, int
     if (bad) atomicOr(flag, 1);
 }
 
-// Per-triangle AABB and doubled centroid c2 = lo + hi; per-block min / max of c2.
+// Per-triangle AABB and doubled centroid c2 = lo + hi; per-block scene bounds
+// (min of the lower and max of the upper AABB corners).
 __global__ void k_tri_aabb(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
                            float* __restrict__ aabb, float* __restrict__ c2, float* __restrict__ blk) {
     __shared__ float smin[3][256], smax[3][256];
@@ -60,8 +66,8 @@ __global__ void k_tri_aabb(const float* __restrict__ verts, const int32_t* __res
             aabb[6 * i + a] = lo;
             aabb[6 * i + 3 + a] = hi;
             c2[3 * i + a] = c;
-            mn[a] = c;
-            mx[a] = c;
+            mn[a] = lo;
+            mx[a] = hi;
         }
     }
     for (int a = 0; a < 3; ++a) { smin[a][tid] = mn[a]; smax[a][tid] = mx[a]; }
@@ -98,6 +104,46 @@ __global__ void k_minmax_final(const float* __restrict__ blk, int nblk, float* _
         for (int a = 0; a < 3; ++a) { out[a] = smin[a][0]; out[3 + a] = smax[a][0]; }
 }
 
+__device__ __forceinline__ float extent3(const float* lo, const float* hi) {
+    return fmax_sel(fmax_sel(__fsub_rn(hi[0], lo[0]), __fsub_rn(hi[1], lo[1])), __fsub_rn(hi[2], lo[2]));
+}
+
+// Large triangles: largest AABB extent >= 0.25 x the scene's largest extent.
+// They are kept out of the tree (tested from a short list) when there are at
+// most MAX_LARGE of them; the count decides that on the host.
+__global__ void k_flag_large(const float* __restrict__ aabb, const float* __restrict__ sb, int64_t nt,
+                             int8_t* __restrict__ large, int32_t* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const float thr = __fmul_rn(0.25f, extent3(sb, sb + 3));
+    const bool l = extent3(aabb + 6 * i, aabb + 6 * i + 3) >= thr;
+    large[i] = l ? 1 : 0;
+    if (l) atomicAdd(count, 1);
+}
+
+// per-block min / max of the doubled centroids of the triangles that stay in the tree
+__global__ void k_c2_bounds(const float* __restrict__ c2, const int8_t* __restrict__ large, int use_large,
+                            int64_t nt, float* __restrict__ blk) {
+    __shared__ float smin[3][256], smax[3][256];
+    const int tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (i < nt && !(use_large && large[i]))
+        for (int a = 0; a < 3; ++a) { mn[a] = c2[3 * i + a]; mx[a] = c2[3 * i + a]; }
+    for (int a = 0; a < 3; ++a) { smin[a][tid] = mn[a]; smax[a][tid] = mx[a]; }
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (tid < st)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][tid] = fmin_sel(smin[a][tid], smin[a][tid + st]);
+                smax[a][tid] = fmax_sel(smax[a][tid], smax[a][tid + st]);
+            }
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int a = 0; a < 3; ++a) { blk[6 * blockIdx.x + a] = smin[a][0]; blk[6 * blockIdx.x + 3 + a] = smax[a][0]; }
+}
+
 // spread the low 21 bits of v to every third bit of a 64-bit word
 __device__ __forceinline__ uint64_t spread21(uint32_t v) {
     uint64_t x = v & 0x1fffffu;
@@ -112,9 +158,15 @@ __device__ __forceinline__ uint64_t spread21(uint32_t v) {
 // q_a = min(trunc((c2_a - cmin_a) * (2097151 / (cmax_a - cmin_a))), 2097151)
 // key = interleave(qx, qy, qz) with x on bit 3i+2, y on 3i+1, z on 3i.
 __global__ void k_morton(const float* __restrict__ c2, const float* __restrict__ bounds, int64_t nt,
-                         uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+                         const int8_t* __restrict__ large, int use_large, uint64_t* __restrict__ keys,
+                         int32_t* __restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nt) return;
+    vals[i] = (int32_t)i;
+    if (use_large && large[i]) {  // after every Morton code: the large triangles end the sorted order
+        keys[i] = ~0ULL;
+        return;
+    }
     uint32_t q[3];
     for (int a = 0; a < 3; ++a) {
         const float e = __fsub_rn(bounds[3 + a], bounds[a]);
@@ -124,7 +176,6 @@ __global__ void k_morton(const float* __restrict__ c2, const float* __restrict__
         q[a] = u > 2097151u ? 2097151u : u;
     }
     keys[i] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
-    vals[i] = (int32_t)i;
 }
 
 // ---------------- stable LSD radix sort of (key, value), 8-bit digits ----------------
@@ -310,8 +361,9 @@ cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t n
     return cudaGetLastError();
 }
 
-cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s) {
+cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int64_t* nlarge_out) {
     const int64_t n = B.nt;
+    *nlarge_out = 0;
     if (n <= 0) return cudaSuccess;
     cudaError_t err;
     const int nblk_a = (int)nb(n, 256);
@@ -325,7 +377,8 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s) {
                  o_k2 = take(sizeof(uint64_t) * n), o_v1 = take(sizeof(int32_t) * n),
                  o_v2 = take(sizeof(int32_t) * n), o_h = take(sizeof(uint32_t) * 256 * (size_t)nblk_s),
                  o_pl = take(sizeof(int32_t) * n), o_pn = take(sizeof(int32_t) * n),
-                 o_vis = take(sizeof(int32_t) * n);
+                 o_vis = take(sizeof(int32_t) * n), o_sb = take(sizeof(float) * 6),
+                 o_lg = take(sizeof(int8_t) * n), o_cnt = take(sizeof(int32_t));
     char* base = nullptr;
     if ((err = cudaMallocAsync((void**)&base, off, s)) != cudaSuccess) return err;
     float* aabb = (float*)(base + o_aabb);
@@ -340,10 +393,24 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s) {
     int32_t* pl = (int32_t*)(base + o_pl);
     int32_t* pn = (int32_t*)(base + o_pn);
     int32_t* vis = (int32_t*)(base + o_vis);
+    float* sb = (float*)(base + o_sb);
+    int8_t* lg = (int8_t*)(base + o_lg);
+    int32_t* cnt = (int32_t*)(base + o_cnt);
 
     k_tri_aabb<<<nblk_a, 256, 0, s>>>(B.verts, B.tris, n, aabb, c2, blk);
+    k_minmax_final<<<1, 256, 0, s>>>(blk, nblk_a, sb);
+    if ((err = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
+    k_flag_large<<<nblk_a, 256, 0, s>>>(aabb, sb, n, lg, cnt);
+    int32_t hcount = 0;
+    if ((err = cudaMemcpyAsync(&hcount, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return err;
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
+    const int use_large = (hcount > 0 && hcount <= MAX_LARGE) ? 1 : 0;
+    const int64_t nl = use_large ? hcount : 0;
+    const int64_t ns = n - nl;  // the tree covers sorted positions [0, ns)
+    *nlarge_out = nl;
+    k_c2_bounds<<<nblk_a, 256, 0, s>>>(c2, lg, use_large, n, blk);
     k_minmax_final<<<1, 256, 0, s>>>(blk, nblk_a, bnd);
-    k_morton<<<nblk_a, 256, 0, s>>>(c2, bnd, n, k1, v1);
+    k_morton<<<nblk_a, 256, 0, s>>>(c2, bnd, n, lg, use_large, k1, v1);
     // 8 passes; after an even number of passes the result is back in (k1, v1)
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 8 * pass;
@@ -357,10 +424,10 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s) {
     }
     if ((err = cudaMemcpyAsync(B.order, v1, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return err;
-    if (n >= 2) {
-        k_karras<<<nb(n - 1, 256), 256, 0, s>>>(k1, n, B.nodes, pl, pn);
-        if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * n, s)) != cudaSuccess) return err;
-        k_refit<<<nb(n, 256), 256, 0, s>>>(aabb, B.order, n, pl, pn, B.nodes, vis);
+    if (ns >= 2) {
+        k_karras<<<nb(ns - 1, 256), 256, 0, s>>>(k1, ns, B.nodes, pl, pn);
+        if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * ns, s)) != cudaSuccess) return err;
+        k_refit<<<nb(ns, 256), 256, 0, s>>>(aabb, B.order, ns, pl, pn, B.nodes, vis);
     }
     k_trirec<<<nb(n, 256), 256, 0, s>>>(B.verts, B.tris, B.tri_mat, B.order, n, B.trirec);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;

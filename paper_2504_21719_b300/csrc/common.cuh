@@ -53,8 +53,9 @@ struct Scratch {
 
 struct TraceArgs {
     const float4* nodes;         // [nt-1][4]
-    const float4* tris;          // [nt][3], leaf order
-    int32_t nt;
+    const float4* tris;          // [nt][3], leaf order: tree leaves, then the large triangles
+    int32_t nt;                  // triangles in the tree
+    int32_t nlarge;              // large triangles, tested from a list at slots nt .. nt+nlarge-1
     int32_t ntx, nm;
     int32_t L;
     uint32_t flags;
@@ -90,7 +91,7 @@ struct BvhBuffers {
     float4* nodes;           // [nt-1][4]
     float4* trirec;          // [nt][3]
 };
-cudaError_t build_bvh(const BvhBuffers& b, cudaStream_t s);
+cudaError_t build_bvh(const BvhBuffers& b, cudaStream_t s, int64_t* nlarge_out);
 cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t nt, int64_t nv, int32_t nm,
                           int32_t* flag_dev, cudaStream_t s);
 

@@ -209,10 +209,10 @@ struct Hit {
 // TIE_REL) count as equal, so coplanar triangles resolve by index.
 constexpr float TIE_REL = 4.8e-7f;
 __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, int nt,
-                                           const Ray& r, int exclude, unsigned& c_nodes, unsigned& c_tris,
-                                           bool& overflow) {
+                                           int nlarge, const Ray& r, int exclude, unsigned& c_nodes,
+                                           unsigned& c_tris, bool& overflow) {
     Hit h{-1, 0x7fffffff, INFINITY};
-    if (nt <= 0) return h;
+    if (nt <= 0 && nlarge <= 0) return h;
     const float ooeps = 0x1p-80f;
     const float ix = 1.0f / (fabsf(r.kx) > ooeps ? r.kx : copysignf(ooeps, r.kx));
     const float iy = 1.0f / (fabsf(r.ky) > ooeps ? r.ky : copysignf(ooeps, r.ky));
@@ -274,6 +274,9 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
             h.prim = prim;
         }
     };
+    // large triangles first: their hit distance then prunes the traversal
+    for (int j = 0; j < nlarge; ++j) test_leaf(nt + j);
+    if (nt <= 0) return h;
     if (nt == 1) {
         test_leaf(0);
         return h;
@@ -472,7 +475,7 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
         // ---------------- closest hit ----------------
         Hit h{-1, 0x7fffffff, INFINITY};
         if (active) {
-            h = closest_hit(A.nodes, A.tris, A.nt, r, prev, c_nodes, c_tris, overflow);
+            h = closest_hit(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris, overflow);
             ++c_seg;
             if (h.slot < 0) ++c_esc;
         }

@@ -37,6 +37,7 @@ def _compare(orc, api, sc):
     got = gs.export_bvh()
     assert np.array_equal(got["keys"], ref["keys"])
     assert np.array_equal(got["order"], ref["order"])
+    assert got["nlarge"] == ref["nlarge"]
     assert np.array_equal(got["child"], ref["child"])
     assert np.array_equal(got["child_aabb"].view(np.uint32), ref["child_aabb"].view(np.uint32))
     gs.free()
