@@ -34,13 +34,16 @@ class OrTx(C.Structure):
     _fields_ = [("pos", C.c_double * 3), ("yaw", C.c_double), ("pitch", C.c_double),
                 ("roll", C.c_double), ("pol", C.c_int32), ("pattern", C.c_int32),
                 ("num_rays", C.c_int64), ("ray_begin", C.c_int64), ("ray_count", C.c_int64),
-                ("ray_stride", C.c_int64), ("seed", C.c_uint64)]
+                ("ray_stride", C.c_int64), ("seed", C.c_uint64), ("n_ant", C.c_int64),
+                ("ant_pos", C.c_void_p), ("precoding", C.c_void_p)]
 
 
 class OrParams(C.Structure):
     _fields_ = [("freq_hz", C.c_double), ("max_depth", C.c_int32), ("flags", C.c_int32),
                 ("map_origin", C.c_double * 3), ("cell_size", C.c_double), ("nx", C.c_int32),
-                ("ny", C.c_int32), ("deposit", C.c_int32), ("pad", C.c_int32)]
+                ("ny", C.c_int32), ("deposit", C.c_int32), ("pad", C.c_int32),
+                ("rr_depth", C.c_int32), ("pad2", C.c_int32), ("rr_max_prob", C.c_double),
+                ("gain_threshold", C.c_double)]
 
 
 class OrReport(C.Structure):
@@ -113,6 +116,15 @@ def make_tx(tx) -> OrTx:
     t.num_rays, t.ray_begin = int(tx.num_rays), int(tx.ray_begin)
     t.ray_count, t.ray_stride = int(tx.ray_count), int(tx.ray_stride)
     t.seed = int(tx.seed)
+    ant = getattr(tx, "ant_pos", None)
+    if ant is not None and len(ant):
+        a = np.ascontiguousarray(ant, np.float64).reshape(-1, 3)
+        pre = np.asarray(tx.precoding, np.complex128).reshape(-1)
+        pc = np.ascontiguousarray(np.stack([pre.real, pre.imag], 1), np.float64)
+        t._keep = (a, pc)  # keep the buffers alive with the struct
+        t.n_ant = len(a)
+        t.ant_pos = a.ctypes.data
+        t.precoding = pc.ctypes.data
     return t
 
 
@@ -125,6 +137,9 @@ def make_params(p) -> OrParams:
         q.map_origin[i] = float(p.map_origin[i])
     q.cell_size = float(p.cell_size)
     q.nx, q.ny, q.deposit = int(p.nx), int(p.ny), int(p.deposit)
+    q.rr_depth = int(getattr(p, "rr_depth", 0))
+    q.rr_max_prob = float(getattr(p, "rr_max_prob", 0.0))
+    q.gain_threshold = float(getattr(p, "gain_threshold", 0.0))
     return q
 
 

@@ -200,6 +200,10 @@ inline double rng_u(uint64_t seed, uint64_t n, int l) {
     uint64_t h = splitmix64(seed ^ splitmix64((n << 4) | (uint64_t)(l & 15)));
     return (double)(h >> 40) * (1.0 / 16777216.0);
 }
+// The Russian-roulette variate of the same interaction comes from a second
+// stream: the seed xor-ed with a fixed odd constant.
+constexpr uint64_t RR_STREAM = 0xD6E8FEB86659FD93ULL;
+inline double rng_rr(uint64_t seed, uint64_t n, int l) { return rng_u(seed ^ RR_STREAM, n, l); }
 
 // ---------------------------------------------------------------------------
 // Spherical Fibonacci lattice (Sec. 3.1.1)
@@ -442,6 +446,9 @@ struct or_tx {
     int32_t pol, pattern;
     int64_t num_rays, ray_begin, ray_count, ray_stride;
     uint64_t seed;
+    int64_t n_ant;             // synthetic array (Sec. 4.5): 0 = single antenna
+    const double* ant_pos;     // [n_ant][3] element positions in the antenna frame (m)
+    const double* precoding;   // [n_ant][2] complex precoding weights
 };
 struct or_params {
     double freq_hz;
@@ -449,6 +456,9 @@ struct or_params {
     double map_origin[3];
     double cell_size;
     int32_t nx, ny, deposit, pad;
+    int32_t rr_depth, pad2;    // early termination after this many interactions (Sec. 4.7); 0 = off
+    double rr_max_prob;        // p_rr,max; 0 = no Russian roulette
+    double gain_threshold;     // linear gain below which a path stops; 0 = off
 };
 enum { F_REFLECT = 1, F_REFRACT = 2, F_LOS = 4 };
 struct or_report {
@@ -573,7 +583,38 @@ struct TxC {
     int pattern, pol;
     int64_t N;
     uint64_t seed;
+    // synthetic array: element positions in the global frame (R d) and precoding
+    std::vector<V3<double>> ant;
+    std::vector<std::complex<double>> prec;
 };
+
+// Array factor of a synthetic transmit array for departure direction k
+// (Sec. 4.5 with the array response vector of Eq. path-solver-array-response-vector):
+//   alpha = sum_k u_P,k exp(j (2 pi / lambda0) k^T d_k).
+// The non-coherent map sees |alpha|^2 times the single-antenna power.
+std::complex<double> array_factor(const TxC& T, const V3<double>& k, double k0) {
+    if (T.ant.empty()) return {1.0, 0.0};
+    std::complex<double> a(0.0, 0.0);
+    for (size_t i = 0; i < T.ant.size(); ++i) {
+        const double ph = k0 * dot(k, T.ant[i]);
+        a += T.prec[i] * std::complex<double>(std::cos(ph), std::sin(ph));
+    }
+    return a;
+}
+
+TxC make_txc(const or_tx& t) {
+    TxC T;
+    T.R = rotation(t.yaw, t.pitch, t.roll);
+    T.pattern = t.pattern;
+    T.pol = t.pol;
+    T.N = t.num_rays;
+    T.seed = t.seed;
+    for (int64_t i = 0; i < t.n_ant; ++i) {
+        T.ant.push_back(mul(T.R, V3<double>{t.ant_pos[3 * i], t.ant_pos[3 * i + 1], t.ant_pos[3 * i + 2]}));
+        T.prec.emplace_back(t.precoding[2 * i], t.precoding[2 * i + 1]);
+    }
+    return T;
+}
 
 struct Ctx {
     const Scene* S;
@@ -581,6 +622,9 @@ struct Ctx {
     double omega, k0;  // angular frequency, vacuum wavenumber
     int L, flags;
     int mode;
+    // early termination (Sec. 4.7)
+    int rr_depth = 0;
+    double rr_pmax = 0.0, gain_thr = 0.0, lam4pi2 = 0.0;
     // sampling materials (detached q): eps, sigma
     const double* s_eps;
     const double* s_sig;
@@ -645,10 +689,12 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
     const int npol = (tx.pol == 2) ? 2 : 1;
     V3<double> k = fibonacci_dir(n, tx.N);
     CV3<R> E[2];
+    const std::complex<double> alpha = array_factor(tx, k, C.k0);
     for (int p = 0; p < npol; ++p) {
         int pol = (tx.pol == 2) ? p : tx.pol;
         V3<double> f = tx_field(k, tx.R, tx.pattern, pol);
-        E[p] = {Cx<R>(R(f.x)), Cx<R>(R(f.y)), Cx<R>(R(f.z))};
+        E[p] = {Cx<R>(R(f.x * alpha.real()), R(f.x * alpha.imag())), Cx<R>(R(f.y * alpha.real()), R(f.y * alpha.imag())),
+                Cx<R>(R(f.z * alpha.real()), R(f.z * alpha.imag()))};
     }
     V3<R> o = txpos;
     double inv_pr = 1.0;  // 1 / Pr(chi): detached from the parameters
@@ -788,12 +834,12 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         double u = rng_u(tx.seed, (uint64_t)n, l);
         int dec = (u < qR) ? 0 : 1;
         if (C.mode == MODE_FROZEN) {
-            dec = rec->dec;
+            dec = rec->dec & 3;
         } else if (C.mode == MODE_REPLAY) {
-            if (rec->dec != dec) {
-                if (std::fabs(u - qR) <= 1e-5 && (rec->dec == 0 || rec->dec == 1)) {
+            if ((rec->dec & 3) != dec) {
+                if (std::fabs(u - qR) <= 1e-5 && rec->dec >= 0 && (rec->dec & 3) <= 1) {
                     rs->rep.adopted_decision++;
-                    dec = rec->dec;
+                    dec = rec->dec & 3;
                 } else {
                     rs->fail(i_sub, l, 3, dec, rec->dec, u, qR);
                     return;
@@ -850,6 +896,53 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         path += val(t_h);
         k = k_out;
         prev = prim;
+        // ---- early termination after rr_depth interactions (Sec. 4.7) ----
+        // Reading: the gain of a sample is w |E|^2 with w = 1 / Pr(chi) (the
+        // tube-length-normalised gain of the paper); gain thresholding stops a
+        // path when (lambda0 / 4 pi)^2 w |E|^2 / r^2 < threshold at its tube
+        // length r; Russian roulette (Eq. radio-map-solver-rr-prob) keeps it
+        // with p = min(w |E|^2, p_max) and reweights the power of survivors by
+        // 1 / p (the field by 1 / sqrt(p)); p is detached like q.
+        if (C.rr_depth > 0 && l + 1 >= C.rr_depth && (C.gain_thr > 0.0 || C.rr_pmax > 0.0)) {
+            double w2v = 0.0;
+            for (int p = 0; p < npol; ++p) w2v += val(cnorm2(E[p]));
+            w2v *= inv_pr;
+            int kill = 0;
+            if (C.gain_thr > 0.0) {
+                const double gain = C.lam4pi2 * w2v / (path * path);
+                kill = gain < C.gain_thr ? 8 : 0;
+                if (C.mode == MODE_FROZEN) {
+                    kill = rec->dec & 8;
+                } else if (C.mode == MODE_REPLAY && (rec->dec & 8) != kill) {
+                    if (std::fabs(gain - C.gain_thr) <= 1e-5 * C.gain_thr) {
+                        rs->rep.adopted_decision++;
+                        kill = rec->dec & 8;
+                    } else {
+                        rs->fail(i_sub, l, 3, kill, rec->dec, gain, C.gain_thr);
+                        return;
+                    }
+                }
+            }
+            if (!kill && C.rr_pmax > 0.0) {
+                const double prr = std::min(w2v, C.rr_pmax);
+                const double urr = rng_rr(tx.seed, (uint64_t)n, l);
+                kill = (urr < prr) ? 0 : 4;
+                if (C.mode == MODE_FROZEN) {
+                    kill = rec->dec & 4;
+                } else if (C.mode == MODE_REPLAY && (rec->dec & 4) != kill) {
+                    if (std::fabs(urr - prr) <= 1e-5) {
+                        rs->rep.adopted_decision++;
+                        kill = rec->dec & 4;
+                    } else {
+                        rs->fail(i_sub, l, 3, kill, rec->dec, urr, prr);
+                        return;
+                    }
+                }
+                if (!kill) inv_pr /= prr;
+            }
+            if (rec && C.mode == MODE_PLAIN) rec->dec |= kill;
+            if (kill) break;
+        }
     }
     // remaining record slots: no segment
     if (rec_io && C.mode == MODE_PLAIN)
@@ -857,6 +950,14 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
     if (C.mode == MODE_REPLAY)
         for (int j = l + 1; j <= L; ++j)
             if (rec_io[(size_t)i_sub * (L + 1) + j].prim != -2) { rs->fail(i_sub, j, 4, -2, rec_io[(size_t)i_sub * (L + 1) + j].prim, 0, 0); return; }
+}
+
+void set_early_termination(Ctx& C, const or_params& P) {
+    C.rr_depth = P.rr_depth;
+    C.rr_pmax = P.rr_max_prob;
+    C.gain_thr = P.gain_threshold;
+    const double a = C0 / P.freq_hz / (4.0 * PI);
+    C.lam4pi2 = a * a;
 }
 
 MapGeom make_geom(const or_params& P, int64_t N) {
@@ -1018,12 +1119,8 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
     C.mode = mode;
     C.s_eps = seps.data();
     C.s_sig = ssig.data();
-    TxC T;
-    T.R = rotation(tx->yaw, tx->pitch, tx->roll);
-    T.pattern = tx->pattern;
-    T.pol = tx->pol;
-    T.N = tx->num_rays;
-    T.seed = tx->seed;
+    set_early_termination(C, *P);
+    TxC T = make_txc(*tx);
     std::vector<Cx<double>> eta(nm);
     std::vector<double> k0d(nm);
     for (int m = 0; m < nm; ++m) {
@@ -1113,12 +1210,8 @@ int or_grad(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, con
     C.mode = MODE_FROZEN;
     C.s_eps = S.eps.data();
     C.s_sig = S.sigma.data();
-    TxC T;
-    T.R = rotation(tx->yaw, tx->pitch, tx->roll);
-    T.pattern = tx->pattern;
-    T.pol = tx->pol;
-    T.N = tx->num_rays;
-    T.seed = tx->seed;
+    set_early_termination(C, *P);
+    TxC T = make_txc(*tx);
     std::vector<Cx<D>> eta(nm);
     std::vector<D> k0d(nm);
     for (int m = 0; m < nm; ++m) {
@@ -1255,7 +1348,8 @@ int or_branch_all(const float* verts, int64_t nv, const int32_t* tris, int64_t n
         eta[m] = permittivity(S.eps[m], S.sigma[m], C.omega);
         k0d[m] = C.k0 * S.thick[m];
     }
-    Rot R = rotation(tx->yaw, tx->pitch, tx->roll);
+    TxC T = make_txc(*tx);
+    const Rot& R = T.R;
     const int npol = tx->pol == 2 ? 2 : 1;
     const int64_t cnt = subset_count(*tx);
     const int L = P->max_depth;
@@ -1271,10 +1365,12 @@ int or_branch_all(const float* verts, int64_t nv, const int32_t* tris, int64_t n
         for (int64_t i = c * CH; i < e; ++i) {
             int64_t n = tx->ray_begin + i * tx->ray_stride;
             V3<double> k = fibonacci_dir(n, tx->num_rays);
+            const std::complex<double> al = array_factor(T, k, C.k0);
             CV3<double> E[2];
             for (int p = 0; p < npol; ++p) {
                 V3<double> f = tx_field(k, R, tx->pattern, tx->pol == 2 ? p : tx->pol);
-                E[p] = {Cx<double>(f.x), Cx<double>(f.y), Cx<double>(f.z)};
+                E[p] = {Cx<double>(f.x * al.real(), f.x * al.imag()), Cx<double>(f.y * al.real(), f.y * al.imag()),
+                        Cx<double>(f.z * al.real(), f.z * al.imag())};
             }
             branch(B, {tx->pos[0], tx->pos[1], tx->pos[2]}, k, E, -1, 0);
         }

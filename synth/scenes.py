@@ -69,6 +69,8 @@ class Tx:
     ray_count: int = -1   # -1 = all num_rays
     ray_stride: int = 1
     seed: int = 0
+    ant_pos: object = None      # synthetic array: [n_ant, 3] element positions (m), antenna frame
+    precoding: object = None    # [n_ant] complex precoding weights
 
     def count(self) -> int:
         if self.ray_count >= 0:
@@ -88,6 +90,9 @@ class TraceParams:
     nx: int = 100
     ny: int = 100
     deposit: int = 0      # 0 = box cells, 1 = bilinear (tent) splat
+    rr_depth: int = 0     # early termination after this many interactions (0 = off)
+    rr_max_prob: float = 0.0
+    gain_threshold: float = 0.0
 
     def map_corner(self):
         """Lower-left corner (x0, y0) of a map centred on map_origin."""
@@ -347,6 +352,24 @@ def perturb_materials(mats: np.ndarray, seed: int) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # the five workloads
 # ----------------------------------------------------------------------------
+
+def uniform_linear_array(n: int, freq_hz: float, spacing_wavelengths: float = 0.5, axis: int = 1,
+                         steer=None):
+    """Element positions of an n-element uniform linear array along a local axis
+    and unit-norm precoding weights (uniform, or steering towards a direction).
+
+    Positions only: no method arithmetic (the array factor is computed by the
+    oracle and by the CUDA path, each on its own)."""
+    lam = 299792458.0 / freq_hz
+    pos = np.zeros((n, 3))
+    pos[:, axis] = (np.arange(n) - 0.5 * (n - 1)) * spacing_wavelengths * lam
+    w = np.ones(n, np.complex128) / np.sqrt(n)
+    if steer is not None:
+        k = np.asarray(steer, np.float64)
+        k = k / np.linalg.norm(k)
+        w = np.exp(-2j * np.pi / lam * (pos @ k)) / np.sqrt(n)
+    return pos, w
+
 
 def workload(cfg: int):
     """Return (scene, [Tx], TraceParams) for workload 1..5.
