@@ -82,6 +82,15 @@ typedef struct {
     uint64_t ray_count;  /* UINT64_MAX: all of ceil((num_rays - ray_begin) / ray_stride) */
     uint64_t ray_stride; /* >= 1 */
     uint64_t seed;       /* seed of the counter-based interaction sampler */
+    /* Synthetic array (Sec. 4.5): n_ant elements at ant_pos_host [n_ant][3] (m,
+     * antenna frame, rotated with the antenna) with complex precoding weights
+     * precoding_host [n_ant][2] (re, im).  Each ray's launch field is scaled by
+     * alpha = sum_k u_P,k exp(j 2 pi / lambda0 k.d_k) (array response vector,
+     * Eq. path-solver-array-response-vector).  n_ant = 0: one antenna. */
+    int32_t n_ant;
+    int32_t reserved;
+    const float* ant_pos_host;
+    const float* precoding_host;
 } rm_tx;
 
 /* trace flags */
@@ -102,6 +111,16 @@ typedef struct {
     int32_t blocks_per_sm;   /* resident blocks per SM of the persistent grid; 0 = tuned default */
     int32_t queue_chunk;     /* work items a warp takes per work-queue access, in units of 32 (1..64);
                                 0 = default (1) */
+    /* Early termination (Sec. 4.7), applied after an interaction once a path
+     * has rr_depth interactions (0 = off).  The gain of a sample is w |E|^2,
+     * w = 1 / Pr(chi).  gain_threshold > 0: stop when (lambda0/4pi)^2 w |E|^2 / r^2,
+     * r the tube length, is below it (biased).  rr_max_prob in (0, 1]: Russian
+     * roulette, continue with p = min(w |E|^2, rr_max_prob) (Eq.
+     * radio-map-solver-rr-prob) and reweight survivors by 1/p (unbiased). */
+    int32_t rr_depth;
+    float rr_max_prob;
+    float gain_threshold;
+    int32_t reserved2;
 } rm_trace_params;
 
 /* Counters of one trace call, summed over all transmitters. */
@@ -128,7 +147,8 @@ typedef struct {
  * l = 0..L).  prim: original triangle index hit, -1 escaped, -2 the ray had
  * already terminated.  ix, iy: deposited cell (bilinear: lower-left cell of
  * the 2x2 stencil), -32768 for no deposit.  decision: 0 reflection,
- * 1 refraction, -1 none. */
+ * 1 refraction, -1 none; plus 4 if Russian roulette then stopped the path,
+ * 8 if the gain threshold did. */
 typedef struct {
     int32_t prim, ix, iy, decision;
 } rm_segment_record;
@@ -235,10 +255,10 @@ void rm_trace_plan_free(rm_trace_plan* plan);
  * entry point calls no cudaMalloc, cudaFree or other allocating routine.
  * The paper has no counterpart of it: it only changes where the tracer's
  * scratch lives.
- *   Scratch: one static device array of 16 KB, enough for the largest call
- *   (RM_MAX_MATERIALS materials, RM_MAX_TX transmitters); every GPU that
- *   loads the library holds it until the process exits.  A call that would
- *   need more is rejected with RM_EINVAL.
+ *   Scratch: one static device array of 16 KB, enough for RM_MAX_MATERIALS
+ *   materials and RM_MAX_TX transmitters plus ~130 synthetic-array elements
+ *   (32 bytes each); every GPU that loads the library holds it until the
+ *   process exits.  A call that would need more is rejected with RM_EINVAL.
  *   Set-up: the first call on a device looks up the array's device address
  *   (with that device current); make that first call before any stream
  *   capture.

@@ -28,14 +28,16 @@ class rm_tx(C.Structure):
     _fields_ = [("pos", C.c_float * 3), ("yaw", C.c_float), ("pitch", C.c_float), ("roll", C.c_float),
                 ("pol", C.c_int32), ("pattern", C.c_int32), ("num_rays", C.c_uint64),
                 ("ray_begin", C.c_uint64), ("ray_count", C.c_uint64), ("ray_stride", C.c_uint64),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("n_ant", C.c_int32), ("reserved", C.c_int32),
+                ("ant_pos_host", C.c_void_p), ("precoding_host", C.c_void_p)]
 
 
 class rm_trace_params(C.Structure):
     _fields_ = [("freq_hz", C.c_double), ("max_depth", C.c_int32), ("flags", C.c_uint32),
                 ("map_origin", C.c_float * 3), ("cell_size", C.c_float), ("nx", C.c_int32),
                 ("ny", C.c_int32), ("deposit", C.c_int32), ("block_size", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("queue_chunk", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("queue_chunk", C.c_int32), ("rr_depth", C.c_int32),
+                ("rr_max_prob", C.c_float), ("gain_threshold", C.c_float), ("reserved2", C.c_int32)]
 
 
 _D = RM_MAX_DEPTH + 1

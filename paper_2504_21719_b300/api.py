@@ -44,8 +44,16 @@ def materials(mats) -> C.Array:
 
 
 def tx_struct(pos, num_rays, yaw=0.0, pitch=0.0, roll=0.0, pol=0, pattern=0, ray_begin=0, ray_count=None,
-              ray_stride=1, seed=0) -> L.rm_tx:
+              ray_stride=1, seed=0, ant_pos=None, precoding=None) -> L.rm_tx:
     t = L.rm_tx()
+    if ant_pos is not None and len(ant_pos):
+        a = np.ascontiguousarray(np.asarray(ant_pos, np.float64).reshape(-1, 3), np.float32)
+        w = np.asarray(precoding, np.complex128).reshape(-1)
+        pc = np.ascontiguousarray(np.stack([w.real, w.imag], 1), np.float32)
+        t._keep = (a, pc)  # the buffers live as long as the struct
+        t.n_ant = len(a)
+        t.ant_pos_host = a.ctypes.data
+        t.precoding_host = pc.ctypes.data
     for i in range(3):
         t.pos[i] = float(pos[i])
     t.yaw, t.pitch, t.roll = float(yaw), float(pitch), float(roll)
@@ -59,12 +67,14 @@ def tx_struct(pos, num_rays, yaw=0.0, pitch=0.0, roll=0.0, pol=0, pattern=0, ray
 def tx_from(obj) -> L.rm_tx:
     """rm_tx from any object with the rm_tx field names as attributes."""
     return tx_struct(obj.pos, obj.num_rays, obj.yaw, obj.pitch, obj.roll, obj.pol, obj.pattern, obj.ray_begin,
-                     obj.ray_count, obj.ray_stride, obj.seed)
+                     obj.ray_count, obj.ray_stride, obj.seed, getattr(obj, "ant_pos", None),
+                     getattr(obj, "precoding", None))
 
 
 def params_struct(freq_hz, max_depth, map_origin=(0.0, 0.0, 1.5), cell_size=1.0, nx=100, ny=100,
                   reflect=True, refract=True, los=True, stats=False, deposit=0, block_size=0,
-                  blocks_per_sm=0, queue_chunk=0) -> L.rm_trace_params:
+                  blocks_per_sm=0, queue_chunk=0, rr_depth=0, rr_max_prob=0.0,
+                  gain_threshold=0.0) -> L.rm_trace_params:
     p = L.rm_trace_params()
     p.freq_hz = float(freq_hz)
     p.max_depth = int(max_depth)
@@ -75,12 +85,15 @@ def params_struct(freq_hz, max_depth, map_origin=(0.0, 0.0, 1.5), cell_size=1.0,
     p.cell_size = float(cell_size)
     p.nx, p.ny, p.deposit = int(nx), int(ny), int(deposit)
     p.block_size, p.blocks_per_sm, p.queue_chunk = int(block_size), int(blocks_per_sm), int(queue_chunk)
+    p.rr_depth, p.rr_max_prob, p.gain_threshold = int(rr_depth), float(rr_max_prob), float(gain_threshold)
     return p
 
 
 def params_from(obj, stats=False, block_size=0, blocks_per_sm=0, queue_chunk=0) -> L.rm_trace_params:
     return params_struct(obj.freq_hz, obj.max_depth, obj.map_origin, obj.cell_size, obj.nx, obj.ny, obj.reflect,
-                         obj.refract, obj.los, stats, obj.deposit, block_size, blocks_per_sm, queue_chunk)
+                         obj.refract, obj.los, stats, obj.deposit, block_size, blocks_per_sm, queue_chunk,
+                         getattr(obj, "rr_depth", 0), getattr(obj, "rr_max_prob", 0.0),
+                         getattr(obj, "gain_threshold", 0.0))
 
 
 def _tx_array(txs):
@@ -272,6 +285,7 @@ class RadioMap(torch.autograd.Function):
         for i, t in enumerate(txs):
             s = t if isinstance(t, L.rm_tx) else tx_from(t)
             s2 = L.rm_tx.from_buffer_copy(s)
+            s2._keep = getattr(s, "_keep", None)
             for a in range(3):
                 s2.pos[a] = float(pos[i, a])
             txl.append(s2)

@@ -41,6 +41,7 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double C0 = 299792458.0;          // m/s
 constexpr double EPS0 = 8.8541878128e-12;   // F/m (CODATA 2018)
 constexpr int DEFAULT_BLOCK = 128;
+constexpr int MAX_ANT = 4096;   // synthetic-array elements per call
 
 thread_local std::string g_err;
 
@@ -98,6 +99,8 @@ rm_status validate(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_tr
         return fail(RM_EINVAL, "block_size must be 0 or a multiple of 32 in [32, 256]");
     if (p->blocks_per_sm < 0) return fail(RM_EINVAL, "blocks_per_sm must be >= 0");
     if (p->queue_chunk < 0 || p->queue_chunk > 64) return fail(RM_EINVAL, "queue_chunk must be in [0, 64]");
+    if (p->rr_depth < 0 || !(p->rr_max_prob >= 0.0f && p->rr_max_prob <= 1.0f) || !(p->gain_threshold >= 0.0f))
+        return fail(RM_EINVAL, "rr_depth >= 0, rr_max_prob in [0, 1] and gain_threshold >= 0 are required");
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(p->map_origin[i])) return fail(RM_EINVAL, "map_origin must be finite");
     for (int t = 0; t < ntx; ++t) {
@@ -111,6 +114,12 @@ rm_status validate(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_tr
             if (!std::isfinite(x.pos[i])) return fail(RM_EINVAL, w + "position must be finite");
         if (!std::isfinite(x.yaw) || !std::isfinite(x.pitch) || !std::isfinite(x.roll))
             return fail(RM_EINVAL, w + "orientation must be finite");
+        if (x.n_ant < 0 || x.n_ant > MAX_ANT || (x.n_ant > 0 && (!x.ant_pos_host || !x.precoding_host)))
+            return fail(RM_EINVAL, w + "n_ant must be in [0, 4096] with element positions and precoding");
+        for (int a = 0; a < x.n_ant; ++a)
+            for (int c3 = 0; c3 < 3; ++c3)
+                if (!std::isfinite(x.ant_pos_host[3 * a + c3]) || (c3 < 2 && !std::isfinite(x.precoding_host[2 * a + c3])))
+                    return fail(RM_EINVAL, w + "antenna positions and precoding must be finite");
         const uint64_t c = tx_count(x);
         if (c > 0) {
             if (x.ray_begin >= x.num_rays) return fail(RM_EINVAL, w + "ray_begin >= num_rays");
@@ -118,6 +127,9 @@ rm_status validate(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_tr
                 return fail(RM_EINVAL, w + "ray subset exceeds the lattice");
         }
     }
+    int64_t nant = 0;
+    for (int t = 0; t < ntx; ++t) nant += tx[t].n_ant;
+    if (nant > MAX_ANT) return fail(RM_EINVAL, "more than 4096 array elements in one call");
     if (ntx > 1) {
         const int np = tx[0].pol == 2 ? 2 : 1;
         for (int t = 1; t < ntx; ++t)
@@ -131,6 +143,7 @@ struct Prepared {
     TraceArgs a;
     std::vector<MatDev> mats;
     std::vector<TxDev> tx;
+    std::vector<AntDev> ant;
     int npol = 1;
     bool bilinear = false;
     int block = DEFAULT_BLOCK;
@@ -222,6 +235,25 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
         d.seed = tx[t].seed;
         d.rec_begin = rec;
         d.perm = visit_step(tx[t], d.count);
+        d.n_ant = tx[t].n_ant;
+        d.ant_begin = (int32_t)P->ant.size();
+        for (int a = 0; a < tx[t].n_ant; ++a) {
+            // element position rotated with the antenna (R d), in double, then FP32
+            const double lx = tx[t].ant_pos_host[3 * a], ly = tx[t].ant_pos_host[3 * a + 1],
+                         lz = tx[t].ant_pos_host[3 * a + 2];
+            const double ca = std::cos(tx[t].yaw), sa = std::sin(tx[t].yaw), cb = std::cos(tx[t].pitch),
+                         sb = std::sin(tx[t].pitch), cg = std::cos(tx[t].roll), sg = std::sin(tx[t].roll);
+            const double M[9] = {ca * cb, ca * sb * sg - sa * cg, ca * sb * cg + sa * sg,
+                                 sa * cb, sa * sb * sg + ca * cg, sa * sb * cg - ca * sg,
+                                 -sb,     cb * sg,                cb * cg};
+            AntDev e{};
+            e.dx = (float)(M[0] * lx + M[1] * ly + M[2] * lz);
+            e.dy = (float)(M[3] * lx + M[4] * ly + M[5] * lz);
+            e.dz = (float)(M[6] * lx + M[7] * ly + M[8] * lz);
+            e.pre = tx[t].precoding_host[2 * a];
+            e.pim = tx[t].precoding_host[2 * a + 1];
+            P->ant.push_back(e);
+        }
         work += d.count;
         rec += d.count * (unsigned long long)(p->max_depth + 1);
     }
@@ -243,6 +275,11 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
     A.nx = p->nx;
     A.ny = p->ny;
     A.inv_eps0_omega = (float)(1.0 / (EPS0 * omega));
+    A.k0 = (float)k0;
+    A.rr_depth = p->rr_depth;
+    A.rr_pmax = p->rr_depth > 0 ? p->rr_max_prob : 0.0f;
+    A.gain_thr = p->rr_depth > 0 ? p->gain_threshold : 0.0f;
+    A.lam4pi2 = (float)(a * a);
     A.same_sampling = same ? 1 : 0;
     A.total = work;
     A.qchunk = 32ULL * (unsigned long long)(p->queue_chunk > 0 ? p->queue_chunk : 1);
@@ -253,14 +290,19 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
     P->bps = p->blocks_per_sm;
 }
 
-// device block: [Scratch | MatDev[nm] | TxDev[ntx]]
+// device block: [Scratch | MatDev[nm] | TxDev[ntx] | AntDev[n_ant total]]
 size_t table_bytes(const Prepared& P, size_t* o_mat, size_t* o_tx) {
     size_t off = (sizeof(Scratch) + 255) & ~size_t(255);
     *o_mat = off;
     off += (P.mats.size() * sizeof(MatDev) + 255) & ~size_t(255);
     *o_tx = off;
     off += P.tx.size() * sizeof(TxDev);
+    off = (off + 255) & ~size_t(255);
+    off += P.ant.size() * sizeof(AntDev);
     return off;
+}
+size_t ant_offset(const Prepared& P, size_t o_tx) {
+    return (o_tx + P.tx.size() * sizeof(TxDev) + 255) & ~size_t(255);
 }
 
 // the same block followed by the FP64 accumulation maps [ntx][ny][nx]
@@ -322,6 +364,8 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
                                  cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice,
                                  S(stream))) != cudaSuccess) break;
+        if (!P.ant.empty() && (e = cudaMemcpyAsync(dev + ant_offset(P, o_tx), P.ant.data(), P.ant.size() * sizeof(AntDev),
+                                                   cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
         if (!adjoint && (e = cudaMemsetAsync(dev + o_m64, 0, sizeof(double) * P.a.ncell * ntx, S(stream))) != cudaSuccess)
             break;
         unsigned long long nrec = 0;
@@ -329,6 +373,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         if (record && (e = launch_fill_record(record, nrec, S(stream))) != cudaSuccess) break;
         P.a.mats = reinterpret_cast<const MatDev*>(dev + o_mat);
         P.a.tx = reinterpret_cast<const TxDev*>(dev + o_tx);
+        P.a.ant = reinterpret_cast<const AntDev*>(dev + ant_offset(P, o_tx));
         P.a.scratch = reinterpret_cast<Scratch*>(dev);
         P.a.maps = maps;
         P.a.maps64 = adjoint ? nullptr : reinterpret_cast<double*>(dev + o_m64);
@@ -525,9 +570,13 @@ rm_status rm_trace_plan_create(const rm_scene* sc, const rm_tx* tx, int32_t ntx,
         return cleanup(cuda_fail(e, "cudaMemcpy"));
     if ((e = cudaMemcpy(pl->dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaMemcpy"));
+    if (!P.ant.empty() && (e = cudaMemcpy(pl->dev + ant_offset(P, o_tx), P.ant.data(), P.ant.size() * sizeof(AntDev),
+                                          cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMemcpy"));
     pl->scratch = reinterpret_cast<Scratch*>(pl->dev);
     P.a.mats = reinterpret_cast<const MatDev*>(pl->dev + o_mat);
     P.a.tx = reinterpret_cast<const TxDev*>(pl->dev + o_tx);
+    P.a.ant = reinterpret_cast<const AntDev*>(pl->dev + ant_offset(P, o_tx));
     P.a.scratch = pl->scratch;
     P.a.maps = maps_dev;
     P.a.maps64 = reinterpret_cast<double*>(pl->dev + o_m64);
@@ -662,9 +711,12 @@ extern "C" rm_status rm_radio_map_trace_noalloc(const rm_scene* sc, const rm_tx*
                                  cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice,
                                  S(stream))) != cudaSuccess) break;
+        if (!P.ant.empty() && (e = cudaMemcpyAsync(dev + ant_offset(P, o_tx), P.ant.data(), P.ant.size() * sizeof(AntDev),
+                                                   cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(maps_dev, 0, sizeof(float) * P.a.ncell * ntx, S(stream))) != cudaSuccess) break;
         P.a.mats = reinterpret_cast<const MatDev*>(dev + o_mat);
         P.a.tx = reinterpret_cast<const TxDev*>(dev + o_tx);
+        P.a.ant = reinterpret_cast<const AntDev*>(dev + ant_offset(P, o_tx));
         P.a.scratch = reinterpret_cast<Scratch*>(dev);
         P.a.maps = maps_dev;
         if (P.a.total > 0 &&

@@ -38,6 +38,13 @@ struct TxDev {
     unsigned long long seed;
     unsigned long long rec_begin;   // first debug record of this transmitter
     unsigned long long perm;        // visit order: subset index i = (j * perm) mod count (1 = identity)
+    int32_t n_ant, ant_begin;       // synthetic array elements in the antenna table
+};
+
+// One element of a synthetic transmit array: position in the global frame
+// (relative to the array centre) and complex precoding weight.
+struct AntDev {
+    float dx, dy, dz, pre, pim, pad0, pad1, pad2;
 };
 
 // Scratch of one trace launch (zeroed before the launch).
@@ -68,6 +75,12 @@ struct TraceArgs {
     unsigned long long ncell;    // nx * ny
     const MatDev* mats;          // [nm]
     const TxDev* tx;             // [ntx]
+    const AntDev* ant;           // synthetic-array elements of all transmitters
+    float k0;                    // 2 pi / lambda0
+    int32_t rr_depth;            // early termination after this many interactions (0 = off)
+    float rr_pmax;               // Russian roulette p_max (0 = off)
+    float gain_thr;              // gain threshold (0 = off)
+    float lam4pi2;               // (lambda0 / 4 pi)^2
     Scratch* scratch;
     float* maps;                 // [ntx][ny][nx] (forward, FP32 accumulation when maps64 is null)
     double* maps64;              // [ntx][ny][nx] FP64 accumulation buffer (forward), or null

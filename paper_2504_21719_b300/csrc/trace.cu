@@ -93,6 +93,8 @@ __device__ __forceinline__ float rng_u(unsigned long long seed, unsigned long lo
     const unsigned long long h = splitmix64(seed ^ splitmix64((n << 4) | (unsigned long long)(l & 15)));
     return (float)(unsigned)(h >> 40) * 0x1p-24f;
 }
+// the Russian-roulette variate of the same interaction: a second stream
+constexpr unsigned long long RR_STREAM = 0xD6E8FEB86659FD93ULL;
 
 // ------------------------------------------------------------------ Fresnel
 struct Coef {
@@ -365,6 +367,7 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
     Ray r{0, 0, 0, 0, 0, 1};
     cf E[NPOL][3];
     float inv_pr = 1.0f;
+    float plen = 0.0f;  // unfolded tube length to the current origin
     int depth = 0, prev = -1, txi = 0;
     unsigned long long n = 0, isub = 0;
     // adjoint state: tangents dE/d eta per material met on the path
@@ -438,14 +441,30 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                         if (sxy > 0.0f) { cph = lx / sxy; sph = ly / sxy; }
                         const float g = (T.pattern == 1) ? 1.2247448713915890f * sxy : 1.0f;
                         const f3 th_l{lz * cph, lz * sph, -sxy}, ph_l{-sph, cph, 0.0f};
+                        // synthetic array (Sec. 4.5): alpha = sum_k u_P,k exp(j k0 k.d_k)
+                        float are = 1.0f, aim = 0.0f;
+                        if (T.n_ant > 0) {
+                            are = 0.0f;
+                            for (int a = 0; a < T.n_ant; ++a) {
+                                const AntDev el = A.ant[T.ant_begin + a];
+                                float sn, cs;
+                                sincosf(A.k0 * (r.kx * el.dx + r.ky * el.dy + r.kz * el.dz), &sn, &cs);
+                                are += el.pre * cs - el.pim * sn;
+                                aim += el.pre * sn + el.pim * cs;
+                            }
+                        }
                         for (int p = 0; p < NPOL; ++p) {
                             const int pol = (NPOL == 2) ? p : T.pol;
                             const f3 e = pol == 0 ? th_l : ph_l;
-                            E[p][0] = C(g * (T.R[0] * e.x + T.R[1] * e.y + T.R[2] * e.z));
-                            E[p][1] = C(g * (T.R[3] * e.x + T.R[4] * e.y + T.R[5] * e.z));
-                            E[p][2] = C(g * (T.R[6] * e.x + T.R[7] * e.y + T.R[8] * e.z));
+                            const float ex = g * (T.R[0] * e.x + T.R[1] * e.y + T.R[2] * e.z);
+                            const float ey = g * (T.R[3] * e.x + T.R[4] * e.y + T.R[5] * e.z);
+                            const float ez = g * (T.R[6] * e.x + T.R[7] * e.y + T.R[8] * e.z);
+                            E[p][0] = C(ex * are, ex * aim);
+                            E[p][1] = C(ey * are, ey * aim);
+                            E[p][2] = C(ez * are, ez * aim);
                         }
                         inv_pr = 1.0f;
+                        plen = 0.0f;
                         depth = 0;
                         prev = -1;
                         active = true;
@@ -728,7 +747,28 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                     r.oz = pz + sgn * nrm.z;
                     r.kx = ko.x; r.ky = ko.y; r.kz = ko.z;
                     prev = h.slot;
+                    plen += h.t;
                     ++depth;
+                    // early termination once the path has rr_depth interactions (Sec. 4.7):
+                    // threshold on (lambda0/4pi)^2 w|E|^2 / r^2, then Russian roulette with
+                    // p = min(w|E|^2, p_max) (Eq. radio-map-solver-rr-prob), survivors x 1/p
+                    if (A.rr_depth > 0 && depth >= A.rr_depth && (A.gain_thr > 0.0f || A.rr_pmax > 0.0f)) {
+                        float w2 = 0.0f;
+                        for (int p = 0; p < NPOL; ++p) w2 += cabs2(E[p][0]) + cabs2(E[p][1]) + cabs2(E[p][2]);
+                        w2 *= inv_pr;
+                        int kill = 0;
+                        if (A.gain_thr > 0.0f && A.lam4pi2 * w2 / (plen * plen) < A.gain_thr) kill = 8;
+                        if (!kill && A.rr_pmax > 0.0f) {
+                            const float prr = fminf(w2, A.rr_pmax);
+                            const float urr = rng_u(s_tx[txi].seed ^ RR_STREAM, n, depth - 1);
+                            if (urr < prr) inv_pr = inv_pr / prr;
+                            else kill = 4;
+                        }
+                        if (kill) {
+                            active = false;
+                            if (rec) rec->decision |= kill;
+                        }
+                    }
                 }
             }
         }

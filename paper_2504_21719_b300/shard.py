@@ -27,6 +27,8 @@ def partition_tx(tx, rank: int, world: int):
     try:
         import ctypes
         t = type(tx).from_buffer_copy(tx) if isinstance(tx, ctypes.Structure) else copy.copy(tx)
+        if isinstance(tx, ctypes.Structure) and hasattr(tx, "_keep"):
+            t._keep = tx._keep  # antenna buffers referenced by pointer
     except Exception:
         t = copy.copy(tx)
     cnt = tx.ray_count

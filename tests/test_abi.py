@@ -42,9 +42,11 @@ def test_every_declared_symbol_is_exported(L):
 def test_struct_layouts_match_header(L, tmp_path):
     fields = {
         "rm_material": ["eps_r", "sigma", "thickness"],
-        "rm_tx": ["pos", "yaw", "pol", "pattern", "num_rays", "ray_begin", "ray_count", "ray_stride", "seed"],
+        "rm_tx": ["pos", "yaw", "pol", "pattern", "num_rays", "ray_begin", "ray_count", "ray_stride", "seed",
+                  "n_ant", "ant_pos_host", "precoding_host"],
         "rm_trace_params": ["freq_hz", "max_depth", "flags", "map_origin", "cell_size", "nx", "ny", "deposit",
-                            "block_size", "blocks_per_sm", "queue_chunk"],
+                            "block_size", "blocks_per_sm", "queue_chunk", "rr_depth", "rr_max_prob",
+                            "gain_threshold"],
         "rm_stats": ["rays", "segments", "escapes", "segments_per_depth", "power_per_depth", "power2_per_depth",
                      "escaped_power_per_depth", "status", "kernel_ms"],
         "rm_segment_record": ["prim", "ix", "iy", "decision"],
