@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.cpp")
 
-F_REFLECT, F_REFRACT, F_LOS = 1, 2, 4
+F_REFLECT, F_REFRACT, F_LOS, F_DIFFUSE = 1, 2, 4, 16
 NO_CELL = -32768
 
 
@@ -71,6 +71,14 @@ def lib():
         _lib.or_rng_u.argtypes = [C.c_uint64, C.c_uint64, C.c_int]
         _lib.or_splitmix64.restype = C.c_uint64
         _lib.or_splitmix64.argtypes = [C.c_uint64]
+        _lib.or_rng_diff.restype = C.c_double
+        _lib.or_rng_diff.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int]
+        _lib.or_f_alpha.restype = C.c_double
+        _lib.or_f_alpha.argtypes = [C.c_int, C.c_double]
+        _lib.or_scat_pattern.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, P, P, P, C.c_int64, P]
+        _lib.or_diffuse_dir.argtypes = [P, P, C.c_int64, P]
+        _lib.or_diffuse_interact.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                             C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, P, P, P]
         _lib.or_fibonacci.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
         _lib.or_tx_field.argtypes = [P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int,
                                      C.c_int, P]
@@ -82,10 +90,10 @@ def lib():
                                      C.c_int, P, P]
         _lib.or_closest_hit.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int64, P, P, P]
         _lib.or_radio_map.restype = C.c_int
-        _lib.or_radio_map.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, C.c_int, P,
+        _lib.or_radio_map.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, P, C.c_int, P,
                                       P, P, P, P, P, P]
         _lib.or_grad.restype = C.c_int
-        _lib.or_grad.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, P, P, P]
+        _lib.or_grad.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, P, P, P, P]
         _lib.or_branch_all.restype = C.c_int
         _lib.or_branch_all.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, P, P, P]
         _lib.or_morton.argtypes = [P, P, C.c_int64, P, P, P]
@@ -133,6 +141,8 @@ def make_params(p) -> OrParams:
     q.freq_hz = float(p.freq_hz)
     q.max_depth = int(p.max_depth)
     q.flags = (F_REFLECT if p.reflect else 0) | (F_REFRACT if p.refract else 0) | (F_LOS if p.los else 0)
+    if getattr(p, "diffuse", False):
+        q.flags |= F_DIFFUSE
     for i in range(3):
         q.map_origin[i] = float(p.map_origin[i])
     q.cell_size = float(p.cell_size)
@@ -151,6 +161,11 @@ def _scene_arrays(scene):
     return v, t, m, mats
 
 
+def _scat(scene):
+    sc = getattr(scene, "scat", None)
+    return None if sc is None else np.ascontiguousarray(sc, np.float32).reshape(-1, 6)
+
+
 # ----------------------------------------------------------------------------
 # elementary functions (for the pins)
 # ----------------------------------------------------------------------------
@@ -161,6 +176,35 @@ def rng_u(seed: int, n: int, l: int) -> float:
 
 def splitmix64(x: int) -> int:
     return int(lib().or_splitmix64(x))
+
+
+def rng_diff(seed: int, n: int, l: int, j: int) -> float:
+    """Variate j (0, 1: direction; 2, 3: phases) of a diffuse reflection."""
+    return float(lib().or_rng_diff(seed, n, l, j))
+
+
+def f_alpha(alpha: int, cos_i: float) -> float:
+    return float(lib().or_f_alpha(alpha, cos_i))
+
+
+def scat_pattern(pattern, ki, n, ks, alpha_r=1, alpha_i=1, lam=1.0):
+    """f_s(k_i, k_s, n) for directions ks [m, 3]."""
+    ki = np.ascontiguousarray(ki, np.float64)
+    n = np.ascontiguousarray(n, np.float64)
+    ks = np.ascontiguousarray(ks, np.float64).reshape(-1, 3)
+    out = np.empty(len(ks), np.float64)
+    lib().or_scat_pattern(int(pattern), int(alpha_r), int(alpha_i), float(lam), _p(ki), _p(n), _p(ks), len(ks),
+                          _p(out))
+    return out
+
+
+def diffuse_dir(n, u):
+    """Scattered directions for variate pairs u [m, 2] about the normal n."""
+    n = np.ascontiguousarray(n, np.float64)
+    u = np.ascontiguousarray(u, np.float64).reshape(-1, 2)
+    out = np.empty((len(u), 3), np.float64)
+    lib().or_diffuse_dir(_p(n), _p(u), len(u), _p(out))
+    return out
 
 
 def fibonacci(N: int, begin: int = 0, count: int | None = None, stride: int = 1) -> np.ndarray:
@@ -218,6 +262,23 @@ def interact(k, n, E, eps_r, sigma, freq_hz, thickness, dec):
     return ko, eo[0::2] + 1j * eo[1::2]
 
 
+def diffuse_interact(k, n, E, eps_r, sigma, freq_hz, thickness, S, K_x=0.0, pattern=0, alpha_r=1, alpha_i=1,
+                     lam=1.0, u=(0.3, 0.2, 0.0, 0.0)):
+    """One diffuse reflection: (scattered direction, field)."""
+    k = np.ascontiguousarray(k, np.float64)
+    n = np.ascontiguousarray(n, np.float64)
+    E = np.asarray(E, np.complex128)
+    e6 = np.ascontiguousarray(np.stack([E.real, E.imag], 1).reshape(-1), np.float64)
+    omega = 2 * np.pi * freq_hz
+    k0d = omega / 299792458.0 * thickness if thickness > 0 else 0.0
+    u4 = np.ascontiguousarray(u, np.float64)
+    ko = np.empty(3, np.float64)
+    eo = np.empty(6, np.float64)
+    lib().or_diffuse_interact(_p(k), _p(n), _p(e6), eps_r, sigma, omega, k0d, S, K_x, int(pattern), int(alpha_r),
+                              int(alpha_i), lam, _p(u4), _p(ko), _p(eo))
+    return ko, eo[0::2] + 1j * eo[1::2]
+
+
 def closest_hit(scene, o, k, exclude=None):
     v, t, _, _ = _scene_arrays(scene)
     o = np.ascontiguousarray(o, np.float64).reshape(-1, 3)
@@ -262,7 +323,8 @@ def radio_map(scene, tx, params, mode: str = "plain", record=None, want_record: 
     st = np.empty(3 * (L + 1), np.float64) if stats else None
     ms = np.empty((params.ny, params.nx), np.float64) if mass else None
     rep = OrReport()
-    rc = lib().or_radio_map(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), C.byref(otx),
+    sc = _scat(scene)
+    rc = lib().or_radio_map(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), _p(sc), C.byref(otx),
                             C.byref(op), MODES[mode], _p(rec), _p(sm), _p(em), _p(mp), _p(st),
                             C.byref(rep), _p(ms))
     if rc != 0:
@@ -288,10 +350,11 @@ def grad(scene, tx, params, record, dLdC):
     g = np.ascontiguousarray(dLdC, np.float64)
     nm = len(mats)
     out = np.empty(2 * nm + 3, np.float64)
-    rc = lib().or_grad(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), nm, C.byref(otx), C.byref(op),
+    sc = _scat(scene)
+    rc = lib().or_grad(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), nm, _p(sc), C.byref(otx), C.byref(op),
                        _p(rec), _p(g), _p(out))
     if rc != 0:
-        raise ValueError("or_grad supports at most 8 materials")
+        raise ValueError(f"or_grad failed ({rc}): at most 8 materials, valid scattering parameters")
     return out[:nm].copy(), out[nm:2 * nm].copy(), out[2 * nm:].copy()
 
 
@@ -306,7 +369,7 @@ def branch_all(scene, tx, params):
     rc = lib().or_branch_all(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), C.byref(otx),
                              C.byref(op), _p(mp), _p(pw), _p(es))
     if rc != 0:
-        raise ValueError("or_branch_all: depth too large")
+        raise ValueError(f"or_branch_all failed ({rc}): depth too large or diffuse reflection on")
     return mp, pw, es
 
 

@@ -204,6 +204,11 @@ inline double rng_u(uint64_t seed, uint64_t n, int l) {
 // stream: the seed xor-ed with a fixed odd constant.
 constexpr uint64_t RR_STREAM = 0xD6E8FEB86659FD93ULL;
 inline double rng_rr(uint64_t seed, uint64_t n, int l) { return rng_u(seed ^ RR_STREAM, n, l); }
+// The four variates of a diffuse reflection (two for the direction, two for
+// the random phases) come from four more streams.
+constexpr uint64_t DIFF_STREAM[4] = {0x2545F4914F6CDD1DULL, 0x9E6C63D0676A9A99ULL, 0x7F4A7C159E3779B9ULL,
+                                     0xC2B2AE3D27D4EB4FULL};
+inline double rng_diff(uint64_t seed, uint64_t n, int l, int j) { return rng_u(seed ^ DIFF_STREAM[j], n, l); }
 
 // ---------------------------------------------------------------------------
 // Spherical Fibonacci lattice (Sec. 3.1.1)
@@ -351,10 +356,15 @@ struct Tri {
 struct Scene {
     std::vector<Tri> tris;
     std::vector<double> eps, sigma, thick;
+    // diffuse reflection (App. A.10): scattering coefficient S, cross-polarisation
+    // share K_x, pattern (0 Lambertian, 1 directive, 2 backscattering), alpha_R,
+    // alpha_I, Lambda
+    std::vector<double> scS, scK, scLam;
+    std::vector<int> scPat, scAR, scAI;
 };
 
 Scene make_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
-                 const int32_t* tri_mat, const float* mats, int nm) {
+                 const int32_t* tri_mat, const float* mats, int nm, const float* scat = nullptr) {
     (void)nv;
     Scene s;
     s.tris.resize(nt);
@@ -379,6 +389,13 @@ Scene make_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
         s.eps.push_back(mats[3 * m]);
         s.sigma.push_back(mats[3 * m + 1]);
         s.thick.push_back(mats[3 * m + 2]);
+        const float* sc = scat ? scat + 6 * m : nullptr;
+        s.scS.push_back(sc ? sc[0] : 0.0);
+        s.scK.push_back(sc ? sc[1] : 0.0);
+        s.scPat.push_back(sc ? (int)sc[2] : 0);
+        s.scAR.push_back(sc ? (int)sc[3] : 1);
+        s.scAI.push_back(sc ? (int)sc[4] : 1);
+        s.scLam.push_back(sc ? sc[5] : 1.0);
     }
     return s;
 }
@@ -460,7 +477,7 @@ struct or_params {
     double rr_max_prob;        // p_rr,max; 0 = no Russian roulette
     double gain_threshold;     // linear gain below which a path stops; 0 = off
 };
-enum { F_REFLECT = 1, F_REFRACT = 2, F_LOS = 4 };
+enum { F_REFLECT = 1, F_REFRACT = 2, F_LOS = 4, F_DIFFUSE = 16 };
 struct or_report {
     int64_t segments, deposits, adopted_hit, adopted_cell, adopted_decision, failures;
     int64_t adopted_hit_tie;  // adopted hits whose distance equals the FP64 closest hit within tol
@@ -576,6 +593,73 @@ void deposit(const MapGeom& g, const Crossing<R>& c, int ix, int iy, const R& va
 }
 
 // ---------------------------------------------------------------------------
+// diffuse reflection (App. A.10)
+// ---------------------------------------------------------------------------
+inline double binom(int n, int k) {
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+// F_alpha(theta_i) of Eq. directive_model: the integral of ((1 + k_r.k_s)/2)^alpha
+// over the hemisphere of k_s, in the closed form printed with the model.
+double f_alpha(int alpha, double cos_i) {
+    const double sin2 = (1.0 - cos_i) * (1.0 + cos_i);
+    double F = 0.0;
+    for (int k = 0; k <= alpha; ++k) {
+        double Ik = 2.0 * PI / (k + 1);
+        if (k % 2 == 1) {
+            double s = 0.0;
+            for (int w = 0; w <= (k - 1) / 2; ++w) s += binom(2 * w, w) * std::pow(sin2, w) / std::pow(2.0, 2 * w);
+            Ik *= cos_i * s;
+        }
+        F += binom(alpha, k) * Ik;
+    }
+    return F / std::pow(2.0, alpha);
+}
+// Scattering pattern f_s(k_i, k_s, n): Lambertian (0, Eq. lambertian_model),
+// directive (1, Eq. directive_model) or backscattering (2, Eq.
+// backscattering_model).  n is the unit normal on the incident side.
+double scat_pattern(int pattern, int aR, int aI, double lam, const V3<double>& ki, const V3<double>& ks,
+                    const V3<double>& n) {
+    if (pattern == 0) return dot(n, ks) / PI;
+    const double cos_i = -dot(ki, n);
+    const V3<double> kr = ki - scl(n, 2.0 * dot(ki, n));  // specular direction
+    const double lobe_r = std::pow((1.0 + dot(kr, ks)) / 2.0, aR);
+    if (pattern == 1) return lobe_r / f_alpha(aR, cos_i);
+    const double lobe_i = std::pow((1.0 - dot(ki, ks)) / 2.0, aI);
+    return (lam * lobe_r + (1.0 - lam) * lobe_i) / (lam * f_alpha(aR, cos_i) + (1.0 - lam) * f_alpha(aI, cos_i));
+}
+// Direction of the ray tube a diffuse reflection spawns: uniform on the
+// hemisphere around n (solid angle 2 pi, Sec. 4 estimator).  Reading (the
+// paper fixes no parametrisation): cos theta_s = 1 - u1, phi_s = 2 pi u2 in
+// the tangent frame (t1, t2) of m = n (or m = -n when n_z < -1/2), with
+// t1 = (1 - m_x^2 a, -m_x m_y a, -m_x), t2 = (-m_x m_y a, 1 - m_y^2 a, -m_y),
+// a = 1 / (1 + m_z)  (Frisvad, JGT 2012).
+V3<double> diffuse_dir(const V3<double>& n, double u1, double u2) {
+    const V3<double> m = n.z >= -0.5 ? n : scl(n, -1.0);
+    const double a = 1.0 / (1.0 + m.z), b = -m.x * m.y * a;
+    const V3<double> t1{1.0 - m.x * m.x * a, b, -m.x}, t2{b, 1.0 - m.y * m.y * a, -m.y};
+    const double cs = 1.0 - u1, sn = std::sqrt(u1 * (2.0 - u1)), ph = 2.0 * PI * u2;
+    return scl(t1, sn * std::cos(ph)) + scl(t2, sn * std::sin(ph)) + scl(n, cs);
+}
+// theta_hat(k), phi_hat(k) of a direction (Eq. spherical_vecs); poles: phi = 0.
+inline void sph_basis(const V3<double>& k, V3<double>* th, V3<double>* ph) {
+    const double t = std::acos(std::max(-1.0, std::min(1.0, k.z)));
+    const double p = std::atan2(k.y, k.x);
+    *th = theta_hat(t, p);
+    *ph = phi_hat(p);
+}
+bool scat_valid(const Scene& S) {
+    for (size_t m = 0; m < S.scS.size(); ++m) {
+        if (!(S.scS[m] >= 0.0 && S.scS[m] <= 1.0) || !(S.scK[m] >= 0.0 && S.scK[m] <= 1.0)) return false;
+        if (S.scPat[m] < 0 || S.scPat[m] > 2 || S.scAR[m] < 1 || S.scAR[m] > 32 || S.scAI[m] < 1 ||
+            S.scAI[m] > 32 || !(S.scLam[m] >= 0.0 && S.scLam[m] <= 1.0))
+            return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // the SBR loop for one lattice ray
 // ---------------------------------------------------------------------------
 struct TxC {
@@ -680,6 +764,37 @@ bool certify_hit(const Scene& S, const V3<double>& o, const V3<double>& k, int e
     return true;
 }
 
+// Field of the ray tube a diffuse reflection spawns in direction ks (Eq.
+// scattered_field), for an incident field E travelling along k: the theta/phi
+// components of E (basis of k) are mixed by the cross-polarisation matrix
+// with random phases chi_1, chi_2, mapped onto the theta/phi basis of ks and
+// scaled by S Gamma sqrt(2 pi f_s), with
+//   Gamma^2 = (|r_perp E_perp|^2 + |r_par E_par|^2) / |E|^2
+// from the unreduced reflection coefficients of cf (e_perp, e_par,i: ep, epi).
+// The sqrt(2 pi f_s) collects the sqrt(f_s cos theta_i dA) of the model and the
+// weight 2 pi r^2 / |n.k_i| the estimator gives a diffuse point (Sec. 4): the
+// tube length and cos theta_i cancel.
+template <class R>
+CV3<R> diffuse_field(const V3<double>& k, const V3<double>& ks, const V3<double>& ep, const V3<double>& epi,
+                     const Coefs<R>& cf, double Sd, double Kx, double fs, double chi1, double chi2,
+                     const CV3<R>& E) {
+    CV3<R> out;
+    const Cx<R> a = cdot(ep, E), b = cdot(epi, E);
+    const R g2 = abs2(cf.r_perp * a) + abs2(cf.r_par * b);
+    const R e2 = cnorm2(E);
+    if (!(val(e2) > 0.0 && val(g2) > 0.0 && fs > 0.0)) return out;
+    const R c = r_sqrt(g2 / e2) * (Sd * std::sqrt(2.0 * PI * fs));
+    const double sK = std::sqrt(Kx), cK = std::sqrt(1.0 - Kx);
+    const Cx<R> ph1(R(std::cos(chi1)), R(std::sin(chi1))), ph2(R(std::cos(chi2)), R(std::sin(chi2)));
+    V3<double> thi, phi_i, ths, phs;
+    sph_basis(k, &thi, &phi_i);
+    sph_basis(ks, &ths, &phs);
+    const Cx<R> Et = cdot(thi, E), Ef = cdot(phi_i, E);
+    const Cx<R> As = (Et * R(cK) - Ef * R(sK)) * ph1 * c;
+    const Cx<R> Bs = (Et * R(sK) + Ef * R(cK)) * ph2 * c;
+    return outer(ths, As) + outer(phs, Bs);
+}
+
 template <class R, class SinkT>
 void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta, const R* k0d,
                int64_t n, int64_t i_sub, Rec* rec_io, SinkT& sink, ReplayState* rs,
@@ -699,6 +814,7 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
     V3<R> o = txpos;
     double inv_pr = 1.0;  // 1 / Pr(chi): detached from the parameters
     double path = 0.0;    // unfolded length (only used for tie tolerances)
+    double tube = 0.0;    // length of the current ray tube (since the source or the last diffuse point)
     int prev = -1;
     int l = 0;
     for (; l <= L; ++l) {
@@ -815,8 +931,16 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         cos1 = std::min(1.0, std::max(0.0, cos1));
         bool slab = S.thick[m] > 0.0;
         Coefs<R> cf = fresnel(eta[m], cos1, k0d[m], slab);
-        // sampling probabilities from the (detached) sampling materials
-        double qR, qT;
+        // Diffuse reflection (App. A.10) takes the share S^2 of the reflected
+        // power; the specular coefficients are reduced by R = sqrt(1 - S^2)
+        // (Eq. R).  Sampling (Eq. path-solver-used-dist-event, q(D) = 0):
+        // q(R) = R^2 wR / (wR + wT), q(S) = S^2 wR / (wR + wT), q(T) = wT / (wR + wT)
+        // with wR, wT the squared magnitudes of the unreduced coefficients.
+        // The coin: u < q(R) -> R, else u < wR / (wR + wT) -> S, else T.
+        const double Sd = ((C.flags & F_DIFFUSE) && (C.flags & F_REFLECT)) ? S.scS[m] : 0.0;
+        const double R2 = (1.0 - Sd) * (1.0 + Sd);
+        const double Rred = std::sqrt(R2);
+        double c1, c2, qR, qS, qT;
         {
             Cx<double> es = permittivity(C.s_eps[m], C.s_sig[m], C.omega);
             double kd = C.k0 * S.thick[m];
@@ -828,20 +952,28 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
                 if (C.mode == MODE_REPLAY && rec->dec != -1) rs->fail(i_sub, l, 3, -1, rec->dec, 0, 0);
                 break;
             }
-            qR = wR / (wR + wT);
+            c2 = wR / (wR + wT);
+            c1 = R2 * c2;
+            qR = c1;
+            qS = Sd * Sd * c2;
             qT = wT / (wR + wT);
         }
         double u = rng_u(tx.seed, (uint64_t)n, l);
-        int dec = (u < qR) ? 0 : 1;
+        int dec = (u < c1) ? 0 : (u < c2 ? 2 : 1);
         if (C.mode == MODE_FROZEN) {
             dec = rec->dec & 3;
         } else if (C.mode == MODE_REPLAY) {
             if ((rec->dec & 3) != dec) {
-                if (std::fabs(u - qR) <= 1e-5 && rec->dec >= 0 && (rec->dec & 3) <= 1) {
+                // adopt the GPU's choice g if u lies within 1e-5 of g's interval
+                // [lo, hi) of positive probability
+                const int g = rec->dec & 3;
+                const double lo = g == 0 ? 0.0 : (g == 2 ? c1 : c2);
+                const double hi = g == 0 ? c1 : (g == 2 ? c2 : 1.0);
+                if (rec->dec >= 0 && g != 3 && hi > lo && u > lo - 1e-5 && u < hi + 1e-5) {
                     rs->rep.adopted_decision++;
-                    dec = rec->dec & 3;
+                    dec = g;
                 } else {
-                    rs->fail(i_sub, l, 3, dec, rec->dec, u, qR);
+                    rs->fail(i_sub, l, 3, dec, rec->dec, u, dec == 0 || g == 0 ? c1 : c2);
                     return;
                 }
             }
@@ -863,25 +995,42 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         }
         V3<double> epi = cross(ep, k);
         V3<double> k_out;
-        V3<double> epo;
-        Cx<R> cperp, cpar;
-        if (dec == 0) {
-            k_out = k - scl(nn, 2.0 * dot(k, nn));
-            epo = unit(cross(ep, k_out));
-            cperp = cf.r_perp;
-            cpar = cf.r_par;
-            inv_pr /= qR;
+        if (dec == 2) {
+            // Diffuse reflection: a new ray tube in a uniformly sampled direction
+            // of the incident-side hemisphere.  Its field follows Eq.
+            // scattered_field with Gamma^2 = (|r_perp E_perp|^2 + |r_par E_par|^2) / |E|^2
+            // (unreduced r), the cross-polarisation split K_x and the random
+            // phases chi_1, chi_2 = 2 pi u.  The estimator (Sec. 4, weight
+            // 2 pi r^2 / |n.k_i| per diffuse point) cancels the tube length and
+            // cos theta_i against Eq. scattered_field's 1/r and
+            // sqrt(cos theta_i dA), which leaves the factor sqrt(2 pi f_s).
+            k_out = diffuse_dir(nn, rng_diff(tx.seed, (uint64_t)n, l, 0), rng_diff(tx.seed, (uint64_t)n, l, 1));
+            const double fs = scat_pattern(S.scPat[m], S.scAR[m], S.scAI[m], S.scLam[m], k, k_out, nn);
+            const double x1 = 2.0 * PI * rng_diff(tx.seed, (uint64_t)n, l, 2);
+            const double x2 = 2.0 * PI * rng_diff(tx.seed, (uint64_t)n, l, 3);
+            for (int p = 0; p < npol; ++p) E[p] = diffuse_field(k, k_out, ep, epi, cf, Sd, S.scK[m], fs, x1, x2, E[p]);
+            inv_pr /= qS;
         } else {
-            k_out = k;  // thin slab: no deflection (Sec. 2.3)
-            epo = epi;
-            cperp = cf.t_perp;
-            cpar = cf.t_par;
-            inv_pr /= qT;
-        }
-        for (int p = 0; p < npol; ++p) {
-            Cx<R> a = cdot(ep, E[p]);
-            Cx<R> b = cdot(epi, E[p]);
-            E[p] = outer(ep, cperp * a) + outer(epo, cpar * b);
+            V3<double> epo;
+            Cx<R> cperp, cpar;
+            if (dec == 0) {
+                k_out = k - scl(nn, 2.0 * dot(k, nn));
+                epo = unit(cross(ep, k_out));
+                cperp = cf.r_perp * R(Rred);
+                cpar = cf.r_par * R(Rred);
+                inv_pr /= qR;
+            } else {
+                k_out = k;  // thin slab: no deflection (Sec. 2.3)
+                epo = epi;
+                cperp = cf.t_perp;
+                cpar = cf.t_par;
+                inv_pr /= qT;
+            }
+            for (int p = 0; p < npol; ++p) {
+                Cx<R> a = cdot(ep, E[p]);
+                Cx<R> b = cdot(epi, E[p]);
+                E[p] = outer(ep, cperp * a) + outer(epo, cpar * b);
+            }
         }
         // new origin: hit point pushed off the surface along the outgoing side.
         // Reading (paper silent): offset 2^-16 * max(1, |p|_inf) metres.
@@ -891,16 +1040,18 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         if (std::fabs(phv.y) > std::fabs(val(*big))) big = &ph.y;
         if (std::fabs(phv.z) > std::fabs(val(*big))) big = &ph.z;
         R delta = std::fabs(val(*big)) > 1.0 ? r_abs(*big) * 0x1.0p-16 : R(0x1.0p-16);
-        V3<double> nout = (dec == 0) ? nn : scl(nn, -1.0);
+        V3<double> nout = (dec == 1) ? scl(nn, -1.0) : nn;
         o = {ph.x + delta * nout.x, ph.y + delta * nout.y, ph.z + delta * nout.z};
         path += val(t_h);
+        tube = (dec == 2) ? 0.0 : tube + val(t_h);  // a diffuse reflection starts a new tube
         k = k_out;
         prev = prim;
         // ---- early termination after rr_depth interactions (Sec. 4.7) ----
         // Reading: the gain of a sample is w |E|^2 with w = 1 / Pr(chi) (the
         // tube-length-normalised gain of the paper); gain thresholding stops a
         // path when (lambda0 / 4 pi)^2 w |E|^2 / r^2 < threshold at its tube
-        // length r; Russian roulette (Eq. radio-map-solver-rr-prob) keeps it
+        // length r > 0 (a tube a diffuse reflection has just spawned has r = 0
+        // and is not thresholded); Russian roulette (Eq. radio-map-solver-rr-prob) keeps it
         // with p = min(w |E|^2, p_max) and reweights the power of survivors by
         // 1 / p (the field by 1 / sqrt(p)); p is detached like q.
         if (C.rr_depth > 0 && l + 1 >= C.rr_depth && (C.gain_thr > 0.0 || C.rr_pmax > 0.0)) {
@@ -908,8 +1059,8 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
             for (int p = 0; p < npol; ++p) w2v += val(cnorm2(E[p]));
             w2v *= inv_pr;
             int kill = 0;
-            if (C.gain_thr > 0.0) {
-                const double gain = C.lam4pi2 * w2v / (path * path);
+            if (C.gain_thr > 0.0 && tube > 0.0) {
+                const double gain = C.lam4pi2 * w2v / (tube * tube);
                 kill = gain < C.gain_thr ? 8 : 0;
                 if (C.mode == MODE_FROZEN) {
                     kill = rec->dec & 8;
@@ -996,6 +1147,23 @@ int or_num_threads(void) {
 }
 
 double or_rng_u(uint64_t seed, uint64_t n, int l) { return rng_u(seed, n, l); }
+double or_rng_diff(uint64_t seed, uint64_t n, int l, int j) { return rng_diff(seed, n, l, j & 3); }
+
+// Diffuse-reflection pieces, for the pins.
+double or_f_alpha(int alpha, double cos_i) { return f_alpha(alpha, cos_i); }
+void or_scat_pattern(int pattern, int aR, int aI, double lam, const double* ki, const double* n,
+                     const double* ks, int64_t count, double* out) {
+    const V3<double> a{ki[0], ki[1], ki[2]}, nn{n[0], n[1], n[2]};
+    for (int64_t i = 0; i < count; ++i)
+        out[i] = scat_pattern(pattern, aR, aI, lam, a, {ks[3 * i], ks[3 * i + 1], ks[3 * i + 2]}, nn);
+}
+void or_diffuse_dir(const double* n, const double* u, int64_t count, double* out) {
+    const V3<double> nn{n[0], n[1], n[2]};
+    for (int64_t i = 0; i < count; ++i) {
+        V3<double> d = diffuse_dir(nn, u[2 * i], u[2 * i + 1]);
+        out[3 * i] = d.x; out[3 * i + 1] = d.y; out[3 * i + 2] = d.z;
+    }
+}
 uint64_t or_splitmix64(uint64_t x) { return splitmix64(x); }
 
 void or_fibonacci(int64_t N, int64_t begin, int64_t count, int64_t stride, double* out) {
@@ -1070,6 +1238,36 @@ void or_interact(const double* k3, const double* n3, const double* E6, double ep
     Eout[4] = Eo.z.re; Eout[5] = Eo.z.im;
 }
 
+// A diffuse reflection at one interface, for the pins: incident direction k,
+// normal n (any sign), field E (6 doubles), material (eps_r, sigma, k0d),
+// scattering parameters and the four variates u4 (direction, phases).
+// Writes the scattered direction (3) and field (6).
+void or_diffuse_interact(const double* k3, const double* n3, const double* E6, double eps_r, double sigma,
+                         double omega, double k0d, double Sd, double Kx, int pattern, int aR, int aI, double lam,
+                         const double* u4, double* kout, double* Eout) {
+    V3<double> k{k3[0], k3[1], k3[2]}, n{n3[0], n3[1], n3[2]};
+    n = unit(n);
+    V3<double> nn = dot(n, k) < 0.0 ? n : scl(n, -1.0);
+    double cos1 = std::min(1.0, std::max(0.0, -dot(k, nn)));
+    Coefs<double> cf = fresnel(permittivity(eps_r, sigma, omega), cos1, k0d, k0d > 0.0);
+    V3<double> kxn = cross(k, nn);
+    double kn = norm(kxn);
+    V3<double> ep;
+    if (kn > 1e-12) ep = scl(kxn, 1.0 / kn);
+    else {
+        V3<double> ax = std::fabs(k.x) < 0.5 ? V3<double>{1, 0, 0} : V3<double>{0, 1, 0};
+        ep = unit(cross(k, ax));
+    }
+    V3<double> epi = cross(ep, k);
+    V3<double> ks = diffuse_dir(nn, u4[0], u4[1]);
+    double fs = scat_pattern(pattern, aR, aI, lam, k, ks, nn);
+    CV3<double> E{Cx<double>(E6[0], E6[1]), Cx<double>(E6[2], E6[3]), Cx<double>(E6[4], E6[5])};
+    CV3<double> Eo = diffuse_field(k, ks, ep, epi, cf, Sd, Kx, fs, 2.0 * PI * u4[2], 2.0 * PI * u4[3], E);
+    kout[0] = ks.x; kout[1] = ks.y; kout[2] = ks.z;
+    Eout[0] = Eo.x.re; Eout[1] = Eo.x.im; Eout[2] = Eo.y.re; Eout[3] = Eo.y.im;
+    Eout[4] = Eo.z.re; Eout[5] = Eo.z.im;
+}
+
 // Closest hit of a batch of rays (brute force), for the pins.
 void or_closest_hit(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     const double* o, const double* k, int64_t nrays, const int32_t* exclude,
@@ -1098,12 +1296,13 @@ void or_closest_hit(const float* verts, int64_t nv, const int32_t* tris, int64_t
 // map_out [ny][nx] is overwritten.  stats (or null): per depth 0..L
 // [power, power^2, escaped power] sums of w |E|^2 (without the 4 pi / N factor).
 int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
-                 const int32_t* tri_mat, const float* mats, int nm, const or_tx* tx,
+                 const int32_t* tri_mat, const float* mats, int nm, const float* scat, const or_tx* tx,
                  const or_params* P, int mode, int32_t* rec, const double* sampling_mats,
                  const double* eval_mats, double* map_out, double* stats, or_report* report,
                  double* mass_out) {
     if (P->max_depth < 0 || P->max_depth > 15) return 1;
-    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
+    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm, scat);
+    if (!scat_valid(S)) return 2;
     if (eval_mats)
         for (int m = 0; m < nm; ++m) { S.eps[m] = eval_mats[2 * m]; S.sigma[m] = eval_mats[2 * m + 1]; }
     std::vector<double> seps(S.eps), ssig(S.sigma);
@@ -1196,10 +1395,11 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
 // plain run) and the sampling probabilities detached.  Forward-mode dual
 // numbers; nm <= 8.  grad_out: [nm] d/deps, [nm] d/dsigma, [3] d/dtx.
 int or_grad(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
-            const float* mats, int nm, const or_tx* tx, const or_params* P, const int32_t* rec,
-            const double* dLdC, double* grad_out) {
+            const float* mats, int nm, const float* scat, const or_tx* tx, const or_params* P,
+            const int32_t* rec, const double* dLdC, double* grad_out) {
     if (nm > 8) return 1;
-    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
+    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm, scat);
+    if (!scat_valid(S)) return 2;
     Ctx C;
     C.S = &S;
     C.g = make_geom(*P, tx->num_rays);
@@ -1333,6 +1533,8 @@ int or_branch_all(const float* verts, int64_t nv, const int32_t* tris, int64_t n
                   const int32_t* tri_mat, const float* mats, int nm, const or_tx* tx,
                   const or_params* P, double* map_out, double* power_out, double* escaped_out) {
     if (P->max_depth < 0 || P->max_depth > 12) return 1;
+    // diffuse directions are continuous: they cannot be enumerated
+    if (P->flags & F_DIFFUSE) return 3;
     Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
     Ctx C;
     C.S = &S;

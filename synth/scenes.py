@@ -36,6 +36,10 @@ class Scene:
     tri_mat: np.ndarray    # int32 [nt]
     mats: np.ndarray       # float32 [nm, 3] = (eps_r, sigma S/m, thickness m)
     footprints: list = field(default_factory=list)  # (cx, cy, r) or (x0,x1,y0,y1)
+    # diffuse reflection parameters, float32 [nm, 6] = (S, K_x, pattern, alpha_R,
+    # alpha_I, Lambda) with pattern 0 Lambertian, 1 directive, 2 backscattering;
+    # None = no diffuse reflection (S = 0)
+    scat: np.ndarray | None = None
 
     @property
     def nt(self) -> int:
@@ -46,13 +50,23 @@ class Scene:
         return int(self.mats.shape[0])
 
     def save(self, path: str) -> None:
+        extra = {} if self.scat is None else {"scat": self.scat}
         np.savez(path, verts=self.verts, tris=self.tris, tri_mat=self.tri_mat,
-                 mats=self.mats, name=np.array(self.name))
+                 mats=self.mats, name=np.array(self.name), **extra)
 
     @staticmethod
     def load(path: str) -> "Scene":
         z = np.load(path)
-        return Scene(str(z["name"]), z["verts"], z["tris"], z["tri_mat"], z["mats"])
+        return Scene(str(z["name"]), z["verts"], z["tris"], z["tri_mat"], z["mats"],
+                     scat=z["scat"] if "scat" in z else None)
+
+    def with_scattering(self, S, K_x=0.0, pattern=0, alpha_r=1, alpha_i=1, lam=1.0) -> "Scene":
+        """A copy whose materials all get the diffuse parameters given (scalars or
+        per-material sequences)."""
+        nm = self.nm
+        cols = [np.broadcast_to(np.asarray(c, np.float32), (nm,)) for c in (S, K_x, pattern, alpha_r, alpha_i, lam)]
+        return Scene(self.name, self.verts, self.tris, self.tri_mat, self.mats, list(self.footprints),
+                     np.ascontiguousarray(np.stack(cols, 1)))
 
 
 @dataclass
@@ -93,6 +107,7 @@ class TraceParams:
     rr_depth: int = 0     # early termination after this many interactions (0 = off)
     rr_max_prob: float = 0.0
     gain_threshold: float = 0.0
+    diffuse: bool = False  # diffuse reflection on materials with S > 0
 
     def map_corner(self):
         """Lower-left corner (x0, y0) of a map centred on map_origin."""
