@@ -57,11 +57,28 @@ typedef enum {
  * evaluated at the trace frequency.  thickness > 0: a single-layer slab of
  * that thickness in metres (Eqs. fresnel_slab, q_fresnel_slab) that reflects
  * and transmits without deflection (Sec. 2.3); thickness <= 0: a half-space
- * that only reflects (Eq. fresnel_vac, transmission coefficient 0). */
+ * that only reflects (Eq. fresnel_vac, transmission coefficient 0).
+ *
+ * Diffuse reflection (App. A.10; used only under RM_DIFFUSE): the share
+ * S^2 of the reflected power is scattered into the incident-side hemisphere,
+ * the specular coefficients are reduced by R = sqrt(1 - S^2) (Eq. R), and
+ * the scattered field follows Eq. scattered_field with the cross-polarisation
+ * share K_x and the scattering pattern f_s: 0 Lambertian (Eq.
+ * lambertian_model), 1 directive with lobe exponent alpha_r (Eq.
+ * directive_model), 2 backscattering with exponents alpha_r, alpha_i and lobe
+ * split lambda (Eq. backscattering_model).  scattering = 0 disables it for
+ * the material; the remaining fields are then ignored.  All-zero diffuse
+ * fields are valid (no diffuse reflection). */
 typedef struct {
     float eps_r;
-    float sigma;      /* S/m */
-    float thickness;  /* m */
+    float sigma;        /* S/m */
+    float thickness;    /* m */
+    float scattering;   /* S in [0, 1] */
+    float xpd_k;        /* K_x in [0, 1] */
+    int32_t pattern;    /* 0, 1 or 2 (see above) */
+    int32_t alpha_r;    /* 1..32 for patterns 1 and 2 */
+    int32_t alpha_i;    /* 1..32 for pattern 2 */
+    float lobe_lambda;  /* Lambda in [0, 1] for pattern 2 */
 } rm_material;
 
 /* One transmitter.  Rays are the lattice directions n = ray_begin + i *
@@ -98,11 +115,12 @@ typedef struct {
 #define RM_REFRACT 2u   /* allow refraction through slabs */
 #define RM_LOS 4u       /* deposit the line-of-sight segment (depth 0) */
 #define RM_STATS 8u     /* collect per-depth power statistics (slower) */
+#define RM_DIFFUSE 16u  /* diffuse reflection on materials with scattering > 0 (needs RM_REFLECT) */
 
 typedef struct {
     double freq_hz;          /* carrier frequency f; lambda0 = c0 / f */
     int32_t max_depth;       /* L in [0, RM_MAX_DEPTH]; segments l = 0..L are deposited */
-    uint32_t flags;          /* RM_REFLECT | RM_REFRACT | RM_LOS [| RM_STATS] */
+    uint32_t flags;          /* RM_REFLECT | RM_REFRACT | RM_LOS [| RM_STATS] [| RM_DIFFUSE] */
     float map_origin[3];     /* centre of the map; the plane is z = map_origin[2], normal +z */
     float cell_size;         /* m, > 0 */
     int32_t nx, ny;          /* cells, >= 1, nx * ny <= 2^31 - 1, nx, ny <= 32767 */
@@ -169,7 +187,9 @@ rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tri
 
 /* Replaces the material table (no BVH rebuild).  sampling_host_or_null
  * (nm entries) sets the materials from which the interaction probabilities
- * q(R), q(T) are computed (detached from the fields); NULL = mats_host. */
+ * q(R), q(S), q(T) are computed (detached from the fields); NULL = mats_host.
+ * Only eps_r and sigma of a sampling material are used: thickness and the
+ * diffuse parameters always come from mats_host. */
 rm_status rm_scene_set_materials(rm_scene* scene, const rm_material* mats_host, int32_t nm,
                                  const rm_material* sampling_host_or_null);
 

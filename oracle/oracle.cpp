@@ -551,10 +551,12 @@ struct Sink;
 template <>
 struct Sink<double> {
     DepList* list;
-    DepList* mass = nullptr;  // unweighted deposit value per stencil cell (bilinear error bound)
+    DepList* mass = nullptr;   // unweighted deposit value per stencil cell (bilinear error bound)
+    DepList* cmass = nullptr;  // the same, times the crossing's conditioning factor
     void add(int cell, const double& v) { list->cell.push_back(cell); list->val.push_back(v); }
-    void add_mass(int cell, const double& v) {
+    void add_mass(int cell, const double& v, double cond) {
         if (mass) { mass->cell.push_back(cell); mass->val.push_back(v); }
+        if (cmass) { cmass->cell.push_back(cell); cmass->val.push_back(v * cond); }
     }
 };
 template <>
@@ -565,15 +567,19 @@ struct Sink<D> {
         const double w = gmap[cell];
         for (int i = 0; i < NT; ++i) acc[i] += w * v.g[i];
     }
-    void add_mass(int, const D&) {}
+    void add_mass(int, const D&, double) {}
 };
 
+// cond: first-order conditioning of the crossing point x_c = o + t_c k against
+// perturbations of the origin and direction (test bookkeeping only, see
+// trace_ray); it does not enter the map.
 template <class R, class SinkT>
-void deposit(const MapGeom& g, const Crossing<R>& c, int ix, int iy, const R& value, SinkT& sink) {
+void deposit(const MapGeom& g, const Crossing<R>& c, int ix, int iy, const R& value, SinkT& sink,
+             double cond = 1.0) {
     if (!g.bilinear) {
         if (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny) {
             sink.add(iy * g.nx + ix, value);
-            sink.add_mass(iy * g.nx + ix, value);
+            sink.add_mass(iy * g.nx + ix, value, cond);
         }
         return;
     }
@@ -588,7 +594,7 @@ void deposit(const MapGeom& g, const Crossing<R>& c, int ix, int iy, const R& va
             int cx = ix + a, cy = iy + b;
             if (cx < 0 || cx >= g.nx || cy < 0 || cy >= g.ny) continue;
             sink.add(cy * g.nx + cx, value * (wx[a] * wy[b]));
-            sink.add_mass(cy * g.nx + cx, value);
+            sink.add_mass(cy * g.nx + cx, value, cond);
         }
 }
 
@@ -917,7 +923,14 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
             R e2(0.0);
             for (int p = 0; p < npol; ++p) e2 = e2 + cnorm2(E[p]);
             R value = e2 * (C.g.K * inv_pr / std::fabs(k.z));
-            deposit(C.g, cr, dix, diy, value, sink);
+            // A perturbation (d o, d k) of the segment moves x_c by at most
+            //   (|d o| + t_c |d k|) (1 + (|k_x| + |k_y|) / |k_z|);
+            // with |d o| ~ eps (1 + |o|_inf + path) and |d k| ~ eps this is
+            // eps * cond with the cond below.
+            const double tcv = (C.g.z - ov.z) / k.z;
+            const double om = std::max(std::fabs(ov.x), std::max(std::fabs(ov.y), std::fabs(ov.z)));
+            const double cond = (1.0 + om + path + std::fabs(tcv)) * (1.0 + (std::fabs(k.x) + std::fabs(k.y)) / std::fabs(k.z));
+            deposit(C.g, cr, dix, diy, value, sink, cond);
             if (rs) rs->rep.deposits++;
         }
         // ---- termination ---------------------------------------------------
@@ -1295,6 +1308,9 @@ void or_closest_hit(const float* verts, int64_t nv, const int32_t* tris, int64_t
 // eval_mats likewise overrides the materials the fields are evaluated with.
 // map_out [ny][nx] is overwritten.  stats (or null): per depth 0..L
 // [power, power^2, escaped power] sums of w |E|^2 (without the 4 pi / N factor).
+// mass_out (or null) [2][ny][nx]: per cell, the sum of the unweighted values
+// of the deposits whose stencil covers it, and the same sum with every value
+// multiplied by its crossing's conditioning factor (test error bounds).
 int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                  const int32_t* tri_mat, const float* mats, int nm, const float* scat, const or_tx* tx,
                  const or_params* P, int mode, int32_t* rec, const double* sampling_mats,
@@ -1331,7 +1347,7 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
     const int L = P->max_depth;
     const int64_t CH = 2048;  // fixed chunking: the summation order is independent of threads
     const int64_t nch = (cnt + CH - 1) / CH;
-    std::vector<DepList> lists(nch), masses(mass_out ? nch : 0);
+    std::vector<DepList> lists(nch), masses(mass_out ? nch : 0), cmasses(mass_out ? nch : 0);
     const int nthr = or_num_threads();
     std::vector<double> st((size_t)nthr * 3 * (L + 1), 0.0);
     std::vector<ReplayState> rss(nch);
@@ -1344,7 +1360,7 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
         int tid = 0;
 #endif
         double* sp = stats ? st.data() + (size_t)tid * 3 * (L + 1) : nullptr;
-        Sink<double> sink{&lists[c], mass_out ? &masses[c] : nullptr};
+        Sink<double> sink{&lists[c], mass_out ? &masses[c] : nullptr, mass_out ? &cmasses[c] : nullptr};
         int64_t e = std::min(cnt, (c + 1) * CH);
         for (int64_t i = c * CH; i < e; ++i) {
             int64_t n = tx->ray_begin + i * tx->ray_stride;
@@ -1357,9 +1373,12 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
     for (int64_t c = 0; c < nch; ++c)
         for (size_t j = 0; j < lists[c].cell.size(); ++j) map_out[lists[c].cell[j]] += lists[c].val[j];
     if (mass_out) {
-        std::memset(mass_out, 0, sizeof(double) * (size_t)P->nx * P->ny);
-        for (int64_t c = 0; c < nch; ++c)
+        const size_t nc = (size_t)P->nx * P->ny;
+        std::memset(mass_out, 0, sizeof(double) * 2 * nc);
+        for (int64_t c = 0; c < nch; ++c) {
             for (size_t j = 0; j < masses[c].cell.size(); ++j) mass_out[masses[c].cell[j]] += masses[c].val[j];
+            for (size_t j = 0; j < cmasses[c].cell.size(); ++j) mass_out[nc + cmasses[c].cell[j]] += cmasses[c].val[j];
+        }
     }
     if (stats) {
         std::memset(stats, 0, sizeof(double) * 3 * (L + 1));

@@ -15,13 +15,15 @@ LIB_PATH = os.path.join(HERE, "librmsbr.so")
 RM_OK, RM_EINVAL, RM_ENOMEM, RM_ECUDA, RM_EOVERFLOW, RM_ETIMEOUT, RM_ESTATE = range(7)
 STATUS_NAMES = ["RM_OK", "RM_EINVAL", "RM_ENOMEM", "RM_ECUDA", "RM_EOVERFLOW", "RM_ETIMEOUT", "RM_ESTATE"]
 RM_MAX_DEPTH, RM_MAX_MATERIALS, RM_MAX_TX = 15, 32, 64
-RM_REFLECT, RM_REFRACT, RM_LOS, RM_STATS = 1, 2, 4, 8
+RM_REFLECT, RM_REFRACT, RM_LOS, RM_STATS, RM_DIFFUSE = 1, 2, 4, 8, 16
 NO_CELL = -32768
 UINT64_MAX = (1 << 64) - 1
 
 
 class rm_material(C.Structure):
-    _fields_ = [("eps_r", C.c_float), ("sigma", C.c_float), ("thickness", C.c_float)]
+    _fields_ = [("eps_r", C.c_float), ("sigma", C.c_float), ("thickness", C.c_float),
+                ("scattering", C.c_float), ("xpd_k", C.c_float), ("pattern", C.c_int32),
+                ("alpha_r", C.c_int32), ("alpha_i", C.c_int32), ("lobe_lambda", C.c_float)]
 
 
 class rm_tx(C.Structure):

@@ -34,12 +34,21 @@ def _ptr(t: torch.Tensor | None):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
-def materials(mats) -> C.Array:
-    """Array of rm_material from an [nm, 3] (eps_r, sigma, thickness) table."""
+def materials(mats, scat=None) -> C.Array:
+    """Array of rm_material from an [nm, 3] (eps_r, sigma, thickness) table and
+    optional diffuse parameters [nm, 6] = (S, K_x, pattern, alpha_R, alpha_I, Lambda)."""
     m = np.asarray(mats, np.float64).reshape(-1, 3)
+    sc = None if scat is None else np.asarray(scat, np.float64).reshape(-1, 6)
+    if sc is not None and len(sc) != len(m):
+        raise ValueError("scat must have one row per material")
     arr = (L.rm_material * len(m))()
     for i, (e, s, d) in enumerate(m):
-        arr[i] = L.rm_material(float(e), float(s), float(d))
+        x = L.rm_material(float(e), float(s), float(d))
+        if sc is not None:
+            x.scattering, x.xpd_k = float(sc[i, 0]), float(sc[i, 1])
+            x.pattern, x.alpha_r, x.alpha_i = int(sc[i, 2]), int(sc[i, 3]), int(sc[i, 4])
+            x.lobe_lambda = float(sc[i, 5])
+        arr[i] = x
     return arr
 
 
@@ -74,12 +83,12 @@ def tx_from(obj) -> L.rm_tx:
 def params_struct(freq_hz, max_depth, map_origin=(0.0, 0.0, 1.5), cell_size=1.0, nx=100, ny=100,
                   reflect=True, refract=True, los=True, stats=False, deposit=0, block_size=0,
                   blocks_per_sm=0, queue_chunk=0, rr_depth=0, rr_max_prob=0.0,
-                  gain_threshold=0.0) -> L.rm_trace_params:
+                  gain_threshold=0.0, diffuse=False) -> L.rm_trace_params:
     p = L.rm_trace_params()
     p.freq_hz = float(freq_hz)
     p.max_depth = int(max_depth)
     p.flags = ((L.RM_REFLECT if reflect else 0) | (L.RM_REFRACT if refract else 0) |
-               (L.RM_LOS if los else 0) | (L.RM_STATS if stats else 0))
+               (L.RM_LOS if los else 0) | (L.RM_STATS if stats else 0) | (L.RM_DIFFUSE if diffuse else 0))
     for i in range(3):
         p.map_origin[i] = float(map_origin[i])
     p.cell_size = float(cell_size)
@@ -93,7 +102,7 @@ def params_from(obj, stats=False, block_size=0, blocks_per_sm=0, queue_chunk=0) 
     return params_struct(obj.freq_hz, obj.max_depth, obj.map_origin, obj.cell_size, obj.nx, obj.ny, obj.reflect,
                          obj.refract, obj.los, stats, obj.deposit, block_size, blocks_per_sm, queue_chunk,
                          getattr(obj, "rr_depth", 0), getattr(obj, "rr_max_prob", 0.0),
-                         getattr(obj, "gain_threshold", 0.0))
+                         getattr(obj, "gain_threshold", 0.0), getattr(obj, "diffuse", False))
 
 
 def _tx_array(txs):
@@ -113,7 +122,7 @@ def tx_count(t: L.rm_tx) -> int:
 class Scene:
     """A triangle mesh with per-triangle materials, uploaded and with its LBVH built."""
 
-    def __init__(self, verts, tris, tri_mat, mats, device="cuda", stream=None, build=True):
+    def __init__(self, verts, tris, tri_mat, mats, device="cuda", stream=None, build=True, scat=None):
         lib = L.load()
         dev = torch.device(device)
 
@@ -127,7 +136,8 @@ class Scene:
         m = dev_tensor(tri_mat, np.int32, torch.int32)
         self.nm = int(np.asarray(mats).reshape(-1, 3).shape[0])
         self.nt = int(t.shape[0])
-        self._mats = materials(mats)
+        self._scat = None if scat is None else np.asarray(scat, np.float64).reshape(-1, 6)
+        self._mats = materials(mats, self._scat)
         h = C.c_void_p()
         _check(lib.rm_scene_upload(_ptr(v), v.shape[0], _ptr(t), self.nt, _ptr(m), self._mats, self.nm,
                                    _stream(stream), C.byref(h)), "rm_scene_upload")
@@ -137,13 +147,16 @@ class Scene:
 
     @classmethod
     def from_obj(cls, sc, **kw):
-        return cls(sc.verts, sc.tris, sc.tri_mat, sc.mats, **kw)
+        return cls(sc.verts, sc.tris, sc.tri_mat, sc.mats, scat=getattr(sc, "scat", None), **kw)
 
     def build_bvh(self, stream=None):
         _check(L.load().rm_bvh_build(self.handle, _stream(stream)), "rm_bvh_build")
 
-    def set_materials(self, mats, sampling=None):
-        self._mats = materials(mats)
+    def set_materials(self, mats, sampling=None, scat=None):
+        """Replace the materials; the diffuse parameters stay unless `scat` is given."""
+        if scat is not None:
+            self._scat = np.asarray(scat, np.float64).reshape(-1, 6)
+        self._mats = materials(mats, self._scat)
         sm = None if sampling is None else materials(sampling)
         self._smats = sm
         _check(L.load().rm_scene_set_materials(self.handle, self._mats, self.nm, sm), "rm_scene_set_materials")

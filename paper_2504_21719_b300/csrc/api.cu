@@ -71,10 +71,23 @@ rm_status check_device(const rm_scene* sc) {
 rm_status check_materials(const rm_material* m, int32_t nm) {
     if (nm < 1 || nm > RM_MAX_MATERIALS) return fail(RM_EINVAL, "nm must be in [1, 32]");
     if (!m) return fail(RM_EINVAL, "materials pointer is NULL");
-    for (int i = 0; i < nm; ++i)
+    for (int i = 0; i < nm; ++i) {
         if (!std::isfinite(m[i].eps_r) || !std::isfinite(m[i].sigma) || !std::isfinite(m[i].thickness) ||
             m[i].eps_r <= 0.0f || m[i].sigma < 0.0f)
             return fail(RM_EINVAL, "material " + std::to_string(i) + " has eps_r <= 0, sigma < 0 or a non-finite value");
+        if (!(m[i].scattering >= 0.0f && m[i].scattering <= 1.0f))
+            return fail(RM_EINVAL, "material " + std::to_string(i) + ": scattering must be in [0, 1]");
+        if (m[i].scattering > 0.0f) {
+            const rm_material& x = m[i];
+            const bool ok = x.xpd_k >= 0.0f && x.xpd_k <= 1.0f && x.pattern >= 0 && x.pattern <= 2 &&
+                            (x.pattern == 0 || (x.alpha_r >= 1 && x.alpha_r <= 32)) &&
+                            (x.pattern != 2 || (x.alpha_i >= 1 && x.alpha_i <= 32 && x.lobe_lambda >= 0.0f &&
+                                                x.lobe_lambda <= 1.0f));
+            if (!ok)
+                return fail(RM_EINVAL, "material " + std::to_string(i) +
+                                           ": xpd_k, lobe_lambda in [0, 1], pattern in {0, 1, 2}, alpha in [1, 32] required");
+        }
+    }
     return RM_OK;
 }
 
@@ -146,6 +159,7 @@ struct Prepared {
     std::vector<AntDev> ant;
     int npol = 1;
     bool bilinear = false;
+    bool diffuse = false;        // a diffuse-capable kernel is needed
     int block = DEFAULT_BLOCK;
     int bps = 0;
     double kernel_ms = 0.0;
@@ -213,7 +227,18 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
         d.k0d_hi = (float)k0d;
         d.k0d_lo = (float)(k0d - (double)d.k0d_hi);
         d.slab = e.thickness > 0.0f ? 1 : 0;
-        d.pad = 0;
+        const bool dif = (p->flags & RM_DIFFUSE) && (p->flags & RM_REFLECT) && e.scattering > 0.0f;
+        const double Sd = dif ? (double)e.scattering : 0.0;
+        d.S = (float)Sd;
+        d.R2 = (float)((1.0 - Sd) * (1.0 + Sd));
+        d.Rred = (float)std::sqrt((1.0 - Sd) * (1.0 + Sd));
+        d.sqk = dif ? (float)std::sqrt((double)e.xpd_k) : 0.0f;
+        d.sq1k = dif ? (float)std::sqrt(1.0 - (double)e.xpd_k) : 1.0f;
+        d.pattern = dif ? e.pattern : 0;
+        d.alpha_r = dif && e.pattern > 0 ? e.alpha_r : 1;
+        d.alpha_i = dif && e.pattern == 2 ? e.alpha_i : 1;
+        d.lam = dif && e.pattern == 2 ? e.lobe_lambda : 1.0f;
+        if (dif) P->diffuse = true;
         if (s.eps_r != e.eps_r || s.sigma != e.sigma) same = false;
     }
     P->tx.resize(ntx);
@@ -381,7 +406,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         P.a.record = record;
         if (P.a.total > 0) {
             if ((e = cudaEventRecord(ev[0], S(stream))) != cudaSuccess) break;
-            if ((e = launch_trace(P.a, P.npol, debug, P.bilinear, adjoint, P.block, P.bps, S(stream), &grid)) !=
+            if ((e = launch_trace(P.a, P.npol, debug, P.bilinear, adjoint, P.diffuse, P.block, P.bps, S(stream), &grid)) !=
                 cudaSuccess)
                 break;
             if ((e = cudaEventRecord(ev[1], S(stream))) != cudaSuccess) break;
@@ -588,7 +613,7 @@ rm_status rm_trace_plan_create(const rm_scene* sc, const rm_tx* tx, int32_t ntx,
         if (ek == cudaSuccess) ek = cudaMemsetAsync(P.a.maps64, 0, sizeof(double) * P.a.ncell * ntx, cap);
         int grid = 0;
         if (ek == cudaSuccess && P.a.total > 0)
-            ek = launch_trace(P.a, P.npol, false, P.bilinear, false, P.block, P.bps, cap, &grid);
+            ek = launch_trace(P.a, P.npol, false, P.bilinear, false, P.diffuse, P.block, P.bps, cap, &grid);
         if (ek == cudaSuccess) ek = launch_map_to_f32(P.a.maps64, maps_dev, P.a.ncell * ntx, cap);
         ec = cudaStreamEndCapture(cap, &pl->graph);
         if (ek != cudaSuccess) ec = ek;
@@ -720,7 +745,7 @@ extern "C" rm_status rm_radio_map_trace_noalloc(const rm_scene* sc, const rm_tx*
         P.a.scratch = reinterpret_cast<Scratch*>(dev);
         P.a.maps = maps_dev;
         if (P.a.total > 0 &&
-            (e = launch_trace(P.a, P.npol, debug, P.bilinear, false, P.block, P.bps, S(stream), &grid)) != cudaSuccess)
+            (e = launch_trace(P.a, P.npol, debug, P.bilinear, false, P.diffuse, P.block, P.bps, S(stream), &grid)) != cudaSuccess)
             break;
         if ((e = cudaMemcpyAsync(&host, dev, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
     } while (false);

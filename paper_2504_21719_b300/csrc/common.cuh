@@ -17,12 +17,21 @@ constexpr int32_t NO_CELL = -32768;
 // (eps0 omega) for the fields and for the (detached) sampling probabilities;
 // k0d = 2 pi d / lambda0 split into two floats (hi + lo) so the slab phase
 // keeps FP64 accuracy in its constant.
+//
+// Diffuse reflection (App. A.10): S, R^2 = (1 - S)(1 + S) and R = sqrt(1 - S^2)
+// (Eq. R), sqrt(K_x), sqrt(1 - K_x), the pattern (0 Lambertian, 1 directive,
+// 2 backscattering), its lobe exponents and split Lambda.  S = 0, R = R^2 = 1
+// when the material (or the call) has no diffuse reflection.
 struct MatDev {
     float eta_re, eta_im;
     float seta_re, seta_im;
     float k0d_hi, k0d_lo;
     int32_t slab;
-    int32_t pad;
+    int32_t pattern;
+    float S, R2, Rred;
+    float sqk, sq1k;
+    int32_t alpha_r, alpha_i;
+    float lam;
 };
 
 // Per-transmitter constants.
@@ -89,9 +98,9 @@ struct TraceArgs {
 };
 
 // Host-side launchers (trace.cu)
-cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint,
+cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, bool diffuse,
                          int block, int blocks_per_sm, cudaStream_t s, int* grid_out);
-int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, int block);
+int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block);
 
 // BVH build (bvh.cu)
 struct BvhBuffers {

@@ -13,9 +13,11 @@
 //   2. deposit at the plane crossing (Eq. radio-map-solver-ci-all-2-estimator),
 //      warp-aggregated by destination cell before the FP32 atomic;
 //   3. if l < L and the ray hit: Fresnel / slab coefficients (App. A.7),
-//      sampling of reflection vs refraction with q(R), q(T)
-//      (Eq. path-solver-used-dist-event with S = 0, q(D) = 0), field update
-//      with the TE/TM basis, new direction and origin.
+//      sampling of specular reflection, diffuse reflection or refraction with
+//      q(R), q(S), q(T) (Eq. path-solver-used-dist-event, q(D) = 0), field
+//      update with the TE/TM basis (specular) or Eq. scattered_field
+//      (diffuse, App. A.10), new direction and origin.  The diffuse code is
+//      compiled only into the DIFF instantiations.
 // The adjoint instantiation re-traces the identical rays and, instead of
 // writing the map, accumulates d(sum_i g_i C_i)/d(theta) by forward-mode
 // tangents of the field with respect to each material met on the path.
@@ -182,6 +184,137 @@ __device__ __forceinline__ void fresnel_deta(cf eta, float cos1, float k0d, bool
     *dpar = out[1];
 }
 
+// ------------------------------------------------------------------ diffuse reflection
+// App. A.10.  Four more RNG streams give the variates of a diffuse event:
+// u1, u2 the direction, u3, u4 the random phases chi_1, chi_2 = 2 pi u.
+constexpr unsigned long long DIFF_STREAM0 = 0x2545F4914F6CDD1DULL, DIFF_STREAM1 = 0x9E6C63D0676A9A99ULL,
+                             DIFF_STREAM2 = 0x7F4A7C159E3779B9ULL, DIFF_STREAM3 = 0xC2B2AE3D27D4EB4FULL;
+
+// theta_hat(k), phi_hat(k) (Eq. spherical_vecs) from the Cartesian
+// components: with rho = |(k_x, k_y)|, cos phi = k_x / rho, sin phi = k_y / rho,
+// theta_hat = (k_z cos phi, k_z sin phi, -rho), phi_hat = (-sin phi, cos phi, 0);
+// at the poles phi = 0.
+__device__ __forceinline__ void sph_basis(f3 k, f3& th, f3& ph) {
+    const float rho = sqrtf(k.x * k.x + k.y * k.y);
+    float c = 1.0f, s = 0.0f;
+    if (rho > 0.0f) {
+        c = k.x / rho;
+        s = k.y / rho;
+    }
+    th = {k.z * c, k.z * s, -rho};
+    ph = {-s, c, 0.0f};
+}
+
+// Uniform direction on the hemisphere around the unit normal n: cos theta_s =
+// 1 - u1, phi_s = 2 pi u2 in the tangent frame of m = n (or -n when
+// n_z < -1/2): t1 = (1 - m_x^2 a, -m_x m_y a, -m_x), t2 = (-m_x m_y a,
+// 1 - m_y^2 a, -m_y), a = 1 / (1 + m_z)  (Frisvad, JGT 2012).
+__device__ __forceinline__ f3 diffuse_dir(f3 n, float u1, float u2) {
+    const f3 m = n.z >= -0.5f ? n : n * -1.0f;
+    const float a = 1.0f / (1.0f + m.z), b = -m.x * m.y * a;
+    const f3 t1{1.0f - m.x * m.x * a, b, -m.x}, t2{b, 1.0f - m.y * m.y * a, -m.y};
+    const float cs = 1.0f - u1, sn = sqrtf(u1 * (2.0f - u1));
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    const float a1 = sn * cp, a2 = sn * sp;
+    return {t1.x * a1 + t2.x * a2 + n.x * cs, t1.y * a1 + t2.y * a2 + n.y * cs, t1.z * a1 + t2.z * a2 + n.z * cs};
+}
+
+// F_alpha(theta_i) = 2^-alpha sum_k C(alpha, k) I_k (Eq. directive_model) in one
+// pass: C(alpha, k) and the partial sums of C(2w, w) (sin^2 theta_i / 4)^w
+// that the odd I_k share are both updated by their term ratios.
+__device__ __noinline__ float f_alpha(int alpha, float cos_i) {
+    const float x = 0.25f * (1.0f - cos_i) * (1.0f + cos_i);
+    float binom = 1.0f, inner = 0.0f, term = 1.0f, F = 0.0f;
+    for (int k = 0; k <= alpha; ++k) {
+        float ik = 1.0f;
+        if (k & 1) {
+            const float w = (float)(k >> 1);
+            inner += term;
+            term *= x * (2.0f * w + 1.0f) * (2.0f * w + 2.0f) / ((w + 1.0f) * (w + 1.0f));
+            ik = cos_i * inner;
+        }
+        F += binom * ik / (float)(k + 1);
+        binom = binom * (float)(alpha - k) / (float)(k + 1);
+    }
+    return F * 6.283185307179586f * exp2f(-(float)alpha);
+}
+__device__ __forceinline__ float powi(float x, int a) {
+    float r = 1.0f;
+    for (int i = 0; i < a; ++i) r *= x;
+    return r;
+}
+// Scattering pattern f_s(k_i, k_s, n) (Eqs. lambertian_model,
+// directive_model, backscattering_model); n on the incident side,
+// cos_i = -k_i.n, cos_s = k_s.n.
+__device__ float scat_pattern(const MatDev& M, f3 k, f3 ks, f3 n, float cos_i, float cos_s) {
+    if (M.pattern == 0) return cos_s * 0.31830988618379067f;
+    const float kn = 2.0f * dot(k, n);
+    const f3 kr{k.x - kn * n.x, k.y - kn * n.y, k.z - kn * n.z};
+    const float lr = powi(0.5f * (1.0f + dot(kr, ks)), M.alpha_r);
+    const float fr = f_alpha(M.alpha_r, cos_i);
+    if (M.pattern == 1) return lr / fr;
+    const float li = powi(0.5f * (1.0f - dot(k, ks)), M.alpha_i);
+    return (M.lam * lr + (1.0f - M.lam) * li) / (M.lam * fr + (1.0f - M.lam) * f_alpha(M.alpha_i, cos_i));
+}
+
+// Constants of one diffuse event: TE/TM basis of the incidence, spherical
+// bases of k_i and k_s, the unreduced reflection coefficients, the random
+// phases and c0 = S sqrt(2 pi f_s) (the estimator's weight 2 pi r^2 / |n.k_i|
+// per diffuse point cancels the tube length and cos theta_i of Eq.
+// scattered_field).
+struct Diffuse {
+    f3 ep, epi, thi, phi, ths, phs;
+    cf rp, rl, ph1, ph2;
+    float c0, sqk, sq1k;
+};
+// Scattered field of one polarisation column (Eq. scattered_field):
+// E_s = c0 Gamma [(sqrt(1-K) E_th - sqrt(K) E_ph) e^{j chi_1} theta_hat(k_s)
+//               + (sqrt(K) E_th + sqrt(1-K) E_ph) e^{j chi_2} phi_hat(k_s)],
+// Gamma^2 = (|r_perp E_perp|^2 + |r_par E_par|^2) / |E|^2.
+__device__ __forceinline__ void diffuse_field(const Diffuse& D, const cf* E, cf* Eo) {
+    const cf a = edot(D.ep, E), b = edot(D.epi, E);
+    const float g2 = cabs2(D.rp * a) + cabs2(D.rl * b);
+    const float e2 = cabs2(E[0]) + cabs2(E[1]) + cabs2(E[2]);
+    const float c = (e2 > 0.0f && g2 > 0.0f) ? D.c0 * sqrtf(g2 / e2) : 0.0f;
+    const cf et = edot(D.thi, E), ef = edot(D.phi, E);
+    const cf as = (et * D.sq1k - ef * D.sqk) * D.ph1 * c;
+    const cf bs = (et * D.sqk + ef * D.sq1k) * D.ph2 * c;
+    Eo[0] = as * D.ths.x + bs * D.phs.x;
+    Eo[1] = as * D.ths.y + bs * D.phs.y;
+    Eo[2] = as * D.ths.z + bs * D.phs.z;
+}
+// Its derivative along one real parameter direction: T = dE of the incident
+// field, deta = d eta (0 unless the parameter belongs to this material),
+// drp, drl = d r / d eta.  Gamma depends on |.| of complex numbers, so the
+// map is not holomorphic in eta: permittivity and conductivity directions
+// are carried separately through a diffuse event.
+__device__ __forceinline__ void diffuse_tangent(const Diffuse& D, const cf* E, const cf* T, cf deta, cf drp,
+                                                cf drl, cf* To) {
+    const cf a = edot(D.ep, E), b = edot(D.epi, E);
+    const cf A = D.rp * a, B = D.rl * b;
+    const float g2 = cabs2(A) + cabs2(B);
+    const float e2 = cabs2(E[0]) + cabs2(E[1]) + cabs2(E[2]);
+    if (!(e2 > 0.0f && g2 > 0.0f && D.c0 > 0.0f)) {
+        for (int j = 0; j < 3; ++j) To[j] = C(0.0f);
+        return;
+    }
+    const float c = D.c0 * sqrtf(g2 / e2);
+    const cf da = edot(D.ep, T), db = edot(D.epi, T);
+    const cf dA = drp * deta * a + D.rp * da;
+    const cf dB = drl * deta * b + D.rl * db;
+    const float dg2 = 2.0f * (cjmul(A, dA).r + cjmul(B, dB).r);
+    const float de2 = 2.0f * (cjmul(E[0], T[0]).r + cjmul(E[1], T[1]).r + cjmul(E[2], T[2]).r);
+    const float dc = c * (0.5f * dg2 / g2 - 0.5f * de2 / e2);
+    const cf et = edot(D.thi, E), ef = edot(D.phi, E), det = edot(D.thi, T), def = edot(D.phi, T);
+    const cf as = (et * D.sq1k - ef * D.sqk) * D.ph1, bs = (et * D.sqk + ef * D.sq1k) * D.ph2;
+    const cf das = (det * D.sq1k - def * D.sqk) * D.ph1, dbs = (det * D.sqk + def * D.sq1k) * D.ph2;
+    const cf ao = as * dc + das * c, bo = bs * dc + dbs * c;
+    To[0] = ao * D.ths.x + bo * D.phs.x;
+    To[1] = ao * D.ths.y + bo * D.phs.y;
+    To[2] = ao * D.ths.z + bo * D.phs.z;
+}
+
 // ------------------------------------------------------------------ traversal
 struct Ray {
     float ox, oy, oz, kx, ky, kz;
@@ -333,7 +466,7 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
 constexpr int NGRAD = 2 * RM_MAX_MATERIALS + 3 * RM_MAX_TX;
 constexpr int MAXSLOT = RM_MAX_DEPTH;
 
-template <bool ADJ, int NPOL, bool DEBUG, bool BILIN>
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF>
 __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
     __shared__ MatDev s_mat[RM_MAX_MATERIALS];
     __shared__ TxDev s_tx[RM_MAX_TX];
@@ -372,6 +505,7 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
     unsigned long long n = 0, isub = 0;
     // adjoint state: tangents dE/d eta per material met on the path
     cf Tg[ADJ ? MAXSLOT : 1][NPOL][3];
+    cf Ts[(ADJ && DIFF) ? MAXSLOT : 1][NPOL][3];  // dE / d(sigma / (eps0 omega)) once diffuse events occur
     int Tm[ADJ ? MAXSLOT : 1];
     int nslot = 0;
     float J[(ADJ && BILIN) ? 9 : 1];  // d origin / d tx position, column-major
@@ -612,8 +746,16 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                     for (int p = 0; p < NPOL; ++p)
                         for (int a = 0; a < 3; ++a) z = z + cjmul(E[p][a], Tg[s][p][a]);
                     // d|E|^2/d eps_r = 2 Re(E^H T); d|E|^2/d sigma = 2 Re(E^H T (-j/(eps0 w))) = 2 Im(E^H T)/(eps0 w)
+                    // (with diffuse events the sigma direction has its own tangent Ts = dE/d(sigma/(eps0 w)))
+                    float zs = z.i;
+                    if (DIFF) {
+                        cf w = C(0.0f);
+                        for (int p = 0; p < NPOL; ++p)
+                            for (int a = 0; a < 3; ++a) w = w + cjmul(E[p][a], Ts[s][p][a]);
+                        zs = w.r;
+                    }
                     atomicAdd(&s_grad[Tm[s]], 2.0f * sc * G * z.r);
-                    atomicAdd(&s_grad[RM_MAX_MATERIALS + Tm[s]], 2.0f * sc * G * z.i * A.inv_eps0_omega);
+                    atomicAdd(&s_grad[RM_MAX_MATERIALS + Tm[s]], 2.0f * sc * G * zs * A.inv_eps0_omega);
                 }
             }
             if (BILIN && (Gx != 0.0f || Gy != 0.0f)) {
@@ -659,11 +801,17 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                 if (!(wsum > 0.0f)) {
                     active = false;
                 } else {
-                    const float qR = wR / wsum;
+                    // coin (Eq. path-solver-used-dist-event, q(D) = 0): u < q(R) = R^2 wR / wsum
+                    // -> R; u < wR / wsum -> S (diffuse, share S^2); else T
+                    const float c2 = wR / wsum;
+                    const float c1 = DIFF ? M.R2 * c2 : c2;
                     const float u = rng_u(s_tx[txi].seed, n, depth);
-                    const int dec = (u < qR) ? 0 : 1;
+                    const int dec = (u < c1) ? 0 : ((DIFF && u < c2) ? 2 : 1);
                     if (rec) rec->decision = dec;
-                    inv_pr = inv_pr * (wsum / (dec == 0 ? wR : wT));
+                    if (DIFF)
+                        inv_pr = inv_pr * (wsum / (dec == 0 ? M.R2 * wR : (dec == 2 ? M.S * M.S * wR : wT)));
+                    else
+                        inv_pr = inv_pr * (wsum / (dec == 0 ? wR : wT));
                     // TE/TM basis (Eqs. fresnel_in_vectors, fresnel_out_vectors)
                     f3 ep = cross(k, nrm);
                     const float len = sqrtf(dot(ep, ep));
@@ -676,49 +824,107 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                     const f3 epi = cross(ep, k);
                     f3 ko, epo;
                     cf cpe, cpa;
-                    if (dec == 0) {
+                    Diffuse D;
+                    if (DIFF && dec == 2) {
+                        // diffuse reflection: a new tube in a uniform direction of the
+                        // incident-side hemisphere (App. A.10)
+                        const unsigned long long sd = s_tx[txi].seed;
+                        ko = diffuse_dir(nrm, rng_u(sd ^ DIFF_STREAM0, n, depth), rng_u(sd ^ DIFF_STREAM1, n, depth));
+                        const float fs = scat_pattern(M, k, ko, nrm, cos1, dot(ko, nrm));
+                        D.ep = ep;
+                        D.epi = epi;
+                        sph_basis(k, D.thi, D.phi);
+                        sph_basis(ko, D.ths, D.phs);
+                        D.rp = co.rp;
+                        D.rl = co.rl;
+                        float s1, k1, s2, k2;
+                        sincospif(2.0f * rng_u(sd ^ DIFF_STREAM2, n, depth), &s1, &k1);
+                        sincospif(2.0f * rng_u(sd ^ DIFF_STREAM3, n, depth), &s2, &k2);
+                        D.ph1 = C(k1, s1);
+                        D.ph2 = C(k2, s2);
+                        D.c0 = fs > 0.0f ? M.S * sqrtf(6.283185307179586f * fs) : 0.0f;
+                        D.sqk = M.sqk;
+                        D.sq1k = M.sq1k;
+                        epo = epi;
+                        cpe = cpa = C(0.0f);
+                    } else if (dec == 0) {
                         ko = normalize(k - nrm * (2.0f * dot(k, nrm)));
                         epo = normalize(cross(ep, ko));
-                        cpe = co.rp; cpa = co.rl;
+                        cpe = DIFF ? co.rp * M.Rred : co.rp;
+                        cpa = DIFF ? co.rl * M.Rred : co.rl;
                     } else {
                         ko = k;  // thin slab: no deflection (Sec. 2.3)
                         epo = epi;
                         cpe = co.tp; cpa = co.tl;
                     }
                     if (ADJ) {
-                        // existing tangents see the same interaction matrix
-                        for (int s = 0; s < nslot; ++s)
-                            for (int p = 0; p < NPOL; ++p) {
-                                const cf a = edot(ep, Tg[s][p]), b = edot(epi, Tg[s][p]);
-                                const cf ca = cpe * a, cb = cpa * b;
-                                Tg[s][p][0] = ca * ep.x + cb * epo.x;
-                                Tg[s][p][1] = ca * ep.y + cb * epo.y;
-                                Tg[s][p][2] = ca * ep.z + cb * epo.z;
-                            }
-                        // new tangent of this interaction, merged per material
-                        cf dpe, dpa;
-                        fresnel_deta(eta, cos1, M.k0d_hi + M.k0d_lo, M.slab != 0, dec, &dpe, &dpa);
-                        int s = 0;
-                        while (s < nslot && Tm[s] != mat) ++s;
-                        if (s == nslot) {
+                        // slot of this interaction's material (new slots start at zero)
+                        int sm = 0;
+                        while (sm < nslot && Tm[sm] != mat) ++sm;
+                        if (sm == nslot) {
                             if (nslot < MAXSLOT) {
-                                Tm[s] = mat;
+                                Tm[sm] = mat;
                                 for (int p = 0; p < NPOL; ++p)
-                                    for (int a = 0; a < 3; ++a) Tg[s][p][a] = C(0.0f);
+                                    for (int a = 0; a < 3; ++a) {
+                                        Tg[sm][p][a] = C(0.0f);
+                                        if (DIFF) Ts[sm][p][a] = C(0.0f);
+                                    }
                                 ++nslot;
                             } else {
-                                s = -1;
+                                sm = -1;
                                 overflow = true;
                             }
                         }
-                        if (s >= 0)
-                            for (int p = 0; p < NPOL; ++p) {
-                                const cf a = edot(ep, E[p]), b = edot(epi, E[p]);
-                                const cf ca = dpe * a, cb = dpa * b;
-                                Tg[s][p][0] = Tg[s][p][0] + (ca * ep.x + cb * epo.x);
-                                Tg[s][p][1] = Tg[s][p][1] + (ca * ep.y + cb * epo.y);
-                                Tg[s][p][2] = Tg[s][p][2] + (ca * ep.z + cb * epo.z);
+                        if (DIFF && dec == 2) {
+                            // tangents through the (non-holomorphic) diffuse map, eps and
+                            // sigma directions separately; d eta = 1 resp. -j on this material
+                            cf drp, drl;
+                            fresnel_deta(eta, cos1, M.k0d_hi + M.k0d_lo, M.slab != 0, 0, &drp, &drl);
+                            for (int s = 0; s < nslot; ++s) {
+                                const bool own = s == sm;
+                                for (int p = 0; p < NPOL; ++p) {
+                                    cf t[3];
+                                    diffuse_tangent(D, E[p], Tg[s][p], own ? C(1.0f) : C(0.0f), drp, drl, t);
+                                    for (int a = 0; a < 3; ++a) Tg[s][p][a] = t[a];
+                                    diffuse_tangent(D, E[p], Ts[s][p], own ? C(0.0f, -1.0f) : C(0.0f), drp, drl, t);
+                                    for (int a = 0; a < 3; ++a) Ts[s][p][a] = t[a];
+                                }
                             }
+                        } else {
+                            // existing tangents see the same interaction matrix
+                            for (int s = 0; s < nslot; ++s)
+                                for (int p = 0; p < NPOL; ++p) {
+                                    const cf a = edot(ep, Tg[s][p]), b = edot(epi, Tg[s][p]);
+                                    const cf ca = cpe * a, cb = cpa * b;
+                                    Tg[s][p][0] = ca * ep.x + cb * epo.x;
+                                    Tg[s][p][1] = ca * ep.y + cb * epo.y;
+                                    Tg[s][p][2] = ca * ep.z + cb * epo.z;
+                                    if (DIFF) {
+                                        const cf as = edot(ep, Ts[s][p]), bs = edot(epi, Ts[s][p]);
+                                        const cf cas = cpe * as, cbs = cpa * bs;
+                                        Ts[s][p][0] = cas * ep.x + cbs * epo.x;
+                                        Ts[s][p][1] = cas * ep.y + cbs * epo.y;
+                                        Ts[s][p][2] = cas * ep.z + cbs * epo.z;
+                                    }
+                                }
+                            // plus d(interaction matrix)/d eta applied to the field
+                            cf dpe, dpa;
+                            fresnel_deta(eta, cos1, M.k0d_hi + M.k0d_lo, M.slab != 0, dec, &dpe, &dpa);
+                            if (DIFF && dec == 0) {
+                                dpe = dpe * M.Rred;
+                                dpa = dpa * M.Rred;
+                            }
+                            if (sm >= 0)
+                                for (int p = 0; p < NPOL; ++p) {
+                                    const cf a = edot(ep, E[p]), b = edot(epi, E[p]);
+                                    const cf ca = dpe * a, cb = dpa * b;
+                                    const cf v[3] = {ca * ep.x + cb * epo.x, ca * ep.y + cb * epo.y, ca * ep.z + cb * epo.z};
+                                    for (int a2 = 0; a2 < 3; ++a2) {
+                                        Tg[sm][p][a2] = Tg[sm][p][a2] + v[a2];
+                                        if (DIFF) Ts[sm][p][a2] = Ts[sm][p][a2] + v[a2] * C(0.0f, -1.0f);
+                                    }
+                                }
+                        }
                         if (BILIN) {
                             // hit point on the plane of the triangle: dp/do = I - k n^T / (n . k)
                             const float inv_nk = 1.0f / dot(nrm, k);
@@ -730,24 +936,34 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                             }
                         }
                     }
-                    for (int p = 0; p < NPOL; ++p) {
-                        const cf a = edot(ep, E[p]), b = edot(epi, E[p]);
-                        const cf ca = cpe * a, cb = cpa * b;
-                        E[p][0] = ca * ep.x + cb * epo.x;
-                        E[p][1] = ca * ep.y + cb * epo.y;
-                        E[p][2] = ca * ep.z + cb * epo.z;
+                    if (DIFF && dec == 2) {
+                        for (int p = 0; p < NPOL; ++p) {
+                            cf eo[3];
+                            diffuse_field(D, E[p], eo);
+                            for (int a = 0; a < 3; ++a) E[p][a] = eo[a];
+                        }
+                    } else {
+                        for (int p = 0; p < NPOL; ++p) {
+                            const cf a = edot(ep, E[p]), b = edot(epi, E[p]);
+                            const cf ca = cpe * a, cb = cpa * b;
+                            E[p][0] = ca * ep.x + cb * epo.x;
+                            E[p][1] = ca * ep.y + cb * epo.y;
+                            E[p][2] = ca * ep.z + cb * epo.z;
+                        }
                     }
                     // new origin: hit point pushed 2^-16 max(1, |p|_inf) off the surface
+                    // (incident side for R and S, far side for T)
                     const float px = r.ox + h.t * r.kx, py = r.oy + h.t * r.ky, pz = r.oz + h.t * r.kz;
                     const float pm = fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz)));
                     const float delta = fmaxf(1.0f, pm) * 0x1p-16f;
-                    const float sgn = dec == 0 ? delta : -delta;
+                    const float sgn = dec == 1 ? -delta : delta;
                     r.ox = px + sgn * nrm.x;
                     r.oy = py + sgn * nrm.y;
                     r.oz = pz + sgn * nrm.z;
                     r.kx = ko.x; r.ky = ko.y; r.kz = ko.z;
                     prev = h.slot;
                     plen += h.t;
+                    if (DIFF && dec == 2) plen = 0.0f;  // a diffuse reflection starts a new tube
                     ++depth;
                     // early termination once the path has rr_depth interactions (Sec. 4.7):
                     // threshold on (lambda0/4pi)^2 w|E|^2 / r^2, then Russian roulette with
@@ -757,7 +973,8 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                         for (int p = 0; p < NPOL; ++p) w2 += cabs2(E[p][0]) + cabs2(E[p][1]) + cabs2(E[p][2]);
                         w2 *= inv_pr;
                         int kill = 0;
-                        if (A.gain_thr > 0.0f && A.lam4pi2 * w2 / (plen * plen) < A.gain_thr) kill = 8;
+                        // (a tube a diffuse reflection has just spawned, plen = 0, is not thresholded)
+                        if (A.gain_thr > 0.0f && plen > 0.0f && A.lam4pi2 * w2 / (plen * plen) < A.gain_thr) kill = 8;
                         if (!kill && A.rr_pmax > 0.0f) {
                             const float prr = fminf(w2, A.rr_pmax);
                             const float urr = rng_u(s_tx[txi].seed ^ RR_STREAM, n, depth - 1);
@@ -798,14 +1015,19 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
             if (s_grad[i] != 0.0f) atomicAdd(&A.scratch->grad[i], (double)s_grad[i]);
 }
 
-template <bool ADJ, int NPOL, bool DEBUG, bool BILIN>
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF>
 const void* kernel_ptr() {
-    return reinterpret_cast<const void*>(&k_trace<ADJ, NPOL, DEBUG, BILIN>);
+    return reinterpret_cast<const void*>(&k_trace<ADJ, NPOL, DEBUG, BILIN, DIFF>);
 }
 
-const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint) {
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN>
+const void* select_diff(bool diffuse) {
+    return diffuse ? kernel_ptr<ADJ, NPOL, DEBUG, BILIN, true>() : kernel_ptr<ADJ, NPOL, DEBUG, BILIN, false>();
+}
+
+const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse) {
 #define RM_SEL(A, P, D, B) \
-    if (adjoint == A && npol == P && debug == D && bilinear == B) return kernel_ptr<A, P, D, B>();
+    if (adjoint == A && npol == P && debug == D && bilinear == B) return select_diff<A, P, D, B>(diffuse);
     RM_SEL(false, 1, false, false) RM_SEL(false, 1, false, true) RM_SEL(false, 1, true, false)
     RM_SEL(false, 1, true, true) RM_SEL(false, 2, false, false) RM_SEL(false, 2, false, true)
     RM_SEL(false, 2, true, false) RM_SEL(false, 2, true, true) RM_SEL(true, 1, false, false)
@@ -818,16 +1040,16 @@ const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint) {
 
 }  // namespace
 
-int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, int block) {
-    const void* k = select_kernel(npol, debug, bilinear, adjoint);
+int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block) {
+    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse);
     int nb = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0) != cudaSuccess) return 0;
     return nb;
 }
 
-cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, int block,
-                         int blocks_per_sm, cudaStream_t s, int* grid_out) {
-    const void* k = select_kernel(npol, debug, bilinear, adjoint);
+cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, bool diffuse,
+                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out) {
+    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse);
     if (!k) return cudaErrorInvalidValue;
     if (block <= 0 || block > MAX_BLOCK || (block & 31)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, occ = 0;

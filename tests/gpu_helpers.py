@@ -4,12 +4,16 @@ import numpy as np
 MAP_RTOL = 1e-3          # per-cell relative tolerance of the maps
 FLOOR = 1e-15            # cells above -150 dB are compared
 # Bilinear (tent) deposits: a weight is (1 - f) or f with f the FP32 fractional
-# cell coordinate of a crossing point.  FP32 ray origins near |x| ~ 300 m after a
-# few bounces carry ~5 roundings of 2^-24 * 300 m = 1.8e-5 m each, i.e. up to
-# ~1e-4 m, so f is off by up to 5e-5 cells for 2 m cells and a product weight
-# by twice that.  A cell may therefore differ by WEIGHT_ATOL times the
-# unweighted value of the deposits whose stencil covers it (2x margin).
-WEIGHT_ATOL = 2e-4
+# cell coordinate of the crossing x_c = o + t_c k.  FP32 origins carry errors
+# |d o| <= eps (1 m + |o|_inf + path) and directions |d k| <= eps, which move
+# the crossing by at most eps * D with
+#   D = (1 + |o|_inf + path + t_c) (1 + (|k_x| + |k_y|) / |k_z|)
+# (the oracle's conditioning factor: grazing rays that start near the plane,
+# as diffuse reflections spawn them, are the ill-conditioned ones).  A tent
+# weight w = w_x w_y then moves by at most 2 eps D / cell, so a cell may differ
+# by 2 eps / cell times the D-weighted values of the deposits whose stencil
+# covers it.  eps = 4 * 2^-24: a few FP32 roundings per coordinate.
+POS_EPS = 4.0 * 2.0 ** -24
 MAX_ADOPT_FRAC = 1e-2
 
 
@@ -30,7 +34,7 @@ def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max
     err = np.abs(g - ref)[mask]
     bound = rtol * ref[mask]
     if bil:
-        bound = bound + WEIGHT_ATOL * r["mass"][mask]
+        bound = bound + 2.0 * POS_EPS / params.cell_size * r["cmass"][mask]
     rel = err / np.maximum(ref[mask], 1e-300)
     worst = float((err / np.maximum(bound, 1e-300)).max()) if err.size else 0.0
     assert np.all(err <= bound), (worst, float(rel.max()), int(mask.sum()), rep)

@@ -41,7 +41,8 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_struct_layouts_match_header(L, tmp_path):
     fields = {
-        "rm_material": ["eps_r", "sigma", "thickness"],
+        "rm_material": ["eps_r", "sigma", "thickness", "scattering", "xpd_k", "pattern", "alpha_r", "alpha_i",
+                        "lobe_lambda"],
         "rm_tx": ["pos", "yaw", "pol", "pattern", "num_rays", "ray_begin", "ray_count", "ray_stride", "seed",
                   "n_ant", "ant_pos_host", "precoding_host"],
         "rm_trace_params": ["freq_hz", "max_depth", "flags", "map_origin", "cell_size", "nx", "ny", "deposit",
@@ -77,6 +78,15 @@ def test_host_validation_without_gpu(L):
     assert b"nm" in lib.rm_last_error()
     bad = (L.rm_material * 1)(L.rm_material(-1.0, 0.0, 0.0))
     assert lib.rm_scene_upload(None, 0, None, 0, None, bad, 1, None, C.byref(h)) == L.RM_EINVAL
+    # diffuse parameters: S outside [0, 1], an unknown pattern, alpha out of range
+    for kw in (dict(scattering=1.5), dict(scattering=0.5, pattern=3), dict(scattering=0.5, pattern=1, alpha_r=0),
+               dict(scattering=0.5, pattern=2, alpha_r=2, alpha_i=40, lobe_lambda=0.5),
+               dict(scattering=0.5, xpd_k=-0.2)):
+        m = L.rm_material(4.0, 0.01, 0.2)
+        for k, v in kw.items():
+            setattr(m, k, v)
+        assert lib.rm_scene_upload(None, 0, None, 0, None, (L.rm_material * 1)(m), 1, None, C.byref(h)) == L.RM_EINVAL
+        assert b"material 0" in lib.rm_last_error()
     assert lib.rm_radio_map_trace(None, None, 1, None, None, None, None, None) == L.RM_EINVAL
     assert lib.rm_radio_map_grad(None, None, 1, None, None, None, None, None, None, None, None, None) == L.RM_EINVAL
     assert lib.rm_db_mse_loss(None, None, 10, 0.0, None, None, None, None) == L.RM_EINVAL
