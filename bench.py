@@ -15,6 +15,7 @@ no collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import copy
 import hashlib
 import json
 import os
@@ -185,8 +186,8 @@ def run_ours(args, world, rank, local):
     tx = txs[0]
     if args.rays:
         tx.num_rays = args.rays
-    blk, bps, qch = tuned(gpu_name, "manhattan")
-    params = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch)
+    blk, bps, qch, rfm = tuned(gpu_name, "manhattan")
+    params = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
     gs = api.Scene.from_obj(sc)
     maps = torch.empty((1, p.ny, p.nx), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -285,7 +286,8 @@ def run_ours(args, world, rank, local):
                    "triangles": sc.nt, "segments_per_step": int(seg_step),
                    "nodes_per_segment": round(sum(nodes) / sum(segs), 2),
                    "tris_per_segment": round(sum(tris) / sum(segs), 2), "block_size": blk or 128,
-                   "blocks_per_sm": bps or "max occupancy", "queue_chunk": qch or 1, "tuned": bool(blk),
+                   "blocks_per_sm": bps or "max occupancy", "queue_chunk": qch or 1,
+                   "refill_min": rfm or 20, "tuned": bool(blk),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
@@ -297,13 +299,57 @@ def run_ours(args, world, rank, local):
     return line
 
 
+def _kernel_rate(api, gs, txs, prm, reps=5):
+    """Mean tracer kernel time (CUDA events inside the library) and segments/s."""
+    for _ in range(2):
+        api.trace(gs, txs, prm)
+    ms, segs = [], 0
+    for _ in range(reps):
+        r = api.trace(gs, txs, prm)
+        ms.append(r["stats"]["kernel_ms"])
+        segs = r["stats"]["segments"]
+    k = statistics.mean(ms)
+    return {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3), "segments": segs}
+
+
 def run_extra(api, S, torch, gpu_name):
-    """Batched 64-TX form and forward+adjoint of the differentiable workload."""
+    """Batched 64-TX form, forward+adjoint of the differentiable workload, the
+    large city, and the widened model (diffuse reflection, early termination,
+    synthetic arrays) on the Manhattan workload."""
+    import numpy as np
+
     out = {}
-    sc, txs, p = S.workload(3)
-    blk, bps, qch = tuned(gpu_name, "batched")
+    # widened model on the 1e7-ray Manhattan workload (same scene, TX, map)
+    sc, txs, p = S.workload(2)
+    blk, bps, qch, rfm = tuned(gpu_name, "manhattan")
+    kw = dict(block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
+    base = _kernel_rate(api, api.Scene.from_obj(sc), txs, api.params_from(p, **kw))
+    scd = sc.with_scattering(0.5, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
+    pd = copy.copy(p)
+    pd.diffuse = True
+    gsd = api.Scene.from_obj(scd)
+    d = _kernel_rate(api, gsd, txs, api.params_from(pd, **kw))
+    d["vs_specular"] = round(d["value"] / base["value"], 3)
+    d["materials"] = "S = 0.5 on every material; ground Lambertian, buildings directive / backscattering"
+    out["specular_same_call"] = base
+    out["diffuse"] = d
+    gsd.free()
+    pr = copy.copy(p)
+    pr.rr_depth, pr.rr_max_prob = 2, 0.5
     gs = api.Scene.from_obj(sc)
-    prm = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch)
+    e = _kernel_rate(api, gs, txs, api.params_from(pr, **kw))
+    e["setting"] = "Russian roulette after 2 interactions, p_max = 0.5"
+    out["early_termination"] = e
+    ta = copy.copy(txs[0])
+    ta.ant_pos, ta.precoding = S.uniform_linear_array(64, p.freq_hz, 0.5, axis=0)
+    a = _kernel_rate(api, gs, [ta], api.params_from(p, **kw))
+    a["setting"] = "64-element half-wavelength ULA, uniform precoding"
+    out["synthetic_array_64"] = a
+    gs.free()
+    sc, txs, p = S.workload(3)
+    blk, bps, qch, rfm = tuned(gpu_name, "batched")
+    gs = api.Scene.from_obj(sc)
+    prm = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
     maps = torch.empty((len(txs), p.ny, p.nx), dtype=torch.float32, device="cuda")
     plan = api.TracePlan(gs, txs, prm, maps)
     for _ in range(3):
@@ -350,12 +396,28 @@ def run_extra(api, S, torch, gpu_name):
                              "fwd_plus_adj_over_fwd": round((fk + statistics.mean(b_ms)) / fk, 3),
                              "fwd_value": round(segs / (fk / 1e3), 1), "unit": UNIT}
     gs.free()
+    # the same with diffuse reflection on every material (adjoint kernel timed inside the library)
+    scd = sc.with_scattering(np.linspace(0.2, 0.8, sc.nm), 0.3, np.arange(sc.nm) % 3, 2, 3, 0.5)
+    pd = copy.copy(p)
+    pd.diffuse = True
+    gs = api.Scene.from_obj(scd)
+    fk, ak = [], []
+    for i in range(6):
+        f = api.trace(gs, txs, pd)
+        a = api.grad(gs, txs, pd, torch.ones_like(f["maps"]))
+        if i >= 2:
+            fk.append(f["stats"]["kernel_ms"])
+            ak.append(a["stats"]["kernel_ms"])
+    out["differentiable_diffuse"] = {"fwd_kernel_ms": round(statistics.mean(fk), 3),
+                                     "adj_kernel_ms": round(statistics.mean(ak), 3),
+                                     "fwd_plus_adj_over_fwd": round(1 + statistics.mean(ak) / statistics.mean(fk), 3)}
+    gs.free()
 
     # large city: 0.97M triangles, 16 TX x 1e8 rays, depth 8, one launch each way
     sc, txs, p = S.workload(5)
     gs = api.Scene.from_obj(sc)
-    blk, bps, qch = tuned(gpu_name, "city")
-    p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch)
+    blk, bps, qch, rfm = tuned(gpu_name, "city")
+    p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
     small = [S.Tx(pos=txs[0].pos, num_rays=1_000_000, seed=txs[0].seed)]
     api.trace(gs, small, p)
     f = api.trace(gs, txs, p)

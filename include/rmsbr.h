@@ -138,7 +138,9 @@ typedef struct {
     int32_t rr_depth;
     float rr_max_prob;
     float gain_threshold;
-    int32_t reserved2;
+    int32_t refill_min;      /* a warp refills its idle lanes with new rays once at least this many
+                                are idle (1..32): new rays then enter in coherent groups of lattice
+                                neighbours; 0 = default (20) */
 } rm_trace_params;
 
 /* Counters of one trace call, summed over all transmitters. */

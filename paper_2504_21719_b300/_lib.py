@@ -39,7 +39,7 @@ class rm_trace_params(C.Structure):
                 ("map_origin", C.c_float * 3), ("cell_size", C.c_float), ("nx", C.c_int32),
                 ("ny", C.c_int32), ("deposit", C.c_int32), ("block_size", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("queue_chunk", C.c_int32), ("rr_depth", C.c_int32),
-                ("rr_max_prob", C.c_float), ("gain_threshold", C.c_float), ("reserved2", C.c_int32)]
+                ("rr_max_prob", C.c_float), ("gain_threshold", C.c_float), ("refill_min", C.c_int32)]
 
 
 _D = RM_MAX_DEPTH + 1

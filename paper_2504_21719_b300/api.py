@@ -83,7 +83,7 @@ def tx_from(obj) -> L.rm_tx:
 def params_struct(freq_hz, max_depth, map_origin=(0.0, 0.0, 1.5), cell_size=1.0, nx=100, ny=100,
                   reflect=True, refract=True, los=True, stats=False, deposit=0, block_size=0,
                   blocks_per_sm=0, queue_chunk=0, rr_depth=0, rr_max_prob=0.0,
-                  gain_threshold=0.0, diffuse=False) -> L.rm_trace_params:
+                  gain_threshold=0.0, diffuse=False, refill_min=0) -> L.rm_trace_params:
     p = L.rm_trace_params()
     p.freq_hz = float(freq_hz)
     p.max_depth = int(max_depth)
@@ -95,14 +95,15 @@ def params_struct(freq_hz, max_depth, map_origin=(0.0, 0.0, 1.5), cell_size=1.0,
     p.nx, p.ny, p.deposit = int(nx), int(ny), int(deposit)
     p.block_size, p.blocks_per_sm, p.queue_chunk = int(block_size), int(blocks_per_sm), int(queue_chunk)
     p.rr_depth, p.rr_max_prob, p.gain_threshold = int(rr_depth), float(rr_max_prob), float(gain_threshold)
+    p.refill_min = int(refill_min)
     return p
 
 
-def params_from(obj, stats=False, block_size=0, blocks_per_sm=0, queue_chunk=0) -> L.rm_trace_params:
+def params_from(obj, stats=False, block_size=0, blocks_per_sm=0, queue_chunk=0, refill_min=0) -> L.rm_trace_params:
     return params_struct(obj.freq_hz, obj.max_depth, obj.map_origin, obj.cell_size, obj.nx, obj.ny, obj.reflect,
                          obj.refract, obj.los, stats, obj.deposit, block_size, blocks_per_sm, queue_chunk,
                          getattr(obj, "rr_depth", 0), getattr(obj, "rr_max_prob", 0.0),
-                         getattr(obj, "gain_threshold", 0.0), getattr(obj, "diffuse", False))
+                         getattr(obj, "gain_threshold", 0.0), getattr(obj, "diffuse", False), refill_min)
 
 
 def _tx_array(txs):

@@ -41,6 +41,7 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double C0 = 299792458.0;          // m/s
 constexpr double EPS0 = 8.8541878128e-12;   // F/m (CODATA 2018)
 constexpr int DEFAULT_BLOCK = 128;
+constexpr int DEFAULT_REFILL_MIN = 20;  // idle lanes before a warp refills (measured optimum 16..28)
 constexpr int MAX_ANT = 4096;   // synthetic-array elements per call
 
 thread_local std::string g_err;
@@ -112,6 +113,7 @@ rm_status validate(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_tr
         return fail(RM_EINVAL, "block_size must be 0 or a multiple of 32 in [32, 256]");
     if (p->blocks_per_sm < 0) return fail(RM_EINVAL, "blocks_per_sm must be >= 0");
     if (p->queue_chunk < 0 || p->queue_chunk > 64) return fail(RM_EINVAL, "queue_chunk must be in [0, 64]");
+    if (p->refill_min < 0 || p->refill_min > 32) return fail(RM_EINVAL, "refill_min must be in [0, 32]");
     if (p->rr_depth < 0 || !(p->rr_max_prob >= 0.0f && p->rr_max_prob <= 1.0f) || !(p->gain_threshold >= 0.0f))
         return fail(RM_EINVAL, "rr_depth >= 0, rr_max_prob in [0, 1] and gain_threshold >= 0 are required");
     for (int i = 0; i < 3; ++i)
@@ -308,6 +310,7 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
     A.same_sampling = same ? 1 : 0;
     A.total = work;
     A.qchunk = 32ULL * (unsigned long long)(p->queue_chunk > 0 ? p->queue_chunk : 1);
+    A.refill_min = p->refill_min > 0 ? p->refill_min : DEFAULT_REFILL_MIN;
     A.ncell = (unsigned long long)p->nx * p->ny;
     P->npol = tx[0].pol == 2 ? 2 : 1;
     P->bilinear = p->deposit == 1;

@@ -81,6 +81,8 @@ struct TraceArgs {
     int32_t same_sampling;
     unsigned long long total;    // work items (sum of ray counts)
     unsigned long long qchunk;   // work items a warp takes per queue access (multiple of 32)
+    int32_t refill_min;          // idle lanes (1..32) before a warp refills them
+    int32_t pad_refill;
     unsigned long long ncell;    // nx * ny
     const MatDev* mats;          // [nm]
     const TxDev* tx;             // [ntx]

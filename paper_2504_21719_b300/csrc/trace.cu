@@ -315,6 +315,29 @@ __device__ __forceinline__ void diffuse_tangent(const Diffuse& D, const cf* E, c
     To[2] = ao * D.ths.z + bo * D.phs.z;
 }
 
+// Direction, pattern value, bases and random phases of one diffuse event.
+__device__ __noinline__ void diffuse_setup(const MatDev& M, f3 k, f3 nrm, float cos1, cf rp, cf rl, f3 ep, f3 epi,
+                                           unsigned long long seed, unsigned long long n, int depth, Diffuse* D,
+                                           f3* ko_out) {
+    const f3 ko = diffuse_dir(nrm, rng_u(seed ^ DIFF_STREAM0, n, depth), rng_u(seed ^ DIFF_STREAM1, n, depth));
+    const float fs = scat_pattern(M, k, ko, nrm, cos1, dot(ko, nrm));
+    D->ep = ep;
+    D->epi = epi;
+    sph_basis(k, D->thi, D->phi);
+    sph_basis(ko, D->ths, D->phs);
+    D->rp = rp;
+    D->rl = rl;
+    float s1, k1, s2, k2;
+    sincospif(2.0f * rng_u(seed ^ DIFF_STREAM2, n, depth), &s1, &k1);
+    sincospif(2.0f * rng_u(seed ^ DIFF_STREAM3, n, depth), &s2, &k2);
+    D->ph1 = C(k1, s1);
+    D->ph2 = C(k2, s2);
+    D->c0 = fs > 0.0f ? M.S * sqrtf(6.283185307179586f * fs) : 0.0f;
+    D->sqk = M.sqk;
+    D->sq1k = M.sq1k;
+    *ko_out = ko;
+}
+
 // ------------------------------------------------------------------ traversal
 struct Ray {
     float ox, oy, oz, kx, ky, kz;
@@ -466,8 +489,11 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
 constexpr int NGRAD = 2 * RM_MAX_MATERIALS + 3 * RM_MAX_TX;
 constexpr int MAXSLOT = RM_MAX_DEPTH;
 
+// Register budgets: the forward tracer is capped at 64 registers (four
+// 256-thread blocks per SM: the extra resident warps hide more latency than
+// the few spills cost); the adjoint, whose tangents live in local memory, at 128.
 template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF>
-__global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
+__global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArgs A) {
     __shared__ MatDev s_mat[RM_MAX_MATERIALS];
     __shared__ TxDev s_tx[RM_MAX_TX];
     __shared__ float s_agg[MAX_BLOCK];
@@ -514,8 +540,10 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
 
     while (true) {
         // ---------------- refill free lanes (one atomic per warp) ----------------
+        // (refills wait for A.refill_min idle lanes so that new rays, lattice
+        // neighbours, enter a warp in coherent groups; an all-idle warp always refills)
         const unsigned need = __ballot_sync(FULL_MASK, !active);
-        if (need && !(exhausted && qb >= qe)) {
+        if (need && !(exhausted && qb >= qe) && __popc(need) >= A.refill_min) {
             const unsigned long long nneed = (unsigned long long)__popc(need);
             const unsigned long long rem = qe - qb;
             unsigned long long b = 0;
@@ -827,24 +855,9 @@ __global__ void __launch_bounds__(MAX_BLOCK) k_trace(const TraceArgs A) {
                     Diffuse D;
                     if (DIFF && dec == 2) {
                         // diffuse reflection: a new tube in a uniform direction of the
-                        // incident-side hemisphere (App. A.10)
-                        const unsigned long long sd = s_tx[txi].seed;
-                        ko = diffuse_dir(nrm, rng_u(sd ^ DIFF_STREAM0, n, depth), rng_u(sd ^ DIFF_STREAM1, n, depth));
-                        const float fs = scat_pattern(M, k, ko, nrm, cos1, dot(ko, nrm));
-                        D.ep = ep;
-                        D.epi = epi;
-                        sph_basis(k, D.thi, D.phi);
-                        sph_basis(ko, D.ths, D.phs);
-                        D.rp = co.rp;
-                        D.rl = co.rl;
-                        float s1, k1, s2, k2;
-                        sincospif(2.0f * rng_u(sd ^ DIFF_STREAM2, n, depth), &s1, &k1);
-                        sincospif(2.0f * rng_u(sd ^ DIFF_STREAM3, n, depth), &s2, &k2);
-                        D.ph1 = C(k1, s1);
-                        D.ph2 = C(k2, s2);
-                        D.c0 = fs > 0.0f ? M.S * sqrtf(6.283185307179586f * fs) : 0.0f;
-                        D.sqk = M.sqk;
-                        D.sq1k = M.sq1k;
+                        // incident-side hemisphere (App. A.10); set up out of line to keep
+                        // the loop body small
+                        diffuse_setup(M, k, nrm, cos1, co.rp, co.rl, ep, epi, s_tx[txi].seed, n, depth, &D, &ko);
                         epo = epi;
                         cpe = cpa = C(0.0f);
                     } else if (dec == 0) {

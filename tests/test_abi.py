@@ -47,7 +47,7 @@ def test_struct_layouts_match_header(L, tmp_path):
                   "n_ant", "ant_pos_host", "precoding_host"],
         "rm_trace_params": ["freq_hz", "max_depth", "flags", "map_origin", "cell_size", "nx", "ny", "deposit",
                             "block_size", "blocks_per_sm", "queue_chunk", "rr_depth", "rr_max_prob",
-                            "gain_threshold"],
+                            "gain_threshold", "refill_min"],
         "rm_stats": ["rays", "segments", "escapes", "segments_per_depth", "power_per_depth", "power2_per_depth",
                      "escaped_power_per_depth", "status", "kernel_ms"],
         "rm_segment_record": ["prim", "ix", "iy", "decision"],
