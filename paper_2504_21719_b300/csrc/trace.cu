@@ -366,6 +366,7 @@ struct Hit {
 // the smaller original triangle index; distances within 8 ulps (relative
 // TIE_REL) count as equal, so coplanar triangles resolve by index.
 constexpr float TIE_REL = 4.8e-7f;
+template <bool ONE_SITE>
 __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, int nt,
                                            int nlarge, const Ray& r, int exclude, unsigned& c_nodes,
                                            unsigned& c_tris, bool& overflow) {
@@ -432,54 +433,121 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
             h.prim = prim;
         }
     };
-    // large triangles first: their hit distance then prunes the traversal
-    for (int j = 0; j < nlarge; ++j) test_leaf(nt + j);
-    if (nt <= 0) return h;
-    if (nt == 1) {
-        test_leaf(0);
-        return h;
-    }
+    if (ONE_SITE) {
+        // One loop serves the large triangles (tested first: their hit distance
+        // then prunes the traversal), a one-triangle tree, and the stack traversal
+        // over internal nodes, whose hit leaf children are tested in their
+        // parent's step.  Every triangle test goes through the single call site at
+        // the bottom of the loop, which keeps the kernel's code small (the diffuse
+        // instantiations, whose longer shading otherwise crowds the instruction
+        // cache, use this form).
+        const int npre = nlarge + (nt == 1 ? 1 : 0);
+        int stack[STACK_SIZE];
+        int sp = 0;
+        int cur = 0;
+        int j = 0;
+        bool trav = nt > 1;
+        // a valid tree has nt - 1 internal nodes, each visited at most once
+        long long budget = 2LL * nt + 8;
+        while (true) {
+            int la = -1, lb = -1;
+            if (j < npre) {
+                la = j < nlarge ? nt + j : 0;
+                ++j;
+            } else if (trav) {
+                if (--budget < 0) {
+                    overflow = true;
+                    break;
+                }
+                ++c_nodes;
+                const float4* nd = nodes + 4 * (size_t)cur;
+                const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+                float tn0, tn1;
+                const float tmax = h.t * (1.0f + TIE_REL);
+                bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, ix, iy, iz, tmax, tn0);
+                bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, ix, iy, iz, tmax, tn1);
+                const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                if (h0 && c0 < 0) {
+                    la = ~c0;
+                    h0 = false;
+                }
+                if (h1 && c1 < 0) {
+                    lb = ~c1;
+                    h1 = false;
+                }
+                if (h0 && h1) {
+                    const bool first0 = tn0 <= tn1;
+                    if (sp < STACK_SIZE) stack[sp++] = first0 ? c1 : c0;
+                    else overflow = true;
+                    cur = first0 ? c0 : c1;
+                } else if (h0) {
+                    cur = c0;
+                } else if (h1) {
+                    cur = c1;
+                } else if (sp == 0) {
+                    trav = false;
+                } else {
+                    cur = stack[--sp];
+                }
+            } else {
+                break;
+            }
+    #pragma unroll 1
+            for (int q = 0; q < 2; ++q) {
+                const int lf = q ? lb : la;
+                if (lf >= 0) test_leaf(lf);
+            }
+        }
+    } else {
+        // large triangles first: their hit distance then prunes the traversal
+        for (int j = 0; j < nlarge; ++j) test_leaf(nt + j);
+        if (nt <= 0) return h;
+        if (nt == 1) {
+            test_leaf(0);
+            return h;
+        }
 
-    // Stack traversal over internal nodes; a hit leaf child is tested inside
-    // its parent's step, so leaves never take a loop iteration of their own.
-    int stack[STACK_SIZE];
-    int sp = 0;
-    int cur = 0;
-    // a valid tree has nt - 1 internal nodes, each visited at most once
-    long long budget = 2LL * nt + 8;
-    while (true) {
-        if (--budget < 0) {
-            overflow = true;
-            break;
-        }
-        ++c_nodes;
-        const float4* nd = nodes + 4 * (size_t)cur;
-        const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-        float tn0, tn1;
-        const float tmax = h.t * (1.0f + TIE_REL);
-        bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, ix, iy, iz, tmax, tn0);
-        bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, ix, iy, iz, tmax, tn1);
-        const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-        if (h0 && c0 < 0) {
-            test_leaf(~c0);
-            h0 = false;
-        }
-        if (h1 && c1 < 0) {
-            test_leaf(~c1);
-            h1 = false;
-        }
-        if (h0 && h1) {
-            const bool first0 = tn0 <= tn1;
-            if (sp < STACK_SIZE) stack[sp++] = first0 ? c1 : c0;
-            else overflow = true;
-            cur = first0 ? c0 : c1;
-        } else if (h0) {
-            cur = c0;
-        } else if (h1) {
-            cur = c1;
-        } else {
-            if (sp == 0) break;
-            cur = stack[--sp];
+        // Stack traversal over internal nodes; a hit leaf child is tested inside
+        // its parent's step, so leaves never take a loop iteration of their own.
+        int stack[STACK_SIZE];
+        int sp = 0;
+        int cur = 0;
+        // a valid tree has nt - 1 internal nodes, each visited at most once
+        long long budget = 2LL * nt + 8;
+        while (true) {
+            if (--budget < 0) {
+                overflow = true;
+                break;
+            }
+            ++c_nodes;
+            const float4* nd = nodes + 4 * (size_t)cur;
+            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            float tn0, tn1;
+            const float tmax = h.t * (1.0f + TIE_REL);
+            bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, ix, iy, iz, tmax, tn0);
+            bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, ix, iy, iz, tmax, tn1);
+            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            if (h0 && c0 < 0) {
+                test_leaf(~c0);
+                h0 = false;
+            }
+            if (h1 && c1 < 0) {
+                test_leaf(~c1);
+                h1 = false;
+            }
+            if (h0 && h1) {
+                const bool first0 = tn0 <= tn1;
+                if (sp < STACK_SIZE) stack[sp++] = first0 ? c1 : c0;
+                else overflow = true;
+                cur = first0 ? c0 : c1;
+            } else if (h0) {
+                cur = c0;
+            } else if (h1) {
+                cur = c1;
+            } else {
+                if (sp == 0) break;
+                cur = stack[--sp];
+            }
         }
     }
     return h;
@@ -656,7 +724,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArg
         // ---------------- closest hit ----------------
         Hit h{-1, 0x7fffffff, INFINITY};
         if (active) {
-            h = closest_hit(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris, overflow);
+            h = closest_hit<DIFF>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris, overflow);
             ++c_seg;
             if (h.slot < 0) ++c_esc;
         }
