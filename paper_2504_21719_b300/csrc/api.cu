@@ -1,5 +1,6 @@
 // C ABI of the SBR radio-map library (declared in include/rmsbr.h): argument
 // validation, scene and plan lifetime, per-call constant tables and launches.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -358,6 +359,99 @@ void fill_stats(const Scratch& h, const Prepared& P, rm_stats* st) {
     st->kernel_ms = P.kernel_ms;
 }
 
+// Per-thread host resources of run_trace, kept across calls: a pinned staging
+// buffer (the table image goes to the device in one copy, the scratch comes
+// back in one copy) and two timing events.  Every call synchronises its
+// stream before returning, so a staging buffer is never reused while a copy
+// from it is pending.
+struct ThreadRes {
+    char* stage = nullptr;
+    size_t cap = 0;
+    int ev_device = -1;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // device block [Scratch | tables | FP64 maps]: kept between calls so that
+    // a trace does not map fresh device memory every time
+    char* dblock = nullptr;
+    size_t dcap = 0;
+    int d_device = -1;
+    ~ThreadRes() {
+        if (stage) cudaFreeHost(stage);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (dblock) cudaFree(dblock);
+    }
+};
+thread_local ThreadRes g_res;
+
+cudaError_t device_block(size_t bytes, char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (g_res.dblock && (g_res.d_device != dev || g_res.dcap < bytes)) {
+        // the previous call synchronised its stream: nothing uses the block
+        int cur = dev;
+        if (g_res.d_device != dev) cudaSetDevice(g_res.d_device);
+        cudaFree(g_res.dblock);
+        if (g_res.d_device != dev) cudaSetDevice(cur);
+        g_res.dblock = nullptr;
+        g_res.dcap = 0;
+    }
+    if (!g_res.dblock) {
+        const size_t want = (bytes + (size_t(1) << 20) - 1) & ~((size_t(1) << 20) - 1);
+        if ((e = cudaMalloc((void**)&g_res.dblock, want)) != cudaSuccess) return e;
+        g_res.dcap = want;
+        g_res.d_device = dev;
+    }
+    *out = g_res.dblock;
+    return cudaSuccess;
+}
+
+cudaError_t staging(size_t bytes, char** out) {
+    if (g_res.cap < bytes) {
+        if (g_res.stage) cudaFreeHost(g_res.stage);
+        g_res.stage = nullptr;
+        g_res.cap = 0;
+        const size_t want = std::max(bytes, size_t(64) << 10);
+        cudaError_t e = cudaHostAlloc((void**)&g_res.stage, want, cudaHostAllocDefault);
+        if (e != cudaSuccess) return e;
+        g_res.cap = want;
+    }
+    *out = g_res.stage;
+    return cudaSuccess;
+}
+
+cudaError_t timing_events(cudaEvent_t* ev) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (g_res.ev_device != dev) {
+        for (cudaEvent_t& x : g_res.ev)
+            if (x) {
+                cudaEventDestroy(x);
+                x = nullptr;
+            }
+        g_res.ev_device = -1;
+        for (cudaEvent_t& x : g_res.ev)
+            if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
+        g_res.ev_device = dev;
+    }
+    ev[0] = g_res.ev[0];
+    ev[1] = g_res.ev[1];
+    return cudaSuccess;
+}
+
+// The table image [Scratch (zero) | MatDev | TxDev | AntDev] in the layout of
+// table_bytes, written into host memory at `h`; returns its size.
+size_t write_tables(const Prepared& P, size_t o_mat, size_t o_tx, char* h) {
+    const size_t o_ant = ant_offset(P, o_tx);
+    const size_t end = o_ant + P.ant.size() * sizeof(AntDev);
+    std::memset(h, 0, end);
+    std::memcpy(h + o_mat, P.mats.data(), P.mats.size() * sizeof(MatDev));
+    std::memcpy(h + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev));
+    if (!P.ant.empty()) std::memcpy(h + o_ant, P.ant.data(), P.ant.size() * sizeof(AntDev));
+    return end;
+}
+
 rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p, float* maps,
                     const float* dLdC, float* d_eps, float* d_sig, float* d_tx, const rm_material* smats,
                     rm_stats* stats, rm_segment_record* record, void* stream, bool adjoint) {
@@ -378,22 +472,18 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
     size_t o_mat, o_tx, o_m64 = 0;
     const size_t bytes = adjoint ? table_bytes(P, &o_mat, &o_tx) : block_bytes_with_maps64(P, &o_mat, &o_tx, &o_m64);
     cudaEvent_t ev[2];
-    RM_CUDA(cudaEventCreate(&ev[0]));
-    RM_CUDA(cudaEventCreate(&ev[1]));
+    RM_CUDA(timing_events(ev));
+    char* hst = nullptr;
+    RM_CUDA(staging(table_bytes(P, &o_mat, &o_tx), &hst));
+    const size_t tab = write_tables(P, o_mat, o_tx, hst);
     bool timed = false;
     char* dev = nullptr;
-    RM_CUDA(cudaMallocAsync((void**)&dev, bytes, S(stream)));
-    Scratch host;
+    RM_CUDA(device_block(bytes, &dev));
     cudaError_t e = cudaSuccess;
     int grid = 0;
     do {
-        if ((e = cudaMemsetAsync(dev, 0, sizeof(Scratch), S(stream))) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(dev + o_mat, P.mats.data(), P.mats.size() * sizeof(MatDev),
-                                 cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice,
-                                 S(stream))) != cudaSuccess) break;
-        if (!P.ant.empty() && (e = cudaMemcpyAsync(dev + ant_offset(P, o_tx), P.ant.data(), P.ant.size() * sizeof(AntDev),
-                                                   cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
+        // zeroed scratch and all constant tables in one copy from pinned memory
+        if ((e = cudaMemcpyAsync(dev, hst, tab, cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
         if (!adjoint && (e = cudaMemsetAsync(dev + o_m64, 0, sizeof(double) * P.a.ncell * ntx, S(stream))) != cudaSuccess)
             break;
         unsigned long long nrec = 0;
@@ -418,17 +508,15 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         if (adjoint && (e = launch_grad_out(reinterpret_cast<const Scratch*>(dev)->grad, sc->nm, ntx, d_eps, d_sig,
                                             d_tx, S(stream))) != cudaSuccess) break;
         if (!adjoint && (e = launch_map_to_f32(P.a.maps64, maps, P.a.ncell * ntx, S(stream))) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(&host, dev, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(hst, dev, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
     } while (false);
-    cudaError_t e2 = cudaFreeAsync(dev, S(stream));
     cudaError_t e3 = cudaStreamSynchronize(S(stream));
+    Scratch host;
+    std::memcpy(&host, hst, sizeof(Scratch));
     float ms = 0.0f;
     if (timed && e == cudaSuccess && e3 == cudaSuccess && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess)
         P.kernel_ms = ms;
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
     if (e != cudaSuccess) return cuda_fail(e, adjoint ? "rm_radio_map_grad" : "rm_radio_map_trace");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
     if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
     if (stats) fill_stats(host, P, stats);
     if (host.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow; affected rays were dropped");
@@ -571,7 +659,6 @@ rm_status rm_db_mse_loss(const float* maps_dev, const float* target_dev, int64_t
         e = launch_db_mse(maps_dev, target_dev, ncells, floor_linear, acc, loss_dev, dL_dmaps_dev, valid_dev, S(stream));
     cudaError_t e2 = cudaFreeAsync(acc, S(stream));
     if (e != cudaSuccess) return cuda_fail(e, "rm_db_mse_loss");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
     return RM_OK;
 }
 
