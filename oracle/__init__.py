@@ -77,6 +77,15 @@ def lib():
         _lib.or_f_alpha.argtypes = [C.c_int, C.c_double]
         _lib.or_scat_pattern.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, P, P, P, C.c_int64, P]
         _lib.or_diffuse_dir.argtypes = [P, P, C.c_int64, P]
+        _lib.or_wedges.restype = C.c_int64
+        _lib.or_wedges.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int64]
+        _lib.or_utd_F.argtypes = [C.c_double, P]
+        _lib.or_utd_field.argtypes = [P, P, P, P, C.c_double, P, P, C.c_double, P]
+        _lib.or_diffraction_point.restype = C.c_int
+        _lib.or_diffraction_point.argtypes = [P, P, C.c_double, C.c_double, C.c_double, P]
+        _lib.or_diffraction_map.restype = C.c_int
+        _lib.or_diffraction_map.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, C.c_int64, C.c_int,
+                                            P, C.c_int64, P, P, P]
         _lib.or_diffuse_interact.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                              C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, P, P, P]
         _lib.or_fibonacci.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
@@ -397,3 +406,70 @@ def lbvh(scene):
     ns = nt - int(nl.value)
     return {"keys": keys[:nt], "order": order[:nt], "nlarge": int(nl.value), "child": child[:max(ns - 1, 0)],
             "child_aabb": box[:max(ns - 1, 0)]}
+
+
+# ----------------------------------------------------------------------------
+# first-order diffraction radio map
+# ----------------------------------------------------------------------------
+
+def wedges(scene) -> np.ndarray:
+    """[nw, 16] = o(3) e(3) n0(3) nn(3) length n tri0 trin, ordered by (tri0, trin)."""
+    v, t, m, _ = _scene_arrays(scene)
+    n = lib().or_wedges(_p(v), len(v), _p(t), len(t), _p(m), None, 0)
+    out = np.zeros((max(n, 1), 16), np.float64)
+    lib().or_wedges(_p(v), len(v), _p(t), len(t), _p(m), _p(out), n)
+    return out[:n]
+
+
+def utd_F(x: float) -> complex:
+    out = np.empty(2, np.float64)
+    lib().or_utd_F(float(x), _p(out))
+    return complex(out[0], out[1])
+
+
+def utd_field(wedge16, s, v, sd, sobs, E, mats=((3.0, 0.0), (3.0, 0.0)), freq_hz=3.5e9):
+    """(E_d,phi, E_d,beta0) of one incident field E (3 complex) for the pins."""
+    w = np.ascontiguousarray(wedge16, np.float64)
+    E = np.asarray(E, np.complex128)
+    e6 = np.ascontiguousarray(np.stack([E.real, E.imag], 1).reshape(-1), np.float64)
+    m4 = np.ascontiguousarray(np.asarray(mats, np.float64).reshape(-1))
+    out = np.empty(4, np.float64)
+    lib().or_utd_field(_p(w), _p(np.ascontiguousarray(s, np.float64)), _p(np.ascontiguousarray(v, np.float64)),
+                       _p(np.ascontiguousarray(sd, np.float64)), float(sobs), _p(e6), _p(m4),
+                       2 * np.pi * freq_hz, _p(out))
+    return complex(out[0], out[1]), complex(out[2], out[3])
+
+
+def diffraction_point(wedge16, s, x, phi, zM):
+    """(t [3], weighting factor |dt/dx x dt/dphi|) or None when the ray misses the plane."""
+    out = np.empty(4, np.float64)
+    ok = lib().or_diffraction_point(_p(np.ascontiguousarray(wedge16, np.float64)),
+                                    _p(np.ascontiguousarray(s, np.float64)), float(x), float(phi), float(zM), _p(out))
+    return (out[:3].copy(), float(out[3])) if ok else None
+
+
+def diffraction_map(scene, tx, params, samples_per_wedge: int, mode: str = "plain", record=None,
+                    want_record: bool = False):
+    """First-order diffraction map [ny, nx] of one transmitter (oracle)."""
+    v, t, m, mats = _scene_arrays(scene)
+    otx, op = make_tx(tx), make_params(params)
+    nw = len(wedges(scene))
+    rec = None
+    if mode == "replay":
+        rec = np.ascontiguousarray(record, np.int32).reshape(nw * samples_per_wedge, 4).copy()
+    elif want_record:
+        rec = np.zeros((nw * samples_per_wedge, 4), np.int32)
+    mp = np.empty((params.ny, params.nx), np.float64)
+    cnt = np.empty(3, np.float64)
+    rep = OrReport()
+    rc = lib().or_diffraction_map(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), C.byref(otx),
+                                  C.byref(op), int(samples_per_wedge), {"plain": 0, "replay": 1}[mode], _p(rec),
+                                  0 if rec is None else len(rec), _p(mp), _p(cnt), C.byref(rep))
+    if rc != 0:
+        raise ValueError(f"or_diffraction_map failed ({rc})")
+    out = {"map": mp, "crossings": int(cnt[0]), "visible": int(cnt[1]), "wedges": int(cnt[2])}
+    if rec is not None:
+        out["record"] = rec
+    if mode == "replay":
+        out["report"] = rep.as_dict()
+    return out

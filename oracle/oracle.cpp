@@ -36,6 +36,7 @@
 #include <cstdint>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -1771,6 +1772,575 @@ int or_lbvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t* k
         for (int a = 0; a < 3; ++a) {
             nb[a] = std::min(lb[a], rb[a]);
             nb[3 + a] = std::max(lb[3 + a], rb[3 + a]);
+        }
+    }
+    return 0;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// First-order diffraction radio map (Sec. 4, "Computation of Radio Map due to
+// Diffraction"; UTD of App. A.8; weighting factor of the appendix on
+// diffraction radio maps).  Test infrastructure like the rest of this file.
+// ===========================================================================
+namespace {
+
+// 64-point Gauss-Legendre rule on [-1, 1]; nodes by Newton's method on P_64.
+struct GLRule {
+    std::vector<double> x, w;
+};
+const GLRule& gl64() {
+    static const GLRule rule = [] {
+        GLRule r;
+        const int n = 64;
+        r.x.resize(n);
+        r.w.resize(n);
+        auto legendre = [n](double z, double* dp) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            *dp = n * (z * p1 - p0) / (z * z - 1.0);
+            return p1;
+        };
+        for (int i = 0; i < n / 2; ++i) {
+            double z = std::cos(PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+            for (int it = 0; it < 100; ++it) {
+                const double dz = legendre(z, &dp) / dp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-16) break;
+            }
+            legendre(z, &dp);
+            r.x[i] = -z;
+            r.x[n - 1 - i] = z;
+            r.w[i] = r.w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+        return r;
+    }();
+    return rule;
+}
+
+// UTD transition function F(x) = 2 j sqrt(x) e^{jx} int_{sqrt x}^inf e^{-j t^2} dt
+// (App. A.8), from its defining integral.  The path of integration is turned
+// by -pi/4 about t = sqrt(x) (Cauchy: e^{-j t^2} decays in the sector swept),
+// t = sqrt(x) + e^{-j pi/4} u, which gives
+//   F(x) = 2 j e^{-j pi/4} sqrt(x) int_0^inf exp(-u^2 - b (1 + j) u) du,  b = sqrt(2x),
+// a smooth integrand below e^-40 beyond T = (sqrt(b^2 + 160) - b) / 2; the
+// integral over [0, T] is taken with the 64-point Gauss-Legendre rule.
+std::complex<double> utd_F(double x) {
+    if (!(x > 0.0)) return {0.0, 0.0};
+    const double b = std::sqrt(2.0 * x);
+    const double T = 0.5 * (std::sqrt(b * b + 160.0) - b);
+    const GLRule& g = gl64();
+    std::complex<double> I(0.0, 0.0);
+    for (size_t i = 0; i < g.x.size(); ++i) {
+        const double u = 0.5 * T * (g.x[i] + 1.0);
+        const double m = 0.5 * T * g.w[i] * std::exp(-u * u - b * u);
+        I += m * std::complex<double>(std::cos(b * u), -std::sin(b * u));
+    }
+    const std::complex<double> j(0.0, 1.0);
+    return 2.0 * j * std::exp(std::complex<double>(0.0, -PI / 4.0)) * std::sqrt(x) * I;
+}
+
+struct Wedge {
+    V3<double> o, e;      // edge origin and unit edge vector, e = n0 x nn / |n0 x nn|
+    V3<double> n0, nn;    // outward normals of the 0-face and the n-face
+    V3<double> t0;        // t0 = n0 x e, tangent to the 0-face
+    double len, n;        // edge length, exterior angle n pi
+    int tri0, trin, mat0, matn;
+};
+
+// Wedges of a mesh.  Reading (the paper keeps wedges "near the source"
+// found during SBR): every edge shared by exactly two triangles whose
+// outward normals, from the winding, meet at a convex corner (the far
+// vertex of the second triangle lies behind the first one's plane) and are
+// not parallel; visibility from the source is then decided per sample.
+// The triangle of lower index is the 0-face; wedges are ordered by
+// (tri0, trin).
+std::vector<Wedge> find_wedges(const Scene& S, const float* verts, const int32_t* tris, int64_t nt) {
+    std::map<std::pair<int, int>, std::vector<int>> edges;
+    for (int64_t i = 0; i < nt; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const int a = tris[3 * i + k], b = tris[3 * i + (k + 1) % 3];
+            edges[{std::min(a, b), std::max(a, b)}].push_back((int)i);
+        }
+    auto vert = [&](int id) { return V3<double>{verts[3 * id], verts[3 * id + 1], verts[3 * id + 2]}; };
+    std::vector<Wedge> out;
+    for (const auto& kv : edges) {
+        if (kv.second.size() != 2) continue;
+        const int A = std::min(kv.second[0], kv.second[1]), B = std::max(kv.second[0], kv.second[1]);
+        const Tri& TA = S.tris[A];
+        const Tri& TB = S.tris[B];
+        if (TA.area2 == 0.0 || TB.area2 == 0.0) continue;
+        const V3<double> c = cross(TA.n, TB.n);
+        const double sn = norm(c);
+        if (sn < 1e-9) continue;
+        int third = -1;
+        for (int k = 0; k < 3; ++k) {
+            const int id = tris[3 * B + k];
+            if (id != kv.first.first && id != kv.first.second) third = id;
+        }
+        const V3<double> p = vert(kv.first.first), q = vert(kv.first.second);
+        if (third < 0 || !(dot(vert(third) - p, TA.n) < 0.0)) continue;
+        Wedge W;
+        W.e = scl(c, 1.0 / sn);
+        W.n0 = TA.n;
+        W.nn = TB.n;
+        W.t0 = cross(W.n0, W.e);
+        W.n = 1.0 + std::acos(std::max(-1.0, std::min(1.0, dot(TA.n, TB.n)))) / PI;
+        W.o = dot(p, W.e) <= dot(q, W.e) ? p : q;
+        W.len = norm(q - p);
+        W.tri0 = A;
+        W.trin = B;
+        W.mat0 = TA.mat;
+        W.matn = TB.mat;
+        out.push_back(W);
+    }
+    std::sort(out.begin(), out.end(),
+              [](const Wedge& a, const Wedge& b) { return a.tri0 != b.tri0 ? a.tri0 < b.tri0 : a.trin < b.trin; });
+    return out;
+}
+
+// The UTD requires phi' <= pi (the source in front of the 0-face).  Reading:
+// otherwise the faces swap roles (e -> -e, t0 from the new 0-face); the
+// exterior angle is unchanged.  Whether phi' <= pi depends only on which side
+// of the 0-face's plane the source lies.
+Wedge oriented(const Wedge& W, const V3<double>& s) {
+    if (dot(s - W.o, W.n0) >= 0.0) return W;
+    Wedge R = W;
+    std::swap(R.n0, R.nn);
+    std::swap(R.mat0, R.matn);
+    std::swap(R.tri0, R.trin);
+    R.e = scl(W.e, -1.0);
+    R.o = W.o + scl(W.e, W.len);
+    R.t0 = cross(R.n0, R.e);
+    return R;
+}
+
+// Diffraction point v(x) = o + x e and Keller-cone direction
+//   k_s = sin b0' cos phi t0 + sin b0' sin phi n0 + cos b0' e,
+// cos b0' = (v - s).e / |v - s|, sin b0' = |s - s_E| / |v - s| (s_E the
+// projection of s onto the edge line): Eq. radio-map-solver-ci-D-reparametrization
+// and the weighting-factor appendix.  Typed so that dual numbers carry
+// d/dx and d/dphi.
+template <class R>
+void keller(const Wedge& W, const V3<double>& s, const R& x, const R& phi, V3<R>* v, V3<R>* ks) {
+    *v = {R(W.o.x) + x * W.e.x, R(W.o.y) + x * W.e.y, R(W.o.z) + x * W.e.z};
+    const V3<R> d{v->x - s.x, v->y - s.y, v->z - s.z};
+    const R dn = r_sqrt(d.x * d.x + d.y * d.y + d.z * d.z);
+    const V3<double> so = s - W.o;
+    const double rho = norm(so - scl(W.e, dot(so, W.e)));
+    const R cb = (d.x * W.e.x + d.y * W.e.y + d.z * W.e.z) / dn;
+    const R sb = R(rho) / dn;
+    const R cp = r_cos(phi), sp = r_sin(phi);
+    *ks = {sb * cp * W.t0.x + sb * sp * W.n0.x + cb * W.e.x, sb * cp * W.t0.y + sb * sp * W.n0.y + cb * W.e.y,
+           sb * cp * W.t0.z + sb * sp * W.n0.z + cb * W.e.z};
+}
+
+// Diffracted field (Eq. diffracted-field, with D_1..D_4 and the face
+// matrices R_0, R_n of the same appendix) for a 3-D incident field E (the
+// antenna field at unit distance): returns (E_d,phi, E_d,beta0) including the
+// spreading factor sqrt(1 / (s' s (s' + s))), without the phase
+// e^{-jk(s'+s)} (the map is non-coherent).  W must be oriented (phi' <= pi).
+// r_perp, r_par of a face are the half-space coefficients of Eq.
+// fresnel_vac at cos theta_r = |n . s'|.  Reading: a term whose cotangent
+// argument is exactly a multiple of pi (an exact shadow boundary, measure
+// zero) takes the mean of its one-sided limits, 0.
+void utd_field(const Wedge& W, const Cx<double>& eta0, const Cx<double>& etan, double k0, const V3<double>& s,
+               const V3<double>& v, const V3<double>& sd, double sobs, const CV3<double>& E,
+               std::complex<double> out[2]) {
+    typedef std::complex<double> cd;
+    const V3<double> sp_v = v - s;
+    const double sprime = norm(sp_v);
+    const V3<double> si = scl(sp_v, 1.0 / sprime);  // s' hat
+    const V3<double>& e = W.e;
+    const double sinb = norm(cross(sd, e));
+    const V3<double> phi_i = unit(cross(si, e));
+    const V3<double> beta_i = cross(phi_i, si);
+    auto proj = [&](const V3<double>& a) { return unit(a - scl(e, dot(a, e))); };
+    auto sgn = [](double z) { return z >= 0.0 ? 1.0 : -1.0; };
+    auto acl = [](double z) { return std::acos(std::max(-1.0, std::min(1.0, z))); };
+    const V3<double> sit = proj(si), sdt = proj(sd);
+    const double phip = PI - (PI - acl(-dot(sit, W.t0))) * sgn(-dot(sit, W.n0));
+    const double phid = PI - (PI - acl(dot(sdt, W.t0))) * sgn(dot(sdt, W.n0));
+    const double n = W.n;
+    const double L = sobs * sprime / (sobs + sprime) * sinb * sinb;
+    const cd pre = -std::exp(cd(0.0, -PI / 4.0)) / (2.0 * n * std::sqrt(2.0 * PI * k0) * sinb);
+    auto a_pm = [&](double beta, double pm) {
+        const double N = std::round((beta + pm * PI) / (2.0 * n * PI));
+        const double c = std::cos((2.0 * n * PI * N - beta) / 2.0);
+        return 2.0 * c * c;
+    };
+    auto D = [&](double beta, double pm) {
+        const double arg = (PI + pm * beta) / (2.0 * n);
+        const double sa = std::sin(arg);
+        if (sa == 0.0) return cd(0.0, 0.0);
+        return pre * (std::cos(arg) / sa) * utd_F(k0 * L * a_pm(beta, pm));
+    };
+    const cd D1 = D(phid - phip, +1.0), D2 = D(phid - phip, -1.0);
+    const cd D3 = D(phid + phip, +1.0), D4 = D(phid + phip, -1.0);
+    // face matrix W(phi_SB, beta_SB, e_r,perp, e_r,par) diag(r_perp, r_par) W(e_i,perp, e_i,par, phi', beta0')
+    auto face = [&](const V3<double>& nf, const Cx<double>& eta, cd M[2][2]) {
+        const double cr = std::fabs(dot(nf, si));
+        const Coefs<double> c = fresnel(eta, cr, 0.0, false);
+        const cd rp(c.r_perp.re, c.r_perp.im), rl(c.r_par.re, c.r_par.im);
+        const V3<double> sSB = si - scl(nf, 2.0 * dot(si, nf));
+        V3<double> x = cross(si, nf);
+        V3<double> eip;
+        if (norm(x) > 1e-12) {
+            eip = unit(x);
+        } else {
+            V3<double> ax = std::fabs(si.x) < 0.5 ? V3<double>{1, 0, 0} : V3<double>{0, 1, 0};
+            eip = unit(cross(si, ax));
+        }
+        const V3<double> eil = cross(eip, si);
+        const V3<double> erl = cross(eip, sSB);
+        const V3<double> phSB = scl(unit(cross(sSB, e)), -1.0);
+        const V3<double> beSB = cross(phSB, sSB);
+        const double Wo[2][2] = {{dot(phSB, eip), dot(phSB, erl)}, {dot(beSB, eip), dot(beSB, erl)}};
+        const double Wi[2][2] = {{dot(eip, phi_i), dot(eip, beta_i)}, {dot(eil, phi_i), dot(eil, beta_i)}};
+        const cd rr[2] = {rp, rl};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                cd m(0.0, 0.0);
+                for (int q = 0; q < 2; ++q) m += Wo[a][q] * rr[q] * Wi[q][b];
+                M[a][b] = m;
+            }
+    };
+    cd R0[2][2], Rn[2][2];
+    face(W.n0, eta0, R0);
+    if ((n - 1.0) * PI <= phip) {
+        face(W.nn, etan, Rn);
+    } else {
+        Rn[0][0] = Rn[1][1] = -1.0;
+        Rn[0][1] = Rn[1][0] = 0.0;
+    }
+    const cd ein[2] = {cd(E.x.re, E.x.im) * phi_i.x + cd(E.y.re, E.y.im) * phi_i.y + cd(E.z.re, E.z.im) * phi_i.z,
+                       cd(E.x.re, E.x.im) * beta_i.x + cd(E.y.re, E.y.im) * beta_i.y + cd(E.z.re, E.z.im) * beta_i.z};
+    const double spread = 1.0 / std::sqrt(sprime * sobs * (sprime + sobs));
+    for (int a = 0; a < 2; ++a) {
+        cd acc(0.0, 0.0);
+        for (int b = 0; b < 2; ++b) acc += ((-D1 + D4) * R0[a][b] + (-D2 + D3) * Rn[a][b]) * ein[b];
+        out[a] = -acc * spread;
+    }
+}
+
+// Is the open segment o + t d, t in (t0, t1), blocked by a triangle other
+// than ex0, ex1?
+bool blocked(const Scene& S, const V3<double>& o, const V3<double>& d, double t0, double t1, int ex0, int ex1) {
+    for (int i = 0; i < (int)S.tris.size(); ++i) {
+        if (i == ex0 || i == ex1) continue;
+        const double t = hit_mt(S.tris[i], o, d);
+        if (t > t0 && t < t1) return true;
+    }
+    return false;
+}
+// Could an FP32 computation decide the other way?  A triangle whose plane
+// hit lies within tol of the segment's open interval and within tol of the
+// triangle's boundary, or a hit within tol of an end.
+bool blocked_near_tie(const Scene& S, const V3<double>& o, const V3<double>& d, double t0, double t1, int ex0,
+                      int ex1, double tol) {
+    for (int i = 0; i < (int)S.tris.size(); ++i) {
+        if (i == ex0 || i == ex1) continue;
+        double t, m;
+        if (!plane_hit(S.tris[i], o, d, &t, &m)) continue;
+        if (!(t > t0 - tol && t < t1 + tol)) continue;
+        if (std::fabs(m) <= tol) return true;
+        if (m > 0.0 && (std::fabs(t - t0) <= tol || std::fabs(t - t1) <= tol)) return true;
+    }
+    return false;
+}
+
+// Sample i of N on a wedge: (u1, u2) = ((i + 1/2) / N, frac(i (phi_g - 1))),
+// the second coordinate from the 64-bit fixed-point product of the
+// Fibonacci lattice, truncated to 24 bits; x = u1 L_E, phi = u2 n pi.
+// Reading: the paper draws x and phi uniformly; this rank-1 lattice is the
+// quasi-Monte-Carlo counterpart, like the Fibonacci directions of SBR.
+inline void wedge_sample(int64_t i, int64_t N, double* u1, double* u2) {
+    *u1 = ((double)i + 0.5) / (double)N;
+    const uint64_t f = (uint64_t)i * 0x9E3779B97F4A7C16ULL;
+    *u2 = (double)(f >> 40) * 0x1.0p-24;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Wedges of a mesh (see find_wedges).  out (or null): [cap][16] doubles
+// o(3) e(3) n0(3) nn(3) len n tri0 trin; returns the number of wedges.
+int64_t or_wedges(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
+                  double* out, int64_t cap) {
+    std::vector<int32_t> mat(tri_mat, tri_mat + nt);
+    int nm = 1;
+    for (int32_t m : mat) nm = std::max(nm, m + 1);
+    std::vector<float> mats(3 * nm, 1.0f);
+    Scene S = make_scene(verts, nv, tris, nt, mat.data(), mats.data(), nm);
+    std::vector<Wedge> W = find_wedges(S, verts, tris, nt);
+    for (int64_t i = 0; i < (int64_t)W.size() && i < cap && out; ++i) {
+        double* o = out + 16 * i;
+        const Wedge& w = W[i];
+        const double v[16] = {w.o.x, w.o.y, w.o.z, w.e.x, w.e.y, w.e.z, w.n0.x, w.n0.y, w.n0.z,
+                              w.nn.x, w.nn.y, w.nn.z, w.len, w.n, (double)w.tri0, (double)w.trin};
+        std::memcpy(o, v, sizeof v);
+    }
+    return (int64_t)W.size();
+}
+
+// F(x) for the pins: out[2] = (re, im).
+void or_utd_F(double x, double* out) {
+    const std::complex<double> f = utd_F(x);
+    out[0] = f.real();
+    out[1] = f.imag();
+}
+
+// Diffracted field of one incident field for the pins: wedge w16 as written by
+// or_wedges (oriented here), source s, diffraction point v, diffracted
+// direction sd, observation distance sobs, incident field E6, face
+// materials (eps, sigma) x 2 at angular frequency omega.  out[4] = E_d,phi
+// and E_d,beta0 (re, im).
+void or_utd_field(const double* w16, const double* s, const double* v, const double* sd, double sobs,
+                  const double* E6, const double* mats4, double omega, double* out) {
+    Wedge W;
+    W.o = {w16[0], w16[1], w16[2]};
+    W.e = {w16[3], w16[4], w16[5]};
+    W.n0 = {w16[6], w16[7], w16[8]};
+    W.nn = {w16[9], w16[10], w16[11]};
+    W.len = w16[12];
+    W.n = w16[13];
+    W.t0 = cross(W.n0, W.e);
+    W.tri0 = W.trin = -1;
+    W.mat0 = 0;
+    W.matn = 1;
+    const V3<double> S{s[0], s[1], s[2]};
+    Wedge R = oriented(W, S);
+    const Cx<double> e0 = permittivity(mats4[2 * R.mat0], mats4[2 * R.mat0 + 1], omega);
+    const Cx<double> en = permittivity(mats4[2 * R.matn], mats4[2 * R.matn + 1], omega);
+    const CV3<double> E{Cx<double>(E6[0], E6[1]), Cx<double>(E6[2], E6[3]), Cx<double>(E6[4], E6[5])};
+    std::complex<double> o[2];
+    utd_field(R, e0, en, omega / C0, S, {v[0], v[1], v[2]}, {sd[0], sd[1], sd[2]}, sobs, E, o);
+    out[0] = o[0].real(); out[1] = o[0].imag(); out[2] = o[1].real(); out[3] = o[1].imag();
+}
+
+// Measurement point t(x, phi) on the plane z = zM and the weighting factor
+// |dt/dx x dt/dphi| for the pins: out[4] = t (3), J.  Wedge oriented for s.
+// Returns 0 when the diffracted ray does not reach the plane.
+int or_diffraction_point(const double* w16, const double* s, double x, double phi, double zM, double* out) {
+    Wedge W;
+    W.o = {w16[0], w16[1], w16[2]};
+    W.e = {w16[3], w16[4], w16[5]};
+    W.n0 = {w16[6], w16[7], w16[8]};
+    W.nn = {w16[9], w16[10], w16[11]};
+    W.len = w16[12];
+    W.n = w16[13];
+    W.t0 = cross(W.n0, W.e);
+    const V3<double> S{s[0], s[1], s[2]};
+    const Wedge R = oriented(W, S);
+    D xd(x), pd(phi);
+    xd.g[0] = 1.0;
+    pd.g[1] = 1.0;
+    V3<D> v, ks;
+    keller(R, S, xd, pd, &v, &ks);
+    if (!(ks.z.v != 0.0)) return 0;
+    const D gam = (D(zM) - v.z) / ks.z;
+    if (!(gam.v > 0.0)) return 0;
+    const V3<D> t{v.x + gam * ks.x, v.y + gam * ks.y, v.z + gam * ks.z};
+    const V3<double> tx{t.x.g[0], t.y.g[0], t.z.g[0]}, tp{t.x.g[1], t.y.g[1], t.z.g[1]};
+    out[0] = t.x.v; out[1] = t.y.v; out[2] = t.z.v;
+    out[3] = norm(cross(tx, tp));
+    return 1;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// Diffraction radio map of one transmitter (estimator Eq. radio-map-solver-ci-D-est):
+//   C_i += (1 / |M_i|) (L_E n pi / N') e(p) I(p) |dt/dx x dt/dphi|
+// over samples_per_wedge = N' lattice samples (x, phi) of every wedge, with
+// e(p) = (lambda0 / 4 pi)^2 |E_d|^2 (summed over the two field columns of a
+// dual-polarised antenna) and I(p) = 1 when the diffracted ray reaches the map
+// and neither the source-to-edge nor the edge-to-plane segment is blocked
+// (the wedge's own faces excluded, open intervals shortened by
+// 2^-16 max(1, |v|_inf) at the edge end).  mode 0 plain, 1 replay-check of
+// the record (GPU visibility bits and cells certified as FP64 near-ties).
+// rec: [nw][N'][4] = {bits (1: incident blocked, 2: diffracted blocked;
+// -1: no crossing in the map; -2: source behind both faces), ix, iy, 0}.
+// counts_out (or null): [3] samples with a crossing, visible samples, wedges.
+int or_diffraction_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
+                       const float* mats, int nm, const or_tx* tx, const or_params* P, int64_t samples_per_wedge,
+                       int mode, int32_t* rec, int64_t rec_cap, double* map_out, double* counts_out,
+                       or_report* report) {
+    if (samples_per_wedge < 1) return 1;
+    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
+    const std::vector<Wedge> WS = find_wedges(S, verts, tris, nt);
+    const int64_t nw = (int64_t)WS.size(), NS = samples_per_wedge;
+    if (rec && rec_cap < nw * NS) return 2;
+    MapGeom g = make_geom(*P, 1);
+    const double omega = 2.0 * PI * P->freq_hz, k0 = omega / C0;
+    const double lam4pi = C0 / P->freq_hz / (4.0 * PI);
+    TxC T = make_txc(*tx);
+    const int npol = tx->pol == 2 ? 2 : 1;
+    const V3<double> s{tx->pos[0], tx->pos[1], tx->pos[2]};
+    std::vector<DepList> lists(nw);
+    std::vector<ReplayState> rss(nw);
+    for (auto& r : rss) std::memset(&r.rep, 0, sizeof r.rep);
+    std::vector<double> cnt(2 * nw, 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t w = 0; w < nw; ++w) {
+        Sink<double> sink{&lists[w]};
+        ReplayState& rs = rss[w];
+        const Wedge R = oriented(WS[w], s);
+        const bool lit = dot(s - R.o, R.n0) >= 0.0;
+        const Cx<double> eta0 = permittivity(S.eps[R.mat0], S.sigma[R.mat0], omega);
+        const Cx<double> etan = permittivity(S.eps[R.matn], S.sigma[R.matn], omega);
+        for (int64_t i = 0; i < NS; ++i) {
+            int32_t* rc = rec ? rec + 4 * (w * NS + i) : nullptr;
+            if (mode == 1) rs.rep.segments++;
+            int code = -2, ix = NO_CELL, iy = NO_CELL;
+            double u1, u2;
+            wedge_sample(i, NS, &u1, &u2);
+            const double x = u1 * R.len, phi = u2 * R.n * PI;
+            V3<double> v, ks;
+            keller(R, s, x, phi, &v, &ks);
+            Crossing<double> cr = crossing(g, v, ks, INFINITY);
+            const double vm = std::max(std::fabs(v.x), std::max(std::fabs(v.y), std::fabs(v.z)));
+            const double eps = std::ldexp(std::max(1.0, vm), -16);
+            const V3<double> sv = v - s;
+            const double sprime = norm(sv);
+            const V3<double> si = scl(sv, 1.0 / sprime);
+            if (lit && !(mode == 1 && rc[0] == -2)) {
+                code = -1;
+                if (cr.valid) {
+                    ix = cr.ix;
+                    iy = cr.iy;
+                }
+                if (mode == 1 && (rc[1] != ix || rc[2] != iy)) {
+                    // the GPU's cell (or its finding the crossing in or out of the map)
+                    // is adopted only within tol of a cell boundary, the map edge or t_c = 0
+                    const double tc = ks.z != 0.0 ? (g.z - v.z) / ks.z : INFINITY;
+                    bool ok = std::isfinite(tc) && tc > -1.0;
+                    if (ok) {
+                        const V3<double> pc = v + scl(ks, tc);
+                        const double tol = tie_tol(pc, sprime + std::fabs(tc));
+                        const double sh = g.bilinear ? 0.5 : 0.0;
+                        const double ux = (pc.x - g.x0) / g.cell - sh, uy = (pc.y - g.y0) / g.cell - sh;
+                        const double bx = tol / g.cell;
+                        auto near_int = [&](double u) { return std::fabs(u - std::nearbyint(u)) <= bx; };
+                        if (rc[1] != NO_CELL && ix != NO_CELL) {
+                            ok = std::abs(rc[1] - ix) <= 1 && std::abs(rc[2] - iy) <= 1 &&
+                                 (rc[1] == ix || near_int(ux)) && (rc[2] == iy || near_int(uy));
+                        } else {
+                            ok = near_int(ux) || near_int(uy) || std::fabs(tc) <= tol;
+                            if (ok && rc[1] != NO_CELL) {
+                                const int ex = (int)std::floor(ux), ey = (int)std::floor(uy);
+                                ok = std::abs(rc[1] - ex) <= 1 && std::abs(rc[2] - ey) <= 1;
+                            }
+                        }
+                        if (ok && rc[1] != NO_CELL && !cr.valid) {
+                            cr.x = pc.x;
+                            cr.y = pc.y;
+                            cr.tc_v = tc;
+                        }
+                    }
+                    if (!ok) {
+                        rs.fail(w * NS + i, 0, 2, ix, iy, rc[1], rc[2]);
+                        continue;
+                    }
+                    rs.rep.adopted_cell++;
+                    ix = rc[1];
+                    iy = rc[2];
+                }
+                if (ix != NO_CELL) {
+                    const double gam = cr.tc_v;
+                    const bool bi = blocked(S, s, si, eps, sprime - eps, R.tri0, R.trin);
+                    const bool bd = blocked(S, v, ks, eps, gam, R.tri0, R.trin);
+                    code = (bi ? 1 : 0) | (bd ? 2 : 0);
+                    if (mode == 1 && rc[0] != code) {
+                        const double tol = tie_tol(v + scl(ks, gam), sprime + gam);
+                        const int diff = (rc[0] < 0 ? 3 : rc[0]) ^ code;
+                        bool ok = rc[0] >= 0;
+                        if (ok && (diff & 1) && !blocked_near_tie(S, s, si, eps, sprime - eps, R.tri0, R.trin, tol))
+                            ok = false;
+                        if (ok && (diff & 2) && !blocked_near_tie(S, v, ks, eps, gam, R.tri0, R.trin, tol))
+                            ok = false;
+                        if (!ok) {
+                            rs.fail(w * NS + i, 0, 5, code, rc[0], 0, 0);
+                            continue;
+                        }
+                        rs.rep.adopted_hit++;
+                        code = rc[0];
+                    }
+                }
+            }
+            if (mode == 1 && rc[0] != code) {
+                // which side of the 0-face the source lies on is not adopted
+                rs.fail(w * NS + i, 0, 6, code, rc[0], 0, 0);
+                continue;
+            }
+            if (rc && mode == 0) {
+                rc[0] = code;
+                rc[1] = ix;
+                rc[2] = iy;
+                rc[3] = 0;
+            }
+            if (ix != NO_CELL) cnt[2 * w] += 1.0;
+            if (code != 0 || ix == NO_CELL) continue;
+            // weighting factor |dt/dx x dt/dphi| by dual numbers through t(x, phi)
+            D xd(x), pd(phi);
+            xd.g[0] = 1.0;
+            pd.g[1] = 1.0;
+            V3<D> vd, kd;
+            keller(R, s, xd, pd, &vd, &kd);
+            const D gam = (D(g.z) - vd.z) / kd.z;
+            const V3<double> tx_{vd.x.g[0] + gam.g[0] * kd.x.v + gam.v * kd.x.g[0],
+                                 vd.y.g[0] + gam.g[0] * kd.y.v + gam.v * kd.y.g[0],
+                                 vd.z.g[0] + gam.g[0] * kd.z.v + gam.v * kd.z.g[0]};
+            const V3<double> tp_{vd.x.g[1] + gam.g[1] * kd.x.v + gam.v * kd.x.g[1],
+                                 vd.y.g[1] + gam.g[1] * kd.y.v + gam.v * kd.y.g[1],
+                                 vd.z.g[1] + gam.g[1] * kd.z.v + gam.v * kd.z.g[1]};
+            const double J = norm(cross(tx_, tp_));
+            // incident antenna field in the departure direction s' (App. A.1, Sec. 4.5)
+            const std::complex<double> al = array_factor(T, si, k0);
+            double pw = 0.0;
+            for (int p = 0; p < npol; ++p) {
+                const V3<double> f = tx_field(si, T.R, tx->pattern, tx->pol == 2 ? p : tx->pol);
+                const CV3<double> E{Cx<double>(f.x * al.real(), f.x * al.imag()), Cx<double>(f.y * al.real(), f.y * al.imag()),
+                                    Cx<double>(f.z * al.real(), f.z * al.imag())};
+                std::complex<double> ed[2];
+                utd_field(R, eta0, etan, k0, s, v, ks, cr.tc_v, E, ed);
+                pw += std::norm(ed[0]) + std::norm(ed[1]);
+            }
+            const double value = lam4pi * lam4pi * pw * J * (R.len * R.n * PI / (double)NS) / (g.cell * g.cell);
+            deposit(g, cr, ix, iy, value, sink);
+            cnt[2 * w + 1] += 1.0;
+        }
+    }
+    std::memset(map_out, 0, sizeof(double) * (size_t)P->nx * P->ny);
+    for (int64_t w = 0; w < nw; ++w)
+        for (size_t j = 0; j < lists[w].cell.size(); ++j) map_out[lists[w].cell[j]] += lists[w].val[j];
+    if (counts_out) {
+        counts_out[0] = counts_out[1] = 0.0;
+        for (int64_t w = 0; w < nw; ++w) { counts_out[0] += cnt[2 * w]; counts_out[1] += cnt[2 * w + 1]; }
+        counts_out[2] = (double)nw;
+    }
+    if (report) {
+        std::memset(report, 0, sizeof *report);
+        bool have = false;
+        for (int64_t w = 0; w < nw; ++w) {
+            const or_report& r = rss[w].rep;
+            report->segments += r.segments;
+            report->adopted_hit += r.adopted_hit;
+            report->adopted_cell += r.adopted_cell;
+            report->failures += r.failures;
+            if (r.failures && !have) {
+                have = true;
+                report->fail_ray = r.fail_ray;
+                report->fail_kind = r.fail_kind;
+                std::memcpy(report->fail_info, r.fail_info, sizeof r.fail_info);
+            }
         }
     }
     return 0;

@@ -291,6 +291,21 @@ def ground_and_wall(ground_half: float = 500.0, x: float = 20.0, half_w: float =
     return Scene("ground+wall", vv, tt, mm, np.array([GROUND, wall_mat], np.float32))
 
 
+def single_box(x0=0.0, x1=20.0, y0=0.0, y1=30.0, h=25.0, mat=(5.0, 0.1, WALL_THICKNESS), ground=None) -> Scene:
+    """One box building [x0, x1] x [y0, y1] x [0, h] with outward-wound faces (12
+    triangles, material 0), optionally on a square ground of half-size `ground`
+    (material 1, half-space)."""
+    mb = _MeshBuilder()
+    if ground:
+        gv, gt = _quad_ground(ground)
+        mb.add(gv, gt, 1)
+    v, t = _box(x0, x1, y0, y1, 0.0, h)
+    mb.add(v, t, 0)
+    vv, tt, mm = mb.build()
+    mats = [mat] + ([GROUND] if ground else [])
+    return Scene("single-box", vv, tt, mm, np.array(mats, np.float32))
+
+
 def closed_box(half: float = 10.0, mat=(3.0, 0.0, WALL_THICKNESS)) -> Scene:
     """Closed box [-half, half]^3 of slab walls (lossless by default), 12 triangles."""
     v, t = _box(-half, half, -half, half, -half, half)
