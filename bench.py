@@ -345,6 +345,20 @@ def run_extra(api, S, torch, gpu_name):
     a = _kernel_rate(api, gs, [ta], api.params_from(p, **kw))
     a["setting"] = "64-element half-wavelength ULA, uniform precoding"
     out["synthetic_array_64"] = a
+    # first-order diffraction map of the same transmitter: 1200 wedges x 4096 samples
+    wl = gs.wedges()
+    for _ in range(2):
+        api.diffraction_map(gs, txs, p, 4096, wedges=wl)
+    dk, dst = [], None
+    for _ in range(5):
+        r = api.diffraction_map(gs, txs, p, 4096, wedges=wl)
+        dk.append(r["stats"]["kernel_ms"])
+        dst = r["stats"]
+    k = statistics.mean(dk)
+    out["diffraction"] = {"value": round(dst["rays"] / (k / 1e3), 1), "unit": "wedge samples/s",
+                          "kernel_ms": round(k, 3), "samples": dst["rays"], "wedges": wl[1],
+                          "in_map": dst["segments"], "deposits": dst["deposits"],
+                          "setting": "4096 samples per wedge; two visibility queries and the UTD field per sample"}
     gs.free()
     sc, txs, p = S.workload(3)
     blk, bps, qch, rfm = tuned(gpu_name, "batched")

@@ -297,6 +297,62 @@ rm_status rm_radio_map_trace_noalloc(const rm_scene* scene, const rm_tx* tx_host
                                      const rm_trace_params* params, float* maps_dev,
                                      rm_stats* stats_host_or_null, void* stream);
 
+/* ------------------------------------------------------------------------
+ * First-order diffraction radio map (Sec. 4, "Computation of Radio Map due
+ * to Diffraction"; UTD of App. A.8)
+ * ------------------------------------------------------------------------ */
+
+/* A wedge: a mesh edge shared by two triangles that meet at a convex corner.
+ * The 0-face is the triangle of lower index; edge = n0 x nn / |n0 x nn| runs
+ * from origin for `length` metres; the exterior angle is n pi, 1 < n <= 2.
+ * Normals are the outward normals given by the triangles' winding. */
+typedef struct {
+    float origin[3];
+    float edge[3];
+    float n0[3];        /* outward normal of the 0-face */
+    float nn[3];        /* outward normal of the n-face */
+    float length;       /* m */
+    float n;            /* exterior angle / pi */
+    int32_t tri0, trin; /* triangle indices of the two faces (as uploaded) */
+    int32_t mat0, matn; /* their materials */
+} rm_wedge;
+
+/* The wedges of a scene: every edge (by vertex indices) shared by exactly two
+ * triangles whose outward normals are not parallel and whose corner is convex
+ * (the far vertex of the n-face lies behind the 0-face's plane).  Ordered by
+ * (tri0, trin).  Writes min(count, cap) wedges to out_host (may be NULL with
+ * cap 0) and the total to *count.  Synchronous: copies the mesh to the host. */
+rm_status rm_scene_wedges(const rm_scene* scene, rm_wedge* out_host, int64_t cap, int64_t* count);
+
+/* Diffraction radio maps [ntx][ny][nx] (overwritten; add them to the SBR maps
+ * of rm_radio_map_trace for the full map, as the paper does).
+ * Estimator (Eq. radio-map-solver-ci-D-est): every wedge gets
+ * samples_per_wedge samples (x, phi), x = L_E (i + 1/2)/N, phi = n pi
+ * frac(i (phi_g - 1)) (a rank-1 lattice, the quasi-Monte-Carlo form of
+ * uniform sampling); sample i adds
+ *   (1 / Delta^2) (L_E n pi / N) (lambda0 / 4 pi)^2 |E_d|^2 |dt/dx x dt/dphi|
+ * to the cell its diffracted ray crosses, when neither the source-to-edge nor
+ * the edge-to-plane segment is blocked.  E_d follows Eq. diffracted-field
+ * (diffraction coefficients D_1..D_4 with the UTD transition function, face
+ * matrices R_0, R_n with the half-space Fresnel coefficients of both faces'
+ * materials), for the transmitter's antenna field in the direction of the
+ * diffraction point (pattern, orientation, polarisation(s), synthetic array).
+ * The faces swap roles when the source lies behind the 0-face (the UTD
+ * assumes phi' <= pi).  Uses params: freq_hz, map geometry, deposit (box or
+ * bilinear), RM_STATS, block_size; other fields are ignored.
+ * wedges_host: nw wedges (from rm_scene_wedges or any subset of them).
+ * record_dev_or_null: [ntx][nw][samples_per_wedge] records {bits, ix, iy, 0},
+ * bits = 1 incident segment blocked | 2 diffracted segment blocked, -1 no
+ * crossing in the map, -2 source behind both faces.
+ * stats: rays = samples, segments = samples reaching the map, deposits,
+ * nodes_visited / tris_tested of the visibility queries, kernel_ms.
+ * Errors: RM_EINVAL for bad arguments (nw * samples * ntx must stay below
+ * 2^40); synchronises `stream`. */
+rm_status rm_diffraction_map(const rm_scene* scene, const rm_wedge* wedges_host, int64_t nw, const rm_tx* tx_host,
+                             int32_t ntx, const rm_trace_params* params, int64_t samples_per_wedge,
+                             float* maps_dev, rm_stats* stats_host_or_null, rm_segment_record* record_dev_or_null,
+                             void* stream);
+
 /* Number of triangles / internal BVH nodes of a scene (host call, no device work). */
 rm_status rm_scene_info(const rm_scene* scene, int64_t* nt, int64_t* nnodes, int32_t* nm,
                         int32_t* built);

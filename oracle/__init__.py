@@ -85,7 +85,7 @@ def lib():
         _lib.or_diffraction_point.argtypes = [P, P, C.c_double, C.c_double, C.c_double, P]
         _lib.or_diffraction_map.restype = C.c_int
         _lib.or_diffraction_map.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, C.c_int64, C.c_int,
-                                            P, C.c_int64, P, P, P]
+                                            P, C.c_int64, P, P, P, P]
         _lib.or_diffuse_interact.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                              C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, P, P, P]
         _lib.or_fibonacci.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
@@ -449,8 +449,10 @@ def diffraction_point(wedge16, s, x, phi, zM):
 
 
 def diffraction_map(scene, tx, params, samples_per_wedge: int, mode: str = "plain", record=None,
-                    want_record: bool = False):
-    """First-order diffraction map [ny, nx] of one transmitter (oracle)."""
+                    want_record: bool = False, slack: bool = False):
+    """First-order diffraction map [ny, nx] of one transmitter (oracle); with
+    ``slack`` also the per-cell value change of the deposits under a +-1e-5 rad
+    shift of their Keller azimuth."""
     v, t, m, mats = _scene_arrays(scene)
     otx, op = make_tx(tx), make_params(params)
     nw = len(wedges(scene))
@@ -460,11 +462,12 @@ def diffraction_map(scene, tx, params, samples_per_wedge: int, mode: str = "plai
     elif want_record:
         rec = np.zeros((nw * samples_per_wedge, 4), np.int32)
     mp = np.empty((params.ny, params.nx), np.float64)
+    sl = np.empty((params.ny, params.nx), np.float64) if slack else None
     cnt = np.empty(3, np.float64)
     rep = OrReport()
     rc = lib().or_diffraction_map(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), C.byref(otx),
                                   C.byref(op), int(samples_per_wedge), {"plain": 0, "replay": 1}[mode], _p(rec),
-                                  0 if rec is None else len(rec), _p(mp), _p(cnt), C.byref(rep))
+                                  0 if rec is None else len(rec), _p(mp), _p(cnt), C.byref(rep), _p(sl))
     if rc != 0:
         raise ValueError(f"or_diffraction_map failed ({rc})")
     out = {"map": mp, "crossings": int(cnt[0]), "visible": int(cnt[1]), "wedges": int(cnt[2])}
@@ -472,4 +475,6 @@ def diffraction_map(scene, tx, params, samples_per_wedge: int, mode: str = "plai
         out["record"] = rec
     if mode == "replay":
         out["report"] = rep.as_dict()
+    if slack:
+        out["slack"] = sl
     return out

@@ -2169,10 +2169,14 @@ extern "C" {
 // rec: [nw][N'][4] = {bits (1: incident blocked, 2: diffracted blocked;
 // -1: no crossing in the map; -2: source behind both faces), ix, iy, 0}.
 // counts_out (or null): [3] samples with a crossing, visible samples, wedges.
+// slack_out (or null) [ny][nx]: per cell, the sum over deposits of the largest
+// change of a deposit's value when its Keller azimuth moves by +-1e-5 rad
+// (test error bounds: FP32 may put a sample on the other side of a shadow
+// boundary or of a rounding point of N^+-).
 int or_diffraction_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
                        const float* mats, int nm, const or_tx* tx, const or_params* P, int64_t samples_per_wedge,
                        int mode, int32_t* rec, int64_t rec_cap, double* map_out, double* counts_out,
-                       or_report* report) {
+                       or_report* report, double* slack_out) {
     if (samples_per_wedge < 1) return 1;
     Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
     const std::vector<Wedge> WS = find_wedges(S, verts, tris, nt);
@@ -2184,13 +2188,14 @@ int or_diffraction_map(const float* verts, int64_t nv, const int32_t* tris, int6
     TxC T = make_txc(*tx);
     const int npol = tx->pol == 2 ? 2 : 1;
     const V3<double> s{tx->pos[0], tx->pos[1], tx->pos[2]};
-    std::vector<DepList> lists(nw);
+    std::vector<DepList> lists(nw), slacks(slack_out ? nw : 0);
     std::vector<ReplayState> rss(nw);
     for (auto& r : rss) std::memset(&r.rep, 0, sizeof r.rep);
     std::vector<double> cnt(2 * nw, 0.0);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t w = 0; w < nw; ++w) {
         Sink<double> sink{&lists[w]};
+        Sink<double> slack_sink{slack_out ? &slacks[w] : nullptr};
         ReplayState& rs = rss[w];
         const Wedge R = oriented(WS[w], s);
         const bool lit = dot(s - R.o, R.n0) >= 0.0;
@@ -2304,23 +2309,52 @@ int or_diffraction_map(const float* verts, int64_t nv, const int32_t* tris, int6
             const double J = norm(cross(tx_, tp_));
             // incident antenna field in the departure direction s' (App. A.1, Sec. 4.5)
             const std::complex<double> al = array_factor(T, si, k0);
-            double pw = 0.0;
-            for (int p = 0; p < npol; ++p) {
-                const V3<double> f = tx_field(si, T.R, tx->pattern, tx->pol == 2 ? p : tx->pol);
-                const CV3<double> E{Cx<double>(f.x * al.real(), f.x * al.imag()), Cx<double>(f.y * al.real(), f.y * al.imag()),
-                                    Cx<double>(f.z * al.real(), f.z * al.imag())};
-                std::complex<double> ed[2];
-                utd_field(R, eta0, etan, k0, s, v, ks, cr.tc_v, E, ed);
-                pw += std::norm(ed[0]) + std::norm(ed[1]);
-            }
-            const double value = lam4pi * lam4pi * pw * J * (R.len * R.n * PI / (double)NS) / (g.cell * g.cell);
+            auto power = [&](const V3<double>& kd_) {
+                double pw = 0.0;
+                for (int p = 0; p < npol; ++p) {
+                    const V3<double> f = tx_field(si, T.R, tx->pattern, tx->pol == 2 ? p : tx->pol);
+                    const CV3<double> E{Cx<double>(f.x * al.real(), f.x * al.imag()),
+                                        Cx<double>(f.y * al.real(), f.y * al.imag()),
+                                        Cx<double>(f.z * al.real(), f.z * al.imag())};
+                    std::complex<double> ed[2];
+                    utd_field(R, eta0, etan, k0, s, v, kd_, cr.tc_v, E, ed);
+                    pw += std::norm(ed[0]) + std::norm(ed[1]);
+                }
+                return pw;
+            };
+            const double pw = power(ks);
+            const double wgt = lam4pi * lam4pi * J * (R.len * R.n * PI / (double)NS) / (g.cell * g.cell);
+            const double value = wgt * pw;
             deposit(g, cr, ix, iy, value, sink);
+            if (slack_out) {
+                double sl = 0.0;
+                for (double dphi : {-1e-5, 1e-5}) {
+                    V3<double> v2, k2;
+                    keller(R, s, x, phi + dphi, &v2, &k2);
+                    sl = std::max(sl, std::fabs(wgt * power(k2) - value));
+                }
+                Crossing<double> c2 = cr;
+                if (g.bilinear) {
+                    // the slack goes unweighted to every cell of the stencil
+                    for (int b = 0; b < 2; ++b)
+                        for (int a = 0; a < 2; ++a)
+                            if (ix + a >= 0 && ix + a < g.nx && iy + b >= 0 && iy + b < g.ny)
+                                slack_sink.add((iy + b) * g.nx + ix + a, sl);
+                } else {
+                    deposit(g, c2, ix, iy, sl, slack_sink);
+                }
+            }
             cnt[2 * w + 1] += 1.0;
         }
     }
     std::memset(map_out, 0, sizeof(double) * (size_t)P->nx * P->ny);
     for (int64_t w = 0; w < nw; ++w)
         for (size_t j = 0; j < lists[w].cell.size(); ++j) map_out[lists[w].cell[j]] += lists[w].val[j];
+    if (slack_out) {
+        std::memset(slack_out, 0, sizeof(double) * (size_t)P->nx * P->ny);
+        for (int64_t w = 0; w < nw; ++w)
+            for (size_t j = 0; j < slacks[w].cell.size(); ++j) slack_out[slacks[w].cell[j]] += slacks[w].val[j];
+    }
     if (counts_out) {
         counts_out[0] = counts_out[1] = 0.0;
         for (int64_t w = 0; w < nw; ++w) { counts_out[0] += cnt[2 * w]; counts_out[1] += cnt[2 * w + 1]; }

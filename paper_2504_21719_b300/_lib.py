@@ -64,6 +64,12 @@ class rm_segment_record(C.Structure):
     _fields_ = [("prim", C.c_int32), ("ix", C.c_int32), ("iy", C.c_int32), ("decision", C.c_int32)]
 
 
+class rm_wedge(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("edge", C.c_float * 3), ("n0", C.c_float * 3), ("nn", C.c_float * 3),
+                ("length", C.c_float), ("n", C.c_float), ("tri0", C.c_int32), ("trin", C.c_int32),
+                ("mat0", C.c_int32), ("matn", C.c_int32)]
+
+
 P = C.c_void_p
 _SIGS = {
     "rm_scene_upload": ([P, C.c_int64, P, C.c_int64, P, P, C.c_int32, P, C.POINTER(P)], C.c_int),
@@ -78,6 +84,8 @@ _SIGS = {
     "rm_trace_plan_launch": ([P, P], C.c_int),
     "rm_trace_plan_stats": ([P, P, P], C.c_int),
     "rm_trace_plan_free": ([P], None),
+    "rm_scene_wedges": ([P, P, C.c_int64, P], C.c_int),
+    "rm_diffraction_map": ([P, P, C.c_int64, P, C.c_int32, P, C.c_int64, P, P, P, P], C.c_int),
     "rm_scene_info": ([P, P, P, P, P], C.c_int),
     "rm_scene_free": ([P], None),
     "rm_last_error": ([], C.c_char_p),

@@ -182,6 +182,16 @@ class Scene:
         return {"keys": keys[:n], "order": order[:n], "nlarge": nlarge, "child": child[:nn],
                 "child_aabb": box[:nn]}
 
+    def wedges(self):
+        """ctypes array of rm_wedge: the scene's wedges ordered by (tri0, trin)."""
+        n = C.c_int64()
+        _check(L.load().rm_scene_wedges(self.handle, None, 0, C.byref(n)), "rm_scene_wedges")
+        arr = (L.rm_wedge * max(n.value, 1))()
+        _check(L.load().rm_scene_wedges(self.handle, arr, n.value, C.byref(n)), "rm_scene_wedges")
+        self._wedges = arr
+        self._nw = n.value
+        return arr, n.value
+
     def free(self):
         if getattr(self, "handle", None):
             L.load().rm_scene_free(self.handle)
@@ -208,6 +218,27 @@ def trace(scene: Scene, txs, params, record=False, stream=None, out=None):
     _check(lib.rm_radio_map_trace(scene.handle, arr, ntx, C.byref(p), _ptr(maps), C.byref(st), _ptr(rec),
                                   _stream(stream)), "rm_radio_map_trace")
     res = {"maps": maps, "stats": st.as_dict()}
+    if record:
+        res["record"] = rec
+    return res
+
+
+def diffraction_map(scene: Scene, txs, params, samples_per_wedge: int, wedges=None, record=False, stream=None,
+                    out=None):
+    """First-order diffraction maps [ntx, ny, nx] (float32, cuda); add them to trace()'s maps
+    for the full radio map.  wedges: (ctypes array, count) or None for all of the scene's."""
+    lib = L.load()
+    arr, ntx = _tx_array(txs)
+    p = params if isinstance(params, L.rm_trace_params) else params_from(params)
+    w, nw = wedges if wedges is not None else scene.wedges()
+    maps = out if out is not None else torch.empty((ntx, p.ny, p.nx), dtype=torch.float32, device="cuda")
+    rec = None
+    if record:
+        rec = torch.empty((max(ntx * nw * samples_per_wedge, 1), 4), dtype=torch.int32, device="cuda")
+    st = L.rm_stats()
+    _check(lib.rm_diffraction_map(scene.handle, w, nw, arr, ntx, C.byref(p), int(samples_per_wedge), _ptr(maps),
+                                  C.byref(st), _ptr(rec), _stream(stream)), "rm_diffraction_map")
+    res = {"maps": maps, "stats": st.as_dict(), "wedges": nw}
     if record:
         res["record"] = rec
     return res

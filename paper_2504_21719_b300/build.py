@@ -22,7 +22,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-PER_FILE = {"trace.cu": ["-fmad=false"]}
+PER_FILE = {"trace.cu": ["-fmad=false"], "diffraction.cu": ["-fmad=false"]}
 
 
 def _sources():

@@ -740,6 +740,206 @@ void rm_trace_plan_free(rm_trace_plan* pl) {
     delete pl;
 }
 
+rm_status rm_scene_wedges(const rm_scene* sc, rm_wedge* out, int64_t cap, int64_t* count) {
+    if (!sc || !count) return fail(RM_EINVAL, "scene or count is NULL");
+    if (cap < 0 || (cap > 0 && !out)) return fail(RM_EINVAL, "cap must be >= 0 with an output array");
+    rm_status st = check_device(sc);
+    if (st != RM_OK) return st;
+    *count = 0;
+    if (sc->nt == 0) return RM_OK;
+    std::vector<float> v(3 * sc->nv);
+    std::vector<int32_t> t(3 * sc->nt), m(sc->nt);
+    RM_CUDA(cudaMemcpy(v.data(), sc->verts, sizeof(float) * v.size(), cudaMemcpyDeviceToHost));
+    RM_CUDA(cudaMemcpy(t.data(), sc->tris, sizeof(int32_t) * t.size(), cudaMemcpyDeviceToHost));
+    RM_CUDA(cudaMemcpy(m.data(), sc->tri_mat, sizeof(int32_t) * m.size(), cudaMemcpyDeviceToHost));
+    // edges keyed by their vertex indices (low, high) -> the triangles that own them
+    std::vector<std::pair<uint64_t, int32_t>> edges;
+    edges.reserve(3 * sc->nt);
+    for (int64_t i = 0; i < sc->nt; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t a = (uint32_t)t[3 * i + k], b = (uint32_t)t[3 * i + (k + 1) % 3];
+            edges.push_back({((uint64_t)std::min(a, b) << 32) | std::max(a, b), (int32_t)i});
+        }
+    std::sort(edges.begin(), edges.end());
+    auto vert = [&](uint32_t id, double* p) {
+        for (int c = 0; c < 3; ++c) p[c] = v[3 * (size_t)id + c];
+    };
+    auto normal = [&](int32_t tri, double* n) {
+        double a[3], b[3], c[3];
+        vert(t[3 * tri], a);
+        vert(t[3 * tri + 1], b);
+        vert(t[3 * tri + 2], c);
+        const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        const double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(l > 0.0)) return false;
+        for (int q = 0; q < 3; ++q) n[q] /= l;
+        return true;
+    };
+    std::vector<rm_wedge> W;
+    for (size_t i = 0; i < edges.size();) {
+        size_t j = i;
+        while (j < edges.size() && edges[j].first == edges[i].first) ++j;
+        if (j - i == 2) {
+            const int32_t A = std::min(edges[i].second, edges[i + 1].second);
+            const int32_t B = std::max(edges[i].second, edges[i + 1].second);
+            const uint32_t ia = (uint32_t)(edges[i].first >> 32), ib = (uint32_t)(edges[i].first & 0xffffffffu);
+            double na[3], nb[3];
+            if (A != B && normal(A, na) && normal(B, nb)) {
+                const double c[3] = {na[1] * nb[2] - na[2] * nb[1], na[2] * nb[0] - na[0] * nb[2],
+                                     na[0] * nb[1] - na[1] * nb[0]};
+                const double sn = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+                int32_t third = -1;
+                for (int k = 0; k < 3; ++k)
+                    if ((uint32_t)t[3 * B + k] != ia && (uint32_t)t[3 * B + k] != ib) third = t[3 * B + k];
+                double p[3], q[3], r[3];
+                vert(ia, p);
+                vert(ib, q);
+                bool convex = false;
+                if (third >= 0) {
+                    vert((uint32_t)third, r);
+                    convex = (r[0] - p[0]) * na[0] + (r[1] - p[1]) * na[1] + (r[2] - p[2]) * na[2] < 0.0;
+                }
+                if (sn >= 1e-9 && convex) {
+                    rm_wedge w;
+                    double e[3];
+                    for (int k = 0; k < 3; ++k) e[k] = c[k] / sn;
+                    const double dp = p[0] * e[0] + p[1] * e[1] + p[2] * e[2], dq = q[0] * e[0] + q[1] * e[1] + q[2] * e[2];
+                    const double* o = dp <= dq ? p : q;
+                    for (int k = 0; k < 3; ++k) {
+                        w.origin[k] = (float)o[k];
+                        w.edge[k] = (float)e[k];
+                        w.n0[k] = (float)na[k];
+                        w.nn[k] = (float)nb[k];
+                    }
+                    w.length = (float)std::sqrt((q[0] - p[0]) * (q[0] - p[0]) + (q[1] - p[1]) * (q[1] - p[1]) +
+                                                (q[2] - p[2]) * (q[2] - p[2]));
+                    const double cn = std::max(-1.0, std::min(1.0, na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2]));
+                    w.n = (float)(1.0 + std::acos(cn) / PI);
+                    w.tri0 = A;
+                    w.trin = B;
+                    w.mat0 = m[A];
+                    w.matn = m[B];
+                    W.push_back(w);
+                }
+            }
+        }
+        i = j;
+    }
+    std::sort(W.begin(), W.end(), [](const rm_wedge& a, const rm_wedge& b) {
+        return a.tri0 != b.tri0 ? a.tri0 < b.tri0 : a.trin < b.trin;
+    });
+    *count = (int64_t)W.size();
+    if (out && cap > 0) std::memcpy(out, W.data(), sizeof(rm_wedge) * (size_t)std::min<int64_t>(cap, *count));
+    return RM_OK;
+}
+
+rm_status rm_diffraction_map(const rm_scene* sc, const rm_wedge* wedges, int64_t nw, const rm_tx* tx, int32_t ntx,
+                             const rm_trace_params* p, int64_t ns, float* maps, rm_stats* stats,
+                             rm_segment_record* record, void* stream) {
+    rm_status st = validate(sc, tx, ntx, p);
+    if (st != RM_OK) return st;
+    if ((st = check_device(sc)) != RM_OK) return st;
+    if (!maps) return fail(RM_EINVAL, "maps_dev is NULL");
+    if (nw < 0 || (nw > 0 && !wedges)) return fail(RM_EINVAL, "nw must be >= 0 with a wedge array");
+    if (ns < 1) return fail(RM_EINVAL, "samples_per_wedge must be >= 1");
+    if ((double)nw * (double)ns * (double)ntx >= 1099511627776.0)
+        return fail(RM_EINVAL, "nw * samples_per_wedge * ntx must stay below 2^40");
+    for (int64_t i = 0; i < nw; ++i) {
+        const rm_wedge& w = wedges[i];
+        if (!(w.length > 0.0f) || !(w.n > 1.0f && w.n <= 2.0f) || w.mat0 < 0 || w.mat0 >= sc->nm || w.matn < 0 ||
+            w.matn >= sc->nm || !std::isfinite(w.origin[0]) || !std::isfinite(w.origin[1]) ||
+            !std::isfinite(w.origin[2]))
+            return fail(RM_EINVAL, "wedge " + std::to_string(i) + ": length > 0, 1 < n <= 2 and valid materials required");
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RM_CUDA(cudaStreamIsCapturing(S(stream), &cs));
+    if (cs != cudaStreamCaptureStatusNone) return fail(RM_ESTATE, "stream is capturing");
+    Prepared P;
+    prepare(sc, tx, ntx, p, nullptr, &P);
+    size_t o_mat, o_tx;
+    const size_t tab = table_bytes(P, &o_mat, &o_tx);
+    const size_t o_w = (tab + 255) & ~size_t(255);
+    const size_t o_m64 = (o_w + sizeof(rm_wedge) * (size_t)std::max<int64_t>(nw, 1) + 255) & ~size_t(255);
+    const unsigned long long ncell = (unsigned long long)p->nx * p->ny;
+    const size_t bytes = o_m64 + sizeof(double) * ncell * ntx;
+    cudaEvent_t ev[2];
+    RM_CUDA(timing_events(ev));
+    char* hst = nullptr;
+    RM_CUDA(staging(o_w + sizeof(rm_wedge) * (size_t)std::max<int64_t>(nw, 1), &hst));
+    const size_t tab_used = write_tables(P, o_mat, o_tx, hst);
+    if (nw > 0) std::memcpy(hst + o_w, wedges, sizeof(rm_wedge) * (size_t)nw);
+    char* dev = nullptr;
+    RM_CUDA(device_block(bytes, &dev));
+    DiffArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.nodes = sc->nodes;
+    A.tris = sc->trirec;
+    A.nt = (int32_t)(sc->nt - sc->nlarge);
+    A.nlarge = (int32_t)sc->nlarge;
+    A.wedges = reinterpret_cast<const rm_wedge*>(dev + o_w);
+    A.nw = nw;
+    A.mats = reinterpret_cast<const MatDev*>(dev + o_mat);
+    A.tx = reinterpret_cast<const TxDev*>(dev + o_tx);
+    A.ant = reinterpret_cast<const AntDev*>(dev + ant_offset(P, o_tx));
+    A.ntx = ntx;
+    A.nm = sc->nm;
+    A.ns = (unsigned long long)ns;
+    A.total = (unsigned long long)nw * (unsigned long long)ns * (unsigned long long)ntx;
+    A.x0 = P.a.x0;
+    A.y0 = P.a.y0;
+    A.zm = P.a.zm;
+    A.cell = P.a.cell;
+    A.inv_cell = P.a.inv_cell;
+    A.nx = p->nx;
+    A.ny = p->ny;
+    A.bilinear = p->deposit == 1;
+    A.ncell = ncell;
+    A.k0 = P.a.k0;
+    const double lam4pi = C0 / p->freq_hz / (4.0 * PI);
+    A.lam4pi2_over_cell2 = (float)(lam4pi * lam4pi / ((double)p->cell_size * (double)p->cell_size));
+    double L, a[FADDEEVA_N];
+    faddeeva_coefficients(FADDEEVA_N, &L, a);
+    A.wz_L = (float)L;
+    for (int k = 0; k < FADDEEVA_N; ++k) A.wz_a[k] = (float)a[k];
+    A.npol = P.npol;
+    A.stats = (p->flags & RM_STATS) ? 1 : 0;
+    A.maps64 = reinterpret_cast<double*>(dev + o_m64);
+    A.record = record;
+    A.scratch = reinterpret_cast<Scratch*>(dev);
+    cudaError_t e = cudaSuccess;
+    bool timed = false;
+    int grid = 0;
+    do {
+        if ((e = cudaMemcpyAsync(dev, hst, tab_used, cudaMemcpyHostToDevice, S(stream))) != cudaSuccess) break;
+        if (nw > 0 && (e = cudaMemcpyAsync(dev + o_w, hst + o_w, sizeof(rm_wedge) * (size_t)nw, cudaMemcpyHostToDevice,
+                                           S(stream))) != cudaSuccess)
+            break;
+        if ((e = cudaMemsetAsync(dev + o_m64, 0, sizeof(double) * ncell * ntx, S(stream))) != cudaSuccess) break;
+        if (A.total > 0) {
+            if ((e = cudaEventRecord(ev[0], S(stream))) != cudaSuccess) break;
+            if ((e = launch_diffraction(A, p->block_size ? p->block_size : 256, S(stream), &grid)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(ev[1], S(stream))) != cudaSuccess) break;
+            timed = true;
+        }
+        if ((e = launch_map_to_f32(A.maps64, maps, ncell * ntx, S(stream))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(hst, dev, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
+    } while (false);
+    cudaError_t e3 = cudaStreamSynchronize(S(stream));
+    Scratch host;
+    std::memcpy(&host, hst, sizeof(Scratch));
+    float ms = 0.0f;
+    if (timed && e == cudaSuccess && e3 == cudaSuccess && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess)
+        P.kernel_ms = ms;
+    if (e != cudaSuccess) return cuda_fail(e, "rm_diffraction_map");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
+    if (stats) fill_stats(host, P, stats);
+    if (host.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow in a visibility query");
+    return RM_OK;
+}
+
 rm_status rm_scene_info(const rm_scene* sc, int64_t* nt, int64_t* nnodes, int32_t* nm, int32_t* built) {
     if (!sc) return fail(RM_EINVAL, "scene is NULL");
     if (nt) *nt = sc->nt;

@@ -99,6 +99,39 @@ struct TraceArgs {
     rm_segment_record* record;   // optional
 };
 
+// First-order diffraction map (diffraction.cu).  The UTD transition function
+// is evaluated through the Faddeeva function w(z) with Weideman's rational
+// expansion of FADDEEVA_N terms (coefficients from faddeeva_coefficients).
+constexpr int FADDEEVA_N = 16;
+struct DiffArgs {
+    const float4* nodes;         // LBVH (as for the tracer)
+    const float4* tris;
+    int32_t nt, nlarge;
+    const rm_wedge* wedges;      // [nw] (device copy)
+    long long nw;
+    const MatDev* mats;          // [nm]
+    const TxDev* tx;             // [ntx]
+    const AntDev* ant;
+    int32_t ntx, nm;
+    unsigned long long ns;       // samples per wedge
+    unsigned long long total;    // ntx * nw * ns
+    float x0, y0, zm, cell, inv_cell;
+    int32_t nx, ny, bilinear;
+    unsigned long long ncell;
+    float k0;                    // 2 pi / lambda0
+    float lam4pi2_over_cell2;    // (lambda0 / 4 pi)^2 / Delta^2
+    float wz_L;                  // Weideman's L
+    float wz_a[FADDEEVA_N];      // a_1 .. a_N
+    int32_t npol, stats;
+    double* maps64;              // [ntx][ny][nx]
+    rm_segment_record* record;   // optional, [ntx][nw][ns]
+    Scratch* scratch;
+};
+cudaError_t launch_diffraction(const DiffArgs& a, int block, cudaStream_t s, int* grid_out);
+// Weideman's L and a_1..a_N for w(z) = 2 p(Z) / (L - iz)^2 + (1/sqrt(pi)) / (L - iz),
+// p(Z) = sum_{n<N} a_{n+1} Z^n, Z = (L + iz)/(L - iz) (host, double).
+void faddeeva_coefficients(int N, double* L, double* a);
+
 // Host-side launchers (trace.cu)
 cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, bool diffuse,
                          int block, int blocks_per_sm, cudaStream_t s, int* grid_out);

@@ -1,0 +1,439 @@
+// First-order diffraction radio map on sm_103a (Sec. 4, "Computation of
+// Radio Map due to Diffraction"; UTD of App. A.8; weighting factor of the
+// appendix on diffraction radio maps).
+//
+// One thread per sample (x, phi) of a wedge, in a grid-stride loop over
+// (transmitter, wedge, sample); consecutive threads take neighbouring lattice
+// samples of one wedge.  Per sample:
+//   1. diffraction point v = o + x e and Keller-cone direction k_s;
+//   2. crossing of the measurement plane and its cell;
+//   3. two any-hit visibility queries through the LBVH (source -> v and
+//      v -> plane, the wedge's own faces excluded);
+//   4. the UTD field (Eq. diffracted-field) of the antenna field in the
+//      direction of v, for one or two polarisation columns;
+//   5. the weighting factor |dt/dx x dt/dphi|, derived by hand;
+//   6. an FP64 atomic deposit.
+// This file is compiled with -fmad=false like the tracer.
+#include <cmath>
+
+#include "common.cuh"
+#include "vec.cuh"
+
+namespace rmsbr {
+namespace {
+
+constexpr float PI_F = 3.14159265358979323846f;
+
+// ------------------------------------------------------------------ UTD transition function
+// w(z), Im z >= 0, by Weideman's rational expansion in Z = (L + iz)/(L - iz)
+// (SIAM J. Numer. Anal. 31, 1994).
+__device__ __forceinline__ cf faddeeva(cf z, const DiffArgs& A) {
+    const cf iz = C(-z.i, z.r);
+    const cf lp = C(A.wz_L + iz.r, iz.i), lm = C(A.wz_L - iz.r, -iz.i);
+    const cf Z = cdiv(lp, lm);
+    cf p = C(A.wz_a[FADDEEVA_N - 1]);
+    for (int k = FADDEEVA_N - 2; k >= 0; --k) p = p * Z + C(A.wz_a[k]);
+    const cf il = cdiv(C(1.0f), lm);
+    return p * il * il * 2.0f + il * 0.56418958354775628f;
+}
+// F(x) = 2 j sqrt(x) e^{jx} int_{sqrt x}^inf e^{-j t^2} dt = sqrt(pi x) e^{j pi/4} w(sqrt(x/2)(-1 + j))
+__device__ __forceinline__ cf utd_F(float x, const DiffArgs& A) {
+    if (!(x > 0.0f)) return C(0.0f);
+    const float r = sqrtf(0.5f * x);
+    const cf w = faddeeva(C(-r, r), A);
+    const float m = sqrtf(PI_F * x) * 0.70710678118654752f;
+    return w * C(m, m);
+}
+
+// ------------------------------------------------------------------ any-hit visibility
+// Is the open segment o + t d, t in (tmin, tmax), blocked by a triangle other
+// than the original triangles ex0, ex1?  Moeller-Trumbore per triangle,
+// stack traversal without ordering, early exit on the first blocker.
+__device__ __forceinline__ bool tri_blocks(const float4* __restrict__ tris, int slot, f3 o, f3 d, float tmin,
+                                           float tmax, int ex0, int ex1, unsigned& c_tris) {
+    const float4* tp = tris + 3 * (size_t)slot;
+    const float4 r2 = __ldg(tp + 2);
+    const int prim = __float_as_int(r2.z);
+    if (prim == ex0 || prim == ex1) return false;
+    ++c_tris;
+    const float4 r0 = __ldg(tp), r1 = __ldg(tp + 1);
+    const f3 a{r0.x, r0.y, r0.z}, b{r0.w, r1.x, r1.y}, c{r1.z, r1.w, r2.x};
+    const f3 e1 = b - a, e2 = c - a;
+    const f3 p = cross(d, e2);
+    const float det = dot(e1, p);
+    if (det == 0.0f) return false;
+    const float inv = 1.0f / det;
+    const f3 tv = o - a;
+    const float u = dot(tv, p) * inv;
+    if (u < 0.0f || u > 1.0f) return false;
+    const f3 q = cross(tv, e1);
+    const float v = dot(d, q) * inv;
+    if (v < 0.0f || u + v > 1.0f) return false;
+    const float t = dot(e2, q) * inv;
+    return t > tmin && t < tmax;
+}
+
+__device__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float tmax, int ex0, int ex1,
+                                unsigned& c_nodes, unsigned& c_tris, bool& overflow) {
+    for (int j = 0; j < A.nlarge; ++j)
+        if (tri_blocks(A.tris, A.nt + j, o, d, tmin, tmax, ex0, ex1, c_tris)) return true;
+    if (A.nt <= 0) return false;
+    if (A.nt == 1) return tri_blocks(A.tris, 0, o, d, tmin, tmax, ex0, ex1, c_tris);
+    const float ooeps = 0x1p-80f;
+    const float ix = 1.0f / (fabsf(d.x) > ooeps ? d.x : copysignf(ooeps, d.x));
+    const float iy = 1.0f / (fabsf(d.y) > ooeps ? d.y : copysignf(ooeps, d.y));
+    const float iz = 1.0f / (fabsf(d.z) > ooeps ? d.z : copysignf(ooeps, d.z));
+    auto box = [&](float lx, float ly, float lz, float hx, float hy, float hz) {
+        const float t0x = (lx - o.x) * ix, t1x = (hx - o.x) * ix;
+        const float t0y = (ly - o.y) * iy, t1y = (hy - o.y) * iy;
+        const float t0z = (lz - o.z) * iz, t1z = (hz - o.z) * iz;
+        const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), tmin));
+        const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax)) * 1.0000004f;
+        return tn <= tf;
+    };
+    int stack[STACK_SIZE];
+    int sp = 0, cur = 0;
+    long long budget = 2LL * A.nt + 8;
+    while (true) {
+        if (--budget < 0) {
+            overflow = true;
+            return false;
+        }
+        ++c_nodes;
+        const float4* nd = A.nodes + 4 * (size_t)cur;
+        const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+        bool h0 = box(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+        bool h1 = box(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+        const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+        if (h0 && c0 < 0) {
+            if (tri_blocks(A.tris, ~c0, o, d, tmin, tmax, ex0, ex1, c_tris)) return true;
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            if (tri_blocks(A.tris, ~c1, o, d, tmin, tmax, ex0, ex1, c_tris)) return true;
+            h1 = false;
+        }
+        if (h0 && h1) {
+            if (sp < STACK_SIZE) stack[sp++] = c1;
+            else overflow = true;
+            cur = c0;
+        } else if (h0) {
+            cur = c0;
+        } else if (h1) {
+            cur = c1;
+        } else {
+            if (sp == 0) return false;
+            cur = stack[--sp];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ antenna field
+// R (C_theta theta' + C_phi phi') in direction k (App. A.1) times the
+// synthetic-array factor alpha = sum_k u_P,k exp(j k0 k.d_k) (Sec. 4.5).
+__device__ void antenna_field(const TxDev& T, const AntDev* __restrict__ ant, float k0, f3 k, int pol, cf* E) {
+    const float lx = T.R[0] * k.x + T.R[3] * k.y + T.R[6] * k.z;
+    const float ly = T.R[1] * k.x + T.R[4] * k.y + T.R[7] * k.z;
+    const float lz = T.R[2] * k.x + T.R[5] * k.y + T.R[8] * k.z;
+    const float sxy = sqrtf(lx * lx + ly * ly);
+    float cph = 1.0f, sph = 0.0f;
+    if (sxy > 0.0f) {
+        cph = lx / sxy;
+        sph = ly / sxy;
+    }
+    const float g = (T.pattern == 1) ? 1.2247448713915890f * sxy : 1.0f;
+    const f3 e = pol == 0 ? f3{lz * cph, lz * sph, -sxy} : f3{-sph, cph, 0.0f};
+    float are = 1.0f, aim = 0.0f;
+    if (T.n_ant > 0) {
+        are = 0.0f;
+        for (int a = 0; a < T.n_ant; ++a) {
+            const AntDev el = ant[T.ant_begin + a];
+            float sn, cs;
+            sincosf(k0 * (k.x * el.dx + k.y * el.dy + k.z * el.dz), &sn, &cs);
+            are += el.pre * cs - el.pim * sn;
+            aim += el.pre * sn + el.pim * cs;
+        }
+    }
+    const float ex = g * (T.R[0] * e.x + T.R[1] * e.y + T.R[2] * e.z);
+    const float ey = g * (T.R[3] * e.x + T.R[4] * e.y + T.R[5] * e.z);
+    const float ez = g * (T.R[6] * e.x + T.R[7] * e.y + T.R[8] * e.z);
+    E[0] = C(ex * are, ex * aim);
+    E[1] = C(ey * are, ey * aim);
+    E[2] = C(ez * are, ez * aim);
+}
+
+// ------------------------------------------------------------------ UTD field
+struct Mat2 {
+    cf m[2][2];
+};
+__device__ __forceinline__ f3 unit3(f3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+
+// Face matrix W(phi_SB, beta_SB, e_r,perp, e_r,par) diag(r_perp, r_par)
+// W(e_i,perp, e_i,par, phi', beta0') with the half-space coefficients of
+// Eq. fresnel_vac at cos theta = |n . s'|.
+__device__ Mat2 face_matrix(f3 nf, cf eta, f3 si, f3 e, f3 phi_i, f3 beta_i) {
+    const float cr = fminf(1.0f, fabsf(dot(nf, si)));
+    const float sin2 = (1.0f - cr) * (1.0f + cr);
+    const cf s = csqrt_p(C(eta.r - sin2, eta.i));
+    const cf c = C(cr);
+    const cf ec = eta * cr;
+    const cf rp = cdiv(c - s, c + s), rl = cdiv(ec - s, ec + s);
+    const f3 sSB = si - nf * (2.0f * dot(si, nf));
+    f3 eip = cross(si, nf);
+    const float len = sqrtf(dot(eip, eip));
+    if (len > 1e-6f) {
+        eip = eip * (1.0f / len);
+    } else {
+        const f3 ax = fabsf(si.x) < 0.5f ? f3{1.0f, 0.0f, 0.0f} : f3{0.0f, 1.0f, 0.0f};
+        eip = unit3(cross(si, ax));
+    }
+    const f3 eil = cross(eip, si);
+    const f3 erl = cross(eip, sSB);
+    const f3 phSB = unit3(cross(sSB, e)) * -1.0f;
+    const f3 beSB = cross(phSB, sSB);
+    const float wo[2][2] = {{dot(phSB, eip), dot(phSB, erl)}, {dot(beSB, eip), dot(beSB, erl)}};
+    const float wi[2][2] = {{dot(eip, phi_i), dot(eip, beta_i)}, {dot(eil, phi_i), dot(eil, beta_i)}};
+    Mat2 M;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) M.m[a][b] = rp * (wo[a][0] * wi[0][b]) + rl * (wo[a][1] * wi[1][b]);
+    return M;
+}
+
+// One term pre cot((pi + pm beta)/(2n)) F(k L a^pm(beta)), a^pm(beta) = 2 cos^2((2 n pi N - beta)/2),
+// N = round((beta + pm pi)/(2 n pi)); 0 at an exact shadow boundary.  Near a
+// shadow boundary the cotangent grows like 1/eps and F(k L a) shrinks like eps
+// (eps the distance to the boundary): both take eps from the same double-
+// precision reduction of beta (the cotangent's argument modulo pi, the
+// cosine's modulo pi/2), so their product keeps its FP32 accuracy.
+__device__ __forceinline__ cf utd_term(double beta, double pm, double n, float kL, cf pre, const DiffArgs& A) {
+    const double PI_D = 3.14159265358979323846;
+    const double arg = (PI_D + pm * beta) / (2.0 * n);
+    const float d = (float)(arg - PI_D * rint(arg / PI_D));
+    float sd, cd;
+    sincosf(d, &sd, &cd);
+    if (sd == 0.0f) return C(0.0f);
+    const double N = round((beta + pm * PI_D) / (2.0 * n * PI_D));
+    const double h = 0.5 * (2.0 * n * PI_D * N - beta);
+    const double qd = rint(h / (0.5 * PI_D));
+    const float r = (float)(h - qd * (0.5 * PI_D));
+    float sr, cr;
+    sincosf(r, &sr, &cr);
+    const int q = ((int)qd) & 3;  // cos(q pi/2 + r)
+    const float c = q == 0 ? cr : (q == 1 ? -sr : (q == 2 ? -cr : sr));
+    return pre * (cd / sd) * utd_F(kL * 2.0f * c * c, A);
+}
+
+// ------------------------------------------------------------------ kernel
+__global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
+    __shared__ unsigned long long s_cnt[6];
+    if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned c_rays = 0, c_seg = 0, c_nodes = 0, c_tris = 0, c_dep = 0;
+    bool overflow = false;
+    const unsigned long long per_tx = (unsigned long long)A.nw * A.ns;
+    for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < A.total;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        const int txi = (int)(w / per_tx);
+        const unsigned long long rem = w - (unsigned long long)txi * per_tx;
+        const long long wi = (long long)(rem / A.ns);
+        const unsigned long long i = rem - (unsigned long long)wi * A.ns;
+        ++c_rays;
+        const TxDev& T = A.tx[txi];
+        const rm_wedge W = A.wedges[wi];
+        const f3 s{T.pos[0], T.pos[1], T.pos[2]};
+        // orientation: the source in front of the 0-face (phi' <= pi), else the faces swap
+        f3 o{W.origin[0], W.origin[1], W.origin[2]}, e{W.edge[0], W.edge[1], W.edge[2]};
+        f3 n0{W.n0[0], W.n0[1], W.n0[2]}, nn{W.nn[0], W.nn[1], W.nn[2]};
+        int m0 = W.mat0, mn = W.matn;
+        if (dot(s - o, n0) < 0.0f) {
+            o = o + e * W.length;
+            e = e * -1.0f;
+            const f3 t = n0;
+            n0 = nn;
+            nn = t;
+            const int tm = m0;
+            m0 = mn;
+            mn = tm;
+        }
+        rm_segment_record* rec = A.record ? A.record + w : nullptr;
+        int code = -2, cxi = NO_CELL, cyi = NO_CELL;
+        float fx = 0.0f, fy = 0.0f;
+        if (dot(s - o, n0) >= 0.0f) {
+            code = -1;
+            const f3 t0 = cross(n0, e);
+            // sample i: x = L (i + 1/2)/N, phi = n pi frac(i (phi_g - 1)) (24-bit fixed point)
+            const float u1 = (float)(((double)i + 0.5) / (double)A.ns);
+            const unsigned long long fr = i * 0x9E3779B97F4A7C16ULL;
+            const float u2 = (float)(unsigned)(fr >> 40) * 0x1p-24f;
+            const float x = u1 * W.length;
+            float sp, cp;
+            sincospif(u2 * W.n, &sp, &cp);
+            const f3 v = o + e * x;
+            const f3 d = v - s;
+            const float dn = sqrtf(dot(d, d));
+            const f3 so = s - o;
+            const f3 perp = so - e * dot(so, e);
+            const float rho = sqrtf(dot(perp, perp));
+            const float cb = dot(d, e) / dn, sb = rho / dn;
+            const f3 u{cp * t0.x + sp * n0.x, cp * t0.y + sp * n0.y, cp * t0.z + sp * n0.z};
+            const f3 ks = u * sb + e * cb;
+            // plane crossing and cell (as the tracer's deposit)
+            const float tc = (A.zm - v.z) / ks.z;
+            bool dep = false;
+            if (ks.z != 0.0f && tc > 1e-9f) {
+                const float px = v.x + tc * ks.x, py = v.y + tc * ks.y;
+                float ux = (px - A.x0) * A.inv_cell, uy = (py - A.y0) * A.inv_cell;
+                if (A.bilinear) {
+                    ux -= 0.5f;
+                    uy -= 0.5f;
+                    if (ux >= -1.0f && ux < (float)A.nx && uy >= -1.0f && uy < (float)A.ny) {
+                        const float flx = floorf(ux), fly = floorf(uy);
+                        cxi = (int)flx;
+                        cyi = (int)fly;
+                        fx = ux - flx;
+                        fy = uy - fly;
+                        dep = true;
+                    }
+                } else if (ux >= 0.0f && ux < (float)A.nx && uy >= 0.0f && uy < (float)A.ny) {
+                    cxi = (int)ux;
+                    cyi = (int)uy;
+                    dep = true;
+                }
+            }
+            if (dep) {
+                ++c_seg;
+                const float vm = fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)));
+                const float eps = fmaxf(1.0f, vm) * 0x1p-16f;
+                const f3 si = d * (1.0f / dn);
+                const bool bi = segment_blocked(A, s, si, eps, dn - eps, W.tri0, W.trin, c_nodes, c_tris, overflow);
+                const bool bd = segment_blocked(A, v, ks, eps, tc, W.tri0, W.trin, c_nodes, c_tris, overflow);
+                code = (bi ? 1 : 0) | (bd ? 2 : 0);
+                if (code == 0) {
+                    // weighting factor |dt/dx x dt/dphi| (hand-derived): with a = (v - s).e,
+                    // d cb/dx = sb^2/dn, d sb/dx = -sb cb/dn, so
+                    // dk/dx = (sb/dn)(sb e - cb u), dk/dphi = sb (-sin phi t0 + cos phi n0),
+                    // dtc/dq = -(dv_z/dq + tc dk_z/dq)/k_z, dt/dq = dv/dq + dtc/dq k + tc dk/dq.
+                    const f3 dkx = (e * sb - u * cb) * (sb / dn);
+                    const f3 dkp{sb * (cp * n0.x - sp * t0.x), sb * (cp * n0.y - sp * t0.y),
+                                 sb * (cp * n0.z - sp * t0.z)};
+                    const float dtcx = -(e.z + tc * dkx.z) / ks.z;
+                    const float dtcp = -(tc * dkp.z) / ks.z;
+                    const float txx = e.x + dtcx * ks.x + tc * dkx.x, txy = e.y + dtcx * ks.y + tc * dkx.y;
+                    const float tpx = dtcp * ks.x + tc * dkp.x, tpy = dtcp * ks.y + tc * dkp.y;
+                    const float J = fabsf(txx * tpy - txy * tpx);
+                    // UTD (Eq. diffracted-field): angles from the 0-face (double precision:
+                    // the shadow boundaries sit at fixed values of phi +- phi'), phi of the sample
+                    const float nw_ = W.n;
+                    const double phi = (double)u2 * (double)nw_ * 3.14159265358979323846;
+                    const f3 sr = s - v;
+                    const f3 srt = sr - e * dot(sr, e);
+                    double phip = atan2((double)dot(srt, n0), (double)dot(srt, t0));
+                    if (phip < 0.0) phip += 2.0 * 3.14159265358979323846;
+                    const float sobs = tc;
+                    const float L = sobs * dn / (sobs + dn) * sb * sb;
+                    const float kL = A.k0 * L;
+                    const float pm = 1.0f / (2.0f * nw_ * sqrtf(2.0f * PI_F * A.k0) * sb);
+                    const cf pre = C(-0.70710678118654752f * pm, 0.70710678118654752f * pm);  // -e^{-j pi/4} pm
+                    const cf D1 = utd_term(phi - phip, +1.0f, nw_, kL, pre, A);
+                    const cf D2 = utd_term(phi - phip, -1.0f, nw_, kL, pre, A);
+                    const cf D3 = utd_term(phi + phip, +1.0f, nw_, kL, pre, A);
+                    const cf D4 = utd_term(phi + phip, -1.0f, nw_, kL, pre, A);
+                    const f3 phi_i = unit3(cross(si, e));
+                    const f3 beta_i = cross(phi_i, si);
+                    const MatDev& M0 = A.mats[m0];
+                    const MatDev& Mn = A.mats[mn];
+                    const Mat2 R0 = face_matrix(n0, C(M0.eta_re, M0.eta_im), si, e, phi_i, beta_i);
+                    Mat2 Rn;
+                    if (((double)nw_ - 1.0) * 3.14159265358979323846 <= phip) {
+                        Rn = face_matrix(nn, C(Mn.eta_re, Mn.eta_im), si, e, phi_i, beta_i);
+                    } else {
+                        Rn.m[0][0] = Rn.m[1][1] = C(-1.0f);
+                        Rn.m[0][1] = Rn.m[1][0] = C(0.0f);
+                    }
+                    const cf a0 = D4 - D1, an = D3 - D2;
+                    float pw = 0.0f;
+                    for (int p = 0; p < A.npol; ++p) {
+                        cf E[3];
+                        antenna_field(T, A.ant, A.k0, si, A.npol == 2 ? p : T.pol, E);
+                        const cf ein[2] = {edot(phi_i, E), edot(beta_i, E)};
+                        for (int r = 0; r < 2; ++r) {
+                            cf acc = C(0.0f);
+                            for (int c = 0; c < 2; ++c) acc = acc + (a0 * R0.m[r][c] + an * Rn.m[r][c]) * ein[c];
+                            pw += cabs2(acc);
+                        }
+                    }
+                    // (the minus sign of Eq. diffracted-field does not change |E_d|^2)
+                    const float spread = 1.0f / (dn * sobs * (dn + sobs));
+                    const float value = A.lam4pi2_over_cell2 * (W.length * nw_ * PI_F / (float)A.ns) * J * pw * spread;
+                    const unsigned long long mb = (unsigned long long)txi * A.ncell;
+                    if (A.bilinear) {
+                        for (int cn = 0; cn < 4; ++cn) {
+                            const int a = cn & 1, b = cn >> 1;
+                            const int xx = cxi + a, yy = cyi + b;
+                            if (xx < 0 || xx >= A.nx || yy < 0 || yy >= A.ny) continue;
+                            const float wgt = (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy);
+                            atomicAdd(A.maps64 + mb + (unsigned long long)yy * A.nx + xx, (double)(value * wgt));
+                        }
+                    } else {
+                        atomicAdd(A.maps64 + mb + (unsigned long long)cyi * A.nx + cxi, (double)value);
+                    }
+                    ++c_dep;
+                }
+            } else {
+                cxi = cyi = NO_CELL;
+            }
+        }
+        if (rec) {
+            rec->prim = code;
+            rec->ix = code == -2 ? NO_CELL : cxi;
+            rec->iy = code == -2 ? NO_CELL : cyi;
+            rec->decision = 0;
+        }
+    }
+    if (overflow) atomicOr(&A.scratch->status, 1);
+    const unsigned v[6] = {c_rays, c_seg, c_nodes, c_tris, c_dep, 0u};
+    for (int j = 0; j < 6; ++j) {
+        const unsigned sum = __reduce_add_sync(0xffffffffu, v[j]);
+        if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&s_cnt[j], (unsigned long long)sum);
+    }
+    __syncthreads();
+    if (threadIdx.x < 6 && s_cnt[threadIdx.x]) atomicAdd(&A.scratch->cnt[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+}  // namespace
+
+cudaError_t launch_diffraction(const DiffArgs& a, int block, cudaStream_t s, int* grid_out) {
+    if (block <= 0 || block > 256 || (block & 31)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t err;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_diffraction, block, 0)) != cudaSuccess)
+        return err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const unsigned long long need = (a.total + block - 1) / block;
+    const unsigned long long cap = (unsigned long long)occ * sms;
+    const int grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+    if (grid_out) *grid_out = grid;
+    k_diffraction<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+void faddeeva_coefficients(int N, double* L_out, double* a) {
+    // a_n: Fourier coefficients of f(theta) = (L^2 + t^2) exp(-t^2), t = L tan(theta/2),
+    // on (-pi, pi), by the midpoint rule (spectrally accurate for this smooth periodic f)
+    const double L = std::sqrt(N / std::sqrt(2.0));
+    const int M = 4096;
+    for (int n = 1; n <= N; ++n) {
+        double acc = 0.0;
+        for (int k = 0; k < M; ++k) {
+            const double th = -M_PI + (k + 0.5) * 2.0 * M_PI / M;
+            const double t = L * std::tan(0.5 * th);
+            acc += std::exp(-t * t) * (L * L + t * t) * std::cos(n * th);
+        }
+        a[n - 1] = acc / M;
+    }
+    *L_out = L;
+}
+
+}  // namespace rmsbr

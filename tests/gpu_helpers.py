@@ -41,3 +41,30 @@ def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max
     assert np.all(g[~mask] <= FLOOR)
     return {"worst_rel": float(rel.max()) if rel.size else 0.0, "worst_vs_bound": worst,
             "cells": int(mask.sum()), "report": rep}
+
+
+def compare_diffraction(orc, scene, tx, params, samples_per_wedge, gpu_map, gpu_record, rtol=MAP_RTOL,
+                        max_adopt_frac=MAX_ADOPT_FRAC):
+    """Replay the GPU's visibility bits and cells of a diffraction map in the
+    FP64 oracle (every difference certified as a near-tie), then compare the
+    maps cell by cell."""
+    rec = np.asarray(gpu_record).reshape(-1, 4)
+    r = orc.diffraction_map(scene, tx, params, samples_per_wedge, mode="replay", record=rec, slack=True)
+    rep = r["report"]
+    assert rep["failures"] == 0, rep
+    adopted = rep["adopted_hit"] + rep["adopted_cell"] + rep["adopted_decision"]
+    assert adopted <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
+    ref = r["map"]
+    g = np.asarray(gpu_map, np.float64).reshape(ref.shape)
+    mask = (ref > FLOOR) | (g > FLOOR)
+    err = np.abs(g - ref)[mask]
+    # the UTD field jumps across shadow boundaries (and where N^+- rounds the
+    # other way): FP32 angles, good to ~1e-6 rad, may put a sample on the other
+    # side of one; the oracle reports per cell how much its deposits change under
+    # a +-1e-5 rad shift of the Keller azimuth, which bounds such flips
+    bound = rtol * ref[mask] + r["slack"][mask]
+    rel = err / np.maximum(ref[mask], 1e-300)
+    worst = float((err / np.maximum(bound, 1e-300)).max()) if err.size else 0.0
+    assert np.all(err <= bound), (worst, float(rel.max()), int(mask.sum()), rep)
+    assert np.all(g[~mask] <= FLOOR)
+    return {"worst_rel": float(rel.max()) if rel.size else 0.0, "cells": int(mask.sum()), "report": rep}

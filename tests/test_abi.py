@@ -51,6 +51,7 @@ def test_struct_layouts_match_header(L, tmp_path):
         "rm_stats": ["rays", "segments", "escapes", "segments_per_depth", "power_per_depth", "power2_per_depth",
                      "escaped_power_per_depth", "status", "kernel_ms"],
         "rm_segment_record": ["prim", "ix", "iy", "decision"],
+        "rm_wedge": ["origin", "edge", "n0", "nn", "length", "n", "tri0", "trin", "mat0", "matn"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rmsbr.h"', "int main(void){"]
     for s, fs in fields.items():
@@ -90,6 +91,9 @@ def test_host_validation_without_gpu(L):
     assert lib.rm_radio_map_trace(None, None, 1, None, None, None, None, None) == L.RM_EINVAL
     assert lib.rm_radio_map_grad(None, None, 1, None, None, None, None, None, None, None, None, None) == L.RM_EINVAL
     assert lib.rm_db_mse_loss(None, None, 10, 0.0, None, None, None, None) == L.RM_EINVAL
+    n = C.c_int64()
+    assert lib.rm_scene_wedges(None, None, 0, C.byref(n)) == L.RM_EINVAL
+    assert lib.rm_diffraction_map(None, None, 0, None, 1, None, 16, None, None, None, None) == L.RM_EINVAL
     assert lib.rm_trace_plan_launch(None, None) == L.RM_EINVAL
     assert lib.rm_bvh_build(None, None) == L.RM_EINVAL
     assert lib.rm_scene_info(None, None, None, None, None) == L.RM_EINVAL

@@ -1,0 +1,95 @@
+"""GPU parity of the first-order diffraction radio map (Sec. 4, "Computation
+of Radio Map due to Diffraction"; UTD of App. A.8): the library's wedges
+against the oracle's, and the maps, replay-checked against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+from gpu_helpers import compare_diffraction
+
+pytestmark = pytest.mark.gpu
+
+
+def _wedge_array(w, n):
+    return np.array([[*x.origin, *x.edge, *x.n0, *x.nn, x.length, x.n, x.tri0, x.trin] for x in w[:n]])
+
+
+@pytest.mark.parametrize("scene", ["box", "manhattan"])
+def test_wedges_match_oracle(orc, api, scene):
+    sc = S.single_box(ground=500.0) if scene == "box" else S.workload(2)[0]
+    gs = api.Scene.from_obj(sc)
+    w, n = gs.wedges()
+    got = _wedge_array(w, n)
+    ref = orc.wedges(sc)
+    assert got.shape == ref.shape
+    assert np.array_equal(got[:, 14:16], ref[:, 14:16])
+    assert np.allclose(got[:, :14], ref[:, :14], rtol=1e-6, atol=1e-5)
+    gs.free()
+
+
+def _run(api, sc, tx, p, ns):
+    gs = api.Scene.from_obj(sc)
+    r = api.diffraction_map(gs, [tx], p, ns, record=True)
+    torch.cuda.synchronize()
+    out = (r["maps"][0].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
+    gs.free()
+    return out
+
+
+def test_diffraction_parity_single_box(orc, api):
+    sc = S.single_box(ground=500.0)
+    p = S.TraceParams(3.5e9, 0, cell_size=2.0, nx=60, ny=60, map_origin=(10.0, 15.0, 1.5))
+    tx = S.Tx(pos=(-30.0, -20.0, 15.0), num_rays=1)
+    m, rec, st = _run(api, sc, tx, p, 4096)
+    assert st["deposits"] > 5000 and st["rays"] == len(rec)
+    compare_diffraction(orc, sc, tx, p, 4096, m, rec)
+
+
+@pytest.mark.parametrize("pol,pattern,deposit", [(0, 0, 0), (2, 1, 1)])
+def test_diffraction_parity_manhattan(orc, api, pol, pattern, deposit):
+    sc, txs, p = S.workload(2)
+    p.nx = p.ny = 256
+    p.cell_size = 2.0
+    p.deposit = deposit
+    tx = txs[0]
+    tx.pol, tx.pattern = pol, pattern
+    m, rec, st = _run(api, sc, tx, p, 256)
+    assert st["deposits"] > 5000
+    compare_diffraction(orc, sc, tx, p, 256, m, rec)
+
+
+def test_diffraction_batched_transmitters_match_single(api):
+    sc, txs, p = S.workload(2)
+    p.nx = p.ny = 128
+    p.cell_size = 4.0
+    a = S.Tx(pos=(0.0, 0.0, 30.0), num_rays=1)
+    b = S.Tx(pos=(-75.0, 32.0, 12.0), num_rays=1, pol=1)
+    gs = api.Scene.from_obj(sc)
+    both = api.diffraction_map(gs, [a, b], p, 128)["maps"].cpu().numpy()
+    for k, t in enumerate((a, b)):
+        one = api.diffraction_map(gs, [t], p, 128)["maps"][0].cpu().numpy()
+        assert np.allclose(both[k], one, rtol=1e-6, atol=1e-6 * one.max())
+    gs.free()
+
+
+def test_diffraction_rejects_bad_arguments(api):
+    from paper_2504_21719_b300 import _lib as L
+    sc = S.single_box()
+    gs = api.Scene.from_obj(sc)
+    w, n = gs.wedges()
+    p = api.params_from(S.TraceParams(3.5e9, 0))
+    arr, ntx = api._tx_array([S.Tx(pos=(-30.0, -20.0, 15.0), num_rays=1)])
+    maps = torch.empty((1, 100, 100), dtype=torch.float32, device="cuda")
+    lib = L.load()
+    st = L.rm_stats()
+    import ctypes as C
+    assert lib.rm_diffraction_map(gs.handle, w, n, arr, ntx, C.byref(p), 0, maps.data_ptr(), C.byref(st), None,
+                                  None) == L.RM_EINVAL
+    bad = (L.rm_wedge * 1)()
+    bad[0] = w[0]
+    bad[0].n = 2.5
+    assert lib.rm_diffraction_map(gs.handle, bad, 1, arr, ntx, C.byref(p), 16, maps.data_ptr(), C.byref(st), None,
+                                  None) == L.RM_EINVAL
+    assert b"wedge 0" in lib.rm_last_error()
+    gs.free()
