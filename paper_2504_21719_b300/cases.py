@@ -1,0 +1,58 @@
+"""Run one workload of the library a few times, for profilers and timing.
+
+    python -m paper_2504_21719_b300.cases CASE [--rays N] [--reps R]
+
+CASE is one of
+  manhattan    forward trace, Manhattan scene (1202 triangles), 1 TX, depth 5
+  diffuse      the same with diffuse reflection on every material (S = 0.5)
+  adjoint      adjoint of the differentiable workload (8 materials, bilinear)
+  diffraction  first-order diffraction map, Manhattan, 1200 wedges
+Each case prints one line: case, kernel ms of the last call, and its work
+counters.
+"""
+from __future__ import annotations
+
+import argparse
+import copy
+
+
+def main(argv=None):
+    import numpy as np
+    import torch
+
+    from . import api
+    from synth import scenes as S
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction"])
+    ap.add_argument("--rays", type=int, default=0, help="rays per TX (trace cases) or samples per wedge")
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    if a.case in ("manhattan", "diffuse", "diffraction"):
+        sc, txs, p = S.workload(2)
+        if a.case == "diffuse":
+            sc = sc.with_scattering(0.5, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
+            p = copy.copy(p)
+            p.diffuse = True
+    else:
+        sc, txs, p = S.workload(4)
+    if a.rays and a.case != "diffraction":
+        txs[0].num_rays = a.rays
+    gs = api.Scene.from_obj(sc)
+    for _ in range(a.reps):
+        if a.case == "diffraction":
+            r = api.diffraction_map(gs, txs, p, a.rays or 4096)
+        elif a.case == "adjoint":
+            f = api.trace(gs, txs, p)
+            r = api.grad(gs, txs, p, torch.ones_like(f["maps"]))
+        else:
+            r = api.trace(gs, txs, p)
+    torch.cuda.synchronize()
+    st = r["stats"]
+    print(a.case, "kernel_ms", round(st["kernel_ms"], 4), "rays", st["rays"], "segments", st["segments"],
+          "deposits", st["deposits"])
+    gs.free()
+
+
+if __name__ == "__main__":
+    main()

@@ -200,27 +200,25 @@ __device__ Mat2 face_matrix(f3 nf, cf eta, f3 si, f3 e, f3 phi_i, f3 beta_i) {
 }
 
 // One term pre cot((pi + pm beta)/(2n)) F(k L a^pm(beta)), a^pm(beta) = 2 cos^2((2 n pi N - beta)/2),
-// N = round((beta + pm pi)/(2 n pi)); 0 at an exact shadow boundary.  Near a
-// shadow boundary the cotangent grows like 1/eps and F(k L a) shrinks like eps
-// (eps the distance to the boundary): both take eps from the same double-
-// precision reduction of beta (the cotangent's argument modulo pi, the
-// cosine's modulo pi/2), so their product keeps its FP32 accuracy.
-__device__ __forceinline__ cf utd_term(double beta, double pm, double n, float kL, cf pre, const DiffArgs& A) {
-    const double PI_D = 3.14159265358979323846;
-    const double arg = (PI_D + pm * beta) / (2.0 * n);
-    const float d = (float)(arg - PI_D * rint(arg / PI_D));
+// N = round((beta + pm pi)/(2 n pi)).  With u = pi + pm beta, K = round(u / (2 n pi)) and
+// d = u - 2 n pi K (so N = pm K): cot(u / 2n) = cot(d / 2n) and, exactly,
+// a^pm = 2 cos^2(pm (pi - d) / 2) = 2 sin^2(d / 2).  Both factors take the same d
+// (the distance to the nearest shadow boundary, reduced with a two-part 2 n pi),
+// so near a boundary, where the cotangent grows like 1/d and F like d, their
+// product keeps FP32 accuracy.  0 at an exact shadow boundary.
+__device__ __forceinline__ cf utd_term(float beta, float pm, float n, float kL, cf pre, const DiffArgs& A) {
+    const float u = PI_F + pm * beta;
+    const float twon_pi = 2.0f * n * PI_F;
+    const float K = roundf(u / twon_pi);
+    // 2 n pi = hi + lo with hi on 12 significant bits, so that K * hi is exact for |K| < 2^12
+    const float hi = __uint_as_float(__float_as_uint(twon_pi) & 0xfffff000u);
+    const float lo = (float)(2.0 * (double)n * 3.14159265358979323846 - (double)hi);
+    const float d = (u - K * hi) - K * lo;
     float sd, cd;
-    sincosf(d, &sd, &cd);
+    sincosf(d / (2.0f * n), &sd, &cd);
     if (sd == 0.0f) return C(0.0f);
-    const double N = round((beta + pm * PI_D) / (2.0 * n * PI_D));
-    const double h = 0.5 * (2.0 * n * PI_D * N - beta);
-    const double qd = rint(h / (0.5 * PI_D));
-    const float r = (float)(h - qd * (0.5 * PI_D));
-    float sr, cr;
-    sincosf(r, &sr, &cr);
-    const int q = ((int)qd) & 3;  // cos(q pi/2 + r)
-    const float c = q == 0 ? cr : (q == 1 ? -sr : (q == 2 ? -cr : sr));
-    return pre * (cd / sd) * utd_F(kL * 2.0f * c * c, A);
+    const float sh = sinf(0.5f * d);
+    return pre * (cd / sd) * utd_F(kL * 2.0f * sh * sh, A);
 }
 
 // ------------------------------------------------------------------ kernel
@@ -262,7 +260,8 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
             code = -1;
             const f3 t0 = cross(n0, e);
             // sample i: x = L (i + 1/2)/N, phi = n pi frac(i (phi_g - 1)) (24-bit fixed point)
-            const float u1 = (float)(((double)i + 0.5) / (double)A.ns);
+            const float u1 = A.ns < (1ULL << 24) ? ((float)i + 0.5f) / (float)A.ns
+                                                 : (float)(((double)i + 0.5) / (double)A.ns);
             const unsigned long long fr = i * 0x9E3779B97F4A7C16ULL;
             const float u2 = (float)(unsigned)(fr >> 40) * 0x1p-24f;
             const float x = u1 * W.length;
@@ -321,14 +320,13 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
                     const float txx = e.x + dtcx * ks.x + tc * dkx.x, txy = e.y + dtcx * ks.y + tc * dkx.y;
                     const float tpx = dtcp * ks.x + tc * dkp.x, tpy = dtcp * ks.y + tc * dkp.y;
                     const float J = fabsf(txx * tpy - txy * tpx);
-                    // UTD (Eq. diffracted-field): angles from the 0-face (double precision:
-                    // the shadow boundaries sit at fixed values of phi +- phi'), phi of the sample
+                    // UTD (Eq. diffracted-field): angles from the 0-face, phi of the sample
                     const float nw_ = W.n;
-                    const double phi = (double)u2 * (double)nw_ * 3.14159265358979323846;
+                    const float phi = u2 * nw_ * PI_F;
                     const f3 sr = s - v;
                     const f3 srt = sr - e * dot(sr, e);
-                    double phip = atan2((double)dot(srt, n0), (double)dot(srt, t0));
-                    if (phip < 0.0) phip += 2.0 * 3.14159265358979323846;
+                    float phip = atan2f(dot(srt, n0), dot(srt, t0));
+                    if (phip < 0.0f) phip += 2.0f * PI_F;
                     const float sobs = tc;
                     const float L = sobs * dn / (sobs + dn) * sb * sb;
                     const float kL = A.k0 * L;
@@ -344,7 +342,7 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
                     const MatDev& Mn = A.mats[mn];
                     const Mat2 R0 = face_matrix(n0, C(M0.eta_re, M0.eta_im), si, e, phi_i, beta_i);
                     Mat2 Rn;
-                    if (((double)nw_ - 1.0) * 3.14159265358979323846 <= phip) {
+                    if ((nw_ - 1.0f) * PI_F <= phip) {
                         Rn = face_matrix(nn, C(Mn.eta_re, Mn.eta_im), si, e, phi_i, beta_i);
                     } else {
                         Rn.m[0][0] = Rn.m[1][1] = C(-1.0f);
