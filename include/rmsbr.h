@@ -278,7 +278,7 @@ void rm_trace_plan_free(rm_trace_plan* plan);
  * The paper has no counterpart of it: it only changes where the tracer's
  * scratch lives.
  *   Scratch: one static device array of 16 KB, enough for RM_MAX_MATERIALS
- *   materials and RM_MAX_TX transmitters plus ~130 synthetic-array elements
+ *   materials and RM_MAX_TX transmitters plus 72 synthetic-array elements
  *   (32 bytes each); every GPU that loads the library holds it until the
  *   process exits.  A call that would need more is rejected with RM_EINVAL.
  *   Set-up: the first call on a device looks up the array's device address

@@ -263,6 +263,7 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
         d.seed = tx[t].seed;
         d.rec_begin = rec;
         d.perm = visit_step(tx[t], d.count);
+        d.perm_m = d.count > 0 ? ~0ULL / d.count : 0;
         d.n_ant = tx[t].n_ant;
         d.ant_begin = (int32_t)P->ant.size();
         for (int a = 0; a < tx[t].n_ant; ++a) {

@@ -47,6 +47,7 @@ struct TxDev {
     unsigned long long seed;
     unsigned long long rec_begin;   // first debug record of this transmitter
     unsigned long long perm;        // visit order: subset index i = (j * perm) mod count (1 = identity)
+    unsigned long long perm_m;      // floor((2^64 - 1) / count): Barrett reduction of j * perm mod count
     int32_t n_ant, ant_begin;       // synthetic array elements in the antenna table
 };
 

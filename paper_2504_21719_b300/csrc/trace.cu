@@ -595,7 +595,16 @@ __global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArg
                         // neighbouring work items visit neighbouring lattice directions:
                         // i = j * F mod count with F a Fibonacci number (lattice neighbour step)
                         isub = w - T.work_begin;
-                        if (T.perm > 1ULL) isub = (isub * T.perm) % T.count;
+                        if (T.perm > 1ULL) {
+                            // (isub * perm) mod count by Barrett reduction (isub, perm < count,
+                            // product < 2^63): the estimate q is at most 2 below the quotient
+                            const unsigned long long xp = isub * T.perm;
+                            const unsigned long long q = __umul64hi(xp, T.perm_m);
+                            unsigned long long rr = xp - q * T.count;
+                            if (rr >= T.count) rr -= T.count;
+                            if (rr >= T.count) rr -= T.count;
+                            isub = rr;
+                        }
                         n = T.begin + isub * T.stride;
                         // Fibonacci lattice (Sec. 3.1.1): cos theta = 1 - 2n/(N-1),
                         // sin theta = 2 sqrt(n (N-1-n)) / (N-1), phi = 2 pi frac(n (phi_g - 1))
