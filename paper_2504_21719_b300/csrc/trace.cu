@@ -390,8 +390,8 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
         // over internal nodes, whose hit leaf children are tested in their
         // parent's step.  Every triangle test goes through the single call site at
         // the bottom of the loop, which keeps the kernel's code small (the diffuse
-        // instantiations, whose longer shading otherwise crowds the instruction
-        // cache, use this form).
+        // and adjoint instantiations, whose longer shading otherwise crowds the
+        // instruction cache, use this form).
         const int npre = nlarge + (nt == 1 ? 1 : 0);
         int stack[STACK_SIZE];
         int sp = 0;
@@ -508,11 +508,12 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
 constexpr int NGRAD = 2 * RM_MAX_MATERIALS + 3 * RM_MAX_TX;
 constexpr int MAXSLOT = RM_MAX_DEPTH;
 
-// Register budgets: the forward tracer is capped at 64 registers (four
-// 256-thread blocks per SM: the extra resident warps hide more latency than
-// the few spills cost); the adjoint, whose tangents live in local memory, at 128.
+// Register budget: 64 registers (four 256-thread blocks per SM) for every
+// instantiation; the extra resident warps hide more latency (much of it
+// instruction fetch) than the spills cost, for the adjoint as well (its
+// tangents live in local memory anyway).
 template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF>
-__global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArgs A) {
+__global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
     __shared__ MatDev s_mat[RM_MAX_MATERIALS];
     __shared__ TxDev s_tx[RM_MAX_TX];
     __shared__ float s_agg[MAX_BLOCK];
@@ -684,7 +685,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArg
         // ---------------- closest hit ----------------
         Hit h{-1, 0x7fffffff, INFINITY};
         if (active) {
-            h = closest_hit<DIFF>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris, overflow);
+            h = closest_hit<DIFF || ADJ>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris, overflow);
             ++c_seg;
             if (h.slot < 0) ++c_esc;
         }
@@ -780,6 +781,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArg
             // adjoint: gather g = dL/dC at the deposit (and its spatial derivative)
             float G = 0.0f, Gx = 0.0f, Gy = 0.0f;
             if (BILIN) {
+#pragma unroll 1
                 for (int cn = 0; cn < 4; ++cn) {
                     const int a = cn & 1, b = cn >> 1;
                     const int cxi = ix + a, cyi = iy + b;
@@ -797,6 +799,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArg
             }
             const float sc = s_tx[txi].dep_scale * inv_pr / fabsf(r.kz);
             if (G != 0.0f) {
+#pragma unroll 1
                 for (int s = 0; s < nslot; ++s) {
                     cf z = C(0.0f);
                     for (int p = 0; p < NPOL; ++p)
@@ -921,6 +924,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArg
                             // sigma directions separately; d eta = 1 resp. -j on this material
                             cf drp, drl;
                             fresnel_deta(eta, cos1, M.k0d_hi + M.k0d_lo, M.slab != 0, 0, &drp, &drl);
+#pragma unroll 1
                             for (int s = 0; s < nslot; ++s) {
                                 const bool own = s == sm;
                                 for (int p = 0; p < NPOL; ++p) {
@@ -933,6 +937,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, ADJ ? 2 : 4) k_trace(const TraceArg
                             }
                         } else {
                             // existing tangents see the same interaction matrix
+#pragma unroll 1
                             for (int s = 0; s < nslot; ++s)
                                 for (int p = 0; p < NPOL; ++p) {
                                     const cf a = edot(ep, Tg[s][p]), b = edot(epi, Tg[s][p]);
