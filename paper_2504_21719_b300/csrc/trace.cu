@@ -192,6 +192,7 @@ __device__ __noinline__ float f_alpha(int alpha, float cos_i) {
 }
 __device__ __forceinline__ float powi(float x, int a) {
     float r = 1.0f;
+#pragma unroll 1
     for (int i = 0; i < a; ++i) r *= x;
     return r;
 }
@@ -636,6 +637,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                         float are = 1.0f, aim = 0.0f;
                         if (T.n_ant > 0) {
                             are = 0.0f;
+#pragma unroll 1
                             for (int a = 0; a < T.n_ant; ++a) {
                                 const AntDev el = A.ant[T.ant_begin + a];
                                 float sn, cs;
