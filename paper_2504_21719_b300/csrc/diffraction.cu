@@ -304,9 +304,14 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
                 const float vm = fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)));
                 const float eps = fmaxf(1.0f, vm) * 0x1p-16f;
                 const f3 si = d * (1.0f / dn);
-                const bool bi = segment_blocked(A, s, si, eps, dn - eps, W.tri0, W.trin, c_nodes, c_tris, overflow);
-                const bool bd = segment_blocked(A, v, ks, eps, tc, W.tri0, W.trin, c_nodes, c_tris, overflow);
-                code = (bi ? 1 : 0) | (bd ? 2 : 0);
+                // the two visibility queries through one (rolled) call site: source -> v, v -> plane
+                code = 0;
+#pragma unroll 1
+                for (int q = 0; q < 2; ++q) {
+                    const bool blk = segment_blocked(A, q ? v : s, q ? ks : si, eps, q ? tc : dn - eps, W.tri0, W.trin,
+                                                     c_nodes, c_tris, overflow);
+                    if (blk) code |= 1 << q;
+                }
                 if (code == 0) {
                     // weighting factor |dt/dx x dt/dphi| (hand-derived): with a = (v - s).e,
                     // d cb/dx = sb^2/dn, d sb/dx = -sb cb/dn, so
@@ -332,23 +337,30 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
                     const float kL = A.k0 * L;
                     const float pm = 1.0f / (2.0f * nw_ * sqrtf(2.0f * PI_F * A.k0) * sb);
                     const cf pre = C(-0.70710678118654752f * pm, 0.70710678118654752f * pm);  // -e^{-j pi/4} pm
-                    const cf D1 = utd_term(phi - phip, +1.0f, nw_, kL, pre, A);
-                    const cf D2 = utd_term(phi - phip, -1.0f, nw_, kL, pre, A);
-                    const cf D3 = utd_term(phi + phip, +1.0f, nw_, kL, pre, A);
-                    const cf D4 = utd_term(phi + phip, -1.0f, nw_, kL, pre, A);
+                    // D_1..D_4 through one rolled call site (beta = phi -+ phi', pm = +-1)
+                    cf Dq[4];
+#pragma unroll 1
+                    for (int q = 0; q < 4; ++q)
+                        Dq[q] = utd_term(q < 2 ? phi - phip : phi + phip, (q & 1) ? -1.0f : 1.0f, nw_, kL, pre, A);
                     const f3 phi_i = unit3(cross(si, e));
                     const f3 beta_i = cross(phi_i, si);
-                    const MatDev& M0 = A.mats[m0];
-                    const MatDev& Mn = A.mats[mn];
-                    const Mat2 R0 = face_matrix(n0, C(M0.eta_re, M0.eta_im), si, e, phi_i, beta_i);
+                    // R_0 and (when the n-face is lit) R_n through one call site
+                    const bool n_lit = (nw_ - 1.0f) * PI_F <= phip;
+                    Mat2 Rf[2];
+#pragma unroll 1
+                    for (int q = 0; q < (n_lit ? 2 : 1); ++q) {
+                        const MatDev& Mq = A.mats[q ? mn : m0];
+                        Rf[q] = face_matrix(q ? nn : n0, C(Mq.eta_re, Mq.eta_im), si, e, phi_i, beta_i);
+                    }
+                    const Mat2& R0 = Rf[0];
                     Mat2 Rn;
-                    if ((nw_ - 1.0f) * PI_F <= phip) {
-                        Rn = face_matrix(nn, C(Mn.eta_re, Mn.eta_im), si, e, phi_i, beta_i);
+                    if (n_lit) {
+                        Rn = Rf[1];
                     } else {
                         Rn.m[0][0] = Rn.m[1][1] = C(-1.0f);
                         Rn.m[0][1] = Rn.m[1][0] = C(0.0f);
                     }
-                    const cf a0 = D4 - D1, an = D3 - D2;
+                    const cf a0 = Dq[3] - Dq[0], an = Dq[2] - Dq[1];
                     float pw = 0.0f;
                     for (int p = 0; p < A.npol; ++p) {
                         cf E[3];
