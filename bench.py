@@ -115,9 +115,10 @@ def peaks():
         return {}
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the tracer from the committed ncu summary, if
-    the kernel source is unchanged since it was taken; else None."""
+def profiled(key: str):
+    """A figure (dram_bytes_per_launch, issue_active_pct) of the tracer from the
+    committed ncu summary, if the kernel source is unchanged since it was
+    taken; else None."""
     try:
         txt = open(PROFILE).read()
     except OSError:
@@ -133,7 +134,7 @@ def profiled_traffic():
     if vals.get("source_sha256") != h.hexdigest():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -234,12 +235,15 @@ def run_ours(args, world, rank, local):
     kavg = statistics.mean(kern_ms) / 1e3
     seg_step = statistics.mean(segs)
     achieved = SEGMENT_BYTES * seg_step / kavg / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled("dram_bytes_per_launch")
+    issue = profiled("issue_active_pct")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak if peak else 6400.0,
                 "unit": "GB/s", "frac": round(achieved / (peak if peak else 6400.0), 4),
                 "traffic": traffic, "peak_source": "measured" if peak else "fallback",
                 "algorithmic_bytes_per_segment": SEGMENT_BYTES,
-                "kernel": "k_trace (persistent forward tracer)", "kernel_ms": round(1e3 * kavg, 4)}
+                "kernel": "k_trace (persistent forward tracer)", "kernel_ms": round(1e3 * kavg, 4),
+                "issue_slots_busy_frac": None if issue is None else round(issue / 100.0, 3),
+                "binding_limit": "instruction issue (scene and maps stay in L1/L2; see profiles/)"}
 
     # end to end through the public API from pinned host memory
     e2e = None
