@@ -8,24 +8,8 @@ import numpy as np
 import pytest
 
 from synth import scenes as S
-
-C0 = 299792458.0
-EPS0 = 8.8541878128e-12
-
-
-def _cell_avg(fn, x0, y0, cell, nx, ny, order=8):
-    """Cell averages of fn(X, Y) by an order x order Gauss-Legendre rule."""
-    g, w = np.polynomial.legendre.leggauss(order)
-    W = np.outer(w, w) / 4.0
-    out = np.zeros((ny, nx))
-    for iy in range(ny):
-        for ix in range(nx):
-            xs = x0 + ix * cell + (g + 1) * cell / 2
-            ys = y0 + iy * cell + (g + 1) * cell / 2
-            X, Y = np.meshgrid(xs, ys)
-            out[iy, ix] = (W * fn(X, Y)).sum()
-    return out
-
+from closed_forms import (C0, RECIP_A, RECIP_PAIRS, cell_avg as _cell_avg, recip_params, recip_scene,
+                          reciprocity_bound, reciprocity_replicates, two_ray)
 
 # ---------------------------------------------------------------------------
 # one ray -> one deposit, exactly the estimator's term
@@ -97,34 +81,46 @@ def test_free_space_matches_friis(orc):
 # two-ray model over the ground half-space (workload 1, V-pol is pure TM)
 # ---------------------------------------------------------------------------
 def test_two_ray_ground_plane(orc):
+    """Workload 1 at N_S = 1e7 rays against the cell-averaged two-ray gain,
+    within 3 / sqrt(n_i) for every cell that n_i >= 100 rays cross."""
     sc, txs, p = S.workload(1)
     tx = txs[0]
-    tx.num_rays = 4_000_000
+    tx.num_rays = 10_000_000
     m = orc.radio_map(sc, tx, p)["map"]
-    f, ht, hr = p.freq_hz, tx.pos[2], p.map_origin[2]
-    lam = C0 / f
-    eta = 5.24 - 1j * 0.0462 / (EPS0 * 2 * math.pi * f)
-    x0 = -p.nx * p.cell_size / 2
-
-    def gain(X, Y):
-        rho2 = X ** 2 + Y ** 2
-        d1, d2 = rho2 + (ht - hr) ** 2, rho2 + (ht + hr) ** 2
-        c = (ht + hr) / np.sqrt(d2)
-        s = np.sqrt(eta - (1 - c * c))
-        r_par = (eta * c - s) / (eta * c + s)
-        return (lam / (4 * math.pi)) ** 2 * (1 / d1 + np.abs(r_par) ** 2 / d2)
-
-    def rays(X, Y):
-        rho2 = X ** 2 + Y ** 2
-        return tx.num_rays / (4 * math.pi) * ((ht - hr) / (rho2 + (ht - hr) ** 2) ** 1.5 +
-                                              (ht + hr) / (rho2 + (ht + hr) ** 2) ** 1.5)
-
-    ref = _cell_avg(gain, x0, x0, p.cell_size, p.nx, p.ny)
-    n_i = _cell_avg(rays, x0, x0, p.cell_size, p.nx, p.ny) * p.cell_size ** 2
+    ref, n_i = two_ray(tx.pos, p, tx.num_rays)
     rel = np.abs(m / ref - 1)
     ok = n_i >= 100
-    assert ok.sum() > 2000
+    assert ok.sum() > 4000
     assert np.all(rel[ok] <= 3 / np.sqrt(n_i[ok])), rel[ok].max()
+
+
+# ---------------------------------------------------------------------------
+# reciprocity: ground + one slab wall, dual-polarised isotropic TX
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("deposit", [0, 1])
+@pytest.mark.parametrize("rx", RECIP_PAIRS)
+def test_reciprocity_ground_and_wall(orc, rx, deposit):
+    """The centre cell around B with the TX at A equals the centre cell around
+    A with the TX at B.  Reciprocity of the propagation (App. A.5: Fresnel and
+    slab coefficients depend only on the incidence angle; the spreading of
+    specular paths is symmetric) makes the transfer matrix of the reversed path
+    the transpose of the forward one in the theta/phi bases (up to the sign of
+    phi-hat), so its Frobenius norm is reciprocal.  A dual-polarised isotropic
+    TX maps exactly that norm (the sum of both columns' |T C|^2, Sec. 4.5),
+    while a single V column is not polarisation-pure once ground-then-wall
+    paths mix it.  16 replicates of ~1e6 rays in each direction."""
+    sc, cell = recip_scene(), 1.0
+    vals = {}
+    for tx_pos, rx_pos in ((RECIP_A, rx), (rx, RECIP_A)):
+        v = []
+        for n, seed in reciprocity_replicates(1_000_000, 16):
+            t = S.Tx(pos=tx_pos, num_rays=n, pol=2, seed=seed)
+            v.append(orc.radio_map(sc, t, recip_params(rx_pos, cell, deposit))["map"][1, 1])
+        vals[tx_pos] = np.array(v)
+    a, b = vals[RECIP_A], vals[rx]
+    d = math.dist(RECIP_A, rx)
+    assert a.min() > 0 and b.min() > 0
+    assert abs(a.mean() - b.mean()) <= reciprocity_bound(a, b, cell, d), (a.mean(), b.mean())
 
 
 # ---------------------------------------------------------------------------
