@@ -196,7 +196,8 @@ rm_status rm_scene_set_materials(rm_scene* scene, const rm_material* mats_host, 
                                  const rm_material* sampling_host_or_null);
 
 /* Builds the LBVH on `stream`: 63-bit Morton codes of the doubled triangle
- * centroids, a stable 8-bit-digit radix sort, the Karras (HPG 2012) binary
+ * centroids (quantised with one scale for the three axes, 2^21 - 1 over the
+ * largest centroid extent), a stable 8-bit-digit radix sort, the Karras (HPG 2012) binary
  * radix tree with duplicate keys ordered by position, an exact AABB refit,
  * and the 64-byte two-child node layout.  Up to 16 triangles as large as a
  * quarter of the scene are kept out of the tree (see rm_bvh_export).  Not part of the paper (its

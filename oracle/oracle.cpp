@@ -1620,8 +1620,11 @@ int or_branch_all(const float* verts, int64_t nv, const int32_t* tris, int64_t n
 //   lo, hi   = per-triangle AABB (exact min / max of the FP32 vertices);
 //   c2       = lo + hi                    (doubled centroid);
 //   cmin/cmax= min / max of c2 over all triangles;
-//   scale_a  = 2097151 / (cmax_a - cmin_a)     (0 if the extent is 0);
-//   q_a      = min(trunc((c2_a - cmin_a) * scale_a), 2097151);
+//   e        = max_a (cmax_a - cmin_a)     (one scale for the three axes, so
+//              that the Morton order splits space isotropically: a flat city
+//              does not spend a third of its top splits on height);
+//   scale    = 2097151 / e                 (0 if e is 0);
+//   q_a      = min(trunc((c2_a - cmin_a) * scale), 2097151);
 //   key      = interleave(qx, qy, qz): bit i of qx -> bit 3i+2, qy -> 3i+1, qz -> 3i.
 // Keys are sorted stably (ties keep triangle order); equal keys are told
 // apart by their sorted position: delta(i, j) = clz64(k_i ^ k_j) if the keys
@@ -1691,11 +1694,12 @@ void or_morton(const float* verts, const int32_t* tris, int64_t nt, uint64_t* ke
                 cmin[a] = std::min(cmin[a], c2[3 * i + a]);
                 cmax[a] = std::max(cmax[a], c2[3 * i + a]);
             }
-    float scale[3];
+    float e = -INFINITY;
     for (int a = 0; a < 3; ++a) {
-        volatile float e = cmax[a] - cmin[a];
-        scale[a] = (e > 0.0f) ? (float)(2097151.0f / (float)e) : 0.0f;
+        volatile float ea = cmax[a] - cmin[a];
+        e = std::max(e, (float)ea);
     }
+    const float scale = (e > 0.0f) ? (float)(2097151.0f / e) : 0.0f;
     for (int64_t i = 0; i < nt; ++i) {
         if (large[i]) {
             keys_out[i] = ~0ULL;
@@ -1704,7 +1708,7 @@ void or_morton(const float* verts, const int32_t* tris, int64_t nt, uint64_t* ke
         uint32_t q[3];
         for (int a = 0; a < 3; ++a) {
             volatile float d = c2[3 * i + a] - cmin[a];
-            volatile float f = (float)d * scale[a];
+            volatile float f = (float)d * scale;
             uint32_t u = (uint32_t)(float)f;
             q[a] = u > 2097151u ? 2097151u : u;
         }

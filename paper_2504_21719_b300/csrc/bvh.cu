@@ -155,7 +155,9 @@ __device__ __forceinline__ uint64_t spread21(uint32_t v) {
     return x;
 }
 
-// q_a = min(trunc((c2_a - cmin_a) * (2097151 / (cmax_a - cmin_a))), 2097151)
+// One scale for the three axes, so that the Morton order splits space
+// isotropically (a flat city does not spend a third of its top splits on height):
+// e = max_a (cmax_a - cmin_a),  q_a = min(trunc((c2_a - cmin_a) * (2097151 / e)), 2097151)
 // key = interleave(qx, qy, qz) with x on bit 3i+2, y on 3i+1, z on 3i.
 __global__ void k_morton(const float* __restrict__ c2, const float* __restrict__ bounds, int64_t nt,
                          const int8_t* __restrict__ large, int use_large, uint64_t* __restrict__ keys,
@@ -167,10 +169,10 @@ __global__ void k_morton(const float* __restrict__ c2, const float* __restrict__
         keys[i] = ~0ULL;
         return;
     }
+    const float e = extent3(bounds, bounds + 3);
+    const float scale = (e > 0.0f) ? __fdiv_rn(2097151.0f, e) : 0.0f;
     uint32_t q[3];
     for (int a = 0; a < 3; ++a) {
-        const float e = __fsub_rn(bounds[3 + a], bounds[a]);
-        const float scale = (e > 0.0f) ? __fdiv_rn(2097151.0f, e) : 0.0f;
         const float f = __fmul_rn(__fsub_rn(c2[3 * i + a], bounds[a]), scale);
         const uint32_t u = __float2uint_rz(f);
         q[a] = u > 2097151u ? 2097151u : u;

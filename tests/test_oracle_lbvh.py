@@ -27,9 +27,8 @@ def _morton_numpy(scene):
     c2 = (lo + hi).astype(np.float32)
     small = c2[~large] if (~large).any() else c2
     cmin, cmax = small.min(0), small.max(0)
-    ext = (cmax - cmin).astype(np.float32)
-    with np.errstate(divide="ignore"):
-        scale = np.where(ext > 0, np.float32(2097151.0) / ext, np.float32(0)).astype(np.float32)
+    ext = (cmax - cmin).astype(np.float32).max()      # one scale for the three axes
+    scale = np.float32(2097151.0) / ext if ext > 0 else np.float32(0)
     q = ((c2 - cmin).astype(np.float32) * scale).astype(np.float32)
     qi = np.minimum(q.astype(np.uint64), np.uint64(2097151))
     keys = np.zeros(len(t), np.uint64)
