@@ -266,7 +266,8 @@ rm_status rm_trace_plan_create(const rm_scene* scene, const rm_tx* tx_host, int3
                                const rm_trace_params* params, float* maps_dev, void* stream,
                                rm_trace_plan** out);
 rm_status rm_trace_plan_launch(rm_trace_plan* plan, void* stream);
-/* Counters of the last launch (synchronises `stream`). */
+/* Counters of the last launch (synchronises `stream`); kernel_ms is the
+ * tracer node's time, from events the graph records around it. */
 rm_status rm_trace_plan_stats(rm_trace_plan* plan, void* stream, rm_stats* stats_host);
 void rm_trace_plan_free(rm_trace_plan* plan);
 

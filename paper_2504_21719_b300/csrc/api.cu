@@ -34,6 +34,8 @@ struct rm_trace_plan {
     char* dev = nullptr;
     Scratch* scratch = nullptr;
     int ntx = 0, L = 0;
+    // recorded by the graph around its tracer node: the kernel time of the last launch
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace {
@@ -696,15 +698,19 @@ rm_status rm_trace_plan_create(const rm_scene* sc, const rm_tx* tx, int32_t ntx,
     P.a.scratch = pl->scratch;
     P.a.maps = maps_dev;
     P.a.maps64 = reinterpret_cast<double*>(pl->dev + o_m64);
+    if ((e = cudaEventCreate(&pl->ev0)) != cudaSuccess || (e = cudaEventCreate(&pl->ev1)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaEventCreate"));
     cudaStream_t cap;
     if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
     cudaError_t ec = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (ec == cudaSuccess) {
         cudaError_t ek = cudaMemsetAsync(pl->dev, 0, sizeof(Scratch), cap);
         if (ek == cudaSuccess) ek = cudaMemsetAsync(P.a.maps64, 0, sizeof(double) * P.a.ncell * ntx, cap);
+        if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(pl->ev0, cap, cudaEventRecordExternal);
         int grid = 0;
         if (ek == cudaSuccess && P.a.total > 0)
             ek = launch_trace(P.a, P.npol, false, P.bilinear, false, P.diffuse, P.block, P.bps, cap, &grid);
+        if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(pl->ev1, cap, cudaEventRecordExternal);
         if (ek == cudaSuccess) ek = launch_map_to_f32(P.a.maps64, maps_dev, P.a.ncell * ntx, cap);
         ec = cudaStreamEndCapture(cap, &pl->graph);
         if (ek != cudaSuccess) ec = ek;
@@ -728,6 +734,8 @@ rm_status rm_trace_plan_stats(rm_trace_plan* pl, void* stream, rm_stats* out) {
     RM_CUDA(cudaMemcpyAsync(&h, pl->scratch, sizeof(Scratch), cudaMemcpyDeviceToHost, S(stream)));
     RM_CUDA(cudaStreamSynchronize(S(stream)));
     Prepared P;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) == cudaSuccess) P.kernel_ms = ms;
     fill_stats(h, P, out);
     if (h.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow; affected rays were dropped");
     return RM_OK;
@@ -738,6 +746,8 @@ void rm_trace_plan_free(rm_trace_plan* pl) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->dev) cudaFree(pl->dev);
+    if (pl->ev0) cudaEventDestroy(pl->ev0);
+    if (pl->ev1) cudaEventDestroy(pl->ev1);
     delete pl;
 }
 

@@ -737,6 +737,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
         const float value = dep ? s_tx[txi].dep_scale * e2 * inv_pr / fabsf(r.kz) : 0.0f;
         if (dep) ++c_dep;
         const unsigned long long mbase = (unsigned long long)txi * A.ncell;
+        float tg0 = 0.0f, tg1 = 0.0f, tg2 = 0.0f;   // adjoint: this deposit's TX-position gradient
 
         if (!ADJ) {
             // warp-aggregated FP32 atomics: lanes that hit the same cell add
@@ -823,10 +824,41 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                 // crossing x_c = o + t_c k with t_c = (z_M - o_z)/k_z: dx_c/do = I - k e_z^T / k_z
                 const float ax = r.kx / r.kz, ay = r.ky / r.kz;
                 const float v = sc * e2;
+                float tg[3];
                 for (int c = 0; c < 3; ++c) {
                     const float dx = J[3 * c + 0] - ax * J[3 * c + 2];
                     const float dy = J[3 * c + 1] - ay * J[3 * c + 2];
-                    atomicAdd(&s_grad[2 * RM_MAX_MATERIALS + 3 * txi + c], v * (Gx * dx + Gy * dy));
+                    tg[c] = v * (Gx * dx + Gy * dy);
+                }
+                tg0 = tg[0];
+                tg1 = tg[1];
+                tg2 = tg[2];
+            }
+        }
+
+        if (ADJ && BILIN) {
+            // TX-position gradient: one warp sum per transmitter and step instead
+            // of one shared atomic per deposit on the same three words (the lanes
+            // of a warp nearly always trace the same transmitter)
+            const bool c = tg0 != 0.0f || tg1 != 0.0f || tg2 != 0.0f;
+            const unsigned cm = __ballot_sync(FULL_MASK, c);
+            if (cm) {
+                const int t0 = __shfl_sync(FULL_MASK, txi, __ffs(cm) - 1);
+                if (__all_sync(FULL_MASK, !c || txi == t0)) {
+                    for (int o = 16; o > 0; o >>= 1) {
+                        tg0 += __shfl_xor_sync(FULL_MASK, tg0, o);
+                        tg1 += __shfl_xor_sync(FULL_MASK, tg1, o);
+                        tg2 += __shfl_xor_sync(FULL_MASK, tg2, o);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(&s_grad[2 * RM_MAX_MATERIALS + 3 * t0 + 0], tg0);
+                        atomicAdd(&s_grad[2 * RM_MAX_MATERIALS + 3 * t0 + 1], tg1);
+                        atomicAdd(&s_grad[2 * RM_MAX_MATERIALS + 3 * t0 + 2], tg2);
+                    }
+                } else if (c) {
+                    atomicAdd(&s_grad[2 * RM_MAX_MATERIALS + 3 * txi + 0], tg0);
+                    atomicAdd(&s_grad[2 * RM_MAX_MATERIALS + 3 * txi + 1], tg1);
+                    atomicAdd(&s_grad[2 * RM_MAX_MATERIALS + 3 * txi + 2], tg2);
                 }
             }
         }

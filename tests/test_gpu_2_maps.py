@@ -199,6 +199,7 @@ def test_graph_plan_matches_trace(api):
     torch.cuda.synchronize()
     st = plan.stats()
     assert st["rays"] == sum(t.count() for t in txs)
+    assert st["kernel_ms"] > 0.0
     mask = ref > FLOOR
     assert torch.all((out.double() - ref).abs()[mask] <= 2e-5 * ref[mask])
     plan.free()
