@@ -7,6 +7,7 @@ CASE is one of
   diffuse      the same with diffuse reflection on every material (S = 0.5)
   adjoint      adjoint of the differentiable workload (8 materials, bilinear)
   diffraction  first-order diffraction map, Manhattan, 1200 wedges
+  city         forward trace, 0.97M-triangle procedural city, 1 TX, 1e7 rays, depth 8
 Each case prints one line: case, kernel ms of the last call, and its work
 counters.
 """
@@ -24,7 +25,7 @@ def main(argv=None):
     from synth import scenes as S
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction"])
+    ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction", "city"])
     ap.add_argument("--rays", type=int, default=0, help="rays per TX (trace cases) or samples per wedge")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
@@ -34,6 +35,10 @@ def main(argv=None):
             sc = sc.with_scattering(0.5, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
             p = copy.copy(p)
             p.diffuse = True
+    elif a.case == "city":
+        sc, txs, p = S.workload(5)
+        txs = txs[:1]
+        txs[0].num_rays = 10_000_000
     else:
         sc, txs, p = S.workload(4)
     if a.rays and a.case != "diffraction":

@@ -15,6 +15,8 @@ struct rm_scene {
     int device = 0;
     int64_t nv = 0, nt = 0;
     int32_t nm = 0;
+    char* mesh_mem = nullptr;    // one allocation: verts, tris, tri_mat
+    char* bvh_mem = nullptr;     // one allocation: keys, order, nodes, trirec
     float* verts = nullptr;
     int32_t* tris = nullptr;
     int32_t* tri_mat = nullptr;
@@ -39,6 +41,8 @@ struct rm_trace_plan {
 };
 
 namespace {
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 constexpr double PI = 3.14159265358979323846;
 constexpr double C0 = 299792458.0;          // m/s
@@ -553,9 +557,12 @@ rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tri
     auto cleanup = [&](rm_status s) { rm_scene_free(sc); return s; };
     cudaError_t e;
     if (nt > 0) {
-        if ((e = cudaMalloc((void**)&sc->verts, sizeof(float) * 3 * nv)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
-        if ((e = cudaMalloc((void**)&sc->tris, sizeof(int32_t) * 3 * nt)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
-        if ((e = cudaMalloc((void**)&sc->tri_mat, sizeof(int32_t) * nt)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
+        const size_t o_t = align256(sizeof(float) * 3 * nv), o_m = o_t + align256(sizeof(int32_t) * 3 * nt);
+        if ((e = cudaMalloc((void**)&sc->mesh_mem, o_m + sizeof(int32_t) * nt)) != cudaSuccess)
+            return cleanup(cuda_fail(e, "cudaMalloc"));
+        sc->verts = reinterpret_cast<float*>(sc->mesh_mem);
+        sc->tris = reinterpret_cast<int32_t*>(sc->mesh_mem + o_t);
+        sc->tri_mat = reinterpret_cast<int32_t*>(sc->mesh_mem + o_m);
         int32_t* flag = nullptr;
         if ((e = cudaMallocAsync((void**)&flag, sizeof(int32_t), S(stream))) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocAsync"));
         int32_t hflag = 0;
@@ -598,13 +605,18 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
     if (sc->built) return fail(RM_ESTATE, "the BVH of this scene is already built");
     const int64_t n = sc->nt;
     if (n > 0) {
-        RM_CUDA(cudaMalloc((void**)&sc->keys, sizeof(uint64_t) * n));
-        RM_CUDA(cudaMalloc((void**)&sc->order, sizeof(int32_t) * n));
-        RM_CUDA(cudaMalloc((void**)&sc->nodes, sizeof(float4) * 4 * (n > 1 ? n - 1 : 1)));
-        RM_CUDA(cudaMalloc((void**)&sc->trirec, sizeof(float4) * 3 * n));
+        const size_t o_o = align256(sizeof(uint64_t) * n), o_n = o_o + align256(sizeof(int32_t) * n),
+                     o_r = o_n + align256(sizeof(float4) * 4 * (n > 1 ? n - 1 : 1));
+        RM_CUDA(cudaMalloc((void**)&sc->bvh_mem, o_r + sizeof(float4) * 3 * n));
+        sc->keys = reinterpret_cast<uint64_t*>(sc->bvh_mem);
+        sc->order = reinterpret_cast<int32_t*>(sc->bvh_mem + o_o);
+        sc->nodes = reinterpret_cast<float4*>(sc->bvh_mem + o_n);
+        sc->trirec = reinterpret_cast<float4*>(sc->bvh_mem + o_r);
         BvhBuffers B{sc->verts, sc->tris, sc->tri_mat, n, sc->keys, sc->order, sc->nodes, sc->trirec};
-        RM_CUDA(build_bvh(B, S(stream), &sc->nlarge));
+        int32_t large = 0;
+        RM_CUDA(build_bvh(B, S(stream), &large));
         RM_CUDA(cudaStreamSynchronize(S(stream)));
+        sc->nlarge = (large > 0 && large <= MAX_LARGE_TRIS) ? large : 0;
     }
     sc->built = true;
     return RM_OK;
@@ -963,13 +975,8 @@ rm_status rm_scene_info(const rm_scene* sc, int64_t* nt, int64_t* nnodes, int32_
 
 void rm_scene_free(rm_scene* sc) {
     if (!sc) return;
-    cudaFree(sc->verts);
-    cudaFree(sc->tris);
-    cudaFree(sc->tri_mat);
-    cudaFree(sc->keys);
-    cudaFree(sc->order);
-    cudaFree(sc->nodes);
-    cudaFree(sc->trirec);
+    cudaFree(sc->mesh_mem);
+    cudaFree(sc->bvh_mem);
     delete sc;
 }
 

@@ -24,7 +24,7 @@
 namespace rmsbr {
 namespace {
 
-constexpr int MAX_LARGE = 16;   // at most this many large triangles are kept out of the tree
+constexpr int MAX_LARGE = MAX_LARGE_TRIS;
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
@@ -110,7 +110,7 @@ __device__ __forceinline__ float extent3(const float* lo, const float* hi) {
 
 // Large triangles: largest AABB extent >= 0.25 x the scene's largest extent.
 // They are kept out of the tree (tested from a short list) when there are at
-// most MAX_LARGE of them; the count decides that on the host.
+// most MAX_LARGE of them; the count (in device memory) decides that.
 __global__ void k_flag_large(const float* __restrict__ aabb, const float* __restrict__ sb, int64_t nt,
                              int8_t* __restrict__ large, int32_t* __restrict__ count) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,8 +122,18 @@ __global__ void k_flag_large(const float* __restrict__ aabb, const float* __rest
 }
 
 // per-block min / max of the doubled centroids of the triangles that stay in the tree
-__global__ void k_c2_bounds(const float* __restrict__ c2, const int8_t* __restrict__ large, int use_large,
-                            int64_t nt, float* __restrict__ blk) {
+// the large-triangle list is used when 1..MAX_LARGE triangles are large (decided on the device)
+__device__ __forceinline__ bool use_large_list(const int32_t* count) {
+    const int32_t c = *count;
+    return c > 0 && c <= MAX_LARGE;
+}
+__device__ __forceinline__ int64_t tree_size(const int32_t* count, int64_t n) {
+    return use_large_list(count) ? n - *count : n;
+}
+
+__global__ void k_c2_bounds(const float* __restrict__ c2, const int8_t* __restrict__ large,
+                            const int32_t* __restrict__ count, int64_t nt, float* __restrict__ blk) {
+    const bool use_large = use_large_list(count);
     __shared__ float smin[3][256], smax[3][256];
     const int tid = threadIdx.x;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + tid;
@@ -160,10 +170,11 @@ __device__ __forceinline__ uint64_t spread21(uint32_t v) {
 // e = max_a (cmax_a - cmin_a),  q_a = min(trunc((c2_a - cmin_a) * (2097151 / e)), 2097151)
 // key = interleave(qx, qy, qz) with x on bit 3i+2, y on 3i+1, z on 3i.
 __global__ void k_morton(const float* __restrict__ c2, const float* __restrict__ bounds, int64_t nt,
-                         const int8_t* __restrict__ large, int use_large, uint64_t* __restrict__ keys,
-                         int32_t* __restrict__ vals) {
+                         const int8_t* __restrict__ large, const int32_t* __restrict__ count,
+                         uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nt) return;
+    const bool use_large = use_large_list(count);
     vals[i] = (int32_t)i;
     if (use_large && large[i]) {  // after every Morton code: the large triangles end the sorted order
         keys[i] = ~0ULL;
@@ -263,6 +274,45 @@ __global__ void k_scatter(const uint64_t* __restrict__ kin, const int32_t* __res
     }
 }
 
+// ---------------- one-block sort of small meshes ----------------
+// Bitonic sort of (key, position) pairs in shared memory: ordering by the pair
+// is the stable order by key, so the result equals the radix sort's.  One
+// launch instead of 24 for meshes of at most SMALL_SORT triangles.
+constexpr int SMALL_SORT = 2048;
+__global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int32_t* __restrict__ vals,
+                                                     int n) {
+    __shared__ uint64_t sk[SMALL_SORT];
+    __shared__ int32_t sv[SMALL_SORT];
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        sk[i] = i < n ? keys[i] : ~0ULL;
+        sv[i] = i < n ? vals[i] : INT32_MAX;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+                const int i = 2 * t - (t & (stride - 1));   // lower element of the pair
+                const int j = i + stride;
+                const bool up = (i & size) == 0;
+                const uint64_t ki = sk[i], kj = sk[j];
+                const int32_t vi = sv[i], vj = sv[j];
+                const bool gt = ki > kj || (ki == kj && vi > vj);
+                if (gt == up) {
+                    sk[i] = kj; sk[j] = ki;
+                    sv[i] = vj; sv[j] = vi;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        keys[i] = sk[i];
+        vals[i] = sv[i];
+    }
+}
+
 // ---------------- Karras hierarchy ----------------
 __device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
     if (j < 0 || j >= n) return -1;
@@ -271,8 +321,10 @@ __device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, 
     return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
 }
 
-__global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, float4* __restrict__ nodes,
-                         int32_t* __restrict__ parent_leaf, int32_t* __restrict__ parent_node) {
+__global__ void k_karras(const uint64_t* __restrict__ k, int64_t nt, const int32_t* __restrict__ count,
+                         float4* __restrict__ nodes, int32_t* __restrict__ parent_leaf,
+                         int32_t* __restrict__ parent_node) {
+    const int64_t n = tree_size(count, nt);   // the tree covers sorted positions [0, n)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) > 0 ? 1 : -1;
@@ -305,11 +357,12 @@ __global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, float4* __re
 // Bottom-up refit: each leaf writes its triangle box into its parent's
 // child slot; the second child to arrive at a node (atomic visit counter)
 // forms the node's box and carries on upward.  No thread ever waits.
-__global__ void k_refit(const float* __restrict__ tri_aabb, const int32_t* __restrict__ order, int64_t n,
-                        const int32_t* __restrict__ parent_leaf, const int32_t* __restrict__ parent_node,
-                        float4* nodes, int32_t* visit) {
+__global__ void k_refit(const float* __restrict__ tri_aabb, const int32_t* __restrict__ order, int64_t nt,
+                        const int32_t* __restrict__ count, const int32_t* __restrict__ parent_leaf,
+                        const int32_t* __restrict__ parent_node, float4* nodes, int32_t* visit) {
+    const int64_t n = tree_size(count, nt);
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    if (n < 2 || p >= n) return;
     float box[6];
     const int32_t tri = order[p];
     for (int a = 0; a < 6; ++a) box[a] = tri_aabb[6 * (int64_t)tri + a];
@@ -363,9 +416,9 @@ cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t n
     return cudaGetLastError();
 }
 
-cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int64_t* nlarge_out) {
+cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host) {
     const int64_t n = B.nt;
-    *nlarge_out = 0;
+    *nlarge_host = 0;
     if (n <= 0) return cudaSuccess;
     cudaError_t err;
     const int nblk_a = (int)nb(n, 256);
@@ -399,40 +452,41 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int64_t* nlarge_out) 
     int8_t* lg = (int8_t*)(base + o_lg);
     int32_t* cnt = (int32_t*)(base + o_cnt);
 
+    // No host round trip inside the build: the large-triangle decision and the
+    // tree size live in device memory (cnt) and every later kernel reads them.
     k_tri_aabb<<<nblk_a, 256, 0, s>>>(B.verts, B.tris, n, aabb, c2, blk);
     k_minmax_final<<<1, 256, 0, s>>>(blk, nblk_a, sb);
     if ((err = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
     k_flag_large<<<nblk_a, 256, 0, s>>>(aabb, sb, n, lg, cnt);
-    int32_t hcount = 0;
-    if ((err = cudaMemcpyAsync(&hcount, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return err;
-    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
-    const int use_large = (hcount > 0 && hcount <= MAX_LARGE) ? 1 : 0;
-    const int64_t nl = use_large ? hcount : 0;
-    const int64_t ns = n - nl;  // the tree covers sorted positions [0, ns)
-    *nlarge_out = nl;
-    k_c2_bounds<<<nblk_a, 256, 0, s>>>(c2, lg, use_large, n, blk);
+    k_c2_bounds<<<nblk_a, 256, 0, s>>>(c2, lg, cnt, n, blk);
     k_minmax_final<<<1, 256, 0, s>>>(blk, nblk_a, bnd);
-    k_morton<<<nblk_a, 256, 0, s>>>(c2, bnd, n, lg, use_large, k1, v1);
-    // 8 passes; after an even number of passes the result is back in (k1, v1)
-    for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 8 * pass;
-        uint64_t* kin = (pass & 1) ? k2 : k1;
-        uint64_t* kout = (pass & 1) ? k1 : k2;
-        int32_t* vin = (pass & 1) ? v2 : v1;
-        int32_t* vout = (pass & 1) ? v1 : v2;
-        k_hist<<<nblk_s, SORT_THREADS, 0, s>>>(kin, n, shift, hist, nblk_s);
-        k_scan<<<1, 1024, 0, s>>>(hist, (int64_t)256 * nblk_s);
-        k_scatter<<<nblk_s, SORT_THREADS, 0, s>>>(kin, vin, n, shift, hist, nblk_s, kout, vout);
+    k_morton<<<nblk_a, 256, 0, s>>>(c2, bnd, n, lg, cnt, k1, v1);
+    if (n <= SMALL_SORT) {
+        k_sort_small<<<1, 1024, 0, s>>>(k1, v1, (int)n);
+    } else {
+        // 8 passes; after an even number of passes the result is back in (k1, v1)
+        for (int pass = 0; pass < 8; ++pass) {
+            const int shift = 8 * pass;
+            uint64_t* kin = (pass & 1) ? k2 : k1;
+            uint64_t* kout = (pass & 1) ? k1 : k2;
+            int32_t* vin = (pass & 1) ? v2 : v1;
+            int32_t* vout = (pass & 1) ? v1 : v2;
+            k_hist<<<nblk_s, SORT_THREADS, 0, s>>>(kin, n, shift, hist, nblk_s);
+            k_scan<<<1, 1024, 0, s>>>(hist, (int64_t)256 * nblk_s);
+            k_scatter<<<nblk_s, SORT_THREADS, 0, s>>>(kin, vin, n, shift, hist, nblk_s, kout, vout);
+        }
     }
     if ((err = cudaMemcpyAsync(B.order, v1, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return err;
-    if (ns >= 2) {
-        k_karras<<<nb(ns - 1, 256), 256, 0, s>>>(k1, ns, B.nodes, pl, pn);
-        if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * ns, s)) != cudaSuccess) return err;
-        k_refit<<<nb(ns, 256), 256, 0, s>>>(aabb, B.order, ns, pl, pn, B.nodes, vis);
+    if (n >= 2) {
+        k_karras<<<nb(n - 1, 256), 256, 0, s>>>(k1, n, cnt, B.nodes, pl, pn);
+        if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * n, s)) != cudaSuccess) return err;
+        k_refit<<<nb(n, 256), 256, 0, s>>>(aabb, B.order, n, cnt, pl, pn, B.nodes, vis);
     }
     k_trirec<<<nb(n, 256), 256, 0, s>>>(B.verts, B.tris, B.tri_mat, B.order, n, B.trirec);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = cudaMemcpyAsync(nlarge_host, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return err;
     return cudaFreeAsync(base, s);
 }
 
