@@ -24,7 +24,9 @@
 //
 // This file is compiled with -fmad=false: every operation that steers a
 // discrete choice is rounded the same way in the forward and the adjoint
-// instantiations, so both take the same hits, decisions and cells.
+// instantiations, so both take the same hits, decisions and cells.  Division
+// and square root are the approximate (few-ulp) forms, except the slab test's
+// reciprocals.
 #include <cfloat>
 
 #include "common.cuh"
@@ -325,9 +327,11 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
     Hit h{-1, 0x7fffffff, INFINITY};
     if (nt <= 0 && nlarge <= 0) return h;
     const float ooeps = 0x1p-80f;
-    const float ix = 1.0f / (fabsf(r.kx) > ooeps ? r.kx : copysignf(ooeps, r.kx));
-    const float iy = 1.0f / (fabsf(r.ky) > ooeps ? r.ky : copysignf(ooeps, r.ky));
-    const float iz = 1.0f / (fabsf(r.kz) > ooeps ? r.kz : copysignf(ooeps, r.kz));
+    // correctly rounded reciprocals (this file builds with approximate division;
+    // the robust slab test's error bound counts one rounding here)
+    const float ix = __frcp_rn(fabsf(r.kx) > ooeps ? r.kx : copysignf(ooeps, r.kx));
+    const float iy = __frcp_rn(fabsf(r.ky) > ooeps ? r.ky : copysignf(ooeps, r.ky));
+    const float iz = __frcp_rn(fabsf(r.kz) > ooeps ? r.kz : copysignf(ooeps, r.kz));
     // watertight test set-up: kz = dominant axis, (kx, ky) keep the winding
     const float ax = fabsf(r.kx), ay = fabsf(r.ky), az = fabsf(r.kz);
     int kzi = (ay > ax) ? 1 : 0;
