@@ -23,10 +23,10 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 # trace.cu: no contraction (forward, record and adjoint instantiations round
-# every choice-steering operation alike), approximate division and square root
-# (a few ulp; the slab test's reciprocals stay correctly rounded through
-# __frcp_rn, which its robustness bound assumes)
-PER_FILE = {"trace.cu": ["-fmad=false", "-prec-div=false", "-prec-sqrt=false"], "diffraction.cu": ["-fmad=false"]}
+# every choice-steering operation alike).  Both kernels use approximate
+# division and square root (a few ulp); the slab tests' reciprocals stay
+# correctly rounded through __frcp_rn, which their robustness bound assumes.
+PER_FILE = {"trace.cu": ["-fmad=false", "-prec-div=false", "-prec-sqrt=false"], "diffraction.cu": ["-fmad=false", "-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _sources():

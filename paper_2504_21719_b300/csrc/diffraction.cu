@@ -80,9 +80,10 @@ __device__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float
     if (A.nt <= 0) return false;
     if (A.nt == 1) return tri_blocks(A.tris, 0, o, d, tmin, tmax, ex0, ex1, c_tris);
     const float ooeps = 0x1p-80f;
-    const float ix = 1.0f / (fabsf(d.x) > ooeps ? d.x : copysignf(ooeps, d.x));
-    const float iy = 1.0f / (fabsf(d.y) > ooeps ? d.y : copysignf(ooeps, d.y));
-    const float iz = 1.0f / (fabsf(d.z) > ooeps ? d.z : copysignf(ooeps, d.z));
+    // correctly rounded reciprocals: the slab test's widening assumes one rounding
+    const float ix = __frcp_rn(fabsf(d.x) > ooeps ? d.x : copysignf(ooeps, d.x));
+    const float iy = __frcp_rn(fabsf(d.y) > ooeps ? d.y : copysignf(ooeps, d.y));
+    const float iz = __frcp_rn(fabsf(d.z) > ooeps ? d.z : copysignf(ooeps, d.z));
     auto box = [&](float lx, float ly, float lz, float hx, float hy, float hz) {
         const float t0x = (lx - o.x) * ix, t1x = (hx - o.x) * ix;
         const float t0y = (ly - o.y) * iy, t1y = (hy - o.y) * iy;
