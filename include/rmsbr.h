@@ -359,6 +359,10 @@ rm_status rm_diffraction_map(const rm_scene* scene, const rm_wedge* wedges_host,
 rm_status rm_scene_info(const rm_scene* scene, int64_t* nt, int64_t* nnodes, int32_t* nm,
                         int32_t* built);
 
+/* Frees the scene's device memory (waits for the device first).  Scene memory
+ * comes from the device's default stream-ordered pool, whose release
+ * threshold the library raises to 1 GiB for this process so that repeated
+ * uploads reuse cached pages. */
 void rm_scene_free(rm_scene* scene);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */

@@ -44,6 +44,24 @@ namespace {
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Scene memory comes from the device's stream-ordered pool.  By default the
+// pool returns its unused memory to the driver at every synchronisation, so
+// the next scene would map fresh pages; keep up to 1 GiB of it cached instead
+// (a per-process setting of this device's default pool, set once).
+void keep_pool_memory() {
+    static thread_local int done_for = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev == done_for) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = 1ull << 30;
+        uint64_t cur = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < thr)
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done_for = dev;
+}
+
 constexpr double PI = 3.14159265358979323846;
 constexpr double C0 = 299792458.0;          // m/s
 constexpr double EPS0 = 8.8541878128e-12;   // F/m (CODATA 2018)
@@ -557,14 +575,15 @@ rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tri
     auto cleanup = [&](rm_status s) { rm_scene_free(sc); return s; };
     cudaError_t e;
     if (nt > 0) {
-        const size_t o_t = align256(sizeof(float) * 3 * nv), o_m = o_t + align256(sizeof(int32_t) * 3 * nt);
-        if ((e = cudaMalloc((void**)&sc->mesh_mem, o_m + sizeof(int32_t) * nt)) != cudaSuccess)
-            return cleanup(cuda_fail(e, "cudaMalloc"));
+        const size_t o_t = align256(sizeof(float) * 3 * nv), o_m = o_t + align256(sizeof(int32_t) * 3 * nt),
+                     o_f = o_m + align256(sizeof(int32_t) * nt);
+        keep_pool_memory();
+        if ((e = cudaMallocAsync((void**)&sc->mesh_mem, o_f + sizeof(int32_t), S(stream))) != cudaSuccess)
+            return cleanup(cuda_fail(e, "cudaMallocAsync"));
         sc->verts = reinterpret_cast<float*>(sc->mesh_mem);
         sc->tris = reinterpret_cast<int32_t*>(sc->mesh_mem + o_t);
         sc->tri_mat = reinterpret_cast<int32_t*>(sc->mesh_mem + o_m);
-        int32_t* flag = nullptr;
-        if ((e = cudaMallocAsync((void**)&flag, sizeof(int32_t), S(stream))) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocAsync"));
+        int32_t* flag = reinterpret_cast<int32_t*>(sc->mesh_mem + o_f);
         int32_t hflag = 0;
         do {
             if ((e = cudaMemcpyAsync(sc->verts, verts_dev, sizeof(float) * 3 * nv, cudaMemcpyDeviceToDevice, S(stream))) != cudaSuccess) break;
@@ -574,7 +593,6 @@ rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tri
             if ((e = check_indices(sc->tris, sc->tri_mat, nt, nv, nm, flag, S(stream))) != cudaSuccess) break;
             if ((e = cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, S(stream))) != cudaSuccess) break;
         } while (false);
-        cudaFreeAsync(flag, S(stream));
         cudaError_t es = cudaStreamSynchronize(S(stream));
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "rm_scene_upload"));
         if (es != cudaSuccess) return cleanup(cuda_fail(es, "cudaStreamSynchronize"));
@@ -607,7 +625,8 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
     if (n > 0) {
         const size_t o_o = align256(sizeof(uint64_t) * n), o_n = o_o + align256(sizeof(int32_t) * n),
                      o_r = o_n + align256(sizeof(float4) * 4 * (n > 1 ? n - 1 : 1));
-        RM_CUDA(cudaMalloc((void**)&sc->bvh_mem, o_r + sizeof(float4) * 3 * n));
+        keep_pool_memory();
+        RM_CUDA(cudaMallocAsync((void**)&sc->bvh_mem, o_r + sizeof(float4) * 3 * n, S(stream)));
         sc->keys = reinterpret_cast<uint64_t*>(sc->bvh_mem);
         sc->order = reinterpret_cast<int32_t*>(sc->bvh_mem + o_o);
         sc->nodes = reinterpret_cast<float4*>(sc->bvh_mem + o_n);
@@ -975,6 +994,8 @@ rm_status rm_scene_info(const rm_scene* sc, int64_t* nt, int64_t* nnodes, int32_
 
 void rm_scene_free(rm_scene* sc) {
     if (!sc) return;
+    // pool memory: wait for the device first, so that no kernel still reads it
+    if (sc->mesh_mem || sc->bvh_mem) cudaDeviceSynchronize();
     cudaFree(sc->mesh_mem);
     cudaFree(sc->bvh_mem);
     delete sc;
