@@ -351,6 +351,44 @@ def radio_map(scene, tx, params, mode: str = "plain", record=None, want_record: 
     return out
 
 
+def radio_map_mesh(scene, tx, params, surf_verts, surf_tris, mode: str = "plain", record=None,
+                   want_record: bool = False, slack: bool = False):
+    """Radio map on a mesh measurement surface: [n_surf] (float64), one cell per
+    surface triangle.  params' map geometry is unused; mode 'plain' or 'replay'
+    as in radio_map.  ``slack`` returns, per cell, the values of the crossings
+    within tol of its boundary or of a window end."""
+    v, t, m, mats = _scene_arrays(scene)
+    sv = np.ascontiguousarray(surf_verts, np.float32)
+    st_ = np.ascontiguousarray(surf_tris, np.int32)
+    otx, op = make_tx(tx), make_params(params)
+    L = int(params.max_depth)
+    cnt = tx.count()
+    rec = None
+    if mode == "replay":
+        rec = np.ascontiguousarray(record, np.int32).reshape(cnt, L + 1, 4).copy()
+    elif mode != "plain":
+        raise ValueError("mode must be 'plain' or 'replay'")
+    elif want_record:
+        rec = np.zeros((cnt, L + 1, 4), np.int32)
+    mp = np.empty(len(st_), np.float64)
+    sl = np.empty(len(st_), np.float64) if slack else None
+    rep = OrReport()
+    sc = _scat(scene)
+    rc = lib().or_radio_map_mesh(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), _p(sc), C.byref(otx),
+                                 C.byref(op), _p(sv), _p(st_), C.c_int64(len(st_)), MODES[mode], _p(rec), _p(mp), _p(sl),
+                                 C.byref(rep))
+    if rc != 0:
+        raise ValueError(f"or_radio_map_mesh failed ({rc})")
+    out = {"map": mp}
+    if want_record or mode != "plain":
+        out["record"] = rec
+    if mode == "replay":
+        out["report"] = rep.as_dict()
+    if slack:
+        out["slack"] = sl
+    return out
+
+
 def grad(scene, tx, params, record, dLdC):
     """d/d(eps_r, sigma, tx xyz) of sum(dLdC * C) with frozen choices (dual numbers)."""
     v, t, m, mats = _scene_arrays(scene)

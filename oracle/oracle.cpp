@@ -37,6 +37,7 @@
 #include <cstring>
 #include <limits>
 #include <map>
+#include <type_traits>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -554,7 +555,11 @@ struct Sink<double> {
     DepList* list;
     DepList* mass = nullptr;   // unweighted deposit value per stencil cell (bilinear error bound)
     DepList* cmass = nullptr;  // the same, times the crossing's conditioning factor
+    DepList* slack = nullptr;  // mesh surfaces: values of crossings within tol of a cell's boundary
     void add(int cell, const double& v) { list->cell.push_back(cell); list->val.push_back(v); }
+    void add_slack(int cell, double v) {
+        if (slack) { slack->cell.push_back(cell); slack->val.push_back(v); }
+    }
     void add_mass(int cell, const double& v, double cond) {
         if (mass) { mass->cell.push_back(cell); mass->val.push_back(v); }
         if (cmass) { cmass->cell.push_back(cell); cmass->val.push_back(v * cond); }
@@ -569,6 +574,7 @@ struct Sink<D> {
         for (int i = 0; i < NT; ++i) acc[i] += w * v.g[i];
     }
     void add_mass(int, const D&, double) {}
+    void add_slack(int, double) {}
 };
 
 // cond: first-order conditioning of the crossing point x_c = o + t_c k against
@@ -707,8 +713,47 @@ TxC make_txc(const or_tx& t) {
     return T;
 }
 
+// ---------------------------------------------------------------------------
+// mesh-based measurement surface (Sec. 4, practical notes): every triangle of
+// a separate mesh is one cell.  The estimator is the planar one with the
+// cell's own area A_i and unit normal n_i in the change of variables
+// dA = r^2 / |n_i . k| d omega: a crossing of triangle i adds
+//   4 pi / (N A_i) (lambda0 / 4 pi)^2 |E|^2 / (|n_i . k| Pr)
+// to cell i, for every crossing of the open segment (1e-9, t_h).  The surface
+// does not stop or deflect rays.  A crossing exactly on an edge shared by two
+// triangles counts for both (a set of measure zero).
+// ---------------------------------------------------------------------------
+struct MeshSurface {
+    std::vector<V3<double>> a, e1, e2;  // vertex a, edges b - a, c - a
+    std::vector<double> inv_area, max_edge;
+    int64_t n = 0;
+};
+MeshSurface make_surface(const float* verts, const int32_t* tris, int64_t nt) {
+    MeshSurface M;
+    M.n = nt;
+    for (int64_t i = 0; i < nt; ++i) {
+        auto v = [&](int j) {
+            const float* q = verts + 3 * (int64_t)tris[3 * i + j];
+            return V3<double>{q[0], q[1], q[2]};
+        };
+        V3<double> a = v(0), b = v(1), c = v(2);
+        V3<double> e1 = b - a, e2 = c - a;
+        V3<double> cr = cross(e1, e2);
+        double area = 0.5 * std::sqrt(dot(cr, cr));
+        M.a.push_back(a);
+        M.e1.push_back(e1);
+        M.e2.push_back(e2);
+        M.inv_area.push_back(area > 0.0 ? 1.0 / area : 0.0);
+        double le = std::max(std::sqrt(dot(e1, e1)), std::max(std::sqrt(dot(e2, e2)), std::sqrt(dot(c - b, c - b))));
+        M.max_edge.push_back(le);
+    }
+    return M;
+}
+
 struct Ctx {
     const Scene* S;
+    const MeshSurface* meas = nullptr;  // mesh measurement surface, or null for the plane
+    double Kmesh = 0.0;                 // 4 pi / N (lambda0 / 4 pi)^2
     MapGeom g;
     double omega, k0;  // angular frequency, vacuum wavenumber
     int L, flags;
@@ -871,6 +916,53 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         if (pw) { pw[l] += pwr; pw2[l] += pwr * pwr; if (prim < 0) esc[l] += pwr; }
         // ---- deposit -------------------------------------------------------
         bool los_ok = (l > 0) || (C.flags & F_LOS);
+        if constexpr (std::is_same<R, double>::value) {
+            if (C.meas) {
+                // mesh measurement surface: every crossed triangle of the open
+                // segment (1e-9, t_h); crossings within tol of a triangle's
+                // boundary or of the window ends also go to the slack of that
+                // triangle (FP32 may put them on the other side)
+                if (los_ok) {
+                    const MeshSurface& M = *C.meas;
+                    double e2v = 0.0;
+                    for (int p = 0; p < npol; ++p) e2v += cnorm2(E[p]);
+                    const double th_v = prim >= 0 ? t_h : INFINITY;
+                    for (int64_t j = 0; j < M.n; ++j) {
+                        if (M.inv_area[j] == 0.0) continue;
+                        // Moeller-Trumbore in FP64
+                        V3<double> pv = cross(k, M.e2[j]);
+                        double det = dot(M.e1[j], pv);
+                        if (det == 0.0) continue;
+                        V3<double> tv = ov - M.a[j];
+                        double u = dot(tv, pv) / det;
+                        V3<double> qv = cross(tv, M.e1[j]);
+                        double v = dot(k, qv) / det;
+                        double t = dot(M.e2[j], qv) / det;
+                        double w = 1.0 - u - v;
+                        V3<double> pc = ov + scl(k, t);
+                        double tol = tie_tol(pc, path + std::max(t, 0.0));
+                        // barycentric slack: tol over the triangle's smallest altitude
+                        double tb = tol * M.max_edge[j] * 0.5 * M.inv_area[j];
+                        bool inside = u >= 0.0 && v >= 0.0 && w >= 0.0;
+                        bool in_win = t > 1e-9 && t < th_v;
+                        bool near_edge = std::min(u, std::min(v, w)) >= -tb && std::min(u, std::min(v, w)) <= tb;
+                        bool near_win = std::fabs(t - 1e-9) <= tol || (std::isfinite(th_v) && std::fabs(t - th_v) <= tol);
+                        double nk = std::fabs(det) * 0.5 * M.inv_area[j];  // |n_i . k| = |det| / |e1 x e2|
+                        if (nk == 0.0) continue;
+                        double value = C.Kmesh * M.inv_area[j] * e2v * inv_pr / nk;
+                        if (inside && in_win) {
+                            sink.add((int)j, value);
+                            if (rs) rs->rep.deposits++;
+                        }
+                        if ((near_edge && (in_win || near_win)) || ((inside || near_edge) && near_win))
+                            sink.add_slack((int)j, value);
+                    }
+                }
+                if (rec && C.mode == MODE_PLAIN) { rec->prim = prim; rec->ix = NO_CELL; rec->iy = NO_CELL; rec->dec = -1; }
+                goto after_deposit;
+            }
+        }
+        {
         Crossing<R> cr = crossing(C.g, o, k, prim >= 0 ? val(t_h) : INFINITY);
         int dix = NO_CELL, diy = NO_CELL;
         if (cr.valid && los_ok) { dix = cr.ix; diy = cr.iy; }
@@ -934,6 +1026,8 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
             deposit(C.g, cr, dix, diy, value, sink, cond);
             if (rs) rs->rep.deposits++;
         }
+        }
+    after_deposit:
         // ---- termination ---------------------------------------------------
         if (prim < 0 || l == L) break;
         // ---- shading (Sec. 3.1.2 sampling, App. A.7 field update) ---------
@@ -1385,6 +1479,93 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
         std::memset(stats, 0, sizeof(double) * 3 * (L + 1));
         for (int t = 0; t < nthr; ++t)
             for (int j = 0; j < 3 * (L + 1); ++j) stats[j] += st[(size_t)t * 3 * (L + 1) + j];
+    }
+    if (report) {
+        std::memset(report, 0, sizeof *report);
+        bool have_fail = false;
+        for (int64_t c = 0; c < nch; ++c) {
+            const or_report& r = rss[c].rep;
+            report->segments += r.segments;
+            report->deposits += r.deposits;
+            report->adopted_hit += r.adopted_hit;
+            report->adopted_cell += r.adopted_cell;
+            report->adopted_decision += r.adopted_decision;
+            report->adopted_hit_tie += r.adopted_hit_tie;
+            report->failures += r.failures;
+            if (r.failures && !have_fail) {
+                have_fail = true;
+                report->fail_ray = r.fail_ray;
+                report->fail_depth = r.fail_depth;
+                report->fail_kind = r.fail_kind;
+                std::memcpy(report->fail_info, r.fail_info, sizeof r.fail_info);
+            }
+        }
+    }
+    return 0;
+}
+
+// Radio map on a mesh measurement surface (one cell per surface triangle) of
+// one transmitter, mode 0 plain or 1 replay (the map parameters of P other
+// than frequency, depth, flags and early termination are unused).  map_out
+// [n_surf] is overwritten; slack_out [n_surf] (or null) receives per cell the
+// sum of the values of the crossings that lie within tol of its boundary or of
+// a window end, whose cell FP32 arithmetic may decide otherwise.
+int or_radio_map_mesh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
+                      const float* mats, int nm, const float* scat, const or_tx* tx, const or_params* P,
+                      const float* surf_verts, const int32_t* surf_tris, int64_t n_surf, int mode, int32_t* rec,
+                      double* map_out, double* slack_out, or_report* report) {
+    if (P->max_depth < 0 || P->max_depth > 15) return 1;
+    if (mode != MODE_PLAIN && mode != MODE_REPLAY) return 3;
+    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm, scat);
+    if (!scat_valid(S)) return 2;
+    MeshSurface M = make_surface(surf_verts, surf_tris, n_surf);
+    Ctx C;
+    C.S = &S;
+    C.meas = &M;
+    C.g = make_geom(*P, tx->num_rays);
+    C.omega = 2.0 * PI * P->freq_hz;
+    C.k0 = C.omega / C0;
+    const double a = C0 / P->freq_hz / (4.0 * PI);
+    C.Kmesh = 4.0 * PI / (double)tx->num_rays * a * a;
+    C.L = P->max_depth;
+    C.flags = P->flags;
+    C.mode = mode;
+    std::vector<double> seps(S.eps), ssig(S.sigma);
+    C.s_eps = seps.data();
+    C.s_sig = ssig.data();
+    set_early_termination(C, *P);
+    TxC T = make_txc(*tx);
+    std::vector<Cx<double>> eta(nm);
+    std::vector<double> k0d(nm);
+    for (int m = 0; m < nm; ++m) {
+        eta[m] = permittivity(S.eps[m], S.sigma[m], C.omega);
+        k0d[m] = C.k0 * S.thick[m];
+    }
+    V3<double> pos{tx->pos[0], tx->pos[1], tx->pos[2]};
+    const int64_t cnt = subset_count(*tx);
+    const int64_t CH = 2048;
+    const int64_t nch = (cnt + CH - 1) / CH;
+    std::vector<DepList> lists(nch), slacks(nch);
+    std::vector<ReplayState> rss(nch);
+    for (auto& r : rss) std::memset(&r.rep, 0, sizeof r.rep);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < nch; ++c) {
+        Sink<double> sink{&lists[c]};
+        sink.slack = slack_out ? &slacks[c] : nullptr;
+        int64_t e = std::min(cnt, (c + 1) * CH);
+        for (int64_t i = c * CH; i < e; ++i) {
+            int64_t n = tx->ray_begin + i * tx->ray_stride;
+            trace_ray<double>(C, T, pos, eta.data(), k0d.data(), n, i, (Rec*)rec, sink,
+                              mode == MODE_REPLAY ? &rss[c] : nullptr, nullptr, nullptr, nullptr);
+        }
+    }
+    std::memset(map_out, 0, sizeof(double) * (size_t)n_surf);
+    for (int64_t c = 0; c < nch; ++c)
+        for (size_t j = 0; j < lists[c].cell.size(); ++j) map_out[lists[c].cell[j]] += lists[c].val[j];
+    if (slack_out) {
+        std::memset(slack_out, 0, sizeof(double) * (size_t)n_surf);
+        for (int64_t c = 0; c < nch; ++c)
+            for (size_t j = 0; j < slacks[c].cell.size(); ++j) slack_out[slacks[c].cell[j]] += slacks[c].val[j];
     }
     if (report) {
         std::memset(report, 0, sizeof *report);
