@@ -370,6 +370,22 @@ def run_extra(api, S, torch, gpu_name):
                           "kernel_ms": round(k, 3), "samples": dst["rays"], "wedges": wl[1],
                           "in_map": dst["segments"], "deposits": dst["deposits"],
                           "setting": "4096 samples per wedge; two visibility queries and the UTD field per sample"}
+    # the same map on a mesh measurement surface: 256 x 256 x 2 rolling-terrain triangles over the map
+    sv, st_ = S.terrain_surface(256.0, 256)
+    su = api.surface(sv, st_)
+    pm = api.params_from(p, **kw)
+    for _ in range(2):
+        api.trace_mesh(gs, su, txs, pm)
+    mk, mst = [], None
+    for _ in range(5):
+        r = api.trace_mesh(gs, su, txs, pm)
+        mk.append(r["stats"]["kernel_ms"])
+        mst = r["stats"]
+    k = statistics.mean(mk)
+    out["mesh_surface"] = {"value": round(mst["segments"] / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3),
+                           "segments": mst["segments"], "crossings": mst["deposits"], "cells": int(len(st_)),
+                           "setting": "one cell per triangle of a 131072-triangle terrain mesh over the map"}
+    su.free()
     gs.free()
     sc, txs, p = S.workload(3)
     blk, bps, qch, rfm = tuned(gpu_name, "batched")

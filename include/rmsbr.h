@@ -230,6 +230,23 @@ rm_status rm_radio_map_trace(const rm_scene* scene, const rm_tx* tx_host, int32_
                              rm_stats* stats_host_or_null, rm_segment_record* record_dev_or_null,
                              void* stream);
 
+/* Radio maps on a mesh measurement surface (Sec. 4, practical notes): every
+ * triangle of `surface` (an uploaded scene with its BVH built; its materials
+ * are unused, and it neither stops nor deflects rays) is one cell.  A crossing
+ * of triangle i by a segment (open interval (1e-9, hit distance)) adds
+ * 4 pi / (N A_i) (lambda0 / 4 pi)^2 |E|^2 / (|n_i . k| Pr): the estimator of
+ * Eq. radio-map-solver-ci-all-2-estimator with the triangle's own area A_i
+ * and unit normal n_i.  A crossing on an edge shared by two triangles counts
+ * for both.  maps_dev [ntx][surface triangles] (input triangle order) is
+ * overwritten.  params' map plane and cells are unused; deposit must be 0
+ * (box).  Forward only (no gradient).  Otherwise as rm_radio_map_trace; the
+ * record's cells are -32768.  RM_ESTATE if the surface's BVH is not
+ * built, RM_EINVAL for a NULL or empty surface or deposit != 0. */
+rm_status rm_radio_map_trace_mesh(const rm_scene* scene, const rm_scene* surface, const rm_tx* tx_host,
+                                  int32_t ntx, const rm_trace_params* params, float* maps_dev,
+                                  rm_stats* stats_host_or_null, rm_segment_record* record_dev_or_null,
+                                  void* stream);
+
 /* Vector-Jacobian product of the maps: given dL_dmaps_dev [ntx][ny][nx],
  * re-traces the same rays (same lattice, same sampler, hence the same hits,
  * decisions and cells) and accumulates

@@ -223,6 +223,34 @@ def trace(scene: Scene, txs, params, record=False, stream=None, out=None):
     return res
 
 
+def trace_mesh(scene: Scene, surface: Scene, txs, params, record=False, stream=None, out=None):
+    """Radio maps on a mesh measurement surface: [ntx, surface triangles] (float32, cuda),
+    one cell per triangle of `surface` (a Scene whose materials are unused); the counters;
+    optionally the per-segment record."""
+    lib = L.load()
+    arr, ntx = _tx_array(txs)
+    p = params if isinstance(params, L.rm_trace_params) else params_from(params)
+    maps = out if out is not None else torch.empty((ntx, surface.nt), dtype=torch.float32, device="cuda")
+    rec = None
+    if record:
+        nrec = sum(tx_count(arr[i]) for i in range(ntx)) * (p.max_depth + 1)
+        rec = torch.empty((max(nrec, 1), 4), dtype=torch.int32, device="cuda")
+    st = L.rm_stats()
+    _check(lib.rm_radio_map_trace_mesh(scene.handle, surface.handle, arr, ntx, C.byref(p), _ptr(maps), C.byref(st),
+                                       _ptr(rec), _stream(stream)), "rm_radio_map_trace_mesh")
+    res = {"maps": maps, "stats": st.as_dict()}
+    if record:
+        res["record"] = rec
+    return res
+
+
+def surface(verts, tris, device="cuda", stream=None) -> Scene:
+    """A mesh measurement surface: the triangles uploaded with their LBVH (one dummy material)."""
+    t = np.asarray(tris, np.int32).reshape(-1, 3)
+    return Scene(verts, t, np.zeros(len(t), np.int32), np.array([[1.0, 0.0, 0.0]], np.float32), device=device,
+                 stream=stream)
+
+
 def diffraction_map(scene: Scene, txs, params, samples_per_wedge: int, wedges=None, record=False, stream=None,
                     out=None):
     """First-order diffraction maps [ntx, ny, nx] (float32, cuda); add them to trace()'s maps

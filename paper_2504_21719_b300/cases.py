@@ -8,6 +8,7 @@ CASE is one of
   adjoint      adjoint of the differentiable workload (8 materials, bilinear)
   diffraction  first-order diffraction map, Manhattan, 1200 wedges
   city         forward trace, 0.97M-triangle procedural city, 1 TX, 1e7 rays, depth 8
+  mesh         the Manhattan trace on a 131072-triangle terrain measurement surface
 Each case prints one line: case, kernel ms of the last call, and its work
 counters.
 """
@@ -25,11 +26,11 @@ def main(argv=None):
     from synth import scenes as S
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction", "city"])
+    ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction", "city", "mesh"])
     ap.add_argument("--rays", type=int, default=0, help="rays per TX (trace cases) or samples per wedge")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
-    if a.case in ("manhattan", "diffuse", "diffraction"):
+    if a.case in ("manhattan", "diffuse", "diffraction", "mesh"):
         sc, txs, p = S.workload(2)
         if a.case == "diffuse":
             sc = sc.with_scattering(0.5, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
@@ -44,8 +45,11 @@ def main(argv=None):
     if a.rays and a.case != "diffraction":
         txs[0].num_rays = a.rays
     gs = api.Scene.from_obj(sc)
+    su = api.surface(*S.terrain_surface(256.0, 256)) if a.case == "mesh" else None
     for _ in range(a.reps):
-        if a.case == "diffraction":
+        if a.case == "mesh":
+            r = api.trace_mesh(gs, su, txs, p)
+        elif a.case == "diffraction":
             r = api.diffraction_map(gs, txs, p, a.rays or 4096)
         elif a.case == "adjoint":
             f = api.trace(gs, txs, p)
@@ -56,6 +60,8 @@ def main(argv=None):
     st = r["stats"]
     print(a.case, "kernel_ms", round(st["kernel_ms"], 4), "rays", st["rays"], "segments", st["segments"],
           "deposits", st["deposits"])
+    if su is not None:
+        su.free()
     gs.free()
 
 

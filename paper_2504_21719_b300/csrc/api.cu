@@ -190,6 +190,7 @@ struct Prepared {
     int block = DEFAULT_BLOCK;
     int bps = 0;
     double kernel_ms = 0.0;
+    bool mesh = false;          // maps on a mesh measurement surface
 };
 
 uint64_t gcd64(uint64_t a, uint64_t b) {
@@ -237,7 +238,7 @@ void rotation(double a, double b, double g, float* R) {
 }
 
 void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
-             const rm_material* sampling_override, Prepared* P) {
+             const rm_material* sampling_override, Prepared* P, const rm_scene* surf = nullptr) {
     const double f = p->freq_hz, omega = 2.0 * PI * f, k0 = omega / C0, lam = C0 / f;
     const std::vector<rm_material>& sm = sc->has_smats ? sc->smats : sc->mats;
     P->mats.resize(sc->nm);
@@ -278,7 +279,9 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
         rotation(tx[t].yaw, tx[t].pitch, tx[t].roll, d.R);
         d.pattern = tx[t].pattern;
         d.pol = tx[t].pol;
-        d.dep_scale = (float)(4.0 * PI / ((double)tx[t].num_rays * (double)p->cell_size * (double)p->cell_size) * a * a);
+        // planar cells: 4 pi / (N Delta^2) (lambda0 / 4 pi)^2; mesh cells divide by their own area in the kernel
+        const double cell2 = surf ? 1.0 : (double)p->cell_size * (double)p->cell_size;
+        d.dep_scale = (float)(4.0 * PI / ((double)tx[t].num_rays * cell2) * a * a);
         d.N = tx[t].num_rays;
         d.begin = tx[t].ray_begin;
         d.stride = tx[t].ray_stride;
@@ -338,6 +341,14 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
     A.qchunk = 32ULL * (unsigned long long)(p->queue_chunk > 0 ? p->queue_chunk : 1);
     A.refill_min = p->refill_min > 0 ? p->refill_min : DEFAULT_REFILL_MIN;
     A.ncell = (unsigned long long)p->nx * p->ny;
+    if (surf) {
+        A.snodes = surf->nodes;
+        A.stris = surf->trirec;
+        A.snt = (int32_t)(surf->nt - surf->nlarge);
+        A.snlarge = (int32_t)surf->nlarge;
+        A.ncell = (unsigned long long)surf->nt;
+    }
+    P->mesh = surf != nullptr;
     P->npol = tx[0].pol == 2 ? 2 : 1;
     P->bilinear = p->deposit == 1;
     P->block = p->block_size ? p->block_size : DEFAULT_BLOCK;
@@ -479,10 +490,19 @@ size_t write_tables(const Prepared& P, size_t o_mat, size_t o_tx, char* h) {
 
 rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p, float* maps,
                     const float* dLdC, float* d_eps, float* d_sig, float* d_tx, const rm_material* smats,
-                    rm_stats* stats, rm_segment_record* record, void* stream, bool adjoint) {
+                    rm_stats* stats, rm_segment_record* record, void* stream, bool adjoint,
+                    const rm_scene* surf = nullptr) {
     rm_status st = validate(sc, tx, ntx, p);
     if (st != RM_OK) return st;
     if ((st = check_device(sc)) != RM_OK) return st;
+    if (surf) {
+        if (!surf->built) return fail(RM_ESTATE, "rm_bvh_build has not been called on the surface");
+        if ((st = check_device(surf)) != RM_OK) return st;
+        if (surf->device != sc->device) return fail(RM_EINVAL, "scene and surface live on different devices");
+        if (surf->nt < 1) return fail(RM_EINVAL, "the surface has no triangles");
+        if (surf->nt > INT32_MAX) return fail(RM_EINVAL, "the surface has too many triangles");
+        if (p->deposit != 0) return fail(RM_EINVAL, "mesh surfaces take box cells (deposit = 0)");
+    }
     if (!adjoint && !maps) return fail(RM_EINVAL, "maps_dev is NULL");
     if (adjoint && !dLdC) return fail(RM_EINVAL, "dL_dmaps_dev is NULL");
     if (smats && (st = check_materials(smats, sc->nm)) != RM_OK) return st;
@@ -492,7 +512,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         return fail(RM_ESTATE, "stream is capturing; use rm_trace_plan_create for graph launches");
 
     Prepared P;
-    prepare(sc, tx, ntx, p, smats, &P);
+    prepare(sc, tx, ntx, p, smats, &P, surf);
     const bool debug = record != nullptr || (p->flags & RM_STATS);
     size_t o_mat, o_tx, o_m64 = 0;
     const size_t bytes = adjoint ? table_bytes(P, &o_mat, &o_tx) : block_bytes_with_maps64(P, &o_mat, &o_tx, &o_m64);
@@ -524,8 +544,8 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         P.a.record = record;
         if (P.a.total > 0) {
             if ((e = cudaEventRecord(ev[0], S(stream))) != cudaSuccess) break;
-            if ((e = launch_trace(P.a, P.npol, debug, P.bilinear, adjoint, P.diffuse, P.block, P.bps, S(stream), &grid)) !=
-                cudaSuccess)
+            if ((e = launch_trace(P.a, P.npol, debug, P.bilinear, adjoint, P.diffuse, P.block, P.bps, S(stream), &grid,
+                                  P.mesh)) != cudaSuccess)
                 break;
             if ((e = cudaEventRecord(ev[1], S(stream))) != cudaSuccess) break;
             timed = true;
@@ -671,6 +691,14 @@ rm_status rm_radio_map_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, c
                              float* maps_dev, rm_stats* stats, rm_segment_record* record, void* stream) {
     return run_trace(sc, tx, ntx, p, maps_dev, nullptr, nullptr, nullptr, nullptr, nullptr, stats, record, stream,
                      false);
+}
+
+rm_status rm_radio_map_trace_mesh(const rm_scene* sc, const rm_scene* surface, const rm_tx* tx, int32_t ntx,
+                                  const rm_trace_params* p, float* maps_dev, rm_stats* stats,
+                                  rm_segment_record* record, void* stream) {
+    if (!surface) return fail(RM_EINVAL, "surface is NULL");
+    return run_trace(sc, tx, ntx, p, maps_dev, nullptr, nullptr, nullptr, nullptr, nullptr, stats, record, stream,
+                     false, surface);
 }
 
 rm_status rm_radio_map_grad(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,

@@ -98,6 +98,11 @@ struct TraceArgs {
     double* maps64;              // [ntx][ny][nx] FP64 accumulation buffer (forward), or null
     const float* dLdC;           // [ntx][ny][nx] (adjoint)
     rm_segment_record* record;   // optional
+    // mesh measurement surface (forward only): its LBVH and leaf records; the
+    // maps are then [ntx][surface triangles] and the plane fields are unused
+    const float4* snodes;
+    const float4* stris;
+    int32_t snt, snlarge;
 };
 
 // First-order diffraction map (diffraction.cu).  The UTD transition function
@@ -135,8 +140,8 @@ void faddeeva_coefficients(int N, double* L, double* a);
 
 // Host-side launchers (trace.cu)
 cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, bool diffuse,
-                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out);
-int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block);
+                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out, bool mesh = false);
+int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh = false);
 
 // BVH build (bvh.cu)
 struct BvhBuffers {

@@ -509,6 +509,93 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
     return h;
 }
 
+// ------------------------------------------------------------------ mesh measurement surface
+// Crossings of the open segment (1e-9, tmax) with a mesh measurement surface
+// (Sec. 4, practical notes): every crossed triangle is a cell and receives
+// v0 / (A |n . k|), the planar estimator (Eq. radio-map-solver-ci-all-2-
+// estimator) with the triangle's own area and normal; v0 = 4 pi / N
+// (lambda0 / 4 pi)^2 |E|^2 / Pr.  With det = e1 . (k x e2) = -(e1 x e2) . k,
+// A |n . k| = |det| / 2.  Edges count on both sides (u, v >= 0, u + v <= 1).
+// Returns the number of crossings; *overflow is set if the traversal stack or
+// its step budget runs out.
+__device__ __noinline__ unsigned surface_crossings(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                                   int nt, int nlarge, float ox, float oy, float oz, float kx,
+                                                   float ky, float kz, float tmax, float v0,
+                                                   double* __restrict__ map, bool* overflow) {
+    unsigned cnt = 0;
+    const f3 o{ox, oy, oz}, k{kx, ky, kz};
+    auto leaf = [&](int slot) {
+        const float4* tp = tris + 3 * (size_t)slot;
+        const float4 r0 = __ldg(tp), r1 = __ldg(tp + 1), r2 = __ldg(tp + 2);
+        const f3 a{r0.x, r0.y, r0.z}, b{r0.w, r1.x, r1.y}, c{r1.z, r1.w, r2.x};
+        const f3 e1 = b - a, e2 = c - a;
+        const f3 pv = cross(k, e2);
+        const float det = dot(e1, pv);
+        if (det == 0.0f) return;
+        const float inv = 1.0f / det;
+        const f3 tv = o - a;
+        const float u = dot(tv, pv) * inv;
+        if (u < 0.0f || u > 1.0f) return;
+        const f3 q = cross(tv, e1);
+        const float v = dot(k, q) * inv;
+        if (v < 0.0f || u + v > 1.0f) return;
+        const float t = dot(e2, q) * inv;
+        if (!(t > 1e-9f && t < tmax)) return;
+        atomicAdd(map + __float_as_int(r2.z), (double)(2.0f * v0 / fabsf(det)));
+        ++cnt;
+    };
+#pragma unroll 1
+    for (int j = 0; j < nlarge; ++j) leaf(nt + j);
+    if (nt == 1) leaf(0);
+    if (nt < 2) return cnt;
+    const float ooeps = 0x1p-80f;
+    const float ix = __frcp_rn(fabsf(kx) > ooeps ? kx : copysignf(ooeps, kx));
+    const float iy = __frcp_rn(fabsf(ky) > ooeps ? ky : copysignf(ooeps, ky));
+    const float iz = __frcp_rn(fabsf(kz) > ooeps ? kz : copysignf(ooeps, kz));
+    auto box = [&](float lx, float ly, float lz, float hx, float hy, float hz) {
+        const float t0x = (lx - ox) * ix, t1x = (hx - ox) * ix;
+        const float t0y = (ly - oy) * iy, t1y = (hy - oy) * iy;
+        const float t0z = (lz - oz) * iz, t1z = (hz - oz) * iz;
+        const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+        const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax)) * 1.0000004f;
+        return tn <= tf;
+    };
+    int stack[STACK_SIZE];
+    int sp = 0, cur = 0;
+    long long budget = 2LL * nt + 8;
+    while (true) {
+        if (--budget < 0) {
+            *overflow = true;
+            return cnt;
+        }
+        const float4* nd = nodes + 4 * (size_t)cur;
+        const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+        bool h0 = box(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+        bool h1 = box(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+        const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+        if (h0 && c0 < 0) {
+            leaf(~c0);
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            leaf(~c1);
+            h1 = false;
+        }
+        if (h0 && h1) {
+            if (sp < STACK_SIZE) stack[sp++] = c1;
+            else *overflow = true;
+            cur = c0;
+        } else if (h0) {
+            cur = c0;
+        } else if (h1) {
+            cur = c1;
+        } else {
+            if (sp == 0) return cnt;
+            cur = stack[--sp];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 constexpr int NGRAD = 2 * RM_MAX_MATERIALS + 3 * RM_MAX_TX;
 constexpr int MAXSLOT = RM_MAX_DEPTH;
@@ -517,7 +604,7 @@ constexpr int MAXSLOT = RM_MAX_DEPTH;
 // instantiation; the extra resident warps hide more latency (much of it
 // instruction fetch) than the spills cost, for the adjoint as well (its
 // tangents live in local memory anyway).
-template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF>
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF, bool MESH>
 __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
     __shared__ MatDev s_mat[RM_MAX_MATERIALS];
     __shared__ TxDev s_tx[RM_MAX_TX];
@@ -710,7 +797,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
         bool dep = false;
         int ix = NO_CELL, iy = NO_CELL;
         float fx = 0.0f, fy = 0.0f;
-        if (active && r.kz != 0.0f && (depth > 0 || (A.flags & RM_LOS))) {
+        if (!MESH && active && r.kz != 0.0f && (depth > 0 || (A.flags & RM_LOS))) {
             const float tc = (A.zm - r.oz) / r.kz;
             if (tc > 1e-9f && tc < h.t) {
                 const float cx = r.ox + tc * r.kx, cy = r.oy + tc * r.ky;
@@ -743,7 +830,12 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
         const unsigned long long mbase = (unsigned long long)txi * A.ncell;
         float tg0 = 0.0f, tg1 = 0.0f, tg2 = 0.0f;   // adjoint: this deposit's TX-position gradient
 
-        if (!ADJ) {
+        if (MESH) {
+            // mesh measurement surface: every triangle the segment crosses
+            if (active && (depth > 0 || (A.flags & RM_LOS)))
+                c_dep += surface_crossings(A.snodes, A.stris, A.snt, A.snlarge, r.ox, r.oy, r.oz, r.kx, r.ky, r.kz,
+                                           h.t, s_tx[txi].dep_scale * e2 * inv_pr, A.maps64 + mbase, &overflow);
+        } else if (!ADJ) {
             // warp-aggregated FP32 atomics: lanes that hit the same cell add
             // their values first, then one lane issues the atomic
             const int ncorner = BILIN ? 4 : 1;
@@ -1099,9 +1191,9 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
             if (s_grad[i] != 0.0f) atomicAdd(&A.scratch->grad[i], (double)s_grad[i]);
 }
 
-template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF>
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF, bool MESH = false>
 const void* kernel_ptr() {
-    return reinterpret_cast<const void*>(&k_trace<ADJ, NPOL, DEBUG, BILIN, DIFF>);
+    return reinterpret_cast<const void*>(&k_trace<ADJ, NPOL, DEBUG, BILIN, DIFF, MESH>);
 }
 
 template <bool ADJ, int NPOL, bool DEBUG, bool BILIN>
@@ -1109,7 +1201,17 @@ const void* select_diff(bool diffuse) {
     return diffuse ? kernel_ptr<ADJ, NPOL, DEBUG, BILIN, true>() : kernel_ptr<ADJ, NPOL, DEBUG, BILIN, false>();
 }
 
-const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse) {
+const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, bool mesh) {
+    if (mesh) {
+        // mesh surfaces: forward, box cells only
+        if (adjoint || bilinear) return nullptr;
+#define RM_SELM(P, D) \
+    if (npol == P && debug == D) \
+        return diffuse ? kernel_ptr<false, P, D, false, true, true>() : kernel_ptr<false, P, D, false, false, true>();
+        RM_SELM(1, false) RM_SELM(1, true) RM_SELM(2, false) RM_SELM(2, true)
+#undef RM_SELM
+        return nullptr;
+    }
 #define RM_SEL(A, P, D, B) \
     if (adjoint == A && npol == P && debug == D && bilinear == B) return select_diff<A, P, D, B>(diffuse);
     RM_SEL(false, 1, false, false) RM_SEL(false, 1, false, true) RM_SEL(false, 1, true, false)
@@ -1124,16 +1226,16 @@ const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, boo
 
 }  // namespace
 
-int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block) {
-    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse);
+int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh) {
+    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse, mesh);
     int nb = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0) != cudaSuccess) return 0;
     return nb;
 }
 
 cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, bool diffuse,
-                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out) {
-    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse);
+                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out, bool mesh) {
+    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse, mesh);
     if (!k) return cudaErrorInvalidValue;
     if (block <= 0 || block > MAX_BLOCK || (block & 31)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, occ = 0;

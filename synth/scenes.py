@@ -279,6 +279,21 @@ def single_wall(x: float = 20.0, half_w: float = 50.0, h: float = 40.0,
     return Scene("wall", v, t, np.zeros(2, np.int32), np.array([mat], np.float32))
 
 
+def terrain_surface(half: float = 256.0, n: int = 256, z0: float = 1.5, amp: float = 0.5):
+    """A measurement surface: an n x n grid of square cells over [-half, half]^2, two
+    triangles per cell (cell (iy, ix) -> triangles 2 (iy n + ix) and the next), at the
+    rolling height z0 + amp sin(x / 9) cos(y / 7).  Returns (verts f32 [(n+1)^2, 3],
+    tris i32 [2 n^2, 3])."""
+    xs = np.linspace(-half, half, n + 1)
+    X, Y = np.meshgrid(xs, xs)
+    V = np.stack([X.ravel(), Y.ravel(), (z0 + amp * np.sin(X / 9.0) * np.cos(Y / 7.0)).ravel()], 1)
+    a = (np.arange(n)[:, None] * (n + 1) + np.arange(n)[None, :]).ravel()
+    T = np.empty((2 * n * n, 3), np.int64)
+    T[0::2] = np.stack([a, a + 1, a + n + 2], 1)
+    T[1::2] = np.stack([a, a + n + 2, a + n + 1], 1)
+    return V.astype(np.float32), T.astype(np.int32)
+
+
 def ground_and_wall(ground_half: float = 500.0, x: float = 20.0, half_w: float = 100.0,
                     h: float = 60.0, wall_mat=(4.0, 0.01, 0.0)) -> Scene:
     """Ground (material 0, triangles 0-1) plus one wall at x = const (material 1)."""

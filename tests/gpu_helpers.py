@@ -68,3 +68,28 @@ def compare_diffraction(orc, scene, tx, params, samples_per_wedge, gpu_map, gpu_
     assert np.all(err <= bound), (worst, float(rel.max()), int(mask.sum()), rep)
     assert np.all(g[~mask] <= FLOOR)
     return {"worst_rel": float(rel.max()) if rel.size else 0.0, "cells": int(mask.sum()), "report": rep}
+
+
+def compare_mesh(orc, scene, tx, params, surf_v, surf_t, gpu_map, gpu_record, rtol=MAP_RTOL,
+                 max_adopt_frac=MAX_ADOPT_FRAC):
+    """Replay the GPU's hits and decisions in the FP64 oracle on a mesh
+    measurement surface and compare cell by cell.  A crossing within tol of a
+    triangle's boundary (or of the segment's window) may land on either side in
+    FP32; the oracle's per-cell slack bounds those."""
+    L = params.max_depth
+    rec = np.asarray(gpu_record).reshape(tx.count(), L + 1, 4)
+    r = orc.radio_map_mesh(scene, tx, params, surf_v, surf_t, mode="replay", record=rec, slack=True)
+    rep = r["report"]
+    assert rep["failures"] == 0, rep
+    adopted = rep["adopted_hit"] + rep["adopted_decision"]
+    assert adopted <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
+    ref = r["map"]
+    g = np.asarray(gpu_map, np.float64).reshape(ref.shape)
+    mask = (ref > FLOOR) | (g > FLOOR)
+    err = np.abs(g - ref)[mask]
+    bound = rtol * ref[mask] + r["slack"][mask]
+    rel = err / np.maximum(ref[mask], 1e-300)
+    worst = float((err / np.maximum(bound, 1e-300)).max()) if err.size else 0.0
+    assert np.all(err <= bound), (worst, float(rel.max()), int(mask.sum()), rep)
+    assert np.all(g[~mask] <= FLOOR)
+    return {"worst_rel": float(rel.max()) if rel.size else 0.0, "cells": int(mask.sum()), "report": rep}

@@ -1,0 +1,85 @@
+"""GPU radio maps on a mesh measurement surface vs the FP64 oracle, after the
+oracle replays the GPU's hits and decisions; crossings within tol of a
+triangle's boundary are bounded by the oracle's per-cell slack."""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+from gpu_helpers import compare_mesh
+from test_oracle_mesh import grid_surface
+
+pytestmark = pytest.mark.gpu
+
+
+def terrain(n=32, half=64.0):
+    return grid_surface(-half, -half, 2 * half / n, n, n,
+                        lambda X, Y: 1.5 + 0.5 * np.sin(X / 9.0) * np.cos(Y / 7.0))
+
+
+def _run(api, sc, surf_v, surf_t, txs, p):
+    gs = api.Scene.from_obj(sc)
+    su = api.surface(surf_v, surf_t)
+    r = api.trace_mesh(gs, su, txs, p, record=True)
+    torch.cuda.synchronize()
+    out = (r["maps"].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
+    su.free()
+    gs.free()
+    return out
+
+
+@pytest.mark.parametrize("stride,begin", [(997, 0), (1009, 5)])
+def test_mesh_parity_manhattan(orc, api, stride, begin):
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    tx.ray_stride, tx.ray_begin = stride, begin
+    V, T = terrain()
+    m, rec, st = _run(api, sc, V, T, [tx], p)
+    assert st["rays"] == tx.count() and st["deposits"] > 1000
+    info = compare_mesh(orc, sc, tx, p, V, T, m[0], rec)
+    assert info["cells"] > 1000
+
+
+def test_mesh_parity_diffuse_dual_pol(orc, api):
+    sc, txs, p = S.workload(2)
+    sc = sc.with_scattering(0.5, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
+    p = copy.copy(p)
+    p.diffuse = True
+    tx = txs[0]
+    tx.ray_stride, tx.pol = 1499, 2
+    V, T = terrain(24, 80.0)
+    m, rec, st = _run(api, sc, V, T, [tx], p)
+    info = compare_mesh(orc, sc, tx, p, V, T, m[0], rec)
+    assert info["cells"] > 500
+
+
+def test_mesh_batched_equals_single(api):
+    sc, _, p = S.workload(2)
+    txs = [S.Tx(pos=pos, num_rays=n, seed=i) for i, (pos, n) in
+           enumerate((((0.0, 0.0, 30.0), 200_000), ((40.0, -30.0, 25.0), 150_000), ((-60.0, 20.0, 35.0), 250_000)))]
+    V, T = terrain(40, 120.0)
+    gs = api.Scene.from_obj(sc)
+    su = api.surface(V, T)
+    both = api.trace_mesh(gs, su, txs, p)["maps"].double()
+    for i, t in enumerate(txs):
+        one = api.trace_mesh(gs, su, [t], p)["maps"][0].double()
+        mask = one > 1e-15
+        assert mask.sum() > 100
+        assert torch.all((both[i] - one).abs()[mask] <= 2e-5 * one[mask])
+    su.free()
+    gs.free()
+
+
+def test_mesh_rejects_bilinear(api):
+    sc, txs, p = S.workload(1)
+    V, T = terrain(4, 10.0)
+    gs = api.Scene.from_obj(sc)
+    su = api.surface(V, T)
+    q = copy.copy(p)
+    q.deposit = 1
+    with pytest.raises(RuntimeError, match="box cells"):
+        api.trace_mesh(gs, su, txs, q)
+    su.free()
+    gs.free()
