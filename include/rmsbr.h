@@ -9,9 +9,12 @@
  * thin slabs with the radio-material model (App. A.7, Eqs. fresnel_vac,
  * fresnel_slab), choosing one interaction per hit with the Fresnel-power
  * heuristic (Eq. path-solver-used-dist-event), and deposit path gain into the
- * cells of a horizontal measurement plane wherever they cross it
- * (Eq. radio-map-solver-ci-all-2-estimator, n_S = 0, with the squared ray-tube
- * length cancelled by the 1/r spreading of Eq. radio-map-solver-path-gain).
+ * cells of a horizontal measurement plane (or the triangles of a measurement
+ * mesh) wherever they cross it (Eq. radio-map-solver-ci-all-2-estimator,
+ * n_S = 0, with the squared ray-tube length cancelled by the 1/r spreading of
+ * Eq. radio-map-solver-path-gain).  Diffuse reflection (App. A.10), synthetic
+ * arrays, early termination (Sec. 4) and the first-order diffraction map
+ * (Sec. 4, App. A.8) extend it.
  *
  * Conventions shared by every call:
  *  - Pointers named *_dev are CUDA device memory owned by the CALLER; pointers
