@@ -5,6 +5,11 @@ residue: rank r of W traces subset items i = r, r + W, r + 2W, ...  Each
 rank's maps carry the full solid-angle weight 4 pi / N_S, so the maps of all
 ranks add up to the map of the whole subset; one sum all-reduce of the maps
 (the only collective) finishes the job.  The scene is replicated.
+
+The adjoint shards the same way: the gradient of sum_i g_i C_i is linear in
+the rays, so each rank differentiates its share with the same dL/dC (broadcast
+from rank 0) and one sum all-reduce of the 2 nm + 3 ntx gradient values
+finishes it.
 """
 from __future__ import annotations
 
@@ -55,3 +60,29 @@ def sharded_trace(scene, txs, params, group=None):
     r = api.trace(scene, mine, params)
     allreduce_maps(r["maps"], group)
     return r
+
+
+def allreduce_grads(grads, group=None):
+    """Sum the gradient tensors (dict of d_eps, d_sigma, d_tx) of all ranks in place."""
+    import torch
+    import torch.distributed as dist
+    flat = torch.cat([grads["d_eps"].reshape(-1), grads["d_sigma"].reshape(-1), grads["d_tx"].reshape(-1)])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    a, b = grads["d_eps"].numel(), grads["d_sigma"].numel()
+    grads["d_eps"].copy_(flat[:a].view_as(grads["d_eps"]))
+    grads["d_sigma"].copy_(flat[a:a + b].view_as(grads["d_sigma"]))
+    grads["d_tx"].copy_(flat[a + b:].view_as(grads["d_tx"]))
+    return grads
+
+
+def sharded_grad(scene, txs, params, dLdC, group=None, src=0):
+    """Differentiate this rank's share of every transmitter with dL/dC
+    broadcast from rank `src`, and all-reduce the gradients."""
+    import torch.distributed as dist
+
+    from . import api
+    dist.broadcast(dLdC, src=src, group=group)
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    mine = [partition_tx(api.tx_from(t) if not hasattr(t, "_fields_") else t, rank, world) for t in txs]
+    g = api.grad(scene, mine, params, dLdC)
+    return allreduce_grads(g, group)

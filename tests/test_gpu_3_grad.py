@@ -140,3 +140,25 @@ def test_autograd_function(api):
     assert torch.allclose(eps.grad.float().cuda(), ref["d_eps"], rtol=1e-5, atol=0)
     assert torch.allclose(pos.grad.float().cuda(), ref["d_tx"], rtol=1e-5, atol=0)
     gs.free()
+
+
+def test_partition_gradients_sum_to_full(api):
+    """The adjoint is linear in the rays: the gradients of the lattice shares
+    of three ranks (the sharded adjoint's partition) add up to the gradient of
+    the whole subset, to the order of FP32 atomic additions."""
+    from paper_2504_21719_b300.shard import partition_tx
+    sc, tx, p = _setup(stride=7)
+    gs = api.Scene.from_obj(sc)
+    tgt = _target(api, sc, tx, p)
+    f = api.trace(gs, [tx], p)
+    _, dLdC, _ = api.db_mse_loss(f["maps"][0], tgt)
+    g = dLdC.view(1, p.ny, p.nx)
+    full = api.grad(gs, [tx], p, g)
+    parts = [api.grad(gs, [partition_tx(tx, r, 3)], p, g) for r in range(3)]
+    for key in ("d_eps", "d_sigma", "d_tx"):
+        a = full[key].double()
+        b = sum(q[key].double() for q in parts)
+        scale = a.abs().max().item()
+        assert scale > 0
+        assert torch.all((a - b).abs() <= 1e-4 * scale), (key, a, b)
+    gs.free()
