@@ -22,7 +22,17 @@
 //     sampling) that gives the estimator's exact expectation on tiny scenes;
 //   * forward-mode dual numbers for the gradient with frozen discrete choices;
 //   * a reference LBVH (Morton codes + stable sort + top-down binary radix
-//     tree) that the GPU tree must equal bit for bit.
+//     tree) that the GPU tree must equal bit for bit;
+//   * diffuse reflection (App. A.10: S / R split of the sampling, the
+//     scattered field with cross-polarisation, Lambertian / directive /
+//     backscattering patterns);
+//   * early termination by Russian roulette and gain thresholding (Sec. 4);
+//   * synthetic transmit arrays with precoding (Sec. 4);
+//   * the first-order diffraction map (Sec. 4, UTD of App. A.8, the weighting
+//     factor by dual numbers) with the Fresnel transition function by a
+//     Gauss-Legendre integral;
+//   * radio maps on a mesh measurement surface (Sec. 4, practical notes) by
+//     brute force over the surface's triangles.
 //
 // Readings of points the paper leaves open are stated where they are used.
 //
