@@ -270,9 +270,9 @@ __device__ __forceinline__ void diffuse_tangent(const Diffuse& D, const cf* E, c
 }
 
 // Direction, pattern value, bases and random phases of one diffuse event.
-__device__ __noinline__ void diffuse_setup(const MatDev& M, f3 k, f3 nrm, float cos1, cf rp, cf rl, f3 ep, f3 epi,
-                                           unsigned long long seed, unsigned long long n, int depth, Diffuse* D,
-                                           f3* ko_out) {
+__device__ __forceinline__ void diffuse_setup_body(const MatDev& M, f3 k, f3 nrm, float cos1, cf rp, cf rl, f3 ep,
+                                                   f3 epi, unsigned long long seed, unsigned long long n, int depth,
+                                                   Diffuse* D, f3* ko_out) {
     const f3 ko = diffuse_dir(nrm, rng_u(seed ^ DIFF_STREAM0, n, depth), rng_u(seed ^ DIFF_STREAM1, n, depth));
     const float fs = scat_pattern(M, k, ko, nrm, cos1, dot(ko, nrm));
     D->ep = ep;
@@ -290,6 +290,26 @@ __device__ __noinline__ void diffuse_setup(const MatDev& M, f3 k, f3 nrm, float 
     D->sqk = M.sqk;
     D->sq1k = M.sq1k;
     *ko_out = ko;
+}
+// out of line, for the adjoint (which differentiates through D)
+__device__ __noinline__ void diffuse_setup(const MatDev& M, f3 k, f3 nrm, float cos1, cf rp, cf rl, f3 ep, f3 epi,
+                                           unsigned long long seed, unsigned long long n, int depth, Diffuse* D,
+                                           f3* ko_out) {
+    diffuse_setup_body(M, k, nrm, cos1, rp, rl, ep, epi, seed, n, depth, D, ko_out);
+}
+// the forward's whole diffuse event out of line: D stays in this function's
+// registers and only the field goes through memory
+template <int NPOL>
+__device__ __noinline__ void diffuse_event(const MatDev& M, f3 k, f3 nrm, float cos1, cf rp, cf rl, f3 ep, f3 epi,
+                                           unsigned long long seed, unsigned long long n, int depth, cf (*E)[3],
+                                           f3* ko_out) {
+    Diffuse D;
+    diffuse_setup_body(M, k, nrm, cos1, rp, rl, ep, epi, seed, n, depth, &D, ko_out);
+    for (int p = 0; p < NPOL; ++p) {
+        cf eo[3];
+        diffuse_field(D, E[p], eo);
+        for (int a = 0; a < 3; ++a) E[p][a] = eo[a];
+    }
 }
 
 // ------------------------------------------------------------------ traversal
@@ -998,7 +1018,10 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                         // diffuse reflection: a new tube in a uniform direction of the
                         // incident-side hemisphere (App. A.10); set up out of line to keep
                         // the loop body small
-                        diffuse_setup(M, k, nrm, cos1, co.rp, co.rl, ep, epi, s_tx[txi].seed, n, depth, &D, &ko);
+                        if (ADJ)
+                            diffuse_setup(M, k, nrm, cos1, co.rp, co.rl, ep, epi, s_tx[txi].seed, n, depth, &D, &ko);
+                        else
+                            diffuse_event<NPOL>(M, k, nrm, cos1, co.rp, co.rl, ep, epi, s_tx[txi].seed, n, depth, E, &ko);
                         epo = epi;
                         cpe = cpa = C(0.0f);
                     } else if (dec == 0) {
@@ -1093,10 +1116,13 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                         }
                     }
                     if (DIFF && dec == 2) {
-                        for (int p = 0; p < NPOL; ++p) {
-                            cf eo[3];
-                            diffuse_field(D, E[p], eo);
-                            for (int a = 0; a < 3; ++a) E[p][a] = eo[a];
+                        // (the forward updated E in diffuse_event)
+                        if (ADJ) {
+                            for (int p = 0; p < NPOL; ++p) {
+                                cf eo[3];
+                                diffuse_field(D, E[p], eo);
+                                for (int a = 0; a < 3; ++a) E[p][a] = eo[a];
+                            }
                         }
                     } else {
                         for (int p = 0; p < NPOL; ++p) {
