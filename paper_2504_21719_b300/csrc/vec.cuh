@@ -25,7 +25,7 @@ __device__ __forceinline__ cf cjmul(cf a, cf b) { return {a.r * b.r + a.i * b.i,
 // smaller part formed as y / (2 * larger) (Kahan 1987) to avoid cancellation
 __device__ __forceinline__ cf csqrt_p(cf z) {
     if (z.r == 0.0f && z.i == 0.0f) return {0.0f, 0.0f};
-    const float m = hypotf(z.r, z.i);
+    const float m = sqrtf(z.r * z.r + z.i * z.i);   // |eta| << 1e19: no overflow
     if (z.r >= 0.0f) {
         const float a = sqrtf(0.5f * (m + z.r));
         return {a, z.i / (2.0f * a)};
@@ -36,8 +36,10 @@ __device__ __forceinline__ cf csqrt_p(cf z) {
 // exp(-j w) = exp(Im w) (cos Re w - j sin Re w)
 __device__ __forceinline__ cf cexp_mj(cf w) {
     float s, c;
-    sincosf(w.r, &s, &c);
-    const float e = expf(w.i);
+    // reduction by multiples of pi is exact in sincospif; the one rounding of
+    // w / pi is below the rounding of w itself
+    sincospif(w.r * 0.318309886183790672f, &s, &c);
+    const float e = __expf(w.i);
     return {e * c, -e * s};
 }
 
