@@ -147,10 +147,12 @@ __device__ void antenna_field(const TxDev& T, const AntDev* __restrict__ ant, fl
     float are = 1.0f, aim = 0.0f;
     if (T.n_ant > 0) {
         are = 0.0f;
+        // phase k0 k.d as a multiple of pi: sincospif reduces exactly
+        const float k0pi = k0 * 0.318309886183790672f;
         for (int a = 0; a < T.n_ant; ++a) {
             const AntDev el = ant[T.ant_begin + a];
             float sn, cs;
-            sincosf(k0 * (k.x * el.dx + k.y * el.dy + k.z * el.dz), &sn, &cs);
+            sincospif(k0pi * (k.x * el.dx + k.y * el.dy + k.z * el.dz), &sn, &cs);
             are += el.pre * cs - el.pim * sn;
             aim += el.pre * sn + el.pim * cs;
         }

@@ -747,11 +747,13 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                         float are = 1.0f, aim = 0.0f;
                         if (T.n_ant > 0) {
                             are = 0.0f;
+                            // phase k0 k.d as a multiple of pi: sincospif reduces exactly
+                            const float k0pi = A.k0 * 0.318309886183790672f;
 #pragma unroll 1
                             for (int a = 0; a < T.n_ant; ++a) {
                                 const AntDev el = A.ant[T.ant_begin + a];
                                 float sn, cs;
-                                sincosf(A.k0 * (r.kx * el.dx + r.ky * el.dy + r.kz * el.dz), &sn, &cs);
+                                sincospif(k0pi * (r.kx * el.dx + r.ky * el.dy + r.kz * el.dz), &sn, &cs);
                                 are += el.pre * cs - el.pim * sn;
                                 aim += el.pre * sn + el.pim * cs;
                             }
