@@ -94,7 +94,7 @@ __device__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float
     };
     int stack[STACK_SIZE];
     int sp = 0, cur = 0;
-    long long budget = 2LL * A.nt + 8;
+    int budget = 2 * A.nt + 8;   // nt <= INT32_MAX / 4 (checked at upload): no overflow
     while (true) {
         if (--budget < 0) {
             overflow = true;

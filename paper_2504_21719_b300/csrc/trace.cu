@@ -424,7 +424,7 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
         int j = 0;
         bool trav = nt > 1;
         // a valid tree has nt - 1 internal nodes, each visited at most once
-        long long budget = 2LL * nt + 8;
+        int budget = 2 * nt + 8;   // nt <= INT32_MAX / 4 (checked at upload): no overflow
         while (true) {
             int la = -1, lb = -1;
             if (j < npre) {
@@ -489,7 +489,7 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
         int sp = 0;
         int cur = 0;
         // a valid tree has nt - 1 internal nodes, each visited at most once
-        long long budget = 2LL * nt + 8;
+        int budget = 2 * nt + 8;   // nt <= INT32_MAX / 4 (checked at upload): no overflow
         while (true) {
             if (--budget < 0) {
                 overflow = true;
@@ -582,7 +582,7 @@ __device__ __noinline__ unsigned surface_crossings(const float4* __restrict__ no
     };
     int stack[STACK_SIZE];
     int sp = 0, cur = 0;
-    long long budget = 2LL * nt + 8;
+    int budget = 2 * nt + 8;   // nt <= INT32_MAX / 4 (checked at upload): no overflow
     while (true) {
         if (--budget < 0) {
             *overflow = true;
