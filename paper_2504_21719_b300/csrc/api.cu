@@ -646,6 +646,11 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
         const size_t o_o = align256(sizeof(uint64_t) * n), o_n = o_o + align256(sizeof(int32_t) * n),
                      o_r = o_n + align256(sizeof(float4) * 4 * (n > 1 ? n - 1 : 1));
         keep_pool_memory();
+        if (sc->bvh_mem) {  // left by a build that failed: reuse nothing of it
+            RM_CUDA(cudaStreamSynchronize(S(stream)));
+            cudaFree(sc->bvh_mem);
+            sc->bvh_mem = nullptr;
+        }
         RM_CUDA(cudaMallocAsync((void**)&sc->bvh_mem, o_r + sizeof(float4) * 3 * n, S(stream)));
         sc->keys = reinterpret_cast<uint64_t*>(sc->bvh_mem);
         sc->order = reinterpret_cast<int32_t*>(sc->bvh_mem + o_o);

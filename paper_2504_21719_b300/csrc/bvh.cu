@@ -436,6 +436,8 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host)
                  o_lg = take(sizeof(int8_t) * n), o_cnt = take(sizeof(int32_t));
     char* base = nullptr;
     if ((err = cudaMallocAsync((void**)&base, off, s)) != cudaSuccess) return err;
+    // every later error still returns the scratch block to the pool
+    auto fail_free = [&](cudaError_t e) { cudaFreeAsync(base, s); return e; };
     float* aabb = (float*)(base + o_aabb);
     float* c2 = (float*)(base + o_c2);
     float* blk = (float*)(base + o_blk);
@@ -456,7 +458,7 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host)
     // tree size live in device memory (cnt) and every later kernel reads them.
     k_tri_aabb<<<nblk_a, 256, 0, s>>>(B.verts, B.tris, n, aabb, c2, blk);
     k_minmax_final<<<1, 256, 0, s>>>(blk, nblk_a, sb);
-    if ((err = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s)) != cudaSuccess) return fail_free(err);
     k_flag_large<<<nblk_a, 256, 0, s>>>(aabb, sb, n, lg, cnt);
     k_c2_bounds<<<nblk_a, 256, 0, s>>>(c2, lg, cnt, n, blk);
     k_minmax_final<<<1, 256, 0, s>>>(blk, nblk_a, bnd);
@@ -477,16 +479,16 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host)
         }
     }
     if ((err = cudaMemcpyAsync(B.order, v1, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return err;
+        return fail_free(err);
     if (n >= 2) {
         k_karras<<<nb(n - 1, 256), 256, 0, s>>>(k1, n, cnt, B.nodes, pl, pn);
-        if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * n, s)) != cudaSuccess) return err;
+        if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * n, s)) != cudaSuccess) return fail_free(err);
         k_refit<<<nb(n, 256), 256, 0, s>>>(aabb, B.order, n, cnt, pl, pn, B.nodes, vis);
     }
     k_trirec<<<nb(n, 256), 256, 0, s>>>(B.verts, B.tris, B.tri_mat, B.order, n, B.trirec);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = cudaGetLastError()) != cudaSuccess) return fail_free(err);
     if ((err = cudaMemcpyAsync(nlarge_host, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return err;
+        return fail_free(err);
     return cudaFreeAsync(base, s);
 }
 
