@@ -389,6 +389,27 @@ def radio_map_mesh(scene, tx, params, surf_verts, surf_tris, mode: str = "plain"
     return out
 
 
+def grad_mesh(scene, tx, params, surf_verts, surf_tris, record, dLdC):
+    """d/d(eps_r, sigma, tx xyz) of sum(dLdC * C) for a map on a mesh measurement
+    surface (dLdC [n_surf]), along the record's frozen hits and decisions."""
+    v, t, m, mats = _scene_arrays(scene)
+    sv = np.ascontiguousarray(surf_verts, np.float32)
+    st_ = np.ascontiguousarray(surf_tris, np.int32)
+    otx, op = make_tx(tx), make_params(params)
+    rec = np.ascontiguousarray(record, np.int32)
+    g = np.ascontiguousarray(dLdC, np.float64).reshape(-1)
+    if len(g) != len(st_):
+        raise ValueError("dLdC must have one value per surface triangle")
+    nm = len(mats)
+    out = np.empty(2 * nm + 3, np.float64)
+    sc = _scat(scene)
+    rc = lib().or_grad_mesh(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), nm, _p(sc), C.byref(otx), C.byref(op),
+                            _p(sv), _p(st_), C.c_int64(len(st_)), _p(rec), _p(g), _p(out))
+    if rc != 0:
+        raise ValueError(f"or_grad_mesh failed ({rc}): at most 8 materials, valid scattering parameters")
+    return out[:nm].copy(), out[nm:2 * nm].copy(), out[2 * nm:].copy()
+
+
 def grad(scene, tx, params, record, dLdC):
     """d/d(eps_r, sigma, tx xyz) of sum(dLdC * C) with frozen choices (dual numbers)."""
     v, t, m, mats = _scene_arrays(scene)

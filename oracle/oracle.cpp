@@ -926,7 +926,7 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         if (pw) { pw[l] += pwr; pw2[l] += pwr * pwr; if (prim < 0) esc[l] += pwr; }
         // ---- deposit -------------------------------------------------------
         bool los_ok = (l > 0) || (C.flags & F_LOS);
-        if constexpr (std::is_same<R, double>::value) {
+        {
             if (C.meas) {
                 // mesh measurement surface: every crossed triangle of the open
                 // segment (1e-9, t_h); crossings within tol of a triangle's
@@ -934,9 +934,10 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
                 // triangle (FP32 may put them on the other side)
                 if (los_ok) {
                     const MeshSurface& M = *C.meas;
-                    double e2v = 0.0;
-                    for (int p = 0; p < npol; ++p) e2v += cnorm2(E[p]);
-                    const double th_v = prim >= 0 ? t_h : INFINITY;
+                    R e2r(0.0);
+                    for (int p = 0; p < npol; ++p) e2r = e2r + cnorm2(E[p]);
+                    const double e2v = val(e2r);
+                    const double th_v = prim >= 0 ? val(t_h) : INFINITY;
                     for (int64_t j = 0; j < M.n; ++j) {
                         if (M.inv_area[j] == 0.0) continue;
                         // Moeller-Trumbore in FP64
@@ -959,9 +960,10 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
                         bool near_win = std::fabs(t - 1e-9) <= tol || (std::isfinite(th_v) && std::fabs(t - th_v) <= tol);
                         double nk = std::fabs(det) * 0.5 * M.inv_area[j];  // |n_i . k| = |det| / |e1 x e2|
                         if (nk == 0.0) continue;
-                        double value = C.Kmesh * M.inv_area[j] * e2v * inv_pr / nk;
+                        const double scale = C.Kmesh * M.inv_area[j] * inv_pr / nk;
+                        const double value = e2v * scale;
                         if (inside && in_win) {
-                            sink.add((int)j, value);
+                            sink.add((int)j, e2r * scale);
                             if (rs) rs->rep.deposits++;
                         }
                         if ((near_edge && (in_win || near_win)) || ((inside || near_edge) && near_win))
@@ -1605,14 +1607,19 @@ int or_radio_map_mesh(const float* verts, int64_t nv, const int32_t* tris, int64
 // m < nm, tx position), with hits, cells and decisions frozen to rec (from a
 // plain run) and the sampling probabilities detached.  Forward-mode dual
 // numbers; nm <= 8.  grad_out: [nm] d/deps, [nm] d/dsigma, [3] d/dtx.
-int or_grad(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
-            const float* mats, int nm, const float* scat, const or_tx* tx, const or_params* P,
-            const int32_t* rec, const double* dLdC, double* grad_out) {
+static int grad_impl(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
+                     const float* mats, int nm, const float* scat, const or_tx* tx, const or_params* P,
+                     const int32_t* rec, const double* dLdC, double* grad_out, const MeshSurface* meas) {
     if (nm > 8) return 1;
     Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm, scat);
     if (!scat_valid(S)) return 2;
     Ctx C;
     C.S = &S;
+    C.meas = meas;
+    if (meas) {
+        const double a = C0 / P->freq_hz / (4.0 * PI);
+        C.Kmesh = 4.0 * PI / (double)tx->num_rays * a * a;
+    }
     C.g = make_geom(*P, tx->num_rays);
     C.omega = 2.0 * PI * P->freq_hz;
     C.k0 = C.omega / C0;
@@ -1664,6 +1671,23 @@ int or_grad(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, con
     for (int m = 0; m < nm; ++m) { grad_out[m] = g[m]; grad_out[nm + m] = g[8 + m]; }
     for (int j = 0; j < 3; ++j) grad_out[2 * nm + j] = g[16 + j];
     return 0;
+}
+
+int or_grad(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
+            const float* mats, int nm, const float* scat, const or_tx* tx, const or_params* P,
+            const int32_t* rec, const double* dLdC, double* grad_out) {
+    return grad_impl(verts, nv, tris, nt, tri_mat, mats, nm, scat, tx, P, rec, dLdC, grad_out, nullptr);
+}
+
+// The same gradient for a map on a mesh measurement surface: dLdC [n_surf];
+// crossings are recomputed along the frozen path (they do not depend on the
+// materials; the cells are boxes, so the TX-position gradient is zero).
+int or_grad_mesh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
+                 const float* mats, int nm, const float* scat, const or_tx* tx, const or_params* P,
+                 const float* surf_verts, const int32_t* surf_tris, int64_t n_surf, const int32_t* rec,
+                 const double* dLdC, double* grad_out) {
+    MeshSurface M = make_surface(surf_verts, surf_tris, n_surf);
+    return grad_impl(verts, nv, tris, nt, tri_mat, mats, nm, scat, tx, P, rec, dLdC, grad_out, &M);
 }
 
 // ---------------------------------------------------------------------------

@@ -136,3 +136,30 @@ def test_mesh_replay_of_own_record_and_slack(orc):
     hit = np.flatnonzero(r["map"] > 0)
     assert len(hit) >= 2                                   # every triangle sharing the vertex
     assert np.all(r["slack"][hit] >= r["map"][hit])
+
+
+def test_mesh_gradient_equals_planar_gradient(orc):
+    """Dual-number gradient on a flat mesh that tiles the planar cells, with
+    each triangle weighted by half its cell's dL/dC: sum_i g_i C_i equals the
+    planar functional (the pair mean is the cell), so the material gradients
+    agree (to the FP32-area rounding of the mesh), and both TX-position
+    gradients of box cells vanish."""
+    sc, txs, p = S.workload(4)
+    tx = txs[0]
+    tx.ray_stride = 53
+    p.deposit = 0
+    p.nx = p.ny = 64            # 8192 surface triangles: the oracle tests each one per segment
+    p.cell_size *= 4
+    x0, y0 = p.map_corner()
+    V, T = grid_surface(x0, y0, p.cell_size, p.nx, p.ny, flat(p.map_origin[2]))
+    g = np.random.default_rng(5).uniform(0.0, 1.0, (p.ny, p.nx))
+    rec = orc.radio_map(sc, tx, p, want_record=True)["record"]
+    de, ds, dt = orc.grad(sc, tx, p, rec, g)
+    gm = np.repeat(g.ravel() / 2.0, 2)
+    rec_m = orc.radio_map_mesh(sc, tx, p, V, T, want_record=True)["record"]
+    assert np.array_equal(rec_m[..., 0], rec[..., 0]) and np.array_equal(rec_m[..., 3], rec[..., 3])
+    me, ms, mt = orc.grad_mesh(sc, tx, p, V, T, rec_m, gm)
+    ref = np.concatenate([de, ds])
+    assert np.abs(ref).max() > 0
+    assert np.allclose(np.concatenate([me, ms]), ref, rtol=2e-5, atol=2e-5 * np.abs(ref).max())
+    assert np.all(dt == 0.0) and np.all(mt == 0.0)
