@@ -242,7 +242,7 @@ rm_status rm_radio_map_trace(const rm_scene* scene, const rm_tx* tx_host, int32_
  * and unit normal n_i.  A crossing on an edge shared by two triangles counts
  * for both.  maps_dev [ntx][surface triangles] (input triangle order) is
  * overwritten.  params' map plane and cells are unused; deposit must be 0
- * (box).  Forward only (no gradient).  Otherwise as rm_radio_map_trace; the
+ * (box).  Gradient: rm_radio_map_grad_mesh.  Otherwise as rm_radio_map_trace; the
  * record's cells are -32768.  RM_ESTATE if the surface's BVH is not
  * built, RM_EINVAL for a NULL or empty surface or deposit != 0. */
 rm_status rm_radio_map_trace_mesh(const rm_scene* scene, const rm_scene* surface, const rm_tx* tx_host,
@@ -270,6 +270,16 @@ rm_status rm_radio_map_grad(const rm_scene* scene, const rm_tx* tx_host, int32_t
                             float* d_eps_dev, float* d_sigma_dev, float* d_txpos_dev,
                             const rm_material* sampling_host_or_null, rm_stats* stats_host_or_null,
                             rm_segment_record* record_dev_or_null, void* stream);
+
+/* rm_radio_map_grad for maps on a mesh measurement surface (see
+ * rm_radio_map_trace_mesh): dL_dmaps_dev [ntx][surface triangles].  The cells
+ * are boxes, so d_txpos stays 0.  deposit must be 0; otherwise as
+ * rm_radio_map_grad. */
+rm_status rm_radio_map_grad_mesh(const rm_scene* scene, const rm_scene* surface, const rm_tx* tx_host,
+                                 int32_t ntx, const rm_trace_params* params, const float* dL_dmaps_dev,
+                                 float* d_eps_dev, float* d_sigma_dev, float* d_txpos_dev,
+                                 const rm_material* sampling_host_or_null, rm_stats* stats_host_or_null,
+                                 rm_segment_record* record_dev_or_null, void* stream);
 
 /* Loss of the differentiable workload: mean over the cells V where both maps
  * exceed floor_linear of (10 log10 C_i - 10 log10 T_i)^2.  Writes loss_dev[0]

@@ -79,6 +79,7 @@ _SIGS = {
     "rm_radio_map_trace": ([P, P, C.c_int32, P, P, P, P, P], C.c_int),
     "rm_radio_map_trace_mesh": ([P, P, P, C.c_int32, P, P, P, P, P], C.c_int),
     "rm_radio_map_grad": ([P, P, C.c_int32, P, P, P, P, P, P, P, P, P], C.c_int),
+    "rm_radio_map_grad_mesh": ([P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P], C.c_int),
     "rm_radio_map_trace_noalloc": ([P, P, C.c_int32, P, P, P, P], C.c_int),
     "rm_db_mse_loss": ([P, P, C.c_int64, C.c_float, P, P, P, P], C.c_int),
     "rm_trace_plan_create": ([P, P, C.c_int32, P, P, P, C.POINTER(P)], C.c_int),

@@ -244,6 +244,32 @@ def trace_mesh(scene: Scene, surface: Scene, txs, params, record=False, stream=N
     return res
 
 
+def grad_mesh(scene: Scene, surface: Scene, txs, params, dLdC: torch.Tensor, sampling=None, record=False,
+              stream=None):
+    """(d_eps [nm], d_sigma [nm], d_txpos [ntx, 3] = 0) of sum(dLdC * maps) for maps on a mesh
+    measurement surface (dLdC [ntx, surface triangles]); choices frozen, q detached."""
+    lib = L.load()
+    arr, ntx = _tx_array(txs)
+    p = params if isinstance(params, L.rm_trace_params) else params_from(params)
+    d_eps = torch.zeros(scene.nm, dtype=torch.float32, device="cuda")
+    d_sig = torch.zeros(scene.nm, dtype=torch.float32, device="cuda")
+    d_tx = torch.zeros((ntx, 3), dtype=torch.float32, device="cuda")
+    sm = None if sampling is None else materials(sampling)
+    rec = None
+    if record:
+        nrec = sum(tx_count(arr[i]) for i in range(ntx)) * (p.max_depth + 1)
+        rec = torch.empty((max(nrec, 1), 4), dtype=torch.int32, device="cuda")
+    st = L.rm_stats()
+    g = dLdC.contiguous()
+    _check(lib.rm_radio_map_grad_mesh(scene.handle, surface.handle, arr, ntx, C.byref(p), _ptr(g), _ptr(d_eps),
+                                      _ptr(d_sig), _ptr(d_tx), sm, C.byref(st), _ptr(rec), _stream(stream)),
+           "rm_radio_map_grad_mesh")
+    out = {"d_eps": d_eps, "d_sigma": d_sig, "d_tx": d_tx, "stats": st.as_dict()}
+    if record:
+        out["record"] = rec
+    return out
+
+
 def surface(verts, tris, device="cuda", stream=None) -> Scene:
     """A mesh measurement surface: the triangles uploaded with their LBVH (one dummy material)."""
     t = np.asarray(tris, np.int32).reshape(-1, 3)

@@ -714,6 +714,15 @@ rm_status rm_radio_map_grad(const rm_scene* sc, const rm_tx* tx, int32_t ntx, co
                      sampling_host_or_null, stats, record, stream, true);
 }
 
+rm_status rm_radio_map_grad_mesh(const rm_scene* sc, const rm_scene* surface, const rm_tx* tx, int32_t ntx,
+                                 const rm_trace_params* p, const float* dL_dmaps_dev, float* d_eps_dev,
+                                 float* d_sigma_dev, float* d_txpos_dev, const rm_material* sampling_host_or_null,
+                                 rm_stats* stats, rm_segment_record* record, void* stream) {
+    if (!surface) return fail(RM_EINVAL, "surface is NULL");
+    return run_trace(sc, tx, ntx, p, nullptr, dL_dmaps_dev, d_eps_dev, d_sigma_dev, d_txpos_dev,
+                     sampling_host_or_null, stats, record, stream, true, surface);
+}
+
 rm_status rm_db_mse_loss(const float* maps_dev, const float* target_dev, int64_t ncells, float floor_linear,
                          float* loss_dev, float* dL_dmaps_dev, int64_t* valid_dev, void* stream) {
     if (!maps_dev || !target_dev || !dL_dmaps_dev) return fail(RM_EINVAL, "NULL buffer");

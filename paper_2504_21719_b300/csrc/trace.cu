@@ -537,12 +537,17 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
 // (lambda0 / 4 pi)^2 |E|^2 / Pr.  With det = e1 . (k x e2) = -(e1 x e2) . k,
 // A |n . k| = |det| / 2.  Edges count on both sides (u, v >= 0, u + v <= 1).
 // Returns the number of crossings; *overflow is set if the traversal stack or
-// its step budget runs out.
+// its step budget runs out.  GATHER (the adjoint): instead of depositing,
+// *g_out receives sum_i dLdC_i 2 / |det_i| over the crossings, so that
+// sum_i dLdC_i dC_i = v0-derivative times dep_scale / Pr times that sum.
+template <bool GATHER>
 __device__ __noinline__ unsigned surface_crossings(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                                    int nt, int nlarge, float ox, float oy, float oz, float kx,
                                                    float ky, float kz, float tmax, float v0,
-                                                   double* __restrict__ map, bool* overflow) {
+                                                   double* __restrict__ map, const float* __restrict__ dldc,
+                                                   float* g_out, bool* overflow) {
     unsigned cnt = 0;
+    float gsum = 0.0f;
     const f3 o{ox, oy, oz}, k{kx, ky, kz};
     auto leaf = [&](int slot) {
         const float4* tp = tris + 3 * (size_t)slot;
@@ -561,13 +566,17 @@ __device__ __noinline__ unsigned surface_crossings(const float4* __restrict__ no
         if (v < 0.0f || u + v > 1.0f) return;
         const float t = dot(e2, q) * inv;
         if (!(t > 1e-9f && t < tmax)) return;
-        atomicAdd(map + __float_as_int(r2.z), (double)(2.0f * v0 / fabsf(det)));
+        if (GATHER) gsum += __ldg(dldc + __float_as_int(r2.z)) * (2.0f / fabsf(det));
+        else atomicAdd(map + __float_as_int(r2.z), (double)(2.0f * v0 / fabsf(det)));
         ++cnt;
     };
 #pragma unroll 1
     for (int j = 0; j < nlarge; ++j) leaf(nt + j);
     if (nt == 1) leaf(0);
-    if (nt < 2) return cnt;
+    if (nt < 2) {
+        if (GATHER) *g_out = gsum;
+        return cnt;
+    }
     const float ooeps = 0x1p-80f;
     const float ix = __frcp_rn(fabsf(kx) > ooeps ? kx : copysignf(ooeps, kx));
     const float iy = __frcp_rn(fabsf(ky) > ooeps ? ky : copysignf(ooeps, ky));
@@ -586,6 +595,7 @@ __device__ __noinline__ unsigned surface_crossings(const float4* __restrict__ no
     while (true) {
         if (--budget < 0) {
             *overflow = true;
+            if (GATHER) *g_out = gsum;
             return cnt;
         }
         const float4* nd = nodes + 4 * (size_t)cur;
@@ -610,7 +620,10 @@ __device__ __noinline__ unsigned surface_crossings(const float4* __restrict__ no
         } else if (h1) {
             cur = c1;
         } else {
-            if (sp == 0) return cnt;
+            if (sp == 0) {
+                if (GATHER) *g_out = gsum;
+                return cnt;
+            }
             cur = stack[--sp];
         }
     }
@@ -851,11 +864,12 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
         const unsigned long long mbase = (unsigned long long)txi * A.ncell;
         float tg0 = 0.0f, tg1 = 0.0f, tg2 = 0.0f;   // adjoint: this deposit's TX-position gradient
 
-        if (MESH) {
+        if (MESH && !ADJ) {
             // mesh measurement surface: every triangle the segment crosses
             if (active && (depth > 0 || (A.flags & RM_LOS)))
-                c_dep += surface_crossings(A.snodes, A.stris, A.snt, A.snlarge, r.ox, r.oy, r.oz, r.kx, r.ky, r.kz,
-                                           h.t, s_tx[txi].dep_scale * e2 * inv_pr, A.maps64 + mbase, &overflow);
+                c_dep += surface_crossings<false>(A.snodes, A.stris, A.snt, A.snlarge, r.ox, r.oy, r.oz, r.kx, r.ky,
+                                                  r.kz, h.t, s_tx[txi].dep_scale * e2 * inv_pr, A.maps64 + mbase,
+                                                  nullptr, nullptr, &overflow);
         } else if (!ADJ) {
             // one FP64 reduction per deposit (per stencil corner): a cell may
             // receive ~1e5 deposits, which FP32 accumulation would round to
@@ -878,10 +892,15 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                     else atomicAdd(A.maps + key, v);
                 }
             }
-        } else if (dep) {
+        } else if (MESH ? (active && (depth > 0 || (A.flags & RM_LOS))) : dep) {
             // adjoint: gather g = dL/dC at the deposit (and its spatial derivative)
             float G = 0.0f, Gx = 0.0f, Gy = 0.0f;
-            if (BILIN) {
+            float sc = s_tx[txi].dep_scale * inv_pr;
+            if (MESH) {
+                // every crossed triangle: G = sum_i dLdC_i / (A_i |n_i . k|)
+                c_dep += surface_crossings<true>(A.snodes, A.stris, A.snt, A.snlarge, r.ox, r.oy, r.oz, r.kx, r.ky,
+                                                 r.kz, h.t, 0.0f, nullptr, A.dLdC + mbase, &G, &overflow);
+            } else if (BILIN) {
 #pragma unroll 1
                 for (int cn = 0; cn < 4; ++cn) {
                     const int a = cn & 1, b = cn >> 1;
@@ -898,7 +917,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
             } else {
                 G = __ldg(A.dLdC + mbase + (unsigned long long)iy * A.nx + ix);
             }
-            const float sc = s_tx[txi].dep_scale * inv_pr / fabsf(r.kz);
+            if (!MESH) sc /= fabsf(r.kz);
             if (G != 0.0f) {
 #pragma unroll 1
                 for (int s = 0; s < nslot; ++s) {
@@ -1211,12 +1230,13 @@ const void* select_diff(bool diffuse) {
 
 const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, bool mesh) {
     if (mesh) {
-        // mesh surfaces: forward, box cells only
-        if (adjoint || bilinear) return nullptr;
-#define RM_SELM(P, D) \
-    if (npol == P && debug == D) \
-        return diffuse ? kernel_ptr<false, P, D, false, true, true>() : kernel_ptr<false, P, D, false, false, true>();
-        RM_SELM(1, false) RM_SELM(1, true) RM_SELM(2, false) RM_SELM(2, true)
+        // mesh surfaces: box cells only
+        if (bilinear) return nullptr;
+#define RM_SELM(A, P, D) \
+    if (adjoint == A && npol == P && debug == D) \
+        return diffuse ? kernel_ptr<A, P, D, false, true, true>() : kernel_ptr<A, P, D, false, false, true>();
+        RM_SELM(false, 1, false) RM_SELM(false, 1, true) RM_SELM(false, 2, false) RM_SELM(false, 2, true)
+        RM_SELM(true, 1, false) RM_SELM(true, 1, true) RM_SELM(true, 2, false) RM_SELM(true, 2, true)
 #undef RM_SELM
         return nullptr;
     }

@@ -96,6 +96,8 @@ def test_host_validation_without_gpu(L):
     assert lib.rm_diffraction_map(None, None, 0, None, 1, None, 16, None, None, None, None) == L.RM_EINVAL
     assert lib.rm_trace_plan_launch(None, None) == L.RM_EINVAL
     assert lib.rm_radio_map_trace_mesh(None, None, None, 1, None, None, None, None, None) == L.RM_EINVAL
+    assert lib.rm_radio_map_grad_mesh(None, None, None, 1, None, None, None, None, None, None, None, None,
+                                      None) == L.RM_EINVAL
     assert b"surface" in lib.rm_last_error()
     assert lib.rm_bvh_build(None, None) == L.RM_EINVAL
     assert lib.rm_scene_info(None, None, None, None, None) == L.RM_EINVAL

@@ -83,3 +83,36 @@ def test_mesh_rejects_bilinear(api):
         api.trace_mesh(gs, su, txs, q)
     su.free()
     gs.free()
+
+
+@pytest.mark.parametrize("diffuse", [False, True])
+def test_mesh_adjoint_matches_oracle_gradient(orc, api, diffuse):
+    """The mesh adjoint against the oracle's dual-number gradient along the
+    GPU's own record (after the oracle certified the forward's choices); the
+    TX-position gradient of box cells is zero."""
+    sc, txs, p = S.workload(4)
+    tx = txs[0]
+    tx.ray_stride = 13
+    p.deposit = 0
+    if diffuse:
+        sc = sc.with_scattering(np.linspace(0.2, 0.8, sc.nm), 0.3, np.arange(sc.nm) % 3, 2, 3, 0.5)
+        p = copy.copy(p)
+        p.diffuse = True
+    V, T = terrain(48, 60.0)
+    gs = api.Scene.from_obj(sc)
+    su = api.surface(V, T)
+    f = api.trace_mesh(gs, su, [tx], p, record=True)
+    rec = f["record"].view(tx.count(), p.max_depth + 1, 4).cpu().numpy()
+    compare_mesh(orc, sc, tx, p, V, T, f["maps"][0].cpu().numpy(), rec)
+    g = torch.from_numpy(np.random.default_rng(9).uniform(0.0, 1.0, (1, len(T))).astype(np.float32)).cuda()
+    a = api.grad_mesh(gs, su, [tx], p, g, record=True)
+    assert torch.equal(a["record"], f["record"])
+    ad = np.concatenate([a["d_eps"].cpu().numpy(), a["d_sigma"].cpu().numpy()])
+    de, ds, dt = orc.grad_mesh(sc, tx, p, V, T, rec, g[0].double().cpu().numpy())
+    ref = np.concatenate([de, ds])
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    err = np.abs(ad - ref) / scale
+    assert np.all(err <= 1e-2), err
+    assert torch.all(a["d_tx"] == 0.0) and np.all(dt == 0.0)
+    su.free()
+    gs.free()
