@@ -116,3 +116,22 @@ def test_mesh_adjoint_matches_oracle_gradient(orc, api, diffuse):
     assert torch.all(a["d_tx"] == 0.0) and np.all(dt == 0.0)
     su.free()
     gs.free()
+
+
+def test_mesh_edge_cases(orc, api):
+    """Free space over a one-triangle surface (a large-triangle list of one,
+    no tree), a two-triangle surface, and an empty ray subset."""
+    sc = S.empty_scene()
+    tx = S.Tx(pos=(0.3, -0.2, 10.0), num_rays=200_000, seed=1)
+    p = S.TraceParams(3.5e9, 0)
+    for V, T in ((np.array([[-30, -30, 1.5], [30, -30, 1.0], [0, 40, 2.0]], np.float32), np.array([[0, 1, 2]], np.int32)),
+                 terrain(1, 25.0)):
+        m, rec, st = _run(api, sc, V, T, [tx], p)
+        assert st["deposits"] > 1000
+        compare_mesh(orc, sc, tx, p, V, T, m[0], rec)
+    gs = api.Scene.from_obj(sc)
+    su = api.surface(*terrain(2, 10.0))
+    r = api.trace_mesh(gs, su, [S.Tx(pos=(0, 0, 5.0), num_rays=1000, ray_count=0)], p)
+    assert r["stats"]["rays"] == 0 and float(r["maps"].abs().sum()) == 0.0
+    su.free()
+    gs.free()
