@@ -51,6 +51,12 @@ typedef enum {
     RM_ESTATE = 6      /* call order: e.g. tracing before rm_bvh_build, or during stream capture */
 } rm_status;
 
+/* Host-side fault injection kinds (rm_debug_inject, RM_FAULT). */
+#define RM_FAULT_ALLOC 1     /* scene upload / BVH build return RM_ENOMEM before allocating */
+#define RM_FAULT_LAUNCH 2    /* a trace or gradient returns RM_ECUDA before enqueueing anything */
+#define RM_FAULT_OVERFLOW 3  /* a trace or gradient completes, then reports RM_EOVERFLOW as a device
+                                status word would */
+
 #define RM_MAX_DEPTH 15      /* maximum number of interactions L */
 #define RM_MAX_MATERIALS 32  /* radio materials per scene */
 #define RM_MAX_TX 64         /* transmitters per trace call */
@@ -384,6 +390,14 @@ rm_status rm_diffraction_map(const rm_scene* scene, const rm_wedge* wedges_host,
                              int32_t ntx, const rm_trace_params* params, int64_t samples_per_wedge,
                              float* maps_dev, rm_stats* stats_host_or_null, rm_segment_record* record_dev_or_null,
                              void* stream);
+
+/* Failure detection without a GPU fault: the next `count` checks of `kind`
+ * (RM_FAULT_*) fail on the host with the status the real failure returns;
+ * count 0 disarms.  The environment variable RM_FAULT=<alloc|launch|overflow>
+ * [:count] arms one kind once per process.  The context stays usable: the
+ * call after an injected failure runs normally.  RM_EINVAL for another kind
+ * or count < 0. */
+rm_status rm_debug_inject(int32_t kind, int32_t count);
 
 /* Number of triangles / internal BVH nodes of a scene (host call, no device work). */
 rm_status rm_scene_info(const rm_scene* scene, int64_t* nt, int64_t* nnodes, int32_t* nm,

@@ -2,6 +2,8 @@
 // validation, scene and plan lifetime, per-call constant tables and launches.
 #include <algorithm>
 #include <cmath>
+#include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -86,6 +88,30 @@ rm_status cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Host-side fault injection (failure detection is tested without a GPU
+// fault): an armed kind makes its next `count` checks fail on the host, with
+// the status the real failure would return.  Armed by rm_debug_inject or once
+// per process by RM_FAULT=<alloc|launch|overflow>[:count].
+std::atomic<int> g_fault[4];
+std::once_flag g_fault_env;
+void arm_from_env() {
+    const char* v = std::getenv("RM_FAULT");
+    if (!v) return;
+    const std::string sv(v);
+    const std::string kind = sv.substr(0, sv.find(':'));
+    const int count = sv.find(':') == std::string::npos ? 1 : std::atoi(sv.c_str() + sv.find(':') + 1);
+    const int k = kind == "alloc" ? RM_FAULT_ALLOC : kind == "launch" ? RM_FAULT_LAUNCH
+                : kind == "overflow" ? RM_FAULT_OVERFLOW : 0;
+    if (k && count > 0) g_fault[k].store(count);
+}
+bool injected(int kind) {
+    std::call_once(g_fault_env, arm_from_env);
+    int c = g_fault[kind].load();
+    while (c > 0)
+        if (g_fault[kind].compare_exchange_weak(c, c - 1)) return true;
+    return false;
+}
 
 rm_status check_device(const rm_scene* sc) {
     int dev = -1;
@@ -511,6 +537,9 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
     if (cs != cudaStreamCaptureStatusNone)
         return fail(RM_ESTATE, "stream is capturing; use rm_trace_plan_create for graph launches");
 
+    if (injected(RM_FAULT_LAUNCH))
+        return fail(RM_ECUDA, std::string(adjoint ? "rm_radio_map_grad" : "rm_radio_map_trace") +
+                                  ": injected launch failure (nothing was enqueued)");
     Prepared P;
     prepare(sc, tx, ntx, p, smats, &P, surf);
     const bool debug = record != nullptr || (p->flags & RM_STATS);
@@ -563,6 +592,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         P.kernel_ms = ms;
     if (e != cudaSuccess) return cuda_fail(e, adjoint ? "rm_radio_map_grad" : "rm_radio_map_trace");
     if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
+    if (injected(RM_FAULT_OVERFLOW)) host.status |= 1;   // as if the device had set its status word
     if (stats) fill_stats(host, P, stats);
     if (host.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow; affected rays were dropped");
     return RM_OK;
@@ -573,6 +603,14 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
 extern "C" {
 
 const char* rm_last_error(void) { return g_err.c_str(); }
+
+rm_status rm_debug_inject(int32_t kind, int32_t count) {
+    if (kind < RM_FAULT_ALLOC || kind > RM_FAULT_OVERFLOW || count < 0)
+        return fail(RM_EINVAL, "kind must be RM_FAULT_ALLOC, RM_FAULT_LAUNCH or RM_FAULT_OVERFLOW, count >= 0");
+    std::call_once(g_fault_env, arm_from_env);
+    g_fault[kind].store(count);
+    return RM_OK;
+}
 
 const char* rm_version(void) { return "rmsbr 0.1 (sm_103a)"; }
 
@@ -586,6 +624,7 @@ rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tri
         return fail(RM_EINVAL, "mesh pointers are NULL for a non-empty mesh");
     rm_status st = check_materials(mats_host, nm);
     if (st != RM_OK) return st;
+    if (injected(RM_FAULT_ALLOC)) return fail(RM_ENOMEM, "rm_scene_upload: injected allocation failure");
     rm_scene* sc = new rm_scene();
     RM_CUDA(cudaGetDevice(&sc->device));
     sc->nv = nv;
@@ -641,6 +680,7 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
     rm_status st = check_device(sc);
     if (st != RM_OK) return st;
     if (sc->built) return fail(RM_ESTATE, "the BVH of this scene is already built");
+    if (injected(RM_FAULT_ALLOC)) return fail(RM_ENOMEM, "rm_bvh_build: injected allocation failure");
     const int64_t n = sc->nt;
     if (n > 0) {
         const size_t o_o = align256(sizeof(uint64_t) * n), o_n = o_o + align256(sizeof(int32_t) * n),
