@@ -537,3 +537,38 @@ def diffraction_map(scene, tx, params, samples_per_wedge: int, mode: str = "plai
     if slack:
         out["slack"] = sl
     return out
+
+
+def diffraction_map_mesh(scene, tx, params, samples_per_wedge: int, surf_verts, surf_tris, mode: str = "plain",
+                         record=None, want_record: bool = False, slack: bool = False):
+    """Diffraction map on a mesh measurement surface: [n_surf] (float64).  Record
+    [nw * N', 4] = {incident bit (-2 source behind both faces), crossings, 0, 0};
+    replay certifies the incident bit only."""
+    v, t, m, mats = _scene_arrays(scene)
+    sv = np.ascontiguousarray(surf_verts, np.float32)
+    st_ = np.ascontiguousarray(surf_tris, np.int32)
+    otx, op = make_tx(tx), make_params(params)
+    nw = len(wedges(scene))
+    n = nw * int(samples_per_wedge)
+    rec = None
+    if mode == "replay":
+        rec = np.ascontiguousarray(record, np.int32).reshape(n, 4).copy()
+    elif want_record:
+        rec = np.zeros((max(n, 1), 4), np.int32)
+    mp = np.empty(len(st_), np.float64)
+    sl = np.empty(len(st_), np.float64) if slack else None
+    rep = OrReport()
+    rc = lib().or_diffraction_map_mesh(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), C.byref(otx),
+                                       C.byref(op), C.c_int64(int(samples_per_wedge)), _p(sv), _p(st_),
+                                       C.c_int64(len(st_)), MODES[mode], _p(rec), C.c_int64(max(n, 1)), _p(mp),
+                                       _p(sl), C.byref(rep))
+    if rc != 0:
+        raise ValueError(f"or_diffraction_map_mesh failed ({rc})")
+    out = {"map": mp, "wedges": nw}
+    if want_record or mode != "plain":
+        out["record"] = rec
+    if mode == "replay":
+        out["report"] = rep.as_dict()
+    if slack:
+        out["slack"] = sl
+    return out

@@ -2599,4 +2599,179 @@ int or_diffraction_map(const float* verts, int64_t nv, const int32_t* tris, int6
     return 0;
 }
 
+// The diffraction map on a mesh measurement surface (one cell per surface
+// triangle): a sample's diffracted ray deposits at every surface triangle it
+// crosses (t_j > 1e-9) whose segment from the edge is unblocked, with the
+// weighting factor taken on that triangle's plane and 1 / A_j for the cell's
+// area (Eq. radio-map-solver-ci-D-est with the cell's own measure).  The UTD
+// field is evaluated at each crossing's distance.
+// rec [nw][N'][4] = {bits (1 incident blocked; -2 source behind both faces),
+// crossings found, 0, 0}; replay (mode 1) certifies only the incident bit (the
+// per-crossing visibility is recomputed: a near tie goes to the slack).
+// slack_out [n_surf]: per cell, the values of crossings within tol of the
+// triangle's boundary or of a visibility near tie, plus the +-1e-5 rad
+// azimuth change of every deposit.
+int or_diffraction_map_mesh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
+                            const float* mats, int nm, const or_tx* tx, const or_params* P, int64_t samples_per_wedge,
+                            const float* surf_verts, const int32_t* surf_tris, int64_t n_surf, int mode, int32_t* rec,
+                            int64_t rec_cap, double* map_out, double* slack_out, or_report* report) {
+    if (samples_per_wedge < 1) return 1;
+    Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
+    const MeshSurface M = make_surface(surf_verts, surf_tris, n_surf);
+    const std::vector<Wedge> WS = find_wedges(S, verts, tris, nt);
+    const int64_t nw = (int64_t)WS.size(), NS = samples_per_wedge;
+    if (rec && rec_cap < nw * NS) return 2;
+    const double omega = 2.0 * PI * P->freq_hz, k0 = omega / C0;
+    const double lam4pi = C0 / P->freq_hz / (4.0 * PI);
+    TxC T = make_txc(*tx);
+    const int npol = tx->pol == 2 ? 2 : 1;
+    const V3<double> s{tx->pos[0], tx->pos[1], tx->pos[2]};
+    std::vector<DepList> lists(nw), slacks(slack_out ? nw : 0);
+    std::vector<ReplayState> rss(nw);
+    for (auto& r : rss) std::memset(&r.rep, 0, sizeof r.rep);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t w = 0; w < nw; ++w) {
+        Sink<double> sink{&lists[w]};
+        Sink<double> slack_sink{slack_out ? &slacks[w] : nullptr};
+        ReplayState& rs = rss[w];
+        const Wedge R = oriented(WS[w], s);
+        const bool lit = dot(s - R.o, R.n0) >= 0.0;
+        const Cx<double> eta0 = permittivity(S.eps[R.mat0], S.sigma[R.mat0], omega);
+        const Cx<double> etan = permittivity(S.eps[R.matn], S.sigma[R.matn], omega);
+        for (int64_t i = 0; i < NS; ++i) {
+            int32_t* rc = rec ? rec + 4 * (w * NS + i) : nullptr;
+            if (mode == 1) rs.rep.segments++;
+            double u1, u2;
+            wedge_sample(i, NS, &u1, &u2);
+            const double x = u1 * R.len, phi = u2 * R.n * PI;
+            V3<double> v, ks;
+            keller(R, s, x, phi, &v, &ks);
+            const double vm = std::max(std::fabs(v.x), std::max(std::fabs(v.y), std::fabs(v.z)));
+            const double eps = std::ldexp(std::max(1.0, vm), -16);
+            const V3<double> sv = v - s;
+            const double sprime = norm(sv);
+            const V3<double> si = scl(sv, 1.0 / sprime);
+            int code = -2;
+            int ncross = 0;
+            if (lit) {
+                code = blocked(S, s, si, eps, sprime - eps, R.tri0, R.trin) ? 1 : 0;
+                if (mode == 1 && rc[0] != code) {
+                    const double tol = tie_tol(v, sprime);
+                    if (rc[0] < 0 || !blocked_near_tie(S, s, si, eps, sprime - eps, R.tri0, R.trin, tol)) {
+                        rs.fail(w * NS + i, 0, 5, code, rc[0], 0, 0);
+                        continue;
+                    }
+                    rs.rep.adopted_hit++;
+                    code = rc[0];
+                }
+            } else if (mode == 1 && rc[0] != -2) {
+                rs.fail(w * NS + i, 0, 6, code, rc[0], 0, 0);
+                continue;
+            }
+            if (code == 0) {
+                const std::complex<double> al = array_factor(T, si, k0);
+                auto power = [&](const V3<double>& kd_, double sobs) {
+                    double pw = 0.0;
+                    for (int p = 0; p < npol; ++p) {
+                        const V3<double> f = tx_field(si, T.R, tx->pattern, tx->pol == 2 ? p : tx->pol);
+                        const CV3<double> E{Cx<double>(f.x * al.real(), f.x * al.imag()),
+                                            Cx<double>(f.y * al.real(), f.y * al.imag()),
+                                            Cx<double>(f.z * al.real(), f.z * al.imag())};
+                        std::complex<double> ed[2];
+                        utd_field(R, eta0, etan, k0, s, v, kd_, sobs, E, ed);
+                        pw += std::norm(ed[0]) + std::norm(ed[1]);
+                    }
+                    return pw;
+                };
+                for (int64_t j = 0; j < M.n; ++j) {
+                    if (M.inv_area[j] == 0.0) continue;
+                    V3<double> pv = cross(ks, M.e2[j]);
+                    const double det = dot(M.e1[j], pv);
+                    if (det == 0.0) continue;
+                    const V3<double> tv = v - M.a[j];
+                    const double uu = dot(tv, pv) / det;
+                    const V3<double> qv = cross(tv, M.e1[j]);
+                    const double vv = dot(ks, qv) / det;
+                    const double t = dot(M.e2[j], qv) / det;
+                    const double ww = 1.0 - uu - vv;
+                    const double tol = tie_tol(v + scl(ks, t), sprime + std::max(t, 0.0));
+                    const double tb = tol * M.max_edge[j] * 0.5 * M.inv_area[j];
+                    const double mn = std::min(uu, std::min(vv, ww));
+                    const bool inside = mn >= 0.0 && t > 1e-9;
+                    const bool near = (std::fabs(mn) <= tb && t > -tol) || (mn >= -tb && std::fabs(t - 1e-9) <= tol);
+                    if (!inside && !near) continue;
+                    if (inside) ++ncross;
+                    // visibility of the edge-to-crossing segment
+                    const double tt = std::max(t, 0.0);
+                    const bool bd = blocked(S, v, ks, eps, tt, R.tri0, R.trin);
+                    const bool vis_tie = blocked_near_tie(S, v, ks, eps, tt, R.tri0, R.trin, tol);
+                    if (bd && !vis_tie) continue;
+                    // weighting factor on the triangle's plane: t(x, phi) = v + gam ks with
+                    // n.(t - a) = 0, by dual numbers
+                    const V3<double> nj = cross(M.e1[j], M.e2[j]);
+                    D xd(x), pd(phi);
+                    xd.g[0] = 1.0;
+                    pd.g[1] = 1.0;
+                    V3<D> vd, kd;
+                    keller(R, s, xd, pd, &vd, &kd);
+                    const D num = D(dot(nj, M.a[j])) - (vd.x * nj.x + vd.y * nj.y + vd.z * nj.z);
+                    const D den = kd.x * nj.x + kd.y * nj.y + kd.z * nj.z;
+                    const D gam = num / den;
+                    const V3<double> tx_{vd.x.g[0] + gam.g[0] * kd.x.v + gam.v * kd.x.g[0],
+                                         vd.y.g[0] + gam.g[0] * kd.y.v + gam.v * kd.y.g[0],
+                                         vd.z.g[0] + gam.g[0] * kd.z.v + gam.v * kd.z.g[0]};
+                    const V3<double> tp_{vd.x.g[1] + gam.g[1] * kd.x.v + gam.v * kd.x.g[1],
+                                         vd.y.g[1] + gam.g[1] * kd.y.v + gam.v * kd.y.g[1],
+                                         vd.z.g[1] + gam.g[1] * kd.z.v + gam.v * kd.z.g[1]};
+                    const double J = norm(cross(tx_, tp_));
+                    const double wgt = lam4pi * lam4pi * J * (R.len * R.n * PI / (double)NS) * M.inv_area[j];
+                    if (!(tt > 0.0)) continue;
+                    const double value = wgt * power(ks, tt);
+                    if (inside && !bd) sink.add((int)j, value);
+                    if (slack_out) {
+                        double az = 0.0;
+                        for (double dphi : {-1e-5, 1e-5}) {
+                            V3<double> v2, k2;
+                            keller(R, s, x, phi + dphi, &v2, &k2);
+                            az = std::max(az, std::fabs(wgt * power(k2, tt) - value));
+                        }
+                        slack_sink.add((int)j, ((near || vis_tie) ? value : 0.0) + az);
+                    }
+                }
+            }
+            if (rc && mode == 0) {
+                rc[0] = code;
+                rc[1] = ncross;
+                rc[2] = 0;
+                rc[3] = 0;
+            }
+        }
+    }
+    std::memset(map_out, 0, sizeof(double) * (size_t)n_surf);
+    for (int64_t w = 0; w < nw; ++w)
+        for (size_t j = 0; j < lists[w].cell.size(); ++j) map_out[lists[w].cell[j]] += lists[w].val[j];
+    if (slack_out) {
+        std::memset(slack_out, 0, sizeof(double) * (size_t)n_surf);
+        for (int64_t w = 0; w < nw; ++w)
+            for (size_t j = 0; j < slacks[w].cell.size(); ++j) slack_out[slacks[w].cell[j]] += slacks[w].val[j];
+    }
+    if (report) {
+        std::memset(report, 0, sizeof *report);
+        bool have = false;
+        for (int64_t w = 0; w < nw; ++w) {
+            const or_report& r = rss[w].rep;
+            report->segments += r.segments;
+            report->adopted_hit += r.adopted_hit;
+            report->failures += r.failures;
+            if (r.failures && !have) {
+                have = true;
+                report->fail_ray = r.fail_ray;
+                report->fail_kind = r.fail_kind;
+                std::memcpy(report->fail_info, r.fail_info, sizeof r.fail_info);
+            }
+        }
+    }
+    return 0;
+}
+
 }  // extern "C"

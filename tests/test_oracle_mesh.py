@@ -163,3 +163,32 @@ def test_mesh_gradient_equals_planar_gradient(orc):
     assert np.abs(ref).max() > 0
     assert np.allclose(np.concatenate([me, ms]), ref, rtol=2e-5, atol=2e-5 * np.abs(ref).max())
     assert np.all(dt == 0.0) and np.all(mt == 0.0)
+
+
+@pytest.mark.parametrize("ground", [None, 500.0])
+def test_flat_mesh_diffraction_equals_planar_diffraction(orc, ground):
+    """The diffraction map on a flat mesh that tiles the planar cells: each
+    visible crossing falls into one triangle of its cell, the weighting factor
+    on the triangle's plane equals the plane's, and 1/A is twice 1/cell^2, so
+    the mean of a triangle pair equals the planar cell (FP32 vertices: 5e-6)."""
+    sc = S.single_box(0.0, 20.0, 0.0, 30.0, 25.0, mat=(5.0, 0.1, 0.2), ground=ground)
+    p = S.TraceParams(3.5e9, 0, cell_size=4.0, nx=20, ny=20, map_origin=(10.3, 15.2, 1.5))
+    tx = S.Tx(pos=(-30.0, -20.0, 15.0), num_rays=1)
+    x0, y0 = p.map_corner()
+    V, T = grid_surface(x0, y0, p.cell_size, p.nx, p.ny, flat(p.map_origin[2]))
+    pl = orc.diffraction_map(sc, tx, p, 512)["map"]
+    m = orc.diffraction_map_mesh(sc, tx, p, 512, V, T)["map"].reshape(p.ny, p.nx, 2)
+    assert (pl > 0).sum() > 100
+    assert np.allclose(m.mean(2), pl, rtol=5e-6, atol=1e-300)
+
+
+def test_mesh_diffraction_replay_of_own_record(orc):
+    sc = S.single_box(0.0, 20.0, 0.0, 30.0, 25.0, mat=(5.0, 0.1, 0.2), ground=500.0)
+    p = S.TraceParams(3.5e9, 0)
+    tx = S.Tx(pos=(-30.0, -20.0, 15.0), num_rays=1)
+    V, T = grid_surface(-40.0, -40.0, 5.0, 20, 20, lambda X, Y: 1.5 + 0.4 * np.sin(X / 6.0))
+    a = orc.diffraction_map_mesh(sc, tx, p, 256, V, T, want_record=True)
+    b = orc.diffraction_map_mesh(sc, tx, p, 256, V, T, mode="replay", record=a["record"], slack=True)
+    assert b["report"]["failures"] == 0 and b["report"]["adopted_hit"] == 0
+    assert np.array_equal(a["map"], b["map"])
+    assert (a["map"] > 0).sum() > 50 and np.all(b["slack"] >= 0)
