@@ -385,6 +385,17 @@ def run_extra(api, S, torch, gpu_name):
     out["mesh_surface"] = {"value": round(mst["segments"] / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3),
                            "segments": mst["segments"], "crossings": mst["deposits"], "cells": int(len(st_)),
                            "setting": "one cell per triangle of a 131072-triangle terrain mesh over the map"}
+    for _ in range(2):
+        api.diffraction_map_mesh(gs, su, txs, p, 4096, wedges=wl)
+    dk, dst = [], None
+    for _ in range(5):
+        r = api.diffraction_map_mesh(gs, su, txs, p, 4096, wedges=wl)
+        dk.append(r["stats"]["kernel_ms"])
+        dst = r["stats"]
+    k = statistics.mean(dk)
+    out["diffraction_mesh_surface"] = {"value": round(dst["rays"] / (k / 1e3), 1), "unit": "wedge samples/s",
+                                       "kernel_ms": round(k, 3), "samples": dst["rays"], "deposits": dst["deposits"],
+                                       "setting": "4096 samples per wedge onto the same terrain mesh"}
     su.free()
     gs.free()
     sc, txs, p = S.workload(3)

@@ -391,6 +391,21 @@ rm_status rm_diffraction_map(const rm_scene* scene, const rm_wedge* wedges_host,
                              float* maps_dev, rm_stats* stats_host_or_null, rm_segment_record* record_dev_or_null,
                              void* stream);
 
+/* The diffraction map on a mesh measurement surface (see
+ * rm_radio_map_trace_mesh): maps_dev [ntx][surface triangles].  A sample
+ * whose source-to-edge segment is unblocked deposits at every surface
+ * triangle its diffracted ray crosses (t > 1e-9, at most 8 crossings; more
+ * set RM_EOVERFLOW) when the edge-to-crossing segment is unblocked: the term
+ * of rm_diffraction_map with the weighting factor taken on the triangle's
+ * plane, 1 / A_i instead of 1 / Delta^2 and E_d at the crossing's distance.
+ * Records {bits: 1 incident blocked, -2 source behind both faces; crossings
+ * found; 0; 0}.  stats: segments = lit samples.  deposit must be 0;
+ * otherwise as rm_diffraction_map. */
+rm_status rm_diffraction_map_mesh(const rm_scene* scene, const rm_scene* surface, const rm_wedge* wedges_host,
+                                  int64_t nw, const rm_tx* tx_host, int32_t ntx, const rm_trace_params* params,
+                                  int64_t samples_per_wedge, float* maps_dev, rm_stats* stats_host_or_null,
+                                  rm_segment_record* record_dev_or_null, void* stream);
+
 /* Failure detection without a GPU fault: the next `count` checks of `kind`
  * (RM_FAULT_*) fail on the host with the status the real failure returns;
  * count 0 disarms.  The environment variable RM_FAULT=<alloc|launch|overflow>

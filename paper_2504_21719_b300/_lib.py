@@ -89,6 +89,7 @@ _SIGS = {
     "rm_trace_plan_free": ([P], None),
     "rm_scene_wedges": ([P, P, C.c_int64, P], C.c_int),
     "rm_diffraction_map": ([P, P, C.c_int64, P, C.c_int32, P, C.c_int64, P, P, P, P], C.c_int),
+    "rm_diffraction_map_mesh": ([P, P, P, C.c_int64, P, C.c_int32, P, C.c_int64, P, P, P, P], C.c_int),
     "rm_scene_info": ([P, P, P, P, P], C.c_int),
     "rm_scene_free": ([P], None),
     "rm_last_error": ([], C.c_char_p),

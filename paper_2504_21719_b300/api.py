@@ -223,6 +223,28 @@ def trace(scene: Scene, txs, params, record=False, stream=None, out=None):
     return res
 
 
+def diffraction_map_mesh(scene: Scene, surface: Scene, txs, params, samples_per_wedge: int, wedges=None,
+                         record=False, stream=None, out=None):
+    """First-order diffraction maps [ntx, surface triangles] (float32, cuda) on a mesh
+    measurement surface; add them to trace_mesh()'s maps for the full map."""
+    lib = L.load()
+    arr, ntx = _tx_array(txs)
+    p = params if isinstance(params, L.rm_trace_params) else params_from(params)
+    w, nw = wedges if wedges is not None else scene.wedges()
+    maps = out if out is not None else torch.empty((ntx, surface.nt), dtype=torch.float32, device="cuda")
+    rec = None
+    if record:
+        rec = torch.empty((max(ntx * nw * samples_per_wedge, 1), 4), dtype=torch.int32, device="cuda")
+    st = L.rm_stats()
+    _check(lib.rm_diffraction_map_mesh(scene.handle, surface.handle, w, nw, arr, ntx, C.byref(p),
+                                       int(samples_per_wedge), _ptr(maps), C.byref(st), _ptr(rec), _stream(stream)),
+           "rm_diffraction_map_mesh")
+    res = {"maps": maps, "stats": st.as_dict(), "wedges": nw}
+    if record:
+        res["record"] = rec
+    return res
+
+
 def trace_mesh(scene: Scene, surface: Scene, txs, params, record=False, stream=None, out=None):
     """Radio maps on a mesh measurement surface: [ntx, surface triangles] (float32, cuda),
     one cell per triangle of `surface` (a Scene whose materials are unused); the counters;

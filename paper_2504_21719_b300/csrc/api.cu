@@ -960,12 +960,22 @@ rm_status rm_scene_wedges(const rm_scene* sc, rm_wedge* out, int64_t cap, int64_
     return RM_OK;
 }
 
-rm_status rm_diffraction_map(const rm_scene* sc, const rm_wedge* wedges, int64_t nw, const rm_tx* tx, int32_t ntx,
-                             const rm_trace_params* p, int64_t ns, float* maps, rm_stats* stats,
-                             rm_segment_record* record, void* stream) {
+}  // extern "C"
+
+namespace {
+rm_status run_diffraction(const rm_scene* sc, const rm_scene* surf, const rm_wedge* wedges, int64_t nw,
+                          const rm_tx* tx, int32_t ntx, const rm_trace_params* p, int64_t ns, float* maps,
+                          rm_stats* stats, rm_segment_record* record, void* stream) {
     rm_status st = validate(sc, tx, ntx, p);
     if (st != RM_OK) return st;
     if ((st = check_device(sc)) != RM_OK) return st;
+    if (surf) {
+        if (!surf->built) return fail(RM_ESTATE, "rm_bvh_build has not been called on the surface");
+        if ((st = check_device(surf)) != RM_OK) return st;
+        if (surf->device != sc->device) return fail(RM_EINVAL, "scene and surface live on different devices");
+        if (surf->nt < 1 || surf->nt > INT32_MAX) return fail(RM_EINVAL, "the surface needs 1 .. 2^31-1 triangles");
+        if (p->deposit != 0) return fail(RM_EINVAL, "mesh surfaces take box cells (deposit = 0)");
+    }
     if (!maps) return fail(RM_EINVAL, "maps_dev is NULL");
     if (nw < 0 || (nw > 0 && !wedges)) return fail(RM_EINVAL, "nw must be >= 0 with a wedge array");
     if (ns < 1) return fail(RM_EINVAL, "samples_per_wedge must be >= 1");
@@ -987,7 +997,7 @@ rm_status rm_diffraction_map(const rm_scene* sc, const rm_wedge* wedges, int64_t
     const size_t tab = table_bytes(P, &o_mat, &o_tx);
     const size_t o_w = (tab + 255) & ~size_t(255);
     const size_t o_m64 = (o_w + sizeof(rm_wedge) * (size_t)std::max<int64_t>(nw, 1) + 255) & ~size_t(255);
-    const unsigned long long ncell = (unsigned long long)p->nx * p->ny;
+    const unsigned long long ncell = surf ? (unsigned long long)surf->nt : (unsigned long long)p->nx * p->ny;
     const size_t bytes = o_m64 + sizeof(double) * ncell * ntx;
     cudaEvent_t ev[2];
     RM_CUDA(timing_events(ev));
@@ -1023,7 +1033,15 @@ rm_status rm_diffraction_map(const rm_scene* sc, const rm_wedge* wedges, int64_t
     A.ncell = ncell;
     A.k0 = P.a.k0;
     const double lam4pi = C0 / p->freq_hz / (4.0 * PI);
-    A.lam4pi2_over_cell2 = (float)(lam4pi * lam4pi / ((double)p->cell_size * (double)p->cell_size));
+    // a mesh cell divides by its own area in the kernel
+    const double cell2 = surf ? 1.0 : (double)p->cell_size * (double)p->cell_size;
+    A.lam4pi2_over_cell2 = (float)(lam4pi * lam4pi / cell2);
+    if (surf) {
+        A.snodes = surf->nodes;
+        A.stris = surf->trirec;
+        A.snt = (int32_t)(surf->nt - surf->nlarge);
+        A.snlarge = (int32_t)surf->nlarge;
+    }
     double L, a[FADDEEVA_N];
     faddeeva_coefficients(FADDEEVA_N, &L, a);
     A.wz_L = (float)L;
@@ -1044,7 +1062,9 @@ rm_status rm_diffraction_map(const rm_scene* sc, const rm_wedge* wedges, int64_t
         if ((e = cudaMemsetAsync(dev + o_m64, 0, sizeof(double) * ncell * ntx, S(stream))) != cudaSuccess) break;
         if (A.total > 0) {
             if ((e = cudaEventRecord(ev[0], S(stream))) != cudaSuccess) break;
-            if ((e = launch_diffraction(A, p->block_size ? p->block_size : 256, S(stream), &grid)) != cudaSuccess) break;
+            if ((e = launch_diffraction(A, p->block_size ? p->block_size : 256, S(stream), &grid, surf != nullptr)) !=
+                cudaSuccess)
+                break;
             if ((e = cudaEventRecord(ev[1], S(stream))) != cudaSuccess) break;
             timed = true;
         }
@@ -1062,6 +1082,22 @@ rm_status rm_diffraction_map(const rm_scene* sc, const rm_wedge* wedges, int64_t
     if (stats) fill_stats(host, P, stats);
     if (host.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow in a visibility query");
     return RM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+rm_status rm_diffraction_map(const rm_scene* sc, const rm_wedge* wedges, int64_t nw, const rm_tx* tx, int32_t ntx,
+                             const rm_trace_params* p, int64_t ns, float* maps, rm_stats* stats,
+                             rm_segment_record* record, void* stream) {
+    return run_diffraction(sc, nullptr, wedges, nw, tx, ntx, p, ns, maps, stats, record, stream);
+}
+
+rm_status rm_diffraction_map_mesh(const rm_scene* sc, const rm_scene* surface, const rm_wedge* wedges, int64_t nw,
+                                  const rm_tx* tx, int32_t ntx, const rm_trace_params* p, int64_t ns, float* maps,
+                                  rm_stats* stats, rm_segment_record* record, void* stream) {
+    if (!surface) return fail(RM_EINVAL, "surface is NULL");
+    return run_diffraction(sc, surface, wedges, nw, tx, ntx, p, ns, maps, stats, record, stream);
 }
 
 rm_status rm_scene_info(const rm_scene* sc, int64_t* nt, int64_t* nnodes, int32_t* nm, int32_t* built) {

@@ -129,11 +129,16 @@ struct DiffArgs {
     float wz_L;                  // Weideman's L
     float wz_a[FADDEEVA_N];      // a_1 .. a_N
     int32_t npol, stats;
-    double* maps64;              // [ntx][ny][nx]
+    double* maps64;              // [ntx][ny][nx] (or [ntx][surface triangles])
     rm_segment_record* record;   // optional, [ntx][nw][ns]
     Scratch* scratch;
+    // mesh measurement surface (or null for the plane): its LBVH and leaf
+    // records; lam4pi2_over_cell2 is then (lambda0 / 4 pi)^2 (cell = 1)
+    const float4* snodes;
+    const float4* stris;
+    int32_t snt, snlarge;
 };
-cudaError_t launch_diffraction(const DiffArgs& a, int block, cudaStream_t s, int* grid_out);
+cudaError_t launch_diffraction(const DiffArgs& a, int block, cudaStream_t s, int* grid_out, bool mesh = false);
 // Weideman's L and a_1..a_N for w(z) = 2 p(Z) / (L - iz)^2 + (1/sqrt(pi)) / (L - iz),
 // p(Z) = sum_{n<N} a_{n+1} Z^n, Z = (L + iz)/(L - iz) (host, double).
 void faddeeva_coefficients(int N, double* L, double* a);

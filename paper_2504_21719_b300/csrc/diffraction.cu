@@ -224,7 +224,146 @@ __device__ __forceinline__ cf utd_term(float beta, float pm, float n, float kL, 
     return pre * (cd / sd) * utd_F(kL * 2.0f * sh * sh, A);
 }
 
+// |E_d|^2 of one sample at observation distance sobs (Eq. diffracted-field,
+// summed over the antenna's field columns): the UTD coefficients D_1..D_4
+// through one rolled call site, the face matrices R_0 and (when the n-face is
+// lit) R_n through another.
+__device__ __forceinline__ float diffracted_power(const DiffArgs& A, const TxDev& T, f3 s, f3 v, f3 e, f3 n0, f3 nn,
+                                                  f3 t0, int m0, int mn, float nw_, float phi, float sb, f3 si,
+                                                  float dn, float sobs) {
+    const f3 sr = s - v;
+    const f3 srt = sr - e * dot(sr, e);
+    float phip = atan2f(dot(srt, n0), dot(srt, t0));
+    if (phip < 0.0f) phip += 2.0f * PI_F;
+    const float L = sobs * dn / (sobs + dn) * sb * sb;
+    const float kL = A.k0 * L;
+    const float pm = 1.0f / (2.0f * nw_ * sqrtf(2.0f * PI_F * A.k0) * sb);
+    const cf pre = C(-0.70710678118654752f * pm, 0.70710678118654752f * pm);  // -e^{-j pi/4} pm
+    // D_1..D_4 through one rolled call site (beta = phi -+ phi', pm = +-1)
+    cf Dq[4];
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q)
+        Dq[q] = utd_term(q < 2 ? phi - phip : phi + phip, (q & 1) ? -1.0f : 1.0f, nw_, kL, pre, A);
+    const f3 phi_i = unit3(cross(si, e));
+    const f3 beta_i = cross(phi_i, si);
+    // R_0 and (when the n-face is lit) R_n through one call site
+    const bool n_lit = (nw_ - 1.0f) * PI_F <= phip;
+    Mat2 Rf[2];
+#pragma unroll 1
+    for (int q = 0; q < (n_lit ? 2 : 1); ++q) {
+        const MatDev& Mq = A.mats[q ? mn : m0];
+        Rf[q] = face_matrix(q ? nn : n0, C(Mq.eta_re, Mq.eta_im), si, e, phi_i, beta_i);
+    }
+    const Mat2& R0 = Rf[0];
+    Mat2 Rn;
+    if (n_lit) {
+        Rn = Rf[1];
+    } else {
+        Rn.m[0][0] = Rn.m[1][1] = C(-1.0f);
+        Rn.m[0][1] = Rn.m[1][0] = C(0.0f);
+    }
+    const cf a0 = Dq[3] - Dq[0], an = Dq[2] - Dq[1];
+    float pw = 0.0f;
+    for (int p = 0; p < A.npol; ++p) {
+        cf E[3];
+        antenna_field(T, A.ant, A.k0, si, A.npol == 2 ? p : T.pol, E);
+        const cf ein[2] = {edot(phi_i, E), edot(beta_i, E)};
+        for (int r = 0; r < 2; ++r) {
+            cf acc = C(0.0f);
+            for (int c = 0; c < 2; ++c) acc = acc + (a0 * R0.m[r][c] + an * Rn.m[r][c]) * ein[c];
+            pw += cabs2(acc);
+        }
+    }
+    // (the minus sign of Eq. diffracted-field does not change |E_d|^2)
+    return pw;
+}
+
+// Crossings t > 1e-9 of the ray v + t k with a mesh measurement surface, up to
+// MAX_CROSS of them (more set *overflow): distance, triangle, and the
+// unnormalised normal (b - a) x (c - a), whose length is twice the area.
+constexpr int MAX_CROSS = 8;
+struct Crossing {
+    float t;
+    int tri;
+    f3 nrm;
+};
+__device__ __noinline__ int surface_hits(const float4* __restrict__ nodes, const float4* __restrict__ tris, int nt,
+                                         int nlarge, f3 o, f3 k, Crossing* out, bool* overflow) {
+    int nh = 0;
+    auto leaf = [&](int slot) {
+        const float4* tp = tris + 3 * (size_t)slot;
+        const float4 r0 = __ldg(tp), r1 = __ldg(tp + 1), r2 = __ldg(tp + 2);
+        const f3 a{r0.x, r0.y, r0.z}, b{r0.w, r1.x, r1.y}, c{r1.z, r1.w, r2.x};
+        const f3 e1 = b - a, e2 = c - a;
+        const f3 pv = cross(k, e2);
+        const float det = dot(e1, pv);
+        if (det == 0.0f) return;
+        const float inv = 1.0f / det;
+        const f3 tv = o - a;
+        const float uu = dot(tv, pv) * inv;
+        if (uu < 0.0f || uu > 1.0f) return;
+        const f3 q = cross(tv, e1);
+        const float vv = dot(k, q) * inv;
+        if (vv < 0.0f || uu + vv > 1.0f) return;
+        const float t = dot(e2, q) * inv;
+        if (!(t > 1e-9f)) return;
+        if (nh < MAX_CROSS) out[nh++] = Crossing{t, __float_as_int(r2.z), cross(e1, e2)};
+        else *overflow = true;
+    };
+#pragma unroll 1
+    for (int j = 0; j < nlarge; ++j) leaf(nt + j);
+    if (nt == 1) leaf(0);
+    if (nt < 2) return nh;
+    const float ooeps = 0x1p-80f;
+    const float ix = __frcp_rn(fabsf(k.x) > ooeps ? k.x : copysignf(ooeps, k.x));
+    const float iy = __frcp_rn(fabsf(k.y) > ooeps ? k.y : copysignf(ooeps, k.y));
+    const float iz = __frcp_rn(fabsf(k.z) > ooeps ? k.z : copysignf(ooeps, k.z));
+    auto box = [&](float lx, float ly, float lz, float hx, float hy, float hz) {
+        const float t0x = (lx - o.x) * ix, t1x = (hx - o.x) * ix;
+        const float t0y = (ly - o.y) * iy, t1y = (hy - o.y) * iy;
+        const float t0z = (lz - o.z) * iz, t1z = (hz - o.z) * iz;
+        const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+        const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z)) * 1.0000004f;
+        return tn <= tf;
+    };
+    int stack[STACK_SIZE];
+    int sp = 0, cur = 0;
+    int budget = 2 * nt + 8;   // nt <= INT32_MAX / 4 (checked at upload): no overflow
+    while (true) {
+        if (--budget < 0) {
+            *overflow = true;
+            return nh;
+        }
+        const float4* nd = nodes + 4 * (size_t)cur;
+        const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+        bool h0 = box(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+        bool h1 = box(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+        const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+        if (h0 && c0 < 0) {
+            leaf(~c0);
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            leaf(~c1);
+            h1 = false;
+        }
+        if (h0 && h1) {
+            if (sp < STACK_SIZE) stack[sp++] = c1;
+            else *overflow = true;
+            cur = c0;
+        } else if (h0) {
+            cur = c0;
+        } else if (h1) {
+            cur = c1;
+        } else {
+            if (sp == 0) return nh;
+            cur = stack[--sp];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ kernel
+template <bool MESH>
 __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
     __shared__ unsigned long long s_cnt[6];
     if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
@@ -279,6 +418,51 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
             const float cb = dot(d, e) / dn, sb = rho / dn;
             const f3 u{cp * t0.x + sp * n0.x, cp * t0.y + sp * n0.y, cp * t0.z + sp * n0.z};
             const f3 ks = u * sb + e * cb;
+            if (MESH) {
+                // mesh measurement surface: the incident segment once, then every
+                // crossing of the diffracted ray with its own visibility, weighting
+                // factor on the triangle's plane, UTD field at its distance and 1/A
+                ++c_seg;
+                const float vm = fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)));
+                const float eps = fmaxf(1.0f, vm) * 0x1p-16f;
+                const f3 si = d * (1.0f / dn);
+                code = segment_blocked(A, s, si, eps, dn - eps, W.tri0, W.trin, c_nodes, c_tris, overflow) ? 1 : 0;
+                cxi = 0;
+                cyi = 0;
+                if (code == 0) {
+                    Crossing hits[MAX_CROSS];
+                    const int nh = surface_hits(A.snodes, A.stris, A.snt, A.snlarge, v, ks, hits, &overflow);
+                    cxi = nh;
+                    const float nw_ = W.n;
+                    const float phi = u2 * nw_ * PI_F;
+                    const f3 dkx = (e * sb - u * cb) * (sb / dn);
+                    const f3 dkp{sb * (cp * n0.x - sp * t0.x), sb * (cp * n0.y - sp * t0.y),
+                                 sb * (cp * n0.z - sp * t0.z)};
+                    const unsigned long long mb = (unsigned long long)txi * A.ncell;
+#pragma unroll 1
+                    for (int c = 0; c < nh; ++c) {
+                        const float tc = hits[c].t;
+                        if (segment_blocked(A, v, ks, eps, tc, W.tri0, W.trin, c_nodes, c_tris, overflow)) continue;
+                        // weighting factor on the plane n.(t - a) = 0: dtc/dq = -(n.dv/dq + tc n.dk/dq) / (n.k)
+                        const f3 nc = hits[c].nrm;
+                        const float nk = dot(nc, ks);
+                        if (nk == 0.0f) continue;
+                        const float dtcx = -(dot(nc, e) + tc * dot(nc, dkx)) / nk;
+                        const float dtcp = -(tc * dot(nc, dkp)) / nk;
+                        const f3 tx = e + ks * dtcx + dkx * tc;
+                        const f3 tp = ks * dtcp + dkp * tc;
+                        const f3 cr = cross(tx, tp);
+                        const float J = sqrtf(dot(cr, cr));
+                        const float pw = diffracted_power(A, T, s, v, e, n0, nn, t0, m0, mn, nw_, phi, sb, si, dn, tc);
+                        const float spread = 1.0f / (dn * tc * (dn + tc));
+                        const float inv_area = 2.0f / sqrtf(dot(nc, nc));
+                        const float value =
+                            A.lam4pi2_over_cell2 * (W.length * nw_ * PI_F / (float)A.ns) * J * pw * spread * inv_area;
+                        atomicAdd(A.maps64 + mb + (unsigned long long)hits[c].tri, (double)value);
+                        ++c_dep;
+                    }
+                }
+            } else {
             // plane crossing and cell (as the tracer's deposit)
             const float tc = (A.zm - v.z) / ks.z;
             bool dep = false;
@@ -331,51 +515,8 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
                     // UTD (Eq. diffracted-field): angles from the 0-face, phi of the sample
                     const float nw_ = W.n;
                     const float phi = u2 * nw_ * PI_F;
-                    const f3 sr = s - v;
-                    const f3 srt = sr - e * dot(sr, e);
-                    float phip = atan2f(dot(srt, n0), dot(srt, t0));
-                    if (phip < 0.0f) phip += 2.0f * PI_F;
                     const float sobs = tc;
-                    const float L = sobs * dn / (sobs + dn) * sb * sb;
-                    const float kL = A.k0 * L;
-                    const float pm = 1.0f / (2.0f * nw_ * sqrtf(2.0f * PI_F * A.k0) * sb);
-                    const cf pre = C(-0.70710678118654752f * pm, 0.70710678118654752f * pm);  // -e^{-j pi/4} pm
-                    // D_1..D_4 through one rolled call site (beta = phi -+ phi', pm = +-1)
-                    cf Dq[4];
-#pragma unroll 1
-                    for (int q = 0; q < 4; ++q)
-                        Dq[q] = utd_term(q < 2 ? phi - phip : phi + phip, (q & 1) ? -1.0f : 1.0f, nw_, kL, pre, A);
-                    const f3 phi_i = unit3(cross(si, e));
-                    const f3 beta_i = cross(phi_i, si);
-                    // R_0 and (when the n-face is lit) R_n through one call site
-                    const bool n_lit = (nw_ - 1.0f) * PI_F <= phip;
-                    Mat2 Rf[2];
-#pragma unroll 1
-                    for (int q = 0; q < (n_lit ? 2 : 1); ++q) {
-                        const MatDev& Mq = A.mats[q ? mn : m0];
-                        Rf[q] = face_matrix(q ? nn : n0, C(Mq.eta_re, Mq.eta_im), si, e, phi_i, beta_i);
-                    }
-                    const Mat2& R0 = Rf[0];
-                    Mat2 Rn;
-                    if (n_lit) {
-                        Rn = Rf[1];
-                    } else {
-                        Rn.m[0][0] = Rn.m[1][1] = C(-1.0f);
-                        Rn.m[0][1] = Rn.m[1][0] = C(0.0f);
-                    }
-                    const cf a0 = Dq[3] - Dq[0], an = Dq[2] - Dq[1];
-                    float pw = 0.0f;
-                    for (int p = 0; p < A.npol; ++p) {
-                        cf E[3];
-                        antenna_field(T, A.ant, A.k0, si, A.npol == 2 ? p : T.pol, E);
-                        const cf ein[2] = {edot(phi_i, E), edot(beta_i, E)};
-                        for (int r = 0; r < 2; ++r) {
-                            cf acc = C(0.0f);
-                            for (int c = 0; c < 2; ++c) acc = acc + (a0 * R0.m[r][c] + an * Rn.m[r][c]) * ein[c];
-                            pw += cabs2(acc);
-                        }
-                    }
-                    // (the minus sign of Eq. diffracted-field does not change |E_d|^2)
+                    const float pw = diffracted_power(A, T, s, v, e, n0, nn, t0, m0, mn, nw_, phi, sb, si, dn, sobs);
                     const float spread = 1.0f / (dn * sobs * (dn + sobs));
                     const float value = A.lam4pi2_over_cell2 * (W.length * nw_ * PI_F / (float)A.ns) * J * pw * spread;
                     const unsigned long long mb = (unsigned long long)txi * A.ncell;
@@ -394,6 +535,7 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
                 }
             } else {
                 cxi = cyi = NO_CELL;
+            }
             }
         }
         if (rec) {
@@ -415,21 +557,23 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
 
 }  // namespace
 
-cudaError_t launch_diffraction(const DiffArgs& a, int block, cudaStream_t s, int* grid_out) {
+cudaError_t launch_diffraction(const DiffArgs& a, int block, cudaStream_t s, int* grid_out, bool mesh) {
     if (block <= 0 || block > 256 || (block & 31)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, occ = 0;
     cudaError_t err;
+    const void* k = mesh ? reinterpret_cast<const void*>(&k_diffraction<true>)
+                         : reinterpret_cast<const void*>(&k_diffraction<false>);
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_diffraction, block, 0)) != cudaSuccess)
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, 0)) != cudaSuccess)
         return err;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const unsigned long long need = (a.total + block - 1) / block;
     const unsigned long long cap = (unsigned long long)occ * sms;
     const int grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
     if (grid_out) *grid_out = grid;
-    k_diffraction<<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    void* args[] = {const_cast<DiffArgs*>(&a)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, 0, s);
 }
 
 void faddeeva_coefficients(int N, double* L_out, double* a) {

@@ -93,3 +93,27 @@ def compare_mesh(orc, scene, tx, params, surf_v, surf_t, gpu_map, gpu_record, rt
     assert np.all(err <= bound), (worst, float(rel.max()), int(mask.sum()), rep)
     assert np.all(g[~mask] <= FLOOR)
     return {"worst_rel": float(rel.max()) if rel.size else 0.0, "cells": int(mask.sum()), "report": rep}
+
+
+def compare_diffraction_mesh(orc, scene, tx, params, samples_per_wedge, surf_v, surf_t, gpu_map, gpu_record,
+                             rtol=MAP_RTOL, max_adopt_frac=MAX_ADOPT_FRAC):
+    """Replay the GPU's incident-visibility bits in the FP64 oracle's diffraction
+    map on a mesh surface and compare cell by cell.  Crossings near a triangle's
+    boundary, visibility near ties of the edge-to-crossing segments and a
+    +-1e-5 rad Keller azimuth change are bounded by the oracle's per-cell slack."""
+    rec = np.asarray(gpu_record).reshape(-1, 4)
+    r = orc.diffraction_map_mesh(scene, tx, params, samples_per_wedge, surf_v, surf_t, mode="replay", record=rec,
+                                 slack=True)
+    rep = r["report"]
+    assert rep["failures"] == 0, rep
+    assert rep["adopted_hit"] <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
+    ref = r["map"]
+    g = np.asarray(gpu_map, np.float64).reshape(ref.shape)
+    mask = (ref > FLOOR) | (g > FLOOR)
+    err = np.abs(g - ref)[mask]
+    bound = rtol * ref[mask] + r["slack"][mask]
+    rel = err / np.maximum(ref[mask], 1e-300)
+    worst = float((err / np.maximum(bound, 1e-300)).max()) if err.size else 0.0
+    assert np.all(err <= bound), (worst, float(rel.max()), int(mask.sum()), rep)
+    assert np.all(g[~mask] <= FLOOR)
+    return {"worst_rel": float(rel.max()) if rel.size else 0.0, "cells": int(mask.sum()), "report": rep}

@@ -93,3 +93,35 @@ def test_diffraction_rejects_bad_arguments(api):
                                   None) == L.RM_EINVAL
     assert b"wedge 0" in lib.rm_last_error()
     gs.free()
+
+
+@pytest.mark.parametrize("which", ["box", "manhattan"])
+def test_diffraction_mesh_parity(orc, api, which):
+    """The diffraction map on a rolling mesh surface vs the oracle's replay."""
+    import numpy as np
+    from gpu_helpers import compare_diffraction_mesh
+    from test_oracle_mesh import grid_surface
+    if which == "box":
+        sc = S.single_box(ground=500.0)
+        tx = S.Tx(pos=(-30.0, -20.0, 15.0), num_rays=1)
+        V, T = grid_surface(-50.0, -40.0, 4.0, 30, 30, lambda X, Y: 1.5 + 0.4 * np.sin(X / 6.0) * np.cos(Y / 5.0))
+        spw = 2048
+    else:
+        sc, txs, _ = S.workload(2)
+        tx = txs[0]
+        V, T = grid_surface(-100.0, -100.0, 5.0, 40, 40, lambda X, Y: 1.5 + 0.5 * np.sin(X / 9.0) * np.cos(Y / 7.0))
+        spw = 256
+    p = S.TraceParams(3.5e9, 0)
+    gs = api.Scene.from_obj(sc)
+    su = api.surface(V, T)
+    r = api.diffraction_map_mesh(gs, su, [tx], p, spw, record=True)
+    torch.cuda.synchronize()
+    st = r["stats"]
+    assert st["deposits"] > 1000
+    info = compare_diffraction_mesh(orc, sc, tx, p, spw, V, T, r["maps"][0].cpu().numpy(), r["record"].cpu().numpy())
+    assert info["cells"] > 300
+    q = S.TraceParams(3.5e9, 0, deposit=1)
+    with pytest.raises(RuntimeError, match="box cells"):
+        api.diffraction_map_mesh(gs, su, [tx], q, 16)
+    su.free()
+    gs.free()
