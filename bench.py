@@ -36,7 +36,7 @@ WORKLOAD = ("manhattan seed 2: 10x10 box buildings, 1202 triangles, 4 materials 
             "512x512 map of 1 m cells at z=1.5 m")
 PROFILE = os.path.join(ROOT, "profiles", "k_trace_manhattan_1e7.md")
 # the tracer's code and the tree it walks (the LBVH build decides its node visits)
-TRACE_SOURCES = [os.path.join(ROOT, "paper_2504_21719_b300", "csrc", f) for f in ("trace.cu", "common.cuh", "bvh.cu")]
+TRACE_SOURCES = [os.path.join(ROOT, "paper_2504_21719_b300", "csrc", f) for f in ("trace.cu", "common.cuh", "array.cuh", "bvh.cu")]
 
 
 def parse():
@@ -325,8 +325,9 @@ def _kernel_rate(api, gs, txs, prm, reps=5):
 
 def run_extra(api, S, torch, gpu_name):
     """Batched 64-TX form, forward+adjoint of the differentiable workload, the
-    large city, and the widened model (diffuse reflection, early termination,
-    synthetic arrays) on the Manhattan workload."""
+    large city, the widened model (diffuse reflection, early termination,
+    synthetic arrays, diffraction, mesh surfaces) on the Manhattan workload, and
+    the time-vs-N_S-and-N_A sweep on a street canyon."""
     import numpy as np
 
     out = {}
@@ -488,7 +489,48 @@ def run_extra(api, S, torch, gpu_name):
                          "tris_per_segment": round(f["stats"]["tris_tested"] / segs, 2)}
     del f, a, g
     gs.free()
+    out["time_vs_samples_and_antennas"] = sweep_samples_antennas(api, S, torch, gpu_name)
     return out
+
+
+def sweep_samples_antennas(api, S, torch, gpu_name, n_s=(10**6, 10**7, 10**8, 10**9), n_a=(1, 16, 128, 1024)):
+    """Radio-map time of one transmitter 20 m above a street canyon as the number of
+    samples N_S and of transmit-array elements N_A grow (the timing study of
+    Sec. 4.5): depth 5, 3.5 GHz, 256 x 256 cells of 1 m, half-wavelength ULA with
+    uniform precoding (N_A = 1: a single antenna).  Kernel time and the wall time
+    of the `trace()` call, milliseconds, medians of two calls after one warm-up."""
+    sc = S.street_canyon()
+    gs = api.Scene.from_obj(sc)
+    p = S.TraceParams(3.5e9, 5, cell_size=1.0, nx=256, ny=256)
+    blk, bps, qch, rfm = tuned(gpu_name, "manhattan")
+    prm = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
+    kern, call, segs = [], [], []
+    for ns in n_s:
+        kr, cr, sr = [], [], []
+        for na in n_a:
+            tx = S.Tx(pos=(0.0, 0.0, 20.0), num_rays=ns, seed=11)
+            if na > 1:
+                tx.ant_pos, tx.precoding = S.uniform_linear_array(na, p.freq_hz, 0.5)
+            km, cm = [], []
+            for i in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = api.trace(gs, [tx], prm)
+                torch.cuda.synchronize()
+                if i:
+                    cm.append((time.perf_counter() - t0) * 1e3)
+                    km.append(r["stats"]["kernel_ms"])
+            kr.append(round(statistics.median(km), 3))
+            cr.append(round(statistics.median(cm), 3))
+            sr.append(r["stats"]["segments"])
+            del r
+        kern.append(kr)
+        call.append(cr)
+        segs.append(sr)
+    gs.free()
+    return {"scene": sc.name, "triangles": sc.nt, "N_S": list(n_s), "N_A": list(n_a),
+            "kernel_ms": kern, "call_ms": call, "segments": segs,
+            "setting": "TX 20 m above the street, depth 5, 3.5 GHz, 256 x 256 x 1 m map, ULA along y"}
 
 
 # ----------------------------------------------------------------------------- reference arm

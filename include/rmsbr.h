@@ -110,13 +110,19 @@ typedef struct {
     uint64_t seed;       /* seed of the counter-based interaction sampler */
     /* Synthetic array (Sec. 4.5): n_ant elements at ant_pos_host [n_ant][3] (m,
      * antenna frame, rotated with the antenna) with complex precoding weights
-     * precoding_host [n_ant][2] (re, im).  Each ray's launch field is scaled by
+     * precoding_host [n_ant][2] (re, im), both in double (phases reach k0 |d|,
+     * ~1600 rad for a 1024-element half-wavelength array, so positions keep
+     * double precision until the library splits them into hi + lo floats).
+     * Each ray's launch field is scaled by
      * alpha = sum_k u_P,k exp(j 2 pi / lambda0 k.d_k) (array response vector,
-     * Eq. path-solver-array-response-vector).  n_ant = 0: one antenna. */
+     * Eq. path-solver-array-response-vector), evaluated at the ray's lattice
+     * direction in double-float arithmetic; elements on one regular line
+     * (uniform linear arrays) take a blocked Horner recurrence.
+     * n_ant = 0: one antenna.  The host arrays are read during the call only. */
     int32_t n_ant;
     int32_t reserved;
-    const float* ant_pos_host;
-    const float* precoding_host;
+    const double* ant_pos_host;
+    const double* precoding_host;
 } rm_tx;
 
 /* trace flags */

@@ -330,7 +330,7 @@ def radio_map(scene, tx, params, mode: str = "plain", record=None, want_record: 
     em = None if eval_mats is None else np.ascontiguousarray(np.asarray(eval_mats, np.float64)[:, :2])
     mp = np.empty((params.ny, params.nx), np.float64)
     st = np.empty(3 * (L + 1), np.float64) if stats else None
-    ms = np.empty((2, params.ny, params.nx), np.float64) if mass else None
+    ms = np.empty((3, params.ny, params.nx), np.float64) if mass else None
     rep = OrReport()
     sc = _scat(scene)
     rc = lib().or_radio_map(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), _p(sc), C.byref(otx),
@@ -347,7 +347,7 @@ def radio_map(scene, tx, params, mode: str = "plain", record=None, want_record: 
     if mode == "replay":
         out["report"] = rep.as_dict()
     if mass:
-        out["mass"], out["cmass"] = ms[0], ms[1]
+        out["mass"], out["cmass"], out["amass"] = ms[0], ms[1], ms[2]
     return out
 
 

@@ -566,6 +566,10 @@ struct Sink<double> {
     DepList* mass = nullptr;   // unweighted deposit value per stencil cell (bilinear error bound)
     DepList* cmass = nullptr;  // the same, times the crossing's conditioning factor
     DepList* slack = nullptr;  // mesh surfaces: values of crossings within tol of a cell's boundary
+    DepList* amass = nullptr;  // values times the ray's array-factor conditioning (synthetic arrays)
+    double acond = 0.0;        // that factor for the ray being traced
+    bool want_acond() const { return amass != nullptr; }
+    void set_acond(double c) { acond = c; }
     void add(int cell, const double& v) { list->cell.push_back(cell); list->val.push_back(v); }
     void add_slack(int cell, double v) {
         if (slack) { slack->cell.push_back(cell); slack->val.push_back(v); }
@@ -573,6 +577,7 @@ struct Sink<double> {
     void add_mass(int cell, const double& v, double cond) {
         if (mass) { mass->cell.push_back(cell); mass->val.push_back(v); }
         if (cmass) { cmass->cell.push_back(cell); cmass->val.push_back(v * cond); }
+        if (amass && acond > 0.0) { amass->cell.push_back(cell); amass->val.push_back(v * acond); }
     }
 };
 template <>
@@ -585,6 +590,8 @@ struct Sink<D> {
     }
     void add_mass(int, const D&, double) {}
     void add_slack(int, double) {}
+    bool want_acond() const { return false; }
+    void set_acond(double) {}
 };
 
 // cond: first-order conditioning of the crossing point x_c = o + t_c k against
@@ -707,6 +714,40 @@ std::complex<double> array_factor(const TxC& T, const V3<double>& k, double k0) 
         a += T.prec[i] * std::complex<double>(std::cos(ph), std::sin(ph));
     }
     return a;
+}
+
+// Array-factor conditioning (test bookkeeping only; it does not enter the map).
+// A deposit's value is |alpha|^2 times the single-antenna value; an FP32
+// evaluation of alpha that carries the direction and each element's phase in
+// double-float (hi + lo) arithmetic keeps, per element:
+//   - a direction error below 2^-40 per component, i.e. a phase error below
+//     k0 2^-40 |d_i|_1;
+//   - the rounding of the reduced phase (a few units of 2^-24 pi) and of the
+//     sine and cosine (2^-22);
+//   - when elements on a regular line are summed by a Horner recurrence in
+//     blocks of B = 16, the powers z^m (m < B) of z = exp(j k0 k.delta):
+//     m (2^-24 pi + 2^-23 + 4 * 2^-24) of phase and modulus;
+// and the sums over N elements add (B + N / B + 2) 2^-24 sum_i |w_i|.  With
+//   delta = sum_i |w_i| eps_i + (B + N / B + 2) 2^-24 sum_i |w_i|,
+//   eps_i = 15 (2^-24 pi + 2^-23 + 2^-22) + 8 pi 2^-24 + 2^-22 + k0 2^-40 |d_i|_1,
+// |alpha|^2 moves by at most 2 |alpha| delta + delta^2; the factor returned is
+// that over |alpha|^2 (0 for a single antenna).
+double array_cond(const TxC& T, const V3<double>& k, double k0, const std::complex<double>& a) {
+    (void)k;
+    if (T.ant.empty()) return 0.0;
+    const double u = 0x1p-24, B = 16.0;
+    const double eps0 = 15.0 * (u * PI + 2.0 * u + 4.0 * u) + 8.0 * PI * u + 4.0 * u;
+    double sw = 0.0, ew = 0.0;
+    for (size_t i = 0; i < T.ant.size(); ++i) {
+        const V3<double>& d = T.ant[i];
+        const double aw = std::abs(T.prec[i]);
+        sw += aw;
+        ew += aw * (eps0 + k0 * 0x1p-40 * (std::fabs(d.x) + std::fabs(d.y) + std::fabs(d.z)));
+    }
+    const double n = (double)T.ant.size();
+    const double delta = ew + (B + n / B + 2.0) * u * sw;
+    const double a2 = std::norm(a);
+    return (2.0 * std::sqrt(a2) * delta + delta * delta) / std::max(a2, 1e-300);
 }
 
 TxC make_txc(const or_tx& t) {
@@ -867,6 +908,7 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
     V3<double> k = fibonacci_dir(n, tx.N);
     CV3<R> E[2];
     const std::complex<double> alpha = array_factor(tx, k, C.k0);
+    if (sink.want_acond()) sink.set_acond(array_cond(tx, k, C.k0, alpha));
     for (int p = 0; p < npol; ++p) {
         int pol = (tx.pol == 2) ? p : tx.pol;
         V3<double> f = tx_field(k, tx.R, tx.pattern, pol);
@@ -1415,9 +1457,10 @@ void or_closest_hit(const float* verts, int64_t nv, const int32_t* tris, int64_t
 // eval_mats likewise overrides the materials the fields are evaluated with.
 // map_out [ny][nx] is overwritten.  stats (or null): per depth 0..L
 // [power, power^2, escaped power] sums of w |E|^2 (without the 4 pi / N factor).
-// mass_out (or null) [2][ny][nx]: per cell, the sum of the unweighted values
-// of the deposits whose stencil covers it, and the same sum with every value
-// multiplied by its crossing's conditioning factor (test error bounds).
+// mass_out (or null) [3][ny][nx]: per cell, the sum of the unweighted values
+// of the deposits whose stencil covers it, the same sum with every value
+// multiplied by its crossing's conditioning factor, and with every value
+// multiplied by its ray's array-factor conditioning (test error bounds).
 int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                  const int32_t* tri_mat, const float* mats, int nm, const float* scat, const or_tx* tx,
                  const or_params* P, int mode, int32_t* rec, const double* sampling_mats,
@@ -1454,7 +1497,8 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
     const int L = P->max_depth;
     const int64_t CH = 2048;  // fixed chunking: the summation order is independent of threads
     const int64_t nch = (cnt + CH - 1) / CH;
-    std::vector<DepList> lists(nch), masses(mass_out ? nch : 0), cmasses(mass_out ? nch : 0);
+    std::vector<DepList> lists(nch), masses(mass_out ? nch : 0), cmasses(mass_out ? nch : 0),
+        amasses(mass_out ? nch : 0);
     const int nthr = or_num_threads();
     std::vector<double> st((size_t)nthr * 3 * (L + 1), 0.0);
     std::vector<ReplayState> rss(nch);
@@ -1468,6 +1512,7 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
 #endif
         double* sp = stats ? st.data() + (size_t)tid * 3 * (L + 1) : nullptr;
         Sink<double> sink{&lists[c], mass_out ? &masses[c] : nullptr, mass_out ? &cmasses[c] : nullptr};
+        sink.amass = mass_out ? &amasses[c] : nullptr;
         int64_t e = std::min(cnt, (c + 1) * CH);
         for (int64_t i = c * CH; i < e; ++i) {
             int64_t n = tx->ray_begin + i * tx->ray_stride;
@@ -1481,10 +1526,12 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
         for (size_t j = 0; j < lists[c].cell.size(); ++j) map_out[lists[c].cell[j]] += lists[c].val[j];
     if (mass_out) {
         const size_t nc = (size_t)P->nx * P->ny;
-        std::memset(mass_out, 0, sizeof(double) * 2 * nc);
+        std::memset(mass_out, 0, sizeof(double) * 3 * nc);
         for (int64_t c = 0; c < nch; ++c) {
             for (size_t j = 0; j < masses[c].cell.size(); ++j) mass_out[masses[c].cell[j]] += masses[c].val[j];
             for (size_t j = 0; j < cmasses[c].cell.size(); ++j) mass_out[nc + cmasses[c].cell[j]] += cmasses[c].val[j];
+            for (size_t j = 0; j < amasses[c].cell.size(); ++j)
+                mass_out[2 * nc + amasses[c].cell[j]] += amasses[c].val[j];
         }
     }
     if (stats) {

@@ -56,9 +56,9 @@ def tx_struct(pos, num_rays, yaw=0.0, pitch=0.0, roll=0.0, pol=0, pattern=0, ray
               ray_stride=1, seed=0, ant_pos=None, precoding=None) -> L.rm_tx:
     t = L.rm_tx()
     if ant_pos is not None and len(ant_pos):
-        a = np.ascontiguousarray(np.asarray(ant_pos, np.float64).reshape(-1, 3), np.float32)
+        a = np.ascontiguousarray(np.asarray(ant_pos, np.float64).reshape(-1, 3))
         w = np.asarray(precoding, np.complex128).reshape(-1)
-        pc = np.ascontiguousarray(np.stack([w.real, w.imag], 1), np.float32)
+        pc = np.ascontiguousarray(np.stack([w.real, w.imag], 1), np.float64)
         t._keep = (a, pc)  # the buffers live as long as the struct
         t.n_ant = len(a)
         t.ant_pos_host = a.ctypes.data
@@ -109,6 +109,8 @@ def params_from(obj, stats=False, block_size=0, blocks_per_sm=0, queue_chunk=0, 
 def _tx_array(txs):
     txs = [t if isinstance(t, L.rm_tx) else tx_from(t) for t in txs]
     arr = (L.rm_tx * len(txs))(*txs)
+    # the copies in arr point at the antenna buffers that the structs keep alive
+    arr._keep = [getattr(t, "_keep", None) for t in txs]
     return arr, len(txs)
 
 

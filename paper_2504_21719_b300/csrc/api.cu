@@ -262,6 +262,66 @@ void rotation(double a, double b, double g, float* R) {
                          -sb,     cb * sg,                cb * cg};
     for (int i = 0; i < 9; ++i) R[i] = (float)M[i];
 }
+// The synthetic-array table of one transmitter (layout in array.cuh): element
+// positions rotated with the antenna (R d), scaled to d' = 2 d / lambda0 and
+// split into hi + lo floats, in double.  Elements on one regular line (to
+// 1e-8 lambda0) are stored as a uniform linear array: d'_0, the spacing, and
+// the weights packed in pairs.
+void pack_array(const rm_tx& x, double lam, TxDev& d, std::vector<AntDev>& out) {
+    const int n = x.n_ant;
+    d.ant_mode = 0;
+    if (n <= 0) return;
+    const double ca = std::cos(x.yaw), sa = std::sin(x.yaw), cb = std::cos(x.pitch), sb = std::sin(x.pitch),
+                 cg = std::cos(x.roll), sg = std::sin(x.roll);
+    const double M[9] = {ca * cb, ca * sb * sg - sa * cg, ca * sb * cg + sa * sg,
+                         sa * cb, sa * sb * sg + ca * cg, sa * sb * cg - ca * sg,
+                         -sb,     cb * sg,                cb * cg};
+    std::vector<double> g((size_t)3 * n);
+    for (int a = 0; a < n; ++a) {
+        const double* l = x.ant_pos_host + 3 * a;
+        for (int i = 0; i < 3; ++i) g[3 * a + i] = (M[3 * i] * l[0] + M[3 * i + 1] * l[1] + M[3 * i + 2] * l[2]) * 2.0 / lam;
+    }
+    auto split = [](const double* v, AntDev& e) {
+        for (int i = 0; i < 3; ++i) {
+            e.dh[i] = (float)v[i];
+            e.dl[i] = (float)(v[i] - (double)e.dh[i]);
+        }
+    };
+    bool ula = n >= 2;
+    double step[3] = {0.0, 0.0, 0.0};
+    if (ula) {
+        for (int i = 0; i < 3; ++i) step[i] = (g[3 * (n - 1) + i] - g[i]) / (n - 1);
+        for (int a = 0; a < n && ula; ++a)
+            for (int i = 0; i < 3; ++i)
+                if (std::fabs(g[3 * a + i] - (g[i] + a * step[i])) > 2e-8) ula = false;
+    }
+    if (ula) {
+        d.ant_mode = 1;
+        AntDev h0{}, h1{};
+        split(g.data(), h0);
+        split(step, h1);
+        out.push_back(h0);
+        out.push_back(h1);
+        for (int a = 0; a < n; a += 4) {
+            AntDev w{};
+            float* f = reinterpret_cast<float*>(&w);
+            for (int j = 0; j < 4 && a + j < n; ++j) {
+                f[2 * j] = (float)x.precoding_host[2 * (a + j)];
+                f[2 * j + 1] = (float)x.precoding_host[2 * (a + j) + 1];
+            }
+            out.push_back(w);
+        }
+        return;
+    }
+    for (int a = 0; a < n; ++a) {
+        AntDev e{};
+        e.pre = (float)x.precoding_host[2 * a];
+        e.pim = (float)x.precoding_host[2 * a + 1];
+        split(&g[3 * a], e);
+        out.push_back(e);
+    }
+}
+
 
 void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
              const rm_material* sampling_override, Prepared* P, const rm_scene* surf = nullptr) {
@@ -319,23 +379,7 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
         d.perm_m = d.count > 0 ? ~0ULL / d.count : 0;
         d.n_ant = tx[t].n_ant;
         d.ant_begin = (int32_t)P->ant.size();
-        for (int a = 0; a < tx[t].n_ant; ++a) {
-            // element position rotated with the antenna (R d), in double, then FP32
-            const double lx = tx[t].ant_pos_host[3 * a], ly = tx[t].ant_pos_host[3 * a + 1],
-                         lz = tx[t].ant_pos_host[3 * a + 2];
-            const double ca = std::cos(tx[t].yaw), sa = std::sin(tx[t].yaw), cb = std::cos(tx[t].pitch),
-                         sb = std::sin(tx[t].pitch), cg = std::cos(tx[t].roll), sg = std::sin(tx[t].roll);
-            const double M[9] = {ca * cb, ca * sb * sg - sa * cg, ca * sb * cg + sa * sg,
-                                 sa * cb, sa * sb * sg + ca * cg, sa * sb * cg - ca * sg,
-                                 -sb,     cb * sg,                cb * cg};
-            AntDev e{};
-            e.dx = (float)(M[0] * lx + M[1] * ly + M[2] * lz);
-            e.dy = (float)(M[3] * lx + M[4] * ly + M[5] * lz);
-            e.dz = (float)(M[6] * lx + M[7] * ly + M[8] * lz);
-            e.pre = tx[t].precoding_host[2 * a];
-            e.pim = tx[t].precoding_host[2 * a + 1];
-            P->ant.push_back(e);
-        }
+        pack_array(tx[t], lam, d, P->ant);
         work += d.count;
         rec += d.count * (unsigned long long)(p->max_depth + 1);
     }

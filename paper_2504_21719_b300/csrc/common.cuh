@@ -40,7 +40,7 @@ struct TxDev {
     float R[9];                  // antenna orientation, row-major
     int32_t pattern, pol;
     float dep_scale;             // (4 pi / (N Delta^2)) (lambda0 / 4 pi)^2
-    float pad;
+    int32_t ant_mode;            // synthetic array table: 0 one record per element, 1 uniform linear array
     unsigned long long N;        // lattice size
     unsigned long long begin, stride, count;
     unsigned long long work_begin;  // first work item of this transmitter
@@ -51,10 +51,14 @@ struct TxDev {
     int32_t n_ant, ant_begin;       // synthetic array elements in the antenna table
 };
 
-// One element of a synthetic transmit array: position in the global frame
-// (relative to the array centre) and complex precoding weight.
+// One element of a synthetic transmit array: complex precoding weight and
+// position in the global frame in units of lambda0 / 2 (d' = 2 d / lambda0,
+// so that k.d' is the phase in units of pi) as hi + lo floats.  A uniform
+// linear array stores d'_0 and the spacing in two such records, then its
+// weights packed as float2 pairs (array.cuh).
 struct AntDev {
-    float dx, dy, dz, pre, pim, pad0, pad1, pad2;
+    float pre, pim;
+    float dh[3], dl[3];
 };
 
 // Scratch of one trace launch (zeroed before the launch).

@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "array.cuh"
 #include "vec.cuh"
 
 namespace rmsbr {
@@ -132,7 +133,7 @@ __device__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float
 // ------------------------------------------------------------------ antenna field
 // R (C_theta theta' + C_phi phi') in direction k (App. A.1) times the
 // synthetic-array factor alpha = sum_k u_P,k exp(j k0 k.d_k) (Sec. 4.5).
-__device__ void antenna_field(const TxDev& T, const AntDev* __restrict__ ant, float k0, f3 k, int pol, cf* E) {
+__device__ void antenna_field(const TxDev& T, const AntDev* __restrict__ ant, f3 k, int pol, cf* E) {
     const float lx = T.R[0] * k.x + T.R[3] * k.y + T.R[6] * k.z;
     const float ly = T.R[1] * k.x + T.R[4] * k.y + T.R[7] * k.z;
     const float lz = T.R[2] * k.x + T.R[5] * k.y + T.R[8] * k.z;
@@ -145,18 +146,7 @@ __device__ void antenna_field(const TxDev& T, const AntDev* __restrict__ ant, fl
     const float g = (T.pattern == 1) ? 1.2247448713915890f * sxy : 1.0f;
     const f3 e = pol == 0 ? f3{lz * cph, lz * sph, -sxy} : f3{-sph, cph, 0.0f};
     float are = 1.0f, aim = 0.0f;
-    if (T.n_ant > 0) {
-        are = 0.0f;
-        // phase k0 k.d as a multiple of pi: sincospif reduces exactly
-        const float k0pi = k0 * 0.318309886183790672f;
-        for (int a = 0; a < T.n_ant; ++a) {
-            const AntDev el = ant[T.ant_begin + a];
-            float sn, cs;
-            sincospif(k0pi * (k.x * el.dx + k.y * el.dy + k.z * el.dz), &sn, &cs);
-            are += el.pre * cs - el.pim * sn;
-            aim += el.pre * sn + el.pim * cs;
-        }
-    }
+    if (T.n_ant > 0) array_factor_dir(T, ant, k.x, k.y, k.z, are, aim);
     const float ex = g * (T.R[0] * e.x + T.R[1] * e.y + T.R[2] * e.z);
     const float ey = g * (T.R[3] * e.x + T.R[4] * e.y + T.R[5] * e.z);
     const float ez = g * (T.R[6] * e.x + T.R[7] * e.y + T.R[8] * e.z);
@@ -266,7 +256,7 @@ __device__ __forceinline__ float diffracted_power(const DiffArgs& A, const TxDev
     float pw = 0.0f;
     for (int p = 0; p < A.npol; ++p) {
         cf E[3];
-        antenna_field(T, A.ant, A.k0, si, A.npol == 2 ? p : T.pol, E);
+        antenna_field(T, A.ant, si, A.npol == 2 ? p : T.pol, E);
         const cf ein[2] = {edot(phi_i, E), edot(beta_i, E)};
         for (int r = 0; r < 2; ++r) {
             cf acc = C(0.0f);

@@ -30,6 +30,7 @@
 #include <cfloat>
 
 #include "common.cuh"
+#include "array.cuh"
 #include "vec.cuh"
 
 namespace rmsbr {
@@ -756,21 +757,10 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                         if (sxy > 0.0f) { cph = lx / sxy; sph = ly / sxy; }
                         const float g = (T.pattern == 1) ? 1.2247448713915890f * sxy : 1.0f;
                         const f3 th_l{lz * cph, lz * sph, -sxy}, ph_l{-sph, cph, 0.0f};
-                        // synthetic array (Sec. 4.5): alpha = sum_k u_P,k exp(j k0 k.d_k)
+                        // synthetic array (Sec. 4.5): alpha = sum_k u_P,k exp(j k0 k.d_k) at the
+                        // lattice direction rebuilt in double-float (array.cuh)
                         float are = 1.0f, aim = 0.0f;
-                        if (T.n_ant > 0) {
-                            are = 0.0f;
-                            // phase k0 k.d as a multiple of pi: sincospif reduces exactly
-                            const float k0pi = A.k0 * 0.318309886183790672f;
-#pragma unroll 1
-                            for (int a = 0; a < T.n_ant; ++a) {
-                                const AntDev el = A.ant[T.ant_begin + a];
-                                float sn, cs;
-                                sincospif(k0pi * (r.kx * el.dx + r.ky * el.dy + r.kz * el.dz), &sn, &cs);
-                                are += el.pre * cs - el.pim * sn;
-                                aim += el.pre * sn + el.pim * cs;
-                            }
-                        }
+                        if (T.n_ant > 0) array_factor_lattice(T, A.ant, n, are, aim);
                         for (int p = 0; p < NPOL; ++p) {
                             const int pol = (NPOL == 2) ? p : T.pol;
                             const f3 e = pol == 0 ? th_l : ph_l;

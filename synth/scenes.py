@@ -213,6 +213,33 @@ def manhattan(seed: int = 2, n_building_mats: int = 3, nblocks: int = 10,
                  np.array(mats, np.float32), fps)
 
 
+def street_canyon(seed: int = 7, per_side: int = 6, length: float = 30.0, gap: float = 10.0,
+                  depth: float = 20.0, street: float = 20.0, hmin: float = 15.0, hmax: float = 40.0,
+                  ground_half: float = 300.0) -> Scene:
+    """A straight street along x (width `street`, centred on y = 0) lined on each
+    side by `per_side` box buildings of `length` x `depth` m with `gap` m between
+    them, on a ground plane: a seeded stand-in for a small street-canyon scene.
+
+    Draw order: heights U(hmin, hmax), south row then north row, west to east.
+    Material 0 is the ground half-space, material 1 the building walls."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    heights = rng.uniform(hmin, hmax, size=2 * per_side)
+    mats = [GROUND, (5.24, 0.123, WALL_THICKNESS)]
+    mb = _MeshBuilder()
+    gv, gt = _quad_ground(ground_half)
+    mb.add(gv, gt, 0)
+    span = per_side * length + (per_side - 1) * gap
+    fps = []
+    for row, (y0, y1) in enumerate([(-0.5 * street - depth, -0.5 * street), (0.5 * street, 0.5 * street + depth)]):
+        for i in range(per_side):
+            x0 = -0.5 * span + i * (length + gap)
+            bv, bt = _box(x0, x0 + length, y0, y1, 0.0, float(heights[row * per_side + i]))
+            mb.add(bv, bt, 1)
+            fps.append((x0, x0 + length, y0, y1))
+    v, t, m = mb.build()
+    return Scene(f"street_canyon(seed={seed})", v, t, m, np.array(mats, np.float32), fps)
+
+
 def procedural_city(seed: int = 5, ncells: int = 210, cell: float = 19.0,
                     jitter: float = 1.5, nmin: int = 4, nmax: int = 12,
                     rmin: float = 4.0, rmax: float = 8.0, h_median: float = 20.0,

@@ -23,7 +23,8 @@ def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max
     L = params.max_depth
     rec = np.asarray(gpu_record).reshape(tx.count(), L + 1, 4)
     bil = params.deposit == 1
-    r = orc.radio_map(scene, tx, params, mode="replay", record=rec, mass=bil)
+    arr = getattr(tx, "ant_pos", None) is not None and len(tx.ant_pos) > 0
+    r = orc.radio_map(scene, tx, params, mode="replay", record=rec, mass=bil or arr)
     rep = r["report"]
     assert rep["failures"] == 0, rep
     adopted = rep["adopted_hit"] + rep["adopted_cell"] + rep["adopted_decision"]
@@ -35,12 +36,20 @@ def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max
     bound = rtol * ref[mask]
     if bil:
         bound = bound + 2.0 * POS_EPS / params.cell_size * r["cmass"][mask]
+    if arr:
+        # FP32 array factor: first-order propagation of the kernel's direction
+        # and phase roundings through |alpha|^2 (the oracle's array conditioning)
+        bound = bound + r["amass"][mask]
     rel = err / np.maximum(ref[mask], 1e-300)
     worst = float((err / np.maximum(bound, 1e-300)).max()) if err.size else 0.0
     assert np.all(err <= bound), (worst, float(rel.max()), int(mask.sum()), rep)
     assert np.all(g[~mask] <= FLOOR)
-    return {"worst_rel": float(rel.max()) if rel.size else 0.0, "worst_vs_bound": worst,
-            "cells": int(mask.sum()), "report": rep}
+    out = {"worst_rel": float(rel.max()) if rel.size else 0.0, "worst_vs_bound": worst,
+           "cells": int(mask.sum()), "report": rep}
+    if arr:
+        # the array bound is a worst case; report how many cells meet the plain tolerance
+        out["frac_within_rtol"] = float(np.mean(err <= rtol * ref[mask])) if err.size else 1.0
+    return out
 
 
 def compare_diffraction(orc, scene, tx, params, samples_per_wedge, gpu_map, gpu_record, rtol=MAP_RTOL,

@@ -115,3 +115,27 @@ def test_no_fallback_when_library_missing(L, tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
     finally:
         _lib._lib = saved
+
+
+def test_tx_array_keeps_antenna_buffers_alive(L):
+    """The rm_tx copies handed to the library point at the binding's antenna
+    buffers (double positions and precoding); those must outlive the
+    temporary structs the binding builds from user objects."""
+    import gc
+
+    import numpy as np
+
+    from paper_2504_21719_b300 import api
+    from synth import scenes as S
+    tx = S.Tx(pos=(0.0, 0.0, 20.0), num_rays=1000, seed=1)
+    tx.ant_pos, tx.precoding = S.uniform_linear_array(1024, 3.5e9, 0.5)
+    arr, n = api._tx_array([tx])
+    gc.collect()
+    junk = [np.full(2048, 7.0) for _ in range(64)]  # reuse freed blocks, if any
+    t = arr[0]
+    assert n == 1 and t.n_ant == 1024
+    pos = np.ctypeslib.as_array(C.cast(t.ant_pos_host, C.POINTER(C.c_double)), shape=(1024, 3))
+    pre = np.ctypeslib.as_array(C.cast(t.precoding_host, C.POINTER(C.c_double)), shape=(1024, 2))
+    assert np.array_equal(pos, tx.ant_pos)
+    assert np.array_equal(pre[:, 0] + 1j * pre[:, 1], tx.precoding)
+    del junk
