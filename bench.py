@@ -166,7 +166,7 @@ def oracle_sample(target_s: float = 15.0, max_rays: int = 10_000_000):
     stride = max(1, tx.num_rays // rays)
     segs, dt, n = run(stride, 1)
     return {"value": segs / dt, "unit": "segments/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"workload lattice subset: every {stride}th of 1e7 rays ({n} rays, {segs} segments, "
+            "sample": f"workload lattice subset: 1 in {stride} of 1e7 rays ({n} rays, {segs} segments, "
                       f"{dt:.1f} s), FP64 brute force over 1202 triangles"}
 
 
@@ -552,7 +552,7 @@ def run_reference(args, world, rank):
             times.append(dt)
             segs.append(int((r["record"][:, :, 0] != -2).sum()))
     value = sum(segs) / sum(times)
-    sample = (f"per step: every {stride}th ray of the 1e7-ray lattice ({tx.count()} rays), FP64 brute force over "
+    sample = (f"per step: 1 in {stride} rays of the 1e7-ray lattice ({tx.count()} rays), FP64 brute force over "
               f"{sc.nt} triangles, OpenMP")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 2),
