@@ -202,6 +202,17 @@ rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tri
                           const int32_t* tri_mat_dev, const rm_material* mats_host, int32_t nm,
                           void* stream, rm_scene** out);
 
+/* The same from host arrays (verts_host float [nv][3], tris_host int32 [nt][3],
+ * tri_mat_host int32 [nt]): index ranges are checked on the host (RM_EINVAL
+ * before any device work), the mesh is copied into a library-owned pinned
+ * buffer and sent to the device in one asynchronous copy on `stream`; the call
+ * does not wait for it.  Caller buffers may be freed after return.  With
+ * rm_bvh_build, which does not wait either, a scene reaches the tracer with no
+ * host round trip. */
+rm_status rm_scene_upload_host(const float* verts_host, int64_t nv, const int32_t* tris_host, int64_t nt,
+                               const int32_t* tri_mat_host, const rm_material* mats_host, int32_t nm,
+                               void* stream, rm_scene** out);
+
 /* Replaces the material table (no BVH rebuild).  sampling_host_or_null
  * (nm entries) sets the materials from which the interaction probabilities
  * q(R), q(S), q(T) are computed (detached from the fields); NULL = mats_host.
@@ -217,7 +228,12 @@ rm_status rm_scene_set_materials(rm_scene* scene, const rm_material* mats_host, 
  * and the 64-byte two-child node layout.  Up to 16 triangles as large as a
  * quarter of the scene are kept out of the tree (see rm_bvh_export).  Not part of the paper (its
  * implementation uses Mitsuba's acceleration structure).  Must precede
- * tracing; may be called again after rm_scene_upload only. */
+ * tracing; may be called again after rm_scene_upload only.  The call returns
+ * once the build is enqueued: the host does not wait for it.  The number of
+ * large triangles comes back through a pinned slot and the first call that
+ * needs it (a trace, rm_bvh_export, rm_scene_info) waits for the build there;
+ * errors of the build's kernels surface at that call.  Without a free pinned
+ * slot (4096 builds pending at once) the call waits for the build itself. */
 rm_status rm_bvh_build(rm_scene* scene, void* stream);
 
 /* Exports the built tree for inspection (synchronous).  Host outputs:

@@ -74,6 +74,7 @@ class rm_wedge(C.Structure):
 P = C.c_void_p
 _SIGS = {
     "rm_scene_upload": ([P, C.c_int64, P, C.c_int64, P, P, C.c_int32, P, C.POINTER(P)], C.c_int),
+    "rm_scene_upload_host": ([P, C.c_int64, P, C.c_int64, P, P, C.c_int32, P, C.POINTER(P)], C.c_int),
     "rm_scene_set_materials": ([P, P, C.c_int32, P], C.c_int),
     "rm_bvh_build": ([P, P], C.c_int),
     "rm_bvh_export": ([P, P, P, P, P], C.c_int),

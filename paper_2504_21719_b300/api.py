@@ -134,16 +134,32 @@ class Scene:
                 return a.to(device=dev, dtype=dt_t, non_blocking=True).contiguous()
             return torch.as_tensor(np.ascontiguousarray(a, dt_np)).to(dev)
 
-        v = dev_tensor(verts, np.float32, torch.float32)
-        t = dev_tensor(tris, np.int32, torch.int32)
-        m = dev_tensor(tri_mat, np.int32, torch.int32)
         self.nm = int(np.asarray(mats).reshape(-1, 3).shape[0])
-        self.nt = int(t.shape[0])
         self._scat = None if scat is None else np.asarray(scat, np.float64).reshape(-1, 6)
         self._mats = materials(mats, self._scat)
         h = C.c_void_p()
-        _check(lib.rm_scene_upload(_ptr(v), v.shape[0], _ptr(t), self.nt, _ptr(m), self._mats, self.nm,
-                                   _stream(stream), C.byref(h)), "rm_scene_upload")
+        on_host = all(not (isinstance(a, torch.Tensor) and a.is_cuda) for a in (verts, tris, tri_mat))
+        if on_host and dev.type == "cuda":
+            # host arrays: checked on the host, one pinned asynchronous copy, no device round trip
+            def host_array(a, dt_np):
+                if isinstance(a, torch.Tensor):
+                    a = a.numpy()
+                return np.ascontiguousarray(a, dt_np)
+
+            v = host_array(verts, np.float32).reshape(-1, 3)
+            t = host_array(tris, np.int32).reshape(-1, 3)
+            m = host_array(tri_mat, np.int32).reshape(-1)
+            self.nt = int(t.shape[0])
+            _check(lib.rm_scene_upload_host(v.ctypes.data, v.shape[0], t.ctypes.data, self.nt, m.ctypes.data,
+                                            self._mats, self.nm, _stream(stream), C.byref(h)),
+                   "rm_scene_upload_host")
+        else:
+            v = dev_tensor(verts, np.float32, torch.float32)
+            t = dev_tensor(tris, np.int32, torch.int32)
+            m = dev_tensor(tri_mat, np.int32, torch.int32)
+            self.nt = int(t.shape[0])
+            _check(lib.rm_scene_upload(_ptr(v), v.shape[0], _ptr(t), self.nt, _ptr(m), self._mats, self.nm,
+                                       _stream(stream), C.byref(h)), "rm_scene_upload")
         self.handle = h
         if build:
             self.build_bvh(stream)

@@ -25,7 +25,14 @@ struct rm_scene {
     std::vector<rm_material> mats, smats;
     bool has_smats = false;
     bool built = false;
-    int64_t nlarge = 0;          // triangles kept out of the tree (tested from a list)
+    // triangles kept out of the tree (tested from a list).  The build does not
+    // wait for its count: the device copies it into a pinned slot and records
+    // built_ev; the first call that needs it (resolve_nlarge) waits there.
+    mutable int64_t nlarge = 0;
+    mutable bool nlarge_pending = false;
+    mutable int32_t* nlarge_slot = nullptr;
+    mutable cudaEvent_t built_ev = nullptr;
+    mutable std::mutex mu;
     uint64_t* keys = nullptr;
     int32_t* order = nullptr;
     float4* nodes = nullptr;
@@ -120,6 +127,56 @@ rm_status check_device(const rm_scene* sc) {
     return RM_OK;
 }
 
+// Pinned host slots for the large-triangle count of pending builds: one
+// process-wide slab (allocated on first use, kept until exit).
+struct PinPool {
+    std::mutex m;
+    int32_t* slab = nullptr;
+    bool tried = false;
+    std::vector<int> free;
+};
+PinPool g_pin;
+constexpr int PIN_SLOTS = 4096;
+
+int32_t* pin_slot_acquire() {
+    std::lock_guard<std::mutex> g(g_pin.m);
+    if (!g_pin.tried) {
+        g_pin.tried = true;
+        if (cudaHostAlloc((void**)&g_pin.slab, sizeof(int32_t) * PIN_SLOTS, cudaHostAllocPortable) == cudaSuccess)
+            for (int i = PIN_SLOTS - 1; i >= 0; --i) g_pin.free.push_back(i);
+        else
+            g_pin.slab = nullptr;
+    }
+    if (g_pin.free.empty()) return nullptr;
+    const int i = g_pin.free.back();
+    g_pin.free.pop_back();
+    return g_pin.slab + i;
+}
+
+void pin_slot_release(int32_t* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(g_pin.m);
+    g_pin.free.push_back((int)(p - g_pin.slab));
+}
+
+// The large-triangle count of a scene whose build has not been waited for:
+// wait for the build's event, read the slot, release it.  Errors of the
+// asynchronous build surface here.
+rm_status resolve_nlarge(const rm_scene* sc) {
+    std::lock_guard<std::mutex> g(sc->mu);
+    if (!sc->nlarge_pending) return RM_OK;
+    const cudaError_t e = cudaEventSynchronize(sc->built_ev);
+    const int32_t large = *sc->nlarge_slot;
+    pin_slot_release(sc->nlarge_slot);
+    cudaEventDestroy(sc->built_ev);
+    sc->nlarge_slot = nullptr;
+    sc->built_ev = nullptr;
+    sc->nlarge_pending = false;
+    if (e != cudaSuccess) return cuda_fail(e, "rm_bvh_build (asynchronous part)");
+    sc->nlarge = (large > 0 && large <= MAX_LARGE_TRIS) ? large : 0;
+    return RM_OK;
+}
+
 rm_status check_materials(const rm_material* m, int32_t nm) {
     if (nm < 1 || nm > RM_MAX_MATERIALS) return fail(RM_EINVAL, "nm must be in [1, 32]");
     if (!m) return fail(RM_EINVAL, "materials pointer is NULL");
@@ -152,6 +209,7 @@ uint64_t tx_count(const rm_tx& t) {
 rm_status validate(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p) {
     if (!sc) return fail(RM_EINVAL, "scene is NULL");
     if (!sc->built) return fail(RM_ESTATE, "rm_bvh_build has not been called on this scene");
+    if (rm_status r = resolve_nlarge(sc); r != RM_OK) return r;
     if (!tx || !p) return fail(RM_EINVAL, "tx or params is NULL");
     if (ntx < 1 || ntx > RM_MAX_TX) return fail(RM_EINVAL, "ntx must be in [1, 64]");
     if (!(p->freq_hz > 0.0) || !std::isfinite(p->freq_hz)) return fail(RM_EINVAL, "freq_hz must be > 0");
@@ -489,6 +547,51 @@ struct ThreadRes {
 };
 thread_local ThreadRes g_res;
 
+// Per-thread pinned staging of rm_scene_upload_host: the mesh is copied here
+// on the host and goes to the device in one asynchronous copy; `done` marks
+// the end of that copy so that the next upload does not overwrite the buffer
+// before the device has read it.
+struct UploadStage {
+    char* buf = nullptr;
+    size_t cap = 0;
+    int device = -1;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+    ~UploadStage() {
+        if (pending && done) cudaEventSynchronize(done);
+        if (buf) cudaFreeHost(buf);
+        if (done) cudaEventDestroy(done);
+    }
+};
+thread_local UploadStage g_up;
+
+cudaError_t upload_stage(size_t bytes, char** out) {
+    cudaError_t e;
+    if (g_up.pending) {
+        if ((e = cudaEventSynchronize(g_up.done)) != cudaSuccess) return e;
+        g_up.pending = false;
+    }
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (g_up.device != dev) {
+        if (g_up.done) cudaEventDestroy(g_up.done);
+        g_up.done = nullptr;
+        g_up.device = -1;
+        if ((e = cudaEventCreateWithFlags(&g_up.done, cudaEventDisableTiming)) != cudaSuccess) return e;
+        g_up.device = dev;
+    }
+    if (g_up.cap < bytes) {
+        if (g_up.buf) cudaFreeHost(g_up.buf);
+        g_up.buf = nullptr;
+        g_up.cap = 0;
+        const size_t want = std::max(bytes, size_t(256) << 10);
+        if ((e = cudaHostAlloc((void**)&g_up.buf, want, cudaHostAllocPortable)) != cudaSuccess) return e;
+        g_up.cap = want;
+    }
+    *out = g_up.buf;
+    return cudaSuccess;
+}
+
 cudaError_t device_block(size_t bytes, char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -567,6 +670,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
     if ((st = check_device(sc)) != RM_OK) return st;
     if (surf) {
         if (!surf->built) return fail(RM_ESTATE, "rm_bvh_build has not been called on the surface");
+        if ((st = resolve_nlarge(surf)) != RM_OK) return st;
         if ((st = check_device(surf)) != RM_OK) return st;
         if (surf->device != sc->device) return fail(RM_EINVAL, "scene and surface live on different devices");
         if (surf->nt < 1) return fail(RM_EINVAL, "the surface has no triangles");
@@ -705,6 +809,58 @@ rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tri
     return RM_OK;
 }
 
+rm_status rm_scene_upload_host(const float* verts_host, int64_t nv, const int32_t* tris_host, int64_t nt,
+                               const int32_t* tri_mat_host, const rm_material* mats_host, int32_t nm, void* stream,
+                               rm_scene** out) {
+    if (!out) return fail(RM_EINVAL, "out is NULL");
+    if (nv < 0 || nt < 0) return fail(RM_EINVAL, "nv and nt must be >= 0");
+    if (nt > (int64_t)INT32_MAX / 4) return fail(RM_EINVAL, "nt too large");
+    if (nt > 0 && (!verts_host || !tris_host || !tri_mat_host || nv < 1))
+        return fail(RM_EINVAL, "mesh pointers are NULL for a non-empty mesh");
+    rm_status st = check_materials(mats_host, nm);
+    if (st != RM_OK) return st;
+    // index ranges, on the host: no device round trip
+    for (int64_t i = 0; i < 3 * nt; ++i)
+        if (tris_host[i] < 0 || (int64_t)tris_host[i] >= nv)
+            return fail(RM_EINVAL, "a vertex or material index is out of range");
+    for (int64_t i = 0; i < nt; ++i)
+        if (tri_mat_host[i] < 0 || tri_mat_host[i] >= nm)
+            return fail(RM_EINVAL, "a vertex or material index is out of range");
+    if (injected(RM_FAULT_ALLOC)) return fail(RM_ENOMEM, "rm_scene_upload_host: injected allocation failure");
+    rm_scene* sc = new rm_scene();
+    RM_CUDA(cudaGetDevice(&sc->device));
+    sc->nv = nv;
+    sc->nt = nt;
+    sc->nm = nm;
+    sc->mats.assign(mats_host, mats_host + nm);
+    auto cleanup = [&](rm_status s) { rm_scene_free(sc); return s; };
+    if (nt > 0) {
+        const size_t o_t = align256(sizeof(float) * 3 * nv), o_m = o_t + align256(sizeof(int32_t) * 3 * nt),
+                     o_f = o_m + align256(sizeof(int32_t) * nt);
+        keep_pool_memory();
+        cudaError_t e;
+        if ((e = cudaMallocAsync((void**)&sc->mesh_mem, o_f + sizeof(int32_t), S(stream))) != cudaSuccess)
+            return cleanup(cuda_fail(e, "cudaMallocAsync"));
+        sc->verts = reinterpret_cast<float*>(sc->mesh_mem);
+        sc->tris = reinterpret_cast<int32_t*>(sc->mesh_mem + o_t);
+        sc->tri_mat = reinterpret_cast<int32_t*>(sc->mesh_mem + o_m);
+        char* h = nullptr;
+        if ((e = upload_stage(o_f, &h)) != cudaSuccess) return cleanup(cuda_fail(e, "pinned staging"));
+        std::memcpy(h, verts_host, sizeof(float) * 3 * nv);
+        std::memcpy(h + o_t, tris_host, sizeof(int32_t) * 3 * nt);
+        std::memcpy(h + o_m, tri_mat_host, sizeof(int32_t) * nt);
+        if ((e = cudaMemcpyAsync(sc->mesh_mem, h, o_f, cudaMemcpyHostToDevice, S(stream))) != cudaSuccess)
+            return cleanup(cuda_fail(e, "cudaMemcpyAsync"));
+        if ((e = cudaEventRecord(g_up.done, S(stream))) != cudaSuccess) {
+            cudaStreamSynchronize(S(stream));
+            return cleanup(cuda_fail(e, "cudaEventRecord"));
+        }
+        g_up.pending = true;
+    }
+    *out = sc;
+    return RM_OK;
+}
+
 rm_status rm_scene_set_materials(rm_scene* sc, const rm_material* mats_host, int32_t nm,
                                  const rm_material* sampling_host_or_null) {
     if (!sc) return fail(RM_EINVAL, "scene is NULL");
@@ -741,10 +897,33 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
         sc->nodes = reinterpret_cast<float4*>(sc->bvh_mem + o_n);
         sc->trirec = reinterpret_cast<float4*>(sc->bvh_mem + o_r);
         BvhBuffers B{sc->verts, sc->tris, sc->tri_mat, n, sc->keys, sc->order, sc->nodes, sc->trirec};
-        int32_t large = 0;
-        RM_CUDA(build_bvh(B, S(stream), &large));
-        RM_CUDA(cudaStreamSynchronize(S(stream)));
-        sc->nlarge = (large > 0 && large <= MAX_LARGE_TRIS) ? large : 0;
+        // the large-triangle count goes to a pinned slot; the host does not wait for it here
+        int32_t* slot = pin_slot_acquire();
+        cudaEvent_t ev = nullptr;
+        if (slot && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            pin_slot_release(slot);
+            slot = nullptr;
+            ev = nullptr;
+        }
+        if (!slot) {  // no pinned slot: wait for the count
+            int32_t large = 0;
+            RM_CUDA(build_bvh(B, S(stream), &large));
+            RM_CUDA(cudaStreamSynchronize(S(stream)));
+            sc->nlarge = (large > 0 && large <= MAX_LARGE_TRIS) ? large : 0;
+        } else {
+            cudaError_t e = build_bvh(B, S(stream), slot);
+            if (e == cudaSuccess) e = cudaEventRecord(ev, S(stream));
+            if (e != cudaSuccess) {
+                cudaStreamSynchronize(S(stream));
+                pin_slot_release(slot);
+                cudaEventDestroy(ev);
+                return cuda_fail(e, "rm_bvh_build");
+            }
+            std::lock_guard<std::mutex> g(sc->mu);
+            sc->nlarge_slot = slot;
+            sc->built_ev = ev;
+            sc->nlarge_pending = true;
+        }
     }
     sc->built = true;
     return RM_OK;
@@ -756,6 +935,7 @@ rm_status rm_bvh_export(const rm_scene* sc, uint64_t* keys_host, int32_t* order_
     if (!sc->built) return fail(RM_ESTATE, "rm_bvh_build has not been called on this scene");
     rm_status st = check_device(sc);
     if (st != RM_OK) return st;
+    if ((st = resolve_nlarge(sc)) != RM_OK) return st;
     const int64_t n = sc->nt;
     if (n <= 0) return RM_OK;
     if (keys_host) RM_CUDA(cudaMemcpy(keys_host, sc->keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
@@ -1015,6 +1195,7 @@ rm_status run_diffraction(const rm_scene* sc, const rm_scene* surf, const rm_wed
     if ((st = check_device(sc)) != RM_OK) return st;
     if (surf) {
         if (!surf->built) return fail(RM_ESTATE, "rm_bvh_build has not been called on the surface");
+        if ((st = resolve_nlarge(surf)) != RM_OK) return st;
         if ((st = check_device(surf)) != RM_OK) return st;
         if (surf->device != sc->device) return fail(RM_EINVAL, "scene and surface live on different devices");
         if (surf->nt < 1 || surf->nt > INT32_MAX) return fail(RM_EINVAL, "the surface needs 1 .. 2^31-1 triangles");
@@ -1147,6 +1328,10 @@ rm_status rm_diffraction_map_mesh(const rm_scene* sc, const rm_scene* surface, c
 rm_status rm_scene_info(const rm_scene* sc, int64_t* nt, int64_t* nnodes, int32_t* nm, int32_t* built) {
     if (!sc) return fail(RM_EINVAL, "scene is NULL");
     if (nt) *nt = sc->nt;
+    if (sc->built) {
+        rm_status st = resolve_nlarge(sc);
+        if (st != RM_OK) return st;
+    }
     const int64_t ns = sc->nt - sc->nlarge;
     if (nnodes) *nnodes = ns > 1 ? ns - 1 : 0;
     if (nm) *nm = sc->nm;
@@ -1158,6 +1343,10 @@ void rm_scene_free(rm_scene* sc) {
     if (!sc) return;
     // pool memory: wait for the device first, so that no kernel still reads it
     if (sc->mesh_mem || sc->bvh_mem) cudaDeviceSynchronize();
+    if (sc->nlarge_pending) {
+        pin_slot_release(sc->nlarge_slot);
+        cudaEventDestroy(sc->built_ev);
+    }
     cudaFree(sc->mesh_mem);
     cudaFree(sc->bvh_mem);
     delete sc;

@@ -88,6 +88,17 @@ def test_host_validation_without_gpu(L):
             setattr(m, k, v)
         assert lib.rm_scene_upload(None, 0, None, 0, None, (L.rm_material * 1)(m), 1, None, C.byref(h)) == L.RM_EINVAL
         assert b"material 0" in lib.rm_last_error()
+    # host upload: index ranges are checked on the host, before any CUDA call
+    import numpy as np
+    good = (L.rm_material * 1)(L.rm_material(4.0, 0.01, 0.2))
+    v = np.zeros((3, 3), np.float32)
+    for t, m in ((np.array([[0, 1, 3]], np.int32), np.zeros(1, np.int32)),
+                 (np.array([[0, -1, 2]], np.int32), np.zeros(1, np.int32)),
+                 (np.array([[0, 1, 2]], np.int32), np.ones(1, np.int32))):
+        assert lib.rm_scene_upload_host(v.ctypes.data, 3, t.ctypes.data, 1, m.ctypes.data, good, 1, None,
+                                        C.byref(h)) == L.RM_EINVAL
+        assert b"out of range" in lib.rm_last_error()
+    assert lib.rm_scene_upload_host(None, 0, None, 1, None, good, 1, None, C.byref(h)) == L.RM_EINVAL
     assert lib.rm_radio_map_trace(None, None, 1, None, None, None, None, None) == L.RM_EINVAL
     assert lib.rm_radio_map_grad(None, None, 1, None, None, None, None, None, None, None, None, None) == L.RM_EINVAL
     assert lib.rm_db_mse_loss(None, None, 10, 0.0, None, None, None, None) == L.RM_EINVAL

@@ -56,3 +56,44 @@ def test_empty_scene_builds(api):
     gs = api.Scene.from_obj(S.empty_scene())
     assert gs.export_bvh()["keys"].size == 0
     gs.free()
+
+
+def test_device_and_host_upload_agree(orc, api):
+    """A scene uploaded from device tensors (device-side index check, synchronous)
+    and from host arrays (host-side check, no wait) builds the same tree, and
+    a trace from either gives the same map."""
+    import torch
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    tx.ray_stride = 31
+    gh = api.Scene.from_obj(sc)
+    gd = api.Scene(torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.tris).cuda(),
+                   torch.from_numpy(sc.tri_mat).cuda(), sc.mats)
+    eh, ed = gh.export_bvh(), gd.export_bvh()
+    for k in ("keys", "order", "child"):
+        assert np.array_equal(eh[k], ed[k]), k
+    assert np.array_equal(eh["child_aabb"].view(np.uint32), ed["child_aabb"].view(np.uint32))
+    mh = api.trace(gh, [tx], p)["maps"]
+    md = api.trace(gd, [tx], p)["maps"]
+    assert torch.equal(mh, md)
+    gh.free()
+    gd.free()
+
+
+def test_trace_right_after_unwaited_build(orc, api):
+    """Upload, build and trace back to back with no host wait in between, many
+    times over (the build's large-triangle count is read by the trace): the
+    maps equal those of a scene whose count was read before tracing."""
+    import torch
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    tx.ray_stride = 97
+    ref = api.Scene.from_obj(sc)
+    assert ref.info()["nodes"] > 0          # waits for the build
+    want = api.trace(ref, [tx], p)["maps"].clone()
+    for _ in range(20):
+        g = api.Scene.from_obj(sc)
+        got = api.trace(g, [tx], p)["maps"]
+        assert torch.equal(got, want)
+        g.free()
+    ref.free()
