@@ -405,6 +405,229 @@ __global__ void k_trirec(const float* __restrict__ verts, const int32_t* __restr
     rec[3 * p + 2] = make_float4(c[2], __int_as_float(tri_mat[t]), __int_as_float(t), 0.0f);
 }
 
+// ---------------- the whole build of a small mesh in one block ----------------
+// For meshes of at most SMALL_SORT triangles the steps above (boxes, scene
+// bounds, large-triangle flags, centroid bounds, Morton codes, sort, Karras
+// hierarchy, refit, leaf records) run in one launch of one 1024-thread block,
+// with the sort, the hierarchy and the refit in shared memory.  Every value is
+// computed by the same expressions as in the multi-kernel path (min / max are
+// exact, so the order of the reductions does not matter), so the tree is the
+// same bit for bit; it replaces ~14 launches and their gaps.
+constexpr int BUILD_THREADS = 1024;
+struct SmallBuildSmem {
+    uint64_t sk[SMALL_SORT];
+    int32_t sv[SMALL_SORT];
+    int32_t pl[SMALL_SORT], pn[SMALL_SORT], visit[SMALL_SORT];
+    int32_t child[2 * SMALL_SORT];
+    float nb[12 * SMALL_SORT];          // child boxes of the internal nodes
+    int8_t large[SMALL_SORT];
+    float red[33 * 6];
+    int32_t cnt;
+};
+
+__device__ __forceinline__ void tri_box(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t i,
+                                        float lo[3], float hi[3]) {
+    const int32_t i0 = tris[3 * i], i1 = tris[3 * i + 1], i2 = tris[3 * i + 2];
+    for (int a = 0; a < 3; ++a) {
+        const float v0 = verts[3 * (int64_t)i0 + a], v1 = verts[3 * (int64_t)i1 + a],
+                    v2 = verts[3 * (int64_t)i2 + a];
+        lo[a] = fmin_sel(v0, fmin_sel(v1, v2));
+        hi[a] = fmax_sel(v0, fmax_sel(v1, v2));
+    }
+}
+
+// min of mn[], max of mx[] over the block; every thread gets the result
+__device__ void block_minmax(float mn[3], float mx[3], float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin_sel(mn[a], __shfl_xor_sync(FULL_MASK, mn[a], o));
+            mx[a] = fmax_sel(mx[a], __shfl_xor_sync(FULL_MASK, mx[a], o));
+        }
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) { red[6 * warp + a] = mn[a]; red[6 * warp + 3 + a] = mx[a]; }
+    __syncthreads();
+    if (warp == 0) {
+        for (int a = 0; a < 3; ++a) { mn[a] = red[6 * lane + a]; mx[a] = red[6 * lane + 3 + a]; }
+        for (int o = 16; o > 0; o >>= 1)
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = fmin_sel(mn[a], __shfl_xor_sync(FULL_MASK, mn[a], o));
+                mx[a] = fmax_sel(mx[a], __shfl_xor_sync(FULL_MASK, mx[a], o));
+            }
+        if (lane == 0)
+            for (int a = 0; a < 3; ++a) { red[6 * 32 + a] = mn[a]; red[6 * 32 + 3 + a] = mx[a]; }
+    }
+    __syncthreads();
+    for (int a = 0; a < 3; ++a) { mn[a] = red[6 * 32 + a]; mx[a] = red[6 * 32 + 3 + a]; }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(BUILD_THREADS) k_build_small(
+        const float* __restrict__ verts, const int32_t* __restrict__ tris, const int32_t* __restrict__ tri_mat,
+        int n, uint64_t* __restrict__ keys_out, int32_t* __restrict__ order_out, float4* __restrict__ nodes,
+        float4* __restrict__ rec, int32_t* __restrict__ count_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmallBuildSmem& S = *reinterpret_cast<SmallBuildSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+    if (tid == 0) S.cnt = 0;
+    // scene bounds of the triangle boxes
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = tid; i < n; i += BUILD_THREADS) {
+        float lo[3], hi[3];
+        tri_box(verts, tris, i, lo, hi);
+        for (int a = 0; a < 3; ++a) { mn[a] = fmin_sel(mn[a], lo[a]); mx[a] = fmax_sel(mx[a], hi[a]); }
+    }
+    block_minmax(mn, mx, S.red);
+    // large triangles
+    const float thr = __fmul_rn(0.25f, extent3(mn, mx));
+    for (int i = tid; i < n; i += BUILD_THREADS) {
+        float lo[3], hi[3];
+        tri_box(verts, tris, i, lo, hi);
+        const bool l = extent3(lo, hi) >= thr;
+        S.large[i] = l ? 1 : 0;
+        if (l) atomicAdd(&S.cnt, 1);
+    }
+    __syncthreads();
+    const int cnt = S.cnt;
+    const bool use_large = cnt > 0 && cnt <= MAX_LARGE;
+    // bounds of the doubled centroids of the tree's triangles
+    float cmn[3] = {INFINITY, INFINITY, INFINITY}, cmx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = tid; i < n; i += BUILD_THREADS) {
+        if (use_large && S.large[i]) continue;
+        float lo[3], hi[3];
+        tri_box(verts, tris, i, lo, hi);
+        for (int a = 0; a < 3; ++a) {
+            const float c = __fadd_rn(lo[a], hi[a]);
+            cmn[a] = fmin_sel(cmn[a], c);
+            cmx[a] = fmax_sel(cmx[a], c);
+        }
+    }
+    block_minmax(cmn, cmx, S.red);
+    // Morton codes (as k_morton) into the sort buffer, padded to a power of two
+    int P = 1;
+    while (P < n) P <<= 1;
+    {
+        const float e = extent3(cmn, cmx);
+        const float scale = (e > 0.0f) ? __fdiv_rn(2097151.0f, e) : 0.0f;
+        for (int i = tid; i < P; i += BUILD_THREADS) {
+            if (i >= n) { S.sk[i] = ~0ULL; S.sv[i] = INT32_MAX; continue; }
+            S.sv[i] = i;
+            if (use_large && S.large[i]) { S.sk[i] = ~0ULL; continue; }
+            float lo[3], hi[3];
+            tri_box(verts, tris, i, lo, hi);
+            uint32_t q[3];
+            for (int a = 0; a < 3; ++a) {
+                const float f = __fmul_rn(__fsub_rn(__fadd_rn(lo[a], hi[a]), cmn[a]), scale);
+                const uint32_t u = __float2uint_rz(f);
+                q[a] = u > 2097151u ? 2097151u : u;
+            }
+            S.sk[i] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+        }
+    }
+    __syncthreads();
+    // bitonic sort of (key, position): the stable order by key (as k_sort_small)
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < (P >> 1); t += BUILD_THREADS) {
+                const int i = 2 * t - (t & (stride - 1));
+                const int j = i + stride;
+                const bool up = (i & size) == 0;
+                const uint64_t ki = S.sk[i], kj = S.sk[j];
+                const int32_t vi = S.sv[i], vj = S.sv[j];
+                const bool gt = ki > kj || (ki == kj && vi > vj);
+                if (gt == up) {
+                    S.sk[i] = kj; S.sk[j] = ki;
+                    S.sv[i] = vj; S.sv[j] = vi;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n; i += BUILD_THREADS) {
+        keys_out[i] = S.sk[i];
+        order_out[i] = S.sv[i];
+    }
+    const int m = use_large ? n - cnt : n;   // the tree covers sorted positions [0, m)
+    if (m >= 2) {
+        // Karras hierarchy (as k_karras) on the shared keys
+        for (int ii = tid; ii < m - 1; ii += BUILD_THREADS) {
+            const int64_t i = ii;
+            const uint64_t* k = S.sk;
+            const int d = (delta(k, m, i, i + 1) - delta(k, m, i, i - 1)) > 0 ? 1 : -1;
+            const int dmin = delta(k, m, i, i - d);
+            int64_t lmax = 2;
+            while (delta(k, m, i, i + lmax * d) > dmin) lmax <<= 1;
+            int64_t l = 0;
+            for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+                if (delta(k, m, i, i + (l + t) * d) > dmin) l += t;
+            const int64_t j = i + l * d;
+            const int dnode = delta(k, m, i, j);
+            int64_t s = 0;
+            int64_t div = 2;
+            int64_t t = (l + div - 1) / div;
+            while (true) {
+                if (delta(k, m, i, i + (s + t) * d) > dnode) s += t;
+                if (t <= 1) break;
+                div <<= 1;
+                t = (l + div - 1) / div;
+            }
+            const int64_t g = i + s * d + (d < 0 ? -1 : 0);
+            const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+            const int32_t c0 = (lo == g) ? ~(int32_t)g : (int32_t)g;
+            const int32_t c1 = (hi == g + 1) ? ~(int32_t)(g + 1) : (int32_t)(g + 1);
+            S.child[2 * ii] = c0;
+            S.child[2 * ii + 1] = c1;
+            if (c0 < 0) S.pl[g] = ii; else S.pn[g] = ii;
+            if (c1 < 0) S.pl[g + 1] = ii; else S.pn[g + 1] = ii;
+            S.visit[ii] = 0;
+        }
+        __syncthreads();
+        // refit (as k_refit): the second child to arrive at a node forms its box
+        volatile float* nbv = S.nb;
+        for (int p = tid; p < m; p += BUILD_THREADS) {
+            float box[6];
+            tri_box(verts, tris, S.sv[p], box, box + 3);
+            int32_t me = ~(int32_t)p;
+            int32_t node = S.pl[p];
+            for (int step = 0; step < m; ++step) {
+                const int slot = (S.child[2 * node] == me) ? 0 : 1;
+                for (int a = 0; a < 6; ++a) nbv[12 * node + 6 * slot + a] = box[a];
+                __threadfence_block();
+                if (atomicAdd(&S.visit[node], 1) == 0) break;
+                __threadfence_block();
+                float lb[6], rb[6];
+                for (int a = 0; a < 6; ++a) { lb[a] = nbv[12 * node + a]; rb[a] = nbv[12 * node + 6 + a]; }
+                for (int a = 0; a < 3; ++a) {
+                    box[a] = fmin_sel(lb[a], rb[a]);
+                    box[3 + a] = fmax_sel(lb[3 + a], rb[3 + a]);
+                }
+                if (node == 0) break;
+                me = node;
+                node = S.pn[node];
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < m - 1; i += BUILD_THREADS) {
+            const float* b = S.nb + 12 * i;
+            nodes[4 * i + 0] = make_float4(b[0], b[1], b[2], b[3]);
+            nodes[4 * i + 1] = make_float4(b[4], b[5], b[6], b[7]);
+            nodes[4 * i + 2] = make_float4(b[8], b[9], b[10], b[11]);
+            nodes[4 * i + 3] = make_float4(__int_as_float(S.child[2 * i]), __int_as_float(S.child[2 * i + 1]), 0.0f, 0.0f);
+        }
+    }
+    // leaf records (as k_trirec)
+    for (int p = tid; p < n; p += BUILD_THREADS) {
+        const int32_t t = S.sv[p];
+        const float* a = verts + 3 * (int64_t)tris[3 * (int64_t)t];
+        const float* b = verts + 3 * (int64_t)tris[3 * (int64_t)t + 1];
+        const float* c = verts + 3 * (int64_t)tris[3 * (int64_t)t + 2];
+        rec[3 * p + 0] = make_float4(a[0], a[1], a[2], b[0]);
+        rec[3 * p + 1] = make_float4(b[1], b[2], c[0], c[1]);
+        rec[3 * p + 2] = make_float4(c[2], __int_as_float(tri_mat[t]), __int_as_float(t), 0.0f);
+    }
+    if (tid == 0) *count_out = cnt;
+}
+
 inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -421,6 +644,23 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host)
     *nlarge_host = 0;
     if (n <= 0) return cudaSuccess;
     cudaError_t err;
+    if (n <= SMALL_SORT) {
+        // one launch: the count goes through a 4-byte scratch word
+        int32_t* cnt = nullptr;
+        if ((err = cudaMallocAsync((void**)&cnt, sizeof(int32_t), s)) != cudaSuccess) return err;
+        const int smem = (int)sizeof(SmallBuildSmem);
+        if ((err = cudaFuncSetAttribute(k_build_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+            cudaSuccess) {
+            cudaFreeAsync(cnt, s);
+            return err;
+        }
+        k_build_small<<<1, BUILD_THREADS, smem, s>>>(B.verts, B.tris, B.tri_mat, (int)n, B.keys_sorted, B.order,
+                                                     B.nodes, B.trirec, cnt);
+        if ((err = cudaGetLastError()) == cudaSuccess)
+            err = cudaMemcpyAsync(nlarge_host, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        const cudaError_t e2 = cudaFreeAsync(cnt, s);
+        return err != cudaSuccess ? err : e2;
+    }
     const int nblk_a = (int)nb(n, 256);
     const int nblk_s = (int)nb(n, SORT_TILE);
     // scratch: aabb [6n] f32, c2 [3n] f32, blk [6 nblk_a] f32, bounds [6] f32,
