@@ -97,3 +97,40 @@ def test_trace_right_after_unwaited_build(orc, api):
         assert torch.equal(got, want)
         g.free()
     ref.free()
+
+
+def test_scenes_built_and_traced_from_several_threads(orc, api):
+    """Four host threads each upload, build (unwaited) and trace their own
+    scenes on their own streams: the pinned count slots and staging buffers are
+    shared or per thread, and every map equals the single-threaded one."""
+    import threading
+
+    import torch
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    tx.ray_stride = 211
+    ref = api.Scene.from_obj(sc)
+    want = api.trace(ref, [tx], p)["maps"].clone()
+    ref.free()
+    errors = []
+
+    def work():
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for _ in range(8):
+                    g = api.Scene.from_obj(sc, stream=s)
+                    got = api.trace(g, [tx], p, stream=s)["maps"]
+                    s.synchronize()
+                    if not torch.equal(got, want):
+                        errors.append("map differs")
+                    g.free()
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(repr(e))
+
+    th = [threading.Thread(target=work) for _ in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
