@@ -1103,9 +1103,9 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         const double R2 = (1.0 - Sd) * (1.0 + Sd);
         const double Rred = std::sqrt(R2);
         double c1, c2, qR, qS, qT;
+        const Cx<double> es = permittivity(C.s_eps[m], C.s_sig[m], C.omega);
+        const double kd = C.k0 * S.thick[m];
         {
-            Cx<double> es = permittivity(C.s_eps[m], C.s_sig[m], C.omega);
-            double kd = C.k0 * S.thick[m];
             Coefs<double> cs = fresnel(es, cos1, kd, slab);
             double wR = (C.flags & F_REFLECT) ? abs2(cs.r_perp) + abs2(cs.r_par) : 0.0;
             double wT = (C.flags & F_REFRACT) ? abs2(cs.t_perp) + abs2(cs.t_par) : 0.0;
@@ -1126,12 +1126,25 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
             dec = rec->dec & 3;
         } else if (C.mode == MODE_REPLAY) {
             if ((rec->dec & 3) != dec) {
-                // adopt the GPU's choice g if u lies within 1e-5 of g's interval
-                // [lo, hi) of positive probability
+                // adopt the GPU's choice g if u lies within tol of g's interval
+                // [lo, hi) of positive probability.  tol = 1e-5, plus for a slab the
+                // change of the interval bounds when the slab phase (2 pi d / lambda0) s
+                // (App. A.7) moves by 2^-20 of itself: an FP32 phase of ~300 rad, from
+                // an FP32 s and incidence angle, is good to a few units of 2^-24
                 const int g = rec->dec & 3;
                 const double lo = g == 0 ? 0.0 : (g == 2 ? c1 : c2);
                 const double hi = g == 0 ? c1 : (g == 2 ? c2 : 1.0);
-                if (rec->dec >= 0 && g != 3 && hi > lo && u > lo - 1e-5 && u < hi + 1e-5) {
+                double tol = 1e-5;
+                if (slab)
+                    for (double f : {1.0 - 0x1p-20, 1.0 + 0x1p-20}) {
+                        const Coefs<double> cp = fresnel(es, cos1, kd * f, slab);
+                        const double wR = (C.flags & F_REFLECT) ? abs2(cp.r_perp) + abs2(cp.r_par) : 0.0;
+                        const double wT = (C.flags & F_REFRACT) ? abs2(cp.t_perp) + abs2(cp.t_par) : 0.0;
+                        if (!(wR + wT > 0.0)) continue;
+                        const double c2p = wR / (wR + wT), c1p = R2 * c2p;
+                        tol = std::max(tol, 1e-5 + std::max(std::fabs(c1p - c1), std::fabs(c2p - c2)));
+                    }
+                if (rec->dec >= 0 && g != 3 && hi > lo && u > lo - tol && u < hi + tol) {
                     rs->rep.adopted_decision++;
                     dec = g;
                 } else {
