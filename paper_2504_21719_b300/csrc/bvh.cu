@@ -414,6 +414,7 @@ __global__ void k_trirec(const float* __restrict__ verts, const int32_t* __restr
 // exact, so the order of the reductions does not matter), so the tree is the
 // same bit for bit; it replaces ~14 launches and their gaps.
 constexpr int BUILD_THREADS = 1024;
+static_assert(SMALL_SORT / 2 <= BUILD_THREADS, "one sort pair per thread");
 struct SmallBuildSmem {
     uint64_t sk[SMALL_SORT];
     int32_t sv[SMALL_SORT];
@@ -421,9 +422,11 @@ struct SmallBuildSmem {
     int32_t child[2 * SMALL_SORT];
     float nb[12 * SMALL_SORT];          // child boxes of the internal nodes
     int8_t large[SMALL_SORT];
+    float box[6][SMALL_SORT];           // triangle boxes (lo xyz, hi xyz)
     float red[33 * 6];
     int32_t cnt;
 };
+static_assert(sizeof(SmallBuildSmem) <= 227 * 1024, "shared memory of one block");
 
 __device__ __forceinline__ void tri_box(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t i,
                                         float lo[3], float hi[3]) {
@@ -475,14 +478,18 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_small(
     for (int i = tid; i < n; i += BUILD_THREADS) {
         float lo[3], hi[3];
         tri_box(verts, tris, i, lo, hi);
-        for (int a = 0; a < 3; ++a) { mn[a] = fmin_sel(mn[a], lo[a]); mx[a] = fmax_sel(mx[a], hi[a]); }
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin_sel(mn[a], lo[a]);
+            mx[a] = fmax_sel(mx[a], hi[a]);
+            S.box[a][i] = lo[a];
+            S.box[3 + a][i] = hi[a];
+        }
     }
     block_minmax(mn, mx, S.red);
     // large triangles
     const float thr = __fmul_rn(0.25f, extent3(mn, mx));
     for (int i = tid; i < n; i += BUILD_THREADS) {
-        float lo[3], hi[3];
-        tri_box(verts, tris, i, lo, hi);
+        const float lo[3] = {S.box[0][i], S.box[1][i], S.box[2][i]}, hi[3] = {S.box[3][i], S.box[4][i], S.box[5][i]};
         const bool l = extent3(lo, hi) >= thr;
         S.large[i] = l ? 1 : 0;
         if (l) atomicAdd(&S.cnt, 1);
@@ -494,10 +501,8 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_small(
     float cmn[3] = {INFINITY, INFINITY, INFINITY}, cmx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int i = tid; i < n; i += BUILD_THREADS) {
         if (use_large && S.large[i]) continue;
-        float lo[3], hi[3];
-        tri_box(verts, tris, i, lo, hi);
         for (int a = 0; a < 3; ++a) {
-            const float c = __fadd_rn(lo[a], hi[a]);
+            const float c = __fadd_rn(S.box[a][i], S.box[3 + a][i]);
             cmn[a] = fmin_sel(cmn[a], c);
             cmx[a] = fmax_sel(cmx[a], c);
         }
@@ -513,11 +518,9 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_small(
             if (i >= n) { S.sk[i] = ~0ULL; S.sv[i] = INT32_MAX; continue; }
             S.sv[i] = i;
             if (use_large && S.large[i]) { S.sk[i] = ~0ULL; continue; }
-            float lo[3], hi[3];
-            tri_box(verts, tris, i, lo, hi);
             uint32_t q[3];
             for (int a = 0; a < 3; ++a) {
-                const float f = __fmul_rn(__fsub_rn(__fadd_rn(lo[a], hi[a]), cmn[a]), scale);
+                const float f = __fmul_rn(__fsub_rn(__fadd_rn(S.box[a][i], S.box[3 + a][i]), cmn[a]), scale);
                 const uint32_t u = __float2uint_rz(f);
                 q[a] = u > 2097151u ? 2097151u : u;
             }
@@ -525,10 +528,14 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_small(
         }
     }
     __syncthreads();
-    // bitonic sort of (key, position): the stable order by key (as k_sort_small)
+    // bitonic sort of (key, position): the stable order by key (as k_sort_small).
+    // Thread t owns pair t (P / 2 <= BUILD_THREADS).  A stage with stride <= 32
+    // keeps warp w inside elements [64 w, 64 w + 64), so two consecutive such
+    // stages need only a warp barrier; any stage with stride >= 64 a block barrier.
     for (int size = 2; size <= P; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = tid; t < (P >> 1); t += BUILD_THREADS) {
+            if (tid < (P >> 1)) {
+                const int t = tid;
                 const int i = 2 * t - (t & (stride - 1));
                 const int j = i + stride;
                 const bool up = (i & size) == 0;
@@ -540,9 +547,12 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_small(
                     S.sv[i] = vj; S.sv[j] = vi;
                 }
             }
-            __syncthreads();
+            const int next = stride > 1 ? stride >> 1 : size;   // the next stage's stride
+            if (stride >= 64 || next >= 64) __syncthreads();
+            else __syncwarp();
         }
     }
+    __syncthreads();
     for (int i = tid; i < n; i += BUILD_THREADS) {
         keys_out[i] = S.sk[i];
         order_out[i] = S.sv[i];
@@ -586,7 +596,8 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_small(
         volatile float* nbv = S.nb;
         for (int p = tid; p < m; p += BUILD_THREADS) {
             float box[6];
-            tri_box(verts, tris, S.sv[p], box, box + 3);
+            const int32_t tri = S.sv[p];
+            for (int a = 0; a < 6; ++a) box[a] = S.box[a][tri];
             int32_t me = ~(int32_t)p;
             int32_t node = S.pl[p];
             for (int step = 0; step < m; ++step) {
