@@ -38,6 +38,25 @@ def test_synthetic_array(orc, api, nant, steer):
     assert info["frac_within_rtol"] >= 0.999, info
 
 
+@pytest.mark.parametrize("nant", [1, 2, 17, 37, 64])
+def test_array_sizes(orc, api, nant):
+    """Edge and ragged sizes of the array-factor paths: one element (per-element
+    path), two (a uniform linear array of one short block), 17 (one block plus a
+    ragged one), 37 (a pair of 16-element blocks plus a ragged block) and 64 (two
+    pairs), steered precoding along an oblique axis."""
+    sc, tx, p = _manhattan(stride=211)
+    lam = 299792458.0 / p.freq_hz
+    axis = np.array([0.6, -0.3, 0.74])
+    axis /= np.linalg.norm(axis)
+    tx.ant_pos = np.outer(np.arange(nant) - 0.5 * (nant - 1), axis) * 0.5 * lam
+    k = np.array([0.2, 0.9, -0.4]) / np.linalg.norm([0.2, 0.9, -0.4])
+    w = np.exp(-2j * np.pi / lam * (tx.ant_pos @ k)) / np.sqrt(nant)
+    tx.precoding = w
+    m, rec, _ = _run(api, sc, tx, p)
+    info = compare_maps(orc, sc, tx, p, m, rec)
+    assert info["frac_within_rtol"] >= 0.999, info
+
+
 def test_irregular_array(orc, api):
     """Elements off any regular line (the per-element path): 48 seeded positions
     in a 2 m x 0.3 m x 0.3 m box (phases up to ~600 rad at 28 GHz) with seeded
