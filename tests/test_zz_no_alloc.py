@@ -77,3 +77,31 @@ def test_noalloc_batched_and_limits(api):
     rc, _ = _call(L, lib, gs, big, L.RM_MAX_TX + 1, prm, out)
     assert rc == L.RM_EINVAL and b"ntx" in lib.rm_last_error()
     gs.free()
+
+
+def test_noalloc_with_arrays(api):
+    """A 200-element uniform linear array packs into 52 antenna-table records and
+    fits the 16 KB static scratch; 600 irregular elements (600 records of 32 B)
+    do not and are rejected on the host."""
+    from paper_2504_21719_b300 import _lib as L
+    lib = L.load()
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    tx.ray_stride = 50
+    tx.ant_pos, tx.precoding = S.uniform_linear_array(200, p.freq_hz, 0.5, axis=1)
+    gs = api.Scene.from_obj(sc)
+    prm = api.params_from(p)
+    arr, ntx = api._tx_array([tx])
+    ref = api.trace(gs, [tx], prm)
+    out = torch.empty_like(ref["maps"])
+    rc, st = _call(L, lib, gs, arr, ntx, prm, out)
+    assert rc == L.RM_OK, lib.rm_last_error()
+    torch.cuda.synchronize()
+    _same(out, ref["maps"])
+    rng = np.random.default_rng(4)
+    tx.ant_pos = rng.uniform(-0.05, 0.05, size=(600, 3))
+    tx.precoding = np.ones(600) / np.sqrt(600.0)
+    arr2, _ = api._tx_array([tx])
+    rc, _ = _call(L, lib, gs, arr2, 1, prm, out)
+    assert rc == L.RM_EINVAL and b"noalloc" in lib.rm_last_error()
+    gs.free()
