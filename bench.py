@@ -1,16 +1,22 @@
 #!/usr/bin/env python3
 """Radio-map ray-bounces/s of the SBR tracer on B300.
 
-One step = one full radio map of the Manhattan workload: 10 x 10 box
-buildings (1202 triangles, seed 2), one transmitter at (0, 0, 30) m, 28 GHz,
-1e7 Fibonacci rays, up to 5 reflections / refractions, 512 x 512 cells of
-1 m.  The metric counts segments (closest-hit queries with their deposit and
-shading) on the device.
+One step = the radio maps of the largest workload: a procedural city of
+0.97M triangles (210 x 210 extruded convex polygons, seed 5), 16
+transmitters with 1e8 Fibonacci rays each, 28 GHz, up to 8 reflections /
+refractions, 16 maps of 2048 x 2048 cells of 2 m, all in one persistent
+launch.  The metric counts segments (closest-hit queries with their deposit
+and shading) on the device.  The same line carries the adjoint over the
+materials on that workload (its rate and forward+adjoint / forward), the
+end-to-end rate from host arrays, the roofline of the tracer kernel and the
+FP64 oracle timed on the host; `extra` holds the Manhattan, batched and
+differentiable workloads and the widened model, each with its roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun every rank traces its own copy of the workload (weak scaling,
-no collective on the data path); rank 0 prints one JSON line.
+Under torchrun the 16 transmitters are split over the ranks (rank r traces
+transmitters r, r + N, ...; each map lives on one rank, so no collective is
+needed): strong scaling of one fixed job; rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -31,10 +37,22 @@ sys.path.insert(0, ROOT)
 SEGMENT_BYTES = 184      # compulsory wavefront bytes per segment (ray state r/w, hit, queue)
 METRIC = "radio-map ray-bounces/s"
 UNIT = "ray-bounces/s"
-WORKLOAD = ("manhattan seed 2: 10x10 box buildings, 1202 triangles, 4 materials (ground half-space + 3 slab); "
-            "1 TX at (0,0,30) m isotropic V-pol; 28 GHz; 1e7 Fibonacci rays; max depth 5 (R+T); "
-            "512x512 map of 1 m cells at z=1.5 m")
-PROFILE = os.path.join(ROOT, "profiles", "k_trace_manhattan_1e7.md")
+WORKLOADS = {
+    5: ("procedural city seed 5: 210x210 extruded convex 4-12-gon buildings (971006 triangles), 8 materials "
+        "(ground half-space + 7 slab); 16 TX (seed 50, heights 10-50 m) x 1e8 Fibonacci rays, isotropic V-pol; "
+        "28 GHz; max depth 8 (R+T); 16 maps of 2048x2048 cells of 2 m at z=1.5 m"),
+    2: ("manhattan seed 2: 10x10 box buildings, 1202 triangles, 4 materials (ground half-space + 3 slab); "
+        "1 TX at (0,0,30) m isotropic V-pol; 28 GHz; 1e7 Fibonacci rays; max depth 5 (R+T); "
+        "512x512 map of 1 m cells at z=1.5 m"),
+    3: ("manhattan seed 2, 64 TX (seed 3, heights 5-40 m) with 2^U(16,22) rays each; 28 GHz; max depth 3; "
+        "64 maps of 256x256 cells of 2 m; one persistent CUDA-graph launch"),
+    4: ("manhattan seed 4 (8 materials), 1 TX at (0,0,30) m, 1e6 rays, max depth 4, bilinear 256x256 map of "
+        "2 m cells; dB-MSE loss against a map traced with seeded perturbed materials; adjoint over 8 eps_r, "
+        "8 sigma and the TX position"),
+}
+# the committed ncu summaries a roofline's `traffic` comes from, keyed by workload
+PROFILES = {5: "k_trace_city.md", 2: "k_trace_manhattan_1e7.md", 3: "k_trace_batched.md",
+            4: "k_trace_adjoint_differentiable.md"}
 # the tracer's code and the tree it walks (the LBVH build decides its node visits)
 TRACE_SOURCES = [os.path.join(ROOT, "paper_2504_21719_b300", "csrc", f) for f in ("trace.cu", "common.cuh", "array.cuh", "bvh.cu")]
 
@@ -42,13 +60,14 @@ TRACE_SOURCES = [os.path.join(ROOT, "paper_2504_21719_b300", "csrc", f) for f in
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--rays", type=int, default=0, help="override the ray count (profiling a smaller case)")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--rays", type=int, default=0, help="override the rays per transmitter (profiling a smaller case)")
     return ap.parse_args()
 
 
@@ -116,13 +135,13 @@ def peaks():
         return {}
 
 
-def profiled(key: str):
-    """A figure (dram_bytes_per_launch, issue_active_pct) of the tracer from the
-    committed ncu summary, if the kernel source is unchanged since it was
-    taken; else None."""
+def profiled(cfg: int, key: str):
+    """A figure (dram_bytes_per_segment, issue_active_pct, ...) of a tracer
+    workload from its committed ncu summary, if the kernel source is unchanged
+    since it was taken; else None."""
     try:
-        txt = open(PROFILE).read()
-    except OSError:
+        txt = open(os.path.join(ROOT, "profiles", PROFILES[cfg])).read()
+    except (OSError, KeyError):
         return None
     h = hashlib.sha256()
     for p in TRACE_SOURCES:
@@ -140,39 +159,166 @@ def profiled(key: str):
         return None
 
 
+def roofline(cfg: int, kernel: str, segments: float, kernel_ms: float, binding: str, timed_alone: bool):
+    """HBM roofline of one tracer launch: 184 compulsory wavefront bytes per
+    segment over the launch's CUDA-event duration, against the measured copy
+    bandwidth; `traffic` = the committed ncu DRAM bytes per segment (of a
+    capture of the same kernel) times this launch's segments."""
+    pk = peaks()
+    peak = pk.get("hbm_gbs")
+    src = "measured" if peak else "fallback"
+    peak = peak or 6400.0
+    achieved = SEGMENT_BYTES * segments / (kernel_ms / 1e3) / 1e9
+    per_seg = profiled(cfg, "dram_bytes_per_segment")
+    issue = profiled(cfg, "issue_active_pct")
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None if per_seg is None else round(per_seg * segments),
+            "peak_source": src, "algorithmic_bytes_per_segment": SEGMENT_BYTES, "kernel": kernel,
+            "kernel_ms": round(kernel_ms, 4), "segments_per_launch": int(segments),
+            "issue_slots_busy_frac": None if issue is None else round(issue / 100.0, 3),
+            "binding_limit": binding, "peak_kind": "burst copy bandwidth" if timed_alone else "copy bandwidth"}
+
+
 def tuned(gpu_name: str, key: str):
     from paper_2504_21719_b300.autotune import lookup
     return lookup(gpu_name, key)
 
 
-def oracle_sample(target_s: float = 15.0, max_rays: int = 10_000_000):
-    """The FP64 oracle, as it stands, on a bounded lattice subset of the workload."""
+def tuned_params(api, p, gpu_name, key, **kw):
+    blk, bps, qch, rfm = tuned(gpu_name, key)
+    return api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm, **kw), \
+        {"block_size": blk or 128, "blocks_per_sm": bps or "max occupancy", "queue_chunk": qch or 1,
+         "refill_min": rfm or 20, "tuned": bool(blk)}
+
+
+def oracle_sample(cfg: int, target_s: float = 12.0, record_segments=True):
+    """The FP64 oracle, as it stands, on a bounded lattice subset of workload
+    `cfg` (calibrated on a small subset, then sized to about target_s)."""
     import oracle
     from synth import scenes as S
-    sc, txs, p = S.workload(2)
-    tx = txs[0]
+    sc, txs, p = S.workload(cfg)
 
-    def run(stride, begin=0):
-        tx.ray_stride, tx.ray_begin = stride, begin
+    def run(sub):
         t0 = time.perf_counter()
-        r = oracle.radio_map(sc, tx, p, want_record=True)
-        dt = time.perf_counter() - t0
-        segs = int((r["record"][:, :, 0] != -2).sum())
-        return segs, dt, tx.count()
+        segs = 0
+        for tx in sub:
+            r = oracle.radio_map(sc, tx, p, want_record=True)
+            segs += int((r["record"][:, :, 0] != -2).sum())
+        return segs, time.perf_counter() - t0
 
-    segs, dt, n = run(100)                        # calibration: 1e5 rays
-    rate = n / max(dt, 1e-3)
-    rays = int(min(max_rays, max(2e4, rate * target_s)))
-    stride = max(1, tx.num_rays // rays)
-    segs, dt, n = run(stride, 1)
-    return {"value": segs / dt, "unit": "segments/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"workload lattice subset: 1 in {stride} of 1e7 rays ({n} rays, {segs} segments, "
-                      f"{dt:.1f} s), FP64 brute force over 1202 triangles"}
+    def subset(stride, begin):
+        out = []
+        for t in txs:
+            u = copy.copy(t)
+            u.ray_stride, u.ray_begin = max(1, min(stride, t.num_rays)), begin % max(1, min(stride, t.num_rays))
+            out.append(u)
+        return out
+
+    total = sum(t.num_rays for t in txs)
+    # calibration: about 1 in 10^4 of the rays (workload 5: one ray per transmitter)
+    cal = 100_000_000 if cfg == 5 else 10_000
+    segs, dt = run(subset(cal, 0))
+    rays = sum(u.count() for u in subset(cal, 0))
+    rate = rays / max(dt, 1e-3)
+    want = max(rays, rate * target_s)
+    stride = max(1, int(total / want))
+    sub = subset(stride, 1)
+    segs, dt = run(sub)
+    n = sum(u.count() for u in sub)
+    return {"value": round(segs / dt, 1), "unit": "segments/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"workload {cfg} lattice subset: 1 in {stride} rays of every transmitter ({n} rays, {segs} "
+                      f"segments, {dt:.1f} s), FP64 brute force over {sc.nt} triangles, OpenMP"}
+
+
+def time_plan(torch, plan, steps, warmup, flush, clocks=None):
+    """Replay a graph-captured trace: warm-up, then `steps` timed launches with
+    the L2 flushed before each; CUDA events around each launch on the current
+    stream, the plan's own events around its tracer node."""
+    for _ in range(warmup):
+        plan.launch()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+        # nvidia-smi needs a moment to start sampling: keep the GPU busy meanwhile
+        t_end = time.perf_counter() + 0.6
+        while time.perf_counter() < t_end:
+            plan.launch()
+            torch.cuda.synchronize()
+    step_ms, kern_ms, st = [], [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        flush.zero_()                         # L2 (126 MB) flushed between timed steps
+        torch.cuda.synchronize()
+        ev0.record()
+        plan.launch()
+        ev1.record()
+        torch.cuda.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        s = plan.stats()
+        kern_ms.append(s["kernel_ms"])
+        st.append(s)
+    clk = clocks.stop() if clocks is not None else None
+    return step_ms, kern_ms, st, clk
+
+
+def e2e_host(api, torch, sc, txs, prm, out, steps, warmup, flush, breakdown=False):
+    """End to end through the public API from pinned host arrays: scene upload,
+    LBVH build, trace and the read-back of the maps, every step.  With
+    `breakdown`, one more pass times each part alone (synchronised after each)."""
+    vh = torch.from_numpy(sc.verts).pin_memory()
+    th = torch.from_numpy(sc.tris).pin_memory()
+    mh = torch.from_numpy(sc.tri_mat).pin_memory()
+    out_h = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    e_ms, e_segs = [], []
+    for i in range(warmup + steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2 = api.Scene(vh, th, mh, sc.mats)
+        r = api.trace(g2, txs, prm, out=out)
+        out_h.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        g2.free()
+        if i >= warmup:
+            e_ms.append(dt * 1e3)
+            e_segs.append(r["stats"]["segments"])
+    h2d = sc.verts.nbytes + sc.tris.nbytes + sc.tri_mat.nbytes + sc.mats.nbytes + 72 * len(txs) + 56
+    res = {"value": sum(e_segs) / (sum(e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(out_h.numel() * 4 + 576), "ms_per_step": round(statistics.mean(e_ms), 3),
+           "includes": "scene upload + LBVH build + trace + map readback, per step"}
+    if breakdown:
+        parts = {"upload": [], "build": [], "trace_call": [], "trace_kernel": [], "readback": []}
+        for i in range(warmup + steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2 = api.Scene(vh, th, mh, sc.mats, build=False)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            g2.build_bvh()
+            g2.info()                     # waits for the build to finish
+            t2 = time.perf_counter()
+            r = api.trace(g2, txs, prm, out=out)
+            t3 = time.perf_counter()
+            out_h.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            t4 = time.perf_counter()
+            g2.free()
+            if i >= warmup:
+                parts["upload"].append(1e3 * (t1 - t0))
+                parts["build"].append(1e3 * (t2 - t1))
+                parts["trace_call"].append(1e3 * (t3 - t2))
+                parts["trace_kernel"].append(r["stats"]["kernel_ms"])
+                parts["readback"].append(1e3 * (t4 - t3))
+        res["breakdown_ms"] = {k: round(statistics.median(v), 4) for k, v in parts.items()}
+        res["breakdown_ms"]["note"] = ("each part synchronised alone; trace_call - trace_kernel = table copy, "
+                                      "FP64 map clear, FP64->FP32 map, counters read-back and launch latency")
+    return res
 
 
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args, world, rank, local):
-    import numpy as np
     import torch
 
     torch.cuda.set_device(local)
@@ -184,49 +330,25 @@ def run_ours(args, world, rank, local):
     from synth import scenes as S
 
     gpu_name = torch.cuda.get_device_name(local)
-    sc, txs, p = S.workload(2)
-    tx = txs[0]
-    if args.rays:
-        tx.num_rays = args.rays
-    blk, bps, qch, rfm = tuned(gpu_name, "manhattan")
-    params = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
-    gs = api.Scene.from_obj(sc)
-    maps = torch.empty((1, p.ny, p.nx), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    # one step = the trace captured once as a CUDA graph (map clear, tracer, FP64 -> FP32
-    # map) and replayed; the graph times its tracer node with events around it
-    plan = api.TracePlan(gs, [tx], params, maps)
-    for _ in range(args.warmup):
-        plan.launch()
-    torch.cuda.synchronize()
+
+    # ---------------- the step: forward radio maps of the city workload ----------------
+    sc, txs_all, p = S.workload(5)
+    if args.rays:
+        for t in txs_all:
+            t.num_rays = args.rays
+    txs = txs_all[rank::world]                   # this rank's transmitters
+    prm, shape = tuned_params(api, p, gpu_name, "city")
+    gs = api.Scene.from_obj(sc)
+    maps = torch.empty((len(txs), p.ny, p.nx), dtype=torch.float32, device="cuda")
+    plan = api.TracePlan(gs, txs, prm, maps)
     if dist:
+        plan.launch()
+        torch.cuda.synchronize()
         dist.barrier()
-    clocks = Clocks(local)
-    clocks.start()
-    # nvidia-smi needs a moment to start sampling: keep the GPU busy meanwhile
-    t_end = time.perf_counter() + 0.6
-    while time.perf_counter() < t_end:
-        plan.launch()
-    torch.cuda.synchronize()
-    step_ms, kern_ms, segs, nodes, tris = [], [], [], [], []
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
-        flush.zero_()                         # L2 (126 MB) flushed between timed steps
-        torch.cuda.synchronize()
-        ev0.record()
-        plan.launch()
-        ev1.record()
-        torch.cuda.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        st = plan.stats()
-        kern_ms.append(st["kernel_ms"])
-        segs.append(st["segments"])
-        nodes.append(st["nodes_visited"])
-        tris.append(st["tris_tested"])
+    step_ms, kern_ms, st, clk = time_plan(torch, plan, args.steps, args.warmup, flush, Clocks(local))
     plan.free()
-    clk = clocks.stop()
-    total_ms = sum(step_ms)
-    total_segs = sum(segs)
+    total_ms, total_segs = sum(step_ms), sum(s["segments"] for s in st)
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -234,52 +356,29 @@ def run_ours(args, world, rank, local):
         dist.all_reduce(s, op=dist.ReduceOp.SUM)
         total_ms, total_segs = float(t), float(s)
     value = total_segs / (total_ms / 1e3)
+    seg_step = statistics.mean(s["segments"] for s in st)
+    kavg = statistics.mean(kern_ms)
+    nodes = sum(s["nodes_visited"] for s in st) / max(1, sum(s["segments"] for s in st))
+    tris = sum(s["tris_tested"] for s in st) / max(1, sum(s["segments"] for s in st))
+    roof = roofline(5, "k_trace (persistent forward tracer), one launch over all transmitters", seg_step, kavg,
+                    "instruction issue (rays stay in registers; the 109 MB scene is read from L2)", False)
 
-    # roofline of the tracer kernel (its launches timed with CUDA events on its stream)
-    pk = peaks()
-    peak = pk.get("hbm_gbs")
-    kavg = statistics.mean(kern_ms) / 1e3
-    seg_step = statistics.mean(segs)
-    achieved = SEGMENT_BYTES * seg_step / kavg / 1e9
-    traffic = profiled("dram_bytes_per_launch")
-    issue = profiled("issue_active_pct")
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak if peak else 6400.0,
-                "unit": "GB/s", "frac": round(achieved / (peak if peak else 6400.0), 4),
-                "traffic": traffic, "peak_source": "measured" if peak else "fallback",
-                "algorithmic_bytes_per_segment": SEGMENT_BYTES,
-                "kernel": "k_trace (persistent forward tracer)", "kernel_ms": round(1e3 * kavg, 4),
-                "issue_slots_busy_frac": None if issue is None else round(issue / 100.0, 3),
-                "binding_limit": "instruction issue (scene and maps stay in L1/L2; see profiles/)"}
+    # ---------------- forward + adjoint over the materials, same workload ----------------
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = city_adjoint(api, S, torch, sc, txs, p, prm, gs, kavg, seg_step)
 
-    # end to end through the public API from pinned host memory
+    # ---------------- end to end from host arrays ----------------
     e2e = None
     if not args.no_e2e:
-        vh = torch.from_numpy(sc.verts).pin_memory()
-        th = torch.from_numpy(sc.tris).pin_memory()
-        mh = torch.from_numpy(sc.tri_mat).pin_memory()
-        out_h = torch.empty((1, p.ny, p.nx), dtype=torch.float32).pin_memory()
-        e_ms, e_segs = [], []
-        for i in range(args.warmup + args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g2 = api.Scene(vh, th, mh, sc.mats)
-            r = api.trace(g2, [tx], params, out=maps)
-            out_h.copy_(maps, non_blocking=True)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            g2.free()
-            if i >= args.warmup:
-                e_ms.append(dt * 1e3)
-                e_segs.append(r["stats"]["segments"])
-        h2d = sc.verts.nbytes + sc.tris.nbytes + sc.tri_mat.nbytes + sc.mats.nbytes + 72 + 56
-        e2e = {"value": sum(e_segs) / (sum(e_ms) / 1e3) * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(out_h.numel() * 4 + 576),
-               "includes": "scene upload + LBVH build + trace + map readback, per step"}
+        e2e = e2e_host(api, torch, sc, txs, prm, maps, args.steps, 1, flush)
+        e2e["value"] *= world
+    gs.free()
+    del maps
 
     extra = {}
     if not args.no_extra and rank == 0:
-        extra = run_extra(api, S, torch, gpu_name)
+        extra = run_extra(api, S, torch, gpu_name, flush, args)
 
     if rank != 0:
         if dist:
@@ -287,27 +386,50 @@ def run_ours(args, world, rank, local):
         return None
     cpu = None
     if world == 1 and not args.no_cpu_baseline and not args.rays:
-        cpu = oracle_sample()
+        cpu = oracle_sample(5, 15.0)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rays": tx.num_rays, "max_depth": p.max_depth, "map": [p.ny, p.nx],
-                   "triangles": sc.nt, "segments_per_step": int(seg_step),
-                   "nodes_per_segment": round(sum(nodes) / sum(segs), 2),
-                   "tris_per_segment": round(sum(tris) / sum(segs), 2), "block_size": blk or 128,
-                   "blocks_per_sm": bps or "max occupancy", "queue_chunk": qch or 1,
-                   "refill_min": rfm or 20, "tuned": bool(blk),
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[5], "transmitters": len(txs_all), "rays_per_tx": txs_all[0].num_rays,
+                   "max_depth": p.max_depth, "map": [len(txs_all), p.ny, p.nx], "triangles": sc.nt,
+                   "segments_per_step": int(seg_step), "nodes_per_segment": round(nodes, 2),
+                   "tris_per_segment": round(tris, 2), **shape,
                    "l2": "flushed between timed steps (256 MB write)",
-                   "step": "CUDA graph of one trace (map clear, k_trace, k_map_to_f32), replayed",
-                   "parallelism": f"replicas x{world}"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
-        "clocks": clk, "extra": extra,
+                   "step": "CUDA graph of one trace over all transmitters (map clear, k_trace, k_map_to_f32), replayed",
+                   "parallelism": f"transmitters split over {world} rank(s), no collective"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+        "clocks": clk, "adjoint": adjoint, "extra": extra,
     }
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return line
+
+
+def city_adjoint(api, S, torch, sc, txs, p, prm, gs, fwd_kernel_ms, fwd_segments, reps=3):
+    """Adjoint of the dB-MSE loss over the materials on the city workload: the
+    target maps are traced with seeded perturbed materials, the loss gradient
+    comes from the library's loss kernel, then the adjoint kernel is timed."""
+    tgt_sc = S.Scene(sc.name, sc.verts, sc.tris, sc.tri_mat, S.perturb_materials(sc.mats, 40))
+    gt = api.Scene.from_obj(tgt_sc)
+    tgt = api.trace(gt, txs, prm)["maps"]
+    gt.free()
+    f = api.trace(gs, txs, prm)
+    loss, dL, valid = api.db_mse_loss(f["maps"], tgt)
+    del tgt
+    api.grad(gs, txs, prm, dL)                     # warm-up
+    ak, segs = [], 0
+    for _ in range(reps):
+        a = api.grad(gs, txs, prm, dL)
+        ak.append(a["stats"]["kernel_ms"])
+        segs = a["stats"]["segments"]
+    k = statistics.mean(ak)
+    return {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3), "segments": segs,
+            "fwd_kernel_ms": round(fwd_kernel_ms, 3), "fwd_plus_adj_over_fwd": round((fwd_kernel_ms + k) / fwd_kernel_ms, 3),
+            "loss_cells": int(valid), "parameters": "d loss / d(eps_r, sigma) of 8 materials",
+            "roofline": roofline(5, "k_trace<adjoint> (re-traces the forward's rays)", segs, k,
+                                 "instruction issue", False)}
 
 
 def _kernel_rate(api, gs, txs, prm, reps=5):
@@ -323,38 +445,55 @@ def _kernel_rate(api, gs, txs, prm, reps=5):
     return {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3), "segments": segs}
 
 
-def run_extra(api, S, torch, gpu_name):
-    """Batched 64-TX form, forward+adjoint of the differentiable workload, the
-    large city, the widened model (diffuse reflection, early termination,
-    synthetic arrays, diffraction, mesh surfaces) on the Manhattan workload, and
-    the time-vs-N_S-and-N_A sweep on a street canyon."""
+def run_extra(api, S, torch, gpu_name, flush, args):
+    """The Manhattan workload as a full line of its own, the batched 64-TX form,
+    forward+adjoint of the differentiable workload, the widened model (diffuse
+    reflection, early termination, synthetic arrays, diffraction, mesh
+    surfaces) and the time-vs-N_S-and-N_A sweep on a street canyon."""
     import numpy as np
 
     out = {}
-    # widened model on the 1e7-ray Manhattan workload (same scene, TX, map)
+    # ---- Manhattan, 1e7 rays: graph step, roofline, end to end with its breakdown, oracle ----
     sc, txs, p = S.workload(2)
-    blk, bps, qch, rfm = tuned(gpu_name, "manhattan")
-    kw = dict(block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
-    base = _kernel_rate(api, api.Scene.from_obj(sc), txs, api.params_from(p, **kw))
+    prm, shape = tuned_params(api, p, gpu_name, "manhattan")
+    gs = api.Scene.from_obj(sc)
+    maps = torch.empty((1, p.ny, p.nx), dtype=torch.float32, device="cuda")
+    plan = api.TracePlan(gs, txs, prm, maps)
+    steps = max(args.steps, 10)
+    step_ms, kern_ms, st, _ = time_plan(torch, plan, steps, max(args.warmup, 3), flush)
+    plan.free()
+    segs = statistics.mean(s["segments"] for s in st)
+    km = statistics.mean(kern_ms)
+    out["manhattan"] = {"workload": WORKLOADS[2], "value": round(sum(s["segments"] for s in st) / (sum(step_ms) / 1e3), 1),
+                        "unit": UNIT, "ms_per_step": round(statistics.mean(step_ms), 4), "steps": steps,
+                        "segments_per_step": int(segs), **shape,
+                        "nodes_per_segment": round(sum(s["nodes_visited"] for s in st) / sum(s["segments"] for s in st), 2),
+                        "roofline": roofline(2, "k_trace (persistent forward tracer)", segs, km,
+                                             "instruction issue (scene and map stay in L1/L2)", True),
+                        "e2e": e2e_host(api, torch, sc, txs, prm, maps, steps, 3, flush, breakdown=True)}
+    if not args.no_cpu_baseline:
+        out["manhattan"]["cpu_baseline"] = oracle_sample(2, 8.0)
+    base = _kernel_rate(api, gs, txs, prm)
+    # widened model on the same workload (same scene, TX, map)
     scd = sc.with_scattering(0.5, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
     pd = copy.copy(p)
     pd.diffuse = True
     gsd = api.Scene.from_obj(scd)
-    d = _kernel_rate(api, gsd, txs, api.params_from(pd, **kw))
+    d = _kernel_rate(api, gsd, txs, tuned_params(api, pd, gpu_name, "manhattan")[0])
     d["vs_specular"] = round(d["value"] / base["value"], 3)
     d["materials"] = "S = 0.5 on every material; ground Lambertian, buildings directive / backscattering"
+    d["roofline"] = roofline(0, "k_trace<diffuse>", d["segments"], d["kernel_ms"], "instruction issue", True)
     out["specular_same_call"] = base
     out["diffuse"] = d
     gsd.free()
     pr = copy.copy(p)
     pr.rr_depth, pr.rr_max_prob = 2, 0.5
-    gs = api.Scene.from_obj(sc)
-    e = _kernel_rate(api, gs, txs, api.params_from(pr, **kw))
+    e = _kernel_rate(api, gs, txs, tuned_params(api, pr, gpu_name, "manhattan")[0])
     e["setting"] = "Russian roulette after 2 interactions, p_max = 0.5"
     out["early_termination"] = e
     ta = copy.copy(txs[0])
     ta.ant_pos, ta.precoding = S.uniform_linear_array(64, p.freq_hz, 0.5, axis=0)
-    a = _kernel_rate(api, gs, [ta], api.params_from(p, **kw))
+    a = _kernel_rate(api, gs, [ta], prm)
     a["setting"] = "64-element half-wavelength ULA, uniform precoding"
     out["synthetic_array_64"] = a
     # first-order diffraction map of the same transmitter: 1200 wedges x 4096 samples
@@ -374,12 +513,11 @@ def run_extra(api, S, torch, gpu_name):
     # the same map on a mesh measurement surface: 256 x 256 x 2 rolling-terrain triangles over the map
     sv, st_ = S.terrain_surface(256.0, 256)
     su = api.surface(sv, st_)
-    pm = api.params_from(p, **kw)
     for _ in range(2):
-        api.trace_mesh(gs, su, txs, pm)
+        api.trace_mesh(gs, su, txs, prm)
     mk, mst = [], None
     for _ in range(5):
-        r = api.trace_mesh(gs, su, txs, pm)
+        r = api.trace_mesh(gs, su, txs, prm)
         mk.append(r["stats"]["kernel_ms"])
         mst = r["stats"]
     k = statistics.mean(mk)
@@ -399,30 +537,26 @@ def run_extra(api, S, torch, gpu_name):
                                        "setting": "4096 samples per wedge onto the same terrain mesh"}
     su.free()
     gs.free()
+
+    # ---- batched: 64 TX with uneven ray counts in one graph-captured persistent launch ----
     sc, txs, p = S.workload(3)
-    blk, bps, qch, rfm = tuned(gpu_name, "batched")
     gs = api.Scene.from_obj(sc)
-    prm = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
+    prm, shape = tuned_params(api, p, gpu_name, "batched")
     maps = torch.empty((len(txs), p.ny, p.nx), dtype=torch.float32, device="cuda")
     plan = api.TracePlan(gs, txs, prm, maps)
-    for _ in range(3):
-        plan.launch()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms, segs = [], 0
-    for _ in range(5):
-        ev0.record()
-        plan.launch()
-        ev1.record()
-        torch.cuda.synchronize()
-        ms.append(ev0.elapsed_time(ev1))
-        segs = plan.stats()["segments"]
-    out["batched_64tx"] = {"value": round(segs / (statistics.mean(ms) / 1e3), 1), "unit": UNIT,
-                           "ms_per_launch": round(statistics.mean(ms), 3), "segments": segs,
-                           "rays": sum(t.num_rays for t in txs), "form": "CUDA graph, one persistent launch"}
+    step_ms, kern_ms, st, _ = time_plan(torch, plan, 5, 3, flush)
     plan.free()
+    segs = st[-1]["segments"]
+    out["batched_64tx"] = {"workload": WORKLOADS[3], "value": round(segs / (statistics.mean(step_ms) / 1e3), 1),
+                           "unit": UNIT, "ms_per_launch": round(statistics.mean(step_ms), 3), "segments": segs,
+                           "rays": sum(t.num_rays for t in txs), "form": "CUDA graph, one persistent launch", **shape,
+                           "roofline": roofline(3, "k_trace (one launch over 64 transmitters)", segs,
+                                                statistics.mean(kern_ms), "instruction issue", True)}
+    if not args.no_cpu_baseline:
+        out["batched_64tx"]["cpu_baseline"] = oracle_sample(3, 8.0)
     gs.free()
 
+    # ---- differentiable: forward, dB loss, adjoint ----
     sc, txs, p = S.workload(4)
     gs = api.Scene.from_obj(sc)
     tgt_sc = S.Scene(sc.name, sc.verts, sc.tris, sc.tri_mat, S.perturb_materials(sc.mats, 40))
@@ -446,11 +580,16 @@ def run_extra(api, S, torch, gpu_name):
             segs = f["stats"]["segments"]
             b_ms.append((t2 - t1) * 1e3)
     fk, ak = statistics.mean(f_ms), statistics.mean(a_ms)
-    out["differentiable"] = {"fwd_kernel_ms": round(fk, 3), "adj_kernel_ms": round(ak, 3),
+    out["differentiable"] = {"workload": WORKLOADS[4], "fwd_kernel_ms": round(fk, 3), "adj_kernel_ms": round(ak, 3),
                              "fwd_plus_adj_over_fwd": round((fk + ak) / fk, 3),
                              "adj_call_ms": round(statistics.mean(b_ms), 3),
                              "fwd_plus_adj_call_over_fwd": round((fk + statistics.mean(b_ms)) / fk, 3),
-                             "fwd_value": round(segs / (fk / 1e3), 1), "unit": UNIT}
+                             "fwd_value": round(segs / (fk / 1e3), 1), "adj_value": round(segs / (ak / 1e3), 1),
+                             "unit": UNIT, "segments": segs,
+                             "roofline_fwd": roofline(0, "k_trace<bilinear>", segs, fk, "instruction issue", True),
+                             "roofline_adj": roofline(4, "k_trace<adjoint, bilinear>", segs, ak, "instruction issue", True)}
+    if not args.no_cpu_baseline:
+        out["differentiable"]["cpu_baseline"] = oracle_sample(4, 6.0)
     gs.free()
     # the same with diffuse reflection on every material (adjoint kernel timed inside the library)
     scd = sc.with_scattering(np.linspace(0.2, 0.8, sc.nm), 0.3, np.arange(sc.nm) % 3, 2, 3, 0.5)
@@ -468,27 +607,6 @@ def run_extra(api, S, torch, gpu_name):
                                      "adj_kernel_ms": round(statistics.mean(ak), 3),
                                      "fwd_plus_adj_over_fwd": round(1 + statistics.mean(ak) / statistics.mean(fk), 3)}
     gs.free()
-
-    # large city: 0.97M triangles, 16 TX x 1e8 rays, depth 8, one launch each way
-    sc, txs, p = S.workload(5)
-    gs = api.Scene.from_obj(sc)
-    blk, bps, qch, rfm = tuned(gpu_name, "city")
-    p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
-    small = [S.Tx(pos=txs[0].pos, num_rays=1_000_000, seed=txs[0].seed)]
-    api.trace(gs, small, p)
-    f = api.trace(gs, txs, p)
-    g = torch.full_like(f["maps"], 1.0 / f["maps"].numel())
-    a = api.grad(gs, txs, p, g)
-    fk, ak = f["stats"]["kernel_ms"], a["stats"]["kernel_ms"]
-    segs = f["stats"]["segments"]
-    out["large_city"] = {"triangles": sc.nt, "rays": f["stats"]["rays"], "segments": segs,
-                         "fwd_kernel_ms": round(fk, 1), "fwd_value": round(segs / (fk / 1e3), 1),
-                         "adj_kernel_ms": round(ak, 1), "adj_value": round(segs / (ak / 1e3), 1),
-                         "fwd_plus_adj_over_fwd": round((fk + ak) / fk, 3), "unit": UNIT,
-                         "nodes_per_segment": round(f["stats"]["nodes_visited"] / segs, 2),
-                         "tris_per_segment": round(f["stats"]["tris_tested"] / segs, 2)}
-    del f, a, g
-    gs.free()
     out["time_vs_samples_and_antennas"] = sweep_samples_antennas(api, S, torch, gpu_name)
     return out
 
@@ -502,8 +620,7 @@ def sweep_samples_antennas(api, S, torch, gpu_name, n_s=(10**6, 10**7, 10**8, 10
     sc = S.street_canyon()
     gs = api.Scene.from_obj(sc)
     p = S.TraceParams(3.5e9, 5, cell_size=1.0, nx=256, ny=256)
-    blk, bps, qch, rfm = tuned(gpu_name, "manhattan")
-    prm = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
+    prm, _ = tuned_params(api, p, gpu_name, "manhattan")
     kern, call, segs = [], [], []
     for ns in n_s:
         kr, cr, sr = [], [], []
@@ -535,16 +652,18 @@ def sweep_samples_antennas(api, S, torch, gpu_name, n_s=(10**6, 10**7, 10**8, 10
 
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
+    """The FP64 oracle on the host cores: each step a bounded lattice sample of
+    the city workload (one transmitter per step, in turn)."""
     if rank != 0:
         return None
     import oracle
     from synth import scenes as S
-    sc, txs, p = S.workload(2)
-    tx = txs[0]
-    stride = 50                                    # 2e5 rays per step
+    sc, txs, p = S.workload(5)
+    stride = 4_000_000                             # 25 rays of one transmitter per step
     times, segs = [], []
     for i in range(args.warmup + args.steps):
-        tx.ray_stride, tx.ray_begin = stride, i % stride
+        tx = copy.copy(txs[i % len(txs)])
+        tx.ray_stride, tx.ray_begin = stride, (7 * i) % stride
         t0 = time.perf_counter()
         r = oracle.radio_map(sc, tx, p, want_record=True)
         dt = time.perf_counter() - t0
@@ -552,15 +671,15 @@ def run_reference(args, world, rank):
             times.append(dt)
             segs.append(int((r["record"][:, :, 0] != -2).sum()))
     value = sum(segs) / sum(times)
-    sample = (f"per step: 1 in {stride} rays of the 1e7-ray lattice ({tx.count()} rays), FP64 brute force over "
-              f"{sc.nt} triangles, OpenMP")
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+    sample = (f"per step: 1 in {stride} rays of one transmitter's 1e8-ray lattice (25 rays, the transmitters in "
+              f"turn), FP64 brute force over {sc.nt} triangles, OpenMP")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 2),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sampled": True},
-            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.num_threads(),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS[5], "sampled": True},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
-            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return line
 

@@ -131,6 +131,7 @@ typedef struct {
 #define RM_LOS 4u       /* deposit the line-of-sight segment (depth 0) */
 #define RM_STATS 8u     /* collect per-depth power statistics (slower) */
 #define RM_DIFFUSE 16u  /* diffuse reflection on materials with scattering > 0 (needs RM_REFLECT) */
+#define RM_RECORD_COIN 32u  /* debug record only: each decision also carries the coin's q(R) */
 
 typedef struct {
     double freq_hz;          /* carrier frequency f; lambda0 = c0 / f */
@@ -182,8 +183,11 @@ typedef struct {
  * l = 0..L).  prim: original triangle index hit, -1 escaped, -2 the ray had
  * already terminated.  ix, iy: deposited cell (bilinear: lower-left cell of
  * the 2x2 stencil), -32768 for no deposit.  decision: 0 reflection,
- * 1 refraction, -1 none; plus 4 if Russian roulette then stopped the path,
- * 8 if the gain threshold did. */
+ * 1 refraction, 2 diffuse reflection, -1 none; plus 4 if Russian roulette
+ * then stopped the path, 8 if the gain threshold did.  Under RM_RECORD_COIN a
+ * decision >= 0 also carries, in bits 8..30, the probability q(R) the coin
+ * compared its variate with, as round(q(R) 2^22): the parity tests check the
+ * GPU's sampling probabilities interaction by interaction. */
 typedef struct {
     int32_t prim, ix, iy, decision;
 } rm_segment_record;
@@ -350,6 +354,8 @@ void rm_trace_plan_free(rm_trace_plan* plan);
  *   one to finish before starting the next.
  * Arguments, outputs and errors are those of rm_radio_map_trace without the
  * debug record; stats_host_or_null receives the counters (kernel_ms = 0).
+ * The call reads its counters back and waits for `stream`; a stream that is
+ * capturing is refused with RM_ESTATE before anything is enqueued.
  * Deposits are accumulated with FP32 atomics directly in maps_dev (no FP64
  * buffer), so cells that receive very many deposits carry FP32 summation error.
  * Synchronises `stream`. */
@@ -435,6 +441,25 @@ rm_status rm_diffraction_map_mesh(const rm_scene* scene, const rm_scene* surface
  * call after an injected failure runs normally.  RM_EINVAL for another kind
  * or count < 0. */
 rm_status rm_debug_inject(int32_t kind, int32_t count);
+
+/* The coin's weights of one interaction, from the tracer's own device code:
+ * for material `mat` at freq_hz and each cosine of incidence cos1_dev[i] in
+ * [0, 1], wR_dev[i] = |r_perp|^2 + |r_par|^2 and wT_dev[i] = |t_perp|^2 +
+ * |t_par|^2 of Eq. fresnel_vac (half-space) or Eqs. fresnel_slab /
+ * q_fresnel_slab (slab), so that q(R) = wR / (wR + wT) (Eq.
+ * path-solver-used-dist-event with q(D) = 0).  The parity tests compare it
+ * with the FP64 oracle at the same cosines to bound the FP32 error of the
+ * sampling probabilities (in particular of the slab phase (2 pi d / lambda0) s).
+ * Device arrays of n floats owned by the caller; asynchronous on `stream`;
+ * RM_EINVAL for a NULL or invalid material, freq_hz <= 0 or n < 0. */
+rm_status rm_debug_fresnel_probe(const rm_material* mat, double freq_hz, const float* cos1_dev, int64_t n,
+                                 float* wR_dev, float* wT_dev, void* stream);
+
+/* Number of device and pinned-host allocation calls (cudaMalloc,
+ * cudaMallocAsync, cudaHostAlloc) the library has made in this process since
+ * it was loaded: tests read it before and after a call to check whether that
+ * call allocated.  Host call, thread-safe, no device work. */
+uint64_t rm_debug_alloc_count(void);
 
 /* Number of triangles / internal BVH nodes of a scene (host call, no device work). */
 rm_status rm_scene_info(const rm_scene* scene, int64_t* nt, int64_t* nnodes, int32_t* nm,

@@ -51,7 +51,9 @@ class OrReport(C.Structure):
                 ("adopted_cell", C.c_int64), ("adopted_decision", C.c_int64),
                 ("failures", C.c_int64), ("adopted_hit_tie", C.c_int64), ("fail_ray", C.c_int64),
                 ("fail_depth", C.c_int32),
-                ("fail_kind", C.c_int32), ("fail_info", C.c_double * 4)]
+                ("fail_kind", C.c_int32), ("fail_info", C.c_double * 4),
+                ("coin_checked", C.c_int64), ("coin_outside", C.c_int64), ("coin_max_dev", C.c_double),
+                ("coin_max_ratio", C.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "fail_info"}

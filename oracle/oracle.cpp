@@ -496,6 +496,12 @@ struct or_report {
     int64_t fail_ray;
     int32_t fail_depth, fail_kind;  // 1 hit, 2 deposit cell, 3 decision, 4 segment
     double fail_info[4];
+    // Records that carry the GPU's coin probability q(R) (bits 8.. of the
+    // decision, units of 2^-22): how many were checked, the largest
+    // |q_gpu - q(R)| and its largest ratio to the replay's decision window,
+    // and how many fell outside that window.
+    int64_t coin_checked, coin_outside;
+    double coin_max_dev, coin_max_ratio;
 };
 constexpr int32_t NO_CELL = -32768;
 enum { MODE_PLAIN = 0, MODE_REPLAY = 1, MODE_FROZEN = 2 };
@@ -1122,28 +1128,42 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         }
         double u = rng_u(tx.seed, (uint64_t)n, l);
         int dec = (u < c1) ? 0 : (u < c2 ? 2 : 1);
+        // The replay's decision window: 1e-5, plus for a slab the change of the
+        // interval bounds when the slab phase (2 pi d / lambda0) s (App. A.7)
+        // moves by 2^-20 of itself: an FP32 phase of ~300 rad, from an FP32 s
+        // and incidence angle, is good to a few units of 2^-24
+        auto window = [&]() {
+            double tol = 1e-5;
+            if (slab)
+                for (double f : {1.0 - 0x1p-20, 1.0 + 0x1p-20}) {
+                    const Coefs<double> cp = fresnel(es, cos1, kd * f, slab);
+                    const double wR = (C.flags & F_REFLECT) ? abs2(cp.r_perp) + abs2(cp.r_par) : 0.0;
+                    const double wT = (C.flags & F_REFRACT) ? abs2(cp.t_perp) + abs2(cp.t_par) : 0.0;
+                    if (!(wR + wT > 0.0)) continue;
+                    const double c2p = wR / (wR + wT), c1p = R2 * c2p;
+                    tol = std::max(tol, 1e-5 + std::max(std::fabs(c1p - c1), std::fabs(c2p - c2)));
+                }
+            return tol;
+        };
+        if (C.mode == MODE_REPLAY && rec->dec >= 256) {
+            // the GPU recorded the q(R) its coin used: it must lie in the window
+            const double qg = (double)(rec->dec >> 8) * 0x1p-22;
+            const double dev = std::fabs(qg - c1), w = window();
+            rs->rep.coin_checked++;
+            rs->rep.coin_max_dev = std::max(rs->rep.coin_max_dev, dev);
+            rs->rep.coin_max_ratio = std::max(rs->rep.coin_max_ratio, dev / w);
+            if (dev > w) rs->rep.coin_outside++;
+        }
         if (C.mode == MODE_FROZEN) {
             dec = rec->dec & 3;
         } else if (C.mode == MODE_REPLAY) {
             if ((rec->dec & 3) != dec) {
-                // adopt the GPU's choice g if u lies within tol of g's interval
-                // [lo, hi) of positive probability.  tol = 1e-5, plus for a slab the
-                // change of the interval bounds when the slab phase (2 pi d / lambda0) s
-                // (App. A.7) moves by 2^-20 of itself: an FP32 phase of ~300 rad, from
-                // an FP32 s and incidence angle, is good to a few units of 2^-24
+                // adopt the GPU's choice g if u lies within the window of g's
+                // interval [lo, hi) of positive probability
                 const int g = rec->dec & 3;
                 const double lo = g == 0 ? 0.0 : (g == 2 ? c1 : c2);
                 const double hi = g == 0 ? c1 : (g == 2 ? c2 : 1.0);
-                double tol = 1e-5;
-                if (slab)
-                    for (double f : {1.0 - 0x1p-20, 1.0 + 0x1p-20}) {
-                        const Coefs<double> cp = fresnel(es, cos1, kd * f, slab);
-                        const double wR = (C.flags & F_REFLECT) ? abs2(cp.r_perp) + abs2(cp.r_par) : 0.0;
-                        const double wT = (C.flags & F_REFRACT) ? abs2(cp.t_perp) + abs2(cp.t_par) : 0.0;
-                        if (!(wR + wT > 0.0)) continue;
-                        const double c2p = wR / (wR + wT), c1p = R2 * c2p;
-                        tol = std::max(tol, 1e-5 + std::max(std::fabs(c1p - c1), std::fabs(c2p - c2)));
-                    }
+                const double tol = window();
                 if (rec->dec >= 0 && g != 3 && hi > lo && u > lo - tol && u < hi + tol) {
                     rs->rep.adopted_decision++;
                     dec = g;
@@ -1564,6 +1584,10 @@ int or_radio_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt
             report->adopted_decision += r.adopted_decision;
             report->adopted_hit_tie += r.adopted_hit_tie;
             report->failures += r.failures;
+            report->coin_checked += r.coin_checked;
+            report->coin_outside += r.coin_outside;
+            report->coin_max_dev = std::max(report->coin_max_dev, r.coin_max_dev);
+            report->coin_max_ratio = std::max(report->coin_max_ratio, r.coin_max_ratio);
             if (r.failures && !have_fail) {
                 have_fail = true;
                 report->fail_ray = r.fail_ray;
@@ -1651,6 +1675,10 @@ int or_radio_map_mesh(const float* verts, int64_t nv, const int32_t* tris, int64
             report->adopted_decision += r.adopted_decision;
             report->adopted_hit_tie += r.adopted_hit_tie;
             report->failures += r.failures;
+            report->coin_checked += r.coin_checked;
+            report->coin_outside += r.coin_outside;
+            report->coin_max_dev = std::max(report->coin_max_dev, r.coin_max_dev);
+            report->coin_max_ratio = std::max(report->coin_max_ratio, r.coin_max_ratio);
             if (r.failures && !have_fail) {
                 have_fail = true;
                 report->fail_ray = r.fail_ray;

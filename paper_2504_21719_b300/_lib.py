@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "librmsbr.so")
 RM_OK, RM_EINVAL, RM_ENOMEM, RM_ECUDA, RM_EOVERFLOW, RM_ETIMEOUT, RM_ESTATE = range(7)
 STATUS_NAMES = ["RM_OK", "RM_EINVAL", "RM_ENOMEM", "RM_ECUDA", "RM_EOVERFLOW", "RM_ETIMEOUT", "RM_ESTATE"]
 RM_MAX_DEPTH, RM_MAX_MATERIALS, RM_MAX_TX = 15, 32, 64
-RM_REFLECT, RM_REFRACT, RM_LOS, RM_STATS, RM_DIFFUSE = 1, 2, 4, 8, 16
+RM_REFLECT, RM_REFRACT, RM_LOS, RM_STATS, RM_DIFFUSE, RM_RECORD_COIN = 1, 2, 4, 8, 16, 32
 RM_FAULT_ALLOC, RM_FAULT_LAUNCH, RM_FAULT_OVERFLOW = 1, 2, 3
 NO_CELL = -32768
 UINT64_MAX = (1 << 64) - 1
@@ -95,6 +95,8 @@ _SIGS = {
     "rm_scene_free": ([P], None),
     "rm_last_error": ([], C.c_char_p),
     "rm_debug_inject": ([C.c_int32, C.c_int32], C.c_int),
+    "rm_debug_alloc_count": ([], C.c_uint64),
+    "rm_debug_fresnel_probe": ([P, C.c_double, P, C.c_int64, P, P, P], C.c_int),
     "rm_version": ([], C.c_char_p),
 }
 

@@ -83,12 +83,13 @@ def tx_from(obj) -> L.rm_tx:
 def params_struct(freq_hz, max_depth, map_origin=(0.0, 0.0, 1.5), cell_size=1.0, nx=100, ny=100,
                   reflect=True, refract=True, los=True, stats=False, deposit=0, block_size=0,
                   blocks_per_sm=0, queue_chunk=0, rr_depth=0, rr_max_prob=0.0,
-                  gain_threshold=0.0, diffuse=False, refill_min=0) -> L.rm_trace_params:
+                  gain_threshold=0.0, diffuse=False, refill_min=0, record_coin=False) -> L.rm_trace_params:
     p = L.rm_trace_params()
     p.freq_hz = float(freq_hz)
     p.max_depth = int(max_depth)
     p.flags = ((L.RM_REFLECT if reflect else 0) | (L.RM_REFRACT if refract else 0) |
-               (L.RM_LOS if los else 0) | (L.RM_STATS if stats else 0) | (L.RM_DIFFUSE if diffuse else 0))
+               (L.RM_LOS if los else 0) | (L.RM_STATS if stats else 0) | (L.RM_DIFFUSE if diffuse else 0) |
+               (L.RM_RECORD_COIN if record_coin else 0))
     for i in range(3):
         p.map_origin[i] = float(map_origin[i])
     p.cell_size = float(cell_size)
@@ -103,7 +104,8 @@ def params_from(obj, stats=False, block_size=0, blocks_per_sm=0, queue_chunk=0, 
     return params_struct(obj.freq_hz, obj.max_depth, obj.map_origin, obj.cell_size, obj.nx, obj.ny, obj.reflect,
                          obj.refract, obj.los, stats, obj.deposit, block_size, blocks_per_sm, queue_chunk,
                          getattr(obj, "rr_depth", 0), getattr(obj, "rr_max_prob", 0.0),
-                         getattr(obj, "gain_threshold", 0.0), getattr(obj, "diffuse", False), refill_min)
+                         getattr(obj, "gain_threshold", 0.0), getattr(obj, "diffuse", False), refill_min,
+                         getattr(obj, "record_coin", False))
 
 
 def _tx_array(txs):

@@ -8,6 +8,9 @@ CASE is one of
   adjoint      adjoint of the differentiable workload (8 materials, bilinear)
   diffraction  first-order diffraction map, Manhattan, 1200 wedges
   city         forward trace, 0.97M-triangle procedural city, 1 TX, 1e7 rays, depth 8
+  city_adjoint forward then adjoint (uniform dL/dC) of the same city trace
+  batched      the 64-TX batched workload (depth 3) in one launch; --rays sets the
+               lattice stride of every transmitter (default 1: the full workload)
   mesh         the Manhattan trace on a 131072-triangle terrain measurement surface
 Each case prints one line: case, kernel ms of the last call, and its work
 counters.
@@ -26,7 +29,8 @@ def main(argv=None):
     from synth import scenes as S
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction", "city", "mesh"])
+    ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction", "city", "city_adjoint",
+                                    "batched", "mesh"])
     ap.add_argument("--rays", type=int, default=0, help="rays per TX (trace cases) or samples per wedge")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
@@ -36,13 +40,17 @@ def main(argv=None):
             sc = sc.with_scattering(0.5, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
             p = copy.copy(p)
             p.diffuse = True
-    elif a.case == "city":
+    elif a.case in ("city", "city_adjoint"):
         sc, txs, p = S.workload(5)
         txs = txs[:1]
         txs[0].num_rays = 10_000_000
+    elif a.case == "batched":
+        sc, txs, p = S.workload(3)
+        for t in txs:
+            t.ray_stride = max(1, a.rays)
     else:
         sc, txs, p = S.workload(4)
-    if a.rays and a.case != "diffraction":
+    if a.rays and a.case not in ("diffraction", "batched"):
         txs[0].num_rays = a.rays
     gs = api.Scene.from_obj(sc)
     su = api.surface(*S.terrain_surface(256.0, 256)) if a.case == "mesh" else None
@@ -51,7 +59,7 @@ def main(argv=None):
             r = api.trace_mesh(gs, su, txs, p)
         elif a.case == "diffraction":
             r = api.diffraction_map(gs, txs, p, a.rays or 4096)
-        elif a.case == "adjoint":
+        elif a.case in ("adjoint", "city_adjoint"):
             f = api.trace(gs, txs, p)
             r = api.grad(gs, txs, p, torch.ones_like(f["maps"]))
         else:

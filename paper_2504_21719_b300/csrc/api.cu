@@ -142,7 +142,7 @@ int32_t* pin_slot_acquire() {
     std::lock_guard<std::mutex> g(g_pin.m);
     if (!g_pin.tried) {
         g_pin.tried = true;
-        if (cudaHostAlloc((void**)&g_pin.slab, sizeof(int32_t) * PIN_SLOTS, cudaHostAllocPortable) == cudaSuccess)
+        if (lib_host_alloc((void**)&g_pin.slab, sizeof(int32_t) * PIN_SLOTS, cudaHostAllocPortable) == cudaSuccess)
             for (int i = PIN_SLOTS - 1; i >= 0; --i) g_pin.free.push_back(i);
         else
             g_pin.slab = nullptr;
@@ -381,6 +381,34 @@ void pack_array(const rm_tx& x, double lam, TxDev& d, std::vector<AntDev>& out) 
 }
 
 
+// Per-material constants at angular frequency omega (k0 = omega / c0): the
+// field's eta = eps_r - j sigma / (eps0 omega) from e, the sampling eta from s,
+// the slab phase constant k0 d as hi + lo floats and the diffuse parameters.
+// Returns whether the material scatters diffusely in this call.
+bool fill_matdev(const rm_material& e, const rm_material& s, double omega, double k0, unsigned flags, MatDev* out) {
+    MatDev& d = *out;
+    d.eta_re = e.eps_r;
+    d.eta_im = (float)(-(double)e.sigma / (EPS0 * omega));
+    d.seta_re = s.eps_r;
+    d.seta_im = (float)(-(double)s.sigma / (EPS0 * omega));
+    const double k0d = e.thickness > 0.0f ? k0 * (double)e.thickness : 0.0;
+    d.k0d_hi = (float)k0d;
+    d.k0d_lo = (float)(k0d - (double)d.k0d_hi);
+    d.slab = e.thickness > 0.0f ? 1 : 0;
+    const bool dif = (flags & RM_DIFFUSE) && (flags & RM_REFLECT) && e.scattering > 0.0f;
+    const double Sd = dif ? (double)e.scattering : 0.0;
+    d.S = (float)Sd;
+    d.R2 = (float)((1.0 - Sd) * (1.0 + Sd));
+    d.Rred = (float)std::sqrt((1.0 - Sd) * (1.0 + Sd));
+    d.sqk = dif ? (float)std::sqrt((double)e.xpd_k) : 0.0f;
+    d.sq1k = dif ? (float)std::sqrt(1.0 - (double)e.xpd_k) : 1.0f;
+    d.pattern = dif ? e.pattern : 0;
+    d.alpha_r = dif && e.pattern > 0 ? e.alpha_r : 1;
+    d.alpha_i = dif && e.pattern == 2 ? e.alpha_i : 1;
+    d.lam = dif && e.pattern == 2 ? e.lobe_lambda : 1.0f;
+    return dif;
+}
+
 void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
              const rm_material* sampling_override, Prepared* P, const rm_scene* surf = nullptr) {
     const double f = p->freq_hz, omega = 2.0 * PI * f, k0 = omega / C0, lam = C0 / f;
@@ -390,27 +418,7 @@ void prepare(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_pa
     for (int m = 0; m < sc->nm; ++m) {
         const rm_material& e = sc->mats[m];
         const rm_material& s = sampling_override ? sampling_override[m] : sm[m];
-        MatDev& d = P->mats[m];
-        d.eta_re = e.eps_r;
-        d.eta_im = (float)(-(double)e.sigma / (EPS0 * omega));
-        d.seta_re = s.eps_r;
-        d.seta_im = (float)(-(double)s.sigma / (EPS0 * omega));
-        const double k0d = e.thickness > 0.0f ? k0 * (double)e.thickness : 0.0;
-        d.k0d_hi = (float)k0d;
-        d.k0d_lo = (float)(k0d - (double)d.k0d_hi);
-        d.slab = e.thickness > 0.0f ? 1 : 0;
-        const bool dif = (p->flags & RM_DIFFUSE) && (p->flags & RM_REFLECT) && e.scattering > 0.0f;
-        const double Sd = dif ? (double)e.scattering : 0.0;
-        d.S = (float)Sd;
-        d.R2 = (float)((1.0 - Sd) * (1.0 + Sd));
-        d.Rred = (float)std::sqrt((1.0 - Sd) * (1.0 + Sd));
-        d.sqk = dif ? (float)std::sqrt((double)e.xpd_k) : 0.0f;
-        d.sq1k = dif ? (float)std::sqrt(1.0 - (double)e.xpd_k) : 1.0f;
-        d.pattern = dif ? e.pattern : 0;
-        d.alpha_r = dif && e.pattern > 0 ? e.alpha_r : 1;
-        d.alpha_i = dif && e.pattern == 2 ? e.alpha_i : 1;
-        d.lam = dif && e.pattern == 2 ? e.lobe_lambda : 1.0f;
-        if (dif) P->diffuse = true;
+        if (fill_matdev(e, s, omega, k0, p->flags, &P->mats[m])) P->diffuse = true;
         if (s.eps_r != e.eps_r || s.sigma != e.sigma) same = false;
     }
     P->tx.resize(ntx);
@@ -585,7 +593,7 @@ cudaError_t upload_stage(size_t bytes, char** out) {
         g_up.buf = nullptr;
         g_up.cap = 0;
         const size_t want = std::max(bytes, size_t(256) << 10);
-        if ((e = cudaHostAlloc((void**)&g_up.buf, want, cudaHostAllocPortable)) != cudaSuccess) return e;
+        if ((e = lib_host_alloc((void**)&g_up.buf, want, cudaHostAllocPortable)) != cudaSuccess) return e;
         g_up.cap = want;
     }
     *out = g_up.buf;
@@ -607,7 +615,7 @@ cudaError_t device_block(size_t bytes, char** out) {
     }
     if (!g_res.dblock) {
         const size_t want = (bytes + (size_t(1) << 20) - 1) & ~((size_t(1) << 20) - 1);
-        if ((e = cudaMalloc((void**)&g_res.dblock, want)) != cudaSuccess) return e;
+        if ((e = lib_malloc((void**)&g_res.dblock, want)) != cudaSuccess) return e;
         g_res.dcap = want;
         g_res.d_device = dev;
     }
@@ -621,7 +629,7 @@ cudaError_t staging(size_t bytes, char** out) {
         g_res.stage = nullptr;
         g_res.cap = 0;
         const size_t want = std::max(bytes, size_t(64) << 10);
-        cudaError_t e = cudaHostAlloc((void**)&g_res.stage, want, cudaHostAllocDefault);
+        cudaError_t e = lib_host_alloc((void**)&g_res.stage, want, cudaHostAllocDefault);
         if (e != cudaSuccess) return e;
         g_res.cap = want;
     }
@@ -748,15 +756,36 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
 
 }  // namespace
 
+// Allocation calls made by the library in this process (rm_debug_alloc_count).
+static std::atomic<unsigned long long> g_alloc_calls{0};
+void rmsbr::note_alloc() { g_alloc_calls.fetch_add(1, std::memory_order_relaxed); }
+
 extern "C" {
 
 const char* rm_last_error(void) { return g_err.c_str(); }
+
+uint64_t rm_debug_alloc_count(void) { return g_alloc_calls.load(std::memory_order_relaxed); }
 
 rm_status rm_debug_inject(int32_t kind, int32_t count) {
     if (kind < RM_FAULT_ALLOC || kind > RM_FAULT_OVERFLOW || count < 0)
         return fail(RM_EINVAL, "kind must be RM_FAULT_ALLOC, RM_FAULT_LAUNCH or RM_FAULT_OVERFLOW, count >= 0");
     std::call_once(g_fault_env, arm_from_env);
     g_fault[kind].store(count);
+    return RM_OK;
+}
+
+rm_status rm_debug_fresnel_probe(const rm_material* mat, double freq_hz, const float* cos1_dev, int64_t n,
+                                 float* wR_dev, float* wT_dev, void* stream) {
+    if (!mat) return fail(RM_EINVAL, "mat is NULL");
+    if ((n > 0 && (!cos1_dev || !wR_dev || !wT_dev)) || n < 0) return fail(RM_EINVAL, "bad arrays");
+    if (!(freq_hz > 0.0) || !std::isfinite(freq_hz)) return fail(RM_EINVAL, "freq_hz must be > 0");
+    rm_status st = check_materials(mat, 1);
+    if (st != RM_OK) return st;
+    const double omega = 2.0 * PI * freq_hz;
+    MatDev d;
+    std::memset(&d, 0, sizeof d);
+    fill_matdev(*mat, *mat, omega, omega / C0, RM_REFLECT | RM_REFRACT, &d);
+    RM_CUDA(launch_fresnel_probe(d, cos1_dev, n, wR_dev, wT_dev, S(stream)));
     return RM_OK;
 }
 
@@ -785,7 +814,7 @@ rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tri
         const size_t o_t = align256(sizeof(float) * 3 * nv), o_m = o_t + align256(sizeof(int32_t) * 3 * nt),
                      o_f = o_m + align256(sizeof(int32_t) * nt);
         keep_pool_memory();
-        if ((e = cudaMallocAsync((void**)&sc->mesh_mem, o_f + sizeof(int32_t), S(stream))) != cudaSuccess)
+        if ((e = lib_malloc_async((void**)&sc->mesh_mem, o_f + sizeof(int32_t), S(stream))) != cudaSuccess)
             return cleanup(cuda_fail(e, "cudaMallocAsync"));
         sc->verts = reinterpret_cast<float*>(sc->mesh_mem);
         sc->tris = reinterpret_cast<int32_t*>(sc->mesh_mem + o_t);
@@ -839,7 +868,7 @@ rm_status rm_scene_upload_host(const float* verts_host, int64_t nv, const int32_
                      o_f = o_m + align256(sizeof(int32_t) * nt);
         keep_pool_memory();
         cudaError_t e;
-        if ((e = cudaMallocAsync((void**)&sc->mesh_mem, o_f + sizeof(int32_t), S(stream))) != cudaSuccess)
+        if ((e = lib_malloc_async((void**)&sc->mesh_mem, o_f + sizeof(int32_t), S(stream))) != cudaSuccess)
             return cleanup(cuda_fail(e, "cudaMallocAsync"));
         sc->verts = reinterpret_cast<float*>(sc->mesh_mem);
         sc->tris = reinterpret_cast<int32_t*>(sc->mesh_mem + o_t);
@@ -891,7 +920,7 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
             cudaFree(sc->bvh_mem);
             sc->bvh_mem = nullptr;
         }
-        RM_CUDA(cudaMallocAsync((void**)&sc->bvh_mem, o_r + sizeof(float4) * 3 * n, S(stream)));
+        RM_CUDA(lib_malloc_async((void**)&sc->bvh_mem, o_r + sizeof(float4) * 3 * n, S(stream)));
         sc->keys = reinterpret_cast<uint64_t*>(sc->bvh_mem);
         sc->order = reinterpret_cast<int32_t*>(sc->bvh_mem + o_o);
         sc->nodes = reinterpret_cast<float4*>(sc->bvh_mem + o_n);
@@ -993,7 +1022,7 @@ rm_status rm_db_mse_loss(const float* maps_dev, const float* target_dev, int64_t
     if (ncells < 1) return fail(RM_EINVAL, "ncells must be >= 1");
     if (!(floor_linear >= 0.0f)) return fail(RM_EINVAL, "floor_linear must be >= 0");
     double* acc = nullptr;
-    RM_CUDA(cudaMallocAsync((void**)&acc, 2 * sizeof(double), S(stream)));
+    RM_CUDA(lib_malloc_async((void**)&acc, 2 * sizeof(double), S(stream)));
     cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), S(stream));
     if (e == cudaSuccess)
         e = launch_db_mse(maps_dev, target_dev, ncells, floor_linear, acc, loss_dev, dL_dmaps_dev, valid_dev, S(stream));
@@ -1020,7 +1049,7 @@ rm_status rm_trace_plan_create(const rm_scene* sc, const rm_tx* tx, int32_t ntx,
     auto cleanup = [&](rm_status s) { rm_trace_plan_free(pl); return s; };
     cudaError_t e;
     if ((e = cudaStreamSynchronize(S(stream))) != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamSynchronize"));
-    if ((e = cudaMalloc((void**)&pl->dev, bytes)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
+    if ((e = lib_malloc((void**)&pl->dev, bytes)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc"));
     if ((e = cudaMemcpy(pl->dev + o_mat, P.mats.data(), P.mats.size() * sizeof(MatDev), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaMemcpy"));
     if ((e = cudaMemcpy(pl->dev + o_tx, P.tx.data(), P.tx.size() * sizeof(TxDev), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -1396,6 +1425,13 @@ extern "C" rm_status rm_radio_map_trace_noalloc(const rm_scene* sc, const rm_tx*
     if (st != RM_OK) return st;
     if ((st = check_device(sc)) != RM_OK) return st;
     if (!maps_dev) return fail(RM_EINVAL, "maps_dev is NULL");
+    // the call reads its counters back and waits for them: a stream in capture
+    // mode would fail there and invalidate the caller's capture, so it is
+    // refused before anything is enqueued
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RM_CUDA(cudaStreamIsCapturing(S(stream), &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(RM_ESTATE, "rm_radio_map_trace_noalloc synchronises its stream, which is capturing");
     Prepared P;
     prepare(sc, tx, ntx, p, nullptr, &P);
     size_t o_mat, o_tx;

@@ -658,7 +658,7 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host)
     if (n <= SMALL_SORT) {
         // one launch: the count goes through a 4-byte scratch word
         int32_t* cnt = nullptr;
-        if ((err = cudaMallocAsync((void**)&cnt, sizeof(int32_t), s)) != cudaSuccess) return err;
+        if ((err = lib_malloc_async((void**)&cnt, sizeof(int32_t), s)) != cudaSuccess) return err;
         const int smem = (int)sizeof(SmallBuildSmem);
         if ((err = cudaFuncSetAttribute(k_build_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
             cudaSuccess) {
@@ -686,7 +686,7 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host)
                  o_vis = take(sizeof(int32_t) * n), o_sb = take(sizeof(float) * 6),
                  o_lg = take(sizeof(int8_t) * n), o_cnt = take(sizeof(int32_t));
     char* base = nullptr;
-    if ((err = cudaMallocAsync((void**)&base, off, s)) != cudaSuccess) return err;
+    if ((err = lib_malloc_async((void**)&base, off, s)) != cudaSuccess) return err;
     // every later error still returns the scratch block to the pool
     auto fail_free = [&](cudaError_t e) { cudaFreeAsync(base, s); return e; };
     float* aabb = (float*)(base + o_aabb);

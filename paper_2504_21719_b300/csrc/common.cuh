@@ -147,10 +147,29 @@ cudaError_t launch_diffraction(const DiffArgs& a, int block, cudaStream_t s, int
 // p(Z) = sum_{n<N} a_{n+1} Z^n, Z = (L + iz)/(L - iz) (host, double).
 void faddeeva_coefficients(int N, double* L, double* a);
 
+// Every device and pinned-host allocation of the library goes through these
+// wrappers, which count the calls for rm_debug_alloc_count (api.cu).
+void note_alloc();
+inline cudaError_t lib_malloc(void** p, size_t n) {
+    note_alloc();
+    return cudaMalloc(p, n);
+}
+inline cudaError_t lib_malloc_async(void** p, size_t n, cudaStream_t s) {
+    note_alloc();
+    return cudaMallocAsync(p, n, s);
+}
+inline cudaError_t lib_host_alloc(void** p, size_t n, unsigned flags) {
+    note_alloc();
+    return cudaHostAlloc(p, n, flags);
+}
+
 // Host-side launchers (trace.cu)
 cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, bool diffuse,
                          int block, int blocks_per_sm, cudaStream_t s, int* grid_out, bool mesh = false);
 int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh = false);
+// wR, wT (the coin's weights) of one material at n cosines of incidence (trace.cu)
+cudaError_t launch_fresnel_probe(const MatDev& m, const float* cos1, long long n, float* wR, float* wT,
+                                 cudaStream_t s);
 
 // BVH build (bvh.cu)
 struct BvhBuffers {

@@ -27,6 +27,7 @@
 // instantiations, so both take the same hits, decisions and cells.  Division
 // and square root are the approximate (few-ulp) forms, except the slab test's
 // reciprocals.
+#include <algorithm>
 #include <cfloat>
 
 #include "common.cuh"
@@ -1007,7 +1008,8 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                     const float c1 = DIFF ? M.R2 * c2 : c2;
                     const float u = rng_u(s_tx[txi].seed, n, depth);
                     const int dec = (u < c1) ? 0 : ((DIFF && u < c2) ? 2 : 1);
-                    if (rec) rec->decision = dec;
+                    // (debug) the threshold q(R) the coin compared u with, in units of 2^-22
+                    if (rec) rec->decision = dec | ((A.flags & RM_RECORD_COIN) ? __float2int_rn(c1 * 0x1p22f) << 8 : 0);
                     if (DIFF)
                         inv_pr = inv_pr * (wsum / (dec == 0 ? M.R2 * wR : (dec == 2 ? M.S * M.S * wR : wT)));
                     else
@@ -1242,7 +1244,28 @@ const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, boo
     return nullptr;
 }
 
+// The sampling weights of one material at given cosines of incidence, from
+// the tracer's own fresnel() (same translation unit, same rounding): wR =
+// |r_perp|^2 + |r_par|^2 and wT = |t_perp|^2 + |t_par|^2, whose ratio the
+// coin of every interaction compares with its variate.
+__global__ void k_fresnel_probe(const MatDev M, const float* __restrict__ cos1, long long n, float* wR,
+                                float* wT) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const Coef co = fresnel(C(M.eta_re, M.eta_im), cos1[i], M.k0d_hi, M.k0d_lo, M.slab != 0, nullptr);
+        wR[i] = cabs2(co.rp) + cabs2(co.rl);
+        wT[i] = cabs2(co.tp) + cabs2(co.tl);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_fresnel_probe(const MatDev& m, const float* cos1, long long n, float* wR, float* wT,
+                                 cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 148LL * 8);
+    k_fresnel_probe<<<(unsigned)blocks, 256, 0, s>>>(m, cos1, n, wR, wT);
+    return cudaGetLastError();
+}
 
 int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh) {
     const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse, mesh);

@@ -1,4 +1,8 @@
 """Shared helpers of the GPU parity tests (imported by tests only)."""
+import copy
+import json
+import os
+
 import numpy as np
 
 MAP_RTOL = 1e-3          # per-cell relative tolerance of the maps
@@ -17,6 +21,35 @@ POS_EPS = 4.0 * 2.0 ** -24
 MAX_ADOPT_FRAC = 1e-2
 
 
+def _log(kind, rep, extra=None):
+    """Append one replay report to the file named by RM_PARITY_LOG (if set), so
+    that a GPU run can collect the adoption rates of every parity test."""
+    path = os.environ.get("RM_PARITY_LOG")
+    if not path:
+        return
+    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    row = {"test": test, "kind": kind, **{k: v for k, v in rep.items() if k != "fail_info"}}
+    if extra:
+        row.update(extra)
+    with open(path, "a") as f:
+        f.write(json.dumps(row) + "\n")
+
+
+def coin(params):
+    """A copy of the trace parameters whose debug record also carries the
+    GPU's coin probability q(R) of every decision (RM_RECORD_COIN)."""
+    q = copy.copy(params)
+    q.record_coin = True
+    return q
+
+
+def check_coins(rep):
+    """When the GPU recorded its coin probabilities (RM_RECORD_COIN), every one
+    must lie inside the replay's decision window around the oracle's q(R)."""
+    if rep.get("coin_checked", 0) > 0:
+        assert rep["coin_outside"] == 0, rep
+
+
 def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max_adopt_frac=MAX_ADOPT_FRAC):
     """Replay the GPU's discrete choices in the FP64 oracle (certifying every
     difference as a near-tie) and compare the maps cell by cell."""
@@ -26,7 +59,9 @@ def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max
     arr = getattr(tx, "ant_pos", None) is not None and len(tx.ant_pos) > 0
     r = orc.radio_map(scene, tx, params, mode="replay", record=rec, mass=bil or arr)
     rep = r["report"]
+    _log("map", rep)
     assert rep["failures"] == 0, rep
+    check_coins(rep)
     adopted = rep["adopted_hit"] + rep["adopted_cell"] + rep["adopted_decision"]
     assert adopted <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
     ref = r["map"]
@@ -60,6 +95,7 @@ def compare_diffraction(orc, scene, tx, params, samples_per_wedge, gpu_map, gpu_
     rec = np.asarray(gpu_record).reshape(-1, 4)
     r = orc.diffraction_map(scene, tx, params, samples_per_wedge, mode="replay", record=rec, slack=True)
     rep = r["report"]
+    _log("diffraction", rep)
     assert rep["failures"] == 0, rep
     adopted = rep["adopted_hit"] + rep["adopted_cell"] + rep["adopted_decision"]
     assert adopted <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
@@ -89,7 +125,9 @@ def compare_mesh(orc, scene, tx, params, surf_v, surf_t, gpu_map, gpu_record, rt
     rec = np.asarray(gpu_record).reshape(tx.count(), L + 1, 4)
     r = orc.radio_map_mesh(scene, tx, params, surf_v, surf_t, mode="replay", record=rec, slack=True)
     rep = r["report"]
+    _log("mesh", rep)
     assert rep["failures"] == 0, rep
+    check_coins(rep)
     adopted = rep["adopted_hit"] + rep["adopted_decision"]
     assert adopted <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
     ref = r["map"]
@@ -114,6 +152,7 @@ def compare_diffraction_mesh(orc, scene, tx, params, samples_per_wedge, surf_v, 
     r = orc.diffraction_map_mesh(scene, tx, params, samples_per_wedge, surf_v, surf_t, mode="replay", record=rec,
                                  slack=True)
     rep = r["report"]
+    _log("diffraction_mesh", rep)
     assert rep["failures"] == 0, rep
     assert rep["adopted_hit"] <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
     ref = r["map"]

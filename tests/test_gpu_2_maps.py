@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from synth import scenes as S
-from gpu_helpers import compare_maps, FLOOR
+from gpu_helpers import compare_maps, FLOOR, coin
 
 pytestmark = pytest.mark.gpu
 
@@ -17,7 +17,7 @@ def _run(api, sc, tx, p, gs=None, **kw):
     own = gs is None
     if own:
         gs = api.Scene.from_obj(sc)
-    r = api.trace(gs, [tx], p, record=True, **kw)
+    r = api.trace(gs, [tx], coin(p), record=True, **kw)
     torch.cuda.synchronize()
     out = (r["maps"][0].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
     if own:

@@ -1,5 +1,6 @@
 """Adjoint kernel vs the oracle's dual-number gradient (same frozen choices,
 taken from the GPU's own record) and vs GPU finite differences; dB loss."""
+import copy
 import math
 
 import numpy as np
@@ -18,6 +19,7 @@ def _setup(stride=13, deposit=1):
     tx = txs[0]
     tx.ray_stride = stride
     p.deposit = deposit
+    p.record_coin = True              # records carry the GPU's coin probabilities
     return sc, tx, p
 
 
@@ -192,4 +194,62 @@ def test_adjoint_with_array_matches_oracle(orc, api, regular):
     scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
     err = np.abs(ad - ref) / scale
     assert np.all(err <= GRAD_RTOL), err
+    gs.free()
+
+
+@pytest.mark.parametrize("deposit", [0, 1])
+def test_large_city_adjoint_matches_oracle(orc, api, deposit):
+    """Procedural city (0.97M triangles), depth 8, 2048 x 2048 cells: the
+    adjoint of the dB loss on a lattice subset of one transmitter against the
+    oracle's dual-number gradient along the GPU's record, after the oracle (brute
+    force over every triangle) has certified that record.  Box cells give the
+    material gradient only (the TX-position gradient is exactly 0); bilinear
+    cells add the TX position."""
+    sc, txs, p = S.workload(5)
+    tx = copy.copy(txs[0])
+    tx.ray_stride, tx.ray_begin = 166_667, 11                # 600 rays of the 1e8-ray lattice
+    p.deposit = deposit
+    p.record_coin = True
+    gs = api.Scene.from_obj(sc)
+    tgt = _target(api, sc, tx, p)
+    f = api.trace(gs, [tx], p, record=True)
+    loss, dLdC, valid = api.db_mse_loss(f["maps"][0], tgt)
+    assert int(valid) >= 100
+    a = api.grad(gs, [tx], p, dLdC.view(1, p.ny, p.nx), record=True)
+    assert torch.equal(f["record"], a["record"])
+    ad = np.concatenate([a["d_eps"].cpu().numpy(), a["d_sigma"].cpu().numpy(), a["d_tx"][0].cpu().numpy()])
+    rec = f["record"].view(tx.count(), p.max_depth + 1, 4).cpu().numpy()
+    assert (rec[:, 1:, 0] >= 0).sum() > 100                  # paths with interactions reach the map
+    compare_maps(orc, sc, tx, p, f["maps"][0].cpu().numpy(), rec)
+    de, ds, dt = orc.grad(sc, tx, p, rec, dLdC.double().cpu().numpy())
+    ref = np.concatenate([de, ds, dt])
+    assert np.abs(ref[:2 * sc.nm]).max() > 0
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    err = np.abs(ad - ref) / scale
+    assert np.all(err <= GRAD_RTOL), err
+    if deposit == 0:
+        assert np.all(ad[-3:] == 0.0)
+    gs.free()
+
+
+def test_large_city_full_adjoint_partition(api):
+    """The full-size city adjoint (16 TX x 1e8 rays, depth 8, one launch in the
+    benchmark's configuration) equals the sum of the adjoints of two disjoint
+    lattice halves, to the order of the FP32 block sums."""
+    from paper_2504_21719_b300.shard import partition_tx
+    sc, txs, p = S.workload(5)
+    gs = api.Scene.from_obj(sc)
+    f = api.trace(gs, txs, p)
+    # dL/dC of a loss that weights every cell by its own path gain's dB value
+    g = (10.0 * torch.log10(f["maps"].clamp_min(1e-15)) + 150.0) * 1e-6
+    full = api.grad(gs, txs, p, g)
+    assert full["stats"]["segments"] == f["stats"]["segments"]
+    parts = [api.grad(gs, [partition_tx(t, r, 2) for t in txs], p, g) for r in range(2)]
+    for key in ("d_eps", "d_sigma"):
+        a = full[key].double()
+        b = parts[0][key].double() + parts[1][key].double()
+        scale = a.abs().max().item()
+        assert scale > 0
+        assert torch.all((a - b).abs() <= 1e-4 * scale), (key, a, b)
+    assert torch.all(full["d_tx"] == 0)
     gs.free()

@@ -9,7 +9,7 @@ import pytest
 import torch
 
 from synth import scenes as S
-from gpu_helpers import compare_maps
+from gpu_helpers import compare_maps, coin
 
 pytestmark = pytest.mark.gpu
 GRAD_RTOL = 1e-2
@@ -32,7 +32,7 @@ def _manhattan(stride=97):
 
 def _run(api, sc, tx, p):
     gs = api.Scene.from_obj(sc)
-    r = api.trace(gs, [tx], p, record=True)
+    r = api.trace(gs, [tx], coin(p), record=True)
     torch.cuda.synchronize()
     out = (r["maps"][0].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
     gs.free()

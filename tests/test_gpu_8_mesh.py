@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from synth import scenes as S
-from gpu_helpers import compare_mesh
+from gpu_helpers import compare_mesh, coin
 from test_oracle_mesh import grid_surface
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +22,7 @@ def terrain(n=32, half=64.0):
 def _run(api, sc, surf_v, surf_t, txs, p):
     gs = api.Scene.from_obj(sc)
     su = api.surface(surf_v, surf_t)
-    r = api.trace_mesh(gs, su, txs, p, record=True)
+    r = api.trace_mesh(gs, su, txs, coin(p), record=True)
     torch.cuda.synchronize()
     out = (r["maps"].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
     su.free()
