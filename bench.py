@@ -261,10 +261,11 @@ def time_plan(torch, plan, steps, warmup, flush, clocks=None):
     return step_ms, kern_ms, st, clk
 
 
-def e2e_host(api, torch, sc, txs, prm, out, steps, warmup, flush, breakdown=False):
+def e2e_host(api, torch, sc, txs, prm, out, steps, warmup, flush, breakdown=0):
     """End to end through the public API from pinned host arrays: scene upload,
     LBVH build, trace and the read-back of the maps, every step.  With
-    `breakdown`, one more pass times each part alone (synchronised after each)."""
+    `breakdown` > 0, that many more steps time each part alone (synchronised
+    after each)."""
     vh = torch.from_numpy(sc.verts).pin_memory()
     th = torch.from_numpy(sc.tris).pin_memory()
     mh = torch.from_numpy(sc.tri_mat).pin_memory()
@@ -289,7 +290,7 @@ def e2e_host(api, torch, sc, txs, prm, out, steps, warmup, flush, breakdown=Fals
            "includes": "scene upload + LBVH build + trace + map readback, per step"}
     if breakdown:
         parts = {"upload": [], "build": [], "trace_call": [], "trace_kernel": [], "readback": []}
-        for i in range(warmup + steps):
+        for i in range(warmup + breakdown):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -366,12 +367,13 @@ def run_ours(args, world, rank, local):
     # ---------------- forward + adjoint over the materials, same workload ----------------
     adjoint = None
     if not args.no_adjoint:
-        adjoint = city_adjoint(api, S, torch, sc, txs, p, prm, gs, kavg, seg_step)
+        adjoint = city_adjoint(api, S, torch, sc, txs, p, prm, tuned_params(api, p, gpu_name, "city_adjoint")[0], gs,
+                               kavg, seg_step)
 
     # ---------------- end to end from host arrays ----------------
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_host(api, torch, sc, txs, prm, maps, args.steps, 1, flush)
+        e2e = e2e_host(api, torch, sc, txs, prm, maps, args.steps, 1, flush, breakdown=2)
         e2e["value"] *= world
     gs.free()
     del maps
@@ -407,7 +409,7 @@ def run_ours(args, world, rank, local):
     return line
 
 
-def city_adjoint(api, S, torch, sc, txs, p, prm, gs, fwd_kernel_ms, fwd_segments, reps=3):
+def city_adjoint(api, S, torch, sc, txs, p, prm, prm_adj, gs, fwd_kernel_ms, fwd_segments, reps=3):
     """Adjoint of the dB-MSE loss over the materials on the city workload: the
     target maps are traced with seeded perturbed materials, the loss gradient
     comes from the library's loss kernel, then the adjoint kernel is timed."""
@@ -418,10 +420,10 @@ def city_adjoint(api, S, torch, sc, txs, p, prm, gs, fwd_kernel_ms, fwd_segments
     f = api.trace(gs, txs, prm)
     loss, dL, valid = api.db_mse_loss(f["maps"], tgt)
     del tgt
-    api.grad(gs, txs, prm, dL)                     # warm-up
+    api.grad(gs, txs, prm_adj, dL)                 # warm-up
     ak, segs = [], 0
     for _ in range(reps):
-        a = api.grad(gs, txs, prm, dL)
+        a = api.grad(gs, txs, prm_adj, dL)
         ak.append(a["stats"]["kernel_ms"])
         segs = a["stats"]["segments"]
     k = statistics.mean(ak)
@@ -470,7 +472,7 @@ def run_extra(api, S, torch, gpu_name, flush, args):
                         "nodes_per_segment": round(sum(s["nodes_visited"] for s in st) / sum(s["segments"] for s in st), 2),
                         "roofline": roofline(2, "k_trace (persistent forward tracer)", segs, km,
                                              "instruction issue (scene and map stay in L1/L2)", True),
-                        "e2e": e2e_host(api, torch, sc, txs, prm, maps, steps, 3, flush, breakdown=True)}
+                        "e2e": e2e_host(api, torch, sc, txs, prm, maps, steps, 3, flush, breakdown=steps)}
     if not args.no_cpu_baseline:
         out["manhattan"]["cpu_baseline"] = oracle_sample(2, 8.0)
     base = _kernel_rate(api, gs, txs, prm)
@@ -479,7 +481,7 @@ def run_extra(api, S, torch, gpu_name, flush, args):
     pd = copy.copy(p)
     pd.diffuse = True
     gsd = api.Scene.from_obj(scd)
-    d = _kernel_rate(api, gsd, txs, tuned_params(api, pd, gpu_name, "manhattan")[0])
+    d = _kernel_rate(api, gsd, txs, tuned_params(api, pd, gpu_name, "diffuse")[0])
     d["vs_specular"] = round(d["value"] / base["value"], 3)
     d["materials"] = "S = 0.5 on every material; ground Lambertian, buildings directive / backscattering"
     d["roofline"] = roofline(0, "k_trace<diffuse>", d["segments"], d["kernel_ms"], "instruction issue", True)
@@ -498,11 +500,12 @@ def run_extra(api, S, torch, gpu_name, flush, args):
     out["synthetic_array_64"] = a
     # first-order diffraction map of the same transmitter: 1200 wedges x 4096 samples
     wl = gs.wedges()
+    pw = tuned_params(api, p, gpu_name, "diffraction")[0]
     for _ in range(2):
-        api.diffraction_map(gs, txs, p, 4096, wedges=wl)
+        api.diffraction_map(gs, txs, pw, 4096, wedges=wl)
     dk, dst = [], None
     for _ in range(5):
-        r = api.diffraction_map(gs, txs, p, 4096, wedges=wl)
+        r = api.diffraction_map(gs, txs, pw, 4096, wedges=wl)
         dk.append(r["stats"]["kernel_ms"])
         dst = r["stats"]
     k = statistics.mean(dk)
@@ -563,15 +566,17 @@ def run_extra(api, S, torch, gpu_name, flush, args):
     gt = api.Scene.from_obj(tgt_sc)
     tgt = api.trace(gt, txs, p)["maps"][0]
     gt.free()
+    pf = tuned_params(api, p, gpu_name, "manhattan")[0]
+    pa = tuned_params(api, p, gpu_name, "adjoint")[0]
     f_ms, a_ms, b_ms, segs = [], [], [], 0
     for i in range(8):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        f = api.trace(gs, txs, p)
+        f = api.trace(gs, txs, pf)
         loss, dL, _ = api.db_mse_loss(f["maps"][0], tgt)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        a = api.grad(gs, txs, p, dL.view(1, p.ny, p.nx))
+        a = api.grad(gs, txs, pa, dL.view(1, p.ny, p.nx))
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         if i >= 3:

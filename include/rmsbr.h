@@ -46,7 +46,8 @@ typedef enum {
     RM_EINVAL = 1,     /* bad argument; nothing was launched */
     RM_ENOMEM = 2,     /* a device allocation failed */
     RM_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
-    RM_EOVERFLOW = 4,  /* a device-side bound was hit (BVH stack); affected rays were dropped */
+    RM_EOVERFLOW = 4,  /* a device-side bound was hit (BVH stack or step budget, or the 8 crossings a
+                          diffracted ray keeps on a mesh surface); the affected work was dropped */
     RM_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
     RM_ESTATE = 6      /* call order: e.g. tracing before rm_bvh_build, or during stream capture */
 } rm_status;

@@ -527,7 +527,7 @@ void fill_stats(const Scratch& h, const Prepared& P, rm_stats* st) {
         st->power2_per_depth[l] = h.pw2[l];
         st->escaped_power_per_depth[l] = h.esc[l];
     }
-    st->status = (h.status & 1) ? RM_EOVERFLOW : RM_OK;
+    st->status = (h.status & 3) ? RM_EOVERFLOW : RM_OK;
     st->kernel_ms = P.kernel_ms;
 }
 
@@ -1335,6 +1335,9 @@ rm_status run_diffraction(const rm_scene* sc, const rm_scene* surf, const rm_wed
     if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
     if (stats) fill_stats(host, P, stats);
     if (host.status & 1) return fail(RM_EOVERFLOW, "BVH traversal stack overflow in a visibility query");
+    if (host.status & 2)
+        return fail(RM_EOVERFLOW, "a diffracted ray crossed the measurement surface more than 8 times; "
+                                  "its crossings beyond the 8th were dropped");
     return RM_OK;
 }
 }  // namespace

@@ -68,7 +68,7 @@ struct Scratch {
     unsigned long long seg_depth[RM_MAX_DEPTH + 1];
     double pw[RM_MAX_DEPTH + 1], pw2[RM_MAX_DEPTH + 1], esc[RM_MAX_DEPTH + 1];
     double grad[2 * RM_MAX_MATERIALS + 3 * RM_MAX_TX];
-    int32_t status;              // bit 0: stack overflow
+    int32_t status;              // bit 0: traversal stack or step budget overflow; bit 1: crossing limit
     int32_t pad;
 };
 

@@ -89,8 +89,8 @@ __device__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float
         const float t0x = (lx - o.x) * ix, t1x = (hx - o.x) * ix;
         const float t0y = (ly - o.y) * iy, t1y = (hy - o.y) * iy;
         const float t0z = (lz - o.z) * iz, t1z = (hz - o.z) * iz;
-        const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), tmin));
-        const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax)) * 1.0000004f;
+        const float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), tmin));
+        const float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), tmax)) * 1.0000004f;
         return tn <= tf;
     };
     int stack[STACK_SIZE];
@@ -269,8 +269,9 @@ __device__ __forceinline__ float diffracted_power(const DiffArgs& A, const TxDev
 }
 
 // Crossings t > 1e-9 of the ray v + t k with a mesh measurement surface, up to
-// MAX_CROSS of them (more set *overflow): distance, triangle, and the
-// unnormalised normal (b - a) x (c - a), whose length is twice the area.
+// MAX_CROSS of them (more set *xlimit; a traversal overflow sets *overflow):
+// distance, triangle, and the unnormalised normal (b - a) x (c - a), whose
+// length is twice the area.
 constexpr int MAX_CROSS = 8;
 struct Crossing {
     float t;
@@ -278,7 +279,7 @@ struct Crossing {
     f3 nrm;
 };
 __device__ __noinline__ int surface_hits(const float4* __restrict__ nodes, const float4* __restrict__ tris, int nt,
-                                         int nlarge, f3 o, f3 k, Crossing* out, bool* overflow) {
+                                         int nlarge, f3 o, f3 k, Crossing* out, bool* overflow, bool* xlimit) {
     int nh = 0;
     auto leaf = [&](int slot) {
         const float4* tp = tris + 3 * (size_t)slot;
@@ -298,7 +299,7 @@ __device__ __noinline__ int surface_hits(const float4* __restrict__ nodes, const
         const float t = dot(e2, q) * inv;
         if (!(t > 1e-9f)) return;
         if (nh < MAX_CROSS) out[nh++] = Crossing{t, __float_as_int(r2.z), cross(e1, e2)};
-        else *overflow = true;
+        else *xlimit = true;
     };
 #pragma unroll 1
     for (int j = 0; j < nlarge; ++j) leaf(nt + j);
@@ -312,8 +313,8 @@ __device__ __noinline__ int surface_hits(const float4* __restrict__ nodes, const
         const float t0x = (lx - o.x) * ix, t1x = (hx - o.x) * ix;
         const float t0y = (ly - o.y) * iy, t1y = (hy - o.y) * iy;
         const float t0z = (lz - o.z) * iz, t1z = (hz - o.z) * iz;
-        const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
-        const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z)) * 1.0000004f;
+        const float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), 0.0f));
+        const float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fmaxf(t0z, t1z)) * 1.0000004f;
         return tn <= tf;
     };
     int stack[STACK_SIZE];
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
     if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     unsigned c_rays = 0, c_seg = 0, c_nodes = 0, c_tris = 0, c_dep = 0;
-    bool overflow = false;
+    bool overflow = false, xlimit = false;
     const unsigned long long per_tx = (unsigned long long)A.nw * A.ns;
     for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < A.total;
          w += (unsigned long long)gridDim.x * blockDim.x) {
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
                 cyi = 0;
                 if (code == 0) {
                     Crossing hits[MAX_CROSS];
-                    const int nh = surface_hits(A.snodes, A.stris, A.snt, A.snlarge, v, ks, hits, &overflow);
+                    const int nh = surface_hits(A.snodes, A.stris, A.snt, A.snlarge, v, ks, hits, &overflow, &xlimit);
                     cxi = nh;
                     const float nw_ = W.n;
                     const float phi = u2 * nw_ * PI_F;
@@ -536,6 +537,7 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
         }
     }
     if (overflow) atomicOr(&A.scratch->status, 1);
+    if (xlimit) atomicOr(&A.scratch->status, 2);
     const unsigned v[6] = {c_rays, c_seg, c_nodes, c_tris, c_dep, 0u};
     for (int j = 0; j < 6; ++j) {
         const unsigned sum = __reduce_add_sync(0xffffffffu, v[j]);

@@ -324,8 +324,8 @@ __device__ __forceinline__ bool box_hit(float lx, float ly, float lz, float hx, 
     const float t0x = (lx - r.ox) * ix, t1x = (hx - r.ox) * ix;
     const float t0y = (ly - r.oy) * iy, t1y = (hy - r.oy) * iy;
     const float t0z = (lz - r.oz) * iz, t1z = (hz - r.oz) * iz;
-    const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+    const float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), 0.0f));
+    float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), tmax));
     // robust slab test: widen the far distance by 1 + 2 gamma_3 (Ize, JCGT 2013)
     tf = tf * 1.0000004f;
     tnear = tn;
@@ -587,8 +587,8 @@ __device__ __noinline__ unsigned surface_crossings(const float4* __restrict__ no
         const float t0x = (lx - ox) * ix, t1x = (hx - ox) * ix;
         const float t0y = (ly - oy) * iy, t1y = (hy - oy) * iy;
         const float t0z = (lz - oz) * iz, t1z = (hz - oz) * iz;
-        const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
-        const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax)) * 1.0000004f;
+        const float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), 0.0f));
+        const float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), tmax)) * 1.0000004f;
         return tn <= tf;
     };
     int stack[STACK_SIZE];

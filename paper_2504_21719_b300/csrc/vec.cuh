@@ -5,6 +5,21 @@
 
 namespace rmsbr {
 
+// ------------------------------------------------------------------ min / max
+// Three-input minimum and maximum (PTX min.f32 / max.f32 with three sources,
+// sm_100 and later).  Both are exact, so they equal the two-step fminf /
+// fmaxf chains bit for bit on the slab tests' finite distances.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // ------------------------------------------------------------------ complex
 struct cf {
     float r, i;

@@ -18,7 +18,20 @@ FLOOR = 1e-15            # cells above -150 dB are compared
 # by 2 eps / cell times the D-weighted values of the deposits whose stencil
 # covers it.  eps = 4 * 2^-24: a few FP32 roundings per coordinate.
 POS_EPS = 4.0 * 2.0 ** -24
-MAX_ADOPT_FRAC = 1e-2
+# Adopted near-ties, as fractions of the replayed segments.  Distance ties
+# (the GPU's triangle is at the FP64 closest distance within tol: a box floor
+# coplanar with the ground, resolved by index on both sides but with different
+# tolerances) were measured at up to 0.8 % of segments (one transmitter of the
+# batched workload), 0.33 % on the Manhattan subsets; every other adoption
+# (hits that are not distance ties, cells, decisions) at up to 3e-5.  The caps
+# are about 3x the measured maxima (plus a few for small replays).
+MAX_ADOPT_FRAC = 2.5e-2          # distance-tie hit adoptions
+MAX_OTHER_FRAC = 1e-4            # all other adoptions
+MAX_DIFF_VIS_FRAC = 1e-3         # diffraction visibility bits (measured 2.9e-4)
+# The GPU's recorded coin probabilities (RM_RECORD_COIN) were measured within
+# 0.26 of the replay's decision window of the oracle's q(R) on every parity
+# workload (6e-5 at most, city depth 8); they must stay within half of it.
+MAX_COIN_RATIO = 0.5
 
 
 def _log(kind, rep, extra=None):
@@ -45,9 +58,19 @@ def coin(params):
 
 def check_coins(rep):
     """When the GPU recorded its coin probabilities (RM_RECORD_COIN), every one
-    must lie inside the replay's decision window around the oracle's q(R)."""
+    must lie inside half of the replay's decision window around the oracle's q(R)."""
     if rep.get("coin_checked", 0) > 0:
         assert rep["coin_outside"] == 0, rep
+        assert rep["coin_max_ratio"] <= MAX_COIN_RATIO, rep
+
+
+def check_adoptions(rep, max_adopt_frac=MAX_ADOPT_FRAC, max_other_frac=MAX_OTHER_FRAC):
+    """Distance-tie hit adoptions and all other adoptions, each under its cap."""
+    seg = max(rep["segments"], 1)
+    ties = rep.get("adopted_hit_tie", 0)
+    other = rep["adopted_hit"] - ties + rep.get("adopted_cell", 0) + rep["adopted_decision"]
+    assert ties <= max_adopt_frac * seg + 2, rep
+    assert other <= max_other_frac * seg + 3, rep
 
 
 def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max_adopt_frac=MAX_ADOPT_FRAC):
@@ -62,8 +85,7 @@ def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max
     _log("map", rep)
     assert rep["failures"] == 0, rep
     check_coins(rep)
-    adopted = rep["adopted_hit"] + rep["adopted_cell"] + rep["adopted_decision"]
-    assert adopted <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
+    check_adoptions(rep, max_adopt_frac)
     ref = r["map"]
     g = np.asarray(gpu_map, np.float64).reshape(ref.shape)
     mask = (ref > FLOOR) | (g > FLOOR)
@@ -97,8 +119,9 @@ def compare_diffraction(orc, scene, tx, params, samples_per_wedge, gpu_map, gpu_
     rep = r["report"]
     _log("diffraction", rep)
     assert rep["failures"] == 0, rep
-    adopted = rep["adopted_hit"] + rep["adopted_cell"] + rep["adopted_decision"]
-    assert adopted <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
+    seg = max(rep["segments"], 1)
+    assert rep["adopted_hit"] <= MAX_DIFF_VIS_FRAC * seg + 2, rep
+    assert rep["adopted_cell"] + rep["adopted_decision"] <= MAX_OTHER_FRAC * seg + 3, rep
     ref = r["map"]
     g = np.asarray(gpu_map, np.float64).reshape(ref.shape)
     mask = (ref > FLOOR) | (g > FLOOR)
@@ -128,8 +151,7 @@ def compare_mesh(orc, scene, tx, params, surf_v, surf_t, gpu_map, gpu_record, rt
     _log("mesh", rep)
     assert rep["failures"] == 0, rep
     check_coins(rep)
-    adopted = rep["adopted_hit"] + rep["adopted_decision"]
-    assert adopted <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
+    check_adoptions(rep, max_adopt_frac)
     ref = r["map"]
     g = np.asarray(gpu_map, np.float64).reshape(ref.shape)
     mask = (ref > FLOOR) | (g > FLOOR)
@@ -154,7 +176,7 @@ def compare_diffraction_mesh(orc, scene, tx, params, samples_per_wedge, surf_v, 
     rep = r["report"]
     _log("diffraction_mesh", rep)
     assert rep["failures"] == 0, rep
-    assert rep["adopted_hit"] <= max_adopt_frac * max(rep["segments"], 1) + 2, rep
+    assert rep["adopted_hit"] <= MAX_DIFF_VIS_FRAC * max(rep["segments"], 1) + 2, rep
     ref = r["map"]
     g = np.asarray(gpu_map, np.float64).reshape(ref.shape)
     mask = (ref > FLOOR) | (g > FLOOR)

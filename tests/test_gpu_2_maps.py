@@ -240,3 +240,4 @@ def test_large_city_sampled_and_partition(orc, api):
     mask = fm > FLOOR
     assert torch.all((parts - fm).abs()[mask] <= 2e-5 * fm[mask])
     gs.free()
+

@@ -26,16 +26,20 @@ def _call(L, lib, gs, arr, ntx, prm, out, stream=None):
     return rc, st
 
 
-def _deposit_counts(rec, ntx, ny, nx):
-    """Deposits per cell from a (box-deposit) record [.., 4] = {prim, ix, iy, decision}
-    of one transmitter after the other."""
-    r = rec.view(ntx, -1, 4)
-    out = torch.zeros((ntx, ny * nx), dtype=torch.float64, device=rec.device)
-    for t in range(ntx):
-        ix, iy = r[t, :, 1].long(), r[t, :, 2].long()
+def _deposit_counts(rec, txs, L, ny, nx):
+    """Deposits per cell from a (box-deposit) record [.., 4] = {prim, ix, iy, decision}:
+    count x (L + 1) records of each transmitter, one transmitter after the other."""
+    r = rec.view(-1, 4)
+    out = torch.zeros((len(txs), ny * nx), dtype=torch.float64, device=rec.device)
+    b = 0
+    for t, tx in enumerate(txs):
+        e = b + tx.count() * (L + 1)
+        ix, iy = r[b:e, 1].long(), r[b:e, 2].long()
         ok = (ix >= 0) & (ix < nx) & (iy >= 0) & (iy < ny)
         out[t] += torch.bincount((iy * nx + ix)[ok], minlength=ny * nx).double()
-    return out.view(ntx, ny, nx)
+        b = e
+    assert b == r.shape[0]
+    return out.view(len(txs), ny, nx)
 
 
 def _same(a, b, counts):
@@ -65,7 +69,7 @@ def test_noalloc_matches_allocating_trace_twice(api):
     prm = api.params_from(p)
     arr = (L.rm_tx * 1)(api.tx_from(tx))
     ref = api.trace(gs, [tx], prm, record=True)
-    cnt = _deposit_counts(ref["record"], 1, p.ny, p.nx)
+    cnt = _deposit_counts(ref["record"], [tx], p.max_depth, p.ny, p.nx)
     out = torch.empty_like(ref["maps"])
     for _ in range(2):
         out.fill_(-1.0)                                    # the call must overwrite every cell
@@ -89,7 +93,7 @@ def test_noalloc_full_manhattan_map(api):
     prm = api.params_from(p)
     arr = (L.rm_tx * 1)(api.tx_from(tx))
     ref = api.trace(gs, [tx], prm, record=True)
-    cnt = _deposit_counts(ref["record"], 1, p.ny, p.nx)
+    cnt = _deposit_counts(ref["record"], [tx], p.max_depth, p.ny, p.nx)
     del ref["record"]
     out = torch.empty_like(ref["maps"])
     for _ in range(2):
@@ -113,7 +117,7 @@ def test_noalloc_batched_and_limits(api):
     prm = api.params_from(p)
     arr = (L.rm_tx * len(txs))(*[api.tx_from(t) for t in txs])
     ref = api.trace(gs, txs, prm, record=True)
-    cnt = _deposit_counts(ref["record"], len(txs), p.ny, p.nx)
+    cnt = _deposit_counts(ref["record"], txs, p.max_depth, p.ny, p.nx)
     out = torch.empty_like(ref["maps"])
     for _ in range(2):
         rc, st = _call(L, lib, gs, arr, len(txs), prm, out)
@@ -142,7 +146,7 @@ def test_noalloc_with_arrays(api):
     prm = api.params_from(p)
     arr, ntx = api._tx_array([tx])
     ref = api.trace(gs, [tx], prm, record=True)
-    cnt = _deposit_counts(ref["record"], 1, p.ny, p.nx)
+    cnt = _deposit_counts(ref["record"], [tx], p.max_depth, p.ny, p.nx)
     out = torch.empty_like(ref["maps"])
     rc, st = _call(L, lib, gs, arr, ntx, prm, out)
     assert rc == L.RM_OK, lib.rm_last_error()
