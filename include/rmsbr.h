@@ -102,14 +102,14 @@ typedef struct {
 typedef struct {
     float pos[3];        /* m */
     float yaw, pitch, roll;
-    int32_t pol;         /* 0 vertical (theta'), 1 horizontal (phi'), 2 dual: both, maps add (Sec. 4.5) */
+    int32_t pol;         /* 0 vertical (theta'), 1 horizontal (phi'), 2 dual: both, maps add (Sec. 4.4) */
     int32_t pattern;     /* 0 isotropic (G = 1), 1 short dipole (G = 1.5 sin^2 theta') */
     uint64_t num_rays;   /* N_S >= 1 */
     uint64_t ray_begin;
     uint64_t ray_count;  /* UINT64_MAX: all of ceil((num_rays - ray_begin) / ray_stride) */
     uint64_t ray_stride; /* >= 1 */
     uint64_t seed;       /* seed of the counter-based interaction sampler */
-    /* Synthetic array (Sec. 4.5): n_ant elements at ant_pos_host [n_ant][3] (m,
+    /* Synthetic array (Sec. 4.4): n_ant elements at ant_pos_host [n_ant][3] (m,
      * antenna frame, rotated with the antenna) with complex precoding weights
      * precoding_host [n_ant][2] (re, im), both in double (phases reach k0 |d|,
      * ~1600 rad for a 1024-element half-wavelength array, so positions keep
@@ -146,7 +146,7 @@ typedef struct {
     int32_t blocks_per_sm;   /* resident blocks per SM of the persistent grid; 0 = tuned default */
     int32_t queue_chunk;     /* work items a warp takes per work-queue access, in units of 32 (1..64);
                                 0 = default (1) */
-    /* Early termination (Sec. 4.7), applied after an interaction once a path
+    /* Early termination (Sec. 4.5), applied after an interaction once a path
      * has rr_depth interactions (0 = off).  The gain of a sample is w |E|^2,
      * w = 1 / Pr(chi).  gain_threshold > 0: stop when (lambda0/4pi)^2 w |E|^2 / r^2,
      * r the tube length, is below it (biased).  rr_max_prob in (0, 1]: Russian

@@ -475,7 +475,7 @@ struct or_tx {
     int32_t pol, pattern;
     int64_t num_rays, ray_begin, ray_count, ray_stride;
     uint64_t seed;
-    int64_t n_ant;             // synthetic array (Sec. 4.5): 0 = single antenna
+    int64_t n_ant;             // synthetic array (Sec. 4.4): 0 = single antenna
     const double* ant_pos;     // [n_ant][3] element positions in the antenna frame (m)
     const double* precoding;   // [n_ant][2] complex precoding weights
 };
@@ -485,7 +485,7 @@ struct or_params {
     double map_origin[3];
     double cell_size;
     int32_t nx, ny, deposit, pad;
-    int32_t rr_depth, pad2;    // early termination after this many interactions (Sec. 4.7); 0 = off
+    int32_t rr_depth, pad2;    // early termination after this many interactions (Sec. 4.5); 0 = off
     double rr_max_prob;        // p_rr,max; 0 = no Russian roulette
     double gain_threshold;     // linear gain below which a path stops; 0 = off
 };
@@ -709,7 +709,7 @@ struct TxC {
 };
 
 // Array factor of a synthetic transmit array for departure direction k
-// (Sec. 4.5 with the array response vector of Eq. path-solver-array-response-vector):
+// (Sec. 4.4 with the array response vector of Eq. path-solver-array-response-vector):
 //   alpha = sum_k u_P,k exp(j (2 pi / lambda0) k^T d_k).
 // The non-coherent map sees |alpha|^2 times the single-antenna power.
 std::complex<double> array_factor(const TxC& T, const V3<double>& k, double k0) {
@@ -815,7 +815,7 @@ struct Ctx {
     double omega, k0;  // angular frequency, vacuum wavenumber
     int L, flags;
     int mode;
-    // early termination (Sec. 4.7)
+    // early termination (Sec. 4.5)
     int rr_depth = 0;
     double rr_pmax = 0.0, gain_thr = 0.0, lam4pi2 = 0.0;
     // sampling materials (detached q): eps, sigma
@@ -1241,7 +1241,7 @@ void trace_ray(const Ctx& C, const TxC& tx, const V3<R>& txpos, const Cx<R>* eta
         tube = (dec == 2) ? 0.0 : tube + val(t_h);  // a diffuse reflection starts a new tube
         k = k_out;
         prev = prim;
-        // ---- early termination after rr_depth interactions (Sec. 4.7) ----
+        // ---- early termination after rr_depth interactions (Sec. 4.5) ----
         // Reading: the gain of a sample is w |E|^2 with w = 1 / Pr(chi) (the
         // tube-length-normalised gain of the paper); gain thresholding stops a
         // path when (lambda0 / 4 pi)^2 w |E|^2 / r^2 < threshold at its tube
@@ -2614,7 +2614,7 @@ int or_diffraction_map(const float* verts, int64_t nv, const int32_t* tris, int6
                                  vd.y.g[1] + gam.g[1] * kd.y.v + gam.v * kd.y.g[1],
                                  vd.z.g[1] + gam.g[1] * kd.z.v + gam.v * kd.z.g[1]};
             const double J = norm(cross(tx_, tp_));
-            // incident antenna field in the departure direction s' (App. A.1, Sec. 4.5)
+            // incident antenna field in the departure direction s' (App. A.1, Sec. 4.4)
             const std::complex<double> al = array_factor(T, si, k0);
             auto power = [&](const V3<double>& kd_) {
                 double pw = 0.0;

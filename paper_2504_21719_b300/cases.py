@@ -12,8 +12,9 @@ CASE is one of
   batched      the 64-TX batched workload (depth 3) in one launch; --rays sets the
                lattice stride of every transmitter (default 1: the full workload)
   mesh         the Manhattan trace on a 131072-triangle terrain measurement surface
-Each case prints one line: case, kernel ms of the last call, and its work
-counters.
+Each case runs in the launch shape the tuning table holds for its workload
+class on this GPU (the benchmark's shape) and prints one line: case, kernel
+ms of the last call, and its work counters.
 """
 from __future__ import annotations
 
@@ -52,6 +53,11 @@ def main(argv=None):
         sc, txs, p = S.workload(4)
     if a.rays and a.case not in ("diffraction", "batched"):
         txs[0].num_rays = a.rays
+    from .autotune import lookup
+    cls = {"manhattan": "manhattan", "diffuse": "diffuse", "adjoint": "adjoint", "diffraction": "diffraction",
+           "city": "city", "city_adjoint": "city_adjoint", "batched": "batched", "mesh": "manhattan"}[a.case]
+    blk, bps, qch, rfm = lookup(torch.cuda.get_device_name(0), cls)
+    p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
     gs = api.Scene.from_obj(sc)
     su = api.surface(*S.terrain_surface(256.0, 256)) if a.case == "mesh" else None
     for _ in range(a.reps):

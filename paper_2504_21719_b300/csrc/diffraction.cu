@@ -132,7 +132,7 @@ __device__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float
 
 // ------------------------------------------------------------------ antenna field
 // R (C_theta theta' + C_phi phi') in direction k (App. A.1) times the
-// synthetic-array factor alpha = sum_k u_P,k exp(j k0 k.d_k) (Sec. 4.5).
+// synthetic-array factor alpha = sum_k u_P,k exp(j k0 k.d_k) (Sec. 4.4).
 __device__ void antenna_field(const TxDev& T, const AntDev* __restrict__ ant, f3 k, int pol, cf* E) {
     const float lx = T.R[0] * k.x + T.R[3] * k.y + T.R[6] * k.z;
     const float ly = T.R[1] * k.x + T.R[4] * k.y + T.R[7] * k.z;

@@ -168,7 +168,7 @@ def test_partition_gradients_sum_to_full(api):
 
 @pytest.mark.parametrize("regular", [True, False])
 def test_adjoint_with_array_matches_oracle(orc, api, regular):
-    """The adjoint re-evaluates the synthetic-array factor at launch (Sec. 4.5):
+    """The adjoint re-evaluates the synthetic-array factor at launch (Sec. 4.4):
     a steered 8-element ULA (Horner path) or 6 irregular elements (per-element
     path), gradient of the dB loss against the oracle's along the GPU's record."""
     sc, tx, p = _setup()

@@ -1,5 +1,5 @@
-"""GPU parity of the 'next' rows: synthetic transmit arrays (Sec. 4.5) and
-early termination by gain thresholding and Russian roulette (Sec. 4.7)."""
+"""GPU parity of the 'next' rows: synthetic transmit arrays (Sec. 4.4) and
+early termination by gain thresholding and Russian roulette (Sec. 4.5)."""
 import copy
 
 import numpy as np
@@ -72,7 +72,7 @@ def test_irregular_array(orc, api):
 
 
 def test_street_canyon_1024_element_array(orc, api):
-    """The largest array of the time-vs-N_S-and-N_A study (Sec. 4.5): a
+    """The largest array of the time-vs-N_S-and-N_A study (Sec. 4.4): a
     1024-element half-wavelength ULA 20 m above a street canyon, depth 5, on a
     lattice subset of a 1e8-sample launch.  Phases reach k0 |d| ~ 1600 rad and
     a ray near a null of the array factor has no FP32 answer within 1e-3, so

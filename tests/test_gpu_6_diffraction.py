@@ -130,7 +130,7 @@ def test_diffraction_mesh_parity(orc, api, which):
 @pytest.mark.parametrize("regular", [True, False])
 def test_diffraction_parity_with_array(orc, api, regular):
     """The diffraction map's antenna field includes the synthetic-array factor
-    at the direction to each wedge sample (Sec. 4.5): a steered 4-element ULA or
+    at the direction to each wedge sample (Sec. 4.4): a steered 4-element ULA or
     5 irregular elements with complex precoding, single box at 3.5 GHz."""
     sc = S.single_box(ground=500.0)
     p = S.TraceParams(3.5e9, 0, cell_size=2.0, nx=60, ny=60, map_origin=(10.0, 15.0, 1.5))

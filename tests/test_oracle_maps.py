@@ -106,7 +106,7 @@ def test_reciprocity_ground_and_wall(orc, rx, deposit):
     specular paths is symmetric) makes the transfer matrix of the reversed path
     the transpose of the forward one in the theta/phi bases (up to the sign of
     phi-hat), so its Frobenius norm is reciprocal.  A dual-polarised isotropic
-    TX maps exactly that norm (the sum of both columns' |T C|^2, Sec. 4.5),
+    TX maps exactly that norm (the sum of both columns' |T C|^2, Sec. 4.4),
     while a single V column is not polarisation-pure once ground-then-wall
     paths mix it.  16 replicates of ~1e6 rays in each direction."""
     sc, cell = recip_scene(), 1.0

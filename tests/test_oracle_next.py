@@ -1,5 +1,5 @@
-"""Pins of the oracle's synthetic transmit arrays (Sec. 4.5, Eq.
-path-solver-array-response-vector) and early termination (Sec. 4.7, Eq.
+"""Pins of the oracle's synthetic transmit arrays (Sec. 4.4, Eq.
+path-solver-array-response-vector) and early termination (Sec. 4.5, Eq.
 radio-map-solver-rr-prob)."""
 import copy
 import math
