@@ -435,7 +435,7 @@ def city_adjoint(api, S, torch, sc, txs, p, prm, prm_adj, gs, fwd_kernel_ms, fwd
     return {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3), "segments": segs,
             "fwd_kernel_ms": round(fwd_kernel_ms, 3), "fwd_plus_adj_over_fwd": round((fwd_kernel_ms + k) / fwd_kernel_ms, 3),
             "loss_cells": int(valid), "parameters": "d loss / d(eps_r, sigma) of 8 materials",
-            "roofline": roofline(5, "k_trace<adjoint> (re-traces the forward's rays)", segs, k,
+            "roofline": roofline(0, "k_trace<adjoint> (re-traces the forward's rays)", segs, k,
                                  "instruction issue", False)}
 
 

@@ -1,4 +1,4 @@
-// Synthetic transmit arrays (Sec. 4.5): the array factor
+// Synthetic transmit arrays (Sec. 4.4): the array factor
 //   alpha(k) = sum_a w_a exp(j k0 k.d_a)
 // of a ray leaving in direction k, where d_a is element a's position (global
 // frame) and w_a its precoding weight.  Phases reach k0 |d| (about 1600 rad

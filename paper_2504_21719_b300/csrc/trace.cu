@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                         if (sxy > 0.0f) { cph = lx / sxy; sph = ly / sxy; }
                         const float g = (T.pattern == 1) ? 1.2247448713915890f * sxy : 1.0f;
                         const f3 th_l{lz * cph, lz * sph, -sxy}, ph_l{-sph, cph, 0.0f};
-                        // synthetic array (Sec. 4.5): alpha = sum_k u_P,k exp(j k0 k.d_k) at the
+                        // synthetic array (Sec. 4.4): alpha = sum_k u_P,k exp(j k0 k.d_k) at the
                         // lattice direction rebuilt in double-float (array.cuh)
                         float are = 1.0f, aim = 0.0f;
                         if (T.n_ant > 0) array_factor_lattice(T, A.ant, n, are, aim);
@@ -1160,7 +1160,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                     plen += h.t;
                     if (DIFF && dec == 2) plen = 0.0f;  // a diffuse reflection starts a new tube
                     ++depth;
-                    // early termination once the path has rr_depth interactions (Sec. 4.7):
+                    // early termination once the path has rr_depth interactions (Sec. 4.5):
                     // threshold on (lambda0/4pi)^2 w|E|^2 / r^2, then Russian roulette with
                     // p = min(w|E|^2, p_max) (Eq. radio-map-solver-rr-prob), survivors x 1/p
                     if (A.rr_depth > 0 && depth >= A.rr_depth && (A.gain_thr > 0.0f || A.rr_pmax > 0.0f)) {

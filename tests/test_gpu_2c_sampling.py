@@ -64,3 +64,31 @@ def test_coin_probabilities_vs_oracle(orc, api, cfg):
             worst = max(worst, dev / win)
     # the kernel's arithmetic uses at most a quarter of the replay's window
     assert worst <= 0.25, worst
+
+
+def test_coin_record_changes_only_the_coin_bits(api):
+    """RM_RECORD_COIN adds the coin's q(R) to the decision field and nothing
+    else: same hits, cells, decisions and kill bits, q(R) in [0, 1], maps equal
+    to the order of the atomic additions."""
+    import copy
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    tx.ray_stride = 997
+    gs = api.Scene.from_obj(sc)
+    a = api.trace(gs, [tx], p, record=True)
+    q = copy.copy(p)
+    q.record_coin = True
+    b = api.trace(gs, [tx], q, record=True)
+    ra, rb = a["record"], b["record"]
+    assert torch.equal(ra[:, :3], rb[:, :3])
+    da, db = ra[:, 3], rb[:, 3]
+    neg = da < 0
+    assert torch.equal(da[neg], db[neg])
+    assert torch.equal(da[~neg], db[~neg] & 255)
+    coin = (db[~neg] >> 8).double() * 2.0 ** -22
+    assert int((~neg).sum()) > 1000 and float(coin.min()) >= 0.0 and float(coin.max()) <= 1.0
+    assert float((coin > 0).double().mean()) > 0.5
+    ma, mb = a["maps"].double(), b["maps"].double()
+    mask = ma > 1e-15
+    assert torch.all((ma - mb).abs()[mask] <= 2e-5 * ma[mask])
+    gs.free()
