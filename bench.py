@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SEGMENT_BYTES = 184      # compulsory wavefront bytes per segment (ray state r/w, hit, queue)
+SM_COUNT = 148           # set from the device in run_ours
 METRIC = "radio-map ray-bounces/s"
 UNIT = "ray-bounces/s"
 WORKLOADS = {
@@ -171,12 +172,24 @@ def roofline(cfg: int, kernel: str, segments: float, kernel_ms: float, binding: 
     achieved = SEGMENT_BYTES * segments / (kernel_ms / 1e3) / 1e9
     per_seg = profiled(cfg, "dram_bytes_per_segment")
     issue = profiled(cfg, "issue_active_pct")
+    # the limit that binds: warp instructions issued per second against the SMs' issue
+    # peak (4 schedulers per SM, one instruction per cycle each, at the maximum SM clock);
+    # instructions per segment from the committed full-size ncu count of this kernel
+    wips = profiled(cfg, "warp_inst_per_segment")
+    issue_roof = None
+    if wips is not None and pk.get("sm_max_mhz"):
+        ipeak = SM_COUNT * 4 * pk["sm_max_mhz"] * 1e6
+        iach = wips * segments / (kernel_ms / 1e3)
+        issue_roof = {"bound": "issue", "achieved": round(iach / 1e12, 4), "peak": round(ipeak / 1e12, 4),
+                      "unit": "warp instructions/ns (1e12/s)", "frac": round(iach / ipeak, 4),
+                      "warp_inst_per_segment": wips}
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None if per_seg is None else round(per_seg * segments),
             "peak_source": src, "algorithmic_bytes_per_segment": SEGMENT_BYTES, "kernel": kernel,
             "kernel_ms": round(kernel_ms, 4), "segments_per_launch": int(segments),
             "issue_slots_busy_frac": None if issue is None else round(issue / 100.0, 3),
-            "binding_limit": binding, "peak_kind": "burst copy bandwidth" if timed_alone else "copy bandwidth"}
+            "binding_limit": binding, "peak_kind": "burst copy bandwidth" if timed_alone else "copy bandwidth",
+            "issue_roofline": issue_roof}
 
 
 def tuned(gpu_name: str, key: str):
@@ -336,6 +349,8 @@ def run_ours(args, world, rank, local):
     from synth import scenes as S
 
     gpu_name = torch.cuda.get_device_name(local)
+    global SM_COUNT
+    SM_COUNT = torch.cuda.get_device_properties(local).multi_processor_count
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # ---------------- the step: forward radio maps of the city workload ----------------
