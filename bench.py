@@ -248,6 +248,15 @@ def oracle_sample(cfg: int, target_s: float = 12.0, record_segments=True):
                       f"segments, {dt:.1f} s), FP64 brute force over {sc.nt} triangles, OpenMP"}
 
 
+def traversal_counts(api, gs, txs, p, prm):
+    """Node visits and triangle tests per segment, from one untimed trace with
+    statistics on (the plain tracer does not count them)."""
+    q = api.params_from(p, stats=True, block_size=prm.block_size, blocks_per_sm=prm.blocks_per_sm,
+                        queue_chunk=prm.queue_chunk, refill_min=prm.refill_min)
+    s = api.trace(gs, txs, q)["stats"]
+    return s["nodes_visited"] / max(1, s["segments"]), s["tris_tested"] / max(1, s["segments"])
+
+
 def time_plan(torch, plan, steps, warmup, flush, clocks=None):
     """Replay a graph-captured trace: warm-up, then `steps` timed launches with
     the L2 flushed before each; CUDA events around each launch on the current
@@ -379,8 +388,7 @@ def run_ours(args, world, rank, local):
     value = total_segs / (total_ms / 1e3)
     seg_step = statistics.mean(s["segments"] for s in st)
     kavg = statistics.mean(kern_ms)
-    nodes = sum(s["nodes_visited"] for s in st) / max(1, sum(s["segments"] for s in st))
-    tris = sum(s["tris_tested"] for s in st) / max(1, sum(s["segments"] for s in st))
+    nodes, tris = traversal_counts(api, gs, txs, p, prm)
     roof = roofline(5, "k_trace (persistent forward tracer), one launch over all transmitters", seg_step, kavg,
                     "instruction issue (rays stay in registers; the 109 MB scene is read from L2)", False)
 
@@ -489,7 +497,7 @@ def run_extra(api, S, torch, gpu_name, flush, args):
     out["manhattan"] = {"workload": WORKLOADS[2], "value": round(sum(s["segments"] for s in st) / (sum(step_ms) / 1e3), 1),
                         "unit": UNIT, "ms_per_step": round(statistics.mean(step_ms), 4), "steps": steps,
                         "segments_per_step": int(segs), **shape,
-                        "nodes_per_segment": round(sum(s["nodes_visited"] for s in st) / sum(s["segments"] for s in st), 2),
+                        "nodes_per_segment": round(traversal_counts(api, gs, txs, p, prm)[0], 2),
                         "roofline": roofline(2, "k_trace (persistent forward tracer)", segs, km,
                                              "instruction issue (scene and map stay in L1/L2)", True),
                         "e2e": e2e_host(api, torch, sc, txs, prm, maps, steps, 3, flush, breakdown=steps)}

@@ -164,8 +164,9 @@ typedef struct {
 typedef struct {
     uint64_t rays;           /* lattice rays launched */
     uint64_t segments;       /* closest-hit queries = ray-bounces traced */
-    uint64_t nodes_visited;  /* BVH internal nodes fetched */
-    uint64_t tris_tested;    /* ray-triangle tests */
+    uint64_t nodes_visited;  /* BVH internal nodes fetched (counted only under RM_STATS or with a
+                                debug record; 0 otherwise) */
+    uint64_t tris_tested;    /* ray-triangle tests (as nodes_visited) */
     uint64_t deposits;       /* plane crossings deposited into a map */
     uint64_t escapes;        /* segments that hit nothing */
     uint64_t segments_per_depth[RM_MAX_DEPTH + 1];

@@ -340,9 +340,11 @@ struct Hit {
 
 // Closest hit along the ray, excluding leaf `exclude`.  Equal distances go to
 // the smaller original triangle index; distances within 8 ulps (relative
-// TIE_REL) count as equal, so coplanar triangles resolve by index.
+// TIE_REL) count as equal, so coplanar triangles resolve by index.  COUNT:
+// node visits and triangle tests are counted (the debug and statistics
+// instantiations only; the two increments cost the plain tracer 1-2 %).
 constexpr float TIE_REL = 4.8e-7f;
-template <bool ONE_SITE>
+template <bool ONE_SITE, bool COUNT>
 __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, int nt,
                                            int nlarge, const Ray& r, int exclude, unsigned& c_nodes,
                                            unsigned& c_tris, bool& overflow) {
@@ -374,7 +376,7 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
     // ray-triangle test of leaf `slot` (watertight; Woop, Benthin & Wald 2013)
     auto test_leaf = [&](int slot) {
         if (slot == exclude) return;
-        ++c_tris;
+        if (COUNT) ++c_tris;
         const float4* tp = tris + 3 * (size_t)slot;
         const float4 r0 = __ldg(tp), r1 = __ldg(tp + 1), r2 = __ldg(tp + 2);
         const f3 va{r0.x, r0.y, r0.z}, vb{r0.w, r1.x, r1.y}, vc{r1.z, r1.w, r2.x};
@@ -437,7 +439,7 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
                     overflow = true;
                     break;
                 }
-                ++c_nodes;
+                if (COUNT) ++c_nodes;
                 const float4* nd = nodes + 4 * (size_t)cur;
                 const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
                 float tn0, tn1;
@@ -497,7 +499,7 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
                 overflow = true;
                 break;
             }
-            ++c_nodes;
+            if (COUNT) ++c_nodes;
             const float4* nd = nodes + 4 * (size_t)cur;
             const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
             float tn0, tn1;
@@ -803,7 +805,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
         // ---------------- closest hit ----------------
         Hit h{-1, 0x7fffffff, INFINITY};
         if (active) {
-            h = closest_hit<DIFF || ADJ>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris, overflow);
+            h = closest_hit<DIFF || ADJ, DEBUG>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris, overflow);
             ++c_seg;
             if (h.slot < 0) ++c_esc;
         }
