@@ -53,7 +53,8 @@ WORKLOADS = {
 }
 # the committed ncu summaries a roofline's `traffic` comes from, keyed by workload
 PROFILES = {5: "k_trace_city.md", 2: "k_trace_manhattan_1e7.md", 3: "k_trace_batched.md",
-            4: "k_trace_adjoint_differentiable.md"}
+            4: "k_trace_adjoint_differentiable.md", "city_adjoint": "k_trace_adjoint_city.md",
+            "diffuse": "k_trace_diffuse_manhattan.md"}
 # the tracer's code and the tree it walks (the LBVH build decides its node visits)
 TRACE_SOURCES = [os.path.join(ROOT, "paper_2504_21719_b300", "csrc", f) for f in ("trace.cu", "common.cuh", "array.cuh", "bvh.cu")]
 
@@ -136,7 +137,7 @@ def peaks():
         return {}
 
 
-def profiled(cfg: int, key: str):
+def profiled(cfg, key: str):
     """A figure (dram_bytes_per_segment, issue_active_pct, ...) of a tracer
     workload from its committed ncu summary, if the kernel source is unchanged
     since it was taken; else None."""
@@ -160,7 +161,7 @@ def profiled(cfg: int, key: str):
         return None
 
 
-def roofline(cfg: int, kernel: str, segments: float, kernel_ms: float, binding: str, timed_alone: bool):
+def roofline(cfg, kernel: str, segments: float, kernel_ms: float, binding: str, timed_alone: bool):
     """HBM roofline of one tracer launch: 184 compulsory wavefront bytes per
     segment over the launch's CUDA-event duration, against the measured copy
     bandwidth; `traffic` = the committed ncu DRAM bytes per segment (of a
@@ -458,7 +459,7 @@ def city_adjoint(api, S, torch, sc, txs, p, prm, prm_adj, gs, fwd_kernel_ms, fwd
     return {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3), "segments": segs,
             "fwd_kernel_ms": round(fwd_kernel_ms, 3), "fwd_plus_adj_over_fwd": round((fwd_kernel_ms + k) / fwd_kernel_ms, 3),
             "loss_cells": int(valid), "parameters": "d loss / d(eps_r, sigma) of 8 materials",
-            "roofline": roofline(0, "k_trace<adjoint> (re-traces the forward's rays)", segs, k,
+            "roofline": roofline("city_adjoint", "k_trace<adjoint> (re-traces the forward's rays)", segs, k,
                                  "instruction issue", False)}
 
 
@@ -512,7 +513,7 @@ def run_extra(api, S, torch, gpu_name, flush, args):
     d = _kernel_rate(api, gsd, txs, tuned_params(api, pd, gpu_name, "diffuse")[0])
     d["vs_specular"] = round(d["value"] / base["value"], 3)
     d["materials"] = "S = 0.5 on every material; ground Lambertian, buildings directive / backscattering"
-    d["roofline"] = roofline(0, "k_trace<diffuse>", d["segments"], d["kernel_ms"], "instruction issue", True)
+    d["roofline"] = roofline("diffuse", "k_trace<diffuse>", d["segments"], d["kernel_ms"], "instruction issue", True)
     out["specular_same_call"] = base
     out["diffuse"] = d
     gsd.free()
