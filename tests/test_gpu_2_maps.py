@@ -55,9 +55,9 @@ def test_manhattan_depth5_subset(orc, api, stride, begin):
 
 def test_manhattan_full_size_sampled(orc, api):
     """Full workload (1e7 rays, depth 5, 512 x 512) in the benchmark's launch
-    configuration: a sampled 1-in-997 set of its records is replayed by the
-    oracle, the full map equals the sum of disjoint subset maps, and the
-    records of the full run equal those of the subset run."""
+    configuration: a sampled 1-in-97 set of its records (1.0e5 rays) is
+    replayed by the oracle, the full map equals the sum of disjoint subset
+    maps, and the records of the full run equal those of the subset run."""
     sc, txs, p = S.workload(2)
     tx = txs[0]
     gs = api.Scene.from_obj(sc)
@@ -65,7 +65,7 @@ def test_manhattan_full_size_sampled(orc, api):
     fm = full["maps"][0].double().cpu().numpy()
     L = p.max_depth
     frec = full["record"].view(tx.num_rays, L + 1, 4)
-    st = 997
+    st = 97
     sub = copy.copy(tx)
     sub.ray_stride, sub.ray_begin = st, 3
     srec_full = frec[3::st].cpu().numpy()
