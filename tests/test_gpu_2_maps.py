@@ -272,3 +272,30 @@ def test_batched_full_size_sampled_every_tx(orc, api):
         assert np.array_equal(rec_full, rec_sub), i
         compare_maps(orc, sc, s, p, maps[i], rec_sub)
     gs.free()
+
+
+def test_large_city_full_transmitter_records_match_replayed_subset(orc, api):
+    """One city transmitter at its full 1e8 rays (depth 8) with its record (14 GB
+    on the device): the records at a sampled lattice subset (every 333331st
+    ray) equal those of the subset launch, which the oracle replays and
+    certifies, so the full-size launch takes oracle-certified choices there."""
+    sc, txs, p = S.workload(5)
+    tx = txs[3]
+    gs = api.Scene.from_obj(sc)
+    L = p.max_depth
+    full = api.trace(gs, [tx], p, record=True)
+    assert full["stats"]["rays"] == tx.num_rays
+    sub = copy.copy(tx)
+    sub.ray_stride, sub.ray_begin = 333_331, 101
+    rec_full = full["record"].view(tx.num_rays, L + 1, 4)[sub.ray_begin::sub.ray_stride].cpu().numpy()
+    del full
+    torch.cuda.empty_cache()
+    r = api.trace(gs, [sub], coin(p), record=True)
+    rec_sub = r["record"].view(sub.count(), L + 1, 4).cpu().numpy()
+    plain = rec_sub.copy()
+    ok = plain[:, :, 3] >= 0
+    plain[:, :, 3][ok] &= 255                       # without the coin bits
+    assert np.array_equal(rec_full, plain)
+    info = compare_maps(orc, sc, sub, p, r["maps"][0].cpu().numpy(), rec_sub)
+    assert info["cells"] > 100
+    gs.free()
