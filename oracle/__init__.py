@@ -110,6 +110,8 @@ def lib():
         _lib.or_morton.argtypes = [P, P, C.c_int64, P, P, P]
         _lib.or_lbvh.restype = C.c_int
         _lib.or_lbvh.argtypes = [P, P, C.c_int64, P, P, P, P, P]
+        _lib.or_sah_bvh.restype = C.c_int
+        _lib.or_sah_bvh.argtypes = [P, P, C.c_int64, P, P, P, P, P]
         _lib.or_num_threads.restype = C.c_int
     return _lib
 
@@ -456,6 +458,17 @@ def morton(scene):
 def lbvh(scene):
     """Reference LBVH: sorted keys, order, nlarge, child [ns-1, 2], child AABBs [ns-1, 2, 6]
     with ns = nt - nlarge (the large triangles are the last nlarge entries of order)."""
+    return _tree(scene, lib().or_lbvh)
+
+
+def sah_bvh(scene):
+    """Reference binned-SAH tree over the same leaves as ``lbvh`` (32 centroid bins
+    per axis, stable partitions from the Morton order, node i numbered by its
+    split position, root 0); keys[p] is the Morton key of the triangle at p."""
+    return _tree(scene, lib().or_sah_bvh)
+
+
+def _tree(scene, fn):
     v, t, _, _ = _scene_arrays(scene)
     nt = len(t)
     keys = np.zeros(max(nt, 1), np.uint64)
@@ -463,7 +476,7 @@ def lbvh(scene):
     child = np.zeros((max(nt - 1, 1), 2), np.int32)
     box = np.zeros((max(nt - 1, 1), 2, 6), np.float32)
     nl = C.c_int64(0)
-    lib().or_lbvh(_p(v), _p(t), nt, _p(keys), _p(order), _p(child), _p(box), C.byref(nl))
+    fn(_p(v), _p(t), nt, _p(keys), _p(order), _p(child), _p(box), C.byref(nl))
     ns = nt - int(nl.value)
     return {"keys": keys[:nt], "order": order[:nt], "nlarge": int(nl.value), "child": child[:max(ns - 1, 0)],
             "child_aabb": box[:max(ns - 1, 0)]}

@@ -22,7 +22,8 @@
 //     sampling) that gives the estimator's exact expectation on tiny scenes;
 //   * forward-mode dual numbers for the gradient with frozen discrete choices;
 //   * a reference LBVH (Morton codes + stable sort + top-down binary radix
-//     tree) that the GPU tree must equal bit for bit;
+//     tree) and a reference binned-SAH tree over the same leaves, which the
+//     GPU's two builders must equal bit for bit;
 //   * diffuse reflection (App. A.10: S / R split of the sampling, the
 //     scattered field with cross-polarisation, Lambertian / directive /
 //     backscattering patterns);
@@ -2079,6 +2080,168 @@ int or_lbvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t* k
         for (int a = 0; a < 3; ++a) {
             nb[a] = std::min(lb[a], rb[a]);
             nb[3 + a] = std::max(lb[3 + a], rb[3 + a]);
+        }
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Reference binned-SAH BVH.  Not in the paper either; a second tree over the
+// same leaves (one triangle per leaf, the same large-triangle list) whose
+// splits minimise the surface-area heuristic (MacDonald & Booth 1990) over 32
+// centroid bins per axis (Wald, "On fast construction of SAH-based bounding
+// volume hierarchies", 2007).  Written recursively over ranges of positions,
+// one node at a time, independently of the GPU's level-by-level build.
+//
+// Start: the LBVH's stable Morton order; the tree covers positions [0, ns).
+// A range [lo, hi) of at least 2 positions at depth d (the root [0, ns) at
+// d = 0) is split as follows (FP32 with round-to-nearest, no fused operations;
+// the costs in double, left to right):
+//   c2         = lo + hi of each triangle's AABB (the Morton code's centroid);
+//   cl_a, ch_a = min / max of c2_a over the range;
+//   axis a is binned when d < 32, e_a = ch_a - cl_a > 0 and k_a = 32 / e_a is
+//   finite;  bin_a(t) = min(31, trunc((c2_a(t) - cl_a) * k_a));
+//   each bin holds the count and the union of its triangles' AABBs; split b
+//   in 1..31 puts bins < b left (L) and bins >= b right (R); with
+//   H(B) = dx dy + dy dz + dz dx, dx = (double)(hi_x - lo_x),
+//   cost(a, b) = H(L) nL + H(R) nR, skipped when a side is empty; the first
+//   minimum in the order a = 0, 1, 2, b = 1..31 wins (strict <);
+//   the range is partitioned stably (bin_a < b first) and mid = lo + nL;
+//   with no binned axis: mid = lo + (hi - lo) / 2 and the order is kept.
+// (An axis with e_a > 0 puts the smallest c2 in bin 0 and the largest in bin
+// 31, so a binned axis always has a candidate.)  Depth 32 onwards splits at
+// the middle, so no leaf is deeper than 32 + ceil(log2 ns).
+// Children: [lo, mid) and [mid, hi); a child of one position p is the leaf
+// ~p.  Numbering: the node split at mid has g = mid - 1, which no other node
+// of the tree has (g is in [0, ns - 2]); the root is internal node 0, the
+// node with g = 0 takes the root's g, every other node is numbered g.
+// Outputs as or_lbvh, except that keys_out[p] is the Morton key of the
+// triangle at position p (the keys are no longer sorted inside the tree).
+// ---------------------------------------------------------------------------
+int or_sah_bvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t* keys_out, int32_t* order,
+               int32_t* child, float* child_aabb, int64_t* nlarge_out) {
+    if (nlarge_out) *nlarge_out = 0;
+    if (nt_all <= 0) return 0;
+    std::vector<uint64_t> keys(nt_all);
+    std::vector<float> box(6 * nt_all);
+    int64_t nl = 0;
+    or_morton(verts, tris, nt_all, keys.data(), box.data(), &nl);
+    if (nlarge_out) *nlarge_out = nl;
+    std::vector<int32_t> idx(nt_all);
+    for (int64_t i = 0; i < nt_all; ++i) idx[i] = (int32_t)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return keys[a] < keys[b]; });
+    const int64_t ns = nt_all - nl;
+    constexpr int NB = 32, DEPTH_CAP = 32;
+    std::vector<float> c2(3 * nt_all);
+    for (int64_t t = 0; t < nt_all; ++t)
+        for (int a = 0; a < 3; ++a) c2[3 * t + a] = box[6 * t + a] + box[6 * t + 3 + a];
+    auto half_area = [](const float* b) {
+        const double dx = (double)(b[3] - b[0]), dy = (double)(b[4] - b[1]), dz = (double)(b[5] - b[2]);
+        return dx * dy + dy * dz + dz * dx;
+    };
+    auto unite = [](float* acc, const float* b) {
+        for (int a = 0; a < 3; ++a) {
+            acc[a] = std::min(acc[a], b[a]);
+            acc[3 + a] = std::max(acc[3 + a], b[3 + a]);
+        }
+    };
+    const float empty[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    struct Task { int64_t lo, hi; int depth; int64_t parent; int side; };
+    struct Done { int64_t id, lo, hi; };
+    std::vector<Task> st;
+    std::vector<Done> all;
+    if (ns >= 2) st.push_back({0, ns, 0, -1, 0});
+    int64_t g_root = -1;
+    while (!st.empty()) {
+        const Task tk = st.back();
+        st.pop_back();
+        float cl[3] = {INFINITY, INFINITY, INFINITY}, ch[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t p = tk.lo; p < tk.hi; ++p)
+            for (int a = 0; a < 3; ++a) {
+                cl[a] = std::min(cl[a], c2[3 * (size_t)idx[p] + a]);
+                ch[a] = std::max(ch[a], c2[3 * (size_t)idx[p] + a]);
+            }
+        int best_a = -1, best_b = -1;
+        double best = INFINITY;
+        float k[3] = {0.0f, 0.0f, 0.0f};
+        auto bin_of = [&](int32_t t, int a) {
+            const float d = c2[3 * (size_t)t + a] - cl[a];
+            const float f = d * k[a];
+            const int b = (int)f;
+            return b < NB - 1 ? b : NB - 1;
+        };
+        for (int a = 0; a < 3 && tk.depth < DEPTH_CAP; ++a) {
+            const float e = ch[a] - cl[a];
+            if (!(e > 0.0f)) continue;
+            k[a] = (float)NB / e;
+            if (!std::isfinite(k[a])) continue;
+            int64_t cnt[NB] = {0};
+            float bb[NB][6];
+            for (int b = 0; b < NB; ++b) std::memcpy(bb[b], empty, sizeof empty);
+            for (int64_t p = tk.lo; p < tk.hi; ++p) {
+                const int b = bin_of(idx[p], a);
+                ++cnt[b];
+                unite(bb[b], &box[6 * (size_t)idx[p]]);
+            }
+            // H and count of every right side R_b = bins b..31
+            double h_right[NB];
+            int64_t n_right[NB];
+            float acc[6];
+            std::memcpy(acc, empty, sizeof acc);
+            int64_t n = 0;
+            for (int b = NB - 1; b >= 1; --b) {
+                unite(acc, bb[b]);
+                n += cnt[b];
+                h_right[b] = half_area(acc);
+                n_right[b] = n;
+            }
+            std::memcpy(acc, empty, sizeof acc);
+            n = 0;
+            for (int b = 1; b < NB; ++b) {
+                unite(acc, bb[b - 1]);
+                n += cnt[b - 1];
+                if (n == 0 || n_right[b] == 0) continue;
+                const double c = half_area(acc) * (double)n + h_right[b] * (double)n_right[b];
+                if (c < best) {
+                    best = c;
+                    best_a = a;
+                    best_b = b;
+                }
+            }
+        }
+        int64_t mid;
+        if (best_a < 0) {
+            mid = tk.lo + (tk.hi - tk.lo) / 2;
+        } else {
+            const auto it = std::stable_partition(idx.begin() + tk.lo, idx.begin() + tk.hi,
+                                                  [&](int32_t t) { return bin_of(t, best_a) < best_b; });
+            mid = it - idx.begin();
+        }
+        const int64_t g = mid - 1;
+        if (tk.parent < 0) g_root = g;
+        const int64_t id = (tk.parent < 0) ? 0 : (g == 0 ? g_root : g);
+        if (tk.parent >= 0) child[2 * tk.parent + tk.side] = (int32_t)id;
+        all.push_back({id, tk.lo, tk.hi});
+        if (mid - tk.lo == 1) child[2 * id] = ~(int32_t)tk.lo;
+        else st.push_back({tk.lo, mid, tk.depth + 1, id, 0});
+        if (tk.hi - mid == 1) child[2 * id + 1] = ~(int32_t)mid;
+        else st.push_back({mid, tk.hi, tk.depth + 1, id, 1});
+    }
+    for (int64_t p = 0; p < nt_all; ++p) {
+        order[p] = idx[p];
+        keys_out[p] = keys[idx[p]];
+    }
+    // boxes bottom-up: smaller ranges first, so children are done before parents
+    std::vector<float> nodebox(6 * (size_t)std::max<int64_t>(ns - 1, 1));
+    std::sort(all.begin(), all.end(), [](const Done& x, const Done& y) { return (x.hi - x.lo) < (y.hi - y.lo); });
+    for (const Done& d : all) {
+        float* nb = &nodebox[6 * (size_t)d.id];
+        std::memcpy(nb, empty, sizeof empty);
+        for (int s = 0; s < 2; ++s) {
+            const int32_t c = child[2 * d.id + s];
+            const float* src = c < 0 ? &box[6 * (size_t)idx[~c]] : &nodebox[6 * (size_t)c];
+            std::memcpy(&child_aabb[12 * (size_t)d.id + 6 * s], src, 6 * sizeof(float));
+            unite(nb, src);
         }
     }
     return 0;
