@@ -2095,15 +2095,17 @@ int or_lbvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t* k
 //
 // Start: the LBVH's stable Morton order; the tree covers positions [0, ns).
 // A range [lo, hi) of at least 2 positions at depth d (the root [0, ns) at
-// d = 0) is split as follows (FP32 with round-to-nearest, no fused operations;
-// the costs in double, left to right):
+// d = 0) is split as follows (FP32 with round-to-nearest, no fused
+// operations, left to right):
 //   c2         = lo + hi of each triangle's AABB (the Morton code's centroid);
 //   cl_a, ch_a = min / max of c2_a over the range;
 //   axis a is binned when d < 32, e_a = ch_a - cl_a > 0 and k_a = 32 / e_a is
 //   finite;  bin_a(t) = min(31, trunc((c2_a(t) - cl_a) * k_a));
 //   each bin holds the count and the union of its triangles' AABBs; split b
 //   in 1..31 puts bins < b left (L) and bins >= b right (R); with
-//   H(B) = dx dy + dy dz + dz dx, dx = (double)(hi_x - lo_x),
+//   s = 2^-E where max_a e_a = f 2^E, f in [0.5, 1) (an exact power of two,
+//   so that the areas neither overflow nor round differently at any scale),
+//   H(B) = dx dy + dy dz + dz dx, dx = (hi_x - lo_x) s,
 //   cost(a, b) = H(L) nL + H(R) nR, skipped when a side is empty; the first
 //   minimum in the order a = 0, 1, 2, b = 1..31 wins (strict <);
 //   the range is partitioned stably (bin_a < b first) and mid = lo + nL;
@@ -2135,8 +2137,8 @@ int or_sah_bvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t
     std::vector<float> c2(3 * nt_all);
     for (int64_t t = 0; t < nt_all; ++t)
         for (int a = 0; a < 3; ++a) c2[3 * t + a] = box[6 * t + a] + box[6 * t + 3 + a];
-    auto half_area = [](const float* b) {
-        const double dx = (double)(b[3] - b[0]), dy = (double)(b[4] - b[1]), dz = (double)(b[5] - b[2]);
+    auto half_area = [](const float* b, float sc) {
+        const float dx = (b[3] - b[0]) * sc, dy = (b[4] - b[1]) * sc, dz = (b[5] - b[2]) * sc;
         return dx * dy + dy * dz + dz * dx;
     };
     auto unite = [](float* acc, const float* b) {
@@ -2162,8 +2164,11 @@ int or_sah_bvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t
                 ch[a] = std::max(ch[a], c2[3 * (size_t)idx[p] + a]);
             }
         int best_a = -1, best_b = -1;
-        double best = INFINITY;
+        float best = INFINITY;
         float k[3] = {0.0f, 0.0f, 0.0f};
+        int e_exp = 0;
+        std::frexp(std::max(std::max(ch[0] - cl[0], ch[1] - cl[1]), ch[2] - cl[2]), &e_exp);
+        const float sc = std::ldexp(1.0f, -e_exp);
         auto bin_of = [&](int32_t t, int a) {
             const float d = c2[3 * (size_t)t + a] - cl[a];
             const float f = d * k[a];
@@ -2184,7 +2189,7 @@ int or_sah_bvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t
                 unite(bb[b], &box[6 * (size_t)idx[p]]);
             }
             // H and count of every right side R_b = bins b..31
-            double h_right[NB];
+            float h_right[NB];
             int64_t n_right[NB];
             float acc[6];
             std::memcpy(acc, empty, sizeof acc);
@@ -2192,7 +2197,7 @@ int or_sah_bvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t
             for (int b = NB - 1; b >= 1; --b) {
                 unite(acc, bb[b]);
                 n += cnt[b];
-                h_right[b] = half_area(acc);
+                h_right[b] = half_area(acc, sc);
                 n_right[b] = n;
             }
             std::memcpy(acc, empty, sizeof acc);
@@ -2201,7 +2206,7 @@ int or_sah_bvh(const float* verts, const int32_t* tris, int64_t nt_all, uint64_t
                 unite(acc, bb[b - 1]);
                 n += cnt[b - 1];
                 if (n == 0 || n_right[b] == 0) continue;
-                const double c = half_area(acc) * (double)n + h_right[b] * (double)n_right[b];
+                const float c = half_area(acc, sc) * (float)n + h_right[b] * (float)n_right[b];
                 if (c < best) {
                     best = c;
                     best_a = a;

@@ -65,9 +65,16 @@ def _walk(b):
     return out
 
 
-def _half_area(box):
-    d = (box[3:] - box[:3]).astype(np.float32).astype(np.float64)
-    return d[0] * d[1] + d[1] * d[2] + d[2] * d[0]
+def _half_area(box, sc):
+    """dx dy + dy dz + dz dx of the box's extents scaled by sc, in FP32."""
+    d = ((box[3:] - box[:3]).astype(np.float32) * np.float32(sc)).astype(np.float32)
+    return np.float32(np.float32(np.float32(d[0] * d[1]) + np.float32(d[1] * d[2])) + np.float32(d[2] * d[0]))
+
+
+def _scale(cl, ch):
+    """2^-E with the node's largest centroid extent = f 2^E, f in [0.5, 1)."""
+    _, e = math.frexp(float((ch - cl).astype(np.float32).max()))
+    return np.float32(2.0 ** -e)
 
 
 def _check_structure(orc, scene):
@@ -114,9 +121,10 @@ def _bins(c, cl, k):
 @pytest.mark.parametrize("name", ["manhattan", "soup"])
 def test_every_split_is_the_best_candidate_plane(orc, name):
     """For every node: evaluate each of the 3 x 31 candidate planes from the
-    triangle sets (union boxes and counts of the two sides taken directly),
-    and check that the tree's left child holds exactly the triangles of the
-    first minimum."""
+    triangle sets (union boxes and counts of the two sides taken directly,
+    costs in FP32 on extents scaled by the node's power of two), and check
+    that the tree's left child holds exactly the triangles of the first
+    minimum."""
     scene = SCENES[name]()
     b, nodes = _check_structure(orc, scene)
     tb = _boxes(scene)
@@ -125,7 +133,8 @@ def test_every_split_is_the_best_candidate_plane(orc, name):
     for i, (lo, hi, mid, depth) in nodes.items():
         t = b["order"][lo:hi]
         cl, ch = c2[t].min(0), c2[t].max(0)
-        best, pick = math.inf, None
+        sc = _scale(cl, ch)
+        best, pick = np.float32(np.inf), None
         for a in range(3):
             e = np.float32(ch[a] - cl[a])
             if not (e > 0) or depth >= DEPTH_CAP:
@@ -141,9 +150,9 @@ def test_every_split_is_the_best_candidate_plane(orc, name):
                 if nl == 0 or nl == len(t):
                     continue
                 L, R = tb[t[left]], tb[t[~left]]
-                hl = _half_area(np.concatenate([L[:, :3].min(0), L[:, 3:].max(0)]))
-                hr = _half_area(np.concatenate([R[:, :3].min(0), R[:, 3:].max(0)]))
-                cost = hl * nl + hr * (len(t) - nl)
+                hl = _half_area(np.concatenate([L[:, :3].min(0), L[:, 3:].max(0)]), sc)
+                hr = _half_area(np.concatenate([R[:, :3].min(0), R[:, 3:].max(0)]), sc)
+                cost = np.float32(np.float32(hl * np.float32(nl)) + np.float32(hr * np.float32(len(t) - nl)))
                 if cost < best:
                     best, pick = cost, set(t[left].tolist())
         if pick is None:
