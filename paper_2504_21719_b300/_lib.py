@@ -77,6 +77,7 @@ _SIGS = {
     "rm_scene_upload_host": ([P, C.c_int64, P, C.c_int64, P, P, C.c_int32, P, C.POINTER(P)], C.c_int),
     "rm_scene_set_materials": ([P, P, C.c_int32, P], C.c_int),
     "rm_bvh_build": ([P, P], C.c_int),
+    "rm_bvh_build_ex": ([P, C.c_int32, P], C.c_int),
     "rm_bvh_export": ([P, P, P, P, P], C.c_int),
     "rm_radio_map_trace": ([P, P, C.c_int32, P, P, P, P, P], C.c_int),
     "rm_radio_map_trace_mesh": ([P, P, P, C.c_int32, P, P, P, P, P], C.c_int),

@@ -125,9 +125,13 @@ def tx_count(t: L.rm_tx) -> int:
 
 
 class Scene:
-    """A triangle mesh with per-triangle materials, uploaded and with its LBVH built."""
+    """A triangle mesh with per-triangle materials, uploaded and with its BVH built
+    (``builder``: "auto", "lbvh" or "sah"; see rm_bvh_build_ex)."""
 
-    def __init__(self, verts, tris, tri_mat, mats, device="cuda", stream=None, build=True, scat=None):
+    BUILDERS = {"auto": 0, "lbvh": 1, "sah": 2}
+
+    def __init__(self, verts, tris, tri_mat, mats, device="cuda", stream=None, build=True, scat=None,
+                 builder="auto"):
         lib = L.load()
         dev = torch.device(device)
 
@@ -164,14 +168,14 @@ class Scene:
                                        _stream(stream), C.byref(h)), "rm_scene_upload")
         self.handle = h
         if build:
-            self.build_bvh(stream)
+            self.build_bvh(stream, builder)
 
     @classmethod
     def from_obj(cls, sc, **kw):
         return cls(sc.verts, sc.tris, sc.tri_mat, sc.mats, scat=getattr(sc, "scat", None), **kw)
 
-    def build_bvh(self, stream=None):
-        _check(L.load().rm_bvh_build(self.handle, _stream(stream)), "rm_bvh_build")
+    def build_bvh(self, stream=None, builder="auto"):
+        _check(L.load().rm_bvh_build_ex(self.handle, self.BUILDERS[builder], _stream(stream)), "rm_bvh_build_ex")
 
     def set_materials(self, mats, sampling=None, scat=None):
         """Replace the materials; the diffuse parameters stay unless `scat` is given."""
@@ -186,7 +190,8 @@ class Scene:
         nt, nn, nm, built = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
         _check(L.load().rm_scene_info(self.handle, C.byref(nt), C.byref(nn), C.byref(nm), C.byref(built)),
                "rm_scene_info")
-        return {"nt": nt.value, "nodes": nn.value, "nm": nm.value, "built": bool(built.value)}
+        return {"nt": nt.value, "nodes": nn.value, "nm": nm.value, "built": bool(built.value),
+                "builder": {0: None, 1: "lbvh", 2: "sah"}[built.value]}
 
     def export_bvh(self):
         n = self.nt

@@ -1,6 +1,6 @@
 """Run one workload of the library a few times, for profilers and timing.
 
-    python -m paper_2504_21719_b300.cases CASE [--rays N] [--reps R]
+    python -m paper_2504_21719_b300.cases CASE [--rays N] [--reps R] [--builder auto|lbvh|sah]
 
 CASE is one of
   manhattan    forward trace, Manhattan scene (1202 triangles), 1 TX, depth 5
@@ -34,6 +34,7 @@ def main(argv=None):
                                     "batched", "mesh"])
     ap.add_argument("--rays", type=int, default=0, help="rays per TX (trace cases) or samples per wedge")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--builder", default="auto", choices=["auto", "lbvh", "sah"], help="the scene's BVH builder")
     a = ap.parse_args(argv)
     if a.case in ("manhattan", "diffuse", "diffraction", "mesh"):
         sc, txs, p = S.workload(2)
@@ -58,7 +59,7 @@ def main(argv=None):
            "city": "city", "city_adjoint": "city_adjoint", "batched": "batched", "mesh": "manhattan"}[a.case]
     blk, bps, qch, rfm = lookup(torch.cuda.get_device_name(0), cls)
     p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
-    gs = api.Scene.from_obj(sc)
+    gs = api.Scene.from_obj(sc, builder=a.builder)
     su = api.surface(*S.terrain_surface(256.0, 256)) if a.case == "mesh" else None
     for _ in range(a.reps):
         if a.case == "mesh":

@@ -25,6 +25,7 @@ struct rm_scene {
     std::vector<rm_material> mats, smats;
     bool has_smats = false;
     bool built = false;
+    int32_t builder = 0;         // RM_BVH_LBVH or RM_BVH_SAH once built
     // triangles kept out of the tree (tested from a list).  The build does not
     // wait for its count: the device copies it into a pinned slot and records
     // built_ev; the first call that needs it (resolve_nlarge) waits there.
@@ -904,11 +905,16 @@ rm_status rm_scene_set_materials(rm_scene* sc, const rm_material* mats_host, int
     return RM_OK;
 }
 
-rm_status rm_bvh_build(rm_scene* sc, void* stream) {
+rm_status rm_bvh_build(rm_scene* sc, void* stream) { return rm_bvh_build_ex(sc, RM_BVH_AUTO, stream); }
+
+rm_status rm_bvh_build_ex(rm_scene* sc, int32_t builder, void* stream) {
     if (!sc) return fail(RM_EINVAL, "scene is NULL");
+    if (builder != RM_BVH_AUTO && builder != RM_BVH_LBVH && builder != RM_BVH_SAH)
+        return fail(RM_EINVAL, "builder must be RM_BVH_AUTO, RM_BVH_LBVH or RM_BVH_SAH");
     rm_status st = check_device(sc);
     if (st != RM_OK) return st;
     if (sc->built) return fail(RM_ESTATE, "the BVH of this scene is already built");
+    if (builder == RM_BVH_AUTO) builder = sc->nt > RM_BVH_AUTO_SAH_MIN ? RM_BVH_SAH : RM_BVH_LBVH;
     if (injected(RM_FAULT_ALLOC)) return fail(RM_ENOMEM, "rm_bvh_build: injected allocation failure");
     const int64_t n = sc->nt;
     if (n > 0) {
@@ -936,11 +942,11 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
         }
         if (!slot) {  // no pinned slot: wait for the count
             int32_t large = 0;
-            RM_CUDA(build_bvh(B, S(stream), &large));
+            RM_CUDA(build_bvh(B, builder == RM_BVH_SAH ? BVH_SAH : BVH_LBVH, S(stream), &large));
             RM_CUDA(cudaStreamSynchronize(S(stream)));
             sc->nlarge = (large > 0 && large <= MAX_LARGE_TRIS) ? large : 0;
         } else {
-            cudaError_t e = build_bvh(B, S(stream), slot);
+            cudaError_t e = build_bvh(B, builder == RM_BVH_SAH ? BVH_SAH : BVH_LBVH, S(stream), slot);
             if (e == cudaSuccess) e = cudaEventRecord(ev, S(stream));
             if (e != cudaSuccess) {
                 cudaStreamSynchronize(S(stream));
@@ -955,6 +961,7 @@ rm_status rm_bvh_build(rm_scene* sc, void* stream) {
         }
     }
     sc->built = true;
+    sc->builder = builder;
     return RM_OK;
 }
 
@@ -1367,7 +1374,7 @@ rm_status rm_scene_info(const rm_scene* sc, int64_t* nt, int64_t* nnodes, int32_
     const int64_t ns = sc->nt - sc->nlarge;
     if (nnodes) *nnodes = ns > 1 ? ns - 1 : 0;
     if (nm) *nm = sc->nm;
-    if (built) *built = sc->built ? 1 : 0;
+    if (built) *built = sc->built ? sc->builder : 0;
     return RM_OK;
 }
 

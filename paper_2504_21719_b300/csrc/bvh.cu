@@ -19,6 +19,8 @@
 // child >= 0: internal node; child < 0: leaf ~p, the triangle at sorted
 // position p, whose 48-byte record is trirec[3p .. 3p+2]:
 //   [0] a.x a.y a.z b.x   [1] b.y b.z c.x c.y   [2] c.z mat(int) orig(int) 0
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace rmsbr {
@@ -405,6 +407,675 @@ __global__ void k_trirec(const float* __restrict__ verts, const int32_t* __restr
     rec[3 * p + 2] = make_float4(c[2], __int_as_float(tri_mat[t]), __int_as_float(t), 0.0f);
 }
 
+// ---------------- binned-SAH tree, top down, level by level ----------------
+// The same leaves as the LBVH (one triangle per leaf, the large triangles out
+// of the tree) under splits that minimise the surface-area heuristic
+// (MacDonald & Booth 1990) over 32 centroid bins per axis (Wald 2007).
+// Definition, for a range [lo, hi) of positions at depth d, in the Morton
+// order to start with (FP32 rounded to nearest, no fused operations, left
+// to right):
+//   cl, ch = min / max of the doubled centroids c2 over the range;
+//   axis a is binned if d < SAH_DEPTH_CAP, e = ch_a - cl_a > 0 and
+//   k = 32 / e is finite; bin(t) = min(31, trunc((c2_a(t) - cl_a) k));
+//   split b in 1..31: bins < b left; cost = H(L) nL + H(R) nR with
+//   H = dx dy + dy dz + dz dx of the side's AABB, its extents scaled by
+//   s = 2^-E, max_a e_a = f 2^E with f in [0.5, 1) (exact, so neither an
+//   overflow nor a different rounding at any scale; skipped if a side is empty);
+//   the first minimum over (a = 0..2, b = 1..31) wins; stable partition,
+//   mid = lo + nL; no binned axis: mid = lo + (hi - lo) / 2, order kept.
+// Node numbers: the node split at mid is g = mid - 1 (distinct for every
+// node), the root is 0 and the node with g = 0 takes the root's g.  The
+// child boxes come from the LBVH's refit afterwards.
+//
+// Level L holds the ranges at depth L, each with its centroid bounds (the
+// root's are the Morton bounds; a split computes its children's while it
+// partitions).  A range reads its positions from buffer L & 1 and writes
+// its stable partition to the other buffer; a child of one position writes
+// the final order.  Ranges of at most SAH_BIG positions are split by one
+// warp each (bins, sweep, partition); larger ones by every block together in
+// chunks of SAH_CHUNK positions: plan (chunk bases, cleared bins), bin (per
+// chunk histograms merged into the range's bins), decide (sweep, split, each
+// chunk's left offset from its histograms), scatter (partition, children's
+// centroid bounds); the next level's plan writes their nodes and children.
+constexpr int SAH_BINS = 32;
+constexpr int SAH_NB3 = 3 * SAH_BINS;
+constexpr int SAH_DEPTH_CAP = 32;     // from this depth on: middle splits (depth <= 32 + log2 n)
+constexpr int SAH_BIG = 2048;         // larger ranges: chunked over all blocks; others: one warp
+constexpr int SAH_CHUNK = 4096;
+constexpr int SAH_BLOCK = 512;        // threads of the chunk kernels
+constexpr int SAH_PLAN = 1024;        // threads of the plan kernel (one block)
+constexpr int SAH_WARPS = 8;          // warps per block of the warp kernel
+
+struct SahTask {
+    int32_t lo, hi, parent, meta;     // meta = depth << 1 | side in the parent; parent < 0: the root
+    float cl[3], ch[3];               // centroid bounds of the range
+};
+// per big range, by level parity
+struct SahAux {
+    float k[3];
+    int32_t ok;                       // bit a: axis a binned
+    int32_t pick_a, pick_b, mid;      // pick_a < 0: middle split
+    int32_t ccb[2][6];                // children's centroid bounds (order-preserving int images)
+};
+struct SahArgs {
+    const float* c2;                  // [nt][3] doubled centroids
+    const float* aabb;                // [nt][6]
+    int32_t* buf[2];                  // [nt] positions -> triangle, by level parity
+    int32_t* order;                   // [nt] final order (leaves write it)
+    float4* nodes;
+    int32_t* parent_leaf;
+    int32_t* parent_node;
+    SahTask* big[2];                  // task lists by level parity
+    SahTask* small[2];
+    int32_t* cnt_big;                 // [levels + 2] tasks per level
+    int32_t* cnt_small;
+    int32_t cap_big, cap_small, cap_chunks;
+    int32_t* bins;                    // [cap_big][SAH_NB3 * 7]: counts, then lo xyz hi xyz images
+    SahAux* aux[2];                   // [cap_big] by level parity
+    int32_t* chunk_base;              // [cap_big + 1] first chunk of each big range, then the total
+    int32_t* hist;                    // [cap_chunks][SAH_NB3] per-chunk bin counts
+    int32_t* loff;                    // [cap_chunks] each chunk's first left slot within its range
+    int32_t* groot;                   // the root's split position g
+    int32_t* err;                     // bit 0: a list was full (cannot happen for a binary tree)
+};
+
+// float <-> int with the same order (min / max of the ints = min / max of the floats)
+__device__ __forceinline__ int32_t f2o(float f) {
+    const int32_t i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float o2f(int32_t i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ int sah_bin(float c, float cl, float k) {
+    const int b = __float2int_rz(__fmul_rn(__fsub_rn(c, cl), k));
+    return b < SAH_BINS - 1 ? b : SAH_BINS - 1;
+}
+__device__ __forceinline__ float half_area(const float lo[3], const float hi[3], float sc) {
+    const float dx = __fmul_rn(__fsub_rn(hi[0], lo[0]), sc), dy = __fmul_rn(__fsub_rn(hi[1], lo[1]), sc),
+                dz = __fmul_rn(__fsub_rn(hi[2], lo[2]), sc);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx));
+}
+// the range's cost scale: 2^-E with its largest centroid extent = f 2^E, f in [0.5, 1)
+__device__ __forceinline__ float sah_scale(const SahTask& tk) {
+    const float m = fmax_sel(fmax_sel(__fsub_rn(tk.ch[0], tk.cl[0]), __fsub_rn(tk.ch[1], tk.cl[1])),
+                             __fsub_rn(tk.ch[2], tk.cl[2]));
+    int e = 0;
+    frexpf(m, &e);
+    return ldexpf(1.0f, -e);
+}
+__device__ __forceinline__ float sel3(const float v[3], int a) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
+
+// the binned axes of a range and their scales
+__device__ __forceinline__ int sah_axes(const SahTask& tk, float k[3]) {
+    int ok = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float e = __fsub_rn(tk.ch[a], tk.cl[a]);
+        k[a] = __fdiv_rn((float)SAH_BINS, e);
+        if ((tk.meta >> 1) < SAH_DEPTH_CAP && e > 0.0f && k[a] < INFINITY) ok |= 1 << a;
+    }
+    return ok;
+}
+
+// bins of one group: counts [SAH_NB3], then boxes [SAH_NB3][6] as int images
+__device__ __forceinline__ void bins_clear(int32_t* cnt, int32_t* box, int t, int G) {
+    for (int i = t; i < SAH_NB3; i += G) {
+        cnt[i] = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { box[6 * i + j] = f2o(INFINITY); box[6 * i + 3 + j] = f2o(-INFINITY); }
+    }
+}
+
+// a run of equal bins of one axis, summed in registers and flushed with atomics
+struct SahRun {
+    int b = -1, c = 0;
+    float lo[3], hi[3];
+    __device__ __forceinline__ void flush(int32_t* cnt, int32_t* box, int a) {
+        if (c == 0) return;
+        const int i = a * SAH_BINS + b;
+        atomicAdd(&cnt[i], c);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            atomicMin(&box[6 * i + j], f2o(lo[j]));
+            atomicMax(&box[6 * i + 3 + j], f2o(hi[j]));
+        }
+    }
+    __device__ __forceinline__ void add(int32_t* cnt, int32_t* box, int a, int bin, const float blo[3],
+                                        const float bhi[3]) {
+        if (bin != b) {
+            flush(cnt, box, a);
+            b = bin;
+            c = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) { lo[j] = INFINITY; hi[j] = -INFINITY; }
+        }
+        ++c;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { lo[j] = fmin_sel(lo[j], blo[j]); hi[j] = fmax_sel(hi[j], bhi[j]); }
+    }
+};
+
+// Bins the positions p = first + t, first + t + G, ... < end of buffer `src`
+// into (cnt, box) with shared or global atomics.
+__device__ __forceinline__ void bin_positions(const SahArgs& A, const int32_t* __restrict__ src, int first, int end,
+                                              int t, int G, int ok, const float cl[3], const float k[3],
+                                              int32_t* cnt, int32_t* box) {
+    SahRun r0, r1, r2;
+    for (int p = first + t; p < end; p += G) {
+        const int32_t tri = src[p];
+        const float* c = A.c2 + 3 * (int64_t)tri;
+        const float* bx = A.aabb + 6 * (int64_t)tri;
+        float blo[3], bhi[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { blo[j] = bx[j]; bhi[j] = bx[3 + j]; }
+        if (ok & 1) r0.add(cnt, box, 0, sah_bin(c[0], cl[0], k[0]), blo, bhi);
+        if (ok & 2) r1.add(cnt, box, 1, sah_bin(c[1], cl[1], k[1]), blo, bhi);
+        if (ok & 4) r2.add(cnt, box, 2, sah_bin(c[2], cl[2], k[2]), blo, bhi);
+    }
+    r0.flush(cnt, box, 0);
+    r1.flush(cnt, box, 1);
+    r2.flush(cnt, box, 2);
+}
+
+// The best split of axis a by a warp, lane b holding bin b (SAH_BINS == 32
+// bins): the left and right unions by inclusive scans, the cost of split
+// b = lane in lane b, and the first minimum (the lowest b of the least cost)
+// by a reduction.  Returns the split, -1 without a candidate, in every lane.
+static_assert(SAH_BINS == 32, "one bin per lane");
+__device__ __forceinline__ int warp_sweep(const int32_t* cnt, const int32_t* box, int a, float sc, int lane,
+                                          float* best_out) {
+    const int i = a * SAH_BINS + lane;
+    int nl = cnt[i], nr = nl;
+    float llo[3], lhi[3], rlo[3], rhi[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        llo[j] = rlo[j] = o2f(box[6 * i + j]);
+        lhi[j] = rhi[j] = o2f(box[6 * i + 3 + j]);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ul = __shfl_up_sync(0xffffffffu, nl, o), dr = __shfl_down_sync(0xffffffffu, nr, o);
+        float ulo[3], uhi[3], dlo[3], dhi[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            ulo[j] = __shfl_up_sync(0xffffffffu, llo[j], o);
+            uhi[j] = __shfl_up_sync(0xffffffffu, lhi[j], o);
+            dlo[j] = __shfl_down_sync(0xffffffffu, rlo[j], o);
+            dhi[j] = __shfl_down_sync(0xffffffffu, rhi[j], o);
+        }
+        if (lane >= o) {
+            nl += ul;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) { llo[j] = fmin_sel(llo[j], ulo[j]); lhi[j] = fmax_sel(lhi[j], uhi[j]); }
+        }
+        if (lane + o < 32) {
+            nr += dr;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) { rlo[j] = fmin_sel(rlo[j], dlo[j]); rhi[j] = fmax_sel(rhi[j], dhi[j]); }
+        }
+    }
+    // split b = lane: the left side is the union of bins < b, the prefix of lane b - 1
+    const int nL = __shfl_up_sync(0xffffffffu, nl, 1);
+    float Llo[3], Lhi[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        Llo[j] = __shfl_up_sync(0xffffffffu, llo[j], 1);
+        Lhi[j] = __shfl_up_sync(0xffffffffu, lhi[j], 1);
+    }
+    float c = INFINITY;
+    if (lane >= 1 && nL > 0 && nr > 0)
+        c = __fadd_rn(__fmul_rn(half_area(Llo, Lhi, sc), __int2float_rn(nL)),
+                      __fmul_rn(half_area(rlo, rhi, sc), __int2float_rn(nr)));
+    const bool valid = c < INFINITY;   // the serial rule: a cost below the best so far, which starts at +inf
+    float bc = valid ? c : INFINITY;
+    int bb = valid ? lane : SAH_BINS;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, bb, o);
+        if (oc < bc || (oc == bc && ob < bb)) { bc = oc; bb = ob; }
+    }
+    *best_out = bc;
+    return bb < SAH_BINS ? bb : -1;
+}
+
+__device__ __forceinline__ void sah_push(const SahArgs& A, int level, const SahTask& t) {
+    const bool big = (t.hi - t.lo) > SAH_BIG;
+    int32_t* cnt = big ? A.cnt_big + level : A.cnt_small + level;
+    // (selects, not an index: a kernel parameter indexed at run time would be copied to local memory)
+    SahTask* list = big ? ((level & 1) ? A.big[1] : A.big[0]) : ((level & 1) ? A.small[1] : A.small[0]);
+    const int s = atomicAdd(cnt, 1);
+    if (s < (big ? A.cap_big : A.cap_small)) list[s] = t;
+    else atomicOr(A.err, 1);
+}
+
+// The node of a split range: its number, its record, its parent's link and
+// leaf children (whose triangle is at their position of `dst`), and the
+// tasks of its larger children with their centroid bounds.
+__device__ __forceinline__ void sah_node(const SahArgs& A, const SahTask& tk, int level, int mid,
+                                         const int32_t* __restrict__ dst, const float lcl[3], const float lch[3],
+                                         const float rcl[3], const float rch[3]) {
+    const int lo = tk.lo, hi = tk.hi;
+    const int g = mid - 1;
+    int id;
+    if (tk.parent < 0) {
+        *A.groot = g;
+        id = 0;
+    } else {
+        id = (g == 0) ? *A.groot : g;
+        reinterpret_cast<int32_t*>(&A.nodes[4 * (int64_t)tk.parent + 3])[tk.meta & 1] = id;
+        A.parent_node[id] = tk.parent;
+    }
+    const int32_t c0 = (mid - lo == 1) ? ~(int32_t)lo : 0, c1 = (hi - mid == 1) ? ~(int32_t)mid : 0;
+    A.nodes[4 * (int64_t)id + 3] = make_float4(__int_as_float(c0), __int_as_float(c1), 0.0f, 0.0f);
+    const int meta = ((tk.meta >> 1) + 1) << 1;
+    if (mid - lo == 1) {
+        A.parent_leaf[lo] = id;
+        A.order[lo] = dst[lo];
+    } else {
+        sah_push(A, level + 1, SahTask{lo, mid, id, meta, {lcl[0], lcl[1], lcl[2]}, {lch[0], lch[1], lch[2]}});
+    }
+    if (hi - mid == 1) {
+        A.parent_leaf[mid] = id;
+        A.order[mid] = dst[mid];
+    } else {
+        sah_push(A, level + 1, SahTask{mid, hi, id, meta | 1, {rcl[0], rcl[1], rcl[2]}, {rch[0], rch[1], rch[2]}});
+    }
+}
+
+// min / max of three values over a group of G threads (a warp, or a block
+// with G / 32 <= 32 warps and `red` [G / 32][6] of shared scratch); every
+// thread receives them
+template <int G>
+__device__ __forceinline__ void g_minmax3(float mn[3], float mx[3], float (*red)[6]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin_sel(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax_sel(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if (G > 32) {
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { red[w][a] = mn[a]; red[w][3 + a] = mx[a]; }
+        __syncthreads();
+        for (int i = 0; i < G / 32; ++i)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { mn[a] = fmin_sel(mn[a], red[i][a]); mx[a] = fmax_sel(mx[a], red[i][3 + a]); }
+        __syncthreads();
+    }
+}
+
+// rank of f among the group's threads below this one, and the group's count
+// of f (block: `wcnt` [G / 32] of shared scratch)
+template <int G>
+__device__ __forceinline__ int g_rank(bool f, int* total, int32_t* wcnt) {
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int l = threadIdx.x & 31;
+    const int r = __popc(bal & ((1u << l) - 1u));
+    if (G == 32) {
+        *total = __popc(bal);
+        return r;
+    }
+    const int w = threadIdx.x >> 5;
+    if (l == 0) wcnt[w] = __popc(bal);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int i = 0; i < G / 32; ++i) {
+        const int c = wcnt[i];
+        before += (i < w) ? c : 0;
+        tot += c;
+    }
+    __syncthreads();
+    *total = tot;
+    return r + before;
+}
+
+// inclusive prefix sum over a warp
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int l = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (l >= o) v += u;
+    }
+    return v;
+}
+
+// Partitions positions [first, end) of `src` stably into `dst`: elements
+// with f go to lo_dst + done_l + rank, the others to r_dst + done_r + rank
+// (ranks in order), where f = bin on axis pick_a < pick_b, or p < mid when
+// pick_a < 0.  Accumulates each side's centroid bounds per thread.
+template <int G>
+__device__ __forceinline__ void partition_positions(const SahArgs& A, const int32_t* __restrict__ src,
+                                                    int32_t* __restrict__ dst, int first, int end, int t,
+                                                    int pick_a, int pick_b, float cla, float ka, int mid,
+                                                    int l_dst, int r_dst, float lcl[3], float lch[3], float rcl[3],
+                                                    float rch[3], int32_t* wcnt) {
+    int done_l = 0, done_r = 0;
+    for (int base = first; base < end; base += G) {
+        const int p = base + t;
+        int32_t tri = 0;
+        bool f = false;
+        if (p < end) {
+            tri = src[p];
+            const float* c = A.c2 + 3 * (int64_t)tri;
+            const float cx = c[0], cy = c[1], cz = c[2];
+            f = pick_a >= 0 ? sah_bin(pick_a == 0 ? cx : (pick_a == 1 ? cy : cz), cla, ka) < pick_b : p < mid;
+            if (f) {
+                lcl[0] = fmin_sel(lcl[0], cx); lcl[1] = fmin_sel(lcl[1], cy); lcl[2] = fmin_sel(lcl[2], cz);
+                lch[0] = fmax_sel(lch[0], cx); lch[1] = fmax_sel(lch[1], cy); lch[2] = fmax_sel(lch[2], cz);
+            } else {
+                rcl[0] = fmin_sel(rcl[0], cx); rcl[1] = fmin_sel(rcl[1], cy); rcl[2] = fmin_sel(rcl[2], cz);
+                rch[0] = fmax_sel(rch[0], cx); rch[1] = fmax_sel(rch[1], cy); rch[2] = fmax_sel(rch[2], cz);
+            }
+        }
+        int tot;
+        const int r = g_rank<G>(f, &tot, wcnt);
+        if (p < end) dst[f ? l_dst + done_l + r : r_dst + done_r + (t - r)] = tri;
+        done_l += tot;
+        done_r += min(G, end - base) - tot;
+    }
+}
+
+// ---- ranges of at most SAH_BIG positions: one warp each ----
+struct SahWarpShared {
+    int32_t cnt[SAH_NB3];
+    int32_t box[SAH_NB3 * 6];
+};
+
+// the first minimum over the binned axes (a = 0, 1, 2; strict <), by the whole warp
+__device__ __forceinline__ void sah_pick(const int32_t* cnt, const int32_t* box, int ok, float sc, int lane,
+                                         int* pick_a, int* pick_b) {
+    float best = INFINITY;
+    *pick_a = -1;
+    *pick_b = -1;
+    for (int a = 0; a < 3; ++a) {
+        if (!((ok >> a) & 1)) continue;
+        float c;
+        const int b = warp_sweep(cnt, box, a, sc, lane, &c);
+        if (b >= 0 && c < best) {
+            best = c;
+            *pick_a = a;
+            *pick_b = b;
+        }
+    }
+}
+
+__device__ __forceinline__ void sah_split_warp(const SahArgs& A, const SahTask& tk, int level, int lane,
+                                               SahWarpShared& S) {
+    const int32_t* src = (level & 1) ? A.buf[1] : A.buf[0];
+    int32_t* dst = (level & 1) ? A.buf[0] : A.buf[1];
+    float k[3];
+    const int ok = sah_axes(tk, k);
+    int pick_a = -1, pick_b = -1;
+    if (ok) {
+        bins_clear(S.cnt, S.box, lane, 32);
+        __syncwarp();
+        bin_positions(A, src, tk.lo, tk.hi, lane, 32, ok, tk.cl, k, S.cnt, S.box);
+        __syncwarp();
+        sah_pick(S.cnt, S.box, ok, sah_scale(tk), lane, &pick_a, &pick_b);
+    }
+    int nl = (tk.hi - tk.lo) / 2;
+    if (pick_a >= 0) {
+        nl = 0;
+        for (int b = 0; b < pick_b; ++b) nl += S.cnt[pick_a * SAH_BINS + b];
+    }
+    const int mid = tk.lo + nl;
+    float lcl[3] = {INFINITY, INFINITY, INFINITY}, lch[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float rcl[3] = {INFINITY, INFINITY, INFINITY}, rch[3] = {-INFINITY, -INFINITY, -INFINITY};
+    partition_positions<32>(A, src, dst, tk.lo, tk.hi, lane, pick_a, pick_b, sel3(tk.cl, pick_a), sel3(k, pick_a),
+                            mid, tk.lo, mid, lcl, lch, rcl, rch, nullptr);
+    g_minmax3<32>(lcl, lch, nullptr);
+    g_minmax3<32>(rcl, rch, nullptr);
+    __syncwarp();
+    if (lane == 0) sah_node(A, tk, level, mid, dst, lcl, lch, rcl, rch);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * SAH_WARPS) k_sah_small(SahArgs A, int level) {
+    __shared__ SahWarpShared S[SAH_WARPS];
+    const int w = threadIdx.x >> 5;
+    const int n = min(A.cnt_small[level], A.cap_small);
+    const SahTask* in = (level & 1) ? A.small[1] : A.small[0];
+    for (int s = blockIdx.x * SAH_WARPS + w; s < n; s += gridDim.x * SAH_WARPS)
+        sah_split_warp(A, in[s], level, threadIdx.x & 31, S[w]);
+}
+
+// the root task: the tree's positions [0, ns) with the Morton bounds of their centroids
+__global__ void k_sah_root(SahArgs A, const int32_t* __restrict__ count, int64_t nt, const float* __restrict__ bnd) {
+    const int64_t ns = tree_size(count, nt);
+    if (ns >= 2) sah_push(A, 0, SahTask{0, (int32_t)ns, -1, 0, {bnd[0], bnd[1], bnd[2]}, {bnd[3], bnd[4], bnd[5]}});
+}
+
+// ---- ranges of more than SAH_BIG positions: chunked over every block ----
+// the big range holding chunk c: the last i < nb with chunk_base[i] <= c
+__device__ __forceinline__ int chunk_owner(const int32_t* __restrict__ base, int nb, int c) {
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (base[m] <= c) lo = m;
+        else hi = m - 1;
+    }
+    return lo;
+}
+
+// Finishes the big ranges of the previous level (their nodes and children),
+// then plans this level's: chunk bases (exclusive prefix sum of their chunk
+// counts), cleared bins, binned axes, cleared children's bounds.  One block.
+__global__ void __launch_bounds__(SAH_PLAN) k_sah_plan(SahArgs A, int level) {
+    __shared__ int32_t wsum[SAH_PLAN / 32];
+    __shared__ int32_t carry;
+    if (level > 0) {
+        const int pl = level - 1;
+        const int nbp = min(A.cnt_big[pl], A.cap_big);
+        const SahTask* in = (pl & 1) ? A.big[1] : A.big[0];
+        const SahAux* ax = (pl & 1) ? A.aux[1] : A.aux[0];
+        const int32_t* dst = (pl & 1) ? A.buf[0] : A.buf[1];   // where level pl partitioned to
+        for (int i = threadIdx.x; i < nbp; i += SAH_PLAN) {
+            const SahAux& x = ax[i];
+            float lcl[3], lch[3], rcl[3], rch[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lcl[a] = o2f(x.ccb[0][a]);
+                lch[a] = o2f(x.ccb[0][3 + a]);
+                rcl[a] = o2f(x.ccb[1][a]);
+                rch[a] = o2f(x.ccb[1][3 + a]);
+            }
+            sah_node(A, in[i], pl, x.mid, dst, lcl, lch, rcl, rch);
+        }
+        __syncthreads();   // their pushes fill this level's lists
+    }
+    const int nb = min(A.cnt_big[level], A.cap_big);
+    const SahTask* in = (level & 1) ? A.big[1] : A.big[0];
+    SahAux* ax = (level & 1) ? A.aux[1] : A.aux[0];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int base = 0; base < nb; base += SAH_PLAN) {
+        const int i = base + threadIdx.x;
+        int v = 0;
+        if (i < nb) {
+            const SahTask tk = in[i];
+            v = (tk.hi - tk.lo + SAH_CHUNK - 1) / SAH_CHUNK;
+            SahAux& x = ax[i];
+            x.ok = sah_axes(tk, x.k);
+            x.pick_a = -1;
+            x.pick_b = -1;
+            x.mid = tk.lo;
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) { x.ccb[s][a] = f2o(INFINITY); x.ccb[s][3 + a] = f2o(-INFINITY); }
+        }
+        const int incl = warp_incl_scan(v);
+        if (l == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const int s = warp_incl_scan(wsum[l]);
+            wsum[l] = s;   // inclusive over warps
+        }
+        __syncthreads();
+        const int excl = carry + (w > 0 ? wsum[w - 1] : 0) + incl - v;
+        if (i < nb) A.chunk_base[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == SAH_PLAN - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) A.chunk_base[nb] = carry;
+    for (int i = threadIdx.x; i < nb * SAH_NB3; i += SAH_PLAN) {
+        int32_t* g = A.bins + (int64_t)(i / SAH_NB3) * (SAH_NB3 * 7);
+        const int j = i % SAH_NB3;
+        g[j] = 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { g[SAH_NB3 + 6 * j + q] = f2o(INFINITY); g[SAH_NB3 + 6 * j + 3 + q] = f2o(-INFINITY); }
+    }
+}
+
+// Bins every chunk of this level's big ranges: shared bins per chunk, stored
+// as the chunk's histogram and merged into its range's bins.
+__global__ void __launch_bounds__(SAH_BLOCK) k_sah_bin(SahArgs A, int level) {
+    __shared__ int32_t cnt[SAH_NB3];
+    __shared__ int32_t box[SAH_NB3 * 6];
+    const int nb = min(A.cnt_big[level], A.cap_big);
+    if (nb == 0) return;
+    const int nch = min(A.chunk_base[nb], A.cap_chunks);
+    const SahTask* in = (level & 1) ? A.big[1] : A.big[0];
+    const SahAux* ax = (level & 1) ? A.aux[1] : A.aux[0];
+    const int32_t* src = (level & 1) ? A.buf[1] : A.buf[0];
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int i = chunk_owner(A.chunk_base, nb, c);
+        const SahTask tk = in[i];
+        const int ok = ax[i].ok;
+        float k[3] = {ax[i].k[0], ax[i].k[1], ax[i].k[2]};
+        const int first = tk.lo + (c - A.chunk_base[i]) * SAH_CHUNK;
+        const int end = min(tk.hi, first + SAH_CHUNK);
+        bins_clear(cnt, box, threadIdx.x, SAH_BLOCK);
+        __syncthreads();
+        if (ok) bin_positions(A, src, first, end, threadIdx.x, SAH_BLOCK, ok, tk.cl, k, cnt, box);
+        __syncthreads();
+        int32_t* gcnt = A.bins + (int64_t)i * (SAH_NB3 * 7);
+        int32_t* gbox = gcnt + SAH_NB3;
+        for (int j = threadIdx.x; j < SAH_NB3; j += SAH_BLOCK) {
+            const int n = cnt[j];
+            A.hist[(int64_t)c * SAH_NB3 + j] = n;
+            if (n) {
+                atomicAdd(&gcnt[j], n);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    atomicMin(&gbox[6 * j + q], box[6 * j + q]);
+                    atomicMax(&gbox[6 * j + 3 + q], box[6 * j + 3 + q]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One warp per big range: the split, then each chunk's first left slot (an
+// exclusive prefix sum over the range's chunks of their left counts, read
+// from the histograms, or from the middle for a middle split).
+__global__ void __launch_bounds__(32 * SAH_WARPS) k_sah_decide(SahArgs A, int level) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = min(A.cnt_big[level], A.cap_big);
+    const SahTask* in = (level & 1) ? A.big[1] : A.big[0];
+    SahAux* ax = (level & 1) ? A.aux[1] : A.aux[0];
+    for (int i = blockIdx.x * SAH_WARPS + w; i < nb; i += gridDim.x * SAH_WARPS) {
+        const SahTask tk = in[i];
+        const int32_t* gcnt = A.bins + (int64_t)i * (SAH_NB3 * 7);
+        int pick_a = -1, pick_b = -1;
+        const int ok = ax[i].ok;
+        if (ok) sah_pick(gcnt, gcnt + SAH_NB3, ok, sah_scale(tk), lane, &pick_a, &pick_b);
+        int nl = (tk.hi - tk.lo) / 2;
+        if (pick_a >= 0) {
+            nl = 0;
+            for (int b = 0; b < pick_b; ++b) nl += gcnt[pick_a * SAH_BINS + b];
+        }
+        const int mid = tk.lo + nl;
+        const int c0 = A.chunk_base[i];
+        const int nc = (tk.hi - tk.lo + SAH_CHUNK - 1) / SAH_CHUNK;
+        int carry = 0;
+        for (int j0 = 0; j0 < nc; j0 += 32) {
+            const int j = j0 + lane;
+            int v = 0;
+            if (j < nc && c0 + j < A.cap_chunks) {
+                const int first = tk.lo + j * SAH_CHUNK;
+                const int len = min(SAH_CHUNK, tk.hi - first);
+                if (pick_a >= 0) {
+                    const int32_t* h = A.hist + (int64_t)(c0 + j) * SAH_NB3 + pick_a * SAH_BINS;
+                    for (int b = 0; b < pick_b; ++b) v += h[b];
+                } else {
+                    v = max(0, min(mid - first, len));
+                }
+            }
+            const int incl = warp_incl_scan(v);
+            if (j < nc && c0 + j < A.cap_chunks) A.loff[c0 + j] = carry + incl - v;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) {
+            ax[i].pick_a = pick_a;
+            ax[i].pick_b = pick_b;
+            ax[i].mid = mid;
+        }
+        __syncwarp();
+    }
+}
+
+// Partitions every chunk of this level's big ranges into the other buffer
+// and merges each side's centroid bounds into its range's children's bounds.
+__global__ void __launch_bounds__(SAH_BLOCK) k_sah_scatter(SahArgs A, int level) {
+    __shared__ float red[SAH_BLOCK / 32][6];
+    __shared__ int32_t wcnt[SAH_BLOCK / 32];
+    const int nb = min(A.cnt_big[level], A.cap_big);
+    if (nb == 0) return;
+    const int nch = min(A.chunk_base[nb], A.cap_chunks);
+    const SahTask* in = (level & 1) ? A.big[1] : A.big[0];
+    SahAux* ax = (level & 1) ? A.aux[1] : A.aux[0];
+    const int32_t* src = (level & 1) ? A.buf[1] : A.buf[0];
+    int32_t* dst = (level & 1) ? A.buf[0] : A.buf[1];
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int i = chunk_owner(A.chunk_base, nb, c);
+        const SahTask tk = in[i];
+        const int pick_a = ax[i].pick_a, pick_b = ax[i].pick_b, mid = ax[i].mid;
+        const float ka = pick_a == 0 ? ax[i].k[0] : (pick_a == 1 ? ax[i].k[1] : ax[i].k[2]);
+        const int first = tk.lo + (c - A.chunk_base[i]) * SAH_CHUNK;
+        const int end = min(tk.hi, first + SAH_CHUNK);
+        const int loff = A.loff[c];
+        const int roff = (first - tk.lo) - loff;
+        float lcl[3] = {INFINITY, INFINITY, INFINITY}, lch[3] = {-INFINITY, -INFINITY, -INFINITY};
+        float rcl[3] = {INFINITY, INFINITY, INFINITY}, rch[3] = {-INFINITY, -INFINITY, -INFINITY};
+        partition_positions<SAH_BLOCK>(A, src, dst, first, end, threadIdx.x, pick_a, pick_b, sel3(tk.cl, pick_a), ka,
+                                       mid, tk.lo + loff, mid + roff, lcl, lch, rcl, rch, wcnt);
+        g_minmax3<SAH_BLOCK>(lcl, lch, red);
+        g_minmax3<SAH_BLOCK>(rcl, rch, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                atomicMin(&ax[i].ccb[0][a], f2o(lcl[a]));
+                atomicMax(&ax[i].ccb[0][3 + a], f2o(lch[a]));
+                atomicMin(&ax[i].ccb[1][a], f2o(rcl[a]));
+                atomicMax(&ax[i].ccb[1][3 + a], f2o(rch[a]));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Morton key of each triangle at its final position: keys by triangle id
+// (scattered from the sorted pairs), then gathered through the final order.
+__global__ void k_keys_by_tri(const uint64_t* __restrict__ ks, const int32_t* __restrict__ vs, int64_t n,
+                              uint64_t* __restrict__ by_tri) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) by_tri[vs[p]] = ks[p];
+}
+__global__ void k_keys_gather(const uint64_t* __restrict__ by_tri, const int32_t* __restrict__ order, int64_t n,
+                              uint64_t* __restrict__ keys) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) keys[p] = by_tri[order[p]];
+}
+
 // ---------------- the whole build of a small mesh in one block ----------------
 // For meshes of at most SMALL_SORT triangles the steps above (boxes, scene
 // bounds, large-triangle flags, centroid bounds, Morton codes, sort, Karras
@@ -650,12 +1321,13 @@ cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t n
     return cudaGetLastError();
 }
 
-cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host) {
+cudaError_t build_bvh(const BvhBuffers& B, int builder, cudaStream_t s, int32_t* nlarge_host) {
     const int64_t n = B.nt;
     *nlarge_host = 0;
     if (n <= 0) return cudaSuccess;
     cudaError_t err;
-    if (n <= SMALL_SORT) {
+    const bool sah = builder == BVH_SAH;
+    if (n <= SMALL_SORT && !sah) {
         // one launch: the count goes through a 4-byte scratch word
         int32_t* cnt = nullptr;
         if ((err = lib_malloc_async((void**)&cnt, sizeof(int32_t), s)) != cudaSuccess) return err;
@@ -685,6 +1357,23 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host)
                  o_pl = take(sizeof(int32_t) * n), o_pn = take(sizeof(int32_t) * n),
                  o_vis = take(sizeof(int32_t) * n), o_sb = take(sizeof(float) * 6),
                  o_lg = take(sizeof(int8_t) * n), o_cnt = take(sizeof(int32_t));
+    // SAH: task lists by level parity, tasks per level, the root's split, an error word;
+    // the big ranges' bins, plans, chunk histograms and chunk offsets
+    int levels = SAH_DEPTH_CAP + 2;
+    for (int64_t m = 1; m < n; m <<= 1) ++levels;
+    const int32_t cap_small = (int32_t)(n / 2 + 1), cap_big = (int32_t)(n / SAH_BIG + 2);
+    const int32_t cap_chunks = (int32_t)(n / SAH_CHUNK + cap_big + 1);
+    size_t o_tb = 0, o_ts = 0, o_tc = 0, o_bins = 0, o_aux = 0, o_cb = 0, o_hist = 0, o_loff = 0;
+    if (sah) {
+        o_tb = take(sizeof(SahTask) * 2 * (size_t)cap_big);
+        o_ts = take(sizeof(SahTask) * 2 * (size_t)cap_small);
+        o_tc = take(sizeof(int32_t) * (2 * (size_t)(levels + 2) + 2));
+        o_bins = take(sizeof(int32_t) * SAH_NB3 * 7 * (size_t)cap_big);
+        o_aux = take(sizeof(SahAux) * 2 * (size_t)cap_big);
+        o_cb = take(sizeof(int32_t) * ((size_t)cap_big + 1));
+        o_hist = take(sizeof(int32_t) * SAH_NB3 * (size_t)cap_chunks);
+        o_loff = take(sizeof(int32_t) * (size_t)cap_chunks);
+    }
     char* base = nullptr;
     if ((err = lib_malloc_async((void**)&base, off, s)) != cudaSuccess) return err;
     // every later error still returns the scratch block to the pool
@@ -731,10 +1420,64 @@ cudaError_t build_bvh(const BvhBuffers& B, cudaStream_t s, int32_t* nlarge_host)
     }
     if ((err = cudaMemcpyAsync(B.order, v1, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return fail_free(err);
-    if (n >= 2) {
+    if (n >= 2 && !sah) {
         k_karras<<<nb(n - 1, 256), 256, 0, s>>>(k1, n, cnt, B.nodes, pl, pn);
         if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * n, s)) != cudaSuccess) return fail_free(err);
         k_refit<<<nb(n, 256), 256, 0, s>>>(aabb, B.order, n, cnt, pl, pn, B.nodes, vis);
+    }
+    if (n >= 2 && sah) {
+        SahArgs A;
+        A.c2 = c2;
+        A.aabb = aabb;
+        A.buf[0] = v1;         // the Morton order (B.order holds a copy, large triangles included)
+        A.buf[1] = v2;         // free after the sort
+        A.order = B.order;
+        A.nodes = B.nodes;
+        A.parent_leaf = pl;
+        A.parent_node = pn;
+        SahTask* tb = (SahTask*)(base + o_tb);
+        SahTask* ts = (SahTask*)(base + o_ts);
+        A.big[0] = tb;
+        A.big[1] = tb + cap_big;
+        A.small[0] = ts;
+        A.small[1] = ts + cap_small;
+        int32_t* tc = (int32_t*)(base + o_tc);
+        A.cnt_big = tc;
+        A.cnt_small = tc + (levels + 2);
+        A.groot = tc + 2 * (levels + 2);
+        A.err = A.groot + 1;
+        A.cap_big = cap_big;
+        A.cap_small = cap_small;
+        A.cap_chunks = cap_chunks;
+        A.bins = (int32_t*)(base + o_bins);
+        SahAux* aux = (SahAux*)(base + o_aux);
+        A.aux[0] = aux;
+        A.aux[1] = aux + cap_big;
+        A.chunk_base = (int32_t*)(base + o_cb);
+        A.hist = (int32_t*)(base + o_hist);
+        A.loff = (int32_t*)(base + o_loff);
+        if ((err = cudaMemsetAsync(tc, 0, sizeof(int32_t) * (2 * (size_t)(levels + 2) + 2), s)) != cudaSuccess)
+            return fail_free(err);
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int gb = (int)std::min<int64_t>(cap_chunks, 2 * (int64_t)sms);
+        const int gd = (int)std::min<int64_t>((cap_big + SAH_WARPS - 1) / SAH_WARPS, 4 * (int64_t)sms);
+        const int gs = (int)std::min<int64_t>((cap_small + SAH_WARPS - 1) / SAH_WARPS, 8 * (int64_t)sms);
+        // keys by triangle id while v1 still holds the Morton order
+        k_keys_by_tri<<<nb(n, 256), 256, 0, s>>>(k1, v1, n, k2);
+        k_sah_root<<<1, 1, 0, s>>>(A, cnt, n, bnd);
+        // no leaf is deeper than SAH_DEPTH_CAP + ceil(log2 n): later levels are empty
+        for (int level = 0; level < levels; ++level) {
+            k_sah_plan<<<1, SAH_PLAN, 0, s>>>(A, level);
+            k_sah_bin<<<gb, SAH_BLOCK, 0, s>>>(A, level);
+            k_sah_decide<<<gd, 32 * SAH_WARPS, 0, s>>>(A, level);
+            k_sah_scatter<<<gb, SAH_BLOCK, 0, s>>>(A, level);
+            k_sah_small<<<gs, 32 * SAH_WARPS, 0, s>>>(A, level);
+        }
+        k_sah_plan<<<1, SAH_PLAN, 0, s>>>(A, levels);   // the nodes of the last level's big ranges
+        if ((err = cudaMemsetAsync(vis, 0, sizeof(int32_t) * n, s)) != cudaSuccess) return fail_free(err);
+        k_refit<<<nb(n, 256), 256, 0, s>>>(aabb, B.order, n, cnt, pl, pn, B.nodes, vis);
+        k_keys_gather<<<nb(n, 256), 256, 0, s>>>(k2, B.order, n, k1);
     }
     k_trirec<<<nb(n, 256), 256, 0, s>>>(B.verts, B.tris, B.tri_mat, B.order, n, B.trirec);
     if ((err = cudaGetLastError()) != cudaSuccess) return fail_free(err);

@@ -184,9 +184,12 @@ struct BvhBuffers {
 };
 // at most this many large triangles are kept out of the tree (tested from a list)
 constexpr int MAX_LARGE_TRIS = 16;
+// tree builders (rm_bvh_build_ex): the Karras LBVH or the binned-SAH tree over the same leaves
+constexpr int BVH_LBVH = 1;
+constexpr int BVH_SAH = 2;
 // Enqueues the build on s; *large_count_host receives the number of large
 // triangles (the list is used when it is 1..MAX_LARGE_TRIS) once s reaches it.
-cudaError_t build_bvh(const BvhBuffers& b, cudaStream_t s, int32_t* large_count_host);
+cudaError_t build_bvh(const BvhBuffers& b, int builder, cudaStream_t s, int32_t* large_count_host);
 cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t nt, int64_t nv, int32_t nm,
                           int32_t* flag_dev, cudaStream_t s);
 

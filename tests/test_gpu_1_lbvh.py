@@ -1,5 +1,6 @@
-"""GPU LBVH == oracle LBVH, bit for bit (sorted keys, order, children and
-child boxes as raw FP32 bits)."""
+"""GPU trees == oracle trees, bit for bit (keys, order, children and child
+boxes as raw FP32 bits), for both builders: the Karras LBVH and the
+binned-SAH tree over the same leaves."""
 import numpy as np
 import pytest
 
@@ -31,9 +32,10 @@ SCENES = {
 }
 
 
-def _compare(orc, api, sc):
-    ref = orc.lbvh(sc)
-    gs = api.Scene.from_obj(sc)
+def _compare(orc, api, sc, builder="lbvh"):
+    ref = orc.lbvh(sc) if builder == "lbvh" else orc.sah_bvh(sc)
+    gs = api.Scene.from_obj(sc, builder=builder)
+    assert gs.info()["builder"] == builder or sc.nt == 0
     got = gs.export_bvh()
     assert np.array_equal(got["keys"], ref["keys"])
     assert np.array_equal(got["order"], ref["order"])
@@ -43,13 +45,65 @@ def _compare(orc, api, sc):
     gs.free()
 
 
+@pytest.mark.parametrize("builder", ["lbvh", "sah"])
 @pytest.mark.parametrize("name", list(SCENES))
-def test_lbvh_bit_exact(orc, api, name):
-    _compare(orc, api, SCENES[name]())
+def test_tree_bit_exact(orc, api, name, builder):
+    _compare(orc, api, SCENES[name](), builder)
 
 
-def test_lbvh_bit_exact_million_triangle_city(orc, api):
-    _compare(orc, api, S.procedural_city(5))
+@pytest.mark.parametrize("builder", ["lbvh", "sah"])
+def test_tree_bit_exact_million_triangle_city(orc, api, builder):
+    _compare(orc, api, S.procedural_city(5), builder)
+
+
+def test_sah_tree_bit_exact_deep_and_degenerate(orc, api):
+    """Nested growing triangles reach the SAH's depth cap (middle splits below
+    it); a soup with many coincident centroids takes middle splits too."""
+    n = 42
+    s8 = [np.float32(8.0 ** i) for i in range(n)]
+    v = np.array([p for x in s8 for p in ((0, 0, 0), (x, 0, 0), (0, x, x))], np.float32)
+    nested = S.Scene("nested", v, np.arange(3 * n, dtype=np.int32).reshape(n, 3), np.zeros(n, np.int32),
+                     np.array([S.GROUND], np.float32))
+    _compare(orc, api, nested, "sah")
+    rng = np.random.default_rng(11)
+    c = rng.integers(0, 5, (3000, 3)).astype(np.float32) * 10     # 125 distinct centroids
+    vv = np.concatenate([c, c + [1, 0, 0], c + [0, 1, 0]]).astype(np.float32)
+    tt = np.stack([np.arange(3000), np.arange(3000) + 3000, np.arange(3000) + 6000], 1).astype(np.int32)
+    _compare(orc, api, S.Scene("coincident", vv, tt, np.zeros(3000, np.int32), np.array([S.GROUND], np.float32)),
+             "sah")
+
+
+def test_auto_builder(api):
+    """RM_BVH_AUTO: the SAH tree above 2048 triangles, the one-block LBVH below."""
+    small = api.Scene.from_obj(S.manhattan(2, 3))
+    big = api.Scene.from_obj(S.procedural_city(5, ncells=30))
+    assert small.info()["builder"] == "lbvh" and big.info()["builder"] == "sah"
+    small.free()
+    big.free()
+
+
+def test_sah_and_lbvh_trace_the_same_paths(api):
+    """The two trees hold the same triangles, so a trace takes the same closest
+    hits through either, except where two triangles are hit at exactly the same
+    distance (the first one found wins): nearly every ray's record is equal."""
+    import torch
+    sc, txs, p = S.workload(5)
+    tx = txs[5]
+    tx.ray_stride, tx.ray_begin = 997, 3
+    recs, maps = [], []
+    for b in ("lbvh", "sah"):
+        gs = api.Scene.from_obj(sc, builder=b)
+        r = api.trace(gs, [tx], p, record=True)
+        recs.append(r["record"].view(tx.count(), p.max_depth + 1, 4).cpu().numpy())
+        maps.append(r["maps"][0])
+        gs.free()
+    same = (recs[0] == recs[1]).all(axis=(1, 2))
+    assert tx.count() > 90_000
+    assert same.mean() > 0.999, same.mean()
+    # the maps then differ only by the few differing rays' deposits
+    m0, m1 = maps
+    big = m0 > 1e-15
+    assert torch.quantile((m1[big] - m0[big]).abs() / m0[big], 0.99) < 1e-3
 
 
 def test_empty_scene_builds(api):

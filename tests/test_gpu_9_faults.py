@@ -107,7 +107,7 @@ def test_traversal_stack_overflow_is_reported(orc, api):
     sc, tx, p = _small()
     gs = api.Scene.from_obj(sc)
     ref = api.trace(gs, [tx], p)["maps"].clone()
-    gd = api.Scene.from_obj(deep)
+    gd = api.Scene.from_obj(deep, builder="lbvh")   # the chain is the LBVH's
     tdeep = S.Tx(pos=(1.0, 2.0, 3.0), num_rays=2000, seed=3)
     pdeep = S.TraceParams(3.5e9, 2, cell_size=1.0, nx=8, ny=8, map_origin=(0.0, 0.0, 0.0))
     with pytest.raises(api.RmError) as e:
