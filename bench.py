@@ -55,7 +55,7 @@ WORKLOADS = {
 PROFILES = {5: "k_trace_city.md", 2: "k_trace_manhattan_1e7.md", 3: "k_trace_batched.md",
             4: "k_trace_adjoint_differentiable.md", "city_adjoint": "k_trace_adjoint_city.md",
             "diffuse": "k_trace_diffuse_manhattan.md"}
-# the tracer's code and the tree it walks (the LBVH build decides its node visits)
+# the tracer's code and the tree it walks (the BVH builders decide its node visits)
 TRACE_SOURCES = [os.path.join(ROOT, "paper_2504_21719_b300", "csrc", f) for f in ("trace.cu", "common.cuh", "array.cuh", "bvh.cu")]
 
 
@@ -291,7 +291,8 @@ def time_plan(torch, plan, steps, warmup, flush, clocks=None):
 
 def e2e_host(api, torch, sc, txs, prm, out, steps, warmup, flush, breakdown=0):
     """End to end through the public API from pinned host arrays: scene upload,
-    LBVH build, trace and the read-back of the maps, every step.  With
+    BVH build (the default builder: binned SAH above 2048 triangles), trace and
+    the read-back of the maps, every step.  With
     `breakdown` > 0, that many more steps time each part alone (synchronised
     after each)."""
     vh = torch.from_numpy(sc.verts).pin_memory()
@@ -315,7 +316,7 @@ def e2e_host(api, torch, sc, txs, prm, out, steps, warmup, flush, breakdown=0):
     h2d = sc.verts.nbytes + sc.tris.nbytes + sc.tri_mat.nbytes + sc.mats.nbytes + 72 * len(txs) + 56
     res = {"value": sum(e_segs) / (sum(e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(out_h.numel() * 4 + 576), "ms_per_step": round(statistics.mean(e_ms), 3),
-           "includes": "scene upload + LBVH build + trace + map readback, per step"}
+           "includes": "scene upload + BVH build (binned SAH) + trace + map readback, per step"}
     if breakdown:
         parts = {"upload": [], "build": [], "trace_call": [], "trace_kernel": [], "readback": []}
         for i in range(warmup + breakdown):

@@ -318,7 +318,7 @@ def grad_mesh(scene: Scene, surface: Scene, txs, params, dLdC: torch.Tensor, sam
 
 
 def surface(verts, tris, device="cuda", stream=None) -> Scene:
-    """A mesh measurement surface: the triangles uploaded with their LBVH (one dummy material)."""
+    """A mesh measurement surface: the triangles uploaded with their BVH (default builder; one dummy material)."""
     t = np.asarray(tris, np.int32).reshape(-1, 3)
     return Scene(verts, t, np.zeros(len(t), np.int32), np.array([[1.0, 0.0, 0.0]], np.float32), device=device,
                  stream=stream)
