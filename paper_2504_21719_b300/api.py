@@ -317,11 +317,11 @@ def grad_mesh(scene: Scene, surface: Scene, txs, params, dLdC: torch.Tensor, sam
     return out
 
 
-def surface(verts, tris, device="cuda", stream=None) -> Scene:
-    """A mesh measurement surface: the triangles uploaded with their BVH (default builder; one dummy material)."""
+def surface(verts, tris, device="cuda", stream=None, builder="auto") -> Scene:
+    """A mesh measurement surface: the triangles uploaded with their BVH (one dummy material)."""
     t = np.asarray(tris, np.int32).reshape(-1, 3)
     return Scene(verts, t, np.zeros(len(t), np.int32), np.array([[1.0, 0.0, 0.0]], np.float32), device=device,
-                 stream=stream)
+                 stream=stream, builder=builder)
 
 
 def diffraction_map(scene: Scene, txs, params, samples_per_wedge: int, wedges=None, record=False, stream=None,

@@ -30,8 +30,8 @@ def _manhattan(stride=97):
     return _diffuse(sc), tx, p
 
 
-def _run(api, sc, tx, p):
-    gs = api.Scene.from_obj(sc)
+def _run(api, sc, tx, p, builder="auto"):
+    gs = api.Scene.from_obj(sc, builder=builder)
     r = api.trace(gs, [tx], coin(p), record=True)
     torch.cuda.synchronize()
     out = (r["maps"][0].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
@@ -39,9 +39,11 @@ def _run(api, sc, tx, p):
     return out
 
 
-def test_diffuse_map_parity(orc, api):
+@pytest.mark.parametrize("builder", ["auto", "sah"])
+def test_diffuse_map_parity(orc, api, builder):
+    """builder "sah": the diffuse tracer's single-site traversal on the binned-SAH tree."""
     sc, tx, p = _manhattan()
-    m, rec, st = _run(api, sc, tx, p)
+    m, rec, st = _run(api, sc, tx, p, builder)
     dec = rec[:, 3]
     assert ((dec >= 0) & (dec & 3 == 2)).sum() > 1000
     compare_maps(orc, sc, tx, p, m, rec)

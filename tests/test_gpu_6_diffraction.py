@@ -28,8 +28,8 @@ def test_wedges_match_oracle(orc, api, scene):
     gs.free()
 
 
-def _run(api, sc, tx, p, ns):
-    gs = api.Scene.from_obj(sc)
+def _run(api, sc, tx, p, ns, builder="auto"):
+    gs = api.Scene.from_obj(sc, builder=builder)
     r = api.diffraction_map(gs, [tx], p, ns, record=True)
     torch.cuda.synchronize()
     out = (r["maps"][0].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
@@ -46,15 +46,16 @@ def test_diffraction_parity_single_box(orc, api):
     compare_diffraction(orc, sc, tx, p, 4096, m, rec)
 
 
-@pytest.mark.parametrize("pol,pattern,deposit", [(0, 0, 0), (2, 1, 1)])
-def test_diffraction_parity_manhattan(orc, api, pol, pattern, deposit):
+@pytest.mark.parametrize("pol,pattern,deposit,builder", [(0, 0, 0, "auto"), (2, 1, 1, "auto"), (0, 0, 1, "sah")])
+def test_diffraction_parity_manhattan(orc, api, pol, pattern, deposit, builder):
+    """builder "sah": the visibility queries walk the binned-SAH tree of the scene."""
     sc, txs, p = S.workload(2)
     p.nx = p.ny = 256
     p.cell_size = 2.0
     p.deposit = deposit
     tx = txs[0]
     tx.pol, tx.pattern = pol, pattern
-    m, rec, st = _run(api, sc, tx, p, 256)
+    m, rec, st = _run(api, sc, tx, p, 256, builder)
     assert st["deposits"] > 5000
     compare_diffraction(orc, sc, tx, p, 256, m, rec)
 

@@ -19,9 +19,9 @@ def terrain(n=32, half=64.0):
                         lambda X, Y: 1.5 + 0.5 * np.sin(X / 9.0) * np.cos(Y / 7.0))
 
 
-def _run(api, sc, surf_v, surf_t, txs, p):
-    gs = api.Scene.from_obj(sc)
-    su = api.surface(surf_v, surf_t)
+def _run(api, sc, surf_v, surf_t, txs, p, builder="auto"):
+    gs = api.Scene.from_obj(sc, builder=builder)
+    su = api.surface(surf_v, surf_t, builder=builder)
     r = api.trace_mesh(gs, su, txs, coin(p), record=True)
     torch.cuda.synchronize()
     out = (r["maps"].cpu().numpy(), r["record"].cpu().numpy(), r["stats"])
@@ -30,13 +30,14 @@ def _run(api, sc, surf_v, surf_t, txs, p):
     return out
 
 
-@pytest.mark.parametrize("stride,begin", [(997, 0), (1009, 5)])
-def test_mesh_parity_manhattan(orc, api, stride, begin):
+@pytest.mark.parametrize("stride,begin,builder", [(997, 0, "auto"), (1009, 5, "sah")])
+def test_mesh_parity_manhattan(orc, api, stride, begin, builder):
+    """builder "sah": the scene and the surface both walk binned-SAH trees."""
     sc, txs, p = S.workload(2)
     tx = txs[0]
     tx.ray_stride, tx.ray_begin = stride, begin
     V, T = terrain()
-    m, rec, st = _run(api, sc, V, T, [tx], p)
+    m, rec, st = _run(api, sc, V, T, [tx], p, builder)
     assert st["rays"] == tx.count() and st["deposits"] > 1000
     info = compare_mesh(orc, sc, tx, p, V, T, m[0], rec)
     assert info["cells"] > 1000
