@@ -131,7 +131,7 @@ def main(argv=None):
     for key, (sc, txs, p, adj) in jobs.items():
         if only and key not in only:
             continue
-        gs = api.Scene.from_obj(sc)
+        gs = api.Scene.from_obj(sc, builder="sah" if key == "batched" else "auto")   # the benchmark's trees
         best, res, dflt = tune(api, gs, txs, p, adjoint=adj)
         entry[key] = {**best, "default_kernel_ms": dflt, "gain_over_default": round(dflt / best["kernel_ms"], 4),
                       "candidates": len(res)}

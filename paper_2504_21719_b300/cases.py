@@ -9,8 +9,9 @@ CASE is one of
   diffraction  first-order diffraction map, Manhattan, 1200 wedges
   city         forward trace, 0.97M-triangle procedural city, 1 TX, 1e7 rays, depth 8
   city_adjoint forward then adjoint (uniform dL/dC) of the same city trace
-  batched      the 64-TX batched workload (depth 3) in one launch; --rays sets the
-               lattice stride of every transmitter (default 1: the full workload)
+  batched      the 64-TX batched workload (depth 3) in one launch on the binned-SAH tree
+               (as the benchmark); --rays sets the lattice stride of every transmitter
+               (default 1: the full workload)
   mesh         the Manhattan trace on a 131072-triangle terrain measurement surface
 Each case runs in the launch shape the tuning table holds for its workload
 class on this GPU (the benchmark's shape) and prints one line: case, kernel
@@ -59,7 +60,8 @@ def main(argv=None):
            "city": "city", "city_adjoint": "city_adjoint", "batched": "batched", "mesh": "manhattan"}[a.case]
     blk, bps, qch, rfm = lookup(torch.cuda.get_device_name(0), cls)
     p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
-    gs = api.Scene.from_obj(sc, builder=a.builder)
+    builder = "sah" if (a.case == "batched" and a.builder == "auto") else a.builder
+    gs = api.Scene.from_obj(sc, builder=builder)
     su = api.surface(*S.terrain_surface(256.0, 256)) if a.case == "mesh" else None
     for _ in range(a.reps):
         if a.case == "mesh":
