@@ -73,6 +73,22 @@ def test_sah_tree_bit_exact_deep_and_degenerate(orc, api):
              "sah")
 
 
+def test_builder_argument_is_checked(api):
+    """An unknown builder is RM_EINVAL before any device work; the scene can
+    still be built afterwards, and a second build is RM_ESTATE."""
+    import ctypes as C
+    from paper_2504_21719_b300 import _lib as L
+    gs = api.Scene.from_obj(S.manhattan(2, 3), build=False)
+    lib = L.load()
+    assert lib.rm_bvh_build_ex(gs.handle, 7, None) == L.RM_EINVAL
+    assert b"builder" in lib.rm_last_error()
+    assert gs.info()["builder"] is None
+    assert lib.rm_bvh_build_ex(gs.handle, 2, None) == L.RM_OK
+    assert gs.info()["builder"] == "sah"
+    assert lib.rm_bvh_build_ex(gs.handle, 1, None) == L.RM_ESTATE
+    gs.free()
+
+
 def test_auto_builder(api):
     """RM_BVH_AUTO: the SAH tree above 2048 triangles, the one-block LBVH below."""
     small = api.Scene.from_obj(S.manhattan(2, 3))
