@@ -330,6 +330,37 @@ rm_status rm_radio_map_grad(const rm_scene* scene, const rm_tx* tx_host, int32_t
                             const rm_material* sampling_host_or_null, rm_stats* stats_host_or_null,
                             rm_segment_record* record_dev_or_null, void* stream);
 
+/* Forward trace that also records, for the adjoint, the closest hit of every
+ * segment: hits_dev[rec] = the leaf slot hit (a position in the scene's tree
+ * order, -1 if the segment escaped), at the debug record's index rec =
+ * (first item of the transmitter + i) (max_depth + 1) + l (see
+ * rm_radio_map_trace).  hits_dev: device int32 owned by the caller, at least
+ * hits_len >= (sum of the transmitters' ray counts) x (max_depth + 1) entries
+ * (RM_EINVAL otherwise); slots of depths a ray does not reach are not
+ * written.  The maps and counters are those of rm_radio_map_trace; the call
+ * runs the statistics instantiation of the tracer (1-2 % slower than the plain
+ * one).  Synchronises `stream`. */
+rm_status rm_radio_map_trace_hits(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
+                                  const rm_trace_params* params, float* maps_dev, int32_t* hits_dev,
+                                  uint64_t hits_len, rm_stats* stats_host_or_null, void* stream);
+
+/* rm_radio_map_grad replaying recorded hits: hits_dev from
+ * rm_radio_map_trace_hits with the same scene, transmitters and params.  At
+ * every segment the adjoint tests only the recorded leaf (the same watertight
+ * test, so the same distance bit for bit) instead of traversing the BVH; an
+ * entry of -1 is an escape.  An entry outside the scene, or a leaf the ray
+ * misses, falls back to the traversal, so no access leaves the scene; a
+ * buffer recorded with other arguments gives gradients of other paths.  With
+ * the matching buffer the gradients equal rm_radio_map_grad's up to the order
+ * of their atomic sums.  hits_len as above (RM_EINVAL if short); otherwise as
+ * rm_radio_map_grad. */
+rm_status rm_radio_map_grad_hits(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
+                                 const rm_trace_params* params, const float* dL_dmaps_dev,
+                                 const int32_t* hits_dev, uint64_t hits_len, float* d_eps_dev,
+                                 float* d_sigma_dev, float* d_txpos_dev,
+                                 const rm_material* sampling_host_or_null, rm_stats* stats_host_or_null,
+                                 rm_segment_record* record_dev_or_null, void* stream);
+
 /* rm_radio_map_grad for maps on a mesh measurement surface (see
  * rm_radio_map_trace_mesh): dL_dmaps_dev [ntx][surface triangles].  The cells
  * are boxes, so d_txpos stays 0.  deposit must be 0; otherwise as

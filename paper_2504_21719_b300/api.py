@@ -229,12 +229,22 @@ class Scene:
             pass
 
 
-def trace(scene: Scene, txs, params, record=False, stream=None, out=None):
-    """Radio maps [ntx, ny, nx] (float32, cuda) and the counters; optionally the per-segment record."""
+def trace(scene: Scene, txs, params, record=False, stream=None, out=None, keep_hits=False):
+    """Radio maps [ntx, ny, nx] (float32, cuda) and the counters; optionally the per-segment
+    record, or (keep_hits) every segment's closest-hit leaf slot for grad(..., hits=...)."""
     lib = L.load()
     arr, ntx = _tx_array(txs)
     p = params if isinstance(params, L.rm_trace_params) else params_from(params)
     maps = out if out is not None else torch.empty((ntx, p.ny, p.nx), dtype=torch.float32, device="cuda")
+    if keep_hits:
+        if record:
+            raise ValueError("keep_hits and record are separate calls")
+        nh = sum(tx_count(arr[i]) for i in range(ntx)) * (p.max_depth + 1)
+        hits = torch.empty(max(nh, 1), dtype=torch.int32, device="cuda")
+        st = L.rm_stats()
+        _check(lib.rm_radio_map_trace_hits(scene.handle, arr, ntx, C.byref(p), _ptr(maps), _ptr(hits), nh,
+                                           C.byref(st), _stream(stream)), "rm_radio_map_trace_hits")
+        return {"maps": maps, "stats": st.as_dict(), "hits": hits}
     rec = None
     if record:
         nrec = sum(tx_count(arr[i]) for i in range(ntx)) * (p.max_depth + 1)
@@ -345,8 +355,10 @@ def diffraction_map(scene: Scene, txs, params, samples_per_wedge: int, wedges=No
     return res
 
 
-def grad(scene: Scene, txs, params, dLdC: torch.Tensor, sampling=None, record=False, stream=None):
-    """(d_eps [nm], d_sigma [nm], d_txpos [ntx, 3]) of sum(dLdC * maps), choices frozen, q detached."""
+def grad(scene: Scene, txs, params, dLdC: torch.Tensor, sampling=None, record=False, stream=None, hits=None):
+    """(d_eps [nm], d_sigma [nm], d_txpos [ntx, 3]) of sum(dLdC * maps), choices frozen, q detached.
+    hits: trace(..., keep_hits=True)["hits"] of the same scene, transmitters and params: the
+    adjoint then replays the recorded closest hits instead of traversing the BVH."""
     lib = L.load()
     arr, ntx = _tx_array(txs)
     p = params if isinstance(params, L.rm_trace_params) else params_from(params)
@@ -360,8 +372,13 @@ def grad(scene: Scene, txs, params, dLdC: torch.Tensor, sampling=None, record=Fa
         rec = torch.empty((max(nrec, 1), 4), dtype=torch.int32, device="cuda")
     st = L.rm_stats()
     g = dLdC.contiguous()
-    _check(lib.rm_radio_map_grad(scene.handle, arr, ntx, C.byref(p), _ptr(g), _ptr(d_eps), _ptr(d_sig), _ptr(d_tx),
-                                 sm, C.byref(st), _ptr(rec), _stream(stream)), "rm_radio_map_grad")
+    if hits is not None:
+        _check(lib.rm_radio_map_grad_hits(scene.handle, arr, ntx, C.byref(p), _ptr(g), _ptr(hits), hits.numel(),
+                                          _ptr(d_eps), _ptr(d_sig), _ptr(d_tx), sm, C.byref(st), _ptr(rec),
+                                          _stream(stream)), "rm_radio_map_grad_hits")
+    else:
+        _check(lib.rm_radio_map_grad(scene.handle, arr, ntx, C.byref(p), _ptr(g), _ptr(d_eps), _ptr(d_sig),
+                                     _ptr(d_tx), sm, C.byref(st), _ptr(rec), _stream(stream)), "rm_radio_map_grad")
     out = {"d_eps": d_eps, "d_sigma": d_sig, "d_tx": d_tx, "stats": st.as_dict()}
     if record:
         out["record"] = rec

@@ -673,7 +673,7 @@ size_t write_tables(const Prepared& P, size_t o_mat, size_t o_tx, char* h) {
 rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p, float* maps,
                     const float* dLdC, float* d_eps, float* d_sig, float* d_tx, const rm_material* smats,
                     rm_stats* stats, rm_segment_record* record, void* stream, bool adjoint,
-                    const rm_scene* surf = nullptr) {
+                    const rm_scene* surf = nullptr, int32_t* hits = nullptr, uint64_t hits_len = 0) {
     rm_status st = validate(sc, tx, ntx, p);
     if (st != RM_OK) return st;
     if ((st = check_device(sc)) != RM_OK) return st;
@@ -699,7 +699,13 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
                                   ": injected launch failure (nothing was enqueued)");
     Prepared P;
     prepare(sc, tx, ntx, p, smats, &P, surf);
-    const bool debug = record != nullptr || (p->flags & RM_STATS);
+    if (hits) {
+        unsigned long long need = 0;
+        for (const TxDev& t : P.tx) need += t.count * (unsigned long long)(p->max_depth + 1);
+        if (hits_len < need) return fail(RM_EINVAL, "hits_len is below the segments' count (rays x (max_depth + 1))");
+    }
+    // the forward that records its hits runs in the debug instantiation (the plain tracer stays as it is)
+    const bool debug = record != nullptr || (p->flags & RM_STATS) || (hits && !adjoint);
     size_t o_mat, o_tx, o_m64 = 0;
     const size_t bytes = adjoint ? table_bytes(P, &o_mat, &o_tx) : block_bytes_with_maps64(P, &o_mat, &o_tx, &o_m64);
     cudaEvent_t ev[2];
@@ -728,6 +734,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         P.a.maps64 = adjoint ? nullptr : reinterpret_cast<double*>(dev + o_m64);
         P.a.dLdC = dLdC;
         P.a.record = record;
+        P.a.hits = hits;
         if (P.a.total > 0) {
             if ((e = cudaEventRecord(ev[0], S(stream))) != cudaSuccess) break;
             if ((e = launch_trace(P.a, P.npol, debug, P.bilinear, adjoint, P.diffuse, P.block, P.bps, S(stream), &grid,
@@ -1012,6 +1019,26 @@ rm_status rm_radio_map_grad(const rm_scene* sc, const rm_tx* tx, int32_t ntx, co
                             void* stream) {
     return run_trace(sc, tx, ntx, p, nullptr, dL_dmaps_dev, d_eps_dev, d_sigma_dev, d_txpos_dev,
                      sampling_host_or_null, stats, record, stream, true);
+}
+
+rm_status rm_radio_map_trace_hits(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
+                                  float* maps_dev, int32_t* hits_dev, uint64_t hits_len, rm_stats* stats,
+                                  void* stream) {
+    if (!hits_dev) return fail(RM_EINVAL, "hits_dev is NULL");
+    return run_trace(sc, tx, ntx, p, maps_dev, nullptr, nullptr, nullptr, nullptr, nullptr, stats, nullptr, stream,
+                     false, nullptr, hits_dev, hits_len);
+}
+
+rm_status rm_radio_map_grad_hits(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
+                                 const float* dL_dmaps_dev, const int32_t* hits_dev, uint64_t hits_len,
+                                 float* d_eps_dev, float* d_sigma_dev, float* d_txpos_dev,
+                                 const rm_material* sampling_host_or_null, rm_stats* stats,
+                                 rm_segment_record* record, void* stream) {
+    if (!hits_dev) return fail(RM_EINVAL, "hits_dev is NULL");
+    // the adjoint only reads the buffer
+    return run_trace(sc, tx, ntx, p, nullptr, dL_dmaps_dev, d_eps_dev, d_sigma_dev, d_txpos_dev,
+                     sampling_host_or_null, stats, record, stream, true, nullptr, const_cast<int32_t*>(hits_dev),
+                     hits_len);
 }
 
 rm_status rm_radio_map_grad_mesh(const rm_scene* sc, const rm_scene* surface, const rm_tx* tx, int32_t ntx,

@@ -533,6 +533,60 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
     return h;
 }
 
+// The hit of one given leaf (the adjoint's replay of the forward's recorded
+// closest hit): closest_hit's watertight set-up and leaf test, expression for
+// expression and in the same translation unit, so that t equals the
+// forward's bit for bit.  Returns false if the test rejects the leaf (the
+// caller then traverses).
+__device__ __forceinline__ bool recorded_hit(const float4* __restrict__ tris, const Ray& r, int slot, Hit& h) {
+    const float ax = fabsf(r.kx), ay = fabsf(r.ky), az = fabsf(r.kz);
+    int kzi = (ay > ax) ? 1 : 0;
+    if (az > fmaxf(ax, ay)) kzi = 2;
+    int kxi = kzi == 2 ? 0 : kzi + 1;
+    int kyi = kxi == 2 ? 0 : kxi + 1;
+    const f3 k{r.kx, r.ky, r.kz};
+    const float dz = sel(k, kzi);
+    if (dz < 0.0f) {
+        const int t = kxi;
+        kxi = kyi;
+        kyi = t;
+    }
+    const float Sx = sel(k, kxi) / dz, Sy = sel(k, kyi) / dz, Sz = 1.0f / dz;
+    const f3 o{r.ox, r.oy, r.oz};
+    const float opx = sel(o, kxi), opy = sel(o, kyi), opz = sel(o, kzi);
+    const float4* tp = tris + 3 * (size_t)slot;
+    const float4 r0 = __ldg(tp), r1 = __ldg(tp + 1), r2 = __ldg(tp + 2);
+    const f3 va{r0.x, r0.y, r0.z}, vb{r0.w, r1.x, r1.y}, vc{r1.z, r1.w, r2.x};
+    const float Akx = sel(va, kxi) - opx, Aky = sel(va, kyi) - opy, Akz = sel(va, kzi) - opz;
+    const float Bkx = sel(vb, kxi) - opx, Bky = sel(vb, kyi) - opy, Bkz = sel(vb, kzi) - opz;
+    const float Ckx = sel(vc, kxi) - opx, Cky = sel(vc, kyi) - opy, Ckz = sel(vc, kzi) - opz;
+    const float Ax = Akx - Sx * Akz, Ay = Aky - Sy * Akz;
+    const float Bx = Bkx - Sx * Bkz, By = Bky - Sy * Bkz;
+    const float Cx = Ckx - Sx * Ckz, Cy = Cky - Sy * Ckz;
+    float U = Cx * By - Cy * Bx;
+    float V = Ax * Cy - Ay * Cx;
+    float W = Bx * Ay - By * Ax;
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    const bool neg = (U < 0.0f || V < 0.0f || W < 0.0f);
+    const bool pos = (U > 0.0f || V > 0.0f || W > 0.0f);
+    float det = U + V + W;
+    if ((neg && pos) || det == 0.0f) return false;
+    float T = U * (Sz * Akz) + V * (Sz * Bkz) + W * (Sz * Ckz);
+    if (det < 0.0f) {
+        T = -T;
+        det = -det;
+    }
+    if (!(T > 0.0f)) return false;
+    h.t = T / det;
+    h.slot = slot;
+    h.prim = __float_as_int(r2.z);
+    return true;
+}
+
 // ------------------------------------------------------------------ mesh measurement surface
 // Crossings of the open segment (1e-9, tmax) with a mesh measurement surface
 // (Sec. 4, practical notes): every crossed triangle is a cell and receives
@@ -805,7 +859,18 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
         // ---------------- closest hit ----------------
         Hit h{-1, 0x7fffffff, INFINITY};
         if (active) {
-            h = closest_hit<DIFF || ADJ, DEBUG>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris, overflow);
+            bool replayed = false;
+            if (ADJ && A.hits) {
+                // the forward's closest hit of this segment (-1: escaped), tested alone
+                const int s = A.hits[s_tx[txi].rec_begin + isub * (unsigned long long)(A.L + 1) + depth];
+                if (s == -1) replayed = true;
+                else if (s >= 0 && s < A.nt + A.nlarge) replayed = recorded_hit(A.tris, r, s, h);
+            }
+            if (!replayed)
+                h = closest_hit<DIFF || ADJ, DEBUG>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris,
+                                                    overflow);
+            if (DEBUG && !ADJ && A.hits)
+                A.hits[s_tx[txi].rec_begin + isub * (unsigned long long)(A.L + 1) + depth] = h.slot;
             ++c_seg;
             if (h.slot < 0) ++c_esc;
         }

@@ -1,0 +1,109 @@
+"""The adjoint that replays the forward's recorded closest hits
+(rm_radio_map_trace_hits, rm_radio_map_grad_hits) against the re-tracing
+adjoint: the same segment records, the same gradients up to the order of their
+atomic sums, no node visited; the recorded hits against the debug record; the
+length check and the fallback to the traversal."""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare_grads(a, b):
+    for key in ("d_eps", "d_sigma", "d_tx"):
+        x, y = a[key].double(), b[key].double()
+        scale = max(x.abs().max().item(), 1e-30)
+        assert torch.all((x - y).abs() <= 1e-5 * scale), (key, x, y)
+
+
+def _replay_equals_retrace(api, sc, tx, p, builder="auto"):
+    gs = api.Scene.from_obj(sc, builder=builder)
+    f = api.trace(gs, [tx], p, keep_hits=True)
+    # the recording forward runs the record's instantiation: the same maps bit for bit
+    fr = api.trace(gs, [tx], p, record=True)
+    assert torch.equal(f["maps"], fr["maps"])
+    # and the plain tracer's paths (its approximate divisions may round a few ulps apart)
+    plain = api.trace(gs, [tx], p)
+    assert f["stats"]["segments"] == plain["stats"]["segments"]
+    assert torch.allclose(f["maps"], plain["maps"], rtol=1e-5, atol=0)
+    g = (10.0 * torch.log10(f["maps"].clamp_min(1e-15)) + 150.0) * 1e-6
+    ref = api.grad(gs, [tx], p, g, record=True)
+    rep = api.grad(gs, [tx], p, g, record=True, hits=f["hits"])
+    assert torch.equal(ref["record"], rep["record"])
+    assert rep["stats"]["segments"] == ref["stats"]["segments"]
+    assert ref["stats"]["nodes_visited"] > 0 and rep["stats"]["nodes_visited"] == 0
+    _compare_grads(ref, rep)
+    assert ref["d_eps"].abs().max() > 0
+    gs.free()
+
+
+@pytest.mark.parametrize("deposit", [0, 1])
+def test_replay_equals_retrace_differentiable(api, deposit):
+    sc, txs, p = S.workload(4)
+    tx = txs[0]
+    tx.ray_stride = 7
+    p.deposit = deposit
+    _replay_equals_retrace(api, sc, tx, p)
+
+
+def test_replay_equals_retrace_diffuse(api):
+    sc, txs, p = S.workload(4)
+    sc = sc.with_scattering(0.4, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
+    tx = txs[0]
+    tx.ray_stride = 11
+    p.diffuse = True
+    _replay_equals_retrace(api, sc, tx, p)
+
+
+def test_replay_equals_retrace_city(api):
+    """The 0.97M-triangle city on its binned-SAH tree, depth 8, a 1e4-ray subset."""
+    sc, txs, p = S.workload(5)
+    tx = copy.copy(txs[2])
+    tx.ray_stride, tx.ray_begin = 9973, 5
+    _replay_equals_retrace(api, sc, tx, p)
+
+
+def test_hits_are_the_records_hits(api):
+    """hits[rec] is the leaf slot of the record's triangle (order[slot] = prim),
+    -1 where the record says escaped; depths a ray never reached are not written."""
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    tx.ray_stride = 97
+    gs = api.Scene.from_obj(sc)
+    h = api.trace(gs, [tx], p, keep_hits=True)["hits"].cpu().numpy()
+    rec = api.trace(gs, [tx], p, record=True)["record"].cpu().numpy()
+    order = gs.export_bvh()["order"]
+    prim = rec[:, 0]
+    reached = prim != -2
+    assert reached.sum() > 10000
+    assert np.array_equal(h[reached] == -1, prim[reached] == -1)
+    hit = reached & (prim >= 0)
+    assert np.array_equal(order[h[hit]], prim[hit])
+    gs.free()
+
+
+def test_short_or_foreign_hits(api):
+    """A buffer shorter than rays x (L + 1) is RM_EINVAL; slots outside the scene
+    fall back to the traversal, which gives the re-traced adjoint."""
+    from paper_2504_21719_b300 import _lib as L
+    sc, txs, p = S.workload(4)
+    tx = txs[0]
+    tx.ray_stride = 13
+    gs = api.Scene.from_obj(sc)
+    f = api.trace(gs, [tx], p, keep_hits=True)
+    g = torch.full_like(f["maps"], 1e-6)
+    with pytest.raises(api.RmError) as e:
+        api.grad(gs, [tx], p, g, hits=f["hits"][:-1])
+    assert e.value.status == L.RM_EINVAL
+    foreign = torch.full_like(f["hits"], 1 << 30)
+    ref = api.grad(gs, [tx], p, g, record=True)
+    rep = api.grad(gs, [tx], p, g, record=True, hits=foreign)
+    assert torch.equal(ref["record"], rep["record"])
+    assert rep["stats"]["nodes_visited"] == ref["stats"]["nodes_visited"] > 0
+    _compare_grads(ref, rep)
+    gs.free()
