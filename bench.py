@@ -54,6 +54,7 @@ WORKLOADS = {
 # the committed ncu summaries a roofline's `traffic` comes from, keyed by workload
 PROFILES = {5: "k_trace_city.md", 2: "k_trace_manhattan_1e7.md", 3: "k_trace_batched.md",
             4: "k_trace_adjoint_differentiable.md", "city_adjoint": "k_trace_adjoint_city.md",
+            "city_adjoint_replay": "k_trace_adjoint_city_replay.md",
             "diffuse": "k_trace_diffuse_manhattan.md"}
 # the tracer's code and the tree it walks (the BVH builders decide its node visits)
 TRACE_SOURCES = [os.path.join(ROOT, "paper_2504_21719_b300", "csrc", f) for f in ("trace.cu", "common.cuh", "array.cuh", "bvh.cu")]
@@ -457,11 +458,30 @@ def city_adjoint(api, S, torch, sc, txs, p, prm, prm_adj, gs, fwd_kernel_ms, fwd
         ak.append(a["stats"]["kernel_ms"])
         segs = a["stats"]["segments"]
     k = statistics.mean(ak)
-    return {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3), "segments": segs,
-            "fwd_kernel_ms": round(fwd_kernel_ms, 3), "fwd_plus_adj_over_fwd": round((fwd_kernel_ms + k) / fwd_kernel_ms, 3),
-            "loss_cells": int(valid), "parameters": "d loss / d(eps_r, sigma) of 8 materials",
-            "roofline": roofline("city_adjoint", "k_trace<adjoint> (re-traces the forward's rays)", segs, k,
-                                 "instruction issue", False)}
+    out = {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3), "segments": segs,
+           "fwd_kernel_ms": round(fwd_kernel_ms, 3), "fwd_plus_adj_over_fwd": round((fwd_kernel_ms + k) / fwd_kernel_ms, 3),
+           "loss_cells": int(valid), "parameters": "d loss / d(eps_r, sigma) of 8 materials",
+           "roofline": roofline("city_adjoint", "k_trace<adjoint> (re-traces the forward's rays)", segs, k,
+                                "instruction issue", False)}
+    # the same adjoint replaying the closest hits a recording forward kept (4 B per segment
+    # slot on the device): no BVH traversal in the adjoint
+    fr = api.trace(gs, txs, prm, keep_hits=True)
+    fk = fr["stats"]["kernel_ms"]
+    hits = fr["hits"]
+    del fr
+    api.grad(gs, txs, prm_adj, dL, hits=hits)      # warm-up
+    rk = []
+    for _ in range(reps):
+        a = api.grad(gs, txs, prm_adj, dL, hits=hits)
+        rk.append(a["stats"]["kernel_ms"])
+    r = statistics.mean(rk)
+    out["replay"] = {"value": round(segs / (r / 1e3), 1), "unit": UNIT, "kernel_ms": round(r, 3),
+                     "recording_fwd_kernel_ms": round(fk, 3), "hits_bytes": int(hits.numel()) * 4,
+                     "fwd_plus_adj_over_fwd": round((fk + r) / fwd_kernel_ms, 3),
+                     "roofline": roofline("city_adjoint_replay", "k_trace<adjoint> replaying recorded hits", segs, r,
+                                          "instruction issue", False)}
+    del hits
+    return out
 
 
 def _kernel_rate(api, gs, txs, prm, reps=5):

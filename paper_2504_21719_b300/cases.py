@@ -8,7 +8,8 @@ CASE is one of
   adjoint      adjoint of the differentiable workload (8 materials, bilinear)
   diffraction  first-order diffraction map, Manhattan, 1200 wedges
   city         forward trace, 0.97M-triangle procedural city, 1 TX, 1e7 rays, depth 8
-  city_adjoint forward then adjoint (uniform dL/dC) of the same city trace
+  city_adjoint forward then adjoint (uniform dL/dC) of the same city trace; with
+               --replay the forward records its hits and the adjoint replays them
   batched      the 64-TX batched workload (depth 3) in one launch on the binned-SAH tree
                (as the benchmark); --rays sets the lattice stride of every transmitter
                (default 1: the full workload)
@@ -36,6 +37,7 @@ def main(argv=None):
     ap.add_argument("--rays", type=int, default=0, help="rays per TX (trace cases) or samples per wedge")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--builder", default="auto", choices=["auto", "lbvh", "sah"], help="the scene's BVH builder")
+    ap.add_argument("--replay", action="store_true", help="adjoint cases: replay the forward's recorded hits")
     a = ap.parse_args(argv)
     if a.case in ("manhattan", "diffuse", "diffraction", "mesh"):
         sc, txs, p = S.workload(2)
@@ -69,8 +71,8 @@ def main(argv=None):
         elif a.case == "diffraction":
             r = api.diffraction_map(gs, txs, p, a.rays or 4096)
         elif a.case in ("adjoint", "city_adjoint"):
-            f = api.trace(gs, txs, p)
-            r = api.grad(gs, txs, p, torch.ones_like(f["maps"]))
+            f = api.trace(gs, txs, p, keep_hits=a.replay)
+            r = api.grad(gs, txs, p, torch.ones_like(f["maps"]), hits=f.get("hits"))
         else:
             r = api.trace(gs, txs, p)
     torch.cuda.synchronize()
