@@ -432,14 +432,18 @@ class TracePlan:
 
 
 class RadioMap(torch.autograd.Function):
-    """maps = RadioMap.apply(eps_r [nm], sigma [nm], tx_pos [ntx, 3], scene, txs, params, thickness [nm]).
+    """maps = RadioMap.apply(eps_r [nm], sigma [nm], tx_pos [ntx, 3], scene, txs, params, thickness [nm],
+    keep_hits=False).
 
     The forward traces with the given materials and positions; the backward is
     the hand-written adjoint kernel (choices frozen, probabilities detached).
+    With keep_hits the forward records every segment's closest-hit leaf (4 bytes
+    per ray and depth, held until the backward) and the backward replays them
+    instead of traversing the BVH again.
     """
 
     @staticmethod
-    def forward(ctx, eps, sigma, tx_pos, scene, txs, params, thickness):
+    def forward(ctx, eps, sigma, tx_pos, scene, txs, params, thickness, keep_hits=False):
         mats = np.stack([eps.detach().cpu().double().numpy(), sigma.detach().cpu().double().numpy(),
                          np.asarray(thickness, np.float64)], 1)
         scene.set_materials(mats)
@@ -454,10 +458,13 @@ class RadioMap(torch.autograd.Function):
             txl.append(s2)
         ctx.scene, ctx.txs, ctx.params = scene, txl, params
         ctx.meta = [(t.device, t.dtype) for t in (eps, sigma, tx_pos)]
-        return trace(scene, txl, params)["maps"]
+        f = trace(scene, txl, params, keep_hits=bool(keep_hits))
+        ctx.hits = f.get("hits")
+        return f["maps"]
 
     @staticmethod
     def backward(ctx, g):
-        r = grad(ctx.scene, ctx.txs, ctx.params, g.contiguous())
+        r = grad(ctx.scene, ctx.txs, ctx.params, g.contiguous(), hits=ctx.hits)
+        ctx.hits = None
         out = [r[k].to(device=d, dtype=t) for k, (d, t) in zip(("d_eps", "d_sigma", "d_tx"), ctx.meta)]
-        return out[0], out[1], out[2], None, None, None, None
+        return out[0], out[1], out[2], None, None, None, None, None

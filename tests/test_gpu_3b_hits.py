@@ -107,3 +107,25 @@ def test_short_or_foreign_hits(api):
     assert rep["stats"]["nodes_visited"] == ref["stats"]["nodes_visited"] > 0
     _compare_grads(ref, rep)
     gs.free()
+
+
+def test_autograd_function_keeps_hits(api):
+    """RadioMap with keep_hits: the same maps, and the backward's replayed
+    gradients equal those of the re-tracing backward."""
+    sc, txs, p = S.workload(4)
+    tx = txs[0]
+    tx.ray_stride = 17
+    gs = api.Scene.from_obj(sc)
+    res = []
+    for keep in (False, True):
+        eps = torch.tensor(sc.mats[:, 0], dtype=torch.float64, requires_grad=True)
+        sig = torch.tensor(sc.mats[:, 1], dtype=torch.float64, requires_grad=True)
+        pos = torch.tensor([tx.pos], dtype=torch.float64, requires_grad=True)
+        maps = api.RadioMap.apply(eps, sig, pos, gs, [tx], p, sc.mats[:, 2], keep)
+        g = (10.0 * torch.log10(maps.detach().clamp_min(1e-15)) + 150.0) * 1e-6
+        maps.backward(g)
+        res.append({"maps": maps.detach(), "d_eps": eps.grad, "d_sigma": sig.grad, "d_tx": pos.grad})
+    assert torch.allclose(res[0]["maps"], res[1]["maps"], rtol=1e-5, atol=0)
+    _compare_grads(res[0], res[1])
+    assert res[0]["d_eps"].abs().max() > 0
+    gs.free()
