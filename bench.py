@@ -7,9 +7,10 @@ transmitters with 1e8 Fibonacci rays each, 28 GHz, up to 8 reflections /
 refractions, 16 maps of 2048 x 2048 cells of 2 m, all in one persistent
 launch.  The metric counts segments (closest-hit queries with their deposit
 and shading) on the device.  The same line carries the adjoint over the
-materials on that workload (its rate and forward+adjoint / forward), the
-end-to-end rate from host arrays, the roofline of the tracer kernel and the
-FP64 oracle timed on the host; `extra` holds the Manhattan, batched and
+materials on that workload (its rate and forward+adjoint / forward; the
+adjoint replays the closest hits the forward recorded, the re-tracing form
+beside it), the end-to-end rate from host arrays, the roofline of the tracer
+kernel and the FP64 oracle timed on the host; `extra` holds the Manhattan, batched and
 differentiable workloads and the widened model, each with its roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -443,45 +444,46 @@ def run_ours(args, world, rank, local):
 def city_adjoint(api, S, torch, sc, txs, p, prm, prm_adj, gs, fwd_kernel_ms, fwd_segments, reps=3):
     """Adjoint of the dB-MSE loss over the materials on the city workload: the
     target maps are traced with seeded perturbed materials, the loss gradient
-    comes from the library's loss kernel, then the adjoint kernel is timed."""
+    comes from the library's loss kernel, then the adjoint kernel is timed in
+    its two forms: replaying the closest hits a recording forward kept (the
+    line's value) and re-tracing the forward's rays through the BVH."""
     tgt_sc = S.Scene(sc.name, sc.verts, sc.tris, sc.tri_mat, S.perturb_materials(sc.mats, 40))
     gt = api.Scene.from_obj(tgt_sc)
     tgt = api.trace(gt, txs, prm)["maps"]
     gt.free()
-    f = api.trace(gs, txs, prm)
-    loss, dL, valid = api.db_mse_loss(f["maps"], tgt)
-    del tgt
-    api.grad(gs, txs, prm_adj, dL)                 # warm-up
-    ak, segs = [], 0
-    for _ in range(reps):
-        a = api.grad(gs, txs, prm_adj, dL)
-        ak.append(a["stats"]["kernel_ms"])
-        segs = a["stats"]["segments"]
-    k = statistics.mean(ak)
-    out = {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3), "segments": segs,
-           "fwd_kernel_ms": round(fwd_kernel_ms, 3), "fwd_plus_adj_over_fwd": round((fwd_kernel_ms + k) / fwd_kernel_ms, 3),
-           "loss_cells": int(valid), "parameters": "d loss / d(eps_r, sigma) of 8 materials",
-           "roofline": roofline("city_adjoint", "k_trace<adjoint> (re-traces the forward's rays)", segs, k,
-                                "instruction issue", False)}
-    # the same adjoint replaying the closest hits a recording forward kept (4 B per segment
-    # slot on the device): no BVH traversal in the adjoint
+    # the recording forward: the maps, plus the closest hit of every segment (4 B per ray
+    # and depth on the device)
     fr = api.trace(gs, txs, prm, keep_hits=True)
     fk = fr["stats"]["kernel_ms"]
     hits = fr["hits"]
-    del fr
-    api.grad(gs, txs, prm_adj, dL, hits=hits)      # warm-up
-    rk = []
-    for _ in range(reps):
-        a = api.grad(gs, txs, prm_adj, dL, hits=hits)
-        rk.append(a["stats"]["kernel_ms"])
-    r = statistics.mean(rk)
-    out["replay"] = {"value": round(segs / (r / 1e3), 1), "unit": UNIT, "kernel_ms": round(r, 3),
-                     "recording_fwd_kernel_ms": round(fk, 3), "hits_bytes": int(hits.numel()) * 4,
-                     "fwd_plus_adj_over_fwd": round((fk + r) / fwd_kernel_ms, 3),
-                     "roofline": roofline("city_adjoint_replay", "k_trace<adjoint> replaying recorded hits", segs, r,
-                                          "instruction issue", False)}
+    loss, dL, valid = api.db_mse_loss(fr["maps"], tgt)
+    del tgt, fr
+
+    def timed(**kw):
+        api.grad(gs, txs, prm_adj, dL, **kw)       # warm-up
+        ks, segs = [], 0
+        for _ in range(reps):
+            a = api.grad(gs, txs, prm_adj, dL, **kw)
+            ks.append(a["stats"]["kernel_ms"])
+            segs = a["stats"]["segments"]
+        return statistics.mean(ks), segs
+
+    r, segs = timed(hits=hits)
+    hb = int(hits.numel()) * 4
     del hits
-    return out
+    k, _ = timed()
+    return {"value": round(segs / (r / 1e3), 1), "unit": UNIT, "kernel_ms": round(r, 3), "segments": segs,
+            "form": "replays the closest hit the recording forward kept for every segment (rm_radio_map_grad_hits)",
+            "hits_bytes": hb, "recording_fwd_kernel_ms": round(fk, 3), "fwd_kernel_ms": round(fwd_kernel_ms, 3),
+            "fwd_plus_adj_over_fwd": round((fk + r) / fwd_kernel_ms, 3),
+            "loss_cells": int(valid), "parameters": "d loss / d(eps_r, sigma) of 8 materials",
+            "roofline": roofline("city_adjoint_replay", "k_trace<adjoint> replaying recorded hits", segs, r,
+                                 "instruction issue", False),
+            "retrace": {"value": round(segs / (k / 1e3), 1), "unit": UNIT, "kernel_ms": round(k, 3),
+                        "form": "re-traces the forward's rays through the BVH (rm_radio_map_grad)",
+                        "fwd_plus_adj_over_fwd": round((fwd_kernel_ms + k) / fwd_kernel_ms, 3),
+                        "roofline": roofline("city_adjoint", "k_trace<adjoint> (re-traces the forward's rays)", segs,
+                                             k, "instruction issue", False)}}
 
 
 def _kernel_rate(api, gs, txs, prm, reps=5):
@@ -638,6 +640,16 @@ def run_extra(api, S, torch, gpu_name, flush, args):
             segs = f["stats"]["segments"]
             b_ms.append((t2 - t1) * 1e3)
     fk, ak = statistics.mean(f_ms), statistics.mean(a_ms)
+    # the same step with the forward recording its hits and the adjoint replaying them
+    rf_ms, ra_ms = [], []
+    for i in range(8):
+        f = api.trace(gs, txs, pf, keep_hits=True)
+        loss, dL, _ = api.db_mse_loss(f["maps"][0], tgt)
+        a = api.grad(gs, txs, pa, dL.view(1, p.ny, p.nx), hits=f["hits"])
+        if i >= 3:
+            rf_ms.append(f["stats"]["kernel_ms"])
+            ra_ms.append(a["stats"]["kernel_ms"])
+    rfk, rak = statistics.mean(rf_ms), statistics.mean(ra_ms)
     out["differentiable"] = {"workload": WORKLOADS[4], "fwd_kernel_ms": round(fk, 3), "adj_kernel_ms": round(ak, 3),
                              "fwd_plus_adj_over_fwd": round((fk + ak) / fk, 3),
                              "adj_call_ms": round(statistics.mean(b_ms), 3),
@@ -645,7 +657,11 @@ def run_extra(api, S, torch, gpu_name, flush, args):
                              "fwd_value": round(segs / (fk / 1e3), 1), "adj_value": round(segs / (ak / 1e3), 1),
                              "unit": UNIT, "segments": segs,
                              "roofline_fwd": roofline(0, "k_trace<bilinear>", segs, fk, "instruction issue", True),
-                             "roofline_adj": roofline(4, "k_trace<adjoint, bilinear>", segs, ak, "instruction issue", True)}
+                             "roofline_adj": roofline(4, "k_trace<adjoint, bilinear>", segs, ak, "instruction issue", True),
+                             "replay": {"recording_fwd_kernel_ms": round(rfk, 3), "adj_kernel_ms": round(rak, 3),
+                                        "adj_value": round(segs / (rak / 1e3), 1), "unit": UNIT,
+                                        "fwd_plus_adj_over_fwd": round((rfk + rak) / fk, 3),
+                                        "form": "the adjoint replays the closest hits the forward recorded"}}
     if not args.no_cpu_baseline:
         out["differentiable"]["cpu_baseline"] = oracle_sample(4, 6.0)
     gs.free()
