@@ -399,8 +399,8 @@ def run_ours(args, world, rank, local):
     # ---------------- forward + adjoint over the materials, same workload ----------------
     adjoint = None
     if not args.no_adjoint:
-        adjoint = city_adjoint(api, S, torch, sc, txs, p, prm, tuned_params(api, p, gpu_name, "city_adjoint")[0], gs,
-                               kavg, seg_step)
+        adjoint = city_adjoint(api, S, torch, sc, txs, p, prm, tuned_params(api, p, gpu_name, "city_adjoint")[0],
+                               tuned_params(api, p, gpu_name, "city_adjoint_replay")[0], gs, kavg, seg_step)
 
     # ---------------- end to end from host arrays ----------------
     e2e = None
@@ -441,7 +441,7 @@ def run_ours(args, world, rank, local):
     return line
 
 
-def city_adjoint(api, S, torch, sc, txs, p, prm, prm_adj, gs, fwd_kernel_ms, fwd_segments, reps=3):
+def city_adjoint(api, S, torch, sc, txs, p, prm, prm_adj, prm_rep, gs, fwd_kernel_ms, fwd_segments, reps=3):
     """Adjoint of the dB-MSE loss over the materials on the city workload: the
     target maps are traced with seeded perturbed materials, the loss gradient
     comes from the library's loss kernel, then the adjoint kernel is timed in
@@ -459,19 +459,19 @@ def city_adjoint(api, S, torch, sc, txs, p, prm, prm_adj, gs, fwd_kernel_ms, fwd
     loss, dL, valid = api.db_mse_loss(fr["maps"], tgt)
     del tgt, fr
 
-    def timed(**kw):
-        api.grad(gs, txs, prm_adj, dL, **kw)       # warm-up
+    def timed(pa, **kw):
+        api.grad(gs, txs, pa, dL, **kw)            # warm-up
         ks, segs = [], 0
         for _ in range(reps):
-            a = api.grad(gs, txs, prm_adj, dL, **kw)
+            a = api.grad(gs, txs, pa, dL, **kw)
             ks.append(a["stats"]["kernel_ms"])
             segs = a["stats"]["segments"]
         return statistics.mean(ks), segs
 
-    r, segs = timed(hits=hits)
+    r, segs = timed(prm_rep, hits=hits)
     hb = int(hits.numel()) * 4
     del hits
-    k, _ = timed()
+    k, _ = timed(prm_adj)
     return {"value": round(segs / (r / 1e3), 1), "unit": UNIT, "kernel_ms": round(r, 3), "segments": segs,
             "form": "replays the closest hit the recording forward kept for every segment (rm_radio_map_grad_hits)",
             "hits_bytes": hb, "recording_fwd_kernel_ms": round(fk, 3), "fwd_kernel_ms": round(fwd_kernel_ms, 3),
@@ -623,6 +623,7 @@ def run_extra(api, S, torch, gpu_name, flush, args):
     gt.free()
     pf = tuned_params(api, p, gpu_name, "manhattan")[0]
     pa = tuned_params(api, p, gpu_name, "adjoint")[0]
+    par = tuned_params(api, p, gpu_name, "adjoint_replay")[0]
     f_ms, a_ms, b_ms, segs = [], [], [], 0
     for i in range(8):
         torch.cuda.synchronize()
@@ -645,7 +646,7 @@ def run_extra(api, S, torch, gpu_name, flush, args):
     for i in range(8):
         f = api.trace(gs, txs, pf, keep_hits=True)
         loss, dL, _ = api.db_mse_loss(f["maps"][0], tgt)
-        a = api.grad(gs, txs, pa, dL.view(1, p.ny, p.nx), hits=f["hits"])
+        a = api.grad(gs, txs, par, dL.view(1, p.ny, p.nx), hits=f["hits"])
         if i >= 3:
             rf_ms.append(f["stats"]["kernel_ms"])
             ra_ms.append(a["stats"]["kernel_ms"])

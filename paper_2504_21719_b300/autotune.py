@@ -9,8 +9,8 @@ For each workload class it times, with the tracer's own CUDA-event timing
      before it takes new rays);
 and keeps the fastest.  The classes are the forward tracer on the Manhattan
 workload, the batched 64-TX launch, the city, the diffuse forward, the adjoint
-(differentiable workload and city) and the diffraction kernel (block size
-only).  Results go to tuning.json keyed by GPU name and class; bench.py and
+(differentiable workload and city, re-tracing and replaying recorded hits)
+and the diffraction kernel (block size only).  Results go to tuning.json keyed by GPU name and class; bench.py and
 callers read them back with ``lookup``.
 
     python -m paper_2504_21719_b300.autotune            # tunes and writes tuning.json
@@ -51,18 +51,22 @@ def _time(run, reps):
     return statistics.median(run() for _ in range(reps))
 
 
-def tune(api, scene, txs, params_obj, reps: int = 5, adjoint: bool = False):
+def tune(api, scene, txs, params_obj, reps: int = 5, adjoint: bool = False, replay: bool = False):
     """Staged search over the launch shape, then the refill threshold; returns
-    (best, all results, the library defaults' time)."""
+    (best, all results, the library defaults' time).  replay: the adjoint
+    replaying the hits of one recording forward."""
     import torch
-    g = None
+    g = hits = None
     if adjoint:
-        g = torch.full_like(api.trace(scene, txs, params_obj)["maps"], 1e-6)
+        f = api.trace(scene, txs, params_obj, keep_hits=replay)
+        g = torch.full_like(f["maps"], 1e-6)
+        hits = f.get("hits")
+        del f
 
     def run_with(cfg):
         p = api.params_from(params_obj, **cfg)
         if adjoint:
-            return lambda: api.grad(scene, txs, p, g)["stats"]["kernel_ms"]
+            return lambda: api.grad(scene, txs, p, g, hits=hits)["stats"]["kernel_ms"]
         return lambda: api.trace(scene, txs, p)["stats"]["kernel_ms"]
 
     results = []
@@ -126,13 +130,14 @@ def main(argv=None):
     t5.num_rays = 10_000_000
     jobs = {"manhattan": (sc2, txs2, p2, False), "batched": (*S.workload(3), False),
             "city": (sc5, [t5], p5, False), "city_adjoint": (sc5, [t5], p5, True),
-            "diffuse": (scd, txs2, pd, False), "adjoint": (*S.workload(4), True)}
+            "city_adjoint_replay": (sc5, [t5], p5, True), "diffuse": (scd, txs2, pd, False),
+            "adjoint": (*S.workload(4), True), "adjoint_replay": (*S.workload(4), True)}
     only = [k for k in a.only.split(",") if k]
     for key, (sc, txs, p, adj) in jobs.items():
         if only and key not in only:
             continue
         gs = api.Scene.from_obj(sc, builder="sah" if key == "batched" else "auto")   # the benchmark's trees
-        best, res, dflt = tune(api, gs, txs, p, adjoint=adj)
+        best, res, dflt = tune(api, gs, txs, p, adjoint=adj, replay=key.endswith("_replay"))
         entry[key] = {**best, "default_kernel_ms": dflt, "gain_over_default": round(dflt / best["kernel_ms"], 4),
                       "candidates": len(res)}
         gs.free()

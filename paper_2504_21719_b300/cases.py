@@ -60,6 +60,8 @@ def main(argv=None):
     from .autotune import lookup
     cls = {"manhattan": "manhattan", "diffuse": "diffuse", "adjoint": "adjoint", "diffraction": "diffraction",
            "city": "city", "city_adjoint": "city_adjoint", "batched": "batched", "mesh": "manhattan"}[a.case]
+    if a.replay and a.case in ("adjoint", "city_adjoint"):
+        cls += "_replay"
     blk, bps, qch, rfm = lookup(torch.cuda.get_device_name(0), cls)
     p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
     builder = "sah" if (a.case == "batched" and a.builder == "auto") else a.builder
