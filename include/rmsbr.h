@@ -338,8 +338,8 @@ rm_status rm_radio_map_grad(const rm_scene* scene, const rm_tx* tx_host, int32_t
  * hits_len >= (sum of the transmitters' ray counts) x (max_depth + 1) entries
  * (RM_EINVAL otherwise); slots of depths a ray does not reach are not
  * written.  The maps and counters are those of rm_radio_map_trace; the call
- * runs the statistics instantiation of the tracer (1-2 % slower than the plain
- * one).  Synchronises `stream`. */
+ * runs its own instantiation of the plain tracer, which adds one 4-byte store
+ * per segment (or, with RM_STATS, the statistics one).  Synchronises `stream`. */
 rm_status rm_radio_map_trace_hits(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
                                   const rm_trace_params* params, float* maps_dev, int32_t* hits_dev,
                                   uint64_t hits_len, rm_stats* stats_host_or_null, void* stream);

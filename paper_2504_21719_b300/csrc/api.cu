@@ -704,8 +704,10 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         for (const TxDev& t : P.tx) need += t.count * (unsigned long long)(p->max_depth + 1);
         if (hits_len < need) return fail(RM_EINVAL, "hits_len is below the segments' count (rays x (max_depth + 1))");
     }
-    // the forward that records its hits runs in the debug instantiation (the plain tracer stays as it is)
-    const bool debug = record != nullptr || (p->flags & RM_STATS) || (hits && !adjoint);
+    // the forward that records its hits runs its own instantiation of the plain tracer (or the debug
+    // one, which records them too, when a record or statistics are asked for)
+    const bool debug = record != nullptr || (p->flags & RM_STATS);
+    const bool record_hits = hits && !adjoint && !debug;
     size_t o_mat, o_tx, o_m64 = 0;
     const size_t bytes = adjoint ? table_bytes(P, &o_mat, &o_tx) : block_bytes_with_maps64(P, &o_mat, &o_tx, &o_m64);
     cudaEvent_t ev[2];
@@ -738,7 +740,7 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         if (P.a.total > 0) {
             if ((e = cudaEventRecord(ev[0], S(stream))) != cudaSuccess) break;
             if ((e = launch_trace(P.a, P.npol, debug, P.bilinear, adjoint, P.diffuse, P.block, P.bps, S(stream), &grid,
-                                  P.mesh)) != cudaSuccess)
+                                  P.mesh, record_hits)) != cudaSuccess)
                 break;
             if ((e = cudaEventRecord(ev[1], S(stream))) != cudaSuccess) break;
             timed = true;

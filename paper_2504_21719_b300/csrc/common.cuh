@@ -168,9 +168,12 @@ inline cudaError_t lib_host_alloc(void** p, size_t n, unsigned flags) {
 }
 
 // Host-side launchers (trace.cu)
+// hits: the plain forward that records every segment's closest hit in a.hits
 cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, bool diffuse,
-                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out, bool mesh = false);
-int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh = false);
+                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out, bool mesh = false,
+                         bool hits = false);
+int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh = false,
+                      bool hits = false);
 // wR, wT (the coin's weights) of one material at n cosines of incidence (trace.cu)
 cudaError_t launch_fresnel_probe(const MatDev& m, const float* cos1, long long n, float* wR, float* wT,
                                  cudaStream_t s);

@@ -695,7 +695,9 @@ constexpr int MAXSLOT = RM_MAX_DEPTH;
 // instantiation; the extra resident warps hide more latency (much of it
 // instruction fetch) than the spills cost, for the adjoint as well (its
 // tangents live in local memory anyway).
-template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF, bool MESH>
+// HITS: the plain forward that also writes every segment's closest-hit leaf
+// to A.hits (the debug instantiations write it too when A.hits is set).
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF, bool MESH, bool HITS = false>
 __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
     __shared__ MatDev s_mat[RM_MAX_MATERIALS];
     __shared__ TxDev s_tx[RM_MAX_TX];
@@ -869,7 +871,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
             if (!replayed)
                 h = closest_hit<DIFF || ADJ, DEBUG>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris,
                                                     overflow);
-            if (DEBUG && !ADJ && A.hits)
+            if ((DEBUG || HITS) && !ADJ && A.hits)
                 A.hits[s_tx[txi].rec_begin + isub * (unsigned long long)(A.L + 1) + depth] = h.slot;
             ++c_seg;
             if (h.slot < 0) ++c_esc;
@@ -1277,9 +1279,9 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
             if (s_grad[i] != 0.0f) atomicAdd(&A.scratch->grad[i], (double)s_grad[i]);
 }
 
-template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF, bool MESH = false>
+template <bool ADJ, int NPOL, bool DEBUG, bool BILIN, bool DIFF, bool MESH = false, bool HITS = false>
 const void* kernel_ptr() {
-    return reinterpret_cast<const void*>(&k_trace<ADJ, NPOL, DEBUG, BILIN, DIFF, MESH>);
+    return reinterpret_cast<const void*>(&k_trace<ADJ, NPOL, DEBUG, BILIN, DIFF, MESH, HITS>);
 }
 
 template <bool ADJ, int NPOL, bool DEBUG, bool BILIN>
@@ -1287,7 +1289,17 @@ const void* select_diff(bool diffuse) {
     return diffuse ? kernel_ptr<ADJ, NPOL, DEBUG, BILIN, true>() : kernel_ptr<ADJ, NPOL, DEBUG, BILIN, false>();
 }
 
-const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, bool mesh) {
+const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, bool mesh, bool hits) {
+    if (hits && !adjoint && !debug && !mesh) {
+        // the plain forward recording its closest hits
+#define RM_SELH(P, B) \
+    if (npol == P && bilinear == B) \
+        return diffuse ? kernel_ptr<false, P, false, B, true, false, true>() \
+                       : kernel_ptr<false, P, false, B, false, false, true>();
+        RM_SELH(1, false) RM_SELH(1, true) RM_SELH(2, false) RM_SELH(2, true)
+#undef RM_SELH
+        return nullptr;
+    }
     if (mesh) {
         // mesh surfaces: box cells only
         if (bilinear) return nullptr;
@@ -1334,16 +1346,17 @@ cudaError_t launch_fresnel_probe(const MatDev& m, const float* cos1, long long n
     return cudaGetLastError();
 }
 
-int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh) {
-    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse, mesh);
+int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh,
+                      bool hits) {
+    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse, mesh, hits);
     int nb = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0) != cudaSuccess) return 0;
     return nb;
 }
 
 cudaError_t launch_trace(const TraceArgs& a, int npol, bool debug, bool bilinear, bool adjoint, bool diffuse,
-                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out, bool mesh) {
-    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse, mesh);
+                         int block, int blocks_per_sm, cudaStream_t s, int* grid_out, bool mesh, bool hits) {
+    const void* k = select_kernel(npol, debug, bilinear, adjoint, diffuse, mesh, hits);
     if (!k) return cudaErrorInvalidValue;
     if (block <= 0 || block > MAX_BLOCK || (block & 31)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, occ = 0;
