@@ -331,12 +331,16 @@ rm_status rm_radio_map_grad(const rm_scene* scene, const rm_tx* tx_host, int32_t
                             rm_segment_record* record_dev_or_null, void* stream);
 
 /* Forward trace that also records, for the adjoint, the closest hit of every
- * segment: hits_dev[rec] = the leaf slot hit (a position in the scene's tree
- * order, -1 if the segment escaped), at the debug record's index rec =
- * (first item of the transmitter + i) (max_depth + 1) + l (see
- * rm_radio_map_trace).  hits_dev: device int32 owned by the caller, at least
- * hits_len >= (sum of the transmitters' ray counts) x (max_depth + 1) entries
- * (RM_EINVAL otherwise); slots of depths a ray does not reach are not
+ * segment (the paths of Sec. 4's estimator as sequences of hit triangles):
+ * hits_dev[l R + w] = the leaf slot hit at depth l (a position in the scene's
+ * tree order, -1 if the segment escaped) by the ray of work item w, where R =
+ * the sum of the transmitters' ray counts and w runs over the rays in the
+ * tracer's visit order (transmitter by transmitter, each a fixed permutation
+ * of its lattice subset; the order is the library's, so treat the buffer as
+ * opaque and hand it to rm_radio_map_grad_hits unchanged).  Neighbouring
+ * lanes trace neighbouring work items, so the stores coalesce.  hits_dev:
+ * device int32 owned by the caller, at least hits_len >= R x (max_depth + 1)
+ * entries (RM_EINVAL otherwise); slots of depths a ray does not reach are not
  * written.  The maps and counters are those of rm_radio_map_trace; the call
  * runs its own instantiation of the plain tracer, which adds one 4-byte store
  * per segment (or, with RM_STATS, the statistics one).  Synchronises `stream`. */
@@ -346,9 +350,9 @@ rm_status rm_radio_map_trace_hits(const rm_scene* scene, const rm_tx* tx_host, i
 
 /* rm_radio_map_grad replaying recorded hits: hits_dev from
  * rm_radio_map_trace_hits with the same scene, transmitters and params.  At
- * every segment the adjoint tests only the recorded leaf (the same watertight
- * test, so the same distance bit for bit) instead of traversing the BVH; an
- * entry of -1 is an escape.  An entry outside the scene, or a leaf the ray
+ * every segment the adjoint tests only the recorded leaf (the traversal's own
+ * watertight test, so the distance its traversal would find for that leaf)
+ * instead of traversing the BVH; an entry of -1 is an escape.  An entry outside the scene, or a leaf the ray
  * misses, falls back to the traversal, so no access leaves the scene; a
  * buffer recorded with other arguments gives gradients of other paths.  With
  * the matching buffer the gradients equal rm_radio_map_grad's up to the order

@@ -229,9 +229,10 @@ class Scene:
             pass
 
 
-def trace(scene: Scene, txs, params, record=False, stream=None, out=None, keep_hits=False):
+def trace(scene: Scene, txs, params, record=False, stream=None, out=None, keep_hits=False, hits_out=None):
     """Radio maps [ntx, ny, nx] (float32, cuda) and the counters; optionally the per-segment
-    record, or (keep_hits) every segment's closest-hit leaf slot for grad(..., hits=...)."""
+    record, or (keep_hits) every segment's closest-hit leaf slot for grad(..., hits=...),
+    written into hits_out (int32, cuda) when it is given."""
     lib = L.load()
     arr, ntx = _tx_array(txs)
     p = params if isinstance(params, L.rm_trace_params) else params_from(params)
@@ -240,9 +241,11 @@ def trace(scene: Scene, txs, params, record=False, stream=None, out=None, keep_h
         if record:
             raise ValueError("keep_hits and record are separate calls")
         nh = sum(tx_count(arr[i]) for i in range(ntx)) * (p.max_depth + 1)
-        hits = torch.empty(max(nh, 1), dtype=torch.int32, device="cuda")
+        hits = hits_out if hits_out is not None else torch.empty(max(nh, 1), dtype=torch.int32, device="cuda")
         st = L.rm_stats()
-        _check(lib.rm_radio_map_trace_hits(scene.handle, arr, ntx, C.byref(p), _ptr(maps), _ptr(hits), nh,
+        if hits.dtype != torch.int32 or not hits.is_cuda or not hits.is_contiguous():
+            raise ValueError("hits_out must be a contiguous int32 cuda tensor")
+        _check(lib.rm_radio_map_trace_hits(scene.handle, arr, ntx, C.byref(p), _ptr(maps), _ptr(hits), hits.numel(),
                                            C.byref(st), _stream(stream)), "rm_radio_map_trace_hits")
         return {"maps": maps, "stats": st.as_dict(), "hits": hits}
     rec = None

@@ -102,8 +102,9 @@ struct TraceArgs {
     double* maps64;              // [ntx][ny][nx] FP64 accumulation buffer (forward), or null
     const float* dLdC;           // [ntx][ny][nx] (adjoint)
     rm_segment_record* record;   // optional
-    // optional [total][L+1] leaf slot of every segment's closest hit (-1: escaped), at the
-    // debug record's index: the debug forward writes it, the adjoint replays it instead of
+    // optional [L+1][total] leaf slot of every segment's closest hit (-1: escaped), at
+    // [depth][work item]: a warp's lanes hold consecutive work items, so its stores and loads
+    // coalesce.  The recording forward writes it, the adjoint replays it instead of
     // traversing (a slot outside the scene falls back to the traversal)
     int32_t* hits;
     // mesh measurement surface (forward only): its LBVH and leaf records; the

@@ -733,6 +733,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
     float plen = 0.0f;  // unfolded tube length to the current origin
     int depth = 0, prev = -1, txi = 0;
     unsigned long long n = 0, isub = 0;
+    unsigned long long witem = 0;   // the ray's work item: its column of the recorded hits
     // adjoint state: tangents dE/d eta per material met on the path
     cf Tg[ADJ ? MAXSLOT : 1][NPOL][3];
     cf Ts[(ADJ && DIFF) ? MAXSLOT : 1][NPOL][3];  // dE / d(sigma / (eps0 omega)) once diffuse events occur
@@ -780,6 +781,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                         // neighbouring work items visit neighbouring lattice directions:
                         // i = j * F mod count with F a Fibonacci number (lattice neighbour step)
                         isub = w - T.work_begin;
+                        witem = w;
                         if (T.perm > 1ULL) {
                             // (isub * perm) mod count by Barrett reduction (isub, perm < count,
                             // product < 2^63): the estimate q is at most 2 below the quotient
@@ -864,7 +866,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
             bool replayed = false;
             if (ADJ && A.hits) {
                 // the forward's closest hit of this segment (-1: escaped), tested alone
-                const int s = A.hits[s_tx[txi].rec_begin + isub * (unsigned long long)(A.L + 1) + depth];
+                const int s = A.hits[(unsigned long long)depth * A.total + witem];
                 if (s == -1) replayed = true;
                 else if (s >= 0 && s < A.nt + A.nlarge) replayed = recorded_hit(A.tris, r, s, h);
             }
@@ -872,7 +874,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                 h = closest_hit<DIFF || ADJ, DEBUG>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris,
                                                     overflow);
             if ((DEBUG || HITS) && !ADJ && A.hits)
-                A.hits[s_tx[txi].rec_begin + isub * (unsigned long long)(A.L + 1) + depth] = h.slot;
+                A.hits[(unsigned long long)depth * A.total + witem] = h.slot;
             ++c_seg;
             if (h.slot < 0) ++c_esc;
         }

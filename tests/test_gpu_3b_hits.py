@@ -74,21 +74,30 @@ def test_replay_equals_retrace_city(api):
 
 
 def test_hits_are_the_records_hits(api):
-    """hits[rec] is the leaf slot of the record's triangle (order[slot] = prim),
-    -1 where the record says escaped; depths a ray never reached are not written."""
+    """hits[l, w] (depth l, work item w in the tracer's visit order) holds the leaf
+    slots of the record's triangles at depth l (order[slot] = prim), -1 where the
+    record says escaped, per depth the same multiset; depths a ray never reached
+    keep what the buffer held."""
     sc, txs, p = S.workload(2)
     tx = txs[0]
     tx.ray_stride = 97
     gs = api.Scene.from_obj(sc)
-    h = api.trace(gs, [tx], p, keep_hits=True)["hits"].cpu().numpy()
+    f = api.trace(gs, [tx], p, keep_hits=True)
+    h = f["hits"].fill_(-7)
+    f = api.trace(gs, [tx], p, keep_hits=True, hits_out=h)
+    h = f["hits"].cpu().numpy().reshape(p.max_depth + 1, -1)
     rec = api.trace(gs, [tx], p, record=True)["record"].cpu().numpy()
     order = gs.export_bvh()["order"]
-    prim = rec[:, 0]
-    reached = prim != -2
-    assert reached.sum() > 10000
-    assert np.array_equal(h[reached] == -1, prim[reached] == -1)
-    hit = reached & (prim >= 0)
-    assert np.array_equal(order[h[hit]], prim[hit])
+    prim = rec[:, 0].reshape(-1, p.max_depth + 1)
+    assert (prim != -2).sum() > 10000
+    for l in range(p.max_depth + 1):
+        reached = prim[:, l] != -2
+        got = h[l][h[l] != -7]
+        assert len(got) == reached.sum()
+        want = np.where(prim[reached, l] >= 0, 0, -1)
+        hit = got >= 0
+        assert np.array_equal(np.sort(np.where(hit, 0, -1)), np.sort(want))
+        assert np.array_equal(np.sort(order[got[hit]]), np.sort(prim[reached, l][prim[reached, l] >= 0]))
     gs.free()
 
 
