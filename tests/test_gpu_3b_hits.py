@@ -73,6 +73,26 @@ def test_replay_equals_retrace_city(api):
     _replay_equals_retrace(api, sc, tx, p)
 
 
+def test_replay_equals_retrace_city_full(api):
+    """The benchmark's full city workload (16 TX x 1e8 rays, depth 8, one launch):
+    the adjoint replaying the 6.3e9 recorded hits (57.6 GB) gives the re-tracing
+    adjoint's segments and gradients, to the order of the FP32 block sums."""
+    sc, txs, p = S.workload(5)
+    gs = api.Scene.from_obj(sc)
+    f = api.trace(gs, txs, p, keep_hits=True)
+    g = (10.0 * torch.log10(f["maps"].clamp_min(1e-15)) + 150.0) * 1e-6
+    rep = api.grad(gs, txs, p, g, hits=f.pop("hits"))
+    ref = api.grad(gs, txs, p, g)
+    assert rep["stats"]["segments"] == ref["stats"]["segments"] == f["stats"]["segments"]
+    assert rep["stats"]["deposits"] == ref["stats"]["deposits"]
+    for key in ("d_eps", "d_sigma"):
+        a, b = ref[key].double(), rep[key].double()
+        scale = a.abs().max().item()
+        assert scale > 0
+        assert torch.all((a - b).abs() <= 1e-4 * scale), (key, a, b)
+    gs.free()
+
+
 def test_hits_are_the_records_hits(api):
     """hits[l, w] (depth l, work item w in the tracer's visit order) holds the leaf
     slots of the record's triangles at depth l (order[slot] = prim), -1 where the
