@@ -678,9 +678,20 @@ def run_extra(api, S, torch, gpu_name, flush, args):
         if i >= 2:
             fk.append(f["stats"]["kernel_ms"])
             ak.append(a["stats"]["kernel_ms"])
+    rk, rak = [], []
+    for i in range(6):
+        f = api.trace(gs, txs, pd, keep_hits=True)
+        a = api.grad(gs, txs, pd, torch.ones_like(f["maps"]), hits=f["hits"])
+        if i >= 2:
+            rk.append(f["stats"]["kernel_ms"])
+            rak.append(a["stats"]["kernel_ms"])
     out["differentiable_diffuse"] = {"fwd_kernel_ms": round(statistics.mean(fk), 3),
                                      "adj_kernel_ms": round(statistics.mean(ak), 3),
-                                     "fwd_plus_adj_over_fwd": round(1 + statistics.mean(ak) / statistics.mean(fk), 3)}
+                                     "fwd_plus_adj_over_fwd": round(1 + statistics.mean(ak) / statistics.mean(fk), 3),
+                                     "replay": {"recording_fwd_kernel_ms": round(statistics.mean(rk), 3),
+                                                "adj_kernel_ms": round(statistics.mean(rak), 3),
+                                                "fwd_plus_adj_over_fwd": round((statistics.mean(rk) + statistics.mean(rak))
+                                                                               / statistics.mean(fk), 3)}}
     gs.free()
     out["time_vs_samples_and_antennas"] = sweep_samples_antennas(api, S, torch, gpu_name)
     return out
