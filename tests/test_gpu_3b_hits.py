@@ -163,3 +163,32 @@ def test_autograd_function_keeps_hits(api):
     _compare_grads(res[0], res[1])
     assert res[0]["d_eps"].abs().max() > 0
     gs.free()
+
+
+def test_hits_empty_and_depth_zero(api):
+    """Edge cases: a transmitter with no rays (nothing recorded, zero gradients)
+    beside one with rays, and max_depth 0 (one recorded slot per ray)."""
+    sc, txs, p = S.workload(4)
+    gs = api.Scene.from_obj(sc)
+    empty = copy.copy(txs[0])
+    empty.ray_count = 0
+    f = api.trace(gs, [empty], p, keep_hits=True)
+    assert f["stats"]["segments"] == 0 and torch.all(f["maps"] == 0)
+    r = api.grad(gs, [empty], p, torch.ones_like(f["maps"]), hits=f["hits"])
+    assert torch.all(r["d_eps"] == 0) and r["stats"]["segments"] == 0
+    tx = copy.copy(txs[0])
+    tx.ray_stride = 19
+    both = [empty, tx]
+    f2 = api.trace(gs, both, p, keep_hits=True)
+    g2 = (10.0 * torch.log10(f2["maps"].clamp_min(1e-15)) + 150.0) * 1e-6
+    _compare_grads(api.grad(gs, both, p, g2), api.grad(gs, both, p, g2, hits=f2["hits"]))
+    p0 = copy.copy(p)
+    p0.max_depth = 0
+    f0 = api.trace(gs, [tx], p0, keep_hits=True)
+    assert f0["hits"].numel() == api.tx_count(api.tx_from(tx))
+    g0 = (10.0 * torch.log10(f0["maps"].clamp_min(1e-15)) + 150.0) * 1e-6
+    ref = api.grad(gs, [tx], p0, g0, record=True)
+    rep = api.grad(gs, [tx], p0, g0, record=True, hits=f0["hits"])
+    assert torch.equal(ref["record"], rep["record"])
+    _compare_grads(ref, rep)
+    gs.free()
