@@ -375,6 +375,26 @@ rm_status rm_radio_map_grad_mesh(const rm_scene* scene, const rm_scene* surface,
                                  const rm_material* sampling_host_or_null, rm_stats* stats_host_or_null,
                                  rm_segment_record* record_dev_or_null, void* stream);
 
+/* rm_radio_map_trace_hits for maps on a mesh measurement surface (see
+ * rm_radio_map_trace_mesh): the same maps, and the closest hit of every
+ * segment in the scene (not the surface's crossings, which the adjoint walks
+ * again) in hits_dev, with the layout, length rule and errors of
+ * rm_radio_map_trace_hits and of rm_radio_map_trace_mesh. */
+rm_status rm_radio_map_trace_mesh_hits(const rm_scene* scene, const rm_scene* surface, const rm_tx* tx_host,
+                                       int32_t ntx, const rm_trace_params* params, float* maps_dev,
+                                       int32_t* hits_dev, uint64_t hits_len, rm_stats* stats_host_or_null,
+                                       void* stream);
+
+/* rm_radio_map_grad_mesh replaying the hits of rm_radio_map_trace_mesh_hits
+ * (same scene, surface, transmitters and params), as rm_radio_map_grad_hits
+ * does for the plane: only the recorded leaf is tested at each segment. */
+rm_status rm_radio_map_grad_mesh_hits(const rm_scene* scene, const rm_scene* surface, const rm_tx* tx_host,
+                                      int32_t ntx, const rm_trace_params* params, const float* dL_dmaps_dev,
+                                      const int32_t* hits_dev, uint64_t hits_len, float* d_eps_dev,
+                                      float* d_sigma_dev, float* d_txpos_dev,
+                                      const rm_material* sampling_host_or_null, rm_stats* stats_host_or_null,
+                                      rm_segment_record* record_dev_or_null, void* stream);
+
 /* Loss of the differentiable workload: mean over the cells V where both maps
  * exceed floor_linear of (10 log10 C_i - 10 log10 T_i)^2.  Writes loss_dev[0]
  * (float), dL_dmaps_dev [ncells] (0 outside V) and valid_dev[0] = |V|

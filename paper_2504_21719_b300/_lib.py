@@ -84,6 +84,8 @@ _SIGS = {
     "rm_radio_map_grad": ([P, P, C.c_int32, P, P, P, P, P, P, P, P, P], C.c_int),
     "rm_radio_map_trace_hits": ([P, P, C.c_int32, P, P, P, C.c_uint64, P, P], C.c_int),
     "rm_radio_map_grad_hits": ([P, P, C.c_int32, P, P, P, C.c_uint64, P, P, P, P, P, P, P], C.c_int),
+    "rm_radio_map_trace_mesh_hits": ([P, P, P, C.c_int32, P, P, P, C.c_uint64, P, P], C.c_int),
+    "rm_radio_map_grad_mesh_hits": ([P, P, P, C.c_int32, P, P, P, C.c_uint64, P, P, P, P, P, P, P], C.c_int),
     "rm_radio_map_grad_mesh": ([P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P], C.c_int),
     "rm_radio_map_trace_noalloc": ([P, P, C.c_int32, P, P, P, P], C.c_int),
     "rm_db_mse_loss": ([P, P, C.c_int64, C.c_float, P, P, P, P], C.c_int),

@@ -283,14 +283,25 @@ def diffraction_map_mesh(scene: Scene, surface: Scene, txs, params, samples_per_
     return res
 
 
-def trace_mesh(scene: Scene, surface: Scene, txs, params, record=False, stream=None, out=None):
+def trace_mesh(scene: Scene, surface: Scene, txs, params, record=False, stream=None, out=None, keep_hits=False):
     """Radio maps on a mesh measurement surface: [ntx, surface triangles] (float32, cuda),
     one cell per triangle of `surface` (a Scene whose materials are unused); the counters;
-    optionally the per-segment record."""
+    optionally the per-segment record, or (keep_hits) every segment's closest-hit leaf slot
+    in the scene for grad_mesh(..., hits=...)."""
     lib = L.load()
     arr, ntx = _tx_array(txs)
     p = params if isinstance(params, L.rm_trace_params) else params_from(params)
     maps = out if out is not None else torch.empty((ntx, surface.nt), dtype=torch.float32, device="cuda")
+    if keep_hits:
+        if record:
+            raise ValueError("keep_hits and record are separate calls")
+        nh = sum(tx_count(arr[i]) for i in range(ntx)) * (p.max_depth + 1)
+        hits = torch.empty(max(nh, 1), dtype=torch.int32, device="cuda")
+        st = L.rm_stats()
+        _check(lib.rm_radio_map_trace_mesh_hits(scene.handle, surface.handle, arr, ntx, C.byref(p), _ptr(maps),
+                                                _ptr(hits), hits.numel(), C.byref(st), _stream(stream)),
+               "rm_radio_map_trace_mesh_hits")
+        return {"maps": maps, "stats": st.as_dict(), "hits": hits}
     rec = None
     if record:
         nrec = sum(tx_count(arr[i]) for i in range(ntx)) * (p.max_depth + 1)
@@ -305,9 +316,11 @@ def trace_mesh(scene: Scene, surface: Scene, txs, params, record=False, stream=N
 
 
 def grad_mesh(scene: Scene, surface: Scene, txs, params, dLdC: torch.Tensor, sampling=None, record=False,
-              stream=None):
+              stream=None, hits=None):
     """(d_eps [nm], d_sigma [nm], d_txpos [ntx, 3] = 0) of sum(dLdC * maps) for maps on a mesh
-    measurement surface (dLdC [ntx, surface triangles]); choices frozen, q detached."""
+    measurement surface (dLdC [ntx, surface triangles]); choices frozen, q detached.
+    hits: trace_mesh(..., keep_hits=True)["hits"] of the same arguments, replayed instead of
+    traversing the scene's BVH."""
     lib = L.load()
     arr, ntx = _tx_array(txs)
     p = params if isinstance(params, L.rm_trace_params) else params_from(params)
@@ -321,9 +334,14 @@ def grad_mesh(scene: Scene, surface: Scene, txs, params, dLdC: torch.Tensor, sam
         rec = torch.empty((max(nrec, 1), 4), dtype=torch.int32, device="cuda")
     st = L.rm_stats()
     g = dLdC.contiguous()
-    _check(lib.rm_radio_map_grad_mesh(scene.handle, surface.handle, arr, ntx, C.byref(p), _ptr(g), _ptr(d_eps),
-                                      _ptr(d_sig), _ptr(d_tx), sm, C.byref(st), _ptr(rec), _stream(stream)),
-           "rm_radio_map_grad_mesh")
+    if hits is not None:
+        _check(lib.rm_radio_map_grad_mesh_hits(scene.handle, surface.handle, arr, ntx, C.byref(p), _ptr(g),
+                                               _ptr(hits), hits.numel(), _ptr(d_eps), _ptr(d_sig), _ptr(d_tx), sm,
+                                               C.byref(st), _ptr(rec), _stream(stream)), "rm_radio_map_grad_mesh_hits")
+    else:
+        _check(lib.rm_radio_map_grad_mesh(scene.handle, surface.handle, arr, ntx, C.byref(p), _ptr(g), _ptr(d_eps),
+                                          _ptr(d_sig), _ptr(d_tx), sm, C.byref(st), _ptr(rec), _stream(stream)),
+               "rm_radio_map_grad_mesh")
     out = {"d_eps": d_eps, "d_sigma": d_sig, "d_tx": d_tx, "stats": st.as_dict()}
     if record:
         out["record"] = rec

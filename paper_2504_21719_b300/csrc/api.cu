@@ -1052,6 +1052,28 @@ rm_status rm_radio_map_grad_mesh(const rm_scene* sc, const rm_scene* surface, co
                      sampling_host_or_null, stats, record, stream, true, surface);
 }
 
+rm_status rm_radio_map_trace_mesh_hits(const rm_scene* sc, const rm_scene* surface, const rm_tx* tx, int32_t ntx,
+                                       const rm_trace_params* p, float* maps_dev, int32_t* hits_dev,
+                                       uint64_t hits_len, rm_stats* stats, void* stream) {
+    if (!surface) return fail(RM_EINVAL, "surface is NULL");
+    if (!hits_dev) return fail(RM_EINVAL, "hits_dev is NULL");
+    return run_trace(sc, tx, ntx, p, maps_dev, nullptr, nullptr, nullptr, nullptr, nullptr, stats, nullptr, stream,
+                     false, surface, hits_dev, hits_len);
+}
+
+rm_status rm_radio_map_grad_mesh_hits(const rm_scene* sc, const rm_scene* surface, const rm_tx* tx, int32_t ntx,
+                                      const rm_trace_params* p, const float* dL_dmaps_dev, const int32_t* hits_dev,
+                                      uint64_t hits_len, float* d_eps_dev, float* d_sigma_dev, float* d_txpos_dev,
+                                      const rm_material* sampling_host_or_null, rm_stats* stats,
+                                      rm_segment_record* record, void* stream) {
+    if (!surface) return fail(RM_EINVAL, "surface is NULL");
+    if (!hits_dev) return fail(RM_EINVAL, "hits_dev is NULL");
+    // the adjoint only reads the buffer
+    return run_trace(sc, tx, ntx, p, nullptr, dL_dmaps_dev, d_eps_dev, d_sigma_dev, d_txpos_dev,
+                     sampling_host_or_null, stats, record, stream, true, surface, const_cast<int32_t*>(hits_dev),
+                     hits_len);
+}
+
 rm_status rm_db_mse_loss(const float* maps_dev, const float* target_dev, int64_t ncells, float floor_linear,
                          float* loss_dev, float* dL_dmaps_dev, int64_t* valid_dev, void* stream) {
     if (!maps_dev || !target_dev || !dL_dmaps_dev) return fail(RM_EINVAL, "NULL buffer");

@@ -1292,8 +1292,18 @@ const void* select_diff(bool diffuse) {
 }
 
 const void* select_kernel(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, bool mesh, bool hits) {
-    if (hits && !adjoint && !debug && !mesh) {
-        // the plain forward recording its closest hits
+    if (hits && !adjoint && !debug) {
+        // the plain forward recording its closest hits (mesh surfaces: box cells only)
+        if (mesh) {
+            if (bilinear) return nullptr;
+#define RM_SELHM(P) \
+    if (npol == P) \
+        return diffuse ? kernel_ptr<false, P, false, false, true, true, true>() \
+                       : kernel_ptr<false, P, false, false, false, true, true>();
+            RM_SELHM(1) RM_SELHM(2)
+#undef RM_SELHM
+            return nullptr;
+        }
 #define RM_SELH(P, B) \
     if (npol == P && bilinear == B) \
         return diffuse ? kernel_ptr<false, P, false, B, true, false, true>() \

@@ -192,3 +192,39 @@ def test_hits_empty_and_depth_zero(api):
     assert torch.equal(ref["record"], rep["record"])
     _compare_grads(ref, rep)
     gs.free()
+
+
+@pytest.mark.parametrize("diffuse", [False, True])
+def test_mesh_replay_equals_retrace(api, diffuse):
+    """Maps on a mesh measurement surface: the recording forward gives the plain
+    mesh maps, and the mesh adjoint replaying its scene hits gives the re-tracing
+    adjoint's records and gradients with no scene node visited."""
+    sc, txs, p = S.workload(4)
+    tx = copy.copy(txs[0])
+    tx.ray_stride = 13
+    p = copy.copy(p)
+    p.deposit = 0
+    if diffuse:
+        sc = sc.with_scattering(np.linspace(0.2, 0.8, sc.nm), 0.3, np.arange(sc.nm) % 3, 2, 3, 0.5)
+        p.diffuse = True
+    n = 48
+    x = np.linspace(-60.0, 60.0, n + 1)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    V = np.stack([X.ravel(), Y.ravel(), 1.5 + 0.5 * np.sin(X.ravel() / 9.0) * np.cos(Y.ravel() / 7.0)], 1)
+    q = (np.arange(n)[None, :] + (n + 1) * np.arange(n)[:, None]).ravel()
+    T = np.concatenate([np.stack([q, q + 1, q + n + 2], 1), np.stack([q, q + n + 2, q + n + 1], 1)])
+    gs = api.Scene.from_obj(sc)
+    su = api.surface(V.astype(np.float32), T.astype(np.int32))
+    f = api.trace_mesh(gs, su, [tx], p, keep_hits=True)
+    plain = api.trace_mesh(gs, su, [tx], p)
+    assert f["stats"]["segments"] == plain["stats"]["segments"]
+    assert torch.allclose(f["maps"], plain["maps"], rtol=1e-5, atol=0)
+    g = torch.from_numpy(np.random.default_rng(9).uniform(0.0, 1.0, (1, len(T))).astype(np.float32)).cuda()
+    ref = api.grad_mesh(gs, su, [tx], p, g, record=True)
+    rep = api.grad_mesh(gs, su, [tx], p, g, record=True, hits=f["hits"])
+    assert torch.equal(ref["record"], rep["record"])
+    assert ref["stats"]["nodes_visited"] > 0 and rep["stats"]["nodes_visited"] == 0
+    _compare_grads(ref, rep)
+    assert ref["d_eps"].abs().max() > 0
+    su.free()
+    gs.free()
