@@ -50,14 +50,16 @@ def allreduce_maps(maps, group=None):
     return maps
 
 
-def sharded_trace(scene, txs, params, group=None):
-    """Trace this rank's share of every transmitter and all-reduce the maps."""
+def sharded_trace(scene, txs, params, group=None, keep_hits=False):
+    """Trace this rank's share of every transmitter and all-reduce the maps.  With
+    keep_hits the result also holds this rank's recorded closest hits, for
+    sharded_grad(..., hits=...) on the same rank."""
     import torch.distributed as dist
 
     from . import api
     rank, world = dist.get_rank(group), dist.get_world_size(group)
     mine = [partition_tx(api.tx_from(t) if not hasattr(t, "_fields_") else t, rank, world) for t in txs]
-    r = api.trace(scene, mine, params)
+    r = api.trace(scene, mine, params, keep_hits=keep_hits)
     allreduce_maps(r["maps"], group)
     return r
 
@@ -75,14 +77,15 @@ def allreduce_grads(grads, group=None):
     return grads
 
 
-def sharded_grad(scene, txs, params, dLdC, group=None, src=0):
+def sharded_grad(scene, txs, params, dLdC, group=None, src=0, hits=None):
     """Differentiate this rank's share of every transmitter with dL/dC
-    broadcast from rank `src`, and all-reduce the gradients."""
+    broadcast from rank `src`, and all-reduce the gradients.  hits: this rank's
+    sharded_trace(..., keep_hits=True)["hits"], replayed instead of traversing."""
     import torch.distributed as dist
 
     from . import api
     dist.broadcast(dLdC, src=src, group=group)
     rank, world = dist.get_rank(group), dist.get_world_size(group)
     mine = [partition_tx(api.tx_from(t) if not hasattr(t, "_fields_") else t, rank, world) for t in txs]
-    g = api.grad(scene, mine, params, dLdC)
+    g = api.grad(scene, mine, params, dLdC, hits=hits)
     return allreduce_grads(g, group)

@@ -49,4 +49,12 @@ def test_sharded_trace_and_grad_world_size_1(api, nccl_group):
         scale = y.abs().max().item()
         assert scale > 0
         assert torch.all((x - y).abs() <= 1e-4 * scale), (key, x, y)
+    # the same with the forward's hits recorded and replayed by the adjoint
+    shh = sharded_trace(gs, [tx], p, keep_hits=True)
+    assert torch.all((shh["maps"].double() - b).abs()[mask] <= 2e-5 * b[mask])
+    gsh2 = sharded_grad(gs, [tx], p, g.clone(), hits=shh["hits"])
+    for key in ("d_eps", "d_sigma", "d_tx"):
+        x, y = gsh2[key].double(), gr[key].double()
+        scale = y.abs().max().item()
+        assert torch.all((x - y).abs() <= 1e-4 * scale), (key, x, y)
     gs.free()
