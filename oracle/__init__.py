@@ -87,7 +87,7 @@ def lib():
         _lib.or_diffraction_point.argtypes = [P, P, C.c_double, C.c_double, C.c_double, P]
         _lib.or_diffraction_map.restype = C.c_int
         _lib.or_diffraction_map.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int, P, P, C.c_int64, C.c_int,
-                                            P, C.c_int64, P, P, P, P]
+                                            P, C.c_int64, P, P, P, P, P, C.c_int64]
         _lib.or_diffuse_interact.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                              C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, P, P, P]
         _lib.or_fibonacci.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
@@ -523,13 +523,19 @@ def diffraction_point(wedge16, s, x, phi, zM):
 
 
 def diffraction_map(scene, tx, params, samples_per_wedge: int, mode: str = "plain", record=None,
-                    want_record: bool = False, slack: bool = False):
+                    want_record: bool = False, slack: bool = False, wedge_index=None):
     """First-order diffraction map [ny, nx] of one transmitter (oracle); with
     ``slack`` also the per-cell value change of the deposits under a +-1e-5 rad
-    shift of their Keller azimuth."""
+    shift of their Keller azimuth.  ``wedge_index``: positions in wedges(scene)
+    of the wedges to sample (default: all); the record follows that list."""
     v, t, m, mats = _scene_arrays(scene)
     otx, op = make_tx(tx), make_params(params)
-    nw = len(wedges(scene))
+    sel = None
+    if wedge_index is not None:
+        sel = np.ascontiguousarray(wedge_index, np.int64)
+        nw = len(sel)
+    else:
+        nw = len(wedges(scene))
     rec = None
     if mode == "replay":
         rec = np.ascontiguousarray(record, np.int32).reshape(nw * samples_per_wedge, 4).copy()
@@ -541,7 +547,8 @@ def diffraction_map(scene, tx, params, samples_per_wedge: int, mode: str = "plai
     rep = OrReport()
     rc = lib().or_diffraction_map(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), C.byref(otx),
                                   C.byref(op), int(samples_per_wedge), {"plain": 0, "replay": 1}[mode], _p(rec),
-                                  0 if rec is None else len(rec), _p(mp), _p(cnt), C.byref(rep), _p(sl))
+                                  0 if rec is None else len(rec), _p(mp), _p(cnt), C.byref(rep), _p(sl), _p(sel),
+                                  0 if sel is None else len(sel))
     if rc != 0:
         raise ValueError(f"or_diffraction_map failed ({rc})")
     out = {"map": mp, "crossings": int(cnt[0]), "visible": int(cnt[1]), "wedges": int(cnt[2])}

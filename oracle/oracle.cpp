@@ -2648,13 +2648,25 @@ extern "C" {
 // change of a deposit's value when its Keller azimuth moves by +-1e-5 rad
 // (test error bounds: FP32 may put a sample on the other side of a shadow
 // boundary or of a rounding point of N^+-).
+// wsel (or null): the positions, in the (tri0, trin) order of or_wedges, of
+// the nsel wedges to sample (a subset of the estimator's sum over wedges);
+// rec and counts then follow that list.
 int or_diffraction_map(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
                        const float* mats, int nm, const or_tx* tx, const or_params* P, int64_t samples_per_wedge,
                        int mode, int32_t* rec, int64_t rec_cap, double* map_out, double* counts_out,
-                       or_report* report, double* slack_out) {
+                       or_report* report, double* slack_out, const int64_t* wsel, int64_t nsel) {
     if (samples_per_wedge < 1) return 1;
     Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
-    const std::vector<Wedge> WS = find_wedges(S, verts, tris, nt);
+    std::vector<Wedge> WS = find_wedges(S, verts, tris, nt);
+    if (wsel) {
+        std::vector<Wedge> sub;
+        sub.reserve(nsel > 0 ? (size_t)nsel : 0);
+        for (int64_t j = 0; j < nsel; ++j) {
+            if (wsel[j] < 0 || wsel[j] >= (int64_t)WS.size()) return 3;
+            sub.push_back(WS[wsel[j]]);
+        }
+        WS.swap(sub);
+    }
     const int64_t nw = (int64_t)WS.size(), NS = samples_per_wedge;
     if (rec && rec_cap < nw * NS) return 2;
     MapGeom g = make_geom(*P, 1);

@@ -314,3 +314,30 @@ def test_diffraction_replay_and_planted_visibility(orc):
     bad = rec.copy()
     bad[cand[len(cand) // 2], 0] = 2
     assert orc.diffraction_map(sc, tx, p, 64, mode="replay", record=bad)["report"]["failures"] == 1
+
+
+def test_wedge_subsets_partition_the_map(orc):
+    """The estimator is a sum over wedges: maps over a partition of the wedge
+    list add up to the full map, and a subset's records are the full
+    record's rows of those wedges, in the subset's order."""
+    sc, txs, p = S.workload(2)
+    p.nx = p.ny = 64
+    p.cell_size = 8.0
+    tx = txs[0]
+    ns = 16
+    full = orc.diffraction_map(sc, tx, p, ns, want_record=True)
+    nw = len(orc.wedges(sc))
+    rng = np.random.default_rng(11)
+    perm = rng.permutation(nw)
+    parts = [np.sort(perm[: nw // 3]), perm[nw // 3:]]          # the second part out of order
+    total = np.zeros_like(full["map"])
+    for idx in parts:
+        r = orc.diffraction_map(sc, tx, p, ns, want_record=True, wedge_index=idx)
+        rows = (idx[:, None] * ns + np.arange(ns)[None, :]).ravel()
+        assert np.array_equal(r["record"], full["record"][rows])
+        assert r["wedges"] == len(idx)
+        total += r["map"]
+    assert full["visible"] > 400
+    assert np.allclose(total, full["map"], rtol=1e-12, atol=1e-12 * full["map"].max())
+    with pytest.raises(ValueError):
+        orc.diffraction_map(sc, tx, p, ns, wedge_index=[nw])
