@@ -110,12 +110,14 @@ def compare_maps(orc, scene, tx, params, gpu_map, gpu_record, rtol=MAP_RTOL, max
 
 
 def compare_diffraction(orc, scene, tx, params, samples_per_wedge, gpu_map, gpu_record, rtol=MAP_RTOL,
-                        max_adopt_frac=MAX_ADOPT_FRAC):
+                        max_adopt_frac=MAX_ADOPT_FRAC, wedge_index=None):
     """Replay the GPU's visibility bits and cells of a diffraction map in the
     FP64 oracle (every difference certified as a near-tie), then compare the
-    maps cell by cell."""
+    maps cell by cell.  wedge_index: the GPU sampled only these wedges (positions
+    in the oracle's wedge list), in this order."""
     rec = np.asarray(gpu_record).reshape(-1, 4)
-    r = orc.diffraction_map(scene, tx, params, samples_per_wedge, mode="replay", record=rec, slack=True)
+    r = orc.diffraction_map(scene, tx, params, samples_per_wedge, mode="replay", record=rec, slack=True,
+                            wedge_index=wedge_index)
     rep = r["report"]
     _log("diffraction", rep)
     assert rep["failures"] == 0, rep

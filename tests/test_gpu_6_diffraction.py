@@ -146,3 +146,33 @@ def test_diffraction_parity_with_array(orc, api, regular):
     m, rec, st = _run(api, sc, tx, p, 4096)
     assert st["deposits"] > 5000
     compare_diffraction(orc, sc, tx, p, 4096, m, rec)
+
+
+def test_diffraction_parity_city_wedge_subset(orc, api):
+    """The largest scene: the 0.97M-triangle city's wedges equal the oracle's,
+    and a subset of them (300 within 80 m of the transmitter, 100 anywhere, in
+    shuffled order) gives the oracle's visibility bits, cells and map.  The
+    visibility queries walk the binned-SAH tree of the whole city."""
+    from paper_2504_21719_b300 import _lib as L
+    sc, txs, p = S.workload(5)
+    tx = txs[0]
+    gs = api.Scene.from_obj(sc)
+    w, nw = gs.wedges()
+    raw = np.frombuffer(w, dtype=np.float32).reshape(-1, 18)[:nw]      # 14 floats, then tri0 trin mat0 matn
+    got = np.concatenate([raw[:, :14].astype(np.float64), raw[:, 14:16].view(np.int32).astype(np.float64)], 1)
+    ref = orc.wedges(sc)
+    assert got.shape == ref.shape and nw > 500_000
+    assert np.array_equal(got[:, 14:16], ref[:, 14:16])
+    assert np.allclose(got[:, :14], ref[:, :14], rtol=1e-6, atol=1e-4)
+    rng = np.random.default_rng(21)
+    near = np.flatnonzero(np.linalg.norm(ref[:, :2] - np.asarray(tx.pos[:2]), axis=1) < 80.0)
+    idx = np.concatenate([rng.choice(near, 300, replace=False), rng.choice(nw, 100, replace=False)])
+    rng.shuffle(idx)
+    sub = (L.rm_wedge * len(idx))(*[w[int(i)] for i in idx])
+    ns = 16
+    r = api.diffraction_map(gs, [tx], p, ns, wedges=(sub, len(idx)), record=True)
+    torch.cuda.synchronize()
+    rec = r["record"].cpu().numpy()
+    assert (rec[:, 0] == 0).sum() > 200 and (rec[:, 0] > 0).sum() > 1000   # visible and blocked samples
+    compare_diffraction(orc, sc, tx, p, ns, r["maps"][0].cpu().numpy(), rec, wedge_index=idx)
+    gs.free()
