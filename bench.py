@@ -349,6 +349,16 @@ def e2e_host(api, torch, sc, txs, prm, out, steps, warmup, flush, breakdown=0):
     return res
 
 
+def over_ranks(dist, torch, ms, counts, device):
+    """Whole-job figures of a multi-rank run: the slowest rank's time and the
+    sums over ranks of the per-rank counts (segments, bytes)."""
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), [float(x) for x in c]
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args, world, rank, local):
     import torch
@@ -384,11 +394,7 @@ def run_ours(args, world, rank, local):
     plan.free()
     total_ms, total_segs = sum(step_ms), sum(s["segments"] for s in st)
     if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        s = torch.tensor([total_segs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        total_ms, total_segs = float(t), float(s)
+        total_ms, (total_segs,) = over_ranks(dist, torch, total_ms, [total_segs], "cuda")
     value = total_segs / (total_ms / 1e3)
     seg_step = statistics.mean(s["segments"] for s in st)
     kavg = statistics.mean(kern_ms)
@@ -406,7 +412,13 @@ def run_ours(args, world, rank, local):
     e2e = None
     if not args.no_e2e:
         e2e = e2e_host(api, torch, sc, txs, prm, maps, args.steps, 1, flush, breakdown=2)
-        e2e["value"] *= world
+        if dist:
+            # every rank uploads the scene and reads back its own maps
+            ms, (segs, h2d, d2h) = over_ranks(dist, torch, e2e["ms_per_step"],
+                                              [e2e["value"] * e2e["ms_per_step"] / 1e3, e2e["h2d_bytes_per_step"],
+                                               e2e["d2h_bytes_per_step"]], "cuda")
+            e2e.update(value=segs / (ms / 1e3), ms_per_step=round(ms, 3), h2d_bytes_per_step=int(h2d),
+                       d2h_bytes_per_step=int(d2h))
     gs.free()
     del maps
 
