@@ -117,3 +117,22 @@ def test_adjoint_retakes_roulette_and_array(api):
     a = api.grad(gs, [tx], p, torch.rand_like(f["maps"]), record=True)
     assert torch.equal(f["record"], a["record"])
     gs.free()
+
+
+def test_city_roulette_array_dual_pol(orc, api):
+    """The largest scene with the widened model at once: Russian roulette after
+    two interactions (p_max = 0.5), a steered 16-element uniform linear array and
+    dual polarisation, on a sampled lattice subset of one city transmitter
+    (depth 8, 0.97M triangles, binned-SAH tree), replayed by the oracle."""
+    sc, txs, p = S.workload(5)
+    tx = copy.copy(txs[0])
+    tx.ray_stride, tx.ray_begin = 166_661, 7
+    tx.pol = 2
+    tx.ant_pos, tx.precoding = S.uniform_linear_array(16, p.freq_hz, 0.5, axis=1, steer=(0.3, 1.0, -0.2))
+    p.rr_depth, p.rr_max_prob, p.gain_threshold = 2, 0.5, 0.0
+    m, rec, st = _run(api, sc, tx, p)
+    dec = rec[:, 3]
+    assert int(((dec >= 0) & ((dec & 12) != 0)).sum()) > 100      # roulette kills
+    info = compare_maps(orc, sc, tx, p, m, rec)
+    assert info["cells"] > 100
+    assert info["frac_within_rtol"] >= 0.99, info
