@@ -136,3 +136,18 @@ def test_mesh_edge_cases(orc, api):
     assert r["stats"]["rays"] == 0 and float(r["maps"].abs().sum()) == 0.0
     su.free()
     gs.free()
+
+
+def test_mesh_parity_city(orc, api):
+    """The largest scene: a rolling 256 m x 256 m measurement surface (8192
+    triangles) around one transmitter of the 0.97M-triangle city (depth 8), a
+    sampled lattice subset of its rays, replayed by the oracle."""
+    sc, txs, p = S.workload(5)
+    tx = copy.copy(txs[0])
+    tx.ray_stride, tx.ray_begin = 99_991, 3
+    V, T = grid_surface(tx.pos[0] - 128.0, tx.pos[1] - 128.0, 4.0, 64, 64,
+                        lambda X, Y: 1.5 + 0.5 * np.sin(X / 9.0) * np.cos(Y / 7.0))
+    m, rec, st = _run(api, sc, V, T, [tx], p)
+    assert st["rays"] == tx.count() and st["deposits"] > 300
+    info = compare_mesh(orc, sc, tx, p, V, T, m[0], rec)
+    assert info["cells"] > 300
