@@ -49,7 +49,9 @@ __device__ __forceinline__ cf utd_F(float x, const DiffArgs& A) {
 // ------------------------------------------------------------------ any-hit visibility
 // Is the open segment o + t d, t in (tmin, tmax), blocked by a triangle other
 // than the original triangles ex0, ex1?  Moeller-Trumbore per triangle,
-// stack traversal without ordering, early exit on the first blocker.
+// stack traversal without ordering, early exit on the first blocker.  The
+// plane kernel inlines it at its one call site; the mesh kernel calls it
+// (inlined at its two sites it spills).
 __device__ __forceinline__ bool tri_blocks(const float4* __restrict__ tris, int slot, f3 o, f3 d, float tmin,
                                            float tmax, int ex0, int ex1, unsigned& c_tris) {
     const float4* tp = tris + 3 * (size_t)slot;
@@ -74,8 +76,8 @@ __device__ __forceinline__ bool tri_blocks(const float4* __restrict__ tris, int 
     return t > tmin && t < tmax;
 }
 
-__device__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float tmax, int ex0, int ex1,
-                                unsigned& c_nodes, unsigned& c_tris, bool& overflow) {
+__device__ __forceinline__ bool segment_blocked_inl(const DiffArgs& A, f3 o, f3 d, float tmin, float tmax, int ex0,
+                                                   int ex1, unsigned& c_nodes, unsigned& c_tris, bool& overflow) {
     for (int j = 0; j < A.nlarge; ++j)
         if (tri_blocks(A.tris, A.nt + j, o, d, tmin, tmax, ex0, ex1, c_tris)) return true;
     if (A.nt <= 0) return false;
@@ -128,6 +130,11 @@ __device__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float
             cur = stack[--sp];
         }
     }
+}
+
+__device__ __noinline__ bool segment_blocked(const DiffArgs& A, f3 o, f3 d, float tmin, float tmax, int ex0, int ex1,
+                                             unsigned& c_nodes, unsigned& c_tris, bool& overflow) {
+    return segment_blocked_inl(A, o, d, tmin, tmax, ex0, ex1, c_nodes, c_tris, overflow);
 }
 
 // ------------------------------------------------------------------ antenna field
@@ -353,9 +360,284 @@ __device__ __noinline__ int surface_hits(const float4* __restrict__ nodes, const
     }
 }
 
-// ------------------------------------------------------------------ kernel
-template <bool MESH>
-__global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
+// ------------------------------------------------------------------ sample geometry
+// Sample w of the (transmitter, wedge, sample) sequence: the wedge turned so
+// that the source lies in front of its 0-face (the UTD assumes phi' <= pi;
+// otherwise the faces swap, and a source behind both faces gives code -2),
+// the lattice sample x = L (i + 1/2)/N, phi = n pi frac(i (phi_g - 1)) (24-bit
+// fixed point), the diffraction point v, the Keller-cone direction ks and
+// the crossing of the measurement plane with its cell.
+struct DSample {
+    int txi, m0, mn, tri0, trin;
+    int code;            // -2: source behind both faces; -1: lit
+    f3 s, o, e, n0, nn, t0, v, d, u, ks;
+    float wlen, wn, u2, sp, cp, dn, cb, sb;
+    bool dep;            // the diffracted ray crosses the plane inside the map
+    float tc, fx, fy;
+    int cxi, cyi;
+};
+
+__device__ __forceinline__ void diff_sample(const DiffArgs& A, unsigned long long w, DSample& G) {
+    const unsigned long long per_tx = (unsigned long long)A.nw * A.ns;
+    G.txi = (int)(w / per_tx);
+    const unsigned long long rem = w - (unsigned long long)G.txi * per_tx;
+    const long long wi = (long long)(rem / A.ns);
+    const unsigned long long i = rem - (unsigned long long)wi * A.ns;
+    const TxDev& T = A.tx[G.txi];
+    const rm_wedge W = A.wedges[wi];
+    G.s = f3{T.pos[0], T.pos[1], T.pos[2]};
+    G.o = f3{W.origin[0], W.origin[1], W.origin[2]};
+    G.e = f3{W.edge[0], W.edge[1], W.edge[2]};
+    G.n0 = f3{W.n0[0], W.n0[1], W.n0[2]};
+    G.nn = f3{W.nn[0], W.nn[1], W.nn[2]};
+    G.m0 = W.mat0;
+    G.mn = W.matn;
+    G.tri0 = W.tri0;
+    G.trin = W.trin;
+    G.wlen = W.length;
+    G.wn = W.n;
+    if (dot(G.s - G.o, G.n0) < 0.0f) {
+        G.o = G.o + G.e * W.length;
+        G.e = G.e * -1.0f;
+        const f3 t = G.n0;
+        G.n0 = G.nn;
+        G.nn = t;
+        const int tm = G.m0;
+        G.m0 = G.mn;
+        G.mn = tm;
+    }
+    G.code = -2;
+    G.dep = false;
+    G.cxi = G.cyi = NO_CELL;
+    G.tc = G.fx = G.fy = 0.0f;
+    if (!(dot(G.s - G.o, G.n0) >= 0.0f)) return;
+    G.code = -1;
+    G.t0 = cross(G.n0, G.e);
+    const float u1 = A.ns < (1ULL << 24) ? ((float)i + 0.5f) / (float)A.ns : (float)(((double)i + 0.5) / (double)A.ns);
+    const unsigned long long fr = i * 0x9E3779B97F4A7C16ULL;
+    G.u2 = (float)(unsigned)(fr >> 40) * 0x1p-24f;
+    const float x = u1 * W.length;
+    sincospif(G.u2 * W.n, &G.sp, &G.cp);
+    G.v = G.o + G.e * x;
+    G.d = G.v - G.s;
+    G.dn = sqrtf(dot(G.d, G.d));
+    const f3 so = G.s - G.o;
+    const f3 perp = so - G.e * dot(so, G.e);
+    const float rho = sqrtf(dot(perp, perp));
+    G.cb = dot(G.d, G.e) / G.dn;
+    G.sb = rho / G.dn;
+    G.u = f3{G.cp * G.t0.x + G.sp * G.n0.x, G.cp * G.t0.y + G.sp * G.n0.y, G.cp * G.t0.z + G.sp * G.n0.z};
+    G.ks = G.u * G.sb + G.e * G.cb;
+    {
+        // plane crossing and cell (as the tracer's deposit)
+        const float tc = (A.zm - G.v.z) / G.ks.z;
+        if (G.ks.z != 0.0f && tc > 1e-9f) {
+            const float px = G.v.x + tc * G.ks.x, py = G.v.y + tc * G.ks.y;
+            float ux = (px - A.x0) * A.inv_cell, uy = (py - A.y0) * A.inv_cell;
+            if (A.bilinear) {
+                ux -= 0.5f;
+                uy -= 0.5f;
+                if (ux >= -1.0f && ux < (float)A.nx && uy >= -1.0f && uy < (float)A.ny) {
+                    const float flx = floorf(ux), fly = floorf(uy);
+                    G.cxi = (int)flx;
+                    G.cyi = (int)fly;
+                    G.fx = ux - flx;
+                    G.fy = uy - fly;
+                    G.dep = true;
+                }
+            } else if (ux >= 0.0f && ux < (float)A.nx && uy >= 0.0f && uy < (float)A.ny) {
+                G.cxi = (int)ux;
+                G.cyi = (int)uy;
+                G.dep = true;
+            }
+            G.tc = tc;
+        }
+    }
+}
+
+__device__ __forceinline__ void put_record(const DiffArgs& A, unsigned long long w, int code, int ix, int iy) {
+    if (!A.record) return;
+    rm_segment_record* rec = A.record + w;
+    rec->prim = code;
+    rec->ix = code == -2 ? NO_CELL : ix;
+    rec->iy = code == -2 ? NO_CELL : iy;
+    rec->decision = 0;
+}
+
+// The two visibility queries of a sample that reaches the plane (source -> v,
+// v -> plane, the wedge's own faces excluded) through one rolled call site:
+// 0 visible, bit 0 incident segment blocked, bit 1 diffracted segment blocked.
+__device__ __forceinline__ int plane_visibility(const DiffArgs& A, const DSample& G, unsigned& c_nodes,
+                                                unsigned& c_tris, bool& overflow) {
+    const float vm = fmaxf(fabsf(G.v.x), fmaxf(fabsf(G.v.y), fabsf(G.v.z)));
+    const float eps = fmaxf(1.0f, vm) * 0x1p-16f;
+    const f3 si = G.d * (1.0f / G.dn);
+    int code = 0;
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+        const bool blk = segment_blocked_inl(A, q ? G.v : G.s, q ? G.ks : si, eps, q ? G.tc : G.dn - eps, G.tri0,
+                                             G.trin, c_nodes, c_tris, overflow);
+        if (blk) code |= 1 << q;
+    }
+    return code;
+}
+
+// The deposit of a visible sample: weighting factor |dt/dx x dt/dphi|
+// (hand-derived), UTD field (Eq. diffracted-field) and FP64 atomics.
+__device__ __forceinline__ void plane_deposit(const DiffArgs& A, const DSample& G) {
+    // with a = (v - s).e, d cb/dx = sb^2/dn, d sb/dx = -sb cb/dn, so
+    // dk/dx = (sb/dn)(sb e - cb u), dk/dphi = sb (-sin phi t0 + cos phi n0),
+    // dtc/dq = -(dv_z/dq + tc dk_z/dq)/k_z, dt/dq = dv/dq + dtc/dq k + tc dk/dq.
+    const float sb = G.sb, cb = G.cb, tc = G.tc;
+    const f3 e = G.e, ks = G.ks;
+    const f3 dkx = (e * sb - G.u * cb) * (sb / G.dn);
+    const f3 dkp{sb * (G.cp * G.n0.x - G.sp * G.t0.x), sb * (G.cp * G.n0.y - G.sp * G.t0.y),
+                 sb * (G.cp * G.n0.z - G.sp * G.t0.z)};
+    const float dtcx = -(e.z + tc * dkx.z) / ks.z;
+    const float dtcp = -(tc * dkp.z) / ks.z;
+    const float txx = e.x + dtcx * ks.x + tc * dkx.x, txy = e.y + dtcx * ks.y + tc * dkx.y;
+    const float tpx = dtcp * ks.x + tc * dkp.x, tpy = dtcp * ks.y + tc * dkp.y;
+    const float J = fabsf(txx * tpy - txy * tpx);
+    // UTD: angles from the 0-face, phi of the sample
+    const float phi = G.u2 * G.wn * PI_F;
+    const float sobs = tc;
+    const f3 si = G.d * (1.0f / G.dn);
+    const float pw = diffracted_power(A, A.tx[G.txi], G.s, G.v, e, G.n0, G.nn, G.t0, G.m0, G.mn, G.wn, phi, sb, si,
+                                      G.dn, sobs);
+    const float spread = 1.0f / (G.dn * sobs * (G.dn + sobs));
+    const float value = A.lam4pi2_over_cell2 * (G.wlen * G.wn * PI_F / (float)A.ns) * J * pw * spread;
+    const unsigned long long mb = (unsigned long long)G.txi * A.ncell;
+    if (A.bilinear) {
+        for (int cn = 0; cn < 4; ++cn) {
+            const int a = cn & 1, b = cn >> 1;
+            const int xx = G.cxi + a, yy = G.cyi + b;
+            if (xx < 0 || xx >= A.nx || yy < 0 || yy >= A.ny) continue;
+            const float wgt = (a ? G.fx : 1.0f - G.fx) * (b ? G.fy : 1.0f - G.fy);
+            atomicAdd(A.maps64 + mb + (unsigned long long)yy * A.nx + xx, (double)(value * wgt));
+        }
+    } else {
+        atomicAdd(A.maps64 + mb + (unsigned long long)G.cyi * A.nx + G.cxi, (double)value);
+    }
+}
+
+__device__ __forceinline__ void flush_counters(const DiffArgs& A, unsigned long long* s_cnt, const unsigned (&v)[6],
+                                               bool overflow, bool xlimit) {
+    if (overflow) atomicOr(&A.scratch->status, 1);
+    if (xlimit) atomicOr(&A.scratch->status, 2);
+    for (int j = 0; j < 6; ++j) {
+        const unsigned sum = __reduce_add_sync(0xffffffffu, v[j]);
+        if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&s_cnt[j], (unsigned long long)sum);
+    }
+    __syncthreads();
+    if (threadIdx.x < 6 && s_cnt[threadIdx.x]) atomicAdd(&A.scratch->cnt[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// ------------------------------------------------------------------ kernel: measurement plane
+// Most samples end early (their diffracted ray leaves upwards or outside the
+// map, or the source is behind both faces), so one sample per thread would
+// run the visibility queries and the UTD field with a few lanes of a warp.
+// Instead each warp works in three stages with two queues of sample indices
+// in shared memory: it classifies 32 samples at a time and queues those that
+// reach the map; once 32 are queued it runs their visibility queries together
+// and queues the visible ones; once 32 of those are queued it evaluates their
+// field and deposits them.  Every stage recomputes the sample's geometry from
+// its index (the same arithmetic, so the same cell).  Warps take their
+// samples 128 at a time from a queue head in the scratch block; the queue
+// lengths and the head are warp-uniform, and every pass of the loop either
+// consumes queued samples or takes new ones, so the loop ends after
+// O(samples / 32) passes.
+constexpr int DQ_CAP = 64;                     // per warp and stage; never holds more than 63
+constexpr unsigned long long DQ_CHUNK = 128;   // samples per queue-head access
+
+__global__ void __launch_bounds__(256) k_diffraction_plane(const DiffArgs A) {
+    __shared__ unsigned long long s_cnt[6];
+    __shared__ unsigned long long s_q[2][256 / 32][DQ_CAP];
+    if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long* qa = s_q[0][wid];   // samples that reach the map
+    unsigned long long* qb = s_q[1][wid];   // ... and are visible from the source and the plane
+    unsigned c_rays = 0, c_seg = 0, c_nodes = 0, c_tris = 0, c_dep = 0;
+    bool overflow = false;
+    int na = 0, nb = 0;
+    bool done = false;
+    unsigned long long base = 0, end = 0;
+    while (true) {
+        if (nb >= 32 || (done && na == 0 && nb > 0)) {
+            // stage 3: field and deposit of up to 32 visible samples
+            const int take = nb < 32 ? nb : 32;
+            if (lane < take) {
+                const unsigned long long w = qb[nb - take + lane];
+                DSample G;
+                diff_sample(A, w, G);
+                plane_deposit(A, G);
+                ++c_dep;
+                put_record(A, w, 0, G.cxi, G.cyi);
+            }
+            __syncwarp();
+            nb -= take;
+        } else if (na >= 32 || (done && na > 0)) {
+            // stage 2: visibility queries of up to 32 samples that reach the map
+            const int take = na < 32 ? na : 32;
+            unsigned long long w = 0;
+            bool vis = false;
+            if (lane < take) {
+                w = qa[na - take + lane];
+                DSample G;
+                diff_sample(A, w, G);
+                ++c_seg;
+                const int code = plane_visibility(A, G, c_nodes, c_tris, overflow);
+                if (code == 0) vis = true;
+                else put_record(A, w, code, G.cxi, G.cyi);
+            }
+            __syncwarp();
+            na -= take;
+            const unsigned m = __ballot_sync(0xffffffffu, vis);
+            if (vis) qb[nb + __popc(m & lt)] = w;
+            nb += __popc(m);
+            __syncwarp();
+        } else if (!done) {
+            // stage 1: take and classify the next 32 samples
+            if (base >= end) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(&A.scratch->next, DQ_CHUNK);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (b >= A.total) {
+                    done = true;
+                    continue;
+                }
+                base = b;
+                end = b + DQ_CHUNK < A.total ? b + DQ_CHUNK : A.total;
+            }
+            const unsigned long long w = base + lane;
+            bool dep = false;
+            if (w < end) {
+                ++c_rays;
+                DSample G;
+                diff_sample(A, w, G);
+                dep = G.dep;
+                if (!dep) put_record(A, w, G.code, NO_CELL, NO_CELL);
+            }
+            base += 32;
+            const unsigned m = __ballot_sync(0xffffffffu, dep);
+            if (dep) qa[na + __popc(m & lt)] = w;
+            na += __popc(m);
+            __syncwarp();
+        } else {
+            break;
+        }
+    }
+    const unsigned v[6] = {c_rays, c_seg, c_nodes, c_tris, c_dep, 0u};
+    flush_counters(A, s_cnt, v, overflow, false);
+}
+
+// ------------------------------------------------------------------ kernel: mesh measurement surface
+// One thread per sample in a grid-stride loop over (transmitter, wedge,
+// sample): the incident segment once, then every crossing of the diffracted
+// ray with the surface, each with its own visibility, weighting factor on the
+// triangle's plane, UTD field at its distance and 1/A.
+__global__ void __launch_bounds__(256) k_diffraction_mesh(const DiffArgs A) {
     __shared__ unsigned long long s_cnt[6];
     if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -386,11 +668,8 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
             m0 = mn;
             mn = tm;
         }
-        rm_segment_record* rec = A.record ? A.record + w : nullptr;
-        int code = -2, cxi = NO_CELL, cyi = NO_CELL;
-        float fx = 0.0f, fy = 0.0f;
+        int code = -2, nh = NO_CELL;
         if (dot(s - o, n0) >= 0.0f) {
-            code = -1;
             const f3 t0 = cross(n0, e);
             // sample i: x = L (i + 1/2)/N, phi = n pi frac(i (phi_g - 1)) (24-bit fixed point)
             const float u1 = A.ns < (1ULL << 24) ? ((float)i + 0.5f) / (float)A.ns
@@ -409,142 +688,49 @@ __global__ void __launch_bounds__(256) k_diffraction(const DiffArgs A) {
             const float cb = dot(d, e) / dn, sb = rho / dn;
             const f3 u{cp * t0.x + sp * n0.x, cp * t0.y + sp * n0.y, cp * t0.z + sp * n0.z};
             const f3 ks = u * sb + e * cb;
-            if (MESH) {
-                // mesh measurement surface: the incident segment once, then every
-                // crossing of the diffracted ray with its own visibility, weighting
-                // factor on the triangle's plane, UTD field at its distance and 1/A
-                ++c_seg;
-                const float vm = fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)));
-                const float eps = fmaxf(1.0f, vm) * 0x1p-16f;
-                const f3 si = d * (1.0f / dn);
-                code = segment_blocked(A, s, si, eps, dn - eps, W.tri0, W.trin, c_nodes, c_tris, overflow) ? 1 : 0;
-                cxi = 0;
-                cyi = 0;
-                if (code == 0) {
-                    Crossing hits[MAX_CROSS];
-                    const int nh = surface_hits(A.snodes, A.stris, A.snt, A.snlarge, v, ks, hits, &overflow, &xlimit);
-                    cxi = nh;
-                    const float nw_ = W.n;
-                    const float phi = u2 * nw_ * PI_F;
-                    const f3 dkx = (e * sb - u * cb) * (sb / dn);
-                    const f3 dkp{sb * (cp * n0.x - sp * t0.x), sb * (cp * n0.y - sp * t0.y),
-                                 sb * (cp * n0.z - sp * t0.z)};
-                    const unsigned long long mb = (unsigned long long)txi * A.ncell;
+            ++c_seg;
+            const float vm = fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)));
+            const float eps = fmaxf(1.0f, vm) * 0x1p-16f;
+            const f3 si = d * (1.0f / dn);
+            code = segment_blocked(A, s, si, eps, dn - eps, W.tri0, W.trin, c_nodes, c_tris, overflow) ? 1 : 0;
+            nh = 0;
+            if (code == 0) {
+                Crossing hits[MAX_CROSS];
+                nh = surface_hits(A.snodes, A.stris, A.snt, A.snlarge, v, ks, hits, &overflow, &xlimit);
+                const float nw_ = W.n;
+                const float phi = u2 * nw_ * PI_F;
+                const f3 dkx = (e * sb - u * cb) * (sb / dn);
+                const f3 dkp{sb * (cp * n0.x - sp * t0.x), sb * (cp * n0.y - sp * t0.y), sb * (cp * n0.z - sp * t0.z)};
+                const unsigned long long mb = (unsigned long long)txi * A.ncell;
 #pragma unroll 1
-                    for (int c = 0; c < nh; ++c) {
-                        const float tc = hits[c].t;
-                        if (segment_blocked(A, v, ks, eps, tc, W.tri0, W.trin, c_nodes, c_tris, overflow)) continue;
-                        // weighting factor on the plane n.(t - a) = 0: dtc/dq = -(n.dv/dq + tc n.dk/dq) / (n.k)
-                        const f3 nc = hits[c].nrm;
-                        const float nk = dot(nc, ks);
-                        if (nk == 0.0f) continue;
-                        const float dtcx = -(dot(nc, e) + tc * dot(nc, dkx)) / nk;
-                        const float dtcp = -(tc * dot(nc, dkp)) / nk;
-                        const f3 tx = e + ks * dtcx + dkx * tc;
-                        const f3 tp = ks * dtcp + dkp * tc;
-                        const f3 cr = cross(tx, tp);
-                        const float J = sqrtf(dot(cr, cr));
-                        const float pw = diffracted_power(A, T, s, v, e, n0, nn, t0, m0, mn, nw_, phi, sb, si, dn, tc);
-                        const float spread = 1.0f / (dn * tc * (dn + tc));
-                        const float inv_area = 2.0f / sqrtf(dot(nc, nc));
-                        const float value =
-                            A.lam4pi2_over_cell2 * (W.length * nw_ * PI_F / (float)A.ns) * J * pw * spread * inv_area;
-                        atomicAdd(A.maps64 + mb + (unsigned long long)hits[c].tri, (double)value);
-                        ++c_dep;
-                    }
-                }
-            } else {
-            // plane crossing and cell (as the tracer's deposit)
-            const float tc = (A.zm - v.z) / ks.z;
-            bool dep = false;
-            if (ks.z != 0.0f && tc > 1e-9f) {
-                const float px = v.x + tc * ks.x, py = v.y + tc * ks.y;
-                float ux = (px - A.x0) * A.inv_cell, uy = (py - A.y0) * A.inv_cell;
-                if (A.bilinear) {
-                    ux -= 0.5f;
-                    uy -= 0.5f;
-                    if (ux >= -1.0f && ux < (float)A.nx && uy >= -1.0f && uy < (float)A.ny) {
-                        const float flx = floorf(ux), fly = floorf(uy);
-                        cxi = (int)flx;
-                        cyi = (int)fly;
-                        fx = ux - flx;
-                        fy = uy - fly;
-                        dep = true;
-                    }
-                } else if (ux >= 0.0f && ux < (float)A.nx && uy >= 0.0f && uy < (float)A.ny) {
-                    cxi = (int)ux;
-                    cyi = (int)uy;
-                    dep = true;
-                }
-            }
-            if (dep) {
-                ++c_seg;
-                const float vm = fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)));
-                const float eps = fmaxf(1.0f, vm) * 0x1p-16f;
-                const f3 si = d * (1.0f / dn);
-                // the two visibility queries through one (rolled) call site: source -> v, v -> plane
-                code = 0;
-#pragma unroll 1
-                for (int q = 0; q < 2; ++q) {
-                    const bool blk = segment_blocked(A, q ? v : s, q ? ks : si, eps, q ? tc : dn - eps, W.tri0, W.trin,
-                                                     c_nodes, c_tris, overflow);
-                    if (blk) code |= 1 << q;
-                }
-                if (code == 0) {
-                    // weighting factor |dt/dx x dt/dphi| (hand-derived): with a = (v - s).e,
-                    // d cb/dx = sb^2/dn, d sb/dx = -sb cb/dn, so
-                    // dk/dx = (sb/dn)(sb e - cb u), dk/dphi = sb (-sin phi t0 + cos phi n0),
-                    // dtc/dq = -(dv_z/dq + tc dk_z/dq)/k_z, dt/dq = dv/dq + dtc/dq k + tc dk/dq.
-                    const f3 dkx = (e * sb - u * cb) * (sb / dn);
-                    const f3 dkp{sb * (cp * n0.x - sp * t0.x), sb * (cp * n0.y - sp * t0.y),
-                                 sb * (cp * n0.z - sp * t0.z)};
-                    const float dtcx = -(e.z + tc * dkx.z) / ks.z;
-                    const float dtcp = -(tc * dkp.z) / ks.z;
-                    const float txx = e.x + dtcx * ks.x + tc * dkx.x, txy = e.y + dtcx * ks.y + tc * dkx.y;
-                    const float tpx = dtcp * ks.x + tc * dkp.x, tpy = dtcp * ks.y + tc * dkp.y;
-                    const float J = fabsf(txx * tpy - txy * tpx);
-                    // UTD (Eq. diffracted-field): angles from the 0-face, phi of the sample
-                    const float nw_ = W.n;
-                    const float phi = u2 * nw_ * PI_F;
-                    const float sobs = tc;
-                    const float pw = diffracted_power(A, T, s, v, e, n0, nn, t0, m0, mn, nw_, phi, sb, si, dn, sobs);
-                    const float spread = 1.0f / (dn * sobs * (dn + sobs));
-                    const float value = A.lam4pi2_over_cell2 * (W.length * nw_ * PI_F / (float)A.ns) * J * pw * spread;
-                    const unsigned long long mb = (unsigned long long)txi * A.ncell;
-                    if (A.bilinear) {
-                        for (int cn = 0; cn < 4; ++cn) {
-                            const int a = cn & 1, b = cn >> 1;
-                            const int xx = cxi + a, yy = cyi + b;
-                            if (xx < 0 || xx >= A.nx || yy < 0 || yy >= A.ny) continue;
-                            const float wgt = (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy);
-                            atomicAdd(A.maps64 + mb + (unsigned long long)yy * A.nx + xx, (double)(value * wgt));
-                        }
-                    } else {
-                        atomicAdd(A.maps64 + mb + (unsigned long long)cyi * A.nx + cxi, (double)value);
-                    }
+                for (int c = 0; c < nh; ++c) {
+                    const float tc = hits[c].t;
+                    if (segment_blocked(A, v, ks, eps, tc, W.tri0, W.trin, c_nodes, c_tris, overflow)) continue;
+                    // weighting factor on the plane n.(t - a) = 0: dtc/dq = -(n.dv/dq + tc n.dk/dq) / (n.k)
+                    const f3 nc = hits[c].nrm;
+                    const float nk = dot(nc, ks);
+                    if (nk == 0.0f) continue;
+                    const float dtcx = -(dot(nc, e) + tc * dot(nc, dkx)) / nk;
+                    const float dtcp = -(tc * dot(nc, dkp)) / nk;
+                    const f3 tx = e + ks * dtcx + dkx * tc;
+                    const f3 tp = ks * dtcp + dkp * tc;
+                    const f3 cr = cross(tx, tp);
+                    const float J = sqrtf(dot(cr, cr));
+                    const float pw = diffracted_power(A, T, s, v, e, n0, nn, t0, m0, mn, nw_, phi, sb, si, dn, tc);
+                    const float spread = 1.0f / (dn * tc * (dn + tc));
+                    const float inv_area = 2.0f / sqrtf(dot(nc, nc));
+                    const float value =
+                        A.lam4pi2_over_cell2 * (W.length * nw_ * PI_F / (float)A.ns) * J * pw * spread * inv_area;
+                    atomicAdd(A.maps64 + mb + (unsigned long long)hits[c].tri, (double)value);
                     ++c_dep;
                 }
-            } else {
-                cxi = cyi = NO_CELL;
-            }
             }
         }
-        if (rec) {
-            rec->prim = code;
-            rec->ix = code == -2 ? NO_CELL : cxi;
-            rec->iy = code == -2 ? NO_CELL : cyi;
-            rec->decision = 0;
-        }
+        // records {bits: 1 incident blocked, -2 source behind both faces; crossings found; 0; 0}
+        put_record(A, w, code, nh, 0);
     }
-    if (overflow) atomicOr(&A.scratch->status, 1);
-    if (xlimit) atomicOr(&A.scratch->status, 2);
     const unsigned v[6] = {c_rays, c_seg, c_nodes, c_tris, c_dep, 0u};
-    for (int j = 0; j < 6; ++j) {
-        const unsigned sum = __reduce_add_sync(0xffffffffu, v[j]);
-        if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&s_cnt[j], (unsigned long long)sum);
-    }
-    __syncthreads();
-    if (threadIdx.x < 6 && s_cnt[threadIdx.x]) atomicAdd(&A.scratch->cnt[threadIdx.x], s_cnt[threadIdx.x]);
+    flush_counters(A, s_cnt, v, overflow, xlimit);
 }
 
 }  // namespace
@@ -553,8 +739,8 @@ cudaError_t launch_diffraction(const DiffArgs& a, int block, cudaStream_t s, int
     if (block <= 0 || block > 256 || (block & 31)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, occ = 0;
     cudaError_t err;
-    const void* k = mesh ? reinterpret_cast<const void*>(&k_diffraction<true>)
-                         : reinterpret_cast<const void*>(&k_diffraction<false>);
+    const void* k = mesh ? reinterpret_cast<const void*>(&k_diffraction_mesh)
+                         : reinterpret_cast<const void*>(&k_diffraction_plane);
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
     if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, 0)) != cudaSuccess)
