@@ -407,6 +407,13 @@ def random_txs(scene: Scene, seed: int, n: int, half: float, hmin: float, hmax: 
     return [Tx(pos=tuple(p), num_rays=int(c), seed=1000 + i) for i, (p, c) in enumerate(zip(out, counts))]
 
 
+def city_transmitters(scene: Scene, n: int, num_rays: int = 100_000_000):
+    """The city workload's transmitters (seed 50, heights U(10, 50) m, outside every
+    footprint of the 3.8 km square), n of them: the first 16 of any n >= 16 are the
+    workload's 16, so n = 16 N gives N disjoint 16-transmitter workloads."""
+    return random_txs(scene, 50, n, 1900.0, 10.0, 50.0, num_rays=num_rays)
+
+
 def perturb_materials(mats: np.ndarray, seed: int) -> np.ndarray:
     """Target materials: eps_r * (1 + 0.2 U(-1, 1)), sigma * exp(0.5 N(0, 1)).
 
@@ -479,7 +486,7 @@ def workload(cfg: int):
         return sc, txs, p
     if cfg == 5:
         sc = procedural_city(5)
-        txs = random_txs(sc, 50, 16, 1900.0, 10.0, 50.0, num_rays=100_000_000)
+        txs = city_transmitters(sc, 16)
         p = TraceParams(28e9, 8, cell_size=2.0, nx=2048, ny=2048)
         return sc, txs, p
     raise ValueError(f"unknown workload {cfg}")

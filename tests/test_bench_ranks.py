@@ -1,7 +1,7 @@
-"""The benchmark's multi-rank bookkeeping on CPU (gloo, world size 2): the
-city's transmitters split over the ranks cover each transmitter once, and the
-whole-job figures take the slowest rank's time and the sum of every rank's
-segments and copied bytes."""
+"""The benchmark's multi-rank bookkeeping on CPU (gloo, world size 2): every
+rank's workload is a distinct 16-transmitter city workload, and the whole-job
+figures take the slowest rank's time and the sum of every rank's segments and
+copied bytes."""
 import os
 import socket
 
@@ -42,9 +42,16 @@ def test_over_ranks_max_time_and_summed_counts(tmp_path):
     assert got[3] == 2.0 ** 41 + 1                          # byte counts stay exact in FP64
 
 
-def test_transmitter_split_covers_each_once():
+def test_rank_workloads_are_disjoint_and_extend_the_city():
+    """Weak scaling: rank r of N traces transmitters 16 r .. 16 r + 15 of one
+    seeded draw of 16 N; the first 16 are the one-GPU city workload's, and no
+    two ranks share a transmitter position or random stream."""
     from synth import scenes as S
-    _, txs, _ = S.workload(5)
-    for world in (1, 2, 3, 4, 8, 16):
-        seen = [id(t) for r in range(world) for t in txs[r::world]]
-        assert sorted(seen) == sorted(id(t) for t in txs)
+    sc, txs, _ = S.workload(5)
+    for world in (1, 2, 4, 8):
+        draw = S.city_transmitters(sc, 16 * world)
+        ranks = [draw[16 * r:16 * (r + 1)] for r in range(world)]
+        assert all(len(rk) == 16 for rk in ranks)
+        assert [t.pos for t in ranks[0]] == [t.pos for t in txs]
+        assert [t.seed for t in ranks[0]] == [t.seed for t in txs]
+        assert len({t.pos for t in draw}) == 16 * world and len({t.seed for t in draw}) == 16 * world
