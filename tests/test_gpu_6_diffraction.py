@@ -176,3 +176,34 @@ def test_diffraction_parity_city_wedge_subset(orc, api):
     assert (rec[:, 0] == 0).sum() > 200 and (rec[:, 0] > 0).sum() > 1000   # visible and blocked samples
     compare_diffraction(orc, sc, tx, p, ns, r["maps"][0].cpu().numpy(), rec, wedge_index=idx)
     gs.free()
+
+
+@pytest.mark.parametrize("nsel,ns,ntx", [(0, 16, 1), (1, 1, 1), (1, 3, 1), (7, 5, 1), (13, 37, 2), (41, 129, 3)])
+def test_diffraction_ragged_sizes(orc, api, nsel, ns, ntx):
+    """Totals that fill no warp, or leave ragged tails of the kernel's 32-sample
+    batches and 128-sample queue chunks (ntx * nsel * ns = 0, 1, 3, 35, 962,
+    15867), and several transmitters in one launch: the records and maps of
+    every transmitter replay against the oracle; no wedges give empty maps."""
+    from paper_2504_21719_b300 import _lib as L
+    sc, txs, p = S.workload(2)
+    p.nx = p.ny = 256
+    p.cell_size = 2.0
+    gs = api.Scene.from_obj(sc)
+    w, nw = gs.wedges()
+    ref = _wedge_array(w, nw)
+    # wedges near the first transmitter, so that some samples are lit and visible
+    near = np.argsort(np.linalg.norm(ref[:, :2] - np.asarray(txs[0].pos[:2]), axis=1))
+    idx = np.random.default_rng(nsel).permutation(near[:200])[:nsel]
+    sub = (L.rm_wedge * max(nsel, 1))(*[w[int(i)] for i in idx])
+    tl = [txs[0], S.Tx(pos=(-75.0, 32.0, 12.0), num_rays=1, pol=1), S.Tx(pos=(40.0, -90.0, 25.0), num_rays=1)][:ntx]
+    r = api.diffraction_map(gs, tl, p, ns, wedges=(sub, nsel), record=True)
+    torch.cuda.synchronize()
+    assert r["stats"]["rays"] == ntx * nsel * ns
+    maps = r["maps"].cpu().numpy()
+    if nsel == 0:
+        assert not maps.any()
+    else:
+        rec = r["record"].cpu().numpy().reshape(ntx, nsel * ns, 4)
+        for k, t in enumerate(tl):
+            compare_diffraction(orc, sc, t, p, ns, maps[k], rec[k], wedge_index=idx)
+    gs.free()
