@@ -709,7 +709,14 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
     const bool debug = record != nullptr || (p->flags & RM_STATS);
     const bool record_hits = hits && !adjoint && !debug;
     size_t o_mat, o_tx, o_m64 = 0;
-    const size_t bytes = adjoint ? table_bytes(P, &o_mat, &o_tx) : block_bytes_with_maps64(P, &o_mat, &o_tx, &o_m64);
+    size_t bytes = adjoint ? table_bytes(P, &o_mat, &o_tx) : block_bytes_with_maps64(P, &o_mat, &o_tx, &o_m64);
+    // transmitters with synthetic arrays: alpha of every work item from a pre-pass (8 B per
+    // ray, up to 2^31 rays per call; beyond that the tracer evaluates it at each launch)
+    bool arrays = false;
+    for (const TxDev& t : P.tx) arrays = arrays || t.n_ant > 0;
+    const bool pre_alpha = arrays && P.a.total > 0 && P.a.total <= (1ULL << 31);
+    const size_t o_alpha = align256(bytes);
+    if (pre_alpha) bytes = o_alpha + sizeof(float2) * (size_t)P.a.total;
     cudaEvent_t ev[2];
     RM_CUDA(timing_events(ev));
     char* hst = nullptr;
@@ -737,8 +744,11 @@ rm_status run_trace(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_t
         P.a.dLdC = dLdC;
         P.a.record = record;
         P.a.hits = hits;
+        if (pre_alpha) P.a.alpha = reinterpret_cast<const float2*>(dev + o_alpha);
         if (P.a.total > 0) {
             if ((e = cudaEventRecord(ev[0], S(stream))) != cudaSuccess) break;
+            if (pre_alpha && (e = launch_alpha(P.a, reinterpret_cast<float2*>(dev + o_alpha), S(stream))) != cudaSuccess)
+                break;
             if ((e = launch_trace(P.a, P.npol, debug, P.bilinear, adjoint, P.diffuse, P.block, P.bps, S(stream), &grid,
                                   P.mesh, record_hits)) != cudaSuccess)
                 break;

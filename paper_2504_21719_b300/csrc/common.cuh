@@ -107,6 +107,10 @@ struct TraceArgs {
     // coalesce.  The recording forward writes it, the adjoint replays it instead of
     // traversing (a slot outside the scene falls back to the traversal)
     int32_t* hits;
+    // optional [total] synthetic-array factor alpha of every work item's ray (transmitters
+    // with arrays only), written by k_alpha before the tracer; null: the tracer evaluates
+    // alpha at each ray's launch
+    const float2* alpha;
     // mesh measurement surface (forward only): its LBVH and leaf records; the
     // maps are then [ntx][surface triangles] and the plane fields are unused
     const float4* snodes;
@@ -205,6 +209,8 @@ cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t n
 cudaError_t launch_db_mse(const float* maps, const float* target, int64_t n, float floor_lin,
                           double* acc_dev, float* loss, float* dLdC, int64_t* valid, cudaStream_t s);
 cudaError_t launch_fill_record(rm_segment_record* rec, unsigned long long n, cudaStream_t s);
+// alpha[w] for every work item w of a transmitter with a synthetic array (trace.cu)
+cudaError_t launch_alpha(const TraceArgs& a, float2* alpha, cudaStream_t s);
 cudaError_t launch_map_to_f32(const double* m64, float* m, unsigned long long n, cudaStream_t s);
 cudaError_t launch_grad_out(const double* grad, int nm, int ntx, float* d_eps, float* d_sigma, float* d_tx,
                             cudaStream_t s);

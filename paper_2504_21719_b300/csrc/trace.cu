@@ -687,6 +687,61 @@ __device__ __noinline__ unsigned surface_crossings(const float4* __restrict__ no
     }
 }
 
+// ------------------------------------------------------------------ work items
+// Transmitter of work item w (the transmitters' work_begin ascending).
+__device__ __forceinline__ int work_tx(const TxDev* tx, int ntx, unsigned long long w) {
+    int lo = 0, hi = ntx - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tx[mid].work_begin <= w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Lattice index n of work item w of transmitter T (and its position isub in
+// T's subset).  Neighbouring work items visit neighbouring lattice directions:
+// i = j * F mod count with F a Fibonacci number (lattice neighbour step).
+__device__ __forceinline__ unsigned long long work_lattice(const TxDev& T, unsigned long long w,
+                                                          unsigned long long& isub) {
+    isub = w - T.work_begin;
+    if (T.perm > 1ULL) {
+        // (isub * perm) mod count by Barrett reduction (isub, perm < count,
+        // product < 2^63): the estimate q is at most 2 below the quotient
+        const unsigned long long xp = isub * T.perm;
+        const unsigned long long q = __umul64hi(xp, T.perm_m);
+        unsigned long long rr = xp - q * T.count;
+        if (rr >= T.count) rr -= T.count;
+        if (rr >= T.count) rr -= T.count;
+        isub = rr;
+    }
+    return T.begin + isub * T.stride;
+}
+
+// The synthetic-array factor of every work item's ray before the tracer runs
+// (transmitters with arrays only): the tracer's own arithmetic (four unrolled
+// Horner chains instead of two rolled ones, the same bits), evaluated here by
+// full warps at the occupancy of a small kernel instead of inside the
+// tracer's ray launch, where its chains run beside the tracer's divergent loop.
+__global__ void __launch_bounds__(256) k_alpha(const TraceArgs A, float2* __restrict__ alpha) {
+    __shared__ TxDev s_tx[RM_MAX_TX];
+    {
+        const int ntw = A.ntx * (int)(sizeof(TxDev) / 4);
+        for (int i = threadIdx.x; i < ntw; i += blockDim.x)
+            reinterpret_cast<int*>(s_tx)[i] = reinterpret_cast<const int*>(A.tx)[i];
+    }
+    __syncthreads();
+    for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < A.total;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        const TxDev& T = s_tx[work_tx(s_tx, A.ntx, w)];
+        if (T.n_ant <= 0) continue;
+        unsigned long long isub;
+        const unsigned long long n = work_lattice(T, w, isub);
+        float are, aim;
+        array_factor_lattice_wide(T, A.ant, n, are, aim);
+        alpha[w] = make_float2(are, aim);
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 constexpr int NGRAD = 2 * RM_MAX_MATERIALS + 3 * RM_MAX_TX;
 constexpr int MAXSLOT = RM_MAX_DEPTH;
@@ -770,29 +825,10 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                     if (rk < rem) w = qb + rk;
                     else if (got_chunk && b + (rk - rem) < ce) w = b + (rk - rem);
                     if (w < A.total) {
-                        // transmitter of item w (work_begin ascending)
-                        int lo = 0, hi = A.ntx - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (s_tx[mid].work_begin <= w) lo = mid; else hi = mid - 1;
-                        }
-                        txi = lo;
+                        txi = work_tx(s_tx, A.ntx, w);
                         const TxDev& T = s_tx[txi];
-                        // neighbouring work items visit neighbouring lattice directions:
-                        // i = j * F mod count with F a Fibonacci number (lattice neighbour step)
-                        isub = w - T.work_begin;
                         witem = w;
-                        if (T.perm > 1ULL) {
-                            // (isub * perm) mod count by Barrett reduction (isub, perm < count,
-                            // product < 2^63): the estimate q is at most 2 below the quotient
-                            const unsigned long long xp = isub * T.perm;
-                            const unsigned long long q = __umul64hi(xp, T.perm_m);
-                            unsigned long long rr = xp - q * T.count;
-                            if (rr >= T.count) rr -= T.count;
-                            if (rr >= T.count) rr -= T.count;
-                            isub = rr;
-                        }
-                        n = T.begin + isub * T.stride;
+                        n = work_lattice(T, w, isub);
                         // Fibonacci lattice (Sec. 3.1.1): cos theta = 1 - 2n/(N-1),
                         // sin theta = 2 sqrt(n (N-1-n)) / (N-1), phi = 2 pi frac(n (phi_g - 1))
                         float ct, st, sp, cp;
@@ -821,7 +857,15 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                         // synthetic array (Sec. 4.4): alpha = sum_k u_P,k exp(j k0 k.d_k) at the
                         // lattice direction rebuilt in double-float (array.cuh)
                         float are = 1.0f, aim = 0.0f;
-                        if (T.n_ant > 0) array_factor_lattice(T, A.ant, n, are, aim);
+                        if (T.n_ant > 0) {
+                            if (A.alpha) {
+                                const float2 al = A.alpha[w];
+                                are = al.x;
+                                aim = al.y;
+                            } else {
+                                array_factor_lattice(T, A.ant, n, are, aim);
+                            }
+                        }
                         for (int p = 0; p < NPOL; ++p) {
                             const int pol = (NPOL == 2) ? p : T.pol;
                             const f3 e = pol == 0 ? th_l : ph_l;
@@ -1355,6 +1399,19 @@ cudaError_t launch_fresnel_probe(const MatDev& m, const float* cos1, long long n
     if (n <= 0) return cudaSuccess;
     const long long blocks = std::min<long long>((n + 255) / 256, 148LL * 8);
     k_fresnel_probe<<<(unsigned)blocks, 256, 0, s>>>(m, cos1, n, wR, wT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alpha(const TraceArgs& a, float2* alpha, cudaStream_t s) {
+    if (a.total == 0) return cudaSuccess;
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t err;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_alpha, 256, 0)) != cudaSuccess) return err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const unsigned long long need = (a.total + 255) / 256, cap = (unsigned long long)occ * sms;
+    k_alpha<<<(unsigned)(need < cap ? need : cap), 256, 0, s>>>(a, alpha);
     return cudaGetLastError();
 }
 
