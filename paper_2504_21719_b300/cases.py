@@ -14,6 +14,9 @@ CASE is one of
                (as the benchmark); --rays sets the lattice stride of every transmitter
                (default 1: the full workload)
   mesh         the Manhattan trace on a 131072-triangle terrain measurement surface
+  array        the timing study's street canyon (depth 5, 3.5 GHz) from one transmitter with
+               a 1024-element uniform linear array, 1e7 rays (the array factor's pre-pass
+               kernel, then the tracer)
 Each case runs in the launch shape the tuning table holds for its workload
 class on this GPU (the benchmark's shape) and prints one line: case, kernel
 ms of the last call, and its work counters.
@@ -33,7 +36,7 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction", "city", "city_adjoint",
-                                    "batched", "mesh"])
+                                    "batched", "mesh", "array"])
     ap.add_argument("--rays", type=int, default=0, help="rays per TX (trace cases) or samples per wedge")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--builder", default="auto", choices=["auto", "lbvh", "sah"], help="the scene's BVH builder")
@@ -49,6 +52,11 @@ def main(argv=None):
         sc, txs, p = S.workload(5)
         txs = txs[:1]
         txs[0].num_rays = 10_000_000
+    elif a.case == "array":
+        sc = S.street_canyon()
+        p = S.TraceParams(3.5e9, 5, cell_size=1.0, nx=256, ny=256)
+        txs = [S.Tx(pos=(0.0, 0.0, 20.0), num_rays=10_000_000, seed=11)]
+        txs[0].ant_pos, txs[0].precoding = S.uniform_linear_array(1024, p.freq_hz, 0.5)
     elif a.case == "batched":
         sc, txs, p = S.workload(3)
         for t in txs:
@@ -59,7 +67,8 @@ def main(argv=None):
         txs[0].num_rays = a.rays
     from .autotune import lookup
     cls = {"manhattan": "manhattan", "diffuse": "diffuse", "adjoint": "adjoint", "diffraction": "diffraction",
-           "city": "city", "city_adjoint": "city_adjoint", "batched": "batched", "mesh": "manhattan"}[a.case]
+           "city": "city", "city_adjoint": "city_adjoint", "batched": "batched", "mesh": "manhattan",
+           "array": "manhattan"}[a.case]
     if a.replay and a.case in ("adjoint", "city_adjoint"):
         cls += "_replay"
     blk, bps, qch, rfm = lookup(torch.cuda.get_device_name(0), cls)
