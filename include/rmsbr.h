@@ -118,7 +118,11 @@ typedef struct {
      * alpha = sum_k u_P,k exp(j 2 pi / lambda0 k.d_k) (array response vector,
      * Eq. path-solver-array-response-vector), evaluated at the ray's lattice
      * direction in double-float arithmetic; elements on one regular line
-     * (uniform linear arrays) take a blocked Horner recurrence.
+     * (uniform linear arrays) take a blocked Horner recurrence.  Trace and
+     * gradient calls evaluate alpha for every ray in a pre-pass kernel before
+     * the tracer (8 B of call-owned device memory per ray, up to 2^31 rays per
+     * call); graph plans, the no-allocation entry point and larger calls
+     * evaluate it at each ray's launch, with the same bits.
      * n_ant = 0: one antenna.  The host arrays are read during the call only. */
     int32_t n_ant;
     int32_t reserved;
