@@ -541,6 +541,20 @@ rm_status rm_debug_inject(int32_t kind, int32_t count);
 rm_status rm_debug_fresnel_probe(const rm_material* mat, double freq_hz, const float* cos1_dev, int64_t n,
                                  float* wR_dev, float* wT_dev, void* stream);
 
+/* The synthetic-array factor alpha (see rm_tx.n_ant) of every work item of
+ * the call (the transmitters' ray subsets in order, the tracer's work-item
+ * order), from the pre-pass kernel of trace and gradient calls into
+ * alpha_prepass_dev and from the tracer's inline form (graph plans, the
+ * no-allocation entry point) into alpha_inline_dev, both [len][2] floats (re,
+ * im) owned by the caller; entries of transmitters without an array are not
+ * written.  Lets a test check that the two forms agree bit for bit.  No
+ * counterpart in the paper (a test aid).  Synchronises `stream`; RM_EINVAL for
+ * NULL buffers, len below the number of work items, or the arguments
+ * rm_radio_map_trace rejects. */
+rm_status rm_debug_array_factor(const rm_scene* scene, const rm_tx* tx_host, int32_t ntx,
+                                const rm_trace_params* params, float* alpha_prepass_dev, float* alpha_inline_dev,
+                                uint64_t len, void* stream);
+
 /* Number of device and pinned-host allocation calls (cudaMalloc,
  * cudaMallocAsync, cudaHostAlloc) the library has made in this process since
  * it was loaded: tests read it before and after a call to check whether that

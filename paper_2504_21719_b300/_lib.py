@@ -88,6 +88,7 @@ _SIGS = {
     "rm_radio_map_grad_mesh_hits": ([P, P, P, C.c_int32, P, P, P, C.c_uint64, P, P, P, P, P, P, P], C.c_int),
     "rm_radio_map_grad_mesh": ([P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P], C.c_int),
     "rm_radio_map_trace_noalloc": ([P, P, C.c_int32, P, P, P, P], C.c_int),
+    "rm_debug_array_factor": ([P, P, C.c_int32, P, P, P, C.c_uint64, P], C.c_int),
     "rm_db_mse_loss": ([P, P, C.c_int64, C.c_float, P, P, P, P], C.c_int),
     "rm_trace_plan_create": ([P, P, C.c_int32, P, P, P, C.POINTER(P)], C.c_int),
     "rm_trace_plan_launch": ([P, P], C.c_int),

@@ -809,6 +809,35 @@ rm_status rm_debug_fresnel_probe(const rm_material* mat, double freq_hz, const f
     return RM_OK;
 }
 
+rm_status rm_debug_array_factor(const rm_scene* sc, const rm_tx* tx, int32_t ntx, const rm_trace_params* p,
+                                float* alpha_prepass_dev, float* alpha_inline_dev, uint64_t len, void* stream) {
+    rm_status st = validate(sc, tx, ntx, p);
+    if (st != RM_OK) return st;
+    if ((st = check_device(sc)) != RM_OK) return st;
+    if (!alpha_prepass_dev || !alpha_inline_dev) return fail(RM_EINVAL, "NULL alpha buffer");
+    Prepared P;
+    prepare(sc, tx, ntx, p, nullptr, &P);
+    if (len < P.a.total) return fail(RM_EINVAL, "len is below the number of work items (sum of ray counts)");
+    size_t o_mat, o_tx;
+    const size_t tab = table_bytes(P, &o_mat, &o_tx);
+    char* hst = nullptr;
+    RM_CUDA(staging(tab, &hst));
+    const size_t used = write_tables(P, o_mat, o_tx, hst);
+    char* dev = nullptr;
+    RM_CUDA(device_block(tab, &dev));
+    P.a.mats = reinterpret_cast<const MatDev*>(dev + o_mat);
+    P.a.tx = reinterpret_cast<const TxDev*>(dev + o_tx);
+    P.a.ant = reinterpret_cast<const AntDev*>(dev + ant_offset(P, o_tx));
+    P.a.scratch = reinterpret_cast<Scratch*>(dev);
+    cudaError_t e = cudaMemcpyAsync(dev, hst, used, cudaMemcpyHostToDevice, S(stream));
+    if (e == cudaSuccess) e = launch_alpha(P.a, reinterpret_cast<float2*>(alpha_prepass_dev), S(stream), true);
+    if (e == cudaSuccess) e = launch_alpha(P.a, reinterpret_cast<float2*>(alpha_inline_dev), S(stream), false);
+    const cudaError_t e2 = cudaStreamSynchronize(S(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rm_debug_array_factor");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize");
+    return RM_OK;
+}
+
 const char* rm_version(void) { return "rmsbr 0.1 (sm_103a)"; }
 
 rm_status rm_scene_upload(const float* verts_dev, int64_t nv, const int32_t* tris_dev, int64_t nt,

@@ -209,8 +209,9 @@ cudaError_t check_indices(const int32_t* tris, const int32_t* tri_mat, int64_t n
 cudaError_t launch_db_mse(const float* maps, const float* target, int64_t n, float floor_lin,
                           double* acc_dev, float* loss, float* dLdC, int64_t* valid, cudaStream_t s);
 cudaError_t launch_fill_record(rm_segment_record* rec, unsigned long long n, cudaStream_t s);
-// alpha[w] for every work item w of a transmitter with a synthetic array (trace.cu)
-cudaError_t launch_alpha(const TraceArgs& a, float2* alpha, cudaStream_t s);
+// alpha[w] for every work item w of a transmitter with a synthetic array (trace.cu);
+// wide = false: the tracer's inline form (debug comparison)
+cudaError_t launch_alpha(const TraceArgs& a, float2* alpha, cudaStream_t s, bool wide = true);
 cudaError_t launch_map_to_f32(const double* m64, float* m, unsigned long long n, cudaStream_t s);
 cudaError_t launch_grad_out(const double* grad, int nm, int ntx, float* d_eps, float* d_sigma, float* d_tx,
                             cudaStream_t s);

@@ -722,6 +722,9 @@ __device__ __forceinline__ unsigned long long work_lattice(const TxDev& T, unsig
 // Horner chains instead of two rolled ones, the same bits), evaluated here by
 // full warps at the occupancy of a small kernel instead of inside the
 // tracer's ray launch, where its chains run beside the tracer's divergent loop.
+// (WIDE = false: the tracer's inline two-chain form, for the debug comparison
+// of the two forms.)
+template <bool WIDE>
 __global__ void __launch_bounds__(256) k_alpha(const TraceArgs A, float2* __restrict__ alpha) {
     __shared__ TxDev s_tx[RM_MAX_TX];
     {
@@ -737,7 +740,8 @@ __global__ void __launch_bounds__(256) k_alpha(const TraceArgs A, float2* __rest
         unsigned long long isub;
         const unsigned long long n = work_lattice(T, w, isub);
         float are, aim;
-        array_factor_lattice_wide(T, A.ant, n, are, aim);
+        if (WIDE) array_factor_lattice_wide(T, A.ant, n, are, aim);
+        else array_factor_lattice(T, A.ant, n, are, aim);
         alpha[w] = make_float2(are, aim);
     }
 }
@@ -1402,17 +1406,18 @@ cudaError_t launch_fresnel_probe(const MatDev& m, const float* cos1, long long n
     return cudaGetLastError();
 }
 
-cudaError_t launch_alpha(const TraceArgs& a, float2* alpha, cudaStream_t s) {
+cudaError_t launch_alpha(const TraceArgs& a, float2* alpha, cudaStream_t s, bool wide) {
     if (a.total == 0) return cudaSuccess;
     int dev = 0, sms = 0, occ = 0;
     cudaError_t err;
+    const void* k = wide ? reinterpret_cast<const void*>(&k_alpha<true>) : reinterpret_cast<const void*>(&k_alpha<false>);
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_alpha, 256, 0)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, 0)) != cudaSuccess) return err;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const unsigned long long need = (a.total + 255) / 256, cap = (unsigned long long)occ * sms;
-    k_alpha<<<(unsigned)(need < cap ? need : cap), 256, 0, s>>>(a, alpha);
-    return cudaGetLastError();
+    void* args[] = {const_cast<TraceArgs*>(&a), &alpha};
+    return cudaLaunchKernel(k, dim3((unsigned)(need < cap ? need : cap)), dim3(256), args, 0, s);
 }
 
 int max_blocks_per_sm(int npol, bool debug, bool bilinear, bool adjoint, bool diffuse, int block, bool mesh,

@@ -136,3 +136,47 @@ def test_city_roulette_array_dual_pol(orc, api):
     info = compare_maps(orc, sc, tx, p, m, rec)
     assert info["cells"] > 100
     assert info["frac_within_rtol"] >= 0.99, info
+
+
+def test_array_factor_prepass_equals_inline(api):
+    """The array factor that trace and gradient calls take from the pre-pass
+    kernel (four unrolled Horner chains) equals, bit for bit, the tracer's
+    inline form (two rolled chains; graph plans and the no-allocation entry
+    point), for every work item of one call mixing a 1024-element and a
+    37-element (ragged) steered uniform linear array, a 48-element irregular
+    array and a transmitter without an array (whose entries stay unwritten)."""
+    import ctypes as C
+    from paper_2504_21719_b300 import _lib as L
+    sc, txs, p = S.workload(2)
+    base = txs[0]
+    tl = []
+    for k, (na, steer) in enumerate([(1024, (0.3, 1.0, -0.2)), (37, (1.0, 0.2, 0.1)), (48, None), (0, None)]):
+        t = copy.copy(base)
+        t.ray_stride, t.ray_begin = 97 + 2 * k, k
+        t.yaw = 0.3 * k
+        if na and steer is not None:
+            t.ant_pos, t.precoding = S.uniform_linear_array(na, p.freq_hz, 0.5, axis=k % 3, steer=steer)
+        elif na:
+            rng = np.random.default_rng(12)
+            t.ant_pos = rng.uniform(-1.0, 1.0, size=(na, 3)) * np.array([1.0, 0.15, 0.15])
+            w = rng.normal(size=na) + 1j * rng.normal(size=na)
+            t.precoding = w / np.linalg.norm(w)
+        tl.append(t)
+    gs = api.Scene.from_obj(sc)
+    arr, ntx = api._tx_array(tl)
+    prm = api.params_from(p)
+    total = sum(t.count() for t in tl)
+    a = torch.full((total, 2), float("nan"), dtype=torch.float32, device="cuda")
+    b = torch.full((total, 2), float("nan"), dtype=torch.float32, device="cuda")
+    lib = L.load()
+    rc = lib.rm_debug_array_factor(gs.handle, arr, ntx, C.byref(prm), C.c_void_p(a.data_ptr()),
+                                   C.c_void_p(b.data_ptr()), total, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == L.RM_OK, lib.rm_last_error()
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+    n_arr = sum(t.count() for t in tl[:3])
+    assert torch.isfinite(a[:n_arr]).all() and torch.isnan(a[n_arr:]).all()
+    assert (a[:n_arr].abs().sum(1) > 0).all()
+    rc = lib.rm_debug_array_factor(gs.handle, arr, ntx, C.byref(prm), C.c_void_p(a.data_ptr()),
+                                   C.c_void_p(b.data_ptr()), total - 1, None)
+    assert rc == L.RM_EINVAL
+    gs.free()
