@@ -180,3 +180,27 @@ def test_array_factor_prepass_equals_inline(api):
                                    C.c_void_p(b.data_ptr()), total - 1, None)
     assert rc == L.RM_EINVAL
     gs.free()
+
+
+def test_array_above_prepass_limit_matches_halves(api):
+    """A call of more than 2^31 rays with a synthetic array evaluates the array
+    factor at each ray's launch instead of in the pre-pass (whose buffer holds
+    at most 2^31 rays); its map equals the sum of the maps of its two lattice
+    halves, each of which takes the pre-pass (depth 0 over a ground plane)."""
+    sc = S.ground_plane(500.0)
+    p = S.TraceParams(3.5e9, 0, reflect=False, refract=False, cell_size=10.0, nx=100, ny=100)
+    tx = S.Tx(pos=(0.0, 0.0, 10.0), num_rays=2 ** 31 + 1000, seed=5)
+    tx.ant_pos, tx.precoding = S.uniform_linear_array(16, p.freq_hz, 0.5, axis=0, steer=(0.4, 0.2, -0.9))
+    gs = api.Scene.from_obj(sc)
+    full = api.trace(gs, [tx], p)
+    assert full["stats"]["rays"] == tx.num_rays
+    parts = torch.zeros_like(full["maps"], dtype=torch.float64)
+    for b in range(2):
+        h = copy.copy(tx)
+        h.ray_begin, h.ray_stride = b, 2
+        parts += api.trace(gs, [h], p)["maps"].double()
+    fm = full["maps"].double()
+    mask = fm > 1e-15
+    assert mask.sum() > 5000
+    assert torch.all((parts - fm).abs()[mask] <= 2e-5 * fm[mask])
+    gs.free()
