@@ -14,6 +14,7 @@ CASE is one of
                (as the benchmark); --rays sets the lattice stride of every transmitter
                (default 1: the full workload)
   mesh         the Manhattan trace on a 131072-triangle terrain measurement surface
+  diffraction_mesh  the diffraction map onto the same terrain surface (1200 wedges)
   array        the timing study's street canyon (depth 5, 3.5 GHz) from one transmitter with
                a 1024-element uniform linear array, 1e7 rays (the array factor's pre-pass
                kernel, then the tracer)
@@ -36,13 +37,13 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["manhattan", "diffuse", "adjoint", "diffraction", "city", "city_adjoint",
-                                    "batched", "mesh", "array"])
+                                    "batched", "mesh", "array", "diffraction_mesh"])
     ap.add_argument("--rays", type=int, default=0, help="rays per TX (trace cases) or samples per wedge")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--builder", default="auto", choices=["auto", "lbvh", "sah"], help="the scene's BVH builder")
     ap.add_argument("--replay", action="store_true", help="adjoint cases: replay the forward's recorded hits")
     a = ap.parse_args(argv)
-    if a.case in ("manhattan", "diffuse", "diffraction", "mesh"):
+    if a.case in ("manhattan", "diffuse", "diffraction", "mesh", "diffraction_mesh"):
         sc, txs, p = S.workload(2)
         if a.case == "diffuse":
             sc = sc.with_scattering(0.5, 0.2, np.arange(sc.nm) % 3, 3, 2, 0.6)
@@ -63,22 +64,24 @@ def main(argv=None):
             t.ray_stride = max(1, a.rays)
     else:
         sc, txs, p = S.workload(4)
-    if a.rays and a.case not in ("diffraction", "batched"):
+    if a.rays and a.case not in ("diffraction", "diffraction_mesh", "batched"):
         txs[0].num_rays = a.rays
     from .autotune import lookup
     cls = {"manhattan": "manhattan", "diffuse": "diffuse", "adjoint": "adjoint", "diffraction": "diffraction",
            "city": "city", "city_adjoint": "city_adjoint", "batched": "batched", "mesh": "manhattan",
-           "array": "manhattan"}[a.case]
+           "array": "manhattan", "diffraction_mesh": "diffraction"}[a.case]
     if a.replay and a.case in ("adjoint", "city_adjoint"):
         cls += "_replay"
     blk, bps, qch, rfm = lookup(torch.cuda.get_device_name(0), cls)
     p = api.params_from(p, block_size=blk, blocks_per_sm=bps, queue_chunk=qch, refill_min=rfm)
     builder = "sah" if (a.case == "batched" and a.builder == "auto") else a.builder
     gs = api.Scene.from_obj(sc, builder=builder)
-    su = api.surface(*S.terrain_surface(256.0, 256)) if a.case == "mesh" else None
+    su = api.surface(*S.terrain_surface(256.0, 256)) if a.case in ("mesh", "diffraction_mesh") else None
     for _ in range(a.reps):
         if a.case == "mesh":
             r = api.trace_mesh(gs, su, txs, p)
+        elif a.case == "diffraction_mesh":
+            r = api.diffraction_map_mesh(gs, su, txs, p, a.rays or 4096)
         elif a.case == "diffraction":
             r = api.diffraction_map(gs, txs, p, a.rays or 4096)
         elif a.case in ("adjoint", "city_adjoint"):

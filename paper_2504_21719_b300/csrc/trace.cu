@@ -418,9 +418,9 @@ __device__ __forceinline__ Hit closest_hit(const float4* __restrict__ nodes, con
         // then prunes the traversal), a one-triangle tree, and the stack traversal
         // over internal nodes, whose hit leaf children are tested in their
         // parent's step.  Every triangle test goes through the single call site at
-        // the bottom of the loop, which keeps the kernel's code small (the diffuse
-        // and adjoint instantiations, whose longer shading otherwise crowds the
-        // instruction cache, use this form).
+        // the bottom of the loop, which keeps the kernel's code small (the diffuse,
+        // adjoint and mesh-surface instantiations, whose longer shading or second
+        // walk otherwise crowds the instruction cache, use this form).
         const int npre = nlarge + (nt == 1 ? 1 : 0);
         int stack[STACK_SIZE];
         int sp = 0;
@@ -918,9 +918,11 @@ __global__ void __launch_bounds__(MAX_BLOCK, 4) k_trace(const TraceArgs A) {
                 if (s == -1) replayed = true;
                 else if (s >= 0 && s < A.nt + A.nlarge) replayed = recorded_hit(A.tris, r, s, h);
             }
+            // the diffuse, adjoint and mesh-surface forms traverse through one triangle-test call site
+            // (their longer code otherwise crowds the instruction cache)
             if (!replayed)
-                h = closest_hit<DIFF || ADJ, DEBUG>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes, c_tris,
-                                                    overflow);
+                h = closest_hit<DIFF || ADJ || MESH, DEBUG>(A.nodes, A.tris, A.nt, A.nlarge, r, prev, c_nodes,
+                                                            c_tris, overflow);
             if ((DEBUG || HITS) && !ADJ && A.hits)
                 A.hits[(unsigned long long)depth * A.total + witem] = h.slot;
             ++c_seg;
