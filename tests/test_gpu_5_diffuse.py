@@ -134,3 +134,33 @@ def test_diffuse_city_sampled(orc, api):
     assert ((dec >= 0) & (dec & 3 == 2)).sum() > 40
     info = compare_maps(orc, sc, tx, p, m, rec)
     assert info["cells"] > 100
+
+
+def test_diffuse_city_adjoint_matches_oracle(orc, api):
+    """The adjoint with diffuse reflection on the largest scene: a sampled
+    lattice subset of one city transmitter (depth 8, bilinear cells, 0.97M
+    triangles), gradient of sum(g C) for a seeded g over the 2048 x 2048 map
+    against the oracle's dual numbers along the GPU's record (which the oracle
+    certifies first), the re-trace taking the forward's choices."""
+    sc, txs, p = S.workload(5)
+    sc = _diffuse(sc)
+    p.diffuse = True
+    p.deposit = 1
+    tx = copy.copy(txs[0])
+    tx.ray_stride, tx.ray_begin = 333_331, 7
+    gs = api.Scene.from_obj(sc)
+    f = api.trace(gs, [tx], p, record=True)
+    g = torch.tensor(np.random.default_rng(9).normal(size=(1, p.ny, p.nx)), dtype=torch.float32, device="cuda")
+    a = api.grad(gs, [tx], p, g, record=True)
+    assert torch.equal(f["record"], a["record"])
+    ad = np.concatenate([a["d_eps"].cpu().numpy(), a["d_sigma"].cpu().numpy(), a["d_tx"][0].cpu().numpy()])
+    rec = f["record"].view(tx.count(), p.max_depth + 1, 4).cpu().numpy()
+    assert ((rec[:, :, 3] >= 0) & (rec[:, :, 3] & 3 == 2)).sum() > 40
+    compare_maps(orc, sc, tx, p, f["maps"][0].cpu().numpy(), rec)
+    de, ds, dt = orc.grad(sc, tx, p, rec, g[0].double().cpu().numpy())
+    ref = np.concatenate([de, ds, dt])
+    assert np.abs(ref[:2 * sc.nm]).max() > 0
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    err = np.abs(ad - ref) / scale
+    assert np.all(err <= GRAD_RTOL), err
+    gs.free()
