@@ -562,15 +562,21 @@ def diffraction_map(scene, tx, params, samples_per_wedge: int, mode: str = "plai
 
 
 def diffraction_map_mesh(scene, tx, params, samples_per_wedge: int, surf_verts, surf_tris, mode: str = "plain",
-                         record=None, want_record: bool = False, slack: bool = False):
+                         record=None, want_record: bool = False, slack: bool = False, wedge_index=None):
     """Diffraction map on a mesh measurement surface: [n_surf] (float64).  Record
     [nw * N', 4] = {incident bit (-2 source behind both faces), crossings, 0, 0};
-    replay certifies the incident bit only."""
+    replay certifies the incident bit only.  ``wedge_index``: positions in
+    wedges(scene) of the wedges to sample (default: all); the record follows it."""
     v, t, m, mats = _scene_arrays(scene)
     sv = np.ascontiguousarray(surf_verts, np.float32)
     st_ = np.ascontiguousarray(surf_tris, np.int32)
     otx, op = make_tx(tx), make_params(params)
-    nw = len(wedges(scene))
+    sel = None
+    if wedge_index is not None:
+        sel = np.ascontiguousarray(wedge_index, np.int64)
+        nw = len(sel)
+    else:
+        nw = len(wedges(scene))
     n = nw * int(samples_per_wedge)
     rec = None
     if mode == "replay":
@@ -583,7 +589,7 @@ def diffraction_map_mesh(scene, tx, params, samples_per_wedge: int, surf_verts, 
     rc = lib().or_diffraction_map_mesh(_p(v), len(v), _p(t), len(t), _p(m), _p(mats), len(mats), C.byref(otx),
                                        C.byref(op), C.c_int64(int(samples_per_wedge)), _p(sv), _p(st_),
                                        C.c_int64(len(st_)), MODES[mode], _p(rec), C.c_int64(max(n, 1)), _p(mp),
-                                       _p(sl), C.byref(rep))
+                                       _p(sl), C.byref(rep), _p(sel), C.c_int64(0 if sel is None else len(sel)))
     if rc != 0:
         raise ValueError(f"or_diffraction_map_mesh failed ({rc})")
     out = {"map": mp, "wedges": nw}

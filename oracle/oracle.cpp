@@ -2882,11 +2882,22 @@ int or_diffraction_map(const float* verts, int64_t nv, const int32_t* tris, int6
 int or_diffraction_map_mesh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const int32_t* tri_mat,
                             const float* mats, int nm, const or_tx* tx, const or_params* P, int64_t samples_per_wedge,
                             const float* surf_verts, const int32_t* surf_tris, int64_t n_surf, int mode, int32_t* rec,
-                            int64_t rec_cap, double* map_out, double* slack_out, or_report* report) {
+                            int64_t rec_cap, double* map_out, double* slack_out, or_report* report,
+                            const int64_t* wsel, int64_t nsel) {
     if (samples_per_wedge < 1) return 1;
     Scene S = make_scene(verts, nv, tris, nt, tri_mat, mats, nm);
     const MeshSurface M = make_surface(surf_verts, surf_tris, n_surf);
-    const std::vector<Wedge> WS = find_wedges(S, verts, tris, nt);
+    std::vector<Wedge> WS = find_wedges(S, verts, tris, nt);
+    if (wsel) {
+        // a subset of the wedges, as or_diffraction_map takes it
+        std::vector<Wedge> sub;
+        sub.reserve(nsel > 0 ? (size_t)nsel : 0);
+        for (int64_t j = 0; j < nsel; ++j) {
+            if (wsel[j] < 0 || wsel[j] >= (int64_t)WS.size()) return 3;
+            sub.push_back(WS[wsel[j]]);
+        }
+        WS.swap(sub);
+    }
     const int64_t nw = (int64_t)WS.size(), NS = samples_per_wedge;
     if (rec && rec_cap < nw * NS) return 2;
     const double omega = 2.0 * PI * P->freq_hz, k0 = omega / C0;

@@ -167,14 +167,14 @@ def compare_mesh(orc, scene, tx, params, surf_v, surf_t, gpu_map, gpu_record, rt
 
 
 def compare_diffraction_mesh(orc, scene, tx, params, samples_per_wedge, surf_v, surf_t, gpu_map, gpu_record,
-                             rtol=MAP_RTOL, max_adopt_frac=MAX_ADOPT_FRAC):
+                             rtol=MAP_RTOL, max_adopt_frac=MAX_ADOPT_FRAC, wedge_index=None):
     """Replay the GPU's incident-visibility bits in the FP64 oracle's diffraction
     map on a mesh surface and compare cell by cell.  Crossings near a triangle's
     boundary, visibility near ties of the edge-to-crossing segments and a
     +-1e-5 rad Keller azimuth change are bounded by the oracle's per-cell slack."""
     rec = np.asarray(gpu_record).reshape(-1, 4)
     r = orc.diffraction_map_mesh(scene, tx, params, samples_per_wedge, surf_v, surf_t, mode="replay", record=rec,
-                                 slack=True)
+                                 slack=True, wedge_index=wedge_index)
     rep = r["report"]
     _log("diffraction_mesh", rep)
     assert rep["failures"] == 0, rep

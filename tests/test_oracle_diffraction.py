@@ -341,3 +341,24 @@ def test_wedge_subsets_partition_the_map(orc):
     assert np.allclose(total, full["map"], rtol=1e-12, atol=1e-12 * full["map"].max())
     with pytest.raises(ValueError):
         orc.diffraction_map(sc, tx, p, ns, wedge_index=[nw])
+
+
+def test_mesh_wedge_subsets_partition_the_map(orc):
+    """The same for the diffraction map on a mesh measurement surface."""
+    from test_oracle_mesh import grid_surface
+    sc, txs, p = S.workload(2)
+    tx = txs[0]
+    V, T = grid_surface(-64.0, -64.0, 8.0, 16, 16, lambda X, Y: 1.5 + 0.5 * np.sin(X / 9.0) * np.cos(Y / 7.0))
+    ns = 8
+    full = orc.diffraction_map_mesh(sc, tx, p, ns, V, T, want_record=True)
+    nw = len(orc.wedges(sc))
+    perm = np.random.default_rng(13).permutation(nw)
+    parts = [np.sort(perm[: nw // 2]), perm[nw // 2:]]
+    total = np.zeros_like(full["map"])
+    for idx in parts:
+        r = orc.diffraction_map_mesh(sc, tx, p, ns, V, T, want_record=True, wedge_index=idx)
+        rows = (idx[:, None] * ns + np.arange(ns)[None, :]).ravel()
+        assert np.array_equal(r["record"], full["record"][rows])
+        total += r["map"]
+    assert full["map"].max() > 0
+    assert np.allclose(total, full["map"], rtol=1e-12, atol=1e-12 * full["map"].max())
