@@ -207,3 +207,31 @@ def test_diffraction_ragged_sizes(orc, api, nsel, ns, ntx):
         for k, t in enumerate(tl):
             compare_diffraction(orc, sc, t, p, ns, maps[k], rec[k], wedge_index=idx)
     gs.free()
+
+
+def test_diffraction_mesh_city_wedge_subset(orc, api):
+    """The mesh-surface diffraction map on the largest scene: 300 wedges within
+    80 m of a city transmitter (16 samples each) onto a 4096-triangle surface
+    around it, replayed against the oracle through the city's SAH tree."""
+    from paper_2504_21719_b300 import _lib as L
+    from gpu_helpers import compare_diffraction_mesh
+    from test_oracle_mesh import grid_surface
+    sc, txs, p = S.workload(5)
+    tx = txs[0]
+    gs = api.Scene.from_obj(sc)
+    w, nw = gs.wedges()
+    raw = np.frombuffer(w, dtype=np.float32).reshape(-1, 18)[:nw]
+    near = np.flatnonzero(np.linalg.norm(raw[:, :2].astype(np.float64) - np.asarray(tx.pos[:2]), axis=1) < 80.0)
+    idx = np.random.default_rng(22).permutation(near)[:300]
+    sub = (L.rm_wedge * len(idx))(*[w[int(i)] for i in idx])
+    V, T = grid_surface(tx.pos[0] - 96.0, tx.pos[1] - 96.0, 6.0, 32, 64,
+                        lambda X, Y: 1.5 + 0.5 * np.sin(X / 9.0) * np.cos(Y / 7.0))
+    su = api.surface(V, T)
+    ns = 16
+    r = api.diffraction_map_mesh(gs, su, [tx], p, ns, wedges=(sub, len(idx)), record=True)
+    torch.cuda.synchronize()
+    rec = r["record"].cpu().numpy()
+    assert (rec[:, 0] == 0).sum() > 200 and r["stats"]["deposits"] > 50
+    compare_diffraction_mesh(orc, sc, tx, p, ns, V, T, r["maps"][0].cpu().numpy(), rec, wedge_index=idx)
+    su.free()
+    gs.free()
