@@ -253,3 +253,32 @@ def test_large_city_full_adjoint_partition(api):
         assert torch.all((a - b).abs() <= 1e-4 * scale), (key, a, b)
     assert torch.all(full["d_tx"] == 0)
     gs.free()
+
+
+def test_large_city_adjoint_with_array(orc, api):
+    """The adjoint with a steered 16-element uniform linear array (its factor from
+    the pre-pass in both the forward and the gradient call) on the city: a
+    lattice subset of one transmitter, depth 8, bilinear cells, against the
+    oracle's dual-number gradient along the certified GPU record."""
+    sc, txs, p = S.workload(5)
+    tx = copy.copy(txs[0])
+    tx.ray_stride, tx.ray_begin = 166_667, 3
+    tx.ant_pos, tx.precoding = S.uniform_linear_array(16, p.freq_hz, 0.5, axis=1, steer=(0.3, 1.0, -0.2))
+    p.deposit = 1
+    gs = api.Scene.from_obj(sc)
+    tgt = _target(api, sc, tx, p)
+    f = api.trace(gs, [tx], p, record=True)
+    loss, dLdC, valid = api.db_mse_loss(f["maps"][0], tgt)
+    assert int(valid) >= 100
+    a = api.grad(gs, [tx], p, dLdC.view(1, p.ny, p.nx), record=True)
+    assert torch.equal(f["record"], a["record"])
+    ad = np.concatenate([a["d_eps"].cpu().numpy(), a["d_sigma"].cpu().numpy(), a["d_tx"][0].cpu().numpy()])
+    rec = f["record"].view(tx.count(), p.max_depth + 1, 4).cpu().numpy()
+    compare_maps(orc, sc, tx, p, f["maps"][0].cpu().numpy(), rec)
+    de, ds, dt = orc.grad(sc, tx, p, rec, dLdC.double().cpu().numpy())
+    ref = np.concatenate([de, ds, dt])
+    assert np.abs(ref[:2 * sc.nm]).max() > 0
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    err = np.abs(ad - ref) / scale
+    assert np.all(err <= GRAD_RTOL), err
+    gs.free()
